@@ -1,0 +1,107 @@
+"""Exact solutions on a disk / ball, used to pin the oracle (test infrastructure).
+
+Each u solves  -Lap u + sigma u = f  with Dirichlet data (the source sign that
+Algorithm 1 uses), and each du/dtheta solves the differential BVP of
+Eq. (bvp_deriv):  (Lap - sigma) udot = 0,  udot = gdot - V_n du/dn  on the
+boundary.  For a disk of radius R with r(t) = R + sum a_m cos mt + b_m sin mt
+at a = b = 0, the normal velocity is V_n = 1 for R, cos mt for a_m and sin mt
+for b_m, and the motion is purely radial.  kappa = sqrt(sigma).
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.special import iv
+
+
+def polar(x):
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    return np.hypot(x[:, 0], x[:, 1]), np.arctan2(x[:, 1], x[:, 0])
+
+
+def disk_screened_const(x, R: float, sigma: float, g: float = 1.0, f: float = 0.0, n_modes: int = 8):
+    """Disk, constant data g, constant source f.  Returns u and du/dtheta for
+    theta = [R, a_1..a_M, b_1..b_M].
+      sigma > 0: u = f/s + (g - f/s) I0(k r)/I0(k R)
+      sigma = 0: u = g + f (R^2 - r^2)/4
+    Boundary value of udot: -V_n du/dn(R) with du/dn = (g - f/s) k I1(kR)/I0(kR)
+    (sigma > 0) or -f R/2 (sigma = 0); each Fourier mode extends harmonically
+    (I_m(kr)/I_m(kR) or (r/R)^m)."""
+    r, th = polar(x)
+    M = n_modes
+    out = np.zeros((r.size, 1 + 2 * M))
+    if sigma > 0:
+        k = np.sqrt(sigma)
+        c = g - f / sigma
+        u = f / sigma + c * iv(0, k * r) / iv(0, k * R)
+        dudn = c * k * iv(1, k * R) / iv(0, k * R)
+        ext = [iv(m, k * r) / iv(m, k * R) for m in range(M + 1)]
+    else:
+        u = g + f * (R * R - r * r) / 4.0
+        dudn = -f * R / 2.0
+        ext = [(r / R) ** m for m in range(M + 1)]
+    out[:, 0] = -dudn * ext[0]
+    for m in range(1, M + 1):
+        out[:, m] = -dudn * ext[m] * np.cos(m * th)
+        out[:, M + m] = -dudn * ext[m] * np.sin(m * th)
+    return u, out
+
+
+def disk_mapped_cos(x, R: float, n_modes: int = 8):
+    """Disk, sigma = 0, mapped data g(t) = cos t (fixed on the reference):
+    u = x / R.  du/dn = cos t / R, so udot = -V_n cos t / R on the boundary:
+      du/dR   = -x / R^2
+      du/da_m = -(1/2R) [(r/R)^(m+1) cos(m+1)th + (r/R)^|m-1| cos(m-1)th]
+      du/db_m = -(1/2R) [(r/R)^(m+1) sin(m+1)th + (r/R)^|m-1| sin(m-1)th]"""
+    r, th = polar(x)
+    M = n_modes
+    u = r * np.cos(th) / R
+    out = np.zeros((r.size, 1 + 2 * M))
+    out[:, 0] = -r * np.cos(th) / R ** 2
+    for m in range(1, M + 1):
+        a = (r / R) ** (m + 1)
+        b = (r / R) ** abs(m - 1)
+        out[:, m] = -(a * np.cos((m + 1) * th) + b * np.cos((m - 1) * th)) / (2 * R)
+        out[:, M + m] = -(a * np.sin((m + 1) * th) + b * np.sin((m - 1) * th)) / (2 * R)
+    return u, out
+
+
+def harmonic_field(x, field):
+    """u = g for restricted data g = c0 + c.x + x^T A x with trace(A) = 0, sigma = 0,
+    f = 0, on any domain; du/dtheta = 0 for every shape parameter."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    X = np.zeros((x.shape[0], 3))
+    X[:, :x.shape[1]] = x
+    c0, c, A6 = field[0], np.asarray(field[1:4]), np.asarray(field[4:10])
+    A = np.array([[A6[0], A6[3], A6[4]], [A6[3], A6[1], A6[5]], [A6[4], A6[5], A6[2]]])
+    return c0 + X @ c + np.einsum("ni,ij,nj->n", X, A, X)
+
+
+def ball_screened_const(x, R: float, sigma: float, g: float = 1.0, f: float = 0.0):
+    """Ball of radius R in 3D, constant data g and source f; theta = [R].
+      sigma > 0: u = f/s + (g - f/s) R sinh(k r) / (r sinh(k R)),
+                 du/dR = (g - f/s) R sinh(kr)/(r sinh kR) (1/R - k coth kR)
+      sigma = 0: u = g + f (R^2 - r^2)/6,  du/dR = f R / 3"""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    r = np.linalg.norm(x, axis=1)
+    if sigma > 0:
+        k = np.sqrt(sigma)
+        c = g - f / sigma
+        rs = np.where(r > 1e-12, r, 1e-12)
+        shape = np.where(r > 1e-12, R * np.sinh(k * rs) / (rs * np.sinh(k * R)), k * R / np.sinh(k * R))
+        u = f / sigma + c * shape
+        dudR = c * shape * (1.0 / R - k / np.tanh(k * R))
+    else:
+        u = g + f * (R * R - r * r) / 6.0
+        dudR = np.full_like(r, f * R / 3.0)
+    return u, dudR[:, None]
+
+
+def expected_exit_weight(dim: int, sigma: float, d: float) -> float:
+    """E over a uniform ball point of |B(d)| G_d(.): the solution at the centre of
+    -Lap w + sigma w = 1, w = 0 on the sphere, i.e. (1 - alpha)/sigma, or
+    d^2 / (2 dim) for sigma = 0."""
+    if sigma <= 0:
+        return d * d / (2.0 * dim)
+    k = np.sqrt(sigma) * d
+    alpha = 1.0 / iv(0, k) if dim == 2 else k / np.sinh(k)
+    return (1.0 - alpha) / sigma

@@ -1,0 +1,626 @@
+/*
+ * FP64 CPU oracle for Differential Walk on Spheres (Miller, Sawhney, Crane,
+ * Gkioulekas, ACM TOG 43(6), 2024).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file; only the tests, the smoke check and the CPU-baseline leg of
+ * the benchmark do.  It shares no code, header or constant table with the
+ * CUDA library: the random-number generator, the sampling formulas, the
+ * Green's-function weights and the closest-point queries below are written
+ * independently from their published definitions.
+ *
+ * Everything is double precision and deliberately naive: the closest point is
+ * a brute-force minimum over every boundary element, and each walk follows the
+ * steps of the paper's Algorithm 1 (WalkOnSpheres) or Algorithm 2
+ * (DiffWalkOnSpheres) in the paper's order.
+ *
+ * Readings of the paper that this file fixes (each is also listed in the
+ * design notes):
+ *  - Source sign.  Eq. (bvp) in Sec. 3.2 writes  Lap u - sigma u = f, but
+ *    Algorithm 1 adds +G f / p with the positive ball Green's function.  The
+ *    oracle follows the algorithm: f is the source of  -Lap u + sigma u = f.
+ *  - G and P on a ball are not printed (Sec. 3.3.1 defers to WoSt App. A).
+ *    They are derived here from the PDE:
+ *      3D: G(r) = sinh(k(R-r)) / (4 pi r sinh(kR)),      alpha = kR / sinh(kR)
+ *      2D: G(r) = (K0(kr) - K0(kR) I0(kr)/I0(kR)) / 2pi,  alpha = 1 / I0(kR)
+ *    with k = sqrt(sigma); sigma = 0 gives the Laplace limits and alpha = 1.
+ *  - Shell test is strict, d < eps (Algorithm 1 and 2).
+ *  - Russian roulette stops the walk when alpha < U (Algorithm 1 and 2); the
+ *    survivor keeps weight 1.
+ *  - BoundaryNormal (Algorithm 2) is the geometric normal of the closest
+ *    element, oriented so that n . (xbar - x) >= 0, i.e. away from the walk.
+ *  - Mapped boundary data (Eq. boundary_deriv_mapped): the reference data is
+ *    extended constant along the normal, so dg/dn = 0 and the tangential term
+ *    is  -grad_Gamma(g) . V  with V the interpolated vertex velocity.
+ *  - A walk phase that reaches max_steps distance queries is treated as if it
+ *    had reached the shell at its current closest point (kind CAPPED).
+ *
+ * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), keyed by
+ * the seed; counter = (walk id lo, walk id hi, step, (phase << 8) | block).
+ * Block 0 of a step gives the sphere direction (words 0, 1) and the roulette
+ * draw (word 2); block 1 gives the ball sample for the source (words 0, 1, 2).
+ * A 32-bit word x maps to the uniform ((x >> 9) * 2 + 1) * 2^-24 in (0, 1).
+ */
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+/* ---------------------------------------------------------------------------
+ * Philox4x32-10, written from the SC'11 paper's definition: ten rounds of two
+ * 32x32->64 multiplications, with a Weyl sequence bumping the 64-bit key.
+ * ------------------------------------------------------------------------- */
+void philox4x32_10(const uint32_t in_ctr[4], const uint32_t in_key[2], uint32_t out[4]) {
+    const uint64_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = in_ctr[0], c1 = in_ctr[1], c2 = in_ctr[2], c3 = in_ctr[3];
+    uint32_t k0 = in_key[0], k1 = in_key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += W0; k1 += W1; }
+        uint64_t p0 = M0 * (uint64_t)c0;
+        uint64_t p1 = M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+double to_uniform(uint32_t x) {
+    /* odd multiples of 2^-24 in (0, 1): never 0, never 1 */
+    return (double)((x >> 9) * 2u + 1u) * (1.0 / 16777216.0);
+}
+
+struct Draws { double u[3]; };
+
+Draws draw(uint32_t seed_lo, uint32_t seed_hi, uint64_t walk_id, uint32_t step,
+           uint32_t phase, uint32_t block) {
+    uint32_t ctr[4] = {(uint32_t)walk_id, (uint32_t)(walk_id >> 32), step, (phase << 8) | block};
+    uint32_t key[2] = {seed_lo, seed_hi};
+    uint32_t out[4];
+    philox4x32_10(ctr, key, out);
+    Draws d;
+    d.u[0] = to_uniform(out[0]);
+    d.u[1] = to_uniform(out[1]);
+    d.u[2] = to_uniform(out[2]);
+    return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+/* Scene description (own layout; unrelated to the CUDA library's header). */
+typedef struct {
+    int dim;                 /* 2: line segments, 3: triangles */
+    int n_vert;
+    const double* vert;      /* n_vert * dim */
+    int n_elem;
+    const int* elem;         /* n_elem * dim vertex ids */
+    int n_param;
+    const double* jac;       /* n_vert * dim * n_param, [v][k][j]; NULL: no shape params */
+    int data_kind;           /* 0: mapped per-vertex data, 1: restricted field */
+    const double* g_vert;    /* n_vert (mapped) */
+    const double* dg_vert;   /* n_vert * n_param or NULL (mapped) */
+    int field_kind;          /* unused by the formulas; kept for bookkeeping */
+    double field[10];        /* g = c0 + c.x + x^T A x: c0, c[3], Axx Ayy Azz Axy Axz Ayz */
+    double sigma;
+    double f;                /* constant source of -Lap u + sigma u = f */
+    double eps;
+    double h;
+    int K;                   /* nested forward walks per differential walk */
+    int max_steps;           /* distance queries per walk phase */
+    uint32_t seed_lo;
+    uint32_t seed_hi;
+} oracle_scene;
+
+enum { KIND_SHELL = 0, KIND_ROULETTE = 1, KIND_CAPPED = 2 };
+
+void oracle_philox4x32_10(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+    philox4x32_10(ctr, key, out);
+}
+
+double oracle_uniform(uint32_t x) { return to_uniform(x); }
+
+/* ---------------------------------------------------------------------------
+ * Closest point on one element.
+ * Segment: project onto the line, clamp the parameter to [0, 1].
+ * Triangle: the Voronoi-region case analysis of Ericson, Real-Time Collision
+ * Detection, Sec. 5.1.5 (vertex regions, edge regions, face region).
+ * Returns the squared distance; bary receives the weights of v1 (and v2).
+ * ------------------------------------------------------------------------- */
+static double closest_on_segment(const double* p, const double* a, const double* b,
+                                 double* xbar, double* bary) {
+    double ab[2] = {b[0] - a[0], b[1] - a[1]};
+    double ap[2] = {p[0] - a[0], p[1] - a[1]};
+    double len2 = ab[0] * ab[0] + ab[1] * ab[1];
+    double t = len2 > 0 ? (ap[0] * ab[0] + ap[1] * ab[1]) / len2 : 0.0;
+    if (t < 0) t = 0;
+    if (t > 1) t = 1;
+    xbar[0] = a[0] + t * ab[0];
+    xbar[1] = a[1] + t * ab[1];
+    bary[0] = t;
+    bary[1] = 0;
+    double dx = p[0] - xbar[0], dy = p[1] - xbar[1];
+    return dx * dx + dy * dy;
+}
+
+static inline double dot3(const double* u, const double* v) { return u[0] * v[0] + u[1] * v[1] + u[2] * v[2]; }
+
+static double closest_on_triangle(const double* p, const double* a, const double* b, const double* c,
+                                  double* xbar, double* bary) {
+    double ab[3], ac[3], ap[3];
+    for (int i = 0; i < 3; ++i) { ab[i] = b[i] - a[i]; ac[i] = c[i] - a[i]; ap[i] = p[i] - a[i]; }
+    double w1 = 0, w2 = 0;  /* weights of b and c */
+    double d1 = dot3(ab, ap), d2 = dot3(ac, ap);
+    if (d1 <= 0 && d2 <= 0) {                       /* vertex region a */
+        w1 = 0; w2 = 0;
+    } else {
+        double bp[3];
+        for (int i = 0; i < 3; ++i) bp[i] = p[i] - b[i];
+        double d3 = dot3(ab, bp), d4 = dot3(ac, bp);
+        if (d3 >= 0 && d4 <= d3) {                   /* vertex region b */
+            w1 = 1; w2 = 0;
+        } else {
+            double vc = d1 * d4 - d3 * d2;
+            if (vc <= 0 && d1 >= 0 && d3 <= 0) {     /* edge region ab */
+                w1 = d1 / (d1 - d3); w2 = 0;
+            } else {
+                double cp[3];
+                for (int i = 0; i < 3; ++i) cp[i] = p[i] - c[i];
+                double d5 = dot3(ab, cp), d6 = dot3(ac, cp);
+                if (d6 >= 0 && d5 <= d6) {           /* vertex region c */
+                    w1 = 0; w2 = 1;
+                } else {
+                    double vb = d5 * d2 - d1 * d6;
+                    if (vb <= 0 && d2 >= 0 && d6 <= 0) {   /* edge region ac */
+                        w1 = 0; w2 = d2 / (d2 - d6);
+                    } else {
+                        double va = d3 * d6 - d5 * d4;
+                        if (va <= 0 && (d4 - d3) >= 0 && (d5 - d6) >= 0) {  /* edge region bc */
+                            double t = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+                            w1 = 1 - t; w2 = t;
+                        } else {                      /* face region */
+                            double denom = 1.0 / (va + vb + vc);
+                            w1 = vb * denom; w2 = vc * denom;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    for (int i = 0; i < 3; ++i) xbar[i] = a[i] + w1 * ab[i] + w2 * ac[i];
+    bary[0] = w1;
+    bary[1] = w2;
+    double dd = 0;
+    for (int i = 0; i < 3; ++i) { double t = p[i] - xbar[i]; dd += t * t; }
+    return dd;
+}
+
+/* DistanceToBoundary (Algorithm 1): brute force over every element.  Ties go
+ * to the smaller element index (strict < keeps the first minimum). */
+static double closest_point(const oracle_scene* s, const double* p, double* xbar, int* e_out, double* bary) {
+    double best = INFINITY;
+    int best_e = -1;
+    double bx[3] = {0, 0, 0}, bb[2] = {0, 0};
+    for (int e = 0; e < s->n_elem; ++e) {
+        double xb[3] = {0, 0, 0}, b2[2];
+        double d2;
+        if (s->dim == 2) {
+            const int* el = s->elem + 2 * e;
+            d2 = closest_on_segment(p, s->vert + 2 * el[0], s->vert + 2 * el[1], xb, b2);
+        } else {
+            const int* el = s->elem + 3 * e;
+            d2 = closest_on_triangle(p, s->vert + 3 * el[0], s->vert + 3 * el[1], s->vert + 3 * el[2], xb, b2);
+        }
+        if (d2 < best) {
+            best = d2; best_e = e;
+            bx[0] = xb[0]; bx[1] = xb[1]; bx[2] = xb[2];
+            bb[0] = b2[0]; bb[1] = b2[1];
+        }
+    }
+    for (int i = 0; i < s->dim; ++i) xbar[i] = bx[i];
+    bary[0] = bb[0];
+    bary[1] = bb[1];
+    *e_out = best_e;
+    return std::sqrt(best);
+}
+
+int oracle_closest_point(const oracle_scene* s, int n, const double* p, double* dist,
+                         double* xbar, int* elem, double* bary) {
+    for (int i = 0; i < n; ++i) {
+        double xb[3], b2[2];
+        int e;
+        dist[i] = closest_point(s, p + (size_t)i * s->dim, xb, &e, b2);
+        for (int k = 0; k < s->dim; ++k) xbar[(size_t)i * s->dim + k] = xb[k];
+        elem[i] = e;
+        bary[2 * (size_t)i] = b2[0];
+        bary[2 * (size_t)i + 1] = b2[1];
+    }
+    return 0;
+}
+
+/* Weights of the element's vertices at barycentric point (bary). */
+static void vertex_weights(int dim, const double* bary, double* w) {
+    if (dim == 2) { w[0] = 1 - bary[0]; w[1] = bary[0]; w[2] = 0; }
+    else { w[0] = 1 - bary[0] - bary[1]; w[1] = bary[0]; w[2] = bary[1]; }
+}
+
+/* Restricted field data g = c0 + c.x + x^T A x and its spatial gradient. */
+static double field_value(const oracle_scene* s, const double* x, double* grad) {
+    const double* c = s->field;
+    double X[3] = {x[0], x[1], s->dim == 3 ? x[2] : 0.0};
+    double A[3][3] = {{c[4], c[7], c[8]}, {c[7], c[5], c[9]}, {c[8], c[9], c[6]}};
+    double g = c[0];
+    for (int i = 0; i < 3; ++i) {
+        g += c[1 + i] * X[i];
+        double Ax = 0;
+        for (int j = 0; j < 3; ++j) Ax += A[i][j] * X[j];
+        g += X[i] * Ax;
+        grad[i] = c[1 + i] + 2 * Ax;
+    }
+    return g;
+}
+
+/* Dirichlet value g at a boundary point. */
+static double dirichlet_value(const oracle_scene* s, int e, const double* bary, const double* xbar) {
+    if (s->data_kind == 1) {
+        double grad[3];
+        return field_value(s, xbar, grad);
+    }
+    double w[3];
+    vertex_weights(s->dim, bary, w);
+    const int* el = s->elem + (size_t)s->dim * e;
+    double g = 0;
+    for (int i = 0; i < s->dim; ++i) g += w[i] * s->g_vert[el[i]];
+    return g;
+}
+
+/* Geometric unit normal of element e (unoriented). */
+static void element_normal(const oracle_scene* s, int e, double* n) {
+    const int* el = s->elem + (size_t)s->dim * e;
+    if (s->dim == 2) {
+        const double* a = s->vert + 2 * el[0];
+        const double* b = s->vert + 2 * el[1];
+        double tx = b[0] - a[0], ty = b[1] - a[1];
+        double L = std::sqrt(tx * tx + ty * ty);
+        n[0] = ty / L; n[1] = -tx / L; n[2] = 0;
+    } else {
+        const double* a = s->vert + 3 * el[0];
+        const double* b = s->vert + 3 * el[1];
+        const double* c = s->vert + 3 * el[2];
+        double u[3], v[3];
+        for (int i = 0; i < 3; ++i) { u[i] = b[i] - a[i]; v[i] = c[i] - a[i]; }
+        double cr[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+        double L = std::sqrt(dot3(cr, cr));
+        for (int i = 0; i < 3; ++i) n[i] = cr[i] / L;
+    }
+}
+
+/* Tangential gradient of the linearly interpolated vertex data on element e. */
+static void surface_gradient(const oracle_scene* s, int e, double* grad) {
+    const int* el = s->elem + (size_t)s->dim * e;
+    grad[0] = grad[1] = grad[2] = 0;
+    if (s->dim == 2) {
+        const double* a = s->vert + 2 * el[0];
+        const double* b = s->vert + 2 * el[1];
+        double tx = b[0] - a[0], ty = b[1] - a[1];
+        double L2 = tx * tx + ty * ty;
+        double dg = s->g_vert[el[1]] - s->g_vert[el[0]];
+        grad[0] = dg * tx / L2;
+        grad[1] = dg * ty / L2;
+    } else {
+        const double* a = s->vert + 3 * el[0];
+        const double* b = s->vert + 3 * el[1];
+        const double* c = s->vert + 3 * el[2];
+        double e1[3], e2[3];
+        for (int i = 0; i < 3; ++i) { e1[i] = b[i] - a[i]; e2[i] = c[i] - a[i]; }
+        double g11 = dot3(e1, e1), g12 = dot3(e1, e2), g22 = dot3(e2, e2);
+        double det = g11 * g22 - g12 * g12;
+        double r1 = s->g_vert[el[1]] - s->g_vert[el[0]];
+        double r2 = s->g_vert[el[2]] - s->g_vert[el[0]];
+        /* coefficients of grad in the (e1, e2) basis: G^{-1} (r1, r2) */
+        double a1 = (g22 * r1 - g12 * r2) / det;
+        double a2 = (-g12 * r1 + g11 * r2) / det;
+        for (int i = 0; i < 3; ++i) grad[i] = a1 * e1[i] + a2 * e2[i];
+    }
+}
+
+/* Recursive weight alpha = P(d) |dB(d)| of Algorithm 1, line "alpha <- P / p". */
+double oracle_alpha(int dim, double sigma, double d) {
+    if (sigma <= 0) return 1.0;
+    double kd = std::sqrt(sigma) * d;
+    if (dim == 2) return 1.0 / std::cyl_bessel_i(0.0, kd);
+    return kd / std::sinh(kd);
+}
+
+/* |B(d)| * G_d(r) with r = rho * d: the source weight of Algorithm 1 per unit f. */
+double oracle_source_weight(int dim, double sigma, double d, double rho) {
+    double r = rho * d;
+    if (dim == 2) {
+        double vol = kPi * d * d;
+        double G;
+        if (sigma <= 0) {
+            G = std::log(d / r) / (2 * kPi);
+        } else {
+            double k = std::sqrt(sigma);
+            G = (std::cyl_bessel_k(0.0, k * r)
+                 - std::cyl_bessel_k(0.0, k * d) * std::cyl_bessel_i(0.0, k * r) / std::cyl_bessel_i(0.0, k * d))
+                / (2 * kPi);
+        }
+        return vol * G;
+    }
+    double vol = 4.0 / 3.0 * kPi * d * d * d;
+    double G;
+    if (sigma <= 0) {
+        G = (1.0 / r - 1.0 / d) / (4 * kPi);
+    } else {
+        double k = std::sqrt(sigma);
+        G = std::sinh(k * (d - r)) / (4 * kPi * r * std::sinh(k * d));
+    }
+    return vol * G;
+}
+
+/* Uniform direction on the unit circle / sphere and uniform point in the ball. */
+static void sample_sphere(int dim, const Draws& r, double* w) {
+    if (dim == 2) {
+        double t = 2 * kPi * r.u[0];
+        w[0] = std::cos(t); w[1] = std::sin(t); w[2] = 0;
+    } else {
+        double z = 1 - 2 * r.u[0];
+        double st = 2 * std::sqrt(r.u[0] * (1 - r.u[0]));
+        double ph = 2 * kPi * r.u[1];
+        w[0] = st * std::cos(ph); w[1] = st * std::sin(ph); w[2] = z;
+    }
+}
+
+static double sample_ball_radius(int dim, const Draws& r) {
+    return dim == 2 ? std::sqrt(r.u[2]) : std::cbrt(r.u[2]);
+}
+
+struct PhaseResult {
+    double u;          /* estimate from this phase */
+    int kind;          /* KIND_* */
+    int steps;         /* distance queries */
+    int e;             /* terminal element */
+    double bary[2];
+    double xbar[3];
+    double x_last[3];  /* walk point at termination */
+};
+
+/* Algorithm 1 (WalkOnSpheres) with Russian roulette, iterated instead of
+ * recursed.  acc collects the source estimates S of every step. */
+static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_t walk_id, uint32_t phase) {
+    PhaseResult res;
+    double x[3] = {x0[0], x0[1], s->dim == 3 ? x0[2] : 0.0};
+    double acc = 0;
+    for (int k = 0;; ++k) {
+        double xbar[3] = {0, 0, 0}, bary[2];
+        int e;
+        double d = closest_point(s, x, xbar, &e, bary);
+        bool shell = d < s->eps;
+        if (shell || k >= s->max_steps) {
+            res.u = acc + dirichlet_value(s, e, bary, xbar);
+            res.kind = shell ? KIND_SHELL : KIND_CAPPED;
+            res.steps = k + 1;
+            res.e = e;
+            res.bary[0] = bary[0]; res.bary[1] = bary[1];
+            for (int i = 0; i < 3; ++i) { res.xbar[i] = xbar[i]; res.x_last[i] = x[i]; }
+            return res;
+        }
+        if (s->f != 0) {
+            Draws rb = draw(s->seed_lo, s->seed_hi, walk_id, (uint32_t)k, phase, 1);
+            double rho = sample_ball_radius(s->dim, rb);
+            acc += oracle_source_weight(s->dim, s->sigma, d, rho) * s->f;
+        }
+        Draws r0 = draw(s->seed_lo, s->seed_hi, walk_id, (uint32_t)k, phase, 0);
+        double alpha = oracle_alpha(s->dim, s->sigma, d);
+        if (alpha < r0.u[2]) {
+            res.u = acc;
+            res.kind = KIND_ROULETTE;
+            res.steps = k + 1;
+            res.e = -1;
+            res.bary[0] = res.bary[1] = 0;
+            for (int i = 0; i < 3; ++i) { res.xbar[i] = 0; res.x_last[i] = x[i]; }
+            return res;
+        }
+        double w[3];
+        sample_sphere(s->dim, r0, w);
+        for (int i = 0; i < s->dim; ++i) x[i] += d * w[i];
+    }
+}
+
+/* Per-walk outputs; any pointer may be NULL. */
+typedef struct {
+    double* u_hat;     /* n: forward estimate of u at the query point */
+    double* udot;      /* n * n_param: differential estimate */
+    double* dudn;      /* n: (g(xbar) - mean nested u) / h */
+    double* u_off;     /* n: mean of the nested walks */
+    int* elem;         /* n: terminal element of the differential walk (-1: roulette) */
+    double* bary;      /* n * 2 */
+    double* normal;    /* n * 3 */
+    double* xbar;      /* n * 3 */
+    int* kind;         /* n * (K + 1) */
+    int* steps;        /* n * (K + 1) */
+} oracle_walk_out;
+
+/* Algorithm 2 (DiffWalkOnSpheres) extended, as Sec. 4.1 observation 2
+ * describes, to also return u from the same path (source sum + g(xbar)).
+ * With mode 0 only Algorithm 1 runs (no nested walks, no derivative). */
+static void run_one(const oracle_scene* s, const double* x0, uint64_t walk_id, int mode,
+                    const oracle_walk_out* o, size_t idx) {
+    int P = s->n_param;
+    int slots = s->K + 1;
+    PhaseResult main = forward_walk(s, x0, walk_id, 0);
+    if (o->u_hat) o->u_hat[idx] = main.u;
+    if (o->kind) { o->kind[idx * slots] = main.kind; }
+    if (o->steps) { o->steps[idx * slots] = main.steps; }
+    if (o->elem) o->elem[idx] = main.e;
+    if (o->bary) { o->bary[2 * idx] = main.bary[0]; o->bary[2 * idx + 1] = main.bary[1]; }
+    if (o->xbar) for (int i = 0; i < 3; ++i) o->xbar[3 * idx + i] = main.xbar[i];
+    if (mode == 0) return;
+    for (int j = 1; j <= s->K; ++j) {
+        if (o->kind) o->kind[idx * slots + j] = -1;
+        if (o->steps) o->steps[idx * slots + j] = 0;
+    }
+    if (o->udot) for (int j = 0; j < P; ++j) o->udot[idx * P + j] = 0;
+    if (o->dudn) o->dudn[idx] = 0;
+    if (o->u_off) o->u_off[idx] = 0;
+    if (o->normal) for (int i = 0; i < 3; ++i) o->normal[3 * idx + i] = 0;
+    if (main.kind == KIND_ROULETTE) return;   /* Algorithm 2: roulette returns 0 */
+
+    /* BoundaryNormal, oriented away from the walk point */
+    double n[3];
+    element_normal(s, main.e, n);
+    double side = 0;
+    for (int i = 0; i < s->dim; ++i) side += n[i] * (main.xbar[i] - main.x_last[i]);
+    if (side < 0) for (int i = 0; i < 3; ++i) n[i] = -n[i];
+
+    /* offset point and nested forward walks */
+    double xoff[3] = {0, 0, 0};
+    for (int i = 0; i < s->dim; ++i) xoff[i] = main.xbar[i] - s->h * n[i];
+    double sum = 0;
+    for (int j = 1; j <= s->K; ++j) {
+        PhaseResult nr = forward_walk(s, xoff, walk_id, (uint32_t)j);
+        sum += nr.u;
+        if (o->kind) o->kind[idx * slots + j] = nr.kind;
+        if (o->steps) o->steps[idx * slots + j] = nr.steps;
+    }
+    double ubar = sum / s->K;
+    double g = dirichlet_value(s, main.e, main.bary, main.xbar);
+    double dudn = (g - ubar) / s->h;     /* Eq. (dudn_fd_estimate) */
+    if (o->dudn) o->dudn[idx] = dudn;
+    if (o->u_off) o->u_off[idx] = ubar;
+    if (o->normal) for (int i = 0; i < 3; ++i) o->normal[3 * idx + i] = n[i];
+
+    if (!o->udot || P == 0) return;
+    /* V_n and the velocity V at xbar, per parameter (explicit surface, Sec. 3.1.2) */
+    double w[3];
+    vertex_weights(s->dim, main.bary, w);
+    const int* el = s->elem + (size_t)s->dim * main.e;
+    double gradg[3] = {0, 0, 0};
+    double dgdn = 0;
+    if (s->data_kind == 1) {
+        field_value(s, main.xbar, gradg);
+        for (int i = 0; i < s->dim; ++i) dgdn += n[i] * gradg[i];
+    } else {
+        surface_gradient(s, main.e, gradg);
+    }
+    for (int j = 0; j < P; ++j) {
+        double V[3] = {0, 0, 0};
+        if (s->jac) {
+            for (int a = 0; a < s->dim; ++a) {
+                const double* J = s->jac + ((size_t)el[a] * s->dim) * P;
+                for (int k = 0; k < s->dim; ++k) V[k] += w[a] * J[(size_t)k * P + j];
+            }
+        }
+        double Vn = 0;
+        for (int k = 0; k < s->dim; ++k) Vn += n[k] * V[k];
+        double gdot;
+        if (s->data_kind == 1) {
+            /* Eq. (boundary_deriv_restricted) with a parameter-free field */
+            gdot = dgdn * Vn;
+        } else {
+            /* Eq. (boundary_deriv_mapped) with dg/dn = 0 */
+            double gt = 0;
+            if (s->dg_vert)
+                for (int a = 0; a < s->dim; ++a) gt += w[a] * s->dg_vert[(size_t)el[a] * P + j];
+            double tang = 0;
+            for (int k = 0; k < s->dim; ++k) tang += gradg[k] * V[k];
+            gdot = gt - tang;
+        }
+        /* Eq. (wos_deriv), shell case */
+        o->udot[idx * P + j] = gdot - Vn * dudn;
+    }
+}
+
+/* Runs walks_per_point walks from each query point.  Walk (p, w) has global
+ * id walk_id_base + p * walks_per_point + w and writes output row
+ * p * walks_per_point + w.  mode 0: Algorithm 1 only; mode 1: Algorithm 2. */
+int oracle_run_walks(const oracle_scene* s, int n_query, const double* xq, int walks_per_point,
+                     uint64_t walk_id_base, int mode, int n_threads, const oracle_walk_out* o) {
+    if (!s || !xq || !o || n_query < 0 || walks_per_point < 0) return 1;
+    if (s->dim != 2 && s->dim != 3) return 1;
+    if (mode == 1 && s->K < 1) return 1;
+    long long total = (long long)n_query * walks_per_point;
+#ifdef _OPENMP
+    int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nt)
+#endif
+    for (long long i = 0; i < total; ++i) {
+        long long p = i / walks_per_point;
+        run_one(s, xq + (size_t)p * s->dim, walk_id_base + (uint64_t)i, mode, o, (size_t)i);
+    }
+    (void)n_threads;
+    return 0;
+}
+
+/* Inside test by ray parity: count crossings of the ray x + t dir (t > 0)
+ * with every element; odd means inside the region the boundary encloses. */
+int oracle_inside(const oracle_scene* s, int n, const double* xq, int* inside) {
+    const double d2[2] = {0.6180339887498949, 0.7861513777574233};
+    const double d3[3] = {0.5773502691896258 * 0.9, 0.5773502691896258 * 1.1, 0.0};
+    double dir3[3] = {d3[0], d3[1], std::sqrt(1 - d3[0] * d3[0] - d3[1] * d3[1])};
+    for (int i = 0; i < n; ++i) {
+        const double* p = xq + (size_t)i * s->dim;
+        int count = 0;
+        for (int e = 0; e < s->n_elem; ++e) {
+            if (s->dim == 2) {
+                const int* el = s->elem + 2 * e;
+                const double* a = s->vert + 2 * el[0];
+                const double* b = s->vert + 2 * el[1];
+                /* solve p + t d = a + u (b - a) */
+                double ex = b[0] - a[0], ey = b[1] - a[1];
+                double det = -d2[0] * ey + d2[1] * ex;
+                if (det == 0) continue;
+                double rx = a[0] - p[0], ry = a[1] - p[1];
+                double t = (-rx * ey + ry * ex) / det;
+                double u = (d2[0] * ry - d2[1] * rx) / det;
+                if (t > 0 && u >= 0 && u < 1) ++count;
+            } else {
+                const int* el = s->elem + 3 * e;
+                const double* a = s->vert + 3 * el[0];
+                const double* b = s->vert + 3 * el[1];
+                const double* c = s->vert + 3 * el[2];
+                double e1[3], e2[3], tv[3];
+                for (int k = 0; k < 3; ++k) { e1[k] = b[k] - a[k]; e2[k] = c[k] - a[k]; tv[k] = p[k] - a[k]; }
+                double pv[3] = {dir3[1] * e2[2] - dir3[2] * e2[1], dir3[2] * e2[0] - dir3[0] * e2[2],
+                                dir3[0] * e2[1] - dir3[1] * e2[0]};
+                double det = dot3(e1, pv);
+                if (det == 0) continue;
+                double u = dot3(tv, pv) / det;
+                if (u < 0 || u > 1) continue;
+                double qv[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2],
+                                tv[0] * e1[1] - tv[1] * e1[0]};
+                double v = dot3(dir3, qv) / det;
+                if (v < 0 || u + v > 1) continue;
+                double t = dot3(e2, qv) / det;
+                if (t > 0) ++count;
+            }
+        }
+        inside[i] = count & 1;
+    }
+    return 0;
+}
+
+int oracle_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+}  /* extern "C" */

@@ -1,0 +1,325 @@
+"""Seeded synthetic scenes for the walk-on-spheres workloads.
+
+This module builds geometry and parameterisations only: polygons, star curves,
+geodesic icospheres perturbed by spherical harmonics, the per-vertex parameter
+Jacobians dv/dtheta of the explicit-surface parameterisation (Sec. 3.1.2), and
+query points.  It contains none of the estimator's arithmetic, so that the CUDA
+path and the FP64 oracle can both be fed from it.  Every array is float64 /
+int32 numpy; the CUDA binding casts to float32 itself.
+
+Scenes (all seeds fixed; geometry seed 0x2405):
+  disk_scene       128-gon of radius R with radial Fourier parameters
+  star_box_scene   star-shaped emitter inside the box [-1, 1]^2
+  sh_sphere_scene  SH-perturbed icosphere inside the box [-2, 2]^3
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field as dc_field
+from math import factorial
+from typing import Optional
+
+import numpy as np
+
+GEOMETRY_SEED = 0x2405
+PHILOX_SEED = 0x12964
+
+
+@dataclass
+class Scene:
+    """Boundary, data and PDE of one Dirichlet screened-Poisson problem.
+
+    vert   (n_vert, dim) float64     elem  (n_elem, dim) int32
+    jac    (n_vert, dim, N) float64 or None: dv/dtheta per vertex
+    data   'mapped' with g_vert (n_vert,) [and dg_vert (n_vert, N)], or
+           'field' with field = [c0, c(3), Axx, Ayy, Azz, Axy, Axz, Ayz]
+    sigma  screening; f: constant source of -Lap u + sigma u = f
+    eps    shell width; h: normal-derivative offset; K: nested walks
+    query  (n_query, dim) float64; walks: walks per query point
+    """
+    name: str
+    vert: np.ndarray
+    elem: np.ndarray
+    jac: Optional[np.ndarray]
+    data: str = "mapped"
+    g_vert: Optional[np.ndarray] = None
+    dg_vert: Optional[np.ndarray] = None
+    field: Optional[np.ndarray] = None
+    sigma: float = 0.0
+    f: float = 0.0
+    eps: float = 1e-3
+    h: float = 1e-2
+    K: int = 1
+    B: int = 8
+    query: Optional[np.ndarray] = None
+    walks: int = 1024
+    u_ref: Optional[np.ndarray] = None
+    seed: int = PHILOX_SEED
+    meta: dict = dc_field(default_factory=dict)
+
+    @property
+    def dim(self) -> int:
+        return int(self.vert.shape[1])
+
+    @property
+    def n_param(self) -> int:
+        return 0 if self.jac is None else int(self.jac.shape[2])
+
+
+def _field(c0=0.0, c=(0.0, 0.0, 0.0), A=(0.0, 0.0, 0.0, 0.0, 0.0, 0.0)) -> np.ndarray:
+    return np.array([c0, *c, *A], dtype=np.float64)
+
+
+# ---------------------------------------------------------------------------- 2D
+def radial_polygon(n_seg: int, radius_fn, center=(0.0, 0.0)):
+    t = 2 * np.pi * np.arange(n_seg) / n_seg
+    r = radius_fn(t)
+    vert = np.stack([center[0] + r * np.cos(t), center[1] + r * np.sin(t)], axis=1)
+    elem = np.stack([np.arange(n_seg), (np.arange(n_seg) + 1) % n_seg], axis=1).astype(np.int32)
+    return t, vert, elem
+
+
+def fourier_jacobian(t: np.ndarray, scale: float, n_modes: int, with_radius: bool) -> np.ndarray:
+    """dv/dtheta for v(t) = r(t) (cos t, sin t),
+    r = [R] + scale * sum_k a_k cos kt + b_k sin kt;  theta = [R,] a_1..a_M, b_1..b_M."""
+    radial = np.stack([np.cos(t), np.sin(t)], axis=1)
+    cols = []
+    if with_radius:
+        cols.append(radial)
+    for k in range(1, n_modes + 1):
+        cols.append(scale * np.cos(k * t)[:, None] * radial)
+    for k in range(1, n_modes + 1):
+        cols.append(scale * np.sin(k * t)[:, None] * radial)
+    return np.stack(cols, axis=2)
+
+
+def disk_points(n: int, r_max: float, seed: int) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    r = r_max * np.sqrt(rng.random(n))
+    a = 2 * np.pi * rng.random(n)
+    return np.stack([r * np.cos(a), r * np.sin(a)], axis=1)
+
+
+def disk_scene(variant: str = "laplace_x", n_seg: int = 128, R: float = 1.0, n_modes: int = 8,
+               n_query: int = 64, walks: int = 1024, eps: float = 1e-3, h: float = 1e-2,
+               K: int = 1, seed: int = GEOMETRY_SEED) -> Scene:
+    """Unit-disk 128-gon, theta = [R, a_1..a_8, b_1..b_8] (all 0 at the scene).
+
+    variant 'laplace_x': sigma = 0, restricted data g = x  (u = x, du/dtheta = 0)
+    variant 'screened_1': sigma = 4, g = 1  (u = I0(2r)/I0(2R))
+    variant 'mapped_cos': sigma = 0, mapped data g_v = cos t_v  (u = x/R)
+    """
+    t, vert, elem = radial_polygon(n_seg, lambda t: np.full_like(t, R))
+    jac = fourier_jacobian(t, 1.0, n_modes, with_radius=True)
+    q = disk_points(n_query, 0.9 * R, seed)
+    if variant == "laplace_x":
+        sc = Scene("disk_laplace_x", vert, elem, jac, data="field", field=_field(c=(1.0, 0.0, 0.0)),
+                   sigma=0.0)
+    elif variant == "screened_1":
+        sc = Scene("disk_screened_1", vert, elem, jac, data="mapped", g_vert=np.ones(n_seg), sigma=4.0)
+    elif variant == "mapped_cos":
+        sc = Scene("disk_mapped_cos", vert, elem, jac, data="mapped", g_vert=np.cos(t), sigma=0.0)
+    else:
+        raise ValueError(variant)
+    sc.eps, sc.h, sc.K, sc.query, sc.walks = eps, h, K, q, walks
+    sc.meta = {"R": R, "t": t, "n_modes": n_modes}
+    return sc
+
+
+def box2d():
+    vert = np.array([[-1.0, -1.0], [1.0, -1.0], [1.0, 1.0], [-1.0, 1.0]])
+    elem = np.array([[0, 1], [1, 2], [2, 3], [3, 0]], dtype=np.int32)
+    return vert, elem
+
+
+def box_perimeter_points(n: int, half: float) -> np.ndarray:
+    """n points evenly spaced by arclength on the square |x|_inf = half."""
+    side = 2 * half
+    s = (np.arange(n) + 0.5) * (4 * side / n)
+    pts = np.zeros((n, 2))
+    for i, si in enumerate(s):
+        k, r = int(si // side), si % side
+        if k == 0:
+            pts[i] = (-half + r, -half)
+        elif k == 1:
+            pts[i] = (half, -half + r)
+        elif k == 2:
+            pts[i] = (half - r, half)
+        else:
+            pts[i] = (-half, half - r)
+    return pts
+
+
+def star_box_scene(n_seg: int = 4096, n_modes: int = 32, coef_std: float = 0.02, base_r: float = 0.3,
+                   sigma: float = 10.0, n_query: int = 256, walks: int = 4096, K: int = 2,
+                   coeffs: Optional[np.ndarray] = None, seed: int = GEOMETRY_SEED) -> Scene:
+    """Shape-from-diffusion in 2D: box [-1,1]^2 (g = 0) around a star emitter (g = 1).
+
+    r(t) = base_r (1 + sum_k a_k cos kt + b_k sin kt); theta = [a_1..a_32, b_1..b_32].
+    eps = 1e-3 x the bounding-cube side (2), h = 10 eps.  Observation points:
+    256 points by arclength on |x|_inf = 0.9.  u_ref is the target profile of a
+    round emitter of radius base_r in free space, K0(k|x|)/K0(k base_r).
+    """
+    rng = np.random.default_rng(seed)
+    if coeffs is None:
+        coeffs = rng.normal(0.0, coef_std, size=2 * n_modes)
+    a, b = coeffs[:n_modes], coeffs[n_modes:]
+    k = np.arange(1, n_modes + 1)
+
+    def radius(t):
+        return base_r * (1 + np.cos(np.outer(t, k)) @ a + np.sin(np.outer(t, k)) @ b)
+
+    t, sv, se = radial_polygon(n_seg, radius)
+    bv, be = box2d()
+    vert = np.concatenate([bv, sv], axis=0)
+    elem = np.concatenate([be, se + 4], axis=0).astype(np.int32)
+    jac = np.zeros((vert.shape[0], 2, 2 * n_modes))
+    jac[4:] = fourier_jacobian(t, base_r, n_modes, with_radius=False)
+    g = np.concatenate([np.zeros(4), np.ones(n_seg)])
+    q = box_perimeter_points(n_query, 0.9)
+    from scipy.special import k0
+    kap = np.sqrt(sigma)
+    u_ref = k0(kap * np.linalg.norm(q, axis=1)) / k0(kap * base_r)
+    eps = 1e-3 * 2.0
+    sc = Scene("star_box", vert, elem, jac, data="mapped", g_vert=g, sigma=sigma, eps=eps, h=10 * eps,
+               K=K, query=q, walks=walks, u_ref=u_ref)
+    sc.meta = {"t": t, "coeffs": coeffs, "base_r": base_r}
+    return sc
+
+
+# ---------------------------------------------------------------------------- 3D
+def icosahedron():
+    p = (1 + 5 ** 0.5) / 2
+    v = np.array([[-1, p, 0], [1, p, 0], [-1, -p, 0], [1, -p, 0], [0, -1, p], [0, 1, p],
+                  [0, -1, -p], [0, 1, -p], [p, 0, -1], [p, 0, 1], [-p, 0, -1], [-p, 0, 1]], float)
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    f = np.array([[0, 11, 5], [0, 5, 1], [0, 1, 7], [0, 7, 10], [0, 10, 11], [1, 5, 9], [5, 11, 4],
+                  [11, 10, 2], [10, 7, 6], [7, 1, 8], [3, 9, 4], [3, 4, 2], [3, 2, 6], [3, 6, 8],
+                  [3, 8, 9], [4, 9, 5], [2, 4, 11], [6, 2, 10], [8, 6, 7], [9, 8, 1]], dtype=np.int64)
+    return v, f
+
+
+def icosphere(freq: int):
+    """Geodesic icosphere: each icosahedron face split into freq^2 triangles,
+    vertices projected to the unit sphere (20 freq^2 faces, 10 freq^2 + 2 vertices)."""
+    v0, f0 = icosahedron()
+    ii, jj = [], []
+    for i in range(freq + 1):
+        for j in range(freq + 1 - i):
+            ii.append(i)
+            jj.append(j)
+    ii, jj = np.array(ii), np.array(jj)
+    index = -np.ones((freq + 1, freq + 1), dtype=np.int64)
+    index[ii, jj] = np.arange(len(ii))
+    tris = []
+    for i in range(freq):
+        for j in range(freq - i):
+            tris.append((index[i, j], index[i + 1, j], index[i, j + 1]))
+            if i + j < freq - 1:
+                tris.append((index[i + 1, j], index[i + 1, j + 1], index[i, j + 1]))
+    tris = np.array(tris, dtype=np.int64)
+    A, B, C = v0[f0[:, 0]], v0[f0[:, 1]], v0[f0[:, 2]]
+    pts = (A[:, None, :] + (ii / freq)[None, :, None] * (B - A)[:, None, :]
+           + (jj / freq)[None, :, None] * (C - A)[:, None, :])
+    pts /= np.linalg.norm(pts, axis=2, keepdims=True)
+    n_local = len(ii)
+    faces = (tris[None, :, :] + (np.arange(20) * n_local)[:, None, None]).reshape(-1, 3)
+    flat = pts.reshape(-1, 3)
+    key = np.round(flat * 1e9).astype(np.int64)
+    _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    vert = flat[first]
+    faces = inv.reshape(-1)[faces]
+    return vert, faces.astype(np.int32)
+
+
+def real_sh(lmax: int, dirs: np.ndarray) -> np.ndarray:
+    """Orthonormal real spherical harmonics Y_lm(dirs), (n, (lmax+1)^2), order (l, m=-l..l)."""
+    from scipy.special import lpmv
+    x, y, z = dirs[:, 0], dirs[:, 1], dirs[:, 2]
+    ct = np.clip(z, -1.0, 1.0)
+    phi = np.arctan2(y, x)
+    out = np.zeros((dirs.shape[0], (lmax + 1) ** 2))
+    col = 0
+    for l in range(lmax + 1):
+        for m in range(-l, l + 1):
+            am = abs(m)
+            norm = np.sqrt((2 * l + 1) / (4 * np.pi) * factorial(l - am) / factorial(l + am))
+            P = lpmv(am, l, ct)
+            if m > 0:
+                out[:, col] = np.sqrt(2) * norm * P * np.cos(am * phi)
+            elif m < 0:
+                out[:, col] = np.sqrt(2) * norm * P * np.sin(am * phi)
+            else:
+                out[:, col] = norm * P
+            col += 1
+    return out
+
+
+def box3d(half: float):
+    c = np.array([[x, y, z] for z in (-half, half) for y in (-half, half) for x in (-half, half)], float)
+    # corners: index = x + 2y + 4z (0/1 for -/+)
+    quads = [(0, 2, 3, 1), (4, 5, 7, 6), (0, 1, 5, 4), (2, 6, 7, 3), (0, 4, 6, 2), (1, 3, 7, 5)]
+    tris = []
+    for a, b, c2, d in quads:
+        tris.append((a, b, c2))
+        tris.append((a, c2, d))
+    return c, np.array(tris, dtype=np.int32)
+
+
+def sh_sphere_scene(freq: int = 100, lmax: int = 8, coef_std: float = 0.01, sigma: float = 1.0,
+                    f: float = 0.5, n_query: int = 4096, walks: int = 2048, K: int = 2,
+                    box_half: float = 2.0, coeffs: Optional[np.ndarray] = None,
+                    eps: Optional[float] = None, seed: int = GEOMETRY_SEED) -> Scene:
+    """3D thermal design: rho(w) = 1 + sum_lm c_lm Y_lm(w) on a geodesic icosphere
+    (20 freq^2 triangles) inside the box [-box_half, box_half]^3.  Object g = 1,
+    box g = 0, sigma = 1, constant source 0.5.  theta = c_lm (81 for lmax = 8);
+    dv/dc_lm = Y_lm(w_v) w_v.  eps = 1e-3 x the bounding-cube side, h = 10 eps.
+    Query points: uniform in |x|_inf < box_half - 0.1, outside the analytic
+    surface by at least 0.02."""
+    rng = np.random.default_rng(seed)
+    nsh = (lmax + 1) ** 2
+    if coeffs is None:
+        coeffs = rng.normal(0.0, coef_std, size=nsh)
+    dirs, faces = icosphere(freq)
+    Y = real_sh(lmax, dirs)
+    rho = 1.0 + Y @ coeffs
+    sv = dirs * rho[:, None]
+    bv, be = box3d(box_half)
+    nb = bv.shape[0]
+    vert = np.concatenate([bv, sv], axis=0)
+    elem = np.concatenate([be, faces + nb], axis=0).astype(np.int32)
+    jac = np.zeros((vert.shape[0], 3, nsh))
+    jac[nb:] = Y[:, None, :] * dirs[:, :, None]
+    g = np.concatenate([np.zeros(nb), np.ones(sv.shape[0])])
+    lim = box_half - 0.1
+    pts = []
+    while sum(len(p) for p in pts) < n_query:
+        c = rng.uniform(-lim, lim, size=(4 * n_query, 3))
+        r = np.linalg.norm(c, axis=1)
+        d = c / np.maximum(r, 1e-12)[:, None]
+        rr = 1.0 + real_sh(lmax, d) @ coeffs
+        pts.append(c[r > rr + 0.02])
+    q = np.concatenate(pts, axis=0)[:n_query]
+    if eps is None:
+        eps = 1e-3 * 2 * box_half
+    sc = Scene("sh_sphere_box", vert, elem, jac, data="mapped", g_vert=g, sigma=sigma, f=f, eps=eps,
+               h=10 * eps, K=K, query=q, walks=walks)
+    sc.meta = {"coeffs": coeffs, "lmax": lmax, "freq": freq, "dirs": dirs}
+    return sc
+
+
+def ball_scene(freq: int = 16, R: float = 1.0, sigma: float = 1.0, f: float = 0.0, g: float = 1.0,
+               n_query: int = 16, walks: int = 256, eps: float = 1e-3, h: float = 1e-2, K: int = 1,
+               seed: int = GEOMETRY_SEED) -> Scene:
+    """Icosphere of radius R (theta = [R], dv/dR = w_v) with constant data g."""
+    dirs, faces = icosphere(freq)
+    vert = R * dirs
+    jac = dirs[:, :, None].copy()
+    rng = np.random.default_rng(seed)
+    d = rng.normal(size=(n_query, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    r = 0.8 * R * rng.random(n_query) ** (1 / 3)
+    q = d * r[:, None]
+    sc = Scene("ball", vert, faces, jac, data="mapped", g_vert=np.full(vert.shape[0], g), sigma=sigma,
+               f=f, eps=eps, h=h, K=K, query=q, walks=walks)
+    sc.meta = {"R": R}
+    return sc
