@@ -32,8 +32,9 @@
  *  - Mapped boundary data (Eq. boundary_deriv_mapped): the reference data is
  *    extended constant along the normal, so dg/dn = 0 and the tangential term
  *    is  -grad_Gamma(g) . V  with V the interpolated vertex velocity.
- *  - A walk phase that reaches max_steps distance queries is treated as if it
- *    had reached the shell at its current closest point (kind CAPPED).
+ *  - A walk phase is capped at max_steps distance queries: the last allowed
+ *    query treats the walk as if it had reached the shell at its current
+ *    closest point (kind CAPPED).  The paper sets no cap.
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), keyed by
  * the seed; counter = (walk id lo, walk id hi, step, (phase << 8) | block).
@@ -411,7 +412,7 @@ static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_
         int e;
         double d = closest_point(s, x, xbar, &e, bary);
         bool shell = d < s->eps;
-        if (shell || k >= s->max_steps) {
+        if (shell || k + 1 >= s->max_steps) {
             res.u = acc + dirichlet_value(s, e, bary, xbar);
             res.kind = shell ? KIND_SHELL : KIND_CAPPED;
             res.steps = k + 1;
