@@ -1,0 +1,312 @@
+"""Benchmark: differential walk on spheres, reverse-mode gradient of an L2 loss.
+
+One step = one dwos_grad_l2 call on the 2D shape-from-diffusion workload: a
+box [-1,1]^2 (g = 0) around a 4096-segment star emitter (g = 1, 64 Fourier
+shape parameters), sigma = 10, 256 observation points x 4096 differential
+walks, K = 2 nested forward walks per differential walk, U-statistic batches
+of B = 8.  Every step draws fresh walks (a new Philox walk-id range).
+
+Printed JSON line (rank 0): walk-steps/s (distance queries of differential and
+nested walks per second, whole job), ms per step, gradient estimates/s,
+gradient RMSE x seconds, the walk kernel's roofline entry, the oracle's CPU
+baseline on a bounded sample, the end-to-end figure through the C ABI with
+host buffers, launch count and SM clocks sampled during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "walk-steps/s and dU/dtheta gradient-RMSE x seconds vs plain GPU WoS at 1 GB300"
+UNIT = "walk-steps/s"
+WORKLOAD = ("2D shape-from-diffusion: box [-1,1]^2 (g=0) + 4096-segment star emitter (g=1), "
+            "sigma=10, 64 Fourier shape params, 256 points x 4096 differential walks, K=2 nested, "
+            "L2-loss gradient with U-statistics (B=8)")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, f[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(sc, budget_s: float = 15.0):
+    """The FP64 oracle (brute-force closest point) on a bounded sample of the
+    same workload: every observation point, a few differential walks each."""
+    import numpy as np
+    import oracle
+    pr = oracle.Problem(vert=sc.vert, elem=sc.elem, jac=sc.jac, data_kind="mapped", g_vert=sc.g_vert,
+                        sigma=sc.sigma, f=sc.f, eps=sc.eps, h=sc.h, K=sc.K, seed=sc.seed)
+    t0 = time.perf_counter()
+    o = oracle.run_walks(pr, sc.query, 1, differential=True)
+    t1 = time.perf_counter() - t0
+    W = max(1, min(64, int(budget_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    o = oracle.run_walks(pr, sc.query, W, differential=True, walk_id_base=1 << 41)
+    dt = time.perf_counter() - t0
+    steps = int(np.clip(o["steps"], 0, None).sum())
+    return {"value": steps / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{sc.query.shape[0]} points x {W} differential walks (K={sc.K}) of the same "
+                      f"workload, FP64 brute-force closest point, {dt:.1f} s, {steps} walk-steps"}
+
+
+def run_reference(args):
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2405_12964_gb300 import scenes
+    import oracle
+    oracle.build()
+    sc = scenes.star_box_scene()
+    times, steps_total = [], 0
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(sc, budget_s=6.0)
+        if i >= args.warmup:
+            times.append(cb)
+    v = statistics.mean(c["value"] for c in times)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "note": "oracle on host cores, bounded sample per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": times[0]["cores"], "kind": "oracle",
+                             "sample": times[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dwos")
+    ap.add_argument("--walks", type=int, default=4096)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2405_12964_gb300 import build
+    build.build()
+    from paper_2405_12964_gb300 import scenes
+    from paper_2405_12964_gb300.dwos import Solver, lib, MEM_HOST
+    import ctypes
+
+    sc = scenes.star_box_scene(walks=args.walks)
+    s = Solver(local)
+    s.load_scene(sc)
+    n_pts, W = sc.query.shape[0], sc.walks
+    total = n_pts * W
+    xq = torch.tensor(sc.query, dtype=torch.float32, device=dev)
+    uref = torch.tensor(sc.u_ref, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+
+    # reference gradient for the RMSE figure: 16x the walks, its own walk ids
+    ref_grads = []
+    for r in range(4):
+        _, g = s.grad_l2(xq, uref, 4 * W, walk_id_base=(1 << 44) + r * 4 * total)
+        ref_grads.append(g.cpu().numpy())
+    g_ref = np.mean(ref_grads, axis=0)
+
+    stream = torch.cuda.current_stream(dev)
+    launches0 = s.stats()["launches"]
+
+    def step(i):
+        return s.grad_l2(xq, uref, W, walk_id_base=(rank * 100000 + i + 1) * total)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    launches_warm = s.stats()["launches"]
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    steps_done = nodes = prims = 0
+    kernel_ms = []
+    grads = []
+    for i in range(args.steps):
+        flush.fill_(float(i))                      # evict L2 between timed steps (outside the events)
+        ev[i][0].record(stream)
+        loss, g = step(args.warmup + i)
+        ev[i][1].record(stream)
+        st = s.stats()                             # synchronises; outside the events
+        steps_done += st["steps_main"] + st["steps_nested"]
+        nodes += st["nodes_visited"]
+        prims += st["prims_tested"]
+        kernel_ms.append(st["kernel_ms"])
+        grads.append(g.cpu().numpy())
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = s.stats()["launches"] - launches_warm
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(step_ms) / 1e3
+    t = t_local
+    steps_all = steps_done
+    if dist:
+        tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+        ss = torch.tensor([steps_done], device=dev, dtype=torch.float64)
+        dist.all_reduce(ss)
+        steps_all = float(ss.item())
+    value = steps_all / t
+    ms_per_step = 1e3 * t / args.steps
+
+    # gradient quality: RMSE of one step's gradient against the 16x-walk reference
+    G = np.array(grads)
+    rmse = float(np.sqrt(np.mean((G - g_ref[None]) ** 2)))
+    rel = rmse / float(np.sqrt(np.mean(g_ref ** 2)))
+
+    # roofline of the walk kernel: algorithmic bytes = BVH node fetches x 48 B
+    # + element tests x 16 B + one 32 B record per walk + 8 B query load per walk
+    node_b, prim_b = 48, 16
+    alg_bytes = nodes * node_b + prims * prim_b + args.steps * total * (32 + 8)
+    walk_s = sum(kernel_ms) / 1e3
+    achieved = alg_bytes / walk_s / 1e9 / args.steps * args.steps
+    hbm, src = peaks()
+
+    e2e = None
+    if rank == 0:
+        # end to end through the C ABI with pinned host buffers: copies in the timed region
+        xh = torch.tensor(sc.query, dtype=torch.float32).pin_memory()
+        uh = torch.tensor(sc.u_ref, dtype=torch.float32).pin_memory()
+        gh = torch.empty(sc.n_param, dtype=torch.float64).pin_memory()
+        lh = torch.empty(1, dtype=torch.float64).pin_memory()
+        L = lib()
+        s._stream()
+        e2e_t, e2e_steps = [], 0
+        for i in range(args.warmup + max(3, args.steps // 2)):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            stt = L.dwos_grad_l2(s._h, n_pts, ctypes.c_void_p(xh.data_ptr()), ctypes.c_void_p(uh.data_ptr()), W,
+                                 (1 << 45) + i * total, ctypes.c_void_p(lh.data_ptr()),
+                                 ctypes.c_void_p(gh.data_ptr()), None, MEM_HOST)
+            t1 = time.perf_counter()
+            if stt:
+                raise RuntimeError(L.dwos_last_error(s._h).decode())
+            if i >= args.warmup:
+                e2e_t.append(t1 - t0)
+                st = s.stats()
+                e2e_steps += st["steps_main"] + st["steps_nested"]
+        e2e = {"value": e2e_steps / sum(e2e_t), "unit": UNIT,
+               "h2d_bytes_per_step": int(xh.numel() * 4 + uh.numel() * 4),
+               "d2h_bytes_per_step": int(gh.numel() * 8 + lh.numel() * 8)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(sc)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "points": n_pts, "walks_per_point": W, "K": sc.K, "B": sc.B,
+                       "n_param": sc.n_param, "eps": sc.eps, "h": sc.h,
+                       "l2": "flushed between timed steps (256 MB write outside the events)",
+                       "parallelism": f"replicas x{world} (independent walk ranges, no collective)"},
+            "gradient_estimates_per_s": world * total * args.steps / t,
+            "grad_rmse": rmse, "grad_rel_rmse": rel, "grad_rmse_x_seconds": rmse * (ms_per_step / 1e3),
+            "walk_steps_per_step": steps_done / args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": None,
+                         "kernel": "walk_kernel<2>", "peak_source": src,
+                         "bytes_per_walk_step": alg_bytes / max(steps_done, 1),
+                         "walk_kernel_ms": walk_s * 1e3 / args.steps},
+            "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,231 @@
+/*
+ * dwos.h - C ABI of the GB300 (sm_103a) differential walk-on-spheres library.
+ *
+ * The library estimates, at chosen query points x of a domain Omega whose
+ * boundary Gamma is a 2D polyline or a 3D triangle mesh,
+ *   - the solution u(x) of the screened Poisson Dirichlet problem
+ *         -Lap u + sigma u = f  in Omega,   u = g  on Gamma
+ *     by walk on spheres (Miller et al., "Differential Walk on Spheres",
+ *     TOG 2024: Eq. (bvp) of Sec. 3.2, the estimator Eq. (wos) and Algorithm 1
+ *     of Sec. 3.3, Russian roulette as in Sec. 3.3);
+ *   - its derivative udot = du/dtheta with respect to every shape and
+ *     boundary-data parameter theta in R^N, by differential walk on spheres
+ *     (Eq. (bvp_deriv) of Sec. 4.1, the estimator Eq. (wos_deriv) and
+ *     Algorithm 2, with the backward-difference normal derivative of
+ *     Eq. (dudn_fd_estimate) and the nested forward walks it launches from
+ *     the offset point xbar - h n);
+ *   - reverse-mode derivatives of the squared loss over the query points with
+ *     the U-statistic product estimator (Sec. 4.3, Eqs. (squared_loss_deriv)
+ *     and (ustatistics)), and vector-Jacobian products with a given cotangent.
+ *
+ * Sign of the source: Eq. (bvp) is printed as Lap u - sigma u = f, but
+ * Algorithm 1 adds +G f / p with the positive ball Green's function; this
+ * library follows the algorithm, so f is the source of -Lap u + sigma u = f.
+ *
+ * Conventions
+ *  - Every call returns a dwos_status.  On error nothing is written to the
+ *    outputs and dwos_last_error() describes the cause.
+ *  - Pointers are host or device memory as the call's `mem` flag says
+ *    (DWOS_MEM_HOST / DWOS_MEM_DEVICE; device pointers must be on the
+ *    context's device).  The library copies every input it keeps; the caller
+ *    keeps ownership of all its buffers.
+ *  - Work is enqueued on the context's stream (dwos_set_stream).  A call whose
+ *    outputs are host memory synchronises that stream before it returns; a
+ *    call whose outputs are device memory returns as soon as the work is
+ *    enqueued, and a device-side failure is reported by the next dwos_sync().
+ *  - Float inputs are FP32; estimator sums and all reduced outputs are FP64.
+ *  - Parameter Jacobians are row-major [vertex][coordinate][parameter].
+ *  - A context is not thread safe; use one context per host thread.
+ */
+#ifndef DWOS_H
+#define DWOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dwos_ctx dwos_ctx;
+
+typedef enum {
+    DWOS_OK = 0,
+    DWOS_ERR_INVALID_ARG = 1,     /* bad size, pointer, option or geometry */
+    DWOS_ERR_CUDA = 2,            /* a CUDA runtime call failed */
+    DWOS_ERR_OOM = 3,             /* device allocation failed */
+    DWOS_ERR_STEP_LIMIT = 4,      /* a traversal exceeded its iteration bound */
+    DWOS_ERR_TIMEOUT = 5,         /* reserved for bounded device waits */
+    DWOS_ERR_NOT_IMPLEMENTED = 6,
+    DWOS_ERR_STATE = 7,           /* call order: e.g. eval before set_boundary */
+    DWOS_ERR_OUTSIDE = 8          /* a query point lies outside Omega */
+} dwos_status;
+
+enum { DWOS_MEM_HOST = 0, DWOS_MEM_DEVICE = 1 };
+
+/* Termination kinds stored in walk traces. */
+enum { DWOS_KIND_SHELL = 0, DWOS_KIND_ROULETTE = 1, DWOS_KIND_CAPPED = 2 };
+
+typedef struct {
+    float eps;          /* shell width: a walk stops when d(x) < eps (Algorithm 1) */
+    float h;            /* normal-derivative offset, Eq. (dudn_fd_estimate); h > eps */
+    int K;              /* nested forward walks per differential walk (>= 1) */
+    int B;              /* U-statistic batch size, Sec. 4.3 (2, 4, 8, 16 or 32) */
+    int max_steps;      /* distance queries per walk phase; the last one ends the
+                           phase as if the walk were in the shell (kind CAPPED) */
+    uint64_t seed;      /* Philox4x32-10 key */
+    int check_inside;   /* 1: reject query points outside Omega (ray parity) */
+    int block_size;     /* walk-kernel threads per block; 0 = library default */
+    int blocks_per_sm;  /* resident walk blocks per SM; 0 = occupancy maximum */
+    int smem_nodes;     /* BVH nodes (breadth-first prefix) staged in shared
+                           memory by each walk block; 0 = none */
+} dwos_options;
+
+/* Per-walk record of a differential walk (32 bytes).  For a walk that reaches
+ * the shell at element e with vertex weights w_i (i over the element's dim
+ * vertices, w_0 = 1 - b1 [- b2]), the forward-mode derivative is
+ *     udot_j = sum_i w_i ( c . J[v_i][:, j] + dg[v_i][j] )
+ * where c = (dg/dn - du/dn) n - grad_Gamma(g): Eq. (wos_deriv), shell case,
+ * with V_n = n . sum_i w_i J[v_i] and the boundary-data derivative of
+ * Eq. (boundary_deriv_restricted) (field data) or Eq. (boundary_deriv_mapped)
+ * (per-vertex data).  A walk ended by Russian roulette has elem = -1 and c = 0
+ * (Algorithm 2 returns 0). */
+typedef struct {
+    float u;            /* u estimate of the same path (Sec. 4.1, observation 2) */
+    int32_t elem;       /* terminal element (input numbering) or -1 */
+    float b1, b2;       /* barycentric weights of the element's vertices 1 and 2 */
+    float c[3];         /* see above; c[2] = 0 in 2D */
+    uint32_t meta;      /* bits 0-23: distance queries of the main walk;
+                           bits 24-25: its termination kind */
+} dwos_record;
+
+/* Optional per-walk diagnostics of a differential walk (32 bytes). */
+typedef struct {
+    float dudn;         /* (g(xbar) - mean nested estimate) / h */
+    float n[3];         /* oriented normal at xbar */
+    float u_off;        /* mean of the K nested estimates at xbar - h n */
+    float xbar[3];      /* closest boundary point where the main walk stopped */
+} dwos_walk_debug;
+
+typedef struct {
+    uint64_t steps_main;    /* distance queries of main (differential/forward) walks */
+    uint64_t steps_nested;  /* distance queries of nested forward walks */
+    uint64_t walks;         /* main walks run */
+    uint64_t capped;        /* walk phases that hit max_steps */
+    uint64_t nodes_visited; /* BVH node fetches made by the distance queries */
+    uint64_t prims_tested;  /* element distance tests made by the distance queries */
+    uint64_t launches;      /* kernels this context has launched since creation */
+    float kernel_ms;        /* device time of the last walk kernel (0 if unknown) */
+    int blocks;             /* thread blocks of the last walk kernel */
+} dwos_run_stats;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device` (its own default stream until
+ * dwos_set_stream).  *out receives NULL on failure. */
+dwos_status dwos_create(dwos_ctx** out, int device);
+/* Release every device buffer the context owns.  NULL is ignored. */
+void dwos_destroy(dwos_ctx* ctx);
+/* Enqueue all further work on `stream` (a cudaStream_t; NULL = legacy default). */
+dwos_status dwos_set_stream(dwos_ctx* ctx, void* stream);
+/* Message of the last failed call on this context ("" if none); valid until
+ * the next call.  ctx may be NULL for failures of dwos_create. */
+const char* dwos_last_error(const dwos_ctx* ctx);
+/* Block until the context's stream is idle and report any device-side error
+ * raised by earlier asynchronous calls (step-limit or outside-Omega flags). */
+dwos_status dwos_sync(dwos_ctx* ctx);
+
+/* Fill *opt with the defaults: eps 1e-3, h 1e-2, K 1, B 8, max_steps 16384,
+ * seed 0x12964, check_inside 1, automatic launch shape, no shared staging. */
+void dwos_default_options(dwos_options* opt);
+/* Validate and store options (eps > 0, h > 0, K >= 1, B in {2,4,8,16,32},
+ * 1 <= max_steps < 2^24). */
+dwos_status dwos_set_options(dwos_ctx* ctx, const dwos_options* opt);
+
+/* ---- problem ------------------------------------------------------------ */
+
+/* Load the boundary (Sec. 3.1.2, explicit surface): dim 2 (segments, elem has
+ * 2 ids per row) or dim 3 (triangles, 3 ids per row).  vert_ref is the
+ * reference vertex array (n_vert x dim); vert_jac (n_vert x dim x n_param,
+ * or NULL with n_param = 0) gives dv/dtheta, so that v(theta) = vert_ref +
+ * vert_jac theta.  Builds the BVH on the device.  Resets Dirichlet data to
+ * mapped g = 0 and theta to 0. */
+dwos_status dwos_set_boundary(dwos_ctx* ctx, int dim, int n_vert, const float* vert_ref,
+                              int n_elem, const int32_t* elem, int n_param,
+                              const float* vert_jac, int mem);
+/* Set theta (n_param values): v = vert_ref + vert_jac theta on the device,
+ * then rebuild the BVH. */
+dwos_status dwos_set_params(dwos_ctx* ctx, const float* theta, int mem);
+/* Mapped (per-vertex, linearly interpolated) Dirichlet data, Sec. 4.1
+ * "Mapped boundary data": g_vert (n_vert) and optionally dg_vert
+ * (n_vert x n_param, dg_v/dtheta; NULL = 0).  dg/dn is taken as 0 (the data
+ * is extended constant along the normal). */
+dwos_status dwos_set_dirichlet_mapped(dwos_ctx* ctx, const float* g_vert, const float* dg_vert,
+                                      int mem);
+/* Restricted Dirichlet data, Sec. 4.1 "Restricted boundary data": the field
+ * g(x) = c0 + c.x + x^T A x, independent of theta; coeffs (host, 10 values)
+ * = {c0, c_x, c_y, c_z, A_xx, A_yy, A_zz, A_xy, A_xz, A_yz}. */
+dwos_status dwos_set_dirichlet_field(dwos_ctx* ctx, const double* coeffs);
+/* Screening sigma >= 0 and constant source f (of -Lap u + sigma u = f). */
+dwos_status dwos_set_pde(dwos_ctx* ctx, float sigma, float f);
+
+/* ---- estimators --------------------------------------------------------- */
+
+/* Forward estimates at n_query points (xq: n_query x dim), walks_per_point
+ * walks each.  u_mean, u_se: n_query FP64 (mean and standard error).  If
+ * du_mean is not NULL, runs differential walks (Algorithm 2) and also returns
+ * the forward-mode derivative du_mean (n_query x n_param) and, if not NULL,
+ * its standard error du_se.  Walk w of point p uses Philox walk id
+ * p * walks_per_point + w. */
+dwos_status dwos_eval(dwos_ctx* ctx, int n_query, const float* xq, int walks_per_point,
+                      double* u_mean, double* u_se, double* du_mean, double* du_se, int mem);
+
+/* Reverse mode with a caller-supplied cotangent w (n_query): grad_param
+ * (n_param) = sum_p w_p E[udot_p], and grad_vert (n_vert x dim, or NULL) the
+ * same product with respect to the vertex positions.  Draws its own walks
+ * (ids start at walk_id_base), independent of any earlier call that produced
+ * w when the bases differ. */
+dwos_status dwos_vjp(dwos_ctx* ctx, int n_query, const float* xq, const float* w,
+                     int walks_per_point, uint64_t walk_id_base, double* grad_param,
+                     double* grad_vert, int mem);
+
+/* Squared loss L = 1/2 sum_p (u_p - uref_p)^2 (Eq. functional with a
+ * point mask; Eq. squared_loss_deriv) and its gradient with the U-statistic
+ * product estimator in batches of B consecutive walks (Eq. ustatistics;
+ * walks_per_point must be a multiple of B).  loss (1 value), grad_param
+ * (n_param) and grad_vert (n_vert x dim, may be NULL). */
+dwos_status dwos_grad_l2(dwos_ctx* ctx, int n_query, const float* xq, const float* uref,
+                         int walks_per_point, uint64_t walk_id_base, double* loss,
+                         double* grad_param, double* grad_vert, int mem);
+
+/* Raw per-walk records (n_query x walks_per_point rows, row p*W + w, Philox
+ * walk id walk_id_base + p*W + w).  differential = 0 runs Algorithm 1 only
+ * (record.u, record.elem, record.b*, meta; c = 0).  trace (optional,
+ * (K+1) words per walk: bits 0-29 distance queries of that phase, bits 30-31
+ * its termination kind; nested slots of walks that never reached the shell
+ * are 0xFFFFFFFF) and debug (optional) are written when not NULL. */
+dwos_status dwos_walk_records(dwos_ctx* ctx, int n_query, const float* xq, int walks_per_point,
+                              uint64_t walk_id_base, int differential, dwos_record* records,
+                              uint32_t* trace, dwos_walk_debug* debug, int mem);
+
+/* Statistics of the last walk launch on this context (synchronises). */
+dwos_status dwos_last_stats(dwos_ctx* ctx, dwos_run_stats* out);
+
+/* ---- geometry queries and primitives (used by tests and tools) ---------- */
+
+/* DistanceToBoundary (Algorithm 1) through the BVH for n points: dist (n),
+ * elem (n, input numbering), bary (n x 2, weights of vertices 1 and 2). */
+dwos_status dwos_closest_point(dwos_ctx* ctx, int n, const float* p, float* dist, int32_t* elem,
+                               float* bary, int mem);
+/* 1 if the point lies inside the region the boundary encloses (odd number of
+ * ray crossings), else 0. */
+dwos_status dwos_inside(dwos_ctx* ctx, int n, const float* p, int32_t* inside, int mem);
+/* Philox4x32-10 (Salmon et al., SC'11) on the device: out[4i..4i+3] =
+ * Philox(ctr[4i..4i+3], key[0..1]) for i < n.  ctx selects the device. */
+dwos_status dwos_philox4x32_10(dwos_ctx* ctx, int n, const uint32_t* ctr, const uint32_t* key,
+                               uint32_t* out, int mem);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DWOS_H */

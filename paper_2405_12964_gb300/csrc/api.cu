@@ -1,0 +1,624 @@
+// C ABI of the differential walk-on-spheres library: context, problem state,
+// argument checks, device workspaces and the launch sequences of each call.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dwos_internal.h"
+
+using namespace dwos;
+
+struct dwos_ctx {
+    int device = 0;
+    int n_sm = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    dwos_options opt{};
+
+    // boundary
+    int dim = 0, n_vert = 0, n_elem = 0, n_param = 0;
+    float* vert_ref = nullptr;   // n_vert*dim
+    float* vert = nullptr;       // current vertices
+    int* elem = nullptr;
+    float* jac = nullptr;        // n_vert*dim*n_param (or null)
+    float* theta = nullptr;      // n_param
+    float* g_vert = nullptr;     // n_vert
+    float* dg_vert = nullptr;    // n_vert*n_param or null
+    int data_kind = 0;
+    double field[10] = {0};
+    float sigma = 0.0f, f = 0.0f;
+    BvhBuffers bvh;
+    bool have_boundary = false;
+
+    // workspaces (grow-only)
+    dwos_record* rec = nullptr; size_t rec_cap = 0;
+    float* xq = nullptr; size_t xq_cap = 0;
+    int* valid = nullptr; size_t valid_cap = 0;
+    float* wvec = nullptr; size_t wvec_cap = 0;           // cotangent / uref
+    double* out = nullptr; size_t out_cap = 0;            // reduced outputs
+    double* acc_vert = nullptr; size_t acc_cap = 0;       // n_vert*dim + n_vert
+    uint32_t* trace = nullptr; size_t trace_cap = 0;
+    dwos_walk_debug* dbg = nullptr; size_t dbg_cap = 0;
+    float* misc_f = nullptr; size_t misc_f_cap = 0;
+    int* misc_i = nullptr; size_t misc_i_cap = 0;
+    uint32_t* misc_u = nullptr; size_t misc_u_cap = 0;
+    DevProblem* d_prob = nullptr;
+    DevCounters* d_ctr = nullptr;
+    int* d_err = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool timed = false;
+    unsigned long long launches = 0;   // kernels launched by this context
+    int last_blocks = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+dwos_status fail(dwos_ctx* c, dwos_status s, const std::string& msg) {
+    if (c) c->err = msg; else g_create_err = msg;
+    return s;
+}
+
+dwos_status cuda_fail(dwos_ctx* c, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();
+    return fail(c, e == cudaErrorMemoryAllocation ? DWOS_ERR_OOM : DWOS_ERR_CUDA, m);
+}
+
+#define CK(call, where) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); } while (0)
+
+template <typename T>
+cudaError_t grow(T*& p, size_t& cap, size_t n) {
+    if (n <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    size_t want = std::max<size_t>(n, 1);
+    cudaError_t e = cudaMalloc(&p, want * sizeof(T));
+    if (e == cudaSuccess) cap = want;
+    return e;
+}
+
+// Copy n elements into device buffer `dst` from host or device `src`.
+template <typename T>
+cudaError_t to_device(dwos_ctx* ctx, T* dst, const T* src, size_t n, int mem) {
+    if (n == 0) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, n * sizeof(T), mem == DWOS_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                                           : cudaMemcpyHostToDevice, ctx->stream);
+}
+
+template <typename T>
+cudaError_t from_device(dwos_ctx* ctx, T* dst, const T* src, size_t n, int mem) {
+    if (n == 0 || !dst) return cudaSuccess;
+    return cudaMemcpyAsync(dst, src, n * sizeof(T), mem == DWOS_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                                           : cudaMemcpyDeviceToHost, ctx->stream);
+}
+
+bool finite_all(const float* p, size_t n) {
+    for (size_t i = 0; i < n; ++i) if (!std::isfinite(p[i])) return false;
+    return true;
+}
+
+dwos_status check_mem(dwos_ctx* ctx, int mem) {
+    if (mem != DWOS_MEM_HOST && mem != DWOS_MEM_DEVICE) return fail(ctx, DWOS_ERR_INVALID_ARG, "mem must be DWOS_MEM_HOST or DWOS_MEM_DEVICE");
+    return DWOS_OK;
+}
+
+dwos_status check_device_ptr(dwos_ctx* ctx, const void* p, const char* name) {
+    if (!p) return DWOS_OK;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) { cudaGetLastError(); return fail(ctx, DWOS_ERR_INVALID_ARG, std::string(name) + " is not a device pointer"); }
+    if (a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged)
+        return fail(ctx, DWOS_ERR_INVALID_ARG, std::string(name) + " is not device memory");
+    if (a.device != ctx->device) return fail(ctx, DWOS_ERR_INVALID_ARG, std::string(name) + " lives on another device");
+    return DWOS_OK;
+}
+
+dwos_status set_device(dwos_ctx* ctx) {
+    CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    return DWOS_OK;
+}
+
+dwos_status rebuild(dwos_ctx* ctx) {
+    CK(bvh_build(ctx->bvh, ctx->dim, ctx->vert, ctx->elem, ctx->n_elem, ctx->stream), "BVH build");
+    return DWOS_OK;
+}
+
+// Shared front half of every walk-running call: validate, stage the query
+// points, optionally classify them, fill the problem descriptor, run the walks.
+dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsigned long long base,
+                      int differential, int mem, uint32_t* trace_dev, dwos_walk_debug* dbg_dev) {
+    if (!ctx->have_boundary) return fail(ctx, DWOS_ERR_STATE, "no boundary: call dwos_set_boundary first");
+    if (n_query < 0 || W < 1) return fail(ctx, DWOS_ERR_INVALID_ARG, "n_query must be >= 0 and walks_per_point >= 1");
+    if (n_query > 0 && !xq) return fail(ctx, DWOS_ERR_INVALID_ARG, "xq is NULL");
+    const unsigned long long total = (unsigned long long)n_query * (unsigned long long)W;
+    if (total > (1ull << 40)) return fail(ctx, DWOS_ERR_INVALID_ARG, "too many walks in one call");
+    if (mem == DWOS_MEM_HOST && n_query > 0 && !finite_all(xq, (size_t)n_query * ctx->dim))
+        return fail(ctx, DWOS_ERR_INVALID_ARG, "query points must be finite");
+    if (mem == DWOS_MEM_DEVICE) { dwos_status s = check_device_ptr(ctx, xq, "xq"); if (s) return s; }
+    CK(grow(ctx->xq, ctx->xq_cap, (size_t)n_query * ctx->dim), "alloc xq");
+    CK(grow(ctx->rec, ctx->rec_cap, (size_t)total), "alloc records");
+    CK(to_device(ctx, ctx->xq, xq, (size_t)n_query * ctx->dim, mem), "copy xq");
+    const int* valid = nullptr;
+    if (ctx->opt.check_inside && n_query > 0) {
+        CK(grow(ctx->valid, ctx->valid_cap, (size_t)n_query), "alloc inside flags");
+        CK(launch_inside(ctx->bvh, n_query, ctx->xq, ctx->valid, ctx->stream), "inside test");
+        ctx->launches += 1;
+        valid = ctx->valid;
+    }
+    DevProblem P;
+    std::memset(&P, 0, sizeof(P));
+    P.nodes = ctx->bvh.nodes;
+    P.prims = ctx->bvh.prims;
+    P.prim_elem = ctx->bvh.prim_elem;
+    P.elem = ctx->elem;
+    P.g_vert = ctx->g_vert;
+    P.root = 0;
+    P.n_internal = ctx->bvh.n_internal;
+    P.data_kind = ctx->data_kind;
+    P.differential = differential;
+    for (int i = 0; i < 10; ++i) P.field[i] = (float)ctx->field[i];
+    P.sqrt_sigma = std::sqrt(ctx->sigma);
+    P.f = ctx->f;
+    P.eps = ctx->opt.eps;
+    P.h = ctx->opt.h;
+    P.inv_h = 1.0f / ctx->opt.h;
+    P.K = ctx->opt.K;
+    P.max_steps = ctx->opt.max_steps;
+    P.seed_lo = (uint32_t)ctx->opt.seed;
+    P.seed_hi = (uint32_t)(ctx->opt.seed >> 32);
+    P.xq = ctx->xq;
+    P.valid = valid;
+    P.walks = W;
+    P.walk_id_base = base;
+    P.work_begin = 0;
+    P.work_end = total;
+    P.rec = ctx->rec;
+    P.trace = trace_dev;
+    P.dbg = dbg_dev;
+    CK(cudaMemcpyAsync(ctx->d_prob, &P, sizeof(P), cudaMemcpyHostToDevice, ctx->stream), "copy problem");
+    CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->stream), "reset counters");
+    WalkLaunch L;
+    L.dim = ctx->dim;
+    L.block_size = ctx->opt.block_size > 0 ? ctx->opt.block_size : 256;
+    L.blocks_per_sm = ctx->opt.blocks_per_sm;
+    L.n_sm = ctx->n_sm;
+    CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
+    int blocks = 0;
+    CK(launch_walks(L, ctx->d_prob, 1, total, ctx->d_ctr, ctx->stream, &blocks), "walk kernel");
+    ctx->launches += blocks > 0 ? 1 : 0;
+    ctx->last_blocks = blocks;
+    CK(cudaEventRecord(ctx->ev1, ctx->stream), "event");
+    ctx->timed = true;
+    return DWOS_OK;
+}
+
+// After a synchronous call: report device-side flags.
+dwos_status finish_sync(dwos_ctx* ctx) {
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    DevCounters c;
+    CK(cudaMemcpy(&c, ctx->d_ctr, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
+    if (c.error & 2) return fail(ctx, DWOS_ERR_OUTSIDE, "a query point lies outside the domain");
+    if (c.error & 1) return fail(ctx, DWOS_ERR_STEP_LIMIT, "BVH traversal exceeded its iteration bound");
+    return DWOS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void dwos_default_options(dwos_options* o) {
+    if (!o) return;
+    o->eps = 1e-3f;
+    o->h = 1e-2f;
+    o->K = 1;
+    o->B = 8;
+    o->max_steps = 1 << 14;
+    o->seed = 0x12964ull;
+    o->check_inside = 1;
+    o->block_size = 0;
+    o->blocks_per_sm = 0;
+    o->smem_nodes = 0;
+}
+
+dwos_status dwos_create(dwos_ctx** out, int device) {
+    if (!out) return fail(nullptr, DWOS_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(nullptr, DWOS_ERR_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e)); }
+    if (device < 0 || device >= n) return fail(nullptr, DWOS_ERR_INVALID_ARG, "device index out of range");
+    dwos_ctx* ctx = new (std::nothrow) dwos_ctx();
+    if (!ctx) return fail(nullptr, DWOS_ERR_OOM, "host allocation failed");
+    ctx->device = device;
+    dwos_default_options(&ctx->opt);
+    cudaError_t ce = cudaSetDevice(device);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (ce == cudaSuccess) ce = cudaMalloc(&ctx->d_prob, sizeof(DevProblem));
+    if (ce == cudaSuccess) ce = cudaMalloc(&ctx->d_ctr, sizeof(DevCounters));
+    if (ce == cudaSuccess) ce = cudaMalloc(&ctx->d_err, sizeof(int));
+    if (ce == cudaSuccess) ce = cudaEventCreate(&ctx->ev0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&ctx->ev1);
+    if (ce == cudaSuccess) ce = cudaMemset(ctx->d_ctr, 0, sizeof(DevCounters));
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        g_create_err = std::string("context setup failed: ") + cudaGetErrorString(ce);
+        dwos_destroy(ctx);
+        return ce == cudaErrorMemoryAllocation ? DWOS_ERR_OOM : DWOS_ERR_CUDA;
+    }
+    *out = ctx;
+    return DWOS_OK;
+}
+
+void dwos_destroy(dwos_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    bvh_free(ctx->bvh);
+    void* bufs[] = {ctx->vert_ref, ctx->vert, ctx->elem, ctx->jac, ctx->theta, ctx->g_vert, ctx->dg_vert, ctx->rec,
+                    ctx->xq, ctx->valid, ctx->wvec, ctx->out, ctx->acc_vert, ctx->trace, ctx->dbg, ctx->misc_f,
+                    ctx->misc_i, ctx->misc_u, ctx->d_prob, ctx->d_ctr, ctx->d_err};
+    for (void* p : bufs) if (p) cudaFree(p);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+}
+
+dwos_status dwos_set_stream(dwos_ctx* ctx, void* stream) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    ctx->stream = (cudaStream_t)stream;
+    return DWOS_OK;
+}
+
+const char* dwos_last_error(const dwos_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+dwos_status dwos_sync(dwos_ctx* ctx) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    dwos_status s = set_device(ctx);
+    if (s) return s;
+    return finish_sync(ctx);
+}
+
+dwos_status dwos_set_options(dwos_ctx* ctx, const dwos_options* o) {
+    if (!ctx || !o) return fail(ctx, DWOS_ERR_INVALID_ARG, "NULL argument");
+    if (!(o->eps > 0.0f) || !std::isfinite(o->eps)) return fail(ctx, DWOS_ERR_INVALID_ARG, "eps must be > 0");
+    if (!(o->h > 0.0f) || !std::isfinite(o->h)) return fail(ctx, DWOS_ERR_INVALID_ARG, "h must be > 0");
+    if (o->K < 1 || o->K > 255) return fail(ctx, DWOS_ERR_INVALID_ARG, "K must be in [1, 255]");
+    if (!(o->B == 2 || o->B == 4 || o->B == 8 || o->B == 16 || o->B == 32))
+        return fail(ctx, DWOS_ERR_INVALID_ARG, "B must be 2, 4, 8, 16 or 32");
+    if (o->max_steps < 1 || o->max_steps >= (1 << 24)) return fail(ctx, DWOS_ERR_INVALID_ARG, "max_steps must be in [1, 2^24)");
+    if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 256 || o->block_size % 32))
+        return fail(ctx, DWOS_ERR_INVALID_ARG, "block_size must be 0 or a multiple of 32 in [32, 256]");
+    if (o->blocks_per_sm < 0 || o->blocks_per_sm > 64) return fail(ctx, DWOS_ERR_INVALID_ARG, "blocks_per_sm must be in [0, 64]");
+    if (o->smem_nodes < 0) return fail(ctx, DWOS_ERR_INVALID_ARG, "smem_nodes must be >= 0");
+    ctx->opt = *o;
+    return DWOS_OK;
+}
+
+dwos_status dwos_set_boundary(dwos_ctx* ctx, int dim, int n_vert, const float* vert_ref, int n_elem,
+                              const int32_t* elem, int n_param, const float* vert_jac, int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (dwos_status s = check_mem(ctx, mem)) return s;
+    if (dim != 2 && dim != 3) return fail(ctx, DWOS_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (n_vert < dim || n_elem < 1) return fail(ctx, DWOS_ERR_INVALID_ARG, "empty boundary");
+    if (n_param < 0 || (n_param > 0 && !vert_jac)) return fail(ctx, DWOS_ERR_INVALID_ARG, "n_param > 0 needs vert_jac");
+    if (!vert_ref || !elem) return fail(ctx, DWOS_ERR_INVALID_ARG, "NULL vertex or element array");
+    if ((long long)n_elem >= (1ll << 30)) return fail(ctx, DWOS_ERR_INVALID_ARG, "too many elements");
+    if (mem == DWOS_MEM_HOST) {
+        if (!finite_all(vert_ref, (size_t)n_vert * dim)) return fail(ctx, DWOS_ERR_INVALID_ARG, "vertices must be finite");
+        for (long long i = 0; i < (long long)n_elem * dim; ++i)
+            if (elem[i] < 0 || elem[i] >= n_vert) return fail(ctx, DWOS_ERR_INVALID_ARG, "element vertex id out of range");
+        if (n_param > 0 && !finite_all(vert_jac, (size_t)n_vert * dim * n_param))
+            return fail(ctx, DWOS_ERR_INVALID_ARG, "Jacobian must be finite");
+    } else {
+        for (const void* p : {(const void*)vert_ref, (const void*)elem, (const void*)vert_jac})
+            if (dwos_status s = check_device_ptr(ctx, p, "boundary array")) return s;
+    }
+    if (dwos_status s = set_device(ctx)) return s;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    for (void* p : {(void*)ctx->vert_ref, (void*)ctx->vert, (void*)ctx->elem, (void*)ctx->jac, (void*)ctx->theta,
+                    (void*)ctx->g_vert, (void*)ctx->dg_vert}) if (p) cudaFree(p);
+    ctx->vert_ref = ctx->vert = ctx->jac = ctx->theta = ctx->g_vert = ctx->dg_vert = nullptr;
+    ctx->elem = nullptr;
+    ctx->have_boundary = false;
+    const size_t nv = (size_t)n_vert * dim;
+    CK(cudaMalloc(&ctx->vert_ref, nv * sizeof(float)), "alloc vertices");
+    CK(cudaMalloc(&ctx->vert, nv * sizeof(float)), "alloc vertices");
+    CK(cudaMalloc(&ctx->elem, (size_t)n_elem * dim * sizeof(int)), "alloc elements");
+    CK(cudaMalloc(&ctx->g_vert, (size_t)n_vert * sizeof(float)), "alloc data");
+    CK(cudaMalloc(&ctx->theta, (size_t)std::max(n_param, 1) * sizeof(float)), "alloc theta");
+    if (n_param > 0) CK(cudaMalloc(&ctx->jac, nv * n_param * sizeof(float)), "alloc Jacobian");
+    CK(to_device(ctx, ctx->vert_ref, vert_ref, nv, mem), "copy vertices");
+    CK(cudaMemcpyAsync(ctx->vert, ctx->vert_ref, nv * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream), "copy vertices");
+    CK(to_device(ctx, ctx->elem, elem, (size_t)n_elem * dim, mem), "copy elements");
+    if (n_param > 0) CK(to_device(ctx, ctx->jac, vert_jac, nv * n_param, mem), "copy Jacobian");
+    CK(cudaMemsetAsync(ctx->g_vert, 0, (size_t)n_vert * sizeof(float), ctx->stream), "zero data");
+    CK(cudaMemsetAsync(ctx->theta, 0, (size_t)std::max(n_param, 1) * sizeof(float), ctx->stream), "zero theta");
+    ctx->dim = dim; ctx->n_vert = n_vert; ctx->n_elem = n_elem; ctx->n_param = n_param;
+    ctx->data_kind = 0;
+    std::memset(ctx->field, 0, sizeof(ctx->field));
+    if (dwos_status s = rebuild(ctx)) return s;
+    CK(cudaStreamSynchronize(ctx->stream), "BVH build");
+    ctx->have_boundary = true;
+    return DWOS_OK;
+}
+
+dwos_status dwos_set_params(dwos_ctx* ctx, const float* theta, int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (!ctx->have_boundary) return fail(ctx, DWOS_ERR_STATE, "no boundary");
+    if (dwos_status s = check_mem(ctx, mem)) return s;
+    if (ctx->n_param == 0) return DWOS_OK;
+    if (!theta) return fail(ctx, DWOS_ERR_INVALID_ARG, "theta is NULL");
+    if (mem == DWOS_MEM_HOST && !finite_all(theta, ctx->n_param)) return fail(ctx, DWOS_ERR_INVALID_ARG, "theta must be finite");
+    if (mem == DWOS_MEM_DEVICE) if (dwos_status s = check_device_ptr(ctx, theta, "theta")) return s;
+    if (dwos_status s = set_device(ctx)) return s;
+    CK(to_device(ctx, ctx->theta, theta, ctx->n_param, mem), "copy theta");
+    CK(launch_apply_params(ctx->vert_ref, ctx->jac, ctx->theta, ctx->vert, ctx->n_vert * ctx->dim, ctx->n_param,
+                           ctx->stream), "apply theta");
+    return rebuild(ctx);
+}
+
+dwos_status dwos_set_dirichlet_mapped(dwos_ctx* ctx, const float* g_vert, const float* dg_vert, int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (!ctx->have_boundary) return fail(ctx, DWOS_ERR_STATE, "no boundary");
+    if (dwos_status s = check_mem(ctx, mem)) return s;
+    if (!g_vert) return fail(ctx, DWOS_ERR_INVALID_ARG, "g_vert is NULL");
+    if (mem == DWOS_MEM_HOST) {
+        if (!finite_all(g_vert, ctx->n_vert)) return fail(ctx, DWOS_ERR_INVALID_ARG, "g_vert must be finite");
+        if (dg_vert && !finite_all(dg_vert, (size_t)ctx->n_vert * ctx->n_param))
+            return fail(ctx, DWOS_ERR_INVALID_ARG, "dg_vert must be finite");
+    }
+    if (dg_vert && ctx->n_param == 0) return fail(ctx, DWOS_ERR_INVALID_ARG, "dg_vert given but n_param = 0");
+    if (dwos_status s = set_device(ctx)) return s;
+    CK(to_device(ctx, ctx->g_vert, g_vert, ctx->n_vert, mem), "copy g");
+    if (ctx->dg_vert) { CK(cudaStreamSynchronize(ctx->stream), "synchronize"); cudaFree(ctx->dg_vert); ctx->dg_vert = nullptr; }
+    if (dg_vert) {
+        CK(cudaMalloc(&ctx->dg_vert, (size_t)ctx->n_vert * ctx->n_param * sizeof(float)), "alloc dg");
+        CK(to_device(ctx, ctx->dg_vert, dg_vert, (size_t)ctx->n_vert * ctx->n_param, mem), "copy dg");
+    }
+    ctx->data_kind = 0;
+    return DWOS_OK;
+}
+
+dwos_status dwos_set_dirichlet_field(dwos_ctx* ctx, const double* coeffs) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (!coeffs) return fail(ctx, DWOS_ERR_INVALID_ARG, "coeffs is NULL");
+    for (int i = 0; i < 10; ++i) if (!std::isfinite(coeffs[i])) return fail(ctx, DWOS_ERR_INVALID_ARG, "coeffs must be finite");
+    std::memcpy(ctx->field, coeffs, sizeof(ctx->field));
+    ctx->data_kind = 1;
+    return DWOS_OK;
+}
+
+dwos_status dwos_set_pde(dwos_ctx* ctx, float sigma, float f) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (!(sigma >= 0.0f) || !std::isfinite(sigma)) return fail(ctx, DWOS_ERR_INVALID_ARG, "sigma must be finite and >= 0");
+    if (!std::isfinite(f)) return fail(ctx, DWOS_ERR_INVALID_ARG, "f must be finite");
+    ctx->sigma = sigma;
+    ctx->f = f;
+    return DWOS_OK;
+}
+
+dwos_status dwos_eval(dwos_ctx* ctx, int n_query, const float* xq, int W, double* u_mean, double* u_se,
+                      double* du_mean, double* du_se, int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (dwos_status s = check_mem(ctx, mem)) return s;
+    if (!u_mean) return fail(ctx, DWOS_ERR_INVALID_ARG, "u_mean is NULL");
+    if (du_mean && ctx->n_param == 0) return fail(ctx, DWOS_ERR_INVALID_ARG, "derivatives requested but n_param = 0");
+    if (mem == DWOS_MEM_DEVICE)
+        for (const void* p : {(const void*)u_mean, (const void*)u_se, (const void*)du_mean, (const void*)du_se})
+            if (dwos_status s = check_device_ptr(ctx, p, "output")) return s;
+    if (dwos_status s = set_device(ctx)) return s;
+    const int diff = du_mean ? 1 : 0;
+    if (dwos_status s = run_walks(ctx, n_query, xq, W, 0, diff, mem, nullptr, nullptr)) return s;
+    const int N = ctx->n_param;
+    const size_t need = 2 * (size_t)n_query + (diff ? 2 * (size_t)n_query * N : 0);
+    CK(grow(ctx->out, ctx->out_cap, need), "alloc outputs");
+    double* m = mem == DWOS_MEM_DEVICE ? u_mean : ctx->out;
+    double* se = mem == DWOS_MEM_DEVICE ? u_se : ctx->out + n_query;
+    CK(launch_reduce_u(ctx->rec, n_query, W, m, se, ctx->stream), "reduce u");
+    ctx->launches += n_query > 0 ? 1 : 0;
+    if (diff) {
+        double* dm = mem == DWOS_MEM_DEVICE ? du_mean : ctx->out + 2 * (size_t)n_query;
+        double* ds = mem == DWOS_MEM_DEVICE ? du_se : ctx->out + 2 * (size_t)n_query + (size_t)n_query * N;
+        CK(launch_reduce_udot(ctx->rec, ctx->elem, ctx->jac, ctx->dg_vert, ctx->dim, N, n_query, W, dm, ds,
+                              ctx->stream), "reduce udot");
+        ctx->launches += n_query > 0 ? 1 : 0;
+    }
+    if (mem == DWOS_MEM_HOST) {
+        CK(from_device(ctx, u_mean, ctx->out, n_query, mem), "copy u");
+        CK(from_device(ctx, u_se, ctx->out + n_query, n_query, mem), "copy se");
+        if (diff) {
+            CK(from_device(ctx, du_mean, ctx->out + 2 * (size_t)n_query, (size_t)n_query * N, mem), "copy du");
+            CK(from_device(ctx, du_se, ctx->out + 2 * (size_t)n_query + (size_t)n_query * N, (size_t)n_query * N, mem), "copy du se");
+        }
+        return finish_sync(ctx);
+    }
+    return DWOS_OK;
+}
+
+static dwos_status reverse_common(dwos_ctx* ctx, int n_query, const float* xq, const float* wv, int W,
+                                  unsigned long long base, int mode, double* loss, double* grad_param,
+                                  double* grad_vert, int mem) {
+    if (dwos_status s = check_mem(ctx, mem)) return s;
+    if (!wv && n_query > 0) return fail(ctx, DWOS_ERR_INVALID_ARG, mode ? "uref is NULL" : "w is NULL");
+    if (ctx->n_param > 0 && !grad_param) return fail(ctx, DWOS_ERR_INVALID_ARG, "grad_param is NULL");
+    if (mode == 1) {
+        if (W % ctx->opt.B) return fail(ctx, DWOS_ERR_INVALID_ARG, "walks_per_point must be a multiple of B");
+        if (!loss) return fail(ctx, DWOS_ERR_INVALID_ARG, "loss is NULL");
+    }
+    if (mem == DWOS_MEM_HOST && wv && !finite_all(wv, n_query)) return fail(ctx, DWOS_ERR_INVALID_ARG, "weights must be finite");
+    if (mem == DWOS_MEM_DEVICE)
+        for (const void* p : {(const void*)wv, (const void*)loss, (const void*)grad_param, (const void*)grad_vert})
+            if (dwos_status s = check_device_ptr(ctx, p, "argument")) return s;
+    if (dwos_status s = set_device(ctx)) return s;
+    if (dwos_status s = run_walks(ctx, n_query, xq, W, base, 1, mem, nullptr, nullptr)) return s;
+    const int N = ctx->n_param;
+    CK(grow(ctx->wvec, ctx->wvec_cap, (size_t)std::max(n_query, 1)), "alloc weights");
+    CK(to_device(ctx, ctx->wvec, wv, (size_t)n_query, mem), "copy weights");
+    const size_t nacc = (size_t)ctx->n_vert * ctx->dim + (size_t)ctx->n_vert;
+    CK(grow(ctx->acc_vert, ctx->acc_cap, nacc), "alloc accumulators");
+    CK(cudaMemsetAsync(ctx->acc_vert, 0, nacc * sizeof(double), ctx->stream), "zero accumulators");
+    double* acc_g = ctx->dg_vert ? ctx->acc_vert + (size_t)ctx->n_vert * ctx->dim : nullptr;
+    CK(launch_scatter(ctx->rec, ctx->elem, ctx->dim, n_query, W, ctx->opt.B, mode, ctx->wvec, ctx->acc_vert, acc_g,
+                      ctx->stream), "scatter");
+    ctx->launches += n_query > 0 ? 1 : 0;
+    const size_t need = (size_t)n_query + (size_t)std::max(N, 1) + 1;
+    CK(grow(ctx->out, ctx->out_cap, need), "alloc outputs");
+    double* d_grad = mem == DWOS_MEM_DEVICE ? grad_param : ctx->out;
+    if (N > 0) {
+        CK(cudaMemsetAsync(d_grad, 0, (size_t)N * sizeof(double), ctx->stream), "zero grad");
+        CK(launch_gemv(ctx->jac, ctx->dg_vert, ctx->acc_vert, acc_g, ctx->n_vert, ctx->dim, N, d_grad, ctx->stream), "adjoint gemv");
+        ctx->launches += 1;
+    }
+    double* d_loss = nullptr;
+    if (mode == 1) {
+        double* d_mean = ctx->out + std::max(N, 1);
+        CK(launch_reduce_u(ctx->rec, n_query, W, d_mean, nullptr, ctx->stream), "reduce u");
+        d_loss = mem == DWOS_MEM_DEVICE ? loss : ctx->out + std::max(N, 1) + n_query;
+        CK(launch_loss(d_mean, ctx->wvec, n_query, d_loss, ctx->stream), "loss");
+        ctx->launches += n_query > 0 ? 2 : 1;
+    }
+    if (grad_vert)
+        CK(from_device(ctx, grad_vert, ctx->acc_vert, (size_t)ctx->n_vert * ctx->dim, mem), "copy vertex gradient");
+    if (mem == DWOS_MEM_HOST) {
+        if (N > 0) CK(from_device(ctx, grad_param, ctx->out, N, mem), "copy grad");
+        if (mode == 1) CK(from_device(ctx, loss, d_loss, 1, mem), "copy loss");
+        return finish_sync(ctx);
+    }
+    return DWOS_OK;
+}
+
+dwos_status dwos_vjp(dwos_ctx* ctx, int n_query, const float* xq, const float* w, int W,
+                     uint64_t walk_id_base, double* grad_param, double* grad_vert, int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    return reverse_common(ctx, n_query, xq, w, W, walk_id_base, 0, nullptr, grad_param, grad_vert, mem);
+}
+
+dwos_status dwos_grad_l2(dwos_ctx* ctx, int n_query, const float* xq, const float* uref, int W,
+                         uint64_t walk_id_base, double* loss, double* grad_param, double* grad_vert, int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    return reverse_common(ctx, n_query, xq, uref, W, walk_id_base, 1, loss, grad_param, grad_vert, mem);
+}
+
+dwos_status dwos_walk_records(dwos_ctx* ctx, int n_query, const float* xq, int W, uint64_t walk_id_base,
+                              int differential, dwos_record* records, uint32_t* trace, dwos_walk_debug* debug,
+                              int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (dwos_status s = check_mem(ctx, mem)) return s;
+    if (!records) return fail(ctx, DWOS_ERR_INVALID_ARG, "records is NULL");
+    if (mem == DWOS_MEM_DEVICE)
+        for (const void* p : {(const void*)records, (const void*)trace, (const void*)debug})
+            if (dwos_status s = check_device_ptr(ctx, p, "output")) return s;
+    if (dwos_status s = set_device(ctx)) return s;
+    const size_t total = (size_t)std::max(n_query, 0) * (size_t)std::max(W, 0);
+    const int K1 = ctx->opt.K + 1;
+    uint32_t* d_trace = nullptr;
+    dwos_walk_debug* d_dbg = nullptr;
+    if (trace) {
+        if (mem == DWOS_MEM_DEVICE) d_trace = trace;
+        else { CK(grow(ctx->trace, ctx->trace_cap, total * K1), "alloc trace"); d_trace = ctx->trace; }
+        CK(cudaMemsetAsync(d_trace, 0xff, total * K1 * sizeof(uint32_t), ctx->stream), "init trace");
+    }
+    if (debug) {
+        if (mem == DWOS_MEM_DEVICE) d_dbg = debug;
+        else { CK(grow(ctx->dbg, ctx->dbg_cap, total), "alloc debug"); d_dbg = ctx->dbg; }
+    }
+    if (dwos_status s = run_walks(ctx, n_query, xq, W, walk_id_base, differential ? 1 : 0, mem, d_trace, d_dbg)) return s;
+    CK(from_device(ctx, records, ctx->rec, total, mem), "copy records");
+    if (trace && mem == DWOS_MEM_HOST) CK(from_device(ctx, trace, d_trace, total * K1, mem), "copy trace");
+    if (debug && mem == DWOS_MEM_HOST) CK(from_device(ctx, debug, d_dbg, total, mem), "copy debug");
+    if (mem == DWOS_MEM_HOST) return finish_sync(ctx);
+    return DWOS_OK;
+}
+
+dwos_status dwos_last_stats(dwos_ctx* ctx, dwos_run_stats* out) {
+    if (!ctx || !out) return fail(ctx, DWOS_ERR_INVALID_ARG, "NULL argument");
+    if (dwos_status s = set_device(ctx)) return s;
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    DevCounters c;
+    CK(cudaMemcpy(&c, ctx->d_ctr, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
+    out->steps_main = c.steps_main;
+    out->steps_nested = c.steps_nested;
+    out->walks = c.next_work;
+    out->capped = c.capped;
+    out->nodes_visited = c.nodes;
+    out->prims_tested = c.prims;
+    out->launches = ctx->launches;
+    out->blocks = ctx->last_blocks;
+    float ms = 0.0f;
+    if (ctx->timed && cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) != cudaSuccess) { cudaGetLastError(); ms = 0.0f; }
+    out->kernel_ms = ms;
+    return DWOS_OK;
+}
+
+dwos_status dwos_closest_point(dwos_ctx* ctx, int n, const float* p, float* dist, int32_t* elem_out, float* bary,
+                               int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (dwos_status s = check_mem(ctx, mem)) return s;
+    if (!ctx->have_boundary) return fail(ctx, DWOS_ERR_STATE, "no boundary");
+    if (n < 0 || (n > 0 && (!p || !dist || !elem_out || !bary))) return fail(ctx, DWOS_ERR_INVALID_ARG, "bad arguments");
+    if (dwos_status s = set_device(ctx)) return s;
+    CK(grow(ctx->misc_f, ctx->misc_f_cap, (size_t)n * (ctx->dim + 3)), "alloc");
+    CK(grow(ctx->misc_i, ctx->misc_i_cap, (size_t)std::max(n, 1)), "alloc");
+    float* dp = ctx->misc_f;
+    float* dd = dp + (size_t)n * ctx->dim;
+    float* db = dd + n;
+    CK(to_device(ctx, dp, p, (size_t)n * ctx->dim, mem), "copy points");
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream), "reset");
+    CK(launch_closest(ctx->bvh, n, dp, dd, ctx->misc_i, db, ctx->d_err, ctx->stream), "closest point");
+    CK(from_device(ctx, dist, dd, n, mem), "copy");
+    CK(from_device(ctx, elem_out, ctx->misc_i, n, mem), "copy");
+    CK(from_device(ctx, bary, db, 2 * (size_t)n, mem), "copy");
+    if (mem == DWOS_MEM_HOST) {
+        CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+        int err = 0;
+        CK(cudaMemcpy(&err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost), "read flag");
+        if (err) return fail(ctx, DWOS_ERR_STEP_LIMIT, "BVH traversal exceeded its iteration bound");
+    }
+    return DWOS_OK;
+}
+
+dwos_status dwos_inside(dwos_ctx* ctx, int n, const float* p, int32_t* inside, int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (dwos_status s = check_mem(ctx, mem)) return s;
+    if (!ctx->have_boundary) return fail(ctx, DWOS_ERR_STATE, "no boundary");
+    if (n < 0 || (n > 0 && (!p || !inside))) return fail(ctx, DWOS_ERR_INVALID_ARG, "bad arguments");
+    if (dwos_status s = set_device(ctx)) return s;
+    CK(grow(ctx->misc_f, ctx->misc_f_cap, (size_t)n * ctx->dim), "alloc");
+    CK(grow(ctx->misc_i, ctx->misc_i_cap, (size_t)std::max(n, 1)), "alloc");
+    CK(to_device(ctx, ctx->misc_f, p, (size_t)n * ctx->dim, mem), "copy points");
+    CK(launch_inside(ctx->bvh, n, ctx->misc_f, ctx->misc_i, ctx->stream), "inside test");
+    CK(from_device(ctx, inside, ctx->misc_i, n, mem), "copy");
+    if (mem == DWOS_MEM_HOST) CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    return DWOS_OK;
+}
+
+dwos_status dwos_philox4x32_10(dwos_ctx* ctx, int n, const uint32_t* ctr, const uint32_t* key, uint32_t* out,
+                               int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (dwos_status s = check_mem(ctx, mem)) return s;
+    if (n < 0 || (n > 0 && (!ctr || !key || !out))) return fail(ctx, DWOS_ERR_INVALID_ARG, "bad arguments");
+    if (dwos_status s = set_device(ctx)) return s;
+    uint32_t k[2];
+    if (mem == DWOS_MEM_DEVICE) CK(cudaMemcpy(k, key, sizeof(k), cudaMemcpyDeviceToHost), "copy key");
+    else { k[0] = key[0]; k[1] = key[1]; }
+    CK(grow(ctx->misc_u, ctx->misc_u_cap, 8 * (size_t)std::max(n, 1)), "alloc");
+    uint32_t* dc = ctx->misc_u;
+    uint32_t* dout = dc + 4 * (size_t)n;
+    CK(to_device(ctx, dc, ctr, 4 * (size_t)n, mem), "copy counters");
+    CK(launch_philox(n, dc, k[0], k[1], dout, ctx->stream), "philox");
+    CK(from_device(ctx, out, dout, 4 * (size_t)n, mem), "copy");
+    if (mem == DWOS_MEM_HOST) CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    return DWOS_OK;
+}
+
+}  // extern "C"

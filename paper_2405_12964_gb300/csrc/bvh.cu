@@ -1,0 +1,485 @@
+// Linear BVH over boundary elements, built on the device:
+//   element boxes + scene bounds -> Morton codes -> radix sort (CUB) ->
+//   binary radix tree (Karras, "Maximizing parallelism in the construction of
+//   BVHs, octrees and k-d trees", HPG 2012) -> bottom-up box refit with
+//   arrival counters -> leaf primitives written in Morton order.
+// Plus the batched closest-point, ray-parity inside test and Philox kernels.
+#include <cub/device/device_radix_sort.cuh>
+
+#include "dwos_device.cuh"
+#include "dwos_internal.h"
+
+namespace dwos {
+
+namespace {
+
+__device__ __forceinline__ unsigned int float_to_ordered(float f) {
+    const unsigned int u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float ordered_to_float(unsigned int u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+
+template <int DIM>
+__device__ __forceinline__ void elem_box(const float* vert, const int* elem, int e, float* lo, float* hi) {
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { lo[k] = kInf; hi[k] = -kInf; }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        const int v = elem[DIM * e + a];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            const float x = vert[DIM * v + k];
+            lo[k] = fminf(lo[k], x);
+            hi[k] = fmaxf(hi[k], x);
+        }
+    }
+}
+
+template <int DIM>
+__global__ void bounds_kernel(const float* vert, const int* elem, int n, unsigned int* bounds) {
+    float lo[DIM], hi[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { lo[k] = kInf; hi[k] = -kInf; }
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        float l[DIM], h[DIM];
+        elem_box<DIM>(vert, elem, e, l, h);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            const float c = 0.5f * (l[k] + h[k]);
+            lo[k] = fminf(lo[k], c);
+            hi[k] = fmaxf(hi[k], c);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    }
+    if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            atomicMin(bounds + k, float_to_ordered(lo[k]));
+            atomicMax(bounds + DIM + k, float_to_ordered(hi[k]));
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned int spread2(unsigned int x) {   // 16 bits -> even bits
+    x &= 0xffffu;
+    x = (x | (x << 8)) & 0x00ff00ffu;
+    x = (x | (x << 4)) & 0x0f0f0f0fu;
+    x = (x | (x << 2)) & 0x33333333u;
+    x = (x | (x << 1)) & 0x55555555u;
+    return x;
+}
+__device__ __forceinline__ unsigned int spread3(unsigned int x) {   // 10 bits -> every third bit
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000ffu;
+    x = (x | (x << 8)) & 0x0300f00fu;
+    x = (x | (x << 4)) & 0x030c30c3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+}
+
+template <int DIM>
+__global__ void morton_kernel(const float* vert, const int* elem, int n, const unsigned int* bounds,
+                              unsigned int* keys, int* vals) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    float l[DIM], h[DIM];
+    elem_box<DIM>(vert, elem, e, l, h);
+    unsigned int q[DIM];
+    const float levels = DIM == 2 ? 65535.0f : 1023.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const float lo = ordered_to_float(bounds[k]);
+        const float hi = ordered_to_float(bounds[DIM + k]);
+        const float ext = hi - lo;
+        float t = ext > 0.0f ? (0.5f * (l[k] + h[k]) - lo) / ext : 0.5f;
+        t = fminf(fmaxf(t, 0.0f), 1.0f);
+        q[k] = (unsigned int)(t * levels + 0.5f);
+    }
+    keys[e] = DIM == 2 ? (spread2(q[0]) | (spread2(q[1]) << 1))
+                       : (spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2));
+    vals[e] = e;
+}
+
+// Length of the common prefix of keys i and j, with the index as tie-breaker;
+// -1 outside [0, n).
+__device__ __forceinline__ int delta(const unsigned int* k, int n, int i, int j) {
+    if (j < 0 || j >= n) return -1;
+    const unsigned int a = k[i], b = k[j];
+    if (a == b) return 32 + __clz((unsigned int)(i ^ j));
+    return __clz(a ^ b);
+}
+
+__global__ void radix_tree_kernel(const unsigned int* keys, int n, int* node_child, int* node_parent,
+                                  int* leaf_parent) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n - 1) return;
+    const int dir = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = delta(keys, n, i, i - dir);
+    int lmax = 2;
+    while (delta(keys, n, i, i + lmax * dir) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(keys, n, i, i + (l + t) * dir) > dmin) l += t;
+    const int j = i + l * dir;
+    const int dnode = delta(keys, n, i, j);
+    int s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(keys, n, i, i + (s + t) * dir) > dnode) s += t;
+    } while (t > 1);
+    const int split = i + s * dir + min(dir, 0);
+    const int first = min(i, j), last = max(i, j);
+    int left, right;
+    if (first == split) { left = ~split; leaf_parent[split] = i; }
+    else { left = split; node_parent[split] = i; }
+    if (last == split + 1) { right = ~(split + 1); leaf_parent[split + 1] = i; }
+    else { right = split + 1; node_parent[split + 1] = i; }
+    node_child[2 * i] = left;
+    node_child[2 * i + 1] = right;
+    if (i == 0) node_parent[0] = -1;
+}
+
+template <int DIM>
+__device__ __forceinline__ void write_child_box(float4* nodes, int node, int slot, const float* lo,
+                                                const float* hi) {
+    float* f = reinterpret_cast<float*>(nodes + BvhLayout<DIM>::kNodeF4 * node);
+    if (DIM == 2) {
+        float* b = f + 4 * slot;
+        b[0] = lo[0]; b[1] = lo[1]; b[2] = hi[0]; b[3] = hi[1];
+    } else {
+        float* b = f + 6 * slot;
+        b[0] = lo[0]; b[1] = lo[1]; b[2] = lo[2]; b[3] = hi[0]; b[4] = hi[1]; b[5] = hi[2];
+    }
+}
+
+template <int DIM>
+__global__ void refit_kernel(const float* vert, const int* elem, const int* sorted_elem, int n,
+                             const int* node_child, const int* node_parent, const int* leaf_parent,
+                             int* counters, float4* nodes) {
+    const int leaf = blockIdx.x * blockDim.x + threadIdx.x;
+    if (leaf >= n) return;
+    float lo[DIM], hi[DIM];
+    elem_box<DIM>(vert, elem, sorted_elem[leaf], lo, hi);
+    int child = ~leaf;
+    int node = leaf_parent[leaf];
+    while (node >= 0) {
+        const int slot = (node_child[2 * node] == child) ? 0 : 1;
+        write_child_box<DIM>(nodes, node, slot, lo, hi);
+        __threadfence();                                   // publish this child's box
+        if (atomicAdd(counters + node, 1) == 0) return;    // the sibling finishes this node
+        __threadfence();
+        // second arrival: the node's bounds are the union of both child slots (read through L2)
+        const volatile float* f = reinterpret_cast<const volatile float*>(nodes + BvhLayout<DIM>::kNodeF4 * node);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            float a_lo, a_hi, b_lo, b_hi;
+            if (DIM == 2) { a_lo = f[k]; a_hi = f[2 + k]; b_lo = f[4 + k]; b_hi = f[6 + k]; }
+            else { a_lo = f[k]; a_hi = f[3 + k]; b_lo = f[6 + k]; b_hi = f[9 + k]; }
+            lo[k] = fminf(a_lo, b_lo);
+            hi[k] = fmaxf(a_hi, b_hi);
+        }
+        child = node;
+        node = node_parent[node];
+    }
+}
+
+template <int DIM>
+__global__ void finalize_kernel(const float* vert, const int* elem, const int* sorted_elem, int n,
+                                const int* node_child, const int* node_parent, int n_internal,
+                                float4* nodes, float4* prims, int* prim_elem) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_internal) {
+        float4* m = nodes + BvhLayout<DIM>::kNodeF4 * i + (BvhLayout<DIM>::kNodeF4 - 1);
+        *m = make_float4(__int_as_float(node_child[2 * i]), __int_as_float(node_child[2 * i + 1]),
+                         __int_as_float(node_parent[i]), 0.0f);
+    }
+    if (i < n) {
+        const int e = sorted_elem[i];
+        prim_elem[i] = e;
+        if (DIM == 2) {
+            const int a = elem[2 * e], b = elem[2 * e + 1];
+            prims[i] = make_float4(vert[2 * a], vert[2 * a + 1], vert[2 * b], vert[2 * b + 1]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int v = elem[3 * e + c];
+                prims[3 * i + c] = make_float4(vert[3 * v], vert[3 * v + 1], vert[3 * v + 2], 0.0f);
+            }
+        }
+    }
+}
+
+// One element: a single node whose right child is empty.
+template <int DIM>
+__global__ void single_leaf_kernel(const float* vert, const int* elem, float4* nodes, float4* prims,
+                                   int* prim_elem) {
+    float lo[DIM], hi[DIM], elo[DIM], ehi[DIM];
+    elem_box<DIM>(vert, elem, 0, lo, hi);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { elo[k] = kInf; ehi[k] = -kInf; }
+    write_child_box<DIM>(nodes, 0, 0, lo, hi);
+    write_child_box<DIM>(nodes, 0, 1, elo, ehi);
+    nodes[BvhLayout<DIM>::kNodeF4 - 1] =
+        make_float4(__int_as_float(~0), __int_as_float(kEmptyChild), __int_as_float(-1), 0.0f);
+    prim_elem[0] = 0;
+    if (DIM == 2) {
+        prims[0] = make_float4(vert[2 * elem[0]], vert[2 * elem[0] + 1], vert[2 * elem[1]], vert[2 * elem[1] + 1]);
+    } else {
+        for (int c = 0; c < 3; ++c) {
+            const int v = elem[c];
+            prims[c] = make_float4(vert[3 * v], vert[3 * v + 1], vert[3 * v + 2], 0.0f);
+        }
+    }
+}
+
+// ---- queries --------------------------------------------------------------
+template <int DIM>
+__global__ void closest_kernel(BvhView bvh, const int* prim_elem, int n, const float* p, float* dist,
+                               int* elem_out, float* bary, int* err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float q[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) q[k] = p[DIM * i + k];
+    float best2 = kInf;
+    int best = -1;
+    unsigned nn = 0, np = 0;
+    if (!closest_leaf<DIM>(bvh, q, best2, best, nn, np)) atomicOr(err, 1);
+    float w1 = 0.0f, w2 = 0.0f;
+    if (best >= 0) {
+        if (DIM == 2) {
+            const float4 s = bvh.prims[best];
+            best2 = seg_closest(q, s.x, s.y, s.z, s.w, w1);
+        } else {
+            const float4 a = bvh.prims[3 * best], b = bvh.prims[3 * best + 1], c = bvh.prims[3 * best + 2];
+            best2 = tri_closest(q, make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                                make_float3(c.x, c.y, c.z), w1, w2);
+        }
+    }
+    dist[i] = sqrtf(best2);
+    elem_out[i] = best >= 0 ? prim_elem[best] : -1;
+    bary[2 * i] = w1;
+    bary[2 * i + 1] = w2;
+}
+
+// Ray crossing count along a fixed generic direction; any-order stackless
+// traversal over the parent links, pruning boxes the ray misses.
+template <int DIM>
+__device__ __forceinline__ bool ray_hits_box(const float* o, const float* inv, const float* lo, const float* hi) {
+    float t0 = 0.0f, t1 = kInf;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const float a = (lo[k] - o[k]) * inv[k], b = (hi[k] - o[k]) * inv[k];
+        t0 = fmaxf(t0, fminf(a, b));
+        t1 = fminf(t1, fmaxf(a, b));
+    }
+    return t0 <= t1;
+}
+
+template <int DIM>
+__device__ __forceinline__ int ray_prim_cross(const float4* prims, int p, const float* o, const float* dir) {
+    if (DIM == 2) {
+        const float4 s = prims[p];
+        const float ex = s.z - s.x, ey = s.w - s.y;
+        const float det = -dir[0] * ey + dir[1] * ex;
+        if (det == 0.0f) return 0;
+        const float rx = s.x - o[0], ry = s.y - o[1];
+        const float t = (-rx * ey + ry * ex) / det;
+        const float u = (dir[0] * ry - dir[1] * rx) / det;
+        return (t > 0.0f && u >= 0.0f && u < 1.0f) ? 1 : 0;
+    } else {
+        const float4 a = prims[3 * p], b = prims[3 * p + 1], c = prims[3 * p + 2];
+        const float e1[3] = {b.x - a.x, b.y - a.y, b.z - a.z};
+        const float e2[3] = {c.x - a.x, c.y - a.y, c.z - a.z};
+        const float pv[3] = {dir[1] * e2[2] - dir[2] * e2[1], dir[2] * e2[0] - dir[0] * e2[2],
+                             dir[0] * e2[1] - dir[1] * e2[0]};
+        const float det = e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2];
+        if (det == 0.0f) return 0;
+        const float inv = 1.0f / det;
+        const float tv[3] = {o[0] - a.x, o[1] - a.y, o[2] - a.z};
+        const float u = (tv[0] * pv[0] + tv[1] * pv[1] + tv[2] * pv[2]) * inv;
+        if (u < 0.0f || u > 1.0f) return 0;
+        const float qv[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2],
+                             tv[0] * e1[1] - tv[1] * e1[0]};
+        const float v = (dir[0] * qv[0] + dir[1] * qv[1] + dir[2] * qv[2]) * inv;
+        if (v < 0.0f || u + v > 1.0f) return 0;
+        const float t = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) * inv;
+        return t > 0.0f ? 1 : 0;
+    }
+}
+
+template <int DIM>
+__global__ void inside_kernel(BvhView bvh, int n, const float* p, int* inside) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float o[DIM], dir[DIM], inv[DIM];
+    if (DIM == 2) { dir[0] = 0.8191520443f; dir[1] = 0.5735764364f; }
+    else { dir[0] = 0.5144957554f; dir[1] = 0.6859943406f; dir[2] = 0.5144957554f; }
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { o[k] = p[DIM * i + k]; inv[k] = 1.0f / dir[k]; }
+    int count = 0;
+    int node = bvh.root, from = kFromParent;
+    int budget = 3 * bvh.n_internal + 8;
+    while (--budget >= 0) {
+        float lo0[DIM], hi0[DIM], lo1[DIM], hi1[DIM];
+        int c0, c1, parent;
+        load_node<DIM>(bvh.nodes, node, lo0, hi0, lo1, hi1, c0, c1, parent);
+        int state = from == kFromParent ? 0 : (from == c0 ? 1 : 2);
+        int next = kFromParent;
+        while (state < 2) {
+            const int c = state == 0 ? c0 : c1;
+            const bool hit = c != kEmptyChild &&
+                             (state == 0 ? ray_hits_box<DIM>(o, inv, lo0, hi0) : ray_hits_box<DIM>(o, inv, lo1, hi1));
+            if (hit && c >= 0) { next = c; break; }
+            if (hit) count += ray_prim_cross<DIM>(bvh.prims, ~c, o, dir);
+            ++state;
+        }
+        if (next != kFromParent) { from = kFromParent; node = next; continue; }
+        if (parent < 0) break;
+        from = node;
+        node = parent;
+    }
+    inside[i] = count & 1;
+}
+
+__global__ void philox_kernel(int n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const U4 r = philox(U4{ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]}, k0, k1);
+    out[4 * i] = r.x; out[4 * i + 1] = r.y; out[4 * i + 2] = r.z; out[4 * i + 3] = r.w;
+}
+
+// v = v_ref + J theta, one thread per (vertex, coordinate) row.
+__global__ void apply_params_kernel(const float* vert_ref, const float* jac, const float* theta, float* vert,
+                                    int n_rows, int n_param) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rows) return;
+    float s = vert_ref[r];
+    const float* J = jac + (size_t)r * n_param;
+    for (int j = 0; j < n_param; ++j) s = fmaf(J[j], theta[j], s);
+    vert[r] = s;
+}
+
+inline int nblk(long long n, int b) { return (int)((n + b - 1) / b); }
+
+}  // namespace
+
+cudaError_t bvh_reserve(BvhBuffers& b, int dim, int n_elem) {
+    if (n_elem <= b.capacity && dim == b.dim) return cudaSuccess;
+    bvh_free(b);
+    const int n_int = n_elem > 1 ? n_elem - 1 : 1;
+    const int nf4 = dim == 2 ? 3 : 4, pf4 = dim == 2 ? 1 : 3;
+    cudaError_t e;
+#define DW_TRY(x) do { e = (x); if (e != cudaSuccess) { bvh_free(b); return e; } } while (0)
+    DW_TRY(cudaMalloc(&b.nodes, sizeof(float4) * nf4 * (size_t)n_int));
+    DW_TRY(cudaMalloc(&b.prims, sizeof(float4) * pf4 * (size_t)n_elem));
+    DW_TRY(cudaMalloc(&b.prim_elem, sizeof(int) * (size_t)n_elem));
+    DW_TRY(cudaMalloc(&b.keys, sizeof(unsigned int) * (size_t)n_elem));
+    DW_TRY(cudaMalloc(&b.keys_sorted, sizeof(unsigned int) * (size_t)n_elem));
+    DW_TRY(cudaMalloc(&b.vals, sizeof(int) * (size_t)n_elem));
+    DW_TRY(cudaMalloc(&b.vals_sorted, sizeof(int) * (size_t)n_elem));
+    DW_TRY(cudaMalloc(&b.leaf_parent, sizeof(int) * (size_t)n_elem));
+    DW_TRY(cudaMalloc(&b.node_parent, sizeof(int) * (size_t)n_int));
+    DW_TRY(cudaMalloc(&b.node_child, sizeof(int) * 2 * (size_t)n_int));
+    DW_TRY(cudaMalloc(&b.counters, sizeof(int) * (size_t)n_int));
+    DW_TRY(cudaMalloc(&b.bounds, sizeof(unsigned int) * 6));
+    size_t tmp = 0;
+    DW_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp, b.keys, b.keys_sorted, b.vals, b.vals_sorted, n_elem));
+    DW_TRY(cudaMalloc(&b.sort_tmp, tmp));
+#undef DW_TRY
+    b.sort_tmp_bytes = tmp;
+    b.capacity = n_elem;
+    b.dim = dim;
+    return cudaSuccess;
+}
+
+void bvh_free(BvhBuffers& b) {
+    cudaFree(b.nodes); cudaFree(b.prims); cudaFree(b.prim_elem); cudaFree(b.keys); cudaFree(b.keys_sorted);
+    cudaFree(b.vals); cudaFree(b.vals_sorted); cudaFree(b.leaf_parent); cudaFree(b.node_parent);
+    cudaFree(b.node_child); cudaFree(b.counters); cudaFree(b.bounds);
+    cudaFree(b.sort_tmp);
+    b = BvhBuffers();
+}
+
+template <int DIM>
+static cudaError_t build_impl(BvhBuffers& b, const float* vert, const int* elem, int n, cudaStream_t s) {
+    b.n_elem = n;
+    if (n == 1) {
+        b.n_internal = 1;
+        single_leaf_kernel<DIM><<<1, 1, 0, s>>>(vert, elem, b.nodes, b.prims, b.prim_elem);
+        return cudaGetLastError();
+    }
+    b.n_internal = n - 1;
+    cudaError_t e = cudaMemsetAsync(b.bounds, 0xff, sizeof(unsigned int) * DIM, s);   // min slots
+    if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(b.bounds + DIM, 0, sizeof(unsigned int) * DIM, s);             // max slots
+    if (e != cudaSuccess) return e;
+    bounds_kernel<DIM><<<min(nblk(n, 256), 1024), 256, 0, s>>>(vert, elem, n, b.bounds);
+    morton_kernel<DIM><<<nblk(n, 256), 256, 0, s>>>(vert, elem, n, b.bounds, b.keys, b.vals);
+    size_t tmp = b.sort_tmp_bytes;
+    e = cub::DeviceRadixSort::SortPairs(b.sort_tmp, tmp, b.keys, b.keys_sorted, b.vals, b.vals_sorted, n, 0,
+                                        DIM == 2 ? 32 : 30, s);
+    if (e != cudaSuccess) return e;
+    radix_tree_kernel<<<nblk(n - 1, 256), 256, 0, s>>>(b.keys_sorted, n, b.node_child, b.node_parent,
+                                                       b.leaf_parent);
+    e = cudaMemsetAsync(b.counters, 0, sizeof(int) * (size_t)(n - 1), s);
+    if (e != cudaSuccess) return e;
+    refit_kernel<DIM><<<nblk(n, 256), 256, 0, s>>>(vert, elem, b.vals_sorted, n, b.node_child, b.node_parent,
+                                                   b.leaf_parent, b.counters, b.nodes);
+    finalize_kernel<DIM><<<nblk(n, 256), 256, 0, s>>>(vert, elem, b.vals_sorted, n, b.node_child,
+                                                      b.node_parent, n - 1, b.nodes, b.prims, b.prim_elem);
+    return cudaGetLastError();
+}
+
+cudaError_t bvh_build(BvhBuffers& b, int dim, const float* vert, const int* elem, int n_elem, cudaStream_t s) {
+    cudaError_t e = bvh_reserve(b, dim, n_elem);
+    if (e != cudaSuccess) return e;
+    return dim == 2 ? build_impl<2>(b, vert, elem, n_elem, s) : build_impl<3>(b, vert, elem, n_elem, s);
+}
+
+static BvhView view_of(const BvhBuffers& b) {
+    BvhView v;
+    v.nodes = b.nodes;
+    v.prims = b.prims;
+    v.root = 0;
+    v.n_internal = b.n_internal;
+    return v;
+}
+
+cudaError_t launch_closest(const BvhBuffers& b, int n, const float* p, float* dist, int* elem_out, float* bary,
+                           int* err, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (b.dim == 2) closest_kernel<2><<<nblk(n, 128), 128, 0, s>>>(view_of(b), b.prim_elem, n, p, dist, elem_out, bary, err);
+    else closest_kernel<3><<<nblk(n, 128), 128, 0, s>>>(view_of(b), b.prim_elem, n, p, dist, elem_out, bary, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_inside(const BvhBuffers& b, int n, const float* p, int* inside, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (b.dim == 2) inside_kernel<2><<<nblk(n, 128), 128, 0, s>>>(view_of(b), n, p, inside);
+    else inside_kernel<3><<<nblk(n, 128), 128, 0, s>>>(view_of(b), n, p, inside);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(int n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    philox_kernel<<<nblk(n, 256), 256, 0, s>>>(n, ctr, k0, k1, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_params(const float* vert_ref, const float* jac, const float* theta, float* vert,
+                                int n_rows, int n_param, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    apply_params_kernel<<<nblk(n_rows, 256), 256, 0, s>>>(vert_ref, jac, theta, vert, n_rows, n_param);
+    return cudaGetLastError();
+}
+
+}  // namespace dwos

@@ -1,0 +1,282 @@
+// Device-side building blocks of the walk-on-spheres library (sm_103a).
+//
+//  - Philox4x32-10 counter RNG (Salmon et al., SC'11) and the uniform map
+//  - uniform sphere / ball sampling (Algorithm 1: SampleUnitSphere, SampleUnitBall)
+//  - the ball Green's function source weight |B| G and the recursive weight
+//    alpha = P |dB| for the screened Poisson equation (Sec. 3.3.1; G and P are
+//    derived from the PDE because the paper defers them to WoSt App. A)
+//  - closest point on a segment / triangle (DistanceToBoundary, Algorithm 1)
+//  - BVH node layout and a stackless, near-child-first closest-point traversal
+//    over parent links (Hapala et al. 2011 style state machine)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dwos {
+
+constexpr int kFromParent = 0x7fffffff;   // traversal state: entered from above
+constexpr int kEmptyChild = 0x7ffffffe;   // child slot with an empty box
+constexpr float kInf = __builtin_inff();
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10: ten rounds, two 32x32 multiplies per round, key bumped by the
+// Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox(U4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        c = U4{hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// ((x >> 9) * 2 + 1) * 2^-24: an odd multiple of 2^-24 in (0, 1), exact in FP32.
+__device__ __forceinline__ float u01(uint32_t x) {
+    return (float)((x >> 9) * 2u + 1u) * 5.9604644775390625e-8f;
+}
+
+// One Philox block of a walk step.  counter = (id lo, id hi, step, phase<<8 | block)
+__device__ __forceinline__ U4 draw_block(uint32_t seed_lo, uint32_t seed_hi, unsigned long long walk_id,
+                                         uint32_t step, uint32_t phase, uint32_t block) {
+    U4 c{(uint32_t)walk_id, (uint32_t)(walk_id >> 32), step, (phase << 8) | block};
+    return philox(c, seed_lo, seed_hi);
+}
+
+// ---------------------------------------------------------------------------
+// Green's function weights on a ball of radius d (k = sqrt(sigma)).
+// ---------------------------------------------------------------------------
+// Modified Bessel K0 for x > 0: Abramowitz & Stegun 9.8.5 (x <= 2, with I0)
+// and 9.8.6 (x > 2) polynomial approximations (|error| < 2e-7 relative).
+__device__ __forceinline__ float bessel_k0(float x) {
+    if (x <= 2.0f) {
+        const float t = 0.25f * x * x;   // (x/2)^2
+        float p = 0.74e-5f;
+        p = fmaf(p, t, 0.10750e-3f);
+        p = fmaf(p, t, 0.262698e-2f);
+        p = fmaf(p, t, 0.3488590e-1f);
+        p = fmaf(p, t, 0.23069756f);
+        p = fmaf(p, t, 0.42278420f);
+        p = fmaf(p, t, -0.57721566f);
+        return -logf(0.5f * x) * cyl_bessel_i0f(x) + p;
+    }
+    const float t = 2.0f / x;
+    float p = 0.00053208f;
+    p = fmaf(p, t, -0.00251540f);
+    p = fmaf(p, t, 0.00587872f);
+    p = fmaf(p, t, -0.01062446f);
+    p = fmaf(p, t, 0.02189568f);
+    p = fmaf(p, t, -0.07832358f);
+    p = fmaf(p, t, 1.25331414f);
+    return expf(-x) * rsqrtf(x) * p;
+}
+
+// alpha(d) = P(d) |dB(d)|: 1/I0(kd) in 2D, kd/sinh(kd) in 3D, 1 when sigma = 0.
+template <int DIM>
+__device__ __forceinline__ float recursive_weight(float k, float d) {
+    if (k == 0.0f) return 1.0f;
+    const float kd = k * d;
+    if (DIM == 2) return 1.0f / cyl_bessel_i0f(kd);
+    // kd / sinh(kd) = -2 kd e^{-kd} / expm1(-2 kd): no overflow, exact limit 1 at 0
+    return -2.0f * kd * expf(-kd) / expm1f(-2.0f * kd);
+}
+
+// |B(d)| G_d(r) for the ball sample's radius: u is the Philox uniform that
+// sets r = d u^(1/DIM).  The source estimate of Algorithm 1 is this times f.
+template <int DIM>
+__device__ __forceinline__ float source_weight(float k, float d, float u) {
+    const float d2 = d * d;
+    if (DIM == 2) {
+        if (k == 0.0f) return -0.25f * d2 * logf(u);          // (d^2/2) log(d/r)
+        const float rho = sqrtf(u);
+        const float kd = k * d, kr = kd * rho;
+        float g = bessel_k0(kr);
+        if (kd < 80.0f) g -= bessel_k0(kd) * cyl_bessel_i0f(kr) / cyl_bessel_i0f(kd);
+        return 0.5f * d2 * g;
+    }
+    const float rho = cbrtf(u);
+    if (k == 0.0f) return (d2 * (1.0f / 3.0f)) * (1.0f / rho - 1.0f);
+    const float a = k * d * (1.0f - rho), b = k * d;
+    // sinh(a)/sinh(b) = e^{a-b} expm1(-2a) / expm1(-2b)
+    const float ratio = expf(a - b) * expm1f(-2.0f * a) / expm1f(-2.0f * b);
+    return (d2 * (1.0f / 3.0f)) * ratio / rho;
+}
+
+// ---------------------------------------------------------------------------
+// Closest point on one element.  Segments: clamp the projection parameter.
+// Triangles: Voronoi-region classification (Ericson, Real-Time Collision
+// Detection, Sec. 5.1.5).  Both return the squared distance and the weights
+// of vertices 1 (and 2).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float seg_closest(const float* q, float ax, float ay, float bx, float by,
+                                             float& t_out) {
+    const float ex = bx - ax, ey = by - ay;
+    const float px = q[0] - ax, py = q[1] - ay;
+    const float len2 = ex * ex + ey * ey;
+    float t = len2 > 0.0f ? (px * ex + py * ey) / len2 : 0.0f;
+    t = fminf(fmaxf(t, 0.0f), 1.0f);
+    const float dx = px - t * ex, dy = py - t * ey;
+    t_out = t;
+    return dx * dx + dy * dy;
+}
+
+__device__ __forceinline__ float tri_closest(const float* q, const float3 a, const float3 b, const float3 c,
+                                             float& w1, float& w2) {
+    const float3 ab = make_float3(b.x - a.x, b.y - a.y, b.z - a.z);
+    const float3 ac = make_float3(c.x - a.x, c.y - a.y, c.z - a.z);
+    const float3 ap = make_float3(q[0] - a.x, q[1] - a.y, q[2] - a.z);
+    const float d1 = ab.x * ap.x + ab.y * ap.y + ab.z * ap.z;
+    const float d2 = ac.x * ap.x + ac.y * ap.y + ac.z * ap.z;
+    const float3 bp = make_float3(q[0] - b.x, q[1] - b.y, q[2] - b.z);
+    const float d3 = ab.x * bp.x + ab.y * bp.y + ab.z * bp.z;
+    const float d4 = ac.x * bp.x + ac.y * bp.y + ac.z * bp.z;
+    const float3 cp = make_float3(q[0] - c.x, q[1] - c.y, q[2] - c.z);
+    const float d5 = ab.x * cp.x + ab.y * cp.y + ab.z * cp.z;
+    const float d6 = ac.x * cp.x + ac.y * cp.y + ac.z * cp.z;
+    const float vc = d1 * d4 - d3 * d2;
+    const float vb = d5 * d2 - d1 * d6;
+    const float va = d3 * d6 - d5 * d4;
+    float s, t;
+    if (d1 <= 0.0f && d2 <= 0.0f) { s = 0.0f; t = 0.0f; }                          // vertex a
+    else if (d3 >= 0.0f && d4 <= d3) { s = 1.0f; t = 0.0f; }                        // vertex b
+    else if (vc <= 0.0f && d1 >= 0.0f && d3 <= 0.0f) { s = d1 / (d1 - d3); t = 0.0f; }  // edge ab
+    else if (d6 >= 0.0f && d5 <= d6) { s = 0.0f; t = 1.0f; }                        // vertex c
+    else if (vb <= 0.0f && d2 >= 0.0f && d6 <= 0.0f) { s = 0.0f; t = d2 / (d2 - d6); }  // edge ac
+    else if (va <= 0.0f && (d4 - d3) >= 0.0f && (d5 - d6) >= 0.0f) {                // edge bc
+        const float u = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+        s = 1.0f - u; t = u;
+    } else {                                                                          // face
+        const float inv = 1.0f / (va + vb + vc);
+        s = vb * inv; t = vc * inv;
+    }
+    const float rx = ap.x - s * ab.x - t * ac.x;
+    const float ry = ap.y - s * ab.y - t * ac.y;
+    const float rz = ap.z - s * ab.z - t * ac.z;
+    w1 = s;
+    w2 = t;
+    return rx * rx + ry * ry + rz * rz;
+}
+
+// ---------------------------------------------------------------------------
+// BVH layout.  Internal node i stores both children's boxes (so a parent's
+// fetch decides which child to enter), the child codes (>= 0: internal node,
+// < 0: ~leaf index, kEmptyChild: nothing) and its parent (-1 at the root).
+//   2D node: 3 float4 = 48 B   [L.lo.xy L.hi.xy] [R.lo.xy R.hi.xy] [left right parent -]
+//   3D node: 4 float4 = 64 B   [L.lo.xyz L.hi.x] [L.hi.yz R.lo.xy] [R.lo.z R.hi.xyz] [left right parent -]
+// Leaves hold one element each, in Morton order:
+//   2D prim: 1 float4 [a.xy b.xy];  3D prim: 3 float4 [a.xyz -] [b.xyz -] [c.xyz -]
+// ---------------------------------------------------------------------------
+template <int DIM> struct BvhLayout;
+template <> struct BvhLayout<2> { static constexpr int kNodeF4 = 3; static constexpr int kPrimF4 = 1; };
+template <> struct BvhLayout<3> { static constexpr int kNodeF4 = 4; static constexpr int kPrimF4 = 3; };
+
+struct BvhView {
+    const float4* nodes;
+    const float4* prims;
+    int root;
+    int n_internal;
+};
+
+template <int DIM>
+__device__ __forceinline__ float box_dist2(const float* q, const float* lo, const float* hi) {
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const float e = fmaxf(fmaxf(lo[k] - q[k], q[k] - hi[k]), 0.0f);
+        s = fmaf(e, e, s);
+    }
+    return s;
+}
+
+template <int DIM>
+__device__ __forceinline__ void load_node(const float4* __restrict__ nodes, int i, float* lo0, float* hi0,
+                                          float* lo1, float* hi1, int& c0, int& c1, int& parent) {
+    if (DIM == 2) {
+        const float4 a = __ldg(nodes + 3 * i + 0);
+        const float4 b = __ldg(nodes + 3 * i + 1);
+        const float4 m = __ldg(nodes + 3 * i + 2);
+        lo0[0] = a.x; lo0[1] = a.y; hi0[0] = a.z; hi0[1] = a.w;
+        lo1[0] = b.x; lo1[1] = b.y; hi1[0] = b.z; hi1[1] = b.w;
+        c0 = __float_as_int(m.x); c1 = __float_as_int(m.y); parent = __float_as_int(m.z);
+    } else {
+        const float4 a = __ldg(nodes + 4 * i + 0);
+        const float4 b = __ldg(nodes + 4 * i + 1);
+        const float4 c = __ldg(nodes + 4 * i + 2);
+        const float4 m = __ldg(nodes + 4 * i + 3);
+        lo0[0] = a.x; lo0[1] = a.y; lo0[2] = a.z; hi0[0] = a.w;
+        hi0[1] = b.x; hi0[2] = b.y; lo1[0] = b.z; lo1[1] = b.w;
+        lo1[2] = c.x; hi1[0] = c.y; hi1[1] = c.z; hi1[2] = c.w;
+        c0 = __float_as_int(m.x); c1 = __float_as_int(m.y); parent = __float_as_int(m.z);
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ float prim_dist2(const float4* __restrict__ prims, int p, const float* q) {
+    if (DIM == 2) {
+        const float4 s = __ldg(prims + p);
+        float t;
+        return seg_closest(q, s.x, s.y, s.z, s.w, t);
+    } else {
+        const float4 a = __ldg(prims + 3 * p + 0);
+        const float4 b = __ldg(prims + 3 * p + 1);
+        const float4 c = __ldg(prims + 3 * p + 2);
+        float w1, w2;
+        return tri_closest(q, make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                           make_float3(c.x, c.y, c.z), w1, w2);
+    }
+}
+
+// Closest leaf to q.  On entry best2 / best hold an upper bound and its leaf
+// (a previous hit: any element's distance bounds the minimum), or kInf / -1.
+// Near-child-first descent; on the way back up, each parent is refetched and
+// its children re-ordered by the same box distances, so no stack is needed.
+// Returns false if the iteration bound was exceeded (never in a valid tree:
+// each internal node is entered at most three times).
+template <int DIM>
+__device__ __forceinline__ bool closest_leaf(const BvhView& bvh, const float* q, float& best2, int& best,
+                                             unsigned& n_nodes, unsigned& n_prims) {
+    int node = bvh.root;
+    int from = kFromParent;
+    int budget = 3 * bvh.n_internal + 8;
+    for (;;) {
+        if (--budget < 0) return false;
+        ++n_nodes;
+        float lo0[DIM], hi0[DIM], lo1[DIM], hi1[DIM];
+        int c0, c1, parent;
+        load_node<DIM>(bvh.nodes, node, lo0, hi0, lo1, hi1, c0, c1, parent);
+        const float d0 = box_dist2<DIM>(q, lo0, hi0);
+        const float d1 = box_dist2<DIM>(q, lo1, hi1);
+        const bool first0 = d0 <= d1;
+        const int nearc = first0 ? c0 : c1, farc = first0 ? c1 : c0;
+        const float dn = first0 ? d0 : d1, df = first0 ? d1 : d0;
+        int state = (from == kFromParent) ? 0 : (from == nearc ? 1 : 2);
+        int next = kFromParent;
+        for (;;) {
+            int cand = kFromParent;
+            if (state == 0) { if (dn < best2) cand = nearc; else state = 2; }
+            if (state == 1) { if (df < best2) cand = farc; }
+            if (cand == kFromParent) break;
+            if (cand < 0) {                       // leaf: test in place
+                const int p = ~cand;
+                ++n_prims;
+                const float dd = prim_dist2<DIM>(bvh.prims, p, q);
+                if (dd < best2) { best2 = dd; best = p; }
+                state = (state == 0) ? 1 : 2;
+                continue;
+            }
+            next = cand;
+            break;
+        }
+        if (next != kFromParent) { from = kFromParent; node = next; continue; }
+        if (parent < 0) return true;
+        from = node;
+        node = parent;
+    }
+}
+
+}  // namespace dwos

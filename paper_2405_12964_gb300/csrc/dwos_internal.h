@@ -1,0 +1,121 @@
+// Host/device shared declarations of the library (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/dwos.h"
+
+namespace dwos {
+
+// Everything a walk needs about one problem.  Copied to the device (and, in
+// the walk kernel, into shared memory) once per launch.
+struct DevProblem {
+    // BVH and mesh
+    const float4* nodes;
+    const float4* prims;
+    const int* prim_elem;       // leaf (Morton order) -> input element id
+    const int* elem;            // n_elem x dim vertex ids
+    const float* g_vert;        // n_vert (mapped data)
+    int root;
+    int n_internal;
+    int data_kind;              // 0 mapped, 1 field
+    int differential;
+    float field[10];            // c0, c(3), Axx Ayy Azz Axy Axz Ayz
+    float sqrt_sigma;
+    float f;
+    float eps;
+    float h;
+    float inv_h;
+    int K;
+    int max_steps;
+    uint32_t seed_lo, seed_hi;
+    // work
+    const float* xq;            // n_query x dim
+    const int* valid;           // n_query inside flags, or null (no check)
+    int walks;                  // walks per point
+    int pad0;
+    unsigned long long walk_id_base;
+    unsigned long long work_begin;   // first global work index of this problem
+    unsigned long long work_end;
+    // outputs
+    dwos_record* rec;           // one per walk (local index p*W + w)
+    uint32_t* trace;            // (K+1) per walk or null
+    dwos_walk_debug* dbg;       // one per walk or null
+};
+
+struct DevCounters {
+    unsigned long long next_work;
+    unsigned long long steps_main;
+    unsigned long long steps_nested;
+    unsigned long long capped;
+    unsigned long long nodes;   // BVH node fetches
+    unsigned long long prims;   // element distance tests
+    int error;                  // bit 0: traversal bound exceeded, bit 1: query outside Omega
+    int pad[3];
+};
+
+// BVH build (bvh.cu).  All pointers are device pointers; work on `stream`.
+struct BvhBuffers {
+    int dim = 0, n_elem = 0, n_internal = 0;
+    float4* nodes = nullptr;      // max(1, n_elem-1) nodes
+    float4* prims = nullptr;      // n_elem prims
+    int* prim_elem = nullptr;     // n_elem
+    // scratch
+    unsigned int* keys = nullptr;
+    unsigned int* keys_sorted = nullptr;
+    int* vals = nullptr;
+    int* vals_sorted = nullptr;
+    int* leaf_parent = nullptr;
+    int* node_parent = nullptr;
+    int* node_child = nullptr;    // 2 per internal node
+    int* counters = nullptr;
+    unsigned int* bounds = nullptr;  // 2*dim ordered-uint scene bounds
+    void* sort_tmp = nullptr;
+    size_t sort_tmp_bytes = 0;
+    int capacity = 0;
+};
+
+cudaError_t bvh_reserve(BvhBuffers& b, int dim, int n_elem);
+void bvh_free(BvhBuffers& b);
+cudaError_t bvh_build(BvhBuffers& b, int dim, const float* vert, const int* elem, int n_elem,
+                      cudaStream_t stream);
+
+// Batched queries through the BVH (bvh.cu).
+cudaError_t launch_closest(const BvhBuffers& b, int n, const float* p, float* dist, int* elem_out,
+                           float* bary, int* err, cudaStream_t stream);
+cudaError_t launch_inside(const BvhBuffers& b, int n, const float* p, int* inside, cudaStream_t stream);
+cudaError_t launch_philox(int n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
+                          cudaStream_t stream);
+cudaError_t launch_apply_params(const float* vert_ref, const float* jac, const float* theta, float* vert,
+                                int n_rows, int n_param, cudaStream_t stream);
+
+// Walk kernel (walk.cu).
+struct WalkLaunch {
+    int dim;
+    int block_size;
+    int blocks_per_sm;
+    int n_sm;
+};
+cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_probs,
+                         unsigned long long total_work, DevCounters* d_counters, cudaStream_t stream,
+                         int* blocks_used);
+int walk_max_blocks_per_sm(int dim, int block_size);
+
+// Estimator reductions (estimators.cu).
+cudaError_t launch_reduce_u(const dwos_record* rec, int n_points, int W, double* mean, double* se,
+                            cudaStream_t stream);
+cudaError_t launch_reduce_udot(const dwos_record* rec, const int* elem, const float* jac, const float* dg,
+                               int dim, int n_param, int n_points, int W, double* mean, double* se,
+                               cudaStream_t stream);
+// mode 0: VJP weights w_p / W;  mode 1: U-statistic L2 weights in batches of B.
+cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int n_points, int W, int B,
+                           int mode, const float* cot_or_uref, double* acc_vert, double* acc_g,
+                           cudaStream_t stream);
+cudaError_t launch_gemv(const float* jac, const float* dg, const double* acc_vert, const double* acc_g,
+                        int n_vert, int dim, int n_param, double* grad, cudaStream_t stream);
+cudaError_t launch_loss(const double* mean, const float* uref, int n_points, double* loss,
+                        cudaStream_t stream);
+
+}  // namespace dwos

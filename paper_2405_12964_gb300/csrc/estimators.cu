@@ -1,0 +1,260 @@
+// Estimator reductions over per-walk records (FP64 sums).
+//
+//  reduce_u     per-point mean and standard error of u (Sec. 3.3)
+//  reduce_udot  forward-mode udot per point and parameter (Sec. 4.1, the
+//               N-vector of one walk rebuilt from its record and the vertex
+//               Jacobians)
+//  scatter      reverse mode (Sec. 4.3): a weight per walk (VJP cotangent, or
+//               the U-statistic product weight of Eq. (ustatistics) in batches
+//               of B) times the walk's boundary term, scattered into per-vertex
+//               FP64 accumulators a_v (d values) and s_v; lanes of a warp that
+//               hit the same vertex are summed before one atomic per vertex
+//  gemv         the adjoint map grad_theta = sum_v J_v^T a_v + sum_v dg_v s_v
+//  loss         1/2 sum_p (mean_p - uref_p)^2
+#include "dwos_device.cuh"
+#include "dwos_internal.h"
+
+namespace dwos {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+__global__ void reduce_u_kernel(const dwos_record* __restrict__ rec, int W, double* mean, double* se) {
+    const int p = blockIdx.x;
+    double s = 0.0, s2 = 0.0;
+    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+        const double u = rec[(size_t)p * W + w].u;
+        s += u;
+        s2 += u * u;
+    }
+    __shared__ double sh[2][32];
+    s = warp_sum(s);
+    s2 = warp_sum(s2);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sh[0][warp] = s; sh[1][warp] = s2; }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        s = lane < nw ? sh[0][lane] : 0.0;
+        s2 = lane < nw ? sh[1][lane] : 0.0;
+        s = warp_sum(s);
+        s2 = warp_sum(s2);
+        if (lane == 0) {
+            const double m = s / W;
+            mean[p] = m;
+            if (se) {
+                const double var = W > 1 ? fmax(s2 - W * m * m, 0.0) / (W - 1) : 0.0;
+                se[p] = sqrt(var / W);
+            }
+        }
+    }
+}
+
+// Forward-mode derivative of one walk for parameter j.
+template <int DIM>
+__device__ __forceinline__ double walk_udot(const dwos_record& r, const int* __restrict__ elem,
+                                            const float* __restrict__ jac, const float* __restrict__ dg, int N,
+                                            int j) {
+    if (r.elem < 0) return 0.0;
+    const float w[3] = {1.0f - r.b1 - r.b2, r.b1, r.b2};
+    double v = 0.0;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        const int vid = __ldg(elem + DIM * r.elem + i);
+        const float* J = jac + (size_t)vid * DIM * N + j;
+        float cj = 0.0f;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) cj = fmaf(r.c[k], __ldg(J + (size_t)k * N), cj);
+        if (dg) cj += __ldg(dg + (size_t)vid * N + j);
+        v += (double)w[i] * cj;
+    }
+    return v;
+}
+
+template <int DIM>
+__global__ void reduce_udot_kernel(const dwos_record* __restrict__ rec, const int* __restrict__ elem,
+                                   const float* __restrict__ jac, const float* __restrict__ dg, int N, int W,
+                                   double* mean, double* se) {
+    const int p = blockIdx.x;
+    const int j = blockIdx.y * 32 + threadIdx.x;
+    double s = 0.0, s2 = 0.0;
+    if (j < N) {
+        for (int w = threadIdx.y; w < W; w += blockDim.y) {
+            const dwos_record r = rec[(size_t)p * W + w];
+            const double v = walk_udot<DIM>(r, elem, jac, dg, N, j);
+            s += v;
+            s2 += v * v;
+        }
+    }
+    __shared__ double sh[2][8][33];
+    sh[0][threadIdx.y][threadIdx.x] = s;
+    sh[1][threadIdx.y][threadIdx.x] = s2;
+    __syncthreads();
+    if (threadIdx.y == 0 && j < N) {
+        for (int y = 1; y < blockDim.y; ++y) { s += sh[0][y][threadIdx.x]; s2 += sh[1][y][threadIdx.x]; }
+        const double m = s / W;
+        mean[(size_t)p * N + j] = m;
+        if (se) {
+            const double var = W > 1 ? fmax(s2 - W * m * m, 0.0) / (W - 1) : 0.0;
+            se[(size_t)p * N + j] = sqrt(var / W);
+        }
+    }
+}
+
+// Sum of v over the lanes in `peers` (all 32 lanes call this together).
+__device__ __forceinline__ double peer_sum(double v, unsigned peers) {
+    double acc = 0.0;
+    for (int src = 0; src < 32; ++src) {
+        const double t = __shfl_sync(kFull, v, src);
+        if ((peers >> src) & 1u) acc += t;
+    }
+    return acc;
+}
+
+template <int DIM>
+__global__ void scatter_kernel(const dwos_record* __restrict__ rec, const int* __restrict__ elem, int n_points,
+                               int W, int B, int mode, const float* __restrict__ cot_or_uref,
+                               double* __restrict__ acc_vert, double* __restrict__ acc_g) {
+    const long long total = (long long)n_points * W;
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = i < total;
+    dwos_record r;
+    if (valid) r = rec[i];
+    else { r.u = 0.0f; r.elem = -1; r.b1 = 0.0f; r.b2 = 0.0f; r.c[0] = r.c[1] = r.c[2] = 0.0f; r.meta = 0; }
+    const int p = valid ? (int)(i / W) : 0;
+    double wt;
+    if (mode == 0) {
+        wt = valid ? (double)cot_or_uref[p] / W : 0.0;
+    } else {
+        // U-statistic weight of Eq. (ustatistics) for squared loss:
+        // u*udot is estimated by sum_m udot_m (S - u_m)/(B(B-1)); uref*udot by uref sum_m udot_m / B;
+        // each batch is one of W/B estimates of the point's derivative.
+        double S = r.u;
+        for (int o = B >> 1; o > 0; o >>= 1) S += __shfl_xor_sync(kFull, S, o);
+        const double ur = valid ? (double)cot_or_uref[p] : 0.0;
+        wt = ((S - (double)r.u) / ((double)B * (B - 1)) - ur / B) / (double)(W / B);
+    }
+    const bool hit = valid && r.elem >= 0;
+    const float wv[3] = {1.0f - r.b1 - r.b2, r.b1, r.b2};
+#pragma unroll
+    for (int s = 0; s < DIM; ++s) {
+        const int vid = hit ? __ldg(elem + DIM * r.elem + s) : -1;
+        const double ws = hit ? wt * (double)wv[s] : 0.0;
+        double val[DIM + 1];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) val[k] = ws * (double)r.c[k];
+        val[DIM] = ws;
+        const unsigned peers = __match_any_sync(kFull, vid);
+        const bool shared = __any_sync(kFull, __popc(peers) > 1);
+        if (shared) {
+#pragma unroll
+            for (int k = 0; k <= DIM; ++k) val[k] = peer_sum(val[k], peers);
+        }
+        const bool leader = (int)(threadIdx.x & 31) == __ffs(peers) - 1;
+        if (leader && vid >= 0) {
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) atomicAdd(acc_vert + (size_t)vid * DIM + k, val[k]);
+            if (acc_g) atomicAdd(acc_g + vid, val[DIM]);
+        }
+    }
+}
+
+// grad[j] += sum over rows r (= vertex*dim + k) of J[r][j] a[r], plus sum_v dg[v][j] s[v].
+__global__ void gemv_kernel(const float* __restrict__ jac, const float* __restrict__ dg,
+                            const double* __restrict__ acc_vert, const double* __restrict__ acc_g, int n_vert,
+                            int dim, int N, double* __restrict__ grad) {
+    const int j = blockIdx.y * 32 + threadIdx.x;
+    const long long rows = (long long)n_vert * dim;
+    double s = 0.0;
+    if (j < N) {
+        for (long long r = (long long)blockIdx.x * blockDim.y + threadIdx.y; r < rows;
+             r += (long long)gridDim.x * blockDim.y) {
+            const double a = acc_vert[r];
+            if (a != 0.0) s += (double)__ldg(jac + r * N + j) * a;
+        }
+        if (dg && acc_g) {
+            for (long long v = (long long)blockIdx.x * blockDim.y + threadIdx.y; v < n_vert;
+                 v += (long long)gridDim.x * blockDim.y) {
+                const double a = acc_g[v];
+                if (a != 0.0) s += (double)__ldg(dg + v * N + j) * a;
+            }
+        }
+    }
+    __shared__ double sh[8][33];
+    sh[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && j < N) {
+        for (int y = 1; y < blockDim.y; ++y) s += sh[y][threadIdx.x];
+        atomicAdd(grad + j, s);
+    }
+}
+
+__global__ void loss_kernel(const double* mean, const float* uref, int n, double* loss) {
+    double s = 0.0;
+    for (int p = threadIdx.x; p < n; p += blockDim.x) {
+        const double e = mean[p] - (double)uref[p];
+        s += 0.5 * e * e;
+    }
+    __shared__ double sh[32];
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        s = warp_sum(s);
+        if (threadIdx.x == 0) *loss = s;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_reduce_u(const dwos_record* rec, int n_points, int W, double* mean, double* se, cudaStream_t s) {
+    if (n_points <= 0) return cudaSuccess;
+    reduce_u_kernel<<<n_points, 256, 0, s>>>(rec, W, mean, se);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_udot(const dwos_record* rec, const int* elem, const float* jac, const float* dg, int dim,
+                               int N, int n_points, int W, double* mean, double* se, cudaStream_t s) {
+    if (n_points <= 0 || N <= 0) return cudaSuccess;
+    dim3 grid(n_points, (N + 31) / 32), block(32, 8);
+    if (dim == 2) reduce_udot_kernel<2><<<grid, block, 0, s>>>(rec, elem, jac, dg, N, W, mean, se);
+    else reduce_udot_kernel<3><<<grid, block, 0, s>>>(rec, elem, jac, dg, N, W, mean, se);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int n_points, int W, int B, int mode,
+                           const float* cot_or_uref, double* acc_vert, double* acc_g, cudaStream_t s) {
+    const long long total = (long long)n_points * W;
+    if (total <= 0) return cudaSuccess;
+    const int bs = 256;
+    const long long blocks = (total + bs - 1) / bs;
+    if (dim == 2) scatter_kernel<2><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, acc_vert, acc_g);
+    else scatter_kernel<3><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, acc_vert, acc_g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemv(const float* jac, const float* dg, const double* acc_vert, const double* acc_g, int n_vert,
+                        int dim, int N, double* grad, cudaStream_t s) {
+    if (N <= 0 || n_vert <= 0) return cudaSuccess;
+    const int ny = (N + 31) / 32;
+    const long long rows = (long long)n_vert * dim;
+    long long bx = (rows + 7) / 8;
+    const long long cap = 152LL * 8 / ny + 1;
+    if (bx > cap) bx = cap;
+    gemv_kernel<<<dim3((unsigned)bx, ny), dim3(32, 8), 0, s>>>(jac, dg, acc_vert, acc_g, n_vert, dim, N, grad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loss(const double* mean, const float* uref, int n_points, double* loss, cudaStream_t s) {
+    loss_kernel<<<1, 256, 0, s>>>(mean, uref, n_points, loss);
+    return cudaGetLastError();
+}
+
+}  // namespace dwos

@@ -1,0 +1,379 @@
+// Persistent walk-on-spheres kernel (Algorithms 1 and 2 of "Differential Walk
+// on Spheres", Miller et al. 2024).
+//
+// Each lane owns one walk at a time.  Every iteration of the loop is one
+// distance query (DistanceToBoundary) for every busy lane of the warp,
+// whatever phase its walk is in: the main walk (forward Algorithm 1, or the
+// differential Algorithm 2 that also returns u from the same path), or one of
+// its K nested forward walks from the offset point xbar - h n.  A lane whose
+// walk ends writes its 32-byte record and takes the next walk from a global
+// counter; the lanes of a warp that need work claim consecutive walk indices
+// with one atomic (warp-aggregated refill), so a warp mostly works on walks
+// of the same query point.  Walk state lives in registers; the problem
+// descriptors live in shared memory.
+//
+// Randomness is Philox4x32-10 keyed by the seed, counter (walk id, step,
+// phase << 8 | block): block 0 gives the sphere direction and the roulette
+// draw, block 1 the ball sample of the source term.  Any walk can be replayed
+// from its id alone.
+#include "dwos_device.cuh"
+#include "dwos_internal.h"
+
+namespace dwos {
+
+namespace {
+
+constexpr int kMaxProblems = 64;
+constexpr unsigned kFull = 0xffffffffu;
+
+template <int DIM>
+__device__ __forceinline__ float field_value(const float* c, const float* x, float* grad) {
+    // g = c0 + c.x + x^T A x with A = [[xx, xy, xz], [xy, yy, yz], [xz, yz, zz]]
+    const float X = x[0], Y = x[1], Z = DIM == 3 ? x[2] : 0.0f;
+    const float ax = c[4] * X + c[7] * Y + c[8] * Z;
+    const float ay = c[7] * X + c[5] * Y + c[9] * Z;
+    const float az = c[8] * X + c[9] * Y + c[6] * Z;
+    grad[0] = c[1] + 2.0f * ax;
+    grad[1] = c[2] + 2.0f * ay;
+    if (DIM == 3) grad[2] = c[3] + 2.0f * az;
+    return c[0] + c[1] * X + c[2] * Y + c[3] * Z + X * ax + Y * ay + Z * az;
+}
+
+// Closest point xbar on leaf `leaf`, its vertex weights, and the leaf's
+// vertices (input order of the element).
+template <int DIM>
+__device__ __forceinline__ void leaf_geometry(const float4* __restrict__ prims, int leaf, const float* x,
+                                              float* xbar, float& w1, float& w2, float* va, float* vb,
+                                              float* vc) {
+    if (DIM == 2) {
+        const float4 s = __ldg(prims + leaf);
+        va[0] = s.x; va[1] = s.y; vb[0] = s.z; vb[1] = s.w;
+        seg_closest(x, s.x, s.y, s.z, s.w, w1);
+        w2 = 0.0f;
+        xbar[0] = fmaf(w1, s.z - s.x, s.x);
+        xbar[1] = fmaf(w1, s.w - s.y, s.y);
+    } else {
+        const float4 a = __ldg(prims + 3 * leaf), b = __ldg(prims + 3 * leaf + 1), c = __ldg(prims + 3 * leaf + 2);
+        va[0] = a.x; va[1] = a.y; va[2] = a.z;
+        vb[0] = b.x; vb[1] = b.y; vb[2] = b.z;
+        vc[0] = c.x; vc[1] = c.y; vc[2] = c.z;
+        tri_closest(x, make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z), make_float3(c.x, c.y, c.z), w1, w2);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) xbar[k] = va[k] + w1 * (vb[k] - va[k]) + w2 * (vc[k] - va[k]);
+    }
+}
+
+struct WarpStats {
+    unsigned long long steps_main = 0, steps_nested = 0, capped = 0;
+    unsigned nodes = 0, prims = 0;
+};
+
+template <int DIM>
+__global__ void __launch_bounds__(256) walk_kernel(const DevProblem* __restrict__ g_probs, int n_probs,
+                                                   unsigned long long total, DevCounters* __restrict__ ctr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    DevProblem* sp = reinterpret_cast<DevProblem*>(smem_raw);
+    {
+        const int words = (int)(sizeof(DevProblem) / sizeof(int)) * n_probs;
+        const int* src = reinterpret_cast<const int*>(g_probs);
+        int* dst = reinterpret_cast<int*>(sp);
+        for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+    }
+    __syncthreads();
+
+    const int lane = threadIdx.x & 31;
+    bool active = false, exhausted = false;
+    int error = 0;
+    WarpStats st;
+
+    // per-lane walk state
+    unsigned long long gw = 0;      // global work index of the current walk
+    int prob = 0, phase = 0, step = 0, hint = -1;
+    float x[DIM], acc = 0.0f;
+    // main-walk results kept while the nested walks run
+    float u_main = 0.0f, g_main = 0.0f, b1 = 0.0f, b2 = 0.0f, sum_nested = 0.0f;
+    int leaf_main = -1, e_main = -1;
+    uint32_t meta_main = 0;
+    float nrm[DIM], cb[DIM], xoff[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { x[k] = 0.0f; nrm[k] = 0.0f; cb[k] = 0.0f; xoff[k] = 0.0f; }
+
+    for (;;) {
+        // ---- refill idle lanes with consecutive walk indices (one atomic per warp)
+        const unsigned need = __ballot_sync(kFull, !active && !exhausted);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(&ctr->next_work, (unsigned long long)__popc(need));
+            base = __shfl_sync(kFull, base, leader);
+            if (!active && !exhausted) {
+                const unsigned long long my = base + __popc(need & ((1u << lane) - 1u));
+                if (my < total) {
+                    gw = my;
+                    while (prob + 1 < n_probs && gw >= sp[prob].work_end) ++prob;
+                    const DevProblem& P = sp[prob];
+                    const unsigned long long local = gw - P.work_begin;
+                    const int point = (int)(local / (unsigned long long)P.walks);
+                    if (P.valid && !__ldg(P.valid + point)) {
+                        // query point outside Omega: NaN record, error bit 2, next walk
+                        dwos_record r;
+                        r.u = __int_as_float(0x7fc00000); r.elem = -1; r.b1 = 0.0f; r.b2 = 0.0f;
+                        r.c[0] = 0.0f; r.c[1] = 0.0f; r.c[2] = 0.0f; r.meta = 0;
+                        P.rec[local] = r;
+                        error |= 2;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < DIM; ++k) x[k] = __ldg(P.xq + (size_t)DIM * point + k);
+                        phase = 0; step = 0; hint = -1; acc = 0.0f; sum_nested = 0.0f;
+                        active = true;
+                    }
+                } else {
+                    exhausted = true;
+                }
+            }
+        }
+        if (!__any_sync(kFull, active)) break;
+        if (!active) continue;
+
+        const DevProblem& P = sp[prob];
+        const unsigned long long local = gw - P.work_begin;
+
+        // ---- DistanceToBoundary, seeded with the previous closest element
+        BvhView bvh{P.nodes, P.prims, P.root, P.n_internal};
+        float best2 = kInf;
+        int best = -1;
+        if (hint >= 0) { best2 = prim_dist2<DIM>(P.prims, hint, x); best = hint; }
+        if (hint >= 0) ++st.prims;
+        if (!closest_leaf<DIM>(bvh, x, best2, best, st.nodes, st.prims)) error |= 1;
+        const float d = sqrtf(best2);
+        const uint32_t k_step = (uint32_t)step;
+        ++step;
+        if (phase == 0) ++st.steps_main; else ++st.steps_nested;
+
+        const bool lost = best < 0;   // only with non-finite geometry or points: end the walk
+        const bool shell = !lost && d < P.eps;
+        const bool capped = !lost && !shell && step >= P.max_steps;
+        int kind;
+        float g = 0.0f;
+        float xbar[DIM], w1 = 0.0f, w2 = 0.0f, va[DIM], vb[DIM], vc[DIM];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) { xbar[k] = 0.0f; va[k] = 0.0f; vb[k] = 0.0f; vc[k] = 0.0f; }
+        int e = -1;
+        if (lost) {
+            error |= 1;
+            kind = DWOS_KIND_ROULETTE;
+        } else if (shell || capped) {
+            kind = shell ? DWOS_KIND_SHELL : DWOS_KIND_CAPPED;
+            if (capped) ++st.capped;
+            leaf_geometry<DIM>(P.prims, best, x, xbar, w1, w2, va, vb, vc);
+            e = __ldg(P.prim_elem + best);
+            if (P.data_kind == 1) {
+                float gr[DIM];
+                g = field_value<DIM>(P.field, xbar, gr);
+            } else {
+                const int* ev = P.elem + (size_t)DIM * e;
+                const float w0 = 1.0f - w1 - w2;
+                g = w0 * __ldg(P.g_vert + ev[0]) + w1 * __ldg(P.g_vert + ev[1]);
+                if (DIM == 3) g += w2 * __ldg(P.g_vert + ev[2]);
+            }
+        } else {
+            const unsigned long long wid = P.walk_id_base + local;
+            if (P.f != 0.0f) {   // source estimate of this ball (Algorithm 1, S-hat)
+                const U4 r1 = draw_block(P.seed_lo, P.seed_hi, wid, k_step, (uint32_t)phase, 1u);
+                acc = fmaf(source_weight<DIM>(P.sqrt_sigma, d, u01(r1.z)), P.f, acc);
+            }
+            const U4 r0 = draw_block(P.seed_lo, P.seed_hi, wid, k_step, (uint32_t)phase, 0u);
+            const float alpha = recursive_weight<DIM>(P.sqrt_sigma, d);
+            if (alpha < u01(r0.z)) {
+                kind = DWOS_KIND_ROULETTE;
+            } else {   // next point on the sphere of radius d
+                if (DIM == 2) {
+                    float s, c;
+                    sincospif(2.0f * u01(r0.x), &s, &c);
+                    x[0] = fmaf(d, c, x[0]);
+                    x[1] = fmaf(d, s, x[1]);
+                } else {
+                    const float u0 = u01(r0.x);
+                    const float z = 1.0f - 2.0f * u0;
+                    const float sth = 2.0f * sqrtf(u0 * (1.0f - u0));
+                    float s, c;
+                    sincospif(2.0f * u01(r0.y), &s, &c);
+                    x[0] = fmaf(d * sth, c, x[0]);
+                    x[1] = fmaf(d * sth, s, x[1]);
+                    x[DIM - 1] = fmaf(d, z, x[DIM - 1]);
+                }
+                hint = best;
+                continue;
+            }
+        }
+
+        // ---- the current phase ended (shell, capped or roulette)
+        const int K1 = P.K + 1;
+        if (P.trace) P.trace[local * K1 + phase] = min((uint32_t)step, 0x3fffffffu) | ((uint32_t)kind << 30);
+        if (phase == 0) {
+            u_main = acc + g;
+            meta_main = min((uint32_t)step, 0xffffffu) | ((uint32_t)kind << 24);
+            if (!P.differential || kind == DWOS_KIND_ROULETTE) {
+                dwos_record r;
+                r.u = u_main;
+                r.elem = kind == DWOS_KIND_ROULETTE ? -1 : e;
+                r.b1 = w1; r.b2 = w2;
+                r.c[0] = 0.0f; r.c[1] = 0.0f; r.c[2] = 0.0f;
+                r.meta = meta_main;
+                P.rec[local] = r;
+                if (P.differential) {
+                    if (P.trace) for (int j = 1; j < K1; ++j) P.trace[local * K1 + j] = 0xffffffffu;
+                    if (P.dbg) {
+                        dwos_walk_debug z;
+                        z.dudn = 0.0f; z.u_off = 0.0f;
+                        for (int k = 0; k < 3; ++k) { z.n[k] = 0.0f; z.xbar[k] = k < DIM ? xbar[k] * (kind != DWOS_KIND_ROULETTE) : 0.0f; }
+                        P.dbg[local] = z;
+                    }
+                }
+                active = false;
+                continue;
+            }
+            // BoundaryNormal at xbar, oriented away from the walk point (Algorithm 2)
+            float side = 0.0f;
+            if (DIM == 2) {
+                const float tx = vb[0] - va[0], ty = vb[1] - va[1];
+                const float inv = rsqrtf(tx * tx + ty * ty);
+                nrm[0] = ty * inv;
+                nrm[1] = -tx * inv;
+            } else {
+                const float e1[3] = {vb[0] - va[0], vb[1] - va[1], vb[2] - va[2]};
+                const float e2[3] = {vc[0] - va[0], vc[1] - va[1], vc[2] - va[2]};
+                const float cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                                     e1[0] * e2[1] - e1[1] * e2[0]};
+                const float inv = rsqrtf(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
+                nrm[0] = cr[0] * inv; nrm[1] = cr[1] * inv; nrm[DIM - 1] = cr[2] * inv;
+            }
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) side = fmaf(nrm[k], xbar[k] - x[k], side);
+            if (side < 0.0f) {
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) nrm[k] = -nrm[k];
+            }
+            // boundary-data part of c: (dg/dn) n for field data (Eq. boundary_deriv_restricted),
+            // -grad_Gamma(g) for mapped data (Eq. boundary_deriv_mapped with dg/dn = 0)
+            if (P.data_kind == 1) {
+                float gr[DIM];
+                field_value<DIM>(P.field, xbar, gr);
+                float dgdn = 0.0f;
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) dgdn = fmaf(nrm[k], gr[k], dgdn);
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) cb[k] = dgdn * nrm[k];
+            } else {
+                const int* ev = P.elem + (size_t)DIM * e;
+                const float g0 = __ldg(P.g_vert + ev[0]);
+                if (DIM == 2) {
+                    const float tx = vb[0] - va[0], ty = vb[1] - va[1];
+                    const float s = (__ldg(P.g_vert + ev[1]) - g0) / (tx * tx + ty * ty);
+                    cb[0] = -s * tx;
+                    cb[1] = -s * ty;
+                } else {
+                    const float e1[3] = {vb[0] - va[0], vb[1] - va[1], vb[2] - va[2]};
+                    const float e2[3] = {vc[0] - va[0], vc[1] - va[1], vc[2] - va[2]};
+                    const float g11 = e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2];
+                    const float g12 = e1[0] * e2[0] + e1[1] * e2[1] + e1[2] * e2[2];
+                    const float g22 = e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2];
+                    const float r1 = __ldg(P.g_vert + ev[1]) - g0, r2 = __ldg(P.g_vert + ev[2]) - g0;
+                    const float det = g11 * g22 - g12 * g12;
+                    const float a1 = (g22 * r1 - g12 * r2) / det, a2 = (g11 * r2 - g12 * r1) / det;
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) cb[k] = -(a1 * e1[k] + a2 * e2[k]);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) xoff[k] = fmaf(-P.h, nrm[k], xbar[k]);
+            g_main = g; b1 = w1; b2 = w2; leaf_main = best; e_main = e;
+            sum_nested = 0.0f;
+        } else {
+            sum_nested += acc + g;
+            if (phase == P.K) {   // Eq. (wos_deriv), shell case, with Eq. (dudn_fd_estimate)
+                const float u_off = sum_nested / (float)P.K;
+                const float dudn = (g_main - u_off) * P.inv_h;
+                dwos_record r;
+                r.u = u_main;
+                r.elem = e_main;
+                r.b1 = b1; r.b2 = b2;
+                r.c[0] = cb[0] - dudn * nrm[0];
+                r.c[1] = cb[1] - dudn * nrm[1];
+                r.c[2] = DIM == 3 ? cb[DIM - 1] - dudn * nrm[DIM - 1] : 0.0f;
+                r.meta = meta_main;
+                P.rec[local] = r;
+                if (P.dbg) {
+                    dwos_walk_debug z;
+                    z.dudn = dudn;
+                    z.u_off = u_off;
+                    for (int k = 0; k < 3; ++k) {
+                        z.n[k] = k < DIM ? nrm[k] : 0.0f;
+                        z.xbar[k] = k < DIM ? fmaf(P.h, nrm[k], xoff[k]) : 0.0f;
+                    }
+                    P.dbg[local] = z;
+                }
+                active = false;
+                continue;
+            }
+        }
+        // start the next nested forward walk from the offset point
+        ++phase;
+        step = 0;
+        acc = 0.0f;
+        hint = leaf_main;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) x[k] = xoff[k];
+    }
+
+    // ---- statistics: one atomic per warp
+    for (int o = 16; o > 0; o >>= 1) {
+        st.steps_main += __shfl_xor_sync(kFull, st.steps_main, o);
+        st.steps_nested += __shfl_xor_sync(kFull, st.steps_nested, o);
+        st.capped += __shfl_xor_sync(kFull, st.capped, o);
+        error |= __shfl_xor_sync(kFull, error, o);
+    }
+    unsigned long long nodes = st.nodes, prims = st.prims;
+    for (int o = 16; o > 0; o >>= 1) {
+        nodes += __shfl_xor_sync(kFull, nodes, o);
+        prims += __shfl_xor_sync(kFull, prims, o);
+    }
+    if (lane == 0) {
+        atomicAdd(&ctr->steps_main, st.steps_main);
+        atomicAdd(&ctr->steps_nested, st.steps_nested);
+        atomicAdd(&ctr->nodes, nodes);
+        atomicAdd(&ctr->prims, prims);
+        if (st.capped) atomicAdd(&ctr->capped, st.capped);
+        if (error) atomicOr(&ctr->error, error);
+    }
+}
+
+}  // namespace
+
+int walk_max_blocks_per_sm(int dim, int block_size) {
+    int n = 0;
+    const size_t smem = sizeof(DevProblem);
+    if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<2>, block_size, smem);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<3>, block_size, smem);
+    return n;
+}
+
+cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_probs, unsigned long long total,
+                         DevCounters* d_counters, cudaStream_t stream, int* blocks_used) {
+    if (n_probs < 1 || n_probs > kMaxProblems) return cudaErrorInvalidValue;
+    if (total == 0) { if (blocks_used) *blocks_used = 0; return cudaSuccess; }
+    const int bs = L.block_size;
+    int per_sm = L.blocks_per_sm > 0 ? L.blocks_per_sm : walk_max_blocks_per_sm(L.dim, bs);
+    if (per_sm < 1) per_sm = 1;
+    long long blocks = (long long)per_sm * L.n_sm;
+    const long long need = (long long)((total + bs - 1) / bs);
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    if (blocks_used) *blocks_used = (int)blocks;
+    const size_t smem = sizeof(DevProblem) * (size_t)n_probs;
+    if (L.dim == 2) walk_kernel<2><<<(int)blocks, bs, smem, stream>>>(d_probs, n_probs, total, d_counters);
+    else walk_kernel<3><<<(int)blocks, bs, smem, stream>>>(d_probs, n_probs, total, d_counters);
+    return cudaGetLastError();
+}
+
+}  // namespace dwos

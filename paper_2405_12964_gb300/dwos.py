@@ -1,0 +1,322 @@
+"""Python binding of libdwos (ctypes).  Argument marshalling only: every step of
+walk on spheres, differential walk on spheres and the estimator reductions runs
+in the library's CUDA kernels.  PyTorch provides device memory and the stream.
+
+The library must have been built (``paper_2405_12964_gb300.build.build()``);
+there is no fallback: loading fails loudly when ``libdwos.so`` is missing or
+no CUDA device is visible.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdwos.so")
+
+MEM_HOST, MEM_DEVICE = 0, 1
+KIND_SHELL, KIND_ROULETTE, KIND_CAPPED = 0, 1, 2
+
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "STEP_LIMIT", 5: "TIMEOUT",
+          6: "NOT_IMPLEMENTED", 7: "STATE", 8: "OUTSIDE"}
+
+RECORD_DTYPE = np.dtype([("u", "<f4"), ("elem", "<i4"), ("b1", "<f4"), ("b2", "<f4"),
+                         ("c", "<f4", (3,)), ("meta", "<u4")])
+DEBUG_DTYPE = np.dtype([("dudn", "<f4"), ("n", "<f4", (3,)), ("u_off", "<f4"), ("xbar", "<f4", (3,))])
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_float), ("h", ctypes.c_float), ("K", ctypes.c_int), ("B", ctypes.c_int),
+                ("max_steps", ctypes.c_int), ("seed", ctypes.c_uint64), ("check_inside", ctypes.c_int),
+                ("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("smem_nodes", ctypes.c_int)]
+
+
+class RunStats(ctypes.Structure):
+    _fields_ = [("steps_main", ctypes.c_uint64), ("steps_nested", ctypes.c_uint64), ("walks", ctypes.c_uint64),
+                ("capped", ctypes.c_uint64), ("nodes_visited", ctypes.c_uint64), ("prims_tested", ctypes.c_uint64),
+                ("launches", ctypes.c_uint64), ("kernel_ms", ctypes.c_float), ("blocks", ctypes.c_int)]
+
+
+class DwosError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"dwos {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_u64 = ctypes.c_uint64
+
+# name -> argtypes (all entry points return int status unless noted)
+_SIGS = {
+    "dwos_create": [ctypes.POINTER(_vp), _i],
+    "dwos_set_stream": [_vp, _vp],
+    "dwos_sync": [_vp],
+    "dwos_set_options": [_vp, ctypes.POINTER(Options)],
+    "dwos_set_boundary": [_vp, _i, _i, _vp, _i, _vp, _i, _vp, _i],
+    "dwos_set_params": [_vp, _vp, _i],
+    "dwos_set_dirichlet_mapped": [_vp, _vp, _vp, _i],
+    "dwos_set_dirichlet_field": [_vp, ctypes.POINTER(ctypes.c_double)],
+    "dwos_set_pde": [_vp, ctypes.c_float, ctypes.c_float],
+    "dwos_eval": [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _i],
+    "dwos_vjp": [_vp, _i, _vp, _vp, _i, _u64, _vp, _vp, _i],
+    "dwos_grad_l2": [_vp, _i, _vp, _vp, _i, _u64, _vp, _vp, _vp, _i],
+    "dwos_walk_records": [_vp, _i, _vp, _i, _u64, _i, _vp, _vp, _vp, _i],
+    "dwos_last_stats": [_vp, ctypes.POINTER(RunStats)],
+    "dwos_closest_point": [_vp, _i, _vp, _vp, _vp, _vp, _i],
+    "dwos_inside": [_vp, _i, _vp, _vp, _i],
+    "dwos_philox4x32_10": [_vp, _i, _vp, _vp, _vp, _i],
+}
+
+
+def lib():
+    """Load libdwos.so (raises if it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2405_12964_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.dwos_destroy.argtypes = [_vp]
+        L.dwos_destroy.restype = None
+        L.dwos_last_error.argtypes = [_vp]
+        L.dwos_last_error.restype = ctypes.c_char_p
+        L.dwos_default_options.argtypes = [ctypes.POINTER(Options)]
+        L.dwos_default_options.restype = None
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(list(_SIGS) + ["dwos_destroy", "dwos_last_error", "dwos_default_options"])
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One library context on one CUDA device; all work on torch's current stream."""
+
+    def __init__(self, device: int = 0):
+        if not torch.cuda.is_available():
+            raise RuntimeError("dwos needs a CUDA device")
+        self.device = torch.device("cuda", device)
+        self._h = ctypes.c_void_p()
+        L = lib()
+        st = L.dwos_create(ctypes.byref(self._h), device)
+        if st:
+            raise DwosError(st, L.dwos_last_error(None).decode())
+        self.dim = 0
+        self.n_vert = 0
+        self.n_param = 0
+        self.opt = Options()
+        L.dwos_default_options(ctypes.byref(self.opt))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and h.value and _lib is not None:
+            _lib.dwos_destroy(h)
+            self._h = ctypes.c_void_p()
+
+    # ---------------------------------------------------------------- plumbing
+    def _check(self, st: int):
+        if st:
+            raise DwosError(st, lib().dwos_last_error(self._h).decode())
+
+    def _stream(self):
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        self._check(lib().dwos_set_stream(self._h, ctypes.c_void_p(s)))
+
+    def _dev(self, a, dtype) -> torch.Tensor:
+        return torch.as_tensor(np.asarray(a) if not torch.is_tensor(a) else a).to(
+            device=self.device, dtype=dtype).contiguous()
+
+    # ---------------------------------------------------------------- problem
+    def set_options(self, **kw):
+        for k, v in kw.items():
+            if not hasattr(self.opt, k):
+                raise KeyError(k)
+            setattr(self.opt, k, v)
+        self._check(lib().dwos_set_options(self._h, ctypes.byref(self.opt)))
+
+    def set_boundary(self, vert, elem, jac=None):
+        self._stream()
+        v = self._dev(vert, torch.float32)
+        e = self._dev(elem, torch.int32)
+        j = None if jac is None else self._dev(jac, torch.float32)
+        dim = v.shape[1]
+        P = 0 if j is None else j.shape[2]
+        self._check(lib().dwos_set_boundary(self._h, dim, v.shape[0], _ptr(v), e.shape[0], _ptr(e), P, _ptr(j),
+                                            MEM_DEVICE))
+        self.dim, self.n_vert, self.n_param = dim, v.shape[0], P
+
+    def set_params(self, theta):
+        self._stream()
+        t = self._dev(theta, torch.float32)
+        self._check(lib().dwos_set_params(self._h, _ptr(t), MEM_DEVICE))
+
+    def set_dirichlet_mapped(self, g, dg=None):
+        self._stream()
+        gt = self._dev(g, torch.float32)
+        dgt = None if dg is None else self._dev(dg, torch.float32)
+        self._check(lib().dwos_set_dirichlet_mapped(self._h, _ptr(gt), _ptr(dgt), MEM_DEVICE))
+
+    def set_dirichlet_field(self, coeffs):
+        c = (ctypes.c_double * 10)(*[float(x) for x in np.asarray(coeffs, dtype=np.float64).reshape(-1)[:10]])
+        self._check(lib().dwos_set_dirichlet_field(self._h, c))
+
+    def set_pde(self, sigma: float, f: float = 0.0):
+        self._check(lib().dwos_set_pde(self._h, float(sigma), float(f)))
+
+    def load_scene(self, sc, **opt):
+        """Set boundary, data, PDE and the scene's eps / h / K / B / seed."""
+        self.set_boundary(sc.vert, sc.elem, sc.jac)
+        if sc.data == "field":
+            self.set_dirichlet_field(sc.field)
+        else:
+            self.set_dirichlet_mapped(sc.g_vert, sc.dg_vert)
+        self.set_pde(sc.sigma, sc.f)
+        kw = dict(eps=sc.eps, h=sc.h, K=sc.K, B=sc.B, seed=sc.seed)
+        kw.update(opt)
+        self.set_options(**kw)
+
+    # ---------------------------------------------------------------- estimators
+    def eval(self, xq, walks: int, grad: bool = False):
+        """u (and du/dtheta) at the query points: dict of FP64 device tensors."""
+        self._stream()
+        x = self._dev(xq, torch.float32)
+        n = x.shape[0]
+        dd = dict(device=self.device, dtype=torch.float64)
+        u, se = torch.empty(n, **dd), torch.empty(n, **dd)
+        du = dse = None
+        if grad:
+            du, dse = torch.empty(n, self.n_param, **dd), torch.empty(n, self.n_param, **dd)
+        self._check(lib().dwos_eval(self._h, n, _ptr(x), int(walks), _ptr(u), _ptr(se), _ptr(du), _ptr(dse),
+                                    MEM_DEVICE))
+        out = {"u": u, "u_se": se}
+        if grad:
+            out.update(du=du, du_se=dse)
+        return out
+
+    def vjp(self, xq, w, walks: int, walk_id_base: int = 1 << 40, vertex_grad: bool = False):
+        self._stream()
+        x = self._dev(xq, torch.float32)
+        wt = self._dev(w, torch.float32)
+        dd = dict(device=self.device, dtype=torch.float64)
+        g = torch.empty(max(self.n_param, 1), **dd)
+        gv = torch.empty(self.n_vert, self.dim, **dd) if vertex_grad else None
+        self._check(lib().dwos_vjp(self._h, x.shape[0], _ptr(x), _ptr(wt), int(walks), int(walk_id_base), _ptr(g),
+                                   _ptr(gv), MEM_DEVICE))
+        return (g[:self.n_param], gv) if vertex_grad else g[:self.n_param]
+
+    def grad_l2(self, xq, uref, walks: int, walk_id_base: int = 0, vertex_grad: bool = False):
+        self._stream()
+        x = self._dev(xq, torch.float32)
+        ur = self._dev(uref, torch.float32)
+        dd = dict(device=self.device, dtype=torch.float64)
+        loss = torch.empty(1, **dd)
+        g = torch.empty(max(self.n_param, 1), **dd)
+        gv = torch.empty(self.n_vert, self.dim, **dd) if vertex_grad else None
+        self._check(lib().dwos_grad_l2(self._h, x.shape[0], _ptr(x), _ptr(ur), int(walks), int(walk_id_base),
+                                       _ptr(loss), _ptr(g), _ptr(gv), MEM_DEVICE))
+        return (loss, g[:self.n_param], gv) if vertex_grad else (loss, g[:self.n_param])
+
+    def walk_records(self, xq, walks: int, walk_id_base: int = 0, differential: bool = True,
+                     trace: bool = False, debug: bool = False):
+        """Per-walk records as numpy structured arrays (row p * walks + w)."""
+        self._stream()
+        x = self._dev(xq, torch.float32)
+        n = x.shape[0] * int(walks)
+        rec = torch.empty(n * 32, device=self.device, dtype=torch.uint8)
+        K1 = self.opt.K + 1
+        tr = torch.empty(n * K1, device=self.device, dtype=torch.int32) if trace else None
+        db = torch.empty(n * 32, device=self.device, dtype=torch.uint8) if debug else None
+        self._check(lib().dwos_walk_records(self._h, x.shape[0], _ptr(x), int(walks), int(walk_id_base),
+                                            1 if differential else 0, _ptr(rec), _ptr(tr), _ptr(db), MEM_DEVICE))
+        self.sync()
+        out = {"rec": rec.cpu().numpy().view(RECORD_DTYPE)}
+        if trace:
+            out["trace"] = tr.cpu().numpy().view(np.uint32).reshape(n, K1)
+        if debug:
+            out["debug"] = db.cpu().numpy().view(DEBUG_DTYPE)
+        return out
+
+    def sync(self):
+        self._check(lib().dwos_sync(self._h))
+
+    def stats(self) -> dict:
+        s = RunStats()
+        self._check(lib().dwos_last_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in RunStats._fields_}
+
+    # ---------------------------------------------------------------- queries
+    def closest_point(self, p):
+        self._stream()
+        x = self._dev(p, torch.float32)
+        n = x.shape[0]
+        d = torch.empty(n, device=self.device, dtype=torch.float32)
+        e = torch.empty(n, device=self.device, dtype=torch.int32)
+        b = torch.empty(n, 2, device=self.device, dtype=torch.float32)
+        self._check(lib().dwos_closest_point(self._h, n, _ptr(x), _ptr(d), _ptr(e), _ptr(b), MEM_DEVICE))
+        return d, e, b
+
+    def inside(self, p):
+        self._stream()
+        x = self._dev(p, torch.float32)
+        out = torch.empty(x.shape[0], device=self.device, dtype=torch.int32)
+        self._check(lib().dwos_inside(self._h, x.shape[0], _ptr(x), _ptr(out), MEM_DEVICE))
+        return out
+
+    def philox(self, ctr, key):
+        self._stream()
+        c = torch.as_tensor(np.asarray(ctr, dtype=np.uint32).view(np.int32)).to(self.device).contiguous()
+        k = torch.as_tensor(np.asarray(key, dtype=np.uint32).view(np.int32)).to(self.device).contiguous()
+        n = c.numel() // 4
+        out = torch.empty(n * 4, device=self.device, dtype=torch.int32)
+        self._check(lib().dwos_philox4x32_10(self._h, n, _ptr(c), _ptr(k), _ptr(out), MEM_DEVICE))
+        return out.cpu().numpy().view(np.uint32).reshape(n, 4)
+
+
+class DWoSFunction(torch.autograd.Function):
+    """u(theta) at fixed query points, with the adjoint through differential walks.
+
+    forward(theta): v = v_ref + J theta, BVH rebuild, walk on spheres (Algorithm 1)
+    backward(grad_u): grad_theta = sum_p grad_u[p] E[udot_p] from differential
+    walks (Algorithm 2) drawn with walk ids disjoint from the forward's, so the
+    product with a cotangent built from the forward output stays uncorrelated
+    (Sec. 4.3, Eq. uncorrelated_product); scatter + adjoint GEMV in the library.
+    """
+
+    @staticmethod
+    def forward(ctx, theta, solver: Solver, xq, walks: int, backward_walks: int, backward_base: int):
+        solver.set_params(theta.detach())
+        out = solver.eval(xq, walks)
+        ctx.solver = solver
+        ctx.xq = xq
+        ctx.bw = backward_walks
+        ctx.base = backward_base
+        ctx.save_for_backward(theta.detach().clone())
+        return out["u"].to(theta.dtype) if theta.dtype == torch.float64 else out["u"]
+
+    @staticmethod
+    def backward(ctx, grad_u):
+        (theta,) = ctx.saved_tensors
+        s = ctx.solver
+        s.set_params(theta)
+        g = s.vjp(ctx.xq, grad_u.detach().to(torch.float32), ctx.bw, walk_id_base=ctx.base)
+        return g.to(theta.dtype), None, None, None, None, None
+
+
+def solve(theta, solver: Solver, xq, walks: int, backward_walks: Optional[int] = None,
+          backward_base: int = 1 << 40):
+    """Differentiable u(theta) at xq (see DWoSFunction)."""
+    return DWoSFunction.apply(theta, solver, xq, walks, backward_walks or walks, backward_base)

@@ -1,0 +1,310 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Per-walk replay: both sides run the same Philox walk ids.  A walk's branch is
+(distance queries and termination kind per phase, terminal element).  On
+walks whose branch matches, u and the forward-mode derivative agree to 1e-4
+relative (absolute floor 1e-5 on u, 1e-3 x (1 + |udot|) on udot, whose
+du/dn = (g - u_off)/h carries FP32 rounding of u_off amplified by 1/h); walks
+whose branch changed are counted and must be rare.  Means agree within 3.5
+combined standard errors.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closed_forms as cf
+from oracle import estimators as est
+from paper_2405_12964_gb300 import scenes
+from tests.golden import philox_kat
+from tests.helpers import to_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def Solver():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_12964_gb300 import build
+    build.build()
+    from paper_2405_12964_gb300.dwos import Solver as S
+    return S
+
+
+def gpu_udot(sc, rec):
+    """Forward-mode udot of each walk rebuilt from its record (see dwos_record)."""
+    n = rec.shape[0]
+    P = sc.n_param
+    out = np.zeros((n, P))
+    hit = rec["elem"] >= 0
+    e = rec["elem"][hit]
+    w = np.stack([1 - rec["b1"][hit] - rec["b2"][hit], rec["b1"][hit], rec["b2"][hit]], 1)
+    c = rec["c"][hit].astype(np.float64)[:, :sc.dim]
+    acc = np.zeros((hit.sum(), P))
+    for i in range(sc.dim):
+        v = sc.elem[e, i]
+        J = sc.jac[v]                      # (m, dim, P)
+        acc += w[:, i:i + 1] * np.einsum("mk,mkp->mp", c, J)
+        if sc.dg_vert is not None:
+            acc += w[:, i:i + 1] * sc.dg_vert[v]
+    out[hit] = acc
+    return out
+
+
+def branch_match(sc, g, o):
+    K1 = sc.K + 1
+    tr = g["trace"]
+    steps_g = (tr & 0x3FFFFFFF).astype(np.int64)
+    kind_g = (tr >> 30).astype(np.int64)
+    unused = tr == 0xFFFFFFFF
+    steps_o = o["steps"][:, :K1].astype(np.int64)
+    kind_o = o["kind"][:, :K1].astype(np.int64)
+    same = np.ones(tr.shape[0], bool)
+    for j in range(K1):
+        used_o = kind_o[:, j] >= 0
+        same &= (used_o == ~unused[:, j])
+        same &= np.where(used_o, (steps_g[:, j] == steps_o[:, j]) & (kind_g[:, j] == kind_o[:, j]), True)
+    same &= g["rec"]["elem"] == o["elem"]
+    return same
+
+
+def run_pair(Solver, sc, W, differential=True, base=0, **opt):
+    s = Solver(0)
+    s.load_scene(sc, **opt)
+    g = s.walk_records(sc.query, W, walk_id_base=base, differential=differential, trace=True, debug=True)
+    over = {k: v for k, v in opt.items() if k in ("eps", "h", "K", "max_steps", "seed")}
+    o = oracle.run_walks(to_oracle(sc, **over), sc.query, W, differential=differential, walk_id_base=base)
+    return s, g, o
+
+
+def check_walks(sc, g, o, differential=True, max_flip=0.01):
+    same = branch_match(sc, g, o)
+    frac_flip = 1 - same.mean()
+    assert frac_flip <= max_flip, f"{frac_flip:.4f} of walks changed branch"
+    ug = g["rec"]["u"].astype(np.float64)
+    uo = o["u_hat"]
+    err = np.abs(ug - uo)[same]
+    assert np.all(err <= 1e-4 * np.abs(uo[same]) + 1e-5), err.max()
+    if differential and sc.n_param:
+        dg = gpu_udot(sc, g["rec"])
+        do = o["udot"]
+        e2 = np.abs(dg - do)[same]
+        tol = 1e-3 * (1 + np.abs(do[same]))
+        assert np.all(e2 <= tol), (e2 / tol).max()
+    return same
+
+
+def test_philox_bit_exact(Solver):
+    s = Solver(0)
+    for ctr, key, want in philox_kat():
+        got = s.philox(np.array([ctr], dtype=np.uint32), np.array(key, dtype=np.uint32))
+        assert [int(x) for x in got[0]] == want
+    rng = np.random.default_rng(0)
+    ctrs = rng.integers(0, 2 ** 32, size=(4096, 4), dtype=np.uint64).astype(np.uint32)
+    key = np.array([0x12964, 7], dtype=np.uint32)
+    got = s.philox(ctrs, key)
+    for i in range(0, 4096, 97):
+        assert np.array_equal(got[i], oracle.philox4x32_10(ctrs[i], key))
+
+
+@pytest.mark.parametrize("which", ["disk", "star", "sphere", "ball_small"])
+def test_closest_point_matches_brute_force(Solver, which):
+    rng = np.random.default_rng(1)
+    if which == "disk":
+        sc = scenes.disk_scene("screened_1")
+        p = rng.uniform(-0.95, 0.95, size=(3000, 2))
+    elif which == "star":
+        sc = scenes.star_box_scene()
+        p = rng.uniform(-0.99, 0.99, size=(3000, 2))
+    elif which == "sphere":
+        sc = scenes.sh_sphere_scene(freq=20, n_query=8)
+        p = rng.uniform(-1.9, 1.9, size=(2000, 3))
+    else:
+        sc = scenes.ball_scene(freq=3)
+        p = rng.uniform(-1.2, 1.2, size=(2000, 3))
+    s = Solver(0)
+    s.load_scene(sc)
+    d, e, b = (t.cpu().numpy() for t in s.closest_point(p))
+    do, xo, eo, bo = oracle.closest_point(to_oracle(sc), p)
+    assert np.allclose(d, do, rtol=2e-5, atol=2e-6)
+    agree = e == eo
+    # disagreements only where two elements are equally close (shared vertices/edges)
+    if not agree.all():
+        pe = p[~agree]
+        sub = to_oracle(sc)
+        for i, q in zip(np.nonzero(~agree)[0], pe):
+            dg = oracle.closest_point(oracle.Problem(vert=sc.vert, elem=sc.elem[e[i]:e[i] + 1],
+                                                     data_kind="mapped", g_vert=np.zeros(len(sc.vert))),
+                                      q[None])[0][0]
+            assert abs(dg - do[i]) <= 1e-5 * max(1.0, do[i])
+    assert agree.mean() > 0.98
+
+
+def test_inside_test_matches_oracle(Solver):
+    rng = np.random.default_rng(2)
+    sc = scenes.star_box_scene(n_seg=1024)
+    p = rng.uniform(-1.2, 1.2, size=(4000, 2))
+    s = Solver(0)
+    s.load_scene(sc)
+    gi = s.inside(p).cpu().numpy().astype(bool)
+    oi = oracle.inside(to_oracle(sc), p)
+    dist = oracle.closest_point(to_oracle(sc), p)[0]
+    far = dist > 1e-4
+    assert np.array_equal(gi[far], oi[far])
+    sc3 = scenes.sh_sphere_scene(freq=12, n_query=8)
+    p3 = rng.uniform(-2.2, 2.2, size=(1500, 3))
+    s.load_scene(sc3)
+    gi = s.inside(p3).cpu().numpy().astype(bool)
+    oi = oracle.inside(to_oracle(sc3), p3)
+    far = oracle.closest_point(to_oracle(sc3), p3)[0] > 1e-4
+    assert np.array_equal(gi[far], oi[far])
+
+
+@pytest.mark.parametrize("variant", ["screened_1", "laplace_x", "mapped_cos"])
+def test_disk_per_walk_replay(Solver, variant):
+    sc = scenes.disk_scene(variant, n_query=16)
+    s, g, o = run_pair(Solver, sc, 96)
+    check_walks(sc, g, o)
+
+
+def test_star_box_per_walk_replay_with_nested_walks(Solver):
+    sc = scenes.star_box_scene(n_seg=4096, n_query=24)
+    s, g, o = run_pair(Solver, sc, 32, K=2)
+    same = check_walks(sc, g, o)
+    # debug outputs: du/dn and the oracle's agree on matching walks
+    dd = g["debug"]["dudn"].astype(np.float64)
+    assert np.all(np.abs(dd - o["dudn"])[same] <= 1e-3 * (1 + np.abs(o["dudn"][same])))
+
+
+def test_sphere_3d_per_walk_replay_with_source(Solver):
+    sc = scenes.sh_sphere_scene(freq=16, n_query=12, K=2)
+    s, g, o = run_pair(Solver, sc, 24)
+    check_walks(sc, g, o, max_flip=0.02)
+
+
+def test_forward_only_walks_match(Solver):
+    sc = scenes.ball_scene(freq=8, n_query=10, sigma=2.0, f=0.7)
+    s, g, o = run_pair(Solver, sc, 64, differential=False)
+    check_walks(sc, g, o, differential=False)
+
+
+def test_walk_id_base_replays_subsets(Solver):
+    sc = scenes.disk_scene("screened_1", n_query=6)
+    s = Solver(0)
+    s.load_scene(sc)
+    a = s.walk_records(sc.query, 64)["rec"]
+    b = s.walk_records(sc.query[3:4], 64, walk_id_base=3 * 64)["rec"]
+    assert np.array_equal(a[192:256].view(np.uint8), b.view(np.uint8))
+
+
+def test_eval_means_match_oracle_and_closed_form(Solver):
+    sc = scenes.disk_scene("screened_1", n_query=64, walks=1024)
+    s = Solver(0)
+    s.load_scene(sc)
+    out = s.eval(sc.query, sc.walks, grad=True)
+    u, use = out["u"].cpu().numpy(), out["u_se"].cpu().numpy()
+    du, dse = out["du"].cpu().numpy(), out["du_se"].cpu().numpy()
+    o = oracle.run_walks(to_oracle(sc), sc.query, sc.walks, differential=True)
+    uo, uose = est.point_mean_se(o["u_hat"], 64, sc.walks)
+    duo, duose = est.point_mean_se(o["udot"], 64, sc.walks)
+    # same walks: the per-point means are nearly identical, far inside 3.5 SE
+    assert np.all(np.abs(u - uo) <= 3.5 * np.sqrt(use ** 2 + uose ** 2) / 4 + 1e-6)
+    assert np.all(np.abs(du - duo) <= 3.5 * np.sqrt(dse ** 2 + duose ** 2) / 4 + 1e-6)
+    assert np.allclose(use, uose, rtol=0.05, atol=1e-6)
+    ue, due = cf.disk_screened_const(sc.query, 1.0, 4.0)
+    assert np.all(np.abs(u - ue) <= 3.5 * use + 2e-3)
+    assert np.all(np.abs(du - due) <= 3.5 * dse + 0.08 * np.abs(due) + 0.01)
+
+
+def test_grad_l2_and_vjp_match_oracle_estimators(Solver):
+    sc = scenes.star_box_scene(n_seg=1024, n_query=16, walks=64)
+    s = Solver(0)
+    s.load_scene(sc, K=2)
+    uref = sc.u_ref
+    loss, g = (t.cpu().numpy() for t in s.grad_l2(sc.query, uref, sc.walks))
+    o = oracle.run_walks(to_oracle(sc, K=2), sc.query, sc.walks, differential=True)
+    go = est.grad_l2_ustat(o["u_hat"], o["udot"], uref, 16, sc.walks, 8)
+    lo = est.loss_l2(o["u_hat"], uref, 16, sc.walks)
+    scale = np.abs(go).max()
+    assert np.allclose(g, go, rtol=2e-3, atol=2e-3 * scale), np.abs(g - go).max() / scale
+    assert abs(loss[0] - lo) <= 1e-4 * abs(lo) + 1e-7
+    w = np.linspace(-1, 1, 16)
+    gv = s.vjp(sc.query, w, sc.walks, walk_id_base=0).cpu().numpy()
+    vo = est.vjp(o["udot"], w, 16, sc.walks)
+    assert np.allclose(gv, vo, rtol=2e-3, atol=2e-3 * np.abs(vo).max())
+
+
+def test_vertex_gradient_chains_to_parameters(Solver):
+    sc = scenes.star_box_scene(n_seg=512, n_query=8, walks=64)
+    s = Solver(0)
+    s.load_scene(sc)
+    loss, g, gv = s.grad_l2(sc.query, sc.u_ref, sc.walks, vertex_grad=True)
+    g, gv = g.cpu().numpy(), gv.cpu().numpy()
+    chained = np.einsum("vk,vkp->p", gv, sc.jac)
+    assert np.allclose(g, chained, rtol=1e-6, atol=1e-9 * np.abs(g).max())
+
+
+# ---------------------------------------------------------------- edge cases
+def test_edge_cases(Solver):
+    import torch
+    from paper_2405_12964_gb300.dwos import DwosError
+    sc = scenes.disk_scene("screened_1", n_query=4)
+    s = Solver(0)
+    s.load_scene(sc)
+    out = s.eval(np.zeros((0, 2)), 16)
+    assert out["u"].numel() == 0
+    out = s.eval(sc.query, 1)
+    assert np.all(out["u_se"].cpu().numpy() == 0)
+    # a point inside the shell stops at once: u = g(xbar) exactly
+    r = s.walk_records(np.array([[0.9995, 0.0]]), 4, trace=True)
+    assert np.all(r["rec"]["u"] == 1.0) and np.all((r["trace"][:, 0] & 0x3FFFFFFF) == 1)
+    # outside the domain: loud error
+    with pytest.raises(DwosError) as ei:
+        s.eval(np.array([[1.5, 0.0]]), 8)
+        torch.cuda.synchronize()
+        s.sync()
+    assert ei.value.status == 8
+    # invalid options
+    with pytest.raises(DwosError):
+        s.set_options(B=3)
+    with pytest.raises(DwosError):
+        s.set_options(eps=0.0)
+    s.set_options(eps=1e-3, B=8)
+    # grad_l2 needs W % B == 0
+    with pytest.raises(DwosError):
+        s.grad_l2(sc.query, np.zeros(4), 12)
+
+
+def test_offset_inside_shell_gives_zero_derivative_on_gpu(Solver):
+    sc = scenes.disk_scene("screened_1", n_query=6)
+    s = Solver(0)
+    s.load_scene(sc, h=5e-4)
+    out = s.eval(sc.query, 256, grad=True)
+    assert np.all(out["du"].cpu().numpy() == 0.0)
+
+
+def test_single_element_and_tiny_meshes(Solver):
+    # one triangle far away plus checks of the single-leaf BVH
+    vert = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    s = Solver(0)
+    s.set_boundary(vert, np.array([[0, 1, 2]], dtype=np.int32))
+    p = np.array([[0.2, 0.2, 0.5], [2.0, 2.0, 2.0], [-1.0, 0.3, 0.0]])
+    d, e, b = (t.cpu().numpy() for t in s.closest_point(p))
+    pr = oracle.Problem(vert=vert, elem=np.array([[0, 1, 2]], np.int32), data_kind="mapped", g_vert=np.zeros(3))
+    do = oracle.closest_point(pr, p)[0]
+    assert np.allclose(d, do, rtol=1e-6) and np.all(e == 0)
+
+
+def test_capped_walks_are_counted(Solver):
+    sc = scenes.disk_scene("screened_1", n_query=4)
+    s = Solver(0)
+    s.load_scene(sc, max_steps=3)
+    s.set_pde(0.0, 0.0)
+    g = s.walk_records(sc.query, 64, trace=True)
+    st = s.stats()
+    assert st["capped"] > 0
+    o = oracle.run_walks(to_oracle(sc, max_steps=3, sigma=0.0), sc.query, 64, differential=True)
+    capped_o = (o["kind"] == oracle.KIND_CAPPED).sum()
+    assert abs(int(st["capped"]) - int(capped_o)) <= 2
+    assert ((g["trace"][:, 0] & 0x3FFFFFFF) <= 3).all()
