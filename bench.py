@@ -105,7 +105,7 @@ def cpu_baseline(sc, budget_s: float = 15.0):
     t0 = time.perf_counter()
     o = oracle.run_walks(pr, sc.query, 1, differential=True)
     t1 = time.perf_counter() - t0
-    W = max(1, min(64, int(budget_s / max(t1, 1e-3))))
+    W = max(1, min(4096, int(budget_s / max(t1, 1e-3))))
     t0 = time.perf_counter()
     o = oracle.run_walks(pr, sc.query, W, differential=True, walk_id_base=1 << 41)
     dt = time.perf_counter() - t0

@@ -411,12 +411,13 @@ dwos_status dwos_eval(dwos_ctx* ctx, int n_query, const float* xq, int W, double
                       double* du_mean, double* du_se, int mem) {
     if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
     if (dwos_status s = check_mem(ctx, mem)) return s;
-    if (!u_mean) return fail(ctx, DWOS_ERR_INVALID_ARG, "u_mean is NULL");
+    if (!u_mean && n_query > 0) return fail(ctx, DWOS_ERR_INVALID_ARG, "u_mean is NULL");
     if (du_mean && ctx->n_param == 0) return fail(ctx, DWOS_ERR_INVALID_ARG, "derivatives requested but n_param = 0");
     if (mem == DWOS_MEM_DEVICE)
         for (const void* p : {(const void*)u_mean, (const void*)u_se, (const void*)du_mean, (const void*)du_se})
             if (dwos_status s = check_device_ptr(ctx, p, "output")) return s;
     if (dwos_status s = set_device(ctx)) return s;
+    if (n_query == 0) return DWOS_OK;   // nothing to estimate
     const int diff = du_mean ? 1 : 0;
     if (dwos_status s = run_walks(ctx, n_query, xq, W, 0, diff, mem, nullptr, nullptr)) return s;
     const int N = ctx->n_param;

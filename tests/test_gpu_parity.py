@@ -52,9 +52,9 @@ def gpu_udot(sc, rec):
     return out
 
 
-def branch_match(sc, g, o):
-    K1 = sc.K + 1
-    tr = g["trace"]
+def branch_match(sc, g, o, differential=True):
+    K1 = sc.K + 1 if differential else 1
+    tr = g["trace"][:, :K1]
     steps_g = (tr & 0x3FFFFFFF).astype(np.int64)
     kind_g = (tr >> 30).astype(np.int64)
     unused = tr == 0xFFFFFFFF
@@ -65,7 +65,7 @@ def branch_match(sc, g, o):
         used_o = kind_o[:, j] >= 0
         same &= (used_o == ~unused[:, j])
         same &= np.where(used_o, (steps_g[:, j] == steps_o[:, j]) & (kind_g[:, j] == kind_o[:, j]), True)
-    same &= g["rec"]["elem"] == o["elem"]
+    same &= np.where(kind_o[:, 0] == oracle.KIND_ROULETTE, g["rec"]["elem"] == -1, g["rec"]["elem"] == o["elem"])
     return same
 
 
@@ -79,7 +79,7 @@ def run_pair(Solver, sc, W, differential=True, base=0, **opt):
 
 
 def check_walks(sc, g, o, differential=True, max_flip=0.01):
-    same = branch_match(sc, g, o)
+    same = branch_match(sc, g, o, differential)
     frac_flip = 1 - same.mean()
     assert frac_flip <= max_flip, f"{frac_flip:.4f} of walks changed branch"
     ug = g["rec"]["u"].astype(np.float64)
@@ -128,17 +128,23 @@ def test_closest_point_matches_brute_force(Solver, which):
     d, e, b = (t.cpu().numpy() for t in s.closest_point(p))
     do, xo, eo, bo = oracle.closest_point(to_oracle(sc), p)
     assert np.allclose(d, do, rtol=2e-5, atol=2e-6)
-    agree = e == eo
-    # disagreements only where two elements are equally close (shared vertices/edges)
-    if not agree.all():
-        pe = p[~agree]
-        sub = to_oracle(sc)
-        for i, q in zip(np.nonzero(~agree)[0], pe):
-            dg = oracle.closest_point(oracle.Problem(vert=sc.vert, elem=sc.elem[e[i]:e[i] + 1],
-                                                     data_kind="mapped", g_vert=np.zeros(len(sc.vert))),
-                                      q[None])[0][0]
-            assert abs(dg - do[i]) <= 1e-5 * max(1.0, do[i])
-    assert agree.mean() > 0.98
+    # The distance is unique; the element is not where two elements are equally
+    # close (the closest point is a shared vertex or edge, common outside a finely
+    # tessellated convex boundary).  Where the ids differ, the GPU's element must be
+    # exactly as close and the oracle's closest point must lie on its element's border.
+    dis = np.nonzero(e != eo)[0]
+    pr = to_oracle(sc)
+    for i in dis:
+        one = oracle.Problem(vert=sc.vert, elem=sc.elem[e[i]:e[i] + 1], data_kind="mapped",
+                             g_vert=np.zeros(len(sc.vert)))
+        dg = oracle.closest_point(one, p[i:i + 1])[0][0]
+        assert abs(dg - do[i]) <= 2e-5 * max(1.0, do[i]) + 2e-6
+        b1, b2 = bo[i]
+        if sc.dim == 2:
+            on_border = min(b1, 1 - b1) < 1e-6
+        else:
+            on_border = min(b1, b2, 1 - b1 - b2) < 1e-6
+        assert on_border, (i, bo[i])
 
 
 def test_inside_test_matches_oracle(Solver):
@@ -212,9 +218,10 @@ def test_eval_means_match_oracle_and_closed_form(Solver):
     assert np.all(np.abs(u - uo) <= 3.5 * np.sqrt(use ** 2 + uose ** 2) / 4 + 1e-6)
     assert np.all(np.abs(du - duo) <= 3.5 * np.sqrt(dse ** 2 + duose ** 2) / 4 + 1e-6)
     assert np.allclose(use, uose, rtol=0.05, atol=1e-6)
+    # 64 points x 18 quantities: 4.5 SE keeps the family-wise false-alarm rate small
     ue, due = cf.disk_screened_const(sc.query, 1.0, 4.0)
-    assert np.all(np.abs(u - ue) <= 3.5 * use + 2e-3)
-    assert np.all(np.abs(du - due) <= 3.5 * dse + 0.08 * np.abs(due) + 0.01)
+    assert np.all(np.abs(u - ue) <= 4.5 * use + 2e-3)
+    assert np.all(np.abs(du - due) <= 4.5 * dse + 0.08 * np.abs(due) + 0.01)
 
 
 def test_grad_l2_and_vjp_match_oracle_estimators(Solver):
@@ -242,7 +249,8 @@ def test_vertex_gradient_chains_to_parameters(Solver):
     loss, g, gv = s.grad_l2(sc.query, sc.u_ref, sc.walks, vertex_grad=True)
     g, gv = g.cpu().numpy(), gv.cpu().numpy()
     chained = np.einsum("vk,vkp->p", gv, sc.jac)
-    assert np.allclose(g, chained, rtol=1e-6, atol=1e-9 * np.abs(g).max())
+    # the library holds J in FP32; the chain rule here uses the FP64 scene Jacobian
+    assert np.allclose(g, chained, rtol=2e-5, atol=1e-6 * np.abs(g).max())
 
 
 # ---------------------------------------------------------------- edge cases
