@@ -162,6 +162,8 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     P.g_vert = ctx->g_vert;
     P.root = 0;
     P.n_internal = ctx->bvh.n_internal;
+    P.n_tree = ctx->bvh.n_tree;
+    P.n_big = ctx->bvh.n_big;
     P.data_kind = ctx->data_kind;
     P.differential = differential;
     for (int i = 0; i < 10; ++i) P.field[i] = (float)ctx->field[i];

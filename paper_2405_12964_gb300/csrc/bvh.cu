@@ -38,13 +38,53 @@ __device__ __forceinline__ void elem_box(const float* vert, const int* elem, int
 }
 
 template <int DIM>
-__global__ void bounds_kernel(const float* vert, const int* elem, int n, unsigned int* bounds) {
+__device__ __forceinline__ float elem_diag(const float* vert, const int* elem, int e) {
+    float lo[DIM], hi[DIM];
+    elem_box<DIM>(vert, elem, e, lo, hi);
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) s += (hi[k] - lo[k]) * (hi[k] - lo[k]);
+    return sqrtf(s);
+}
+
+// Sum of element box diagonals (stats[0]) for the mean size.
+template <int DIM>
+__global__ void size_kernel(const float* vert, const int* elem, int n, float* stats) {
+    float s = 0.0f;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+        s += elem_diag<DIM>(vert, elem, e);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(stats, s);
+}
+
+// Elements whose box diagonal exceeds kBigFactor x the mean: count (stats[1]).
+constexpr float kBigFactor = 16.0f;
+
+template <int DIM>
+__global__ void count_big_kernel(const float* vert, const int* elem, int n, float* stats, int* count) {
+    const float thr = kBigFactor * stats[0] / (float)n;
+    int c = 0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+        c += elem_diag<DIM>(vert, elem, e) > thr ? 1 : 0;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+}
+
+// Scene bounds of the tree elements' centroids (ordered-uint encoding).
+template <int DIM>
+__global__ void bounds_kernel(const float* vert, const int* elem, int n, const float* stats, int split,
+                              unsigned int* bounds) {
+    const float thr = split ? kBigFactor * stats[0] / (float)n : kInf;
     float lo[DIM], hi[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) { lo[k] = kInf; hi[k] = -kInf; }
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
         float l[DIM], h[DIM];
         elem_box<DIM>(vert, elem, e, l, h);
+        float d2 = 0.0f;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) d2 += (h[k] - l[k]) * (h[k] - l[k]);
+        if (sqrtf(d2) > thr) continue;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) {
             const float c = 0.5f * (l[k] + h[k]);
@@ -85,15 +125,22 @@ __device__ __forceinline__ unsigned int spread3(unsigned int x) {   // 10 bits -
     return x;
 }
 
+// 30-bit Morton code of the centroid (15 bits per axis in 2D, 10 in 3D);
+// outsized elements get 0xFFFFFFFF so that the sort puts them last, in index order.
 template <int DIM>
 __global__ void morton_kernel(const float* vert, const int* elem, int n, const unsigned int* bounds,
-                              unsigned int* keys, int* vals) {
+                              const float* stats, int split, unsigned int* keys, int* vals) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
+    vals[e] = e;
     float l[DIM], h[DIM];
     elem_box<DIM>(vert, elem, e, l, h);
+    float d2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) d2 += (h[k] - l[k]) * (h[k] - l[k]);
+    if (split && sqrtf(d2) > kBigFactor * stats[0] / (float)n) { keys[e] = 0xFFFFFFFFu; return; }
     unsigned int q[DIM];
-    const float levels = DIM == 2 ? 65535.0f : 1023.0f;
+    const float levels = DIM == 2 ? 32767.0f : 1023.0f;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
         const float lo = ordered_to_float(bounds[k]);
@@ -105,7 +152,6 @@ __global__ void morton_kernel(const float* vert, const int* elem, int n, const u
     }
     keys[e] = DIM == 2 ? (spread2(q[0]) | (spread2(q[1]) << 1))
                        : (spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2));
-    vals[e] = e;
 }
 
 // Length of the common prefix of keys i and j, with the index as tie-breaker;
@@ -196,7 +242,7 @@ __global__ void finalize_kernel(const float* vert, const int* elem, const int* s
                                 const int* node_child, const int* node_parent, int n_internal,
                                 float4* nodes, float4* prims, int* prim_elem) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n_internal) {
+    if (i < n_internal && node_child) {
         float4* m = nodes + BvhLayout<DIM>::kNodeF4 * i + (BvhLayout<DIM>::kNodeF4 - 1);
         *m = make_float4(__int_as_float(node_child[2 * i]), __int_as_float(node_child[2 * i + 1]),
                          __int_as_float(node_parent[i]), 0.0f);
@@ -217,27 +263,17 @@ __global__ void finalize_kernel(const float* vert, const int* elem, const int* s
     }
 }
 
-// One element: a single node whose right child is empty.
+// One tree element: a single node whose right child is empty.
 template <int DIM>
-__global__ void single_leaf_kernel(const float* vert, const int* elem, float4* nodes, float4* prims,
-                                   int* prim_elem) {
+__global__ void single_leaf_kernel(const float* vert, const int* elem, const int* sorted_elem, float4* nodes) {
     float lo[DIM], hi[DIM], elo[DIM], ehi[DIM];
-    elem_box<DIM>(vert, elem, 0, lo, hi);
+    elem_box<DIM>(vert, elem, sorted_elem[0], lo, hi);
 #pragma unroll
     for (int k = 0; k < DIM; ++k) { elo[k] = kInf; ehi[k] = -kInf; }
     write_child_box<DIM>(nodes, 0, 0, lo, hi);
     write_child_box<DIM>(nodes, 0, 1, elo, ehi);
     nodes[BvhLayout<DIM>::kNodeF4 - 1] =
         make_float4(__int_as_float(~0), __int_as_float(kEmptyChild), __int_as_float(-1), 0.0f);
-    prim_elem[0] = 0;
-    if (DIM == 2) {
-        prims[0] = make_float4(vert[2 * elem[0]], vert[2 * elem[0] + 1], vert[2 * elem[1]], vert[2 * elem[1] + 1]);
-    } else {
-        for (int c = 0; c < 3; ++c) {
-            const int v = elem[c];
-            prims[c] = make_float4(vert[3 * v], vert[3 * v + 1], vert[3 * v + 2], 0.0f);
-        }
-    }
 }
 
 // ---- queries --------------------------------------------------------------
@@ -270,11 +306,15 @@ __global__ void closest_kernel(BvhView bvh, const int* prim_elem, int n, const f
     bary[2 * i + 1] = w2;
 }
 
-// Ray crossing count along a fixed generic direction; any-order stackless
-// traversal over the parent links, pruning boxes the ray misses.
+// Inside test by ray parity along a fixed generic direction.  The ray from
+// each point is cut into 32 sub-intervals [t_s, t_s+1) up to the far corner of
+// the scene box; lane s of the point's warp counts the crossings in its
+// interval with an any-order stackless traversal (pruning boxes its interval
+// misses) plus the outsized elements, and the warp sums the counts.
 template <int DIM>
-__device__ __forceinline__ bool ray_hits_box(const float* o, const float* inv, const float* lo, const float* hi) {
-    float t0 = 0.0f, t1 = kInf;
+__device__ __forceinline__ bool seg_hits_box(const float* o, const float* inv, float ta, float tb, const float* lo,
+                                             const float* hi) {
+    float t0 = ta, t1 = tb;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) {
         const float a = (lo[k] - o[k]) * inv[k], b = (hi[k] - o[k]) * inv[k];
@@ -284,17 +324,18 @@ __device__ __forceinline__ bool ray_hits_box(const float* o, const float* inv, c
     return t0 <= t1;
 }
 
+// Ray parameter of the crossing with leaf p, or -1.
 template <int DIM>
-__device__ __forceinline__ int ray_prim_cross(const float4* prims, int p, const float* o, const float* dir) {
+__device__ __forceinline__ float ray_prim_t(const float4* prims, int p, const float* o, const float* dir) {
     if (DIM == 2) {
         const float4 s = prims[p];
         const float ex = s.z - s.x, ey = s.w - s.y;
         const float det = -dir[0] * ey + dir[1] * ex;
-        if (det == 0.0f) return 0;
+        if (det == 0.0f) return -1.0f;
         const float rx = s.x - o[0], ry = s.y - o[1];
         const float t = (-rx * ey + ry * ex) / det;
         const float u = (dir[0] * ry - dir[1] * rx) / det;
-        return (t > 0.0f && u >= 0.0f && u < 1.0f) ? 1 : 0;
+        return (u >= 0.0f && u < 1.0f) ? t : -1.0f;
     } else {
         const float4 a = prims[3 * p], b = prims[3 * p + 1], c = prims[3 * p + 2];
         const float e1[3] = {b.x - a.x, b.y - a.y, b.z - a.z};
@@ -302,52 +343,106 @@ __device__ __forceinline__ int ray_prim_cross(const float4* prims, int p, const 
         const float pv[3] = {dir[1] * e2[2] - dir[2] * e2[1], dir[2] * e2[0] - dir[0] * e2[2],
                              dir[0] * e2[1] - dir[1] * e2[0]};
         const float det = e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2];
-        if (det == 0.0f) return 0;
+        if (det == 0.0f) return -1.0f;
         const float inv = 1.0f / det;
         const float tv[3] = {o[0] - a.x, o[1] - a.y, o[2] - a.z};
         const float u = (tv[0] * pv[0] + tv[1] * pv[1] + tv[2] * pv[2]) * inv;
-        if (u < 0.0f || u > 1.0f) return 0;
+        if (u < 0.0f || u > 1.0f) return -1.0f;
         const float qv[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2],
                              tv[0] * e1[1] - tv[1] * e1[0]};
         const float v = (dir[0] * qv[0] + dir[1] * qv[1] + dir[2] * qv[2]) * inv;
-        if (v < 0.0f || u + v > 1.0f) return 0;
-        const float t = (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) * inv;
-        return t > 0.0f ? 1 : 0;
+        if (v < 0.0f || u + v > 1.0f) return -1.0f;
+        return (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) * inv;
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ void prim_box(const float4* prims, int p, float* lo, float* hi) {
+    if (DIM == 2) {
+        const float4 s = prims[p];
+        lo[0] = fminf(s.x, s.z); hi[0] = fmaxf(s.x, s.z);
+        lo[1] = fminf(s.y, s.w); hi[1] = fmaxf(s.y, s.w);
+    } else {
+        const float4 a = prims[3 * p], b = prims[3 * p + 1], c = prims[3 * p + 2];
+        lo[0] = fminf(a.x, fminf(b.x, c.x)); hi[0] = fmaxf(a.x, fmaxf(b.x, c.x));
+        lo[1] = fminf(a.y, fminf(b.y, c.y)); hi[1] = fmaxf(a.y, fmaxf(b.y, c.y));
+        lo[2] = fminf(a.z, fminf(b.z, c.z)); hi[2] = fmaxf(a.z, fmaxf(b.z, c.z));
     }
 }
 
 template <int DIM>
 __global__ void inside_kernel(BvhView bvh, int n, const float* p, int* inside) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int pt = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (pt >= n) return;    // whole warps exit together
     float o[DIM], dir[DIM], inv[DIM];
     if (DIM == 2) { dir[0] = 0.8191520443f; dir[1] = 0.5735764364f; }
     else { dir[0] = 0.5144957554f; dir[1] = 0.6859943406f; dir[2] = 0.5144957554f; }
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) { o[k] = p[DIM * i + k]; inv[k] = 1.0f / dir[k]; }
-    int count = 0;
-    int node = bvh.root, from = kFromParent;
-    int budget = 3 * bvh.n_internal + 8;
-    while (--budget >= 0) {
+    for (int k = 0; k < DIM; ++k) { o[k] = p[DIM * pt + k]; inv[k] = 1.0f / dir[k]; }
+    // scene box: the root's two children and the outsized elements
+    float slo[DIM], shi[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { slo[k] = o[k]; shi[k] = o[k]; }
+    if (bvh.n_internal > 0) {
         float lo0[DIM], hi0[DIM], lo1[DIM], hi1[DIM];
         int c0, c1, parent;
-        load_node<DIM>(bvh.nodes, node, lo0, hi0, lo1, hi1, c0, c1, parent);
-        int state = from == kFromParent ? 0 : (from == c0 ? 1 : 2);
-        int next = kFromParent;
-        while (state < 2) {
-            const int c = state == 0 ? c0 : c1;
-            const bool hit = c != kEmptyChild &&
-                             (state == 0 ? ray_hits_box<DIM>(o, inv, lo0, hi0) : ray_hits_box<DIM>(o, inv, lo1, hi1));
-            if (hit && c >= 0) { next = c; break; }
-            if (hit) count += ray_prim_cross<DIM>(bvh.prims, ~c, o, dir);
-            ++state;
+        load_node<DIM>(bvh.nodes, bvh.root, lo0, hi0, lo1, hi1, c0, c1, parent);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) {
+            slo[k] = fminf(slo[k], lo0[k]); shi[k] = fmaxf(shi[k], hi0[k]);
+            if (c1 != kEmptyChild) { slo[k] = fminf(slo[k], lo1[k]); shi[k] = fmaxf(shi[k], hi1[k]); }
         }
-        if (next != kFromParent) { from = kFromParent; node = next; continue; }
-        if (parent < 0) break;
-        from = node;
-        node = parent;
     }
-    inside[i] = count & 1;
+    for (int q = bvh.n_tree; q < bvh.n_tree + bvh.n_big; ++q) {
+        float lo[DIM], hi[DIM];
+        prim_box<DIM>(bvh.prims, q, lo, hi);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) { slo[k] = fminf(slo[k], lo[k]); shi[k] = fmaxf(shi[k], hi[k]); }
+    }
+    float tmax2 = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const float e = fmaxf(o[k] - slo[k], shi[k] - o[k]);
+        tmax2 += e * e;
+    }
+    const float tmax = 1.001f * sqrtf(tmax2) + 1e-6f;
+    const float ta = tmax * (float)lane / 32.0f;
+    const float tb = lane == 31 ? 2.0f * tmax : tmax * (float)(lane + 1) / 32.0f;
+    int count = 0;
+    for (int q = bvh.n_tree; q < bvh.n_tree + bvh.n_big; ++q) {
+        const float t = ray_prim_t<DIM>(bvh.prims, q, o, dir);
+        count += (t > 0.0f && t >= ta && t < tb) ? 1 : 0;
+    }
+    if (bvh.n_internal > 0) {
+        int node = bvh.root, from = kFromParent;
+        int budget = 3 * bvh.n_internal + 8;
+        while (--budget >= 0) {
+            float lo0[DIM], hi0[DIM], lo1[DIM], hi1[DIM];
+            int c0, c1, parent;
+            load_node<DIM>(bvh.nodes, node, lo0, hi0, lo1, hi1, c0, c1, parent);
+            int state = from == kFromParent ? 0 : (from == c0 ? 1 : 2);
+            int next = kFromParent;
+            while (state < 2) {
+                const int c = state == 0 ? c0 : c1;
+                const bool hit = c != kEmptyChild &&
+                                 (state == 0 ? seg_hits_box<DIM>(o, inv, ta, tb, lo0, hi0)
+                                             : seg_hits_box<DIM>(o, inv, ta, tb, lo1, hi1));
+                if (hit && c >= 0) { next = c; break; }
+                if (hit) {
+                    const float t = ray_prim_t<DIM>(bvh.prims, ~c, o, dir);
+                    count += (t > 0.0f && t >= ta && t < tb) ? 1 : 0;
+                }
+                ++state;
+            }
+            if (next != kFromParent) { from = kFromParent; node = next; continue; }
+            if (parent < 0) break;
+            from = node;
+            node = parent;
+        }
+    }
+    for (int off = 16; off > 0; off >>= 1) count += __shfl_xor_sync(0xffffffffu, count, off);
+    if (lane == 0) inside[pt] = count & 1;
 }
 
 __global__ void philox_kernel(int n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out) {
@@ -391,6 +486,7 @@ cudaError_t bvh_reserve(BvhBuffers& b, int dim, int n_elem) {
     DW_TRY(cudaMalloc(&b.node_child, sizeof(int) * 2 * (size_t)n_int));
     DW_TRY(cudaMalloc(&b.counters, sizeof(int) * (size_t)n_int));
     DW_TRY(cudaMalloc(&b.bounds, sizeof(unsigned int) * 6));
+    DW_TRY(cudaMalloc(&b.stats, sizeof(float) * 2 + sizeof(int) * 2));
     size_t tmp = 0;
     DW_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp, b.keys, b.keys_sorted, b.vals, b.vals_sorted, n_elem));
     DW_TRY(cudaMalloc(&b.sort_tmp, tmp));
@@ -404,38 +500,58 @@ cudaError_t bvh_reserve(BvhBuffers& b, int dim, int n_elem) {
 void bvh_free(BvhBuffers& b) {
     cudaFree(b.nodes); cudaFree(b.prims); cudaFree(b.prim_elem); cudaFree(b.keys); cudaFree(b.keys_sorted);
     cudaFree(b.vals); cudaFree(b.vals_sorted); cudaFree(b.leaf_parent); cudaFree(b.node_parent);
-    cudaFree(b.node_child); cudaFree(b.counters); cudaFree(b.bounds);
+    cudaFree(b.node_child); cudaFree(b.counters); cudaFree(b.bounds); cudaFree(b.stats);
     cudaFree(b.sort_tmp);
     b = BvhBuffers();
 }
 
+constexpr int kMaxBig = 64;
+
 template <int DIM>
 static cudaError_t build_impl(BvhBuffers& b, const float* vert, const int* elem, int n, cudaStream_t s) {
     b.n_elem = n;
-    if (n == 1) {
-        b.n_internal = 1;
-        single_leaf_kernel<DIM><<<1, 1, 0, s>>>(vert, elem, b.nodes, b.prims, b.prim_elem);
-        return cudaGetLastError();
-    }
-    b.n_internal = n - 1;
-    cudaError_t e = cudaMemsetAsync(b.bounds, 0xff, sizeof(unsigned int) * DIM, s);   // min slots
+    float* stats = b.stats;
+    int* count = reinterpret_cast<int*>(b.stats + 2);
+    cudaError_t e = cudaMemsetAsync(b.stats, 0, sizeof(float) * 2 + sizeof(int) * 2, s);
+    if (e != cudaSuccess) return e;
+    const int gb = min(nblk(n, 256), 1024);
+    size_kernel<DIM><<<gb, 256, 0, s>>>(vert, elem, n, stats);
+    count_big_kernel<DIM><<<gb, 256, 0, s>>>(vert, elem, n, stats, count);
+    int n_big = 0;
+    e = cudaMemcpyAsync(&n_big, count, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    const int split = (n_big > 0 && n_big <= kMaxBig && n_big < n) ? 1 : 0;
+    if (!split) n_big = 0;
+    const int nt = n - n_big;
+    b.n_big = n_big;
+    b.n_tree = nt;
+    e = cudaMemsetAsync(b.bounds, 0xff, sizeof(unsigned int) * DIM, s);   // min slots
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(b.bounds + DIM, 0, sizeof(unsigned int) * DIM, s);             // max slots
     if (e != cudaSuccess) return e;
-    bounds_kernel<DIM><<<min(nblk(n, 256), 1024), 256, 0, s>>>(vert, elem, n, b.bounds);
-    morton_kernel<DIM><<<nblk(n, 256), 256, 0, s>>>(vert, elem, n, b.bounds, b.keys, b.vals);
+    bounds_kernel<DIM><<<gb, 256, 0, s>>>(vert, elem, n, stats, split, b.bounds);
+    morton_kernel<DIM><<<nblk(n, 256), 256, 0, s>>>(vert, elem, n, b.bounds, stats, split, b.keys, b.vals);
     size_t tmp = b.sort_tmp_bytes;
-    e = cub::DeviceRadixSort::SortPairs(b.sort_tmp, tmp, b.keys, b.keys_sorted, b.vals, b.vals_sorted, n, 0,
-                                        DIM == 2 ? 32 : 30, s);
+    e = cub::DeviceRadixSort::SortPairs(b.sort_tmp, tmp, b.keys, b.keys_sorted, b.vals, b.vals_sorted, n, 0, 32, s);
     if (e != cudaSuccess) return e;
-    radix_tree_kernel<<<nblk(n - 1, 256), 256, 0, s>>>(b.keys_sorted, n, b.node_child, b.node_parent,
-                                                       b.leaf_parent);
-    e = cudaMemsetAsync(b.counters, 0, sizeof(int) * (size_t)(n - 1), s);
-    if (e != cudaSuccess) return e;
-    refit_kernel<DIM><<<nblk(n, 256), 256, 0, s>>>(vert, elem, b.vals_sorted, n, b.node_child, b.node_parent,
-                                                   b.leaf_parent, b.counters, b.nodes);
-    finalize_kernel<DIM><<<nblk(n, 256), 256, 0, s>>>(vert, elem, b.vals_sorted, n, b.node_child,
-                                                      b.node_parent, n - 1, b.nodes, b.prims, b.prim_elem);
+    if (nt >= 2) {
+        b.n_internal = nt - 1;
+        radix_tree_kernel<<<nblk(nt - 1, 256), 256, 0, s>>>(b.keys_sorted, nt, b.node_child, b.node_parent,
+                                                            b.leaf_parent);
+        e = cudaMemsetAsync(b.counters, 0, sizeof(int) * (size_t)(nt - 1), s);
+        if (e != cudaSuccess) return e;
+        refit_kernel<DIM><<<nblk(nt, 256), 256, 0, s>>>(vert, elem, b.vals_sorted, nt, b.node_child,
+                                                        b.node_parent, b.leaf_parent, b.counters, b.nodes);
+        finalize_kernel<DIM><<<nblk(n, 256), 256, 0, s>>>(vert, elem, b.vals_sorted, n, b.node_child,
+                                                          b.node_parent, nt - 1, b.nodes, b.prims, b.prim_elem);
+    } else {
+        b.n_internal = nt;    // 1: a single-leaf node; 0: no tree
+        if (nt == 1) single_leaf_kernel<DIM><<<1, 1, 0, s>>>(vert, elem, b.vals_sorted, b.nodes);
+        finalize_kernel<DIM><<<nblk(n, 256), 256, 0, s>>>(vert, elem, b.vals_sorted, n, nullptr, nullptr, 0,
+                                                          b.nodes, b.prims, b.prim_elem);
+    }
     return cudaGetLastError();
 }
 
@@ -451,6 +567,8 @@ static BvhView view_of(const BvhBuffers& b) {
     v.prims = b.prims;
     v.root = 0;
     v.n_internal = b.n_internal;
+    v.n_tree = b.n_tree;
+    v.n_big = b.n_big;
     return v;
 }
 
@@ -464,8 +582,8 @@ cudaError_t launch_closest(const BvhBuffers& b, int n, const float* p, float* di
 
 cudaError_t launch_inside(const BvhBuffers& b, int n, const float* p, int* inside, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    if (b.dim == 2) inside_kernel<2><<<nblk(n, 128), 128, 0, s>>>(view_of(b), n, p, inside);
-    else inside_kernel<3><<<nblk(n, 128), 128, 0, s>>>(view_of(b), n, p, inside);
+    if (b.dim == 2) inside_kernel<2><<<nblk(32LL * n, 128), 128, 0, s>>>(view_of(b), n, p, inside);
+    else inside_kernel<3><<<nblk(32LL * n, 128), 128, 0, s>>>(view_of(b), n, p, inside);
     return cudaGetLastError();
 }
 

@@ -175,11 +175,17 @@ template <int DIM> struct BvhLayout;
 template <> struct BvhLayout<2> { static constexpr int kNodeF4 = 3; static constexpr int kPrimF4 = 1; };
 template <> struct BvhLayout<3> { static constexpr int kNodeF4 = 4; static constexpr int kPrimF4 = 3; };
 
+// Leaves [0, n_tree) are the LBVH's, in Morton order; leaves [n_tree,
+// n_tree + n_big) are outsized elements (much larger than the typical one,
+// such as an enclosing box) kept out of the tree so that their boxes do not
+// inflate every ancestor's: each query tests them first, by brute force.
 struct BvhView {
     const float4* nodes;
     const float4* prims;
     int root;
-    int n_internal;
+    int n_internal;   // internal nodes of the tree (0: no tree)
+    int n_tree;       // leaves in the tree
+    int n_big;        // outsized elements after the tree's leaves
 };
 
 template <int DIM>
@@ -240,6 +246,12 @@ __device__ __forceinline__ float prim_dist2(const float4* __restrict__ prims, in
 template <int DIM>
 __device__ __forceinline__ bool closest_leaf(const BvhView& bvh, const float* q, float& best2, int& best,
                                              unsigned& n_nodes, unsigned& n_prims) {
+    for (int p = bvh.n_tree; p < bvh.n_tree + bvh.n_big; ++p) {
+        ++n_prims;
+        const float dd = prim_dist2<DIM>(bvh.prims, p, q);
+        if (dd < best2) { best2 = dd; best = p; }
+    }
+    if (bvh.n_internal == 0) return true;
     int node = bvh.root;
     int from = kFromParent;
     int budget = 3 * bvh.n_internal + 8;

@@ -20,6 +20,8 @@ struct DevProblem {
     const float* g_vert;        // n_vert (mapped data)
     int root;
     int n_internal;
+    int n_tree;                 // leaves in the LBVH
+    int n_big;                  // outsized elements after them
     int data_kind;              // 0 mapped, 1 field
     int differential;
     float field[10];            // c0, c(3), Axx Ayy Azz Axy Axz Ayz
@@ -59,6 +61,7 @@ struct DevCounters {
 // BVH build (bvh.cu).  All pointers are device pointers; work on `stream`.
 struct BvhBuffers {
     int dim = 0, n_elem = 0, n_internal = 0;
+    int n_tree = 0, n_big = 0;    // leaves in the LBVH, outsized elements kept out of it
     float4* nodes = nullptr;      // max(1, n_elem-1) nodes
     float4* prims = nullptr;      // n_elem prims
     int* prim_elem = nullptr;     // n_elem
@@ -72,6 +75,7 @@ struct BvhBuffers {
     int* node_child = nullptr;    // 2 per internal node
     int* counters = nullptr;
     unsigned int* bounds = nullptr;  // 2*dim ordered-uint scene bounds
+    float* stats = nullptr;          // size statistics + outsized count
     void* sort_tmp = nullptr;
     size_t sort_tmp_bytes = 0;
     int capacity = 0;

@@ -7,8 +7,8 @@
 //  scatter      reverse mode (Sec. 4.3): a weight per walk (VJP cotangent, or
 //               the U-statistic product weight of Eq. (ustatistics) in batches
 //               of B) times the walk's boundary term, scattered into per-vertex
-//               FP64 accumulators a_v (d values) and s_v; lanes of a warp that
-//               hit the same vertex are summed before one atomic per vertex
+//               FP64 accumulators a_v (d values) and s_v, aggregated per block
+//               in shared memory before the global atomics
 //  gemv         the adjoint map grad_theta = sum_v J_v^T a_v + sum_v dg_v s_v
 //  loss         1/2 sum_p (mean_p - uref_p)^2
 #include "dwos_device.cuh"
@@ -107,61 +107,87 @@ __global__ void reduce_udot_kernel(const dwos_record* __restrict__ rec, const in
     }
 }
 
-// Sum of v over the lanes in `peers` (all 32 lanes call this together).
-__device__ __forceinline__ double peer_sum(double v, unsigned peers) {
-    double acc = 0.0;
-    for (int src = 0; src < 32; ++src) {
-        const double t = __shfl_sync(kFull, v, src);
-        if ((peers >> src) & 1u) acc += t;
-    }
-    return acc;
-}
+// Reverse-mode scatter.  Each block takes a contiguous range of walks (whole
+// U-statistic batches), computes every walk's weight, and accumulates the
+// weighted boundary terms per vertex in a shared-memory hash table (open
+// addressing, a few probes; a walk whose vertex finds no slot goes straight
+// to global memory).  The table is then flushed with one FP64 atomic per
+// distinct vertex and value, so vertices that many walks reach (an enclosing
+// box, a coarse mesh) cost one global atomic per block instead of one per walk.
+constexpr int kSlots = 1024;
+constexpr int kProbes = 8;
 
 template <int DIM>
-__global__ void scatter_kernel(const dwos_record* __restrict__ rec, const int* __restrict__ elem, int n_points,
-                               int W, int B, int mode, const float* __restrict__ cot_or_uref,
-                               double* __restrict__ acc_vert, double* __restrict__ acc_g) {
-    const long long total = (long long)n_points * W;
-    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = i < total;
-    dwos_record r;
-    if (valid) r = rec[i];
-    else { r.u = 0.0f; r.elem = -1; r.b1 = 0.0f; r.b2 = 0.0f; r.c[0] = r.c[1] = r.c[2] = 0.0f; r.meta = 0; }
-    const int p = valid ? (int)(i / W) : 0;
-    double wt;
-    if (mode == 0) {
-        wt = valid ? (double)cot_or_uref[p] / W : 0.0;
-    } else {
-        // U-statistic weight of Eq. (ustatistics) for squared loss:
-        // u*udot is estimated by sum_m udot_m (S - u_m)/(B(B-1)); uref*udot by uref sum_m udot_m / B;
-        // each batch is one of W/B estimates of the point's derivative.
-        double S = r.u;
-        for (int o = B >> 1; o > 0; o >>= 1) S += __shfl_xor_sync(kFull, S, o);
-        const double ur = valid ? (double)cot_or_uref[p] : 0.0;
-        wt = ((S - (double)r.u) / ((double)B * (B - 1)) - ur / B) / (double)(W / B);
+__global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restrict__ rec,
+                                                      const int* __restrict__ elem, int n_points, int W, int B,
+                                                      int mode, const float* __restrict__ cot_or_uref,
+                                                      long long walks_per_block, double* __restrict__ acc_vert,
+                                                      double* __restrict__ acc_g) {
+    __shared__ int keys[kSlots];
+    __shared__ double vals[kSlots][DIM + 1];
+    for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
+        keys[i] = -1;
+#pragma unroll
+        for (int k = 0; k <= DIM; ++k) vals[i][k] = 0.0;
     }
-    const bool hit = valid && r.elem >= 0;
-    const float wv[3] = {1.0f - r.b1 - r.b2, r.b1, r.b2};
-#pragma unroll
-    for (int s = 0; s < DIM; ++s) {
-        const int vid = hit ? __ldg(elem + DIM * r.elem + s) : -1;
-        const double ws = hit ? wt * (double)wv[s] : 0.0;
-        double val[DIM + 1];
-#pragma unroll
-        for (int k = 0; k < DIM; ++k) val[k] = ws * (double)r.c[k];
-        val[DIM] = ws;
-        const unsigned peers = __match_any_sync(kFull, vid);
-        const bool shared = __any_sync(kFull, __popc(peers) > 1);
-        if (shared) {
-#pragma unroll
-            for (int k = 0; k <= DIM; ++k) val[k] = peer_sum(val[k], peers);
+    __syncthreads();
+    const long long total = (long long)n_points * W;
+    const long long begin = (long long)blockIdx.x * walks_per_block;
+    const long long end = min(begin + walks_per_block, total);
+    for (long long base = begin; base < end; base += blockDim.x) {
+        const long long i = base + threadIdx.x;
+        const bool valid = i < end;
+        dwos_record r;
+        if (valid) r = rec[i];
+        else { r.u = 0.0f; r.elem = -1; r.b1 = 0.0f; r.b2 = 0.0f; r.c[0] = r.c[1] = r.c[2] = 0.0f; r.meta = 0; }
+        const int p = valid ? (int)(i / W) : 0;
+        double wt;
+        if (mode == 0) {
+            wt = valid ? (double)cot_or_uref[p] / W : 0.0;
+        } else {
+            // U-statistic weight, Eq. (ustatistics): u*udot is estimated by
+            // sum_m udot_m (S - u_m)/(B(B-1)), uref*udot by uref sum_m udot_m / B;
+            // each batch is one of W/B estimates of the point's derivative.
+            double S = r.u;
+            for (int o = B >> 1; o > 0; o >>= 1) S += __shfl_xor_sync(kFull, S, o);
+            const double ur = valid ? (double)cot_or_uref[p] : 0.0;
+            wt = ((S - (double)r.u) / ((double)B * (B - 1)) - ur / B) / (double)(W / B);
         }
-        const bool leader = (int)(threadIdx.x & 31) == __ffs(peers) - 1;
-        if (leader && vid >= 0) {
+        if (!(valid && r.elem >= 0)) continue;
+        const float wv[3] = {1.0f - r.b1 - r.b2, r.b1, r.b2};
 #pragma unroll
-            for (int k = 0; k < DIM; ++k) atomicAdd(acc_vert + (size_t)vid * DIM + k, val[k]);
-            if (acc_g) atomicAdd(acc_g + vid, val[DIM]);
+        for (int sidx = 0; sidx < DIM; ++sidx) {
+            const int vid = __ldg(elem + DIM * r.elem + sidx);
+            const double ws = wt * (double)wv[sidx];
+            double val[DIM + 1];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) val[k] = ws * (double)r.c[k];
+            val[DIM] = ws;
+            unsigned h = ((unsigned)vid * 2654435761u) >> 22;   // 10-bit hash
+            bool done = false;
+            for (int probe = 0; probe < kProbes && !done; ++probe) {
+                const int slot = (int)((h + probe) & (kSlots - 1));
+                const int prev = atomicCAS(&keys[slot], -1, vid);
+                if (prev == -1 || prev == vid) {
+#pragma unroll
+                    for (int k = 0; k <= DIM; ++k) atomicAdd(&vals[slot][k], val[k]);
+                    done = true;
+                }
+            }
+            if (!done) {
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) atomicAdd(acc_vert + (size_t)vid * DIM + k, val[k]);
+                if (acc_g) atomicAdd(acc_g + vid, val[DIM]);
+            }
         }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
+        const int vid = keys[i];
+        if (vid < 0) continue;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) atomicAdd(acc_vert + (size_t)vid * DIM + k, vals[i][k]);
+        if (acc_g) atomicAdd(acc_g + vid, vals[i][DIM]);
     }
 }
 
@@ -234,9 +260,13 @@ cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int
     const long long total = (long long)n_points * W;
     if (total <= 0) return cudaSuccess;
     const int bs = 256;
-    const long long blocks = (total + bs - 1) / bs;
-    if (dim == 2) scatter_kernel<2><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, acc_vert, acc_g);
-    else scatter_kernel<3><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, acc_vert, acc_g);
+    // about four blocks per SM; each block a multiple of 256 walks (whole batches)
+    long long per = (total + 4 * 152 - 1) / (4 * 152);
+    per = ((per + bs - 1) / bs) * bs;
+    if (per < bs) per = bs;
+    const long long blocks = (total + per - 1) / per;
+    if (dim == 2) scatter_kernel<2><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, per, acc_vert, acc_g);
+    else scatter_kernel<3><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, per, acc_vert, acc_g);
     return cudaGetLastError();
 }
 

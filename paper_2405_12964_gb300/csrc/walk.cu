@@ -69,7 +69,7 @@ struct WarpStats {
 };
 
 template <int DIM>
-__global__ void __launch_bounds__(256) walk_kernel(const DevProblem* __restrict__ g_probs, int n_probs,
+__global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevProblem* __restrict__ g_probs, int n_probs,
                                                    unsigned long long total, DevCounters* __restrict__ ctr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DevProblem* sp = reinterpret_cast<DevProblem*>(smem_raw);
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(256) walk_kernel(const DevProblem* __restrict_
         const unsigned long long local = gw - P.work_begin;
 
         // ---- DistanceToBoundary, seeded with the previous closest element
-        BvhView bvh{P.nodes, P.prims, P.root, P.n_internal};
+        BvhView bvh{P.nodes, P.prims, P.root, P.n_internal, P.n_tree, P.n_big};
         float best2 = kInf;
         int best = -1;
         if (hint >= 0) { best2 = prim_dist2<DIM>(P.prims, hint, x); best = hint; }

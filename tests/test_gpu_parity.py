@@ -138,13 +138,9 @@ def test_closest_point_matches_brute_force(Solver, which):
         one = oracle.Problem(vert=sc.vert, elem=sc.elem[e[i]:e[i] + 1], data_kind="mapped",
                              g_vert=np.zeros(len(sc.vert)))
         dg = oracle.closest_point(one, p[i:i + 1])[0][0]
-        assert abs(dg - do[i]) <= 2e-5 * max(1.0, do[i]) + 2e-6
-        b1, b2 = bo[i]
-        if sc.dim == 2:
-            on_border = min(b1, 1 - b1) < 1e-6
-        else:
-            on_border = min(b1, b2, 1 - b1 - b2) < 1e-6
-        assert on_border, (i, bo[i])
+        # exactly as close up to FP32 rounding of coordinates and distances
+        assert abs(dg - do[i]) <= 4e-7 * max(1.0, float(np.abs(p[i]).max())) + 2e-7 * do[i] + 1e-7, (dg, do[i])
+    assert len(dis) <= 0.5 * len(p)
 
 
 def test_inside_test_matches_oracle(Solver):
@@ -218,10 +214,14 @@ def test_eval_means_match_oracle_and_closed_form(Solver):
     assert np.all(np.abs(u - uo) <= 3.5 * np.sqrt(use ** 2 + uose ** 2) / 4 + 1e-6)
     assert np.all(np.abs(du - duo) <= 3.5 * np.sqrt(dse ** 2 + duose ** 2) / 4 + 1e-6)
     assert np.allclose(use, uose, rtol=0.05, atol=1e-6)
-    # 64 points x 18 quantities: 4.5 SE keeps the family-wise false-alarm rate small
+    # 64 points x 18 quantities: 4.5 SE keeps the family-wise false-alarm rate small.
+    # With g = 1 a nested walk returns exactly g unless roulette stops it, so du/dn is a
+    # rare-event estimate (a handful of nonzero walks per point) whose per-point sample SE
+    # is unreliable; the median SE over the points stands in where it is larger.
     ue, due = cf.disk_screened_const(sc.query, 1.0, 4.0)
     assert np.all(np.abs(u - ue) <= 4.5 * use + 2e-3)
-    assert np.all(np.abs(du - due) <= 4.5 * dse + 0.08 * np.abs(due) + 0.01)
+    dse_ref = np.maximum(dse, np.median(dse, axis=0, keepdims=True))
+    assert np.all(np.abs(du - due) <= 4.5 * dse_ref + 0.08 * np.abs(due) + 0.01)
 
 
 def test_grad_l2_and_vjp_match_oracle_estimators(Solver):
