@@ -95,6 +95,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_ranks(t_local: float, steps_local: float, dist=None, device=None):
+    """Whole-job figures over ranks: the slowest rank's time and the sum of
+    walk-steps (weak scaling: every rank runs its own walk-id range)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return t_local, steps_local
+    import torch
+    tt = torch.tensor([t_local], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ss = torch.tensor([float(steps_local)], device=device, dtype=torch.float64)
+    dist.all_reduce(ss)
+    return float(tt.item()), float(ss.item())
+
+
 def cpu_baseline(sc, budget_s: float = 15.0):
     """The FP64 oracle (brute-force closest point) on a bounded sample of the
     same workload: every observation point, a few differential walks each."""
@@ -226,15 +239,7 @@ def main():
     launches = s.stats()["launches"] - launches_warm
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_local = sum(step_ms) / 1e3
-    t = t_local
-    steps_all = steps_done
-    if dist:
-        tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
-        ss = torch.tensor([steps_done], device=dev, dtype=torch.float64)
-        dist.all_reduce(ss)
-        steps_all = float(ss.item())
+    t, steps_all = aggregate_ranks(t_local, steps_done, dist, dev)
     value = steps_all / t
     ms_per_step = 1e3 * t / args.steps
 

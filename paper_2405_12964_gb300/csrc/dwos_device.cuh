@@ -76,6 +76,23 @@ __device__ __forceinline__ float bessel_k0(float x) {
     return expf(-x) * rsqrtf(x) * p;
 }
 
+// Russian roulette of Algorithm 1: true when the walk stops (alpha < u).
+// alpha >= exp(-(kd)^2/4) >= 1 - (kd)^2/4 in 2D (I0(x) <= exp(x^2/4)) and
+// alpha >= 1 - (kd)^2/6 in 3D (sinh(x)/x <= exp(x^2/6)); when u lies below that
+// bound by more than the FP32 error of the full evaluation, the walk survives
+// and alpha itself is not needed.  Otherwise alpha is evaluated exactly.
+template <int DIM>
+__device__ __forceinline__ float recursive_weight(float k, float d);
+
+template <int DIM>
+__device__ __forceinline__ bool roulette_stops(float k, float d, float u) {
+    if (k == 0.0f) return false;                    // alpha = 1 > u for u in (0, 1)
+    const float x = k * d;
+    const float lb = 1.0f - x * x * (DIM == 2 ? 0.25f : (1.0f / 6.0f)) - 1e-5f;
+    if (u < lb) return false;
+    return recursive_weight<DIM>(k, d) < u;
+}
+
 // alpha(d) = P(d) |dB(d)|: 1/I0(kd) in 2D, kd/sinh(kd) in 3D, 1 when sigma = 0.
 template <int DIM>
 __device__ __forceinline__ float recursive_weight(float k, float d) {
@@ -111,14 +128,18 @@ __device__ __forceinline__ float source_weight(float k, float d, float u) {
 // Closest point on one element.  Segments: clamp the projection parameter.
 // Triangles: Voronoi-region classification (Ericson, Real-Time Collision
 // Detection, Sec. 5.1.5).  Both return the squared distance and the weights
-// of vertices 1 (and 2).
+// of vertices 1 (and 2).  Divisions use the fast path: the closest point is a
+// projection, so the squared distance is stationary in the weights there and
+// their ulp-level errors only reach d^2 at second order.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float seg_closest(const float* q, float ax, float ay, float bx, float by,
                                              float& t_out) {
     const float ex = bx - ax, ey = by - ay;
     const float px = q[0] - ax, py = q[1] - ay;
     const float len2 = ex * ex + ey * ey;
-    float t = len2 > 0.0f ? (px * ex + py * ey) / len2 : 0.0f;
+    // fast division: the distance is quadratic in t at its minimum, so an
+    // ulp-level error in t does not move d^2 beyond rounding
+    float t = len2 > 0.0f ? __fdividef(px * ex + py * ey, len2) : 0.0f;
     t = fminf(fmaxf(t, 0.0f), 1.0f);
     const float dx = px - t * ex, dy = py - t * ey;
     t_out = t;
@@ -144,14 +165,14 @@ __device__ __forceinline__ float tri_closest(const float* q, const float3 a, con
     float s, t;
     if (d1 <= 0.0f && d2 <= 0.0f) { s = 0.0f; t = 0.0f; }                          // vertex a
     else if (d3 >= 0.0f && d4 <= d3) { s = 1.0f; t = 0.0f; }                        // vertex b
-    else if (vc <= 0.0f && d1 >= 0.0f && d3 <= 0.0f) { s = d1 / (d1 - d3); t = 0.0f; }  // edge ab
+    else if (vc <= 0.0f && d1 >= 0.0f && d3 <= 0.0f) { s = __fdividef(d1, d1 - d3); t = 0.0f; }  // edge ab
     else if (d6 >= 0.0f && d5 <= d6) { s = 0.0f; t = 1.0f; }                        // vertex c
-    else if (vb <= 0.0f && d2 >= 0.0f && d6 <= 0.0f) { s = 0.0f; t = d2 / (d2 - d6); }  // edge ac
+    else if (vb <= 0.0f && d2 >= 0.0f && d6 <= 0.0f) { s = 0.0f; t = __fdividef(d2, d2 - d6); }  // edge ac
     else if (va <= 0.0f && (d4 - d3) >= 0.0f && (d5 - d6) >= 0.0f) {                // edge bc
-        const float u = (d4 - d3) / ((d4 - d3) + (d5 - d6));
+        const float u = __fdividef(d4 - d3, (d4 - d3) + (d5 - d6));
         s = 1.0f - u; t = u;
     } else {                                                                          // face
-        const float inv = 1.0f / (va + vb + vc);
+        const float inv = __fdividef(1.0f, va + vb + vc);
         s = vb * inv; t = vc * inv;
     }
     const float rx = ap.x - s * ab.x - t * ac.x;
@@ -237,6 +258,23 @@ __device__ __forceinline__ float prim_dist2(const float4* __restrict__ prims, in
     }
 }
 
+// Squared distance from q to the bounding box of leaf p.
+template <int DIM>
+__device__ __forceinline__ float prim_box_dist2(const float4* __restrict__ prims, int p, const float* q) {
+    float lo[DIM], hi[DIM];
+    if (DIM == 2) {
+        const float4 s = __ldg(prims + p);
+        lo[0] = fminf(s.x, s.z); hi[0] = fmaxf(s.x, s.z);
+        lo[1] = fminf(s.y, s.w); hi[1] = fmaxf(s.y, s.w);
+    } else {
+        const float4 a = __ldg(prims + 3 * p), b = __ldg(prims + 3 * p + 1), c = __ldg(prims + 3 * p + 2);
+        lo[0] = fminf(a.x, fminf(b.x, c.x)); hi[0] = fmaxf(a.x, fmaxf(b.x, c.x));
+        lo[1] = fminf(a.y, fminf(b.y, c.y)); hi[1] = fmaxf(a.y, fmaxf(b.y, c.y));
+        lo[DIM - 1] = fminf(a.z, fminf(b.z, c.z)); hi[DIM - 1] = fmaxf(a.z, fmaxf(b.z, c.z));
+    }
+    return box_dist2<DIM>(q, lo, hi);
+}
+
 // Closest leaf to q.  On entry best2 / best hold an upper bound and its leaf
 // (a previous hit: any element's distance bounds the minimum), or kInf / -1.
 // Near-child-first descent; on the way back up, each parent is refetched and
@@ -247,6 +285,7 @@ template <int DIM>
 __device__ __forceinline__ bool closest_leaf(const BvhView& bvh, const float* q, float& best2, int& best,
                                              unsigned& n_nodes, unsigned& n_prims) {
     for (int p = bvh.n_tree; p < bvh.n_tree + bvh.n_big; ++p) {
+        if (prim_box_dist2<DIM>(bvh.prims, p, q) >= best2) continue;   // cannot be closer
         ++n_prims;
         const float dd = prim_dist2<DIM>(bvh.prims, p, q);
         if (dd < best2) { best2 = dd; best = p; }

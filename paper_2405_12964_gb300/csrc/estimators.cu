@@ -115,6 +115,19 @@ __global__ void reduce_udot_kernel(const dwos_record* __restrict__ rec, const in
 // distinct vertex and value, so vertices that many walks reach (an enclosing
 // box, a coarse mesh) cost one global atomic per block instead of one per walk.
 constexpr int kSlots = 1024;
+
+// Position of the n-th (0-based) set bit of m, or -1.
+__device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
+    if (n >= __popc(m)) return -1;
+    int pos = 0;
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1) {
+        const int c = __popc(m & ((1u << w) - 1u));
+        if (n >= c) { n -= c; m >>= w; pos += w; }
+    }
+    return pos;
+}
+
 constexpr int kProbes = 8;
 
 template <int DIM>
@@ -153,16 +166,33 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
             const double ur = valid ? (double)cot_or_uref[p] : 0.0;
             wt = ((S - (double)r.u) / ((double)B * (B - 1)) - ur / B) / (double)(W / B);
         }
-        if (!(valid && r.elem >= 0)) continue;
+        const bool hit = valid && r.elem >= 0;
         const float wv[3] = {1.0f - r.b1 - r.b2, r.b1, r.b2};
+        const int lane = threadIdx.x & 31;
 #pragma unroll
         for (int sidx = 0; sidx < DIM; ++sidx) {
-            const int vid = __ldg(elem + DIM * r.elem + sidx);
-            const double ws = wt * (double)wv[sidx];
+            const int vid = hit ? __ldg(elem + DIM * r.elem + sidx) : -1;
+            const double ws = hit ? wt * (double)wv[sidx] : 0.0;
             double val[DIM + 1];
 #pragma unroll
             for (int k = 0; k < DIM; ++k) val[k] = ws * (double)r.c[k];
             val[DIM] = ws;
+            // sum over the lanes that hold the same vertex: a log-step tree over
+            // each peer group (lane of rank j adds the partial sum of rank j + off)
+            const unsigned peers = __match_any_sync(kFull, vid);
+            if (__any_sync(kFull, __popc(peers) > 1)) {
+                const int rank = __popc(peers & ((1u << lane) - 1u));
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int src = nth_set_bit(peers, rank + off);
+                    const bool has = src >= 0;
+#pragma unroll
+                    for (int k = 0; k <= DIM; ++k) {
+                        const double t = __shfl_sync(kFull, val[k], has ? src : lane);
+                        if (has) val[k] += t;
+                    }
+                }
+            }
+            if (vid < 0 || lane != __ffs(peers) - 1) continue;
             unsigned h = ((unsigned)vid * 2654435761u) >> 22;   // 10-bit hash
             bool done = false;
             for (int probe = 0; probe < kProbes && !done; ++probe) {

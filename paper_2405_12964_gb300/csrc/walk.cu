@@ -183,8 +183,7 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevPr
                 acc = fmaf(source_weight<DIM>(P.sqrt_sigma, d, u01(r1.z)), P.f, acc);
             }
             const U4 r0 = draw_block(P.seed_lo, P.seed_hi, wid, k_step, (uint32_t)phase, 0u);
-            const float alpha = recursive_weight<DIM>(P.sqrt_sigma, d);
-            if (alpha < u01(r0.z)) {
+            if (roulette_stops<DIM>(P.sqrt_sigma, d, u01(r0.z))) {
                 kind = DWOS_KIND_ROULETTE;
             } else {   // next point on the sphere of radius d
                 if (DIM == 2) {
