@@ -225,6 +225,37 @@ dwos_status dwos_inside(dwos_ctx* ctx, int n, const float* p, int32_t* inside, i
 dwos_status dwos_philox4x32_10(dwos_ctx* ctx, int n, const uint32_t* ctr, const uint32_t* key,
                                uint32_t* out, int mem);
 
+/* ---- allocation-free evaluation ------------------------------------------
+ * The paper has no counterpart to this entry point.  It is dwos_eval for
+ * callers that cannot allocate device memory during the call: code under a
+ * stream capture in global mode, where cudaMalloc is not permitted; hosts
+ * whose device memory belongs to another allocator or a fixed budget; loops
+ * that cannot afford cudaMalloc's implicit device synchronisation.
+ *
+ * It runs the same kernels as dwos_eval (inside test if enabled, walks with
+ * walk id p * W + w, per-point reductions) but keeps all scratch in one fixed
+ * array compiled into the library: about 9.4 MB on every GPU that loads the
+ * library, held until the process exits.  It never calls cudaMalloc or
+ * cudaFree.  Limits and rules:
+ *  - n_query * walks_per_point <= DWOS_STATIC_MAX_WALKS, else
+ *    DWOS_ERR_INVALID_ARG with a message saying so;
+ *  - xq (n_query x dim) and every output are device pointers on the context's
+ *    device (outputs as in dwos_eval; du_mean / du_se may be NULL);
+ *  - the boundary, data and options must already be set on the context (those
+ *    calls do allocate);
+ *  - the first call on a device looks up the array's device address (once per
+ *    device); make that first call before any stream capture;
+ *  - all calls, from every context in the process, share the one array, which
+ *    keeps the previous call's contents (the counters are cleared by each
+ *    call): calls whose work overlaps on the GPU race and must be ordered by
+ *    the caller, e.g. by issuing them on one stream;
+ *  - the work is asynchronous on the context's stream; device-side errors are
+ *    not reported (the counters live in the shared array); dwos_last_stats
+ *    does not describe these calls. */
+#define DWOS_STATIC_MAX_WALKS 262144
+dwos_status dwos_eval_static(dwos_ctx* ctx, int n_query, const float* xq, int walks_per_point,
+                             double* u_mean, double* u_se, double* du_mean, double* du_se);
+
 #ifdef __cplusplus
 }
 #endif

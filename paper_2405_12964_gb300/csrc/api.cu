@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -625,3 +626,122 @@ dwos_status dwos_philox4x32_10(dwos_ctx* ctx, int n, const uint32_t* ctr, const 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free evaluation.
+//
+// Some callers cannot allocate device memory while they call us: code running
+// under a stream capture in global mode (where cudaMalloc is not permitted),
+// hosts whose memory is owned by another allocator (a framework's caching
+// pool, a fixed device budget), or latency-sensitive loops where the implicit
+// device synchronisation of cudaMalloc is unacceptable.  dwos_eval_static
+// serves them: it runs the same walk, inside-test and reduction kernels as
+// dwos_eval, but every byte of scratch (problem descriptor, counters, inside
+// flags, per-walk records) lives in the fixed array below, so the call itself
+// allocates nothing.  The context's boundary and BVH must already be set up.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kStaticHeader = 4096;     // problem descriptor + counters
+constexpr size_t kStaticFlags = (size_t)DWOS_STATIC_MAX_WALKS * sizeof(int);
+constexpr size_t kStaticBytes = kStaticHeader + kStaticFlags + (size_t)DWOS_STATIC_MAX_WALKS * sizeof(dwos_record);
+static_assert(sizeof(DevProblem) + sizeof(DevCounters) <= kStaticHeader, "static header too small");
+
+// Held by every GPU that loads the library, until the process exits.
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+std::mutex g_static_mutex;
+void* g_static_addr[64] = {nullptr};
+
+// Device address of the scratch array on ctx's device (looked up once per
+// device, with that device current; the host-side symbol is not an address).
+dwos_status static_scratch(dwos_ctx* ctx, unsigned char** out) {
+    if (ctx->device < 0 || ctx->device >= 64) return fail(ctx, DWOS_ERR_INVALID_ARG, "device index too large");
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_addr[ctx->device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(ctx, e != cudaSuccess ? e : cudaErrorInvalidSymbol,
+                                                     "cudaGetSymbolAddress(static scratch)");
+        g_static_addr[ctx->device] = p;
+    }
+    *out = static_cast<unsigned char*>(g_static_addr[ctx->device]);
+    return DWOS_OK;
+}
+
+}  // namespace
+
+extern "C" dwos_status dwos_eval_static(dwos_ctx* ctx, int n_query, const float* xq, int W, double* u_mean,
+                                        double* u_se, double* du_mean, double* du_se) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (!ctx->have_boundary) return fail(ctx, DWOS_ERR_STATE, "no boundary: call dwos_set_boundary first");
+    if (n_query < 0 || W < 1) return fail(ctx, DWOS_ERR_INVALID_ARG, "n_query must be >= 0 and walks_per_point >= 1");
+    const unsigned long long total = (unsigned long long)n_query * (unsigned long long)W;
+    if (total > (unsigned long long)DWOS_STATIC_MAX_WALKS)
+        return fail(ctx, DWOS_ERR_INVALID_ARG,
+                    "n_query * walks_per_point exceeds DWOS_STATIC_MAX_WALKS (262144) for dwos_eval_static");
+    if (n_query == 0) return DWOS_OK;
+    if (!xq || !u_mean) return fail(ctx, DWOS_ERR_INVALID_ARG, "xq and u_mean must be device pointers");
+    if (du_mean && ctx->n_param == 0) return fail(ctx, DWOS_ERR_INVALID_ARG, "derivatives requested but n_param = 0");
+    for (const void* p : {(const void*)xq, (const void*)u_mean, (const void*)u_se, (const void*)du_mean,
+                          (const void*)du_se})
+        if (dwos_status s = check_device_ptr(ctx, p, "argument")) return s;
+    if (dwos_status s = set_device(ctx)) return s;
+    unsigned char* base = nullptr;
+    if (dwos_status s = static_scratch(ctx, &base)) return s;
+    DevProblem* d_prob = reinterpret_cast<DevProblem*>(base);
+    DevCounters* d_ctr = reinterpret_cast<DevCounters*>(base + 2048);
+    int* d_valid = reinterpret_cast<int*>(base + kStaticHeader);
+    dwos_record* d_rec = reinterpret_cast<dwos_record*>(base + kStaticHeader + kStaticFlags);
+    const int diff = du_mean ? 1 : 0;
+    const int* valid = nullptr;
+    if (ctx->opt.check_inside) {
+        CK(launch_inside(ctx->bvh, n_query, xq, d_valid, ctx->stream), "inside test");
+        valid = d_valid;
+    }
+    DevProblem P;
+    std::memset(&P, 0, sizeof(P));
+    P.nodes = ctx->bvh.nodes;
+    P.prims = ctx->bvh.prims;
+    P.prim_elem = ctx->bvh.prim_elem;
+    P.elem = ctx->elem;
+    P.g_vert = ctx->g_vert;
+    P.root = 0;
+    P.n_internal = ctx->bvh.n_internal;
+    P.n_tree = ctx->bvh.n_tree;
+    P.n_big = ctx->bvh.n_big;
+    P.data_kind = ctx->data_kind;
+    P.differential = diff;
+    for (int i = 0; i < 10; ++i) P.field[i] = (float)ctx->field[i];
+    P.sqrt_sigma = std::sqrt(ctx->sigma);
+    P.f = ctx->f;
+    P.eps = ctx->opt.eps;
+    P.h = ctx->opt.h;
+    P.inv_h = 1.0f / ctx->opt.h;
+    P.K = ctx->opt.K;
+    P.max_steps = ctx->opt.max_steps;
+    P.seed_lo = (uint32_t)ctx->opt.seed;
+    P.seed_hi = (uint32_t)(ctx->opt.seed >> 32);
+    P.xq = xq;
+    P.valid = valid;
+    P.walks = W;
+    P.walk_id_base = 0;
+    P.work_begin = 0;
+    P.work_end = total;
+    P.rec = d_rec;
+    CK(cudaMemcpyAsync(d_prob, &P, sizeof(P), cudaMemcpyHostToDevice, ctx->stream), "copy problem");
+    // the array keeps the previous call's contents: the work counter and statistics start at zero
+    CK(cudaMemsetAsync(d_ctr, 0, sizeof(DevCounters), ctx->stream), "reset counters");
+    WalkLaunch L;
+    L.dim = ctx->dim;
+    L.block_size = ctx->opt.block_size > 0 ? ctx->opt.block_size : 256;
+    L.blocks_per_sm = ctx->opt.blocks_per_sm;
+    L.n_sm = ctx->n_sm;
+    int blocks = 0;
+    CK(launch_walks(L, d_prob, 1, total, d_ctr, ctx->stream, &blocks), "walk kernel");
+    CK(launch_reduce_u(d_rec, n_query, W, u_mean, u_se, ctx->stream), "reduce u");
+    if (diff)
+        CK(launch_reduce_udot(d_rec, ctx->elem, ctx->jac, ctx->dg_vert, ctx->dim, ctx->n_param, n_query, W, du_mean,
+                              du_se, ctx->stream), "reduce udot");
+    return DWOS_OK;
+}

@@ -71,6 +71,7 @@ _SIGS = {
     "dwos_closest_point": [_vp, _i, _vp, _vp, _vp, _vp, _i],
     "dwos_inside": [_vp, _i, _vp, _vp, _i],
     "dwos_philox4x32_10": [_vp, _i, _vp, _vp, _vp, _i],
+    "dwos_eval_static": [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp],
 }
 
 
