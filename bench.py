@@ -32,9 +32,28 @@ if ROOT not in sys.path:
 
 METRIC = "walk-steps/s and dU/dtheta gradient-RMSE x seconds vs plain GPU WoS at 1 GB300"
 UNIT = "walk-steps/s"
-WORKLOAD = ("2D shape-from-diffusion: box [-1,1]^2 (g=0) + 4096-segment star emitter (g=1), "
-            "sigma=10, 64 Fourier shape params, 256 points x 4096 differential walks, K=2 nested, "
-            "L2-loss gradient with U-statistics (B=8)")
+WORKLOADS = {
+    "c2": ("2D shape-from-diffusion: box [-1,1]^2 (g=0) + 4096-segment star emitter (g=1), "
+           "sigma=10, 64 Fourier shape params, 256 points x 4096 differential walks, K=2 nested, "
+           "L2-loss gradient with U-statistics (B=8)"),
+    "c3": ("3D thermal design: 200k-triangle SH-perturbed icosphere (81 SH coefficients, g=1) in box "
+           "[-2,2]^3 (g=0), sigma=1, source 0.5, 4096 points x 2048 differential walks, K=2 nested, "
+           "gradient of 1/2 sum u^2 with U-statistics (B=8)"),
+}
+WORKLOAD = WORKLOADS["c2"]
+
+
+def make_scene(name: str, walks: int = 0):
+    from paper_2405_12964_gb300 import scenes
+    import numpy as np
+    if name == "c3":
+        sc = scenes.sh_sphere_scene()
+        sc.u_ref = np.zeros(sc.query.shape[0])
+    else:
+        sc = scenes.star_box_scene()
+    if walks:
+        sc.walks = walks
+    return sc
 
 
 def peaks():
@@ -110,22 +129,26 @@ def aggregate_ranks(t_local: float, steps_local: float, dist=None, device=None):
 
 def cpu_baseline(sc, budget_s: float = 15.0):
     """The FP64 oracle (brute-force closest point) on a bounded sample of the
-    same workload: every observation point, a few differential walks each."""
+    same workload: a subset of the points (every point if affordable), as many
+    differential walks each as fit the time budget on all host cores."""
     import numpy as np
     import oracle
     pr = oracle.Problem(vert=sc.vert, elem=sc.elem, jac=sc.jac, data_kind="mapped", g_vert=sc.g_vert,
                         sigma=sc.sigma, f=sc.f, eps=sc.eps, h=sc.h, K=sc.K, seed=sc.seed)
+    n_cal = min(sc.query.shape[0], 2 * oracle.num_threads())
     t0 = time.perf_counter()
-    o = oracle.run_walks(pr, sc.query, 1, differential=True)
-    t1 = time.perf_counter() - t0
-    W = max(1, min(4096, int(budget_s / max(t1, 1e-3))))
+    oracle.run_walks(pr, sc.query[:n_cal], 1, differential=True, walk_id_base=1 << 42)
+    per_walk = (time.perf_counter() - t0) / n_cal
+    total = max(n_cal, int(budget_s / max(per_walk, 1e-9)))
+    n_pts = min(sc.query.shape[0], total)
+    W = max(1, min(4096, total // n_pts))
     t0 = time.perf_counter()
-    o = oracle.run_walks(pr, sc.query, W, differential=True, walk_id_base=1 << 41)
+    o = oracle.run_walks(pr, sc.query[:n_pts], W, differential=True, walk_id_base=1 << 41)
     dt = time.perf_counter() - t0
     steps = int(np.clip(o["steps"], 0, None).sum())
     return {"value": steps / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{sc.query.shape[0]} points x {W} differential walks (K={sc.K}) of the same "
-                      f"workload, FP64 brute-force closest point, {dt:.1f} s, {steps} walk-steps"}
+            "sample": f"{n_pts} points x {W} differential walks (K={sc.K}) of the same workload, "
+                      f"FP64 brute-force closest point, {dt:.1f} s, {steps} walk-steps"}
 
 
 def run_reference(args):
@@ -136,7 +159,7 @@ def run_reference(args):
     from paper_2405_12964_gb300 import scenes
     import oracle
     oracle.build()
-    sc = scenes.star_box_scene()
+    sc = make_scene(args.workload)
     times, steps_total = [], 0
     for i in range(args.warmup + args.steps):
         cb = cpu_baseline(sc, budget_s=6.0)
@@ -146,7 +169,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "note": "oracle on host cores, bounded sample per step"},
+            "config": {"workload": WORKLOADS[args.workload], "note": "oracle on host cores, bounded sample per step"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": times[0]["cores"], "kind": "oracle",
                              "sample": times[0]["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -159,7 +182,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dwos")
-    ap.add_argument("--walks", type=int, default=4096)
+    ap.add_argument("--walks", type=int, default=0, help="walks per point (0: the workload's)")
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -180,11 +204,10 @@ def main():
 
     from paper_2405_12964_gb300 import build
     build.build()
-    from paper_2405_12964_gb300 import scenes
     from paper_2405_12964_gb300.dwos import Solver, lib, MEM_HOST
     import ctypes
 
-    sc = scenes.star_box_scene(walks=args.walks)
+    sc = make_scene(args.workload, args.walks)
     s = Solver(local)
     s.load_scene(sc)
     n_pts, W = sc.query.shape[0], sc.walks
@@ -250,7 +273,7 @@ def main():
 
     # roofline of the walk kernel: algorithmic bytes = BVH node fetches x 48 B
     # + element tests x 16 B + one 32 B record per walk + 8 B query load per walk
-    node_b, prim_b = 48, 16
+    node_b, prim_b = (48, 16) if sc.dim == 2 else (64, 48)
     alg_bytes = nodes * node_b + prims * prim_b + args.steps * total * (32 + 8)
     walk_s = sum(kernel_ms) / 1e3
     achieved = alg_bytes / walk_s / 1e9 / args.steps * args.steps
@@ -292,7 +315,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "points": n_pts, "walks_per_point": W, "K": sc.K, "B": sc.B,
+            "config": {"workload": WORKLOADS[args.workload], "points": n_pts, "walks_per_point": W, "K": sc.K, "B": sc.B,
                        "n_param": sc.n_param, "eps": sc.eps, "h": sc.h,
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": f"replicas x{world} (independent walk ranges, no collective)"},
@@ -301,7 +324,7 @@ def main():
             "walk_steps_per_step": steps_done / args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": None,
-                         "kernel": "walk_kernel<2>", "peak_source": src,
+                         "kernel": f"walk_kernel<{sc.dim}>", "peak_source": src,
                          "bytes_per_walk_step": alg_bytes / max(steps_done, 1),
                          "walk_kernel_ms": walk_s * 1e3 / args.steps},
             "cpu_baseline": cpu, "e2e": e2e,

@@ -64,6 +64,17 @@ class Scene:
     def n_param(self) -> int:
         return 0 if self.jac is None else int(self.jac.shape[2])
 
+    @property
+    def theta0(self) -> np.ndarray:
+        """Parameter vector at which `vert` is given (vertices are linear in theta)."""
+        return np.asarray(self.meta.get("theta0", np.zeros(self.n_param)), dtype=np.float64)
+
+    def reference_vertices(self) -> np.ndarray:
+        """v_ref with vert = v_ref + jac @ theta0, so v(theta) = v_ref + jac theta."""
+        if self.jac is None:
+            return self.vert.copy()
+        return self.vert - np.einsum("vkp,p->vk", self.jac, self.theta0)
+
 
 def _field(c0=0.0, c=(0.0, 0.0, 0.0), A=(0.0, 0.0, 0.0, 0.0, 0.0, 0.0)) -> np.ndarray:
     return np.array([c0, *c, *A], dtype=np.float64)
@@ -121,7 +132,7 @@ def disk_scene(variant: str = "laplace_x", n_seg: int = 128, R: float = 1.0, n_m
     else:
         raise ValueError(variant)
     sc.eps, sc.h, sc.K, sc.query, sc.walks = eps, h, K, q, walks
-    sc.meta = {"R": R, "t": t, "n_modes": n_modes}
+    sc.meta = {"R": R, "t": t, "n_modes": n_modes, "theta0": np.concatenate([[R], np.zeros(2 * n_modes)])}
     return sc
 
 
@@ -182,7 +193,7 @@ def star_box_scene(n_seg: int = 4096, n_modes: int = 32, coef_std: float = 0.02,
     eps = 1e-3 * 2.0
     sc = Scene("star_box", vert, elem, jac, data="mapped", g_vert=g, sigma=sigma, eps=eps, h=10 * eps,
                K=K, query=q, walks=walks, u_ref=u_ref)
-    sc.meta = {"t": t, "coeffs": coeffs, "base_r": base_r}
+    sc.meta = {"t": t, "coeffs": coeffs, "base_r": base_r, "theta0": np.asarray(coeffs, dtype=np.float64)}
     return sc
 
 
@@ -303,7 +314,8 @@ def sh_sphere_scene(freq: int = 100, lmax: int = 8, coef_std: float = 0.01, sigm
         eps = 1e-3 * 2 * box_half
     sc = Scene("sh_sphere_box", vert, elem, jac, data="mapped", g_vert=g, sigma=sigma, f=f, eps=eps,
                h=10 * eps, K=K, query=q, walks=walks)
-    sc.meta = {"coeffs": coeffs, "lmax": lmax, "freq": freq, "dirs": dirs}
+    sc.meta = {"coeffs": coeffs, "lmax": lmax, "freq": freq, "dirs": dirs,
+               "theta0": np.asarray(coeffs, dtype=np.float64)}
     return sc
 
 
@@ -321,5 +333,5 @@ def ball_scene(freq: int = 16, R: float = 1.0, sigma: float = 1.0, f: float = 0.
     q = d * r[:, None]
     sc = Scene("ball", vert, faces, jac, data="mapped", g_vert=np.full(vert.shape[0], g), sigma=sigma,
                f=f, eps=eps, h=h, K=K, query=q, walks=walks)
-    sc.meta = {"R": R}
+    sc.meta = {"R": R, "theta0": np.array([R])}
     return sc
