@@ -77,8 +77,9 @@ typedef struct {
     int check_inside;   /* 1: reject query points outside Omega (ray parity) */
     int block_size;     /* walk-kernel threads per block; 0 = library default */
     int blocks_per_sm;  /* resident walk blocks per SM; 0 = occupancy maximum */
-    int smem_nodes;     /* BVH nodes (breadth-first prefix) staged in shared
-                           memory by each walk block; 0 = none */
+    int traversal;      /* distance-query search order: 0 = from the root, bounded by
+                           the previous step's element; 1 = climbing from that
+                           element's leaf with the Morton-cell stop test */
 } dwos_options;
 
 /* Per-walk record of a differential walk (32 bytes).  For a walk that reaches
@@ -136,7 +137,7 @@ const char* dwos_last_error(const dwos_ctx* ctx);
 dwos_status dwos_sync(dwos_ctx* ctx);
 
 /* Fill *opt with the defaults: eps 1e-3, h 1e-2, K 1, B 8, max_steps 16384,
- * seed 0x12964, check_inside 1, automatic launch shape, no shared staging. */
+ * seed 0x12964, check_inside 1, automatic launch shape, traversal 0. */
 void dwos_default_options(dwos_options* opt);
 /* Validate and store options (eps > 0, h > 0, K >= 1, B in {2,4,8,16,32},
  * 1 <= max_steps < 2^24). */
@@ -217,6 +218,12 @@ dwos_status dwos_last_stats(dwos_ctx* ctx, dwos_run_stats* out);
  * elem (n, input numbering), bary (n x 2, weights of vertices 1 and 2). */
 dwos_status dwos_closest_point(dwos_ctx* ctx, int n, const float* p, float* dist, int32_t* elem,
                                float* bary, int mem);
+/* The same query seeded, as a walk step is, with a known element: hint_elem
+ * (n, input numbering; -1 = no hint) bounds the distance before the search,
+ * which then climbs the BVH from that element's leaf.  Results equal
+ * dwos_closest_point's for any hints (the hint only changes the work done). */
+dwos_status dwos_closest_point_hint(dwos_ctx* ctx, int n, const float* p, const int32_t* hint_elem, float* dist,
+                                    int32_t* elem, float* bary, int mem);
 /* 1 if the point lies inside the region the boundary encloses (odd number of
  * ray crossings), else 0. */
 dwos_status dwos_inside(dwos_ctx* ctx, int n, const float* p, int32_t* inside, int mem);

@@ -165,6 +165,10 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     P.n_internal = ctx->bvh.n_internal;
     P.n_tree = ctx->bvh.n_tree;
     P.n_big = ctx->bvh.n_big;
+    P.leaf_parent = ctx->bvh.leaf_parent;
+    P.node_cell = ctx->bvh.node_cell;
+    P.r_max = ctx->bvh.r_max;
+    P.traversal = ctx->opt.traversal;
     P.data_kind = ctx->data_kind;
     P.differential = differential;
     for (int i = 0; i < 10; ++i) P.field[i] = (float)ctx->field[i];
@@ -228,7 +232,7 @@ void dwos_default_options(dwos_options* o) {
     o->check_inside = 1;
     o->block_size = 0;
     o->blocks_per_sm = 0;
-    o->smem_nodes = 0;
+    o->traversal = 0;
 }
 
 dwos_status dwos_create(dwos_ctx** out, int device) {
@@ -302,7 +306,7 @@ dwos_status dwos_set_options(dwos_ctx* ctx, const dwos_options* o) {
     if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 256 || o->block_size % 32))
         return fail(ctx, DWOS_ERR_INVALID_ARG, "block_size must be 0 or a multiple of 32 in [32, 256]");
     if (o->blocks_per_sm < 0 || o->blocks_per_sm > 64) return fail(ctx, DWOS_ERR_INVALID_ARG, "blocks_per_sm must be in [0, 64]");
-    if (o->smem_nodes < 0) return fail(ctx, DWOS_ERR_INVALID_ARG, "smem_nodes must be >= 0");
+    if (o->traversal < 0 || o->traversal > 1) return fail(ctx, DWOS_ERR_INVALID_ARG, "traversal must be 0 or 1");
     ctx->opt = *o;
     return DWOS_OK;
 }
@@ -564,21 +568,29 @@ dwos_status dwos_last_stats(dwos_ctx* ctx, dwos_run_stats* out) {
     return DWOS_OK;
 }
 
-dwos_status dwos_closest_point(dwos_ctx* ctx, int n, const float* p, float* dist, int32_t* elem_out, float* bary,
-                               int mem) {
+static dwos_status closest_common(dwos_ctx* ctx, int n, const float* p, const int32_t* hint, float* dist,
+                                  int32_t* elem_out, float* bary, int mem) {
     if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
     if (dwos_status s = check_mem(ctx, mem)) return s;
     if (!ctx->have_boundary) return fail(ctx, DWOS_ERR_STATE, "no boundary");
     if (n < 0 || (n > 0 && (!p || !dist || !elem_out || !bary))) return fail(ctx, DWOS_ERR_INVALID_ARG, "bad arguments");
+    if (mem == DWOS_MEM_HOST && hint)
+        for (int i = 0; i < n; ++i)
+            if (hint[i] >= ctx->n_elem) return fail(ctx, DWOS_ERR_INVALID_ARG, "hint element out of range");
     if (dwos_status s = set_device(ctx)) return s;
     CK(grow(ctx->misc_f, ctx->misc_f_cap, (size_t)n * (ctx->dim + 3)), "alloc");
-    CK(grow(ctx->misc_i, ctx->misc_i_cap, (size_t)std::max(n, 1)), "alloc");
+    CK(grow(ctx->misc_i, ctx->misc_i_cap, 2 * (size_t)std::max(n, 1)), "alloc");
     float* dp = ctx->misc_f;
     float* dd = dp + (size_t)n * ctx->dim;
     float* db = dd + n;
+    int* dh = nullptr;
     CK(to_device(ctx, dp, p, (size_t)n * ctx->dim, mem), "copy points");
+    if (hint) { dh = ctx->misc_i + std::max(n, 1); CK(to_device(ctx, dh, hint, (size_t)n, mem), "copy hints"); }
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream), "reset");
-    CK(launch_closest(ctx->bvh, n, dp, dd, ctx->misc_i, db, ctx->d_err, ctx->stream), "closest point");
+    CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->stream), "reset counters");
+    CK(launch_closest(ctx->bvh, n, dp, dh, dd, ctx->misc_i, db, ctx->d_err, ctx->d_ctr, ctx->opt.traversal,
+                      ctx->stream), "closest point");
+    ctx->launches += n > 0 ? 1 : 0;
     CK(from_device(ctx, dist, dd, n, mem), "copy");
     CK(from_device(ctx, elem_out, ctx->misc_i, n, mem), "copy");
     CK(from_device(ctx, bary, db, 2 * (size_t)n, mem), "copy");
@@ -589,6 +601,17 @@ dwos_status dwos_closest_point(dwos_ctx* ctx, int n, const float* p, float* dist
         if (err) return fail(ctx, DWOS_ERR_STEP_LIMIT, "BVH traversal exceeded its iteration bound");
     }
     return DWOS_OK;
+}
+
+dwos_status dwos_closest_point(dwos_ctx* ctx, int n, const float* p, float* dist, int32_t* elem_out, float* bary,
+                               int mem) {
+    return closest_common(ctx, n, p, nullptr, dist, elem_out, bary, mem);
+}
+
+dwos_status dwos_closest_point_hint(dwos_ctx* ctx, int n, const float* p, const int32_t* hint_elem, float* dist,
+                                    int32_t* elem_out, float* bary, int mem) {
+    if (!hint_elem && n > 0) return fail(ctx, DWOS_ERR_INVALID_ARG, "hint_elem is NULL");
+    return closest_common(ctx, n, p, hint_elem, dist, elem_out, bary, mem);
 }
 
 dwos_status dwos_inside(dwos_ctx* ctx, int n, const float* p, int32_t* inside, int mem) {
@@ -710,6 +733,10 @@ extern "C" dwos_status dwos_eval_static(dwos_ctx* ctx, int n_query, const float*
     P.n_internal = ctx->bvh.n_internal;
     P.n_tree = ctx->bvh.n_tree;
     P.n_big = ctx->bvh.n_big;
+    P.leaf_parent = ctx->bvh.leaf_parent;
+    P.node_cell = ctx->bvh.node_cell;
+    P.r_max = ctx->bvh.r_max;
+    P.traversal = ctx->opt.traversal;
     P.data_kind = ctx->data_kind;
     P.differential = diff;
     for (int i = 0; i < 10; ++i) P.field[i] = (float)ctx->field[i];

@@ -6,6 +6,8 @@
 // Plus the batched closest-point, ray-parity inside test and Philox kernels.
 #include <cub/device/device_radix_sort.cuh>
 
+#include <cstring>
+
 #include "dwos_device.cuh"
 #include "dwos_internal.h"
 
@@ -60,14 +62,30 @@ __global__ void size_kernel(const float* vert, const int* elem, int n, float* st
 // Elements whose box diagonal exceeds kBigFactor x the mean: count (stats[1]).
 constexpr float kBigFactor = 16.0f;
 
+// Also the largest half box diagonal over the elements that stay in the tree
+// (stats_i[1]) and over all elements (stats_i[2]), as float bits.
 template <int DIM>
 __global__ void count_big_kernel(const float* vert, const int* elem, int n, float* stats, int* count) {
     const float thr = kBigFactor * stats[0] / (float)n;
     int c = 0;
-    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
-        c += elem_diag<DIM>(vert, elem, e) > thr ? 1 : 0;
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, c);
+    float r_small = 0.0f, r_all = 0.0f;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+        const float dgn = elem_diag<DIM>(vert, elem, e);
+        const bool big = dgn > thr;
+        c += big ? 1 : 0;
+        r_all = fmaxf(r_all, 0.5f * dgn);
+        if (!big) r_small = fmaxf(r_small, 0.5f * dgn);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        r_small = fmaxf(r_small, __shfl_xor_sync(0xffffffffu, r_small, o));
+        r_all = fmaxf(r_all, __shfl_xor_sync(0xffffffffu, r_all, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (c) atomicAdd(count, c);
+        atomicMax(count + 1, __float_as_int(r_small));   // non-negative floats order as ints
+        atomicMax(count + 2, __float_as_int(r_all));
+    }
 }
 
 // Scene bounds of the tree elements' centroids (ordered-uint encoding).
@@ -163,8 +181,36 @@ __device__ __forceinline__ int delta(const unsigned int* k, int n, int i, int j)
     return __clz(a ^ b);
 }
 
+// Box of centroids admitted by a Morton prefix: the top p bits of the 30-bit
+// code fix the top bits of each axis; q = floor(t * levels + 0.5) lies in
+// [q_lo, q_hi] iff t lies in [(q_lo - 0.5)/levels, (q_hi + 0.5)/levels).
+template <int DIM>
+__device__ void morton_cell(unsigned int key, int p, const unsigned int* bounds, float* cell) {
+    const int B = DIM == 2 ? 15 : 10;
+    const float levels = DIM == 2 ? 32767.0f : 1023.0f;
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+        int n_a = 0;
+        for (int b = 29; b >= 30 - p; --b) n_a += (b % DIM == a) ? 1 : 0;
+        unsigned int q = 0;
+        for (int k = 0; k < B; ++k) q |= ((key >> (DIM * k + a)) & 1u) << k;
+        const unsigned int q_lo = n_a > 0 ? ((q >> (B - n_a)) << (B - n_a)) : 0u;
+        const unsigned int q_hi = q_lo + (1u << (B - n_a)) - 1u;
+        const float lo = ordered_to_float(bounds[a]);
+        const float ext = ordered_to_float(bounds[DIM + a]) - lo;
+        if (!(ext > 0.0f)) {              // flat axis: the code does not separate along it
+            cell[a] = -kInf;
+            cell[DIM + a] = kInf;
+            continue;
+        }
+        cell[a] = lo + (((float)q_lo - 0.5f) / levels) * ext;
+        cell[DIM + a] = lo + (((float)q_hi + 0.5f) / levels) * ext;
+    }
+}
+
+template <int DIM>
 __global__ void radix_tree_kernel(const unsigned int* keys, int n, int* node_child, int* node_parent,
-                                  int* leaf_parent) {
+                                  int* leaf_parent, const unsigned int* bounds, float* node_cell) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
     const int dir = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
@@ -191,6 +237,9 @@ __global__ void radix_tree_kernel(const unsigned int* keys, int n, int* node_chi
     node_child[2 * i] = left;
     node_child[2 * i + 1] = right;
     if (i == 0) node_parent[0] = -1;
+    // keys of this node's range share dnode leading bits (>= 32: all equal)
+    const int p = dnode >= 32 ? 30 : dnode - 2;
+    morton_cell<DIM>(keys[i], p, bounds, node_cell + 2 * DIM * i);
 }
 
 template <int DIM>
@@ -240,7 +289,7 @@ __global__ void refit_kernel(const float* vert, const int* elem, const int* sort
 template <int DIM>
 __global__ void finalize_kernel(const float* vert, const int* elem, const int* sorted_elem, int n,
                                 const int* node_child, const int* node_parent, int n_internal,
-                                float4* nodes, float4* prims, int* prim_elem) {
+                                float4* nodes, float4* prims, int* prim_elem, int* leaf_of_elem) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n_internal && node_child) {
         float4* m = nodes + BvhLayout<DIM>::kNodeF4 * i + (BvhLayout<DIM>::kNodeF4 - 1);
@@ -250,6 +299,7 @@ __global__ void finalize_kernel(const float* vert, const int* elem, const int* s
     if (i < n) {
         const int e = sorted_elem[i];
         prim_elem[i] = e;
+        leaf_of_elem[e] = i;
         if (DIM == 2) {
             const int a = elem[2 * e], b = elem[2 * e + 1];
             prims[i] = make_float4(vert[2 * a], vert[2 * a + 1], vert[2 * b], vert[2 * b + 1]);
@@ -265,7 +315,11 @@ __global__ void finalize_kernel(const float* vert, const int* elem, const int* s
 
 // One tree element: a single node whose right child is empty.
 template <int DIM>
-__global__ void single_leaf_kernel(const float* vert, const int* elem, const int* sorted_elem, float4* nodes) {
+__global__ void single_leaf_kernel(const float* vert, const int* elem, const int* sorted_elem, float4* nodes,
+                                   int* leaf_parent, float* node_cell) {
+    leaf_parent[0] = 0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { node_cell[k] = -kInf; node_cell[DIM + k] = kInf; }
     float lo[DIM], hi[DIM], elo[DIM], ehi[DIM];
     elem_box<DIM>(vert, elem, sorted_elem[0], lo, hi);
 #pragma unroll
@@ -278,8 +332,9 @@ __global__ void single_leaf_kernel(const float* vert, const int* elem, const int
 
 // ---- queries --------------------------------------------------------------
 template <int DIM>
-__global__ void closest_kernel(BvhView bvh, const int* prim_elem, int n, const float* p, float* dist,
-                               int* elem_out, float* bary, int* err) {
+__global__ void closest_kernel(BvhView bvh, const int* prim_elem, const int* leaf_of_elem, int n, const float* p,
+                               const int* hint_elem, float* dist, int* elem_out, float* bary, int* err,
+                               DevCounters* ctr) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float q[DIM];
@@ -287,8 +342,19 @@ __global__ void closest_kernel(BvhView bvh, const int* prim_elem, int n, const f
     for (int k = 0; k < DIM; ++k) q[k] = p[DIM * i + k];
     float best2 = kInf;
     int best = -1;
+    if (hint_elem) {   // seed with the caller's element, as a walk seeds with its previous hit
+        const int h = hint_elem[i];
+        if (h >= 0 && h < bvh.n_tree + bvh.n_big) {
+            best = leaf_of_elem[h];
+            best2 = prim_dist2<DIM>(bvh.prims, best, q);
+        }
+    }
     unsigned nn = 0, np = 0;
     if (!closest_leaf<DIM>(bvh, q, best2, best, nn, np)) atomicOr(err, 1);
+    if (ctr) {
+        atomicAdd(&ctr->nodes, (unsigned long long)nn);
+        atomicAdd(&ctr->prims, (unsigned long long)np);
+    }
     float w1 = 0.0f, w2 = 0.0f;
     if (best >= 0) {
         if (DIM == 2) {
@@ -477,6 +543,7 @@ cudaError_t bvh_reserve(BvhBuffers& b, int dim, int n_elem) {
     DW_TRY(cudaMalloc(&b.nodes, sizeof(float4) * nf4 * (size_t)n_int));
     DW_TRY(cudaMalloc(&b.prims, sizeof(float4) * pf4 * (size_t)n_elem));
     DW_TRY(cudaMalloc(&b.prim_elem, sizeof(int) * (size_t)n_elem));
+    DW_TRY(cudaMalloc(&b.leaf_of_elem, sizeof(int) * (size_t)n_elem));
     DW_TRY(cudaMalloc(&b.keys, sizeof(unsigned int) * (size_t)n_elem));
     DW_TRY(cudaMalloc(&b.keys_sorted, sizeof(unsigned int) * (size_t)n_elem));
     DW_TRY(cudaMalloc(&b.vals, sizeof(int) * (size_t)n_elem));
@@ -485,8 +552,9 @@ cudaError_t bvh_reserve(BvhBuffers& b, int dim, int n_elem) {
     DW_TRY(cudaMalloc(&b.node_parent, sizeof(int) * (size_t)n_int));
     DW_TRY(cudaMalloc(&b.node_child, sizeof(int) * 2 * (size_t)n_int));
     DW_TRY(cudaMalloc(&b.counters, sizeof(int) * (size_t)n_int));
+    DW_TRY(cudaMalloc(&b.node_cell, sizeof(float) * 2 * dim * (size_t)n_int));
     DW_TRY(cudaMalloc(&b.bounds, sizeof(unsigned int) * 6));
-    DW_TRY(cudaMalloc(&b.stats, sizeof(float) * 2 + sizeof(int) * 2));
+    DW_TRY(cudaMalloc(&b.stats, sizeof(float) * 2 + sizeof(int) * 4));
     size_t tmp = 0;
     DW_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp, b.keys, b.keys_sorted, b.vals, b.vals_sorted, n_elem));
     DW_TRY(cudaMalloc(&b.sort_tmp, tmp));
@@ -498,9 +566,9 @@ cudaError_t bvh_reserve(BvhBuffers& b, int dim, int n_elem) {
 }
 
 void bvh_free(BvhBuffers& b) {
-    cudaFree(b.nodes); cudaFree(b.prims); cudaFree(b.prim_elem); cudaFree(b.keys); cudaFree(b.keys_sorted);
+    cudaFree(b.nodes); cudaFree(b.prims); cudaFree(b.prim_elem); cudaFree(b.leaf_of_elem); cudaFree(b.keys); cudaFree(b.keys_sorted);
     cudaFree(b.vals); cudaFree(b.vals_sorted); cudaFree(b.leaf_parent); cudaFree(b.node_parent);
-    cudaFree(b.node_child); cudaFree(b.counters); cudaFree(b.bounds); cudaFree(b.stats);
+    cudaFree(b.node_child); cudaFree(b.counters); cudaFree(b.bounds); cudaFree(b.stats); cudaFree(b.node_cell);
     cudaFree(b.sort_tmp);
     b = BvhBuffers();
 }
@@ -512,18 +580,24 @@ static cudaError_t build_impl(BvhBuffers& b, const float* vert, const int* elem,
     b.n_elem = n;
     float* stats = b.stats;
     int* count = reinterpret_cast<int*>(b.stats + 2);
-    cudaError_t e = cudaMemsetAsync(b.stats, 0, sizeof(float) * 2 + sizeof(int) * 2, s);
+    cudaError_t e = cudaMemsetAsync(b.stats, 0, sizeof(float) * 2 + sizeof(int) * 4, s);
     if (e != cudaSuccess) return e;
     const int gb = min(nblk(n, 256), 1024);
     size_kernel<DIM><<<gb, 256, 0, s>>>(vert, elem, n, stats);
     count_big_kernel<DIM><<<gb, 256, 0, s>>>(vert, elem, n, stats, count);
-    int n_big = 0;
-    e = cudaMemcpyAsync(&n_big, count, sizeof(int), cudaMemcpyDeviceToHost, s);
+    int host[3] = {0, 0, 0};
+    e = cudaMemcpyAsync(host, count, sizeof(int) * 3, cudaMemcpyDeviceToHost, s);
     if (e != cudaSuccess) return e;
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return e;
+    int n_big = host[0];
     const int split = (n_big > 0 && n_big <= kMaxBig && n_big < n) ? 1 : 0;
     if (!split) n_big = 0;
+    float r_small, r_all;
+    memcpy(&r_small, &host[1], sizeof(float));
+    memcpy(&r_all, &host[2], sizeof(float));
+    // margin for the FP32 rounding of the Morton quantisation
+    b.r_max = (split ? r_small : r_all) * 1.0001f + 1e-6f;
     const int nt = n - n_big;
     b.n_big = n_big;
     b.n_tree = nt;
@@ -538,19 +612,21 @@ static cudaError_t build_impl(BvhBuffers& b, const float* vert, const int* elem,
     if (e != cudaSuccess) return e;
     if (nt >= 2) {
         b.n_internal = nt - 1;
-        radix_tree_kernel<<<nblk(nt - 1, 256), 256, 0, s>>>(b.keys_sorted, nt, b.node_child, b.node_parent,
-                                                            b.leaf_parent);
+        radix_tree_kernel<DIM><<<nblk(nt - 1, 256), 256, 0, s>>>(b.keys_sorted, nt, b.node_child, b.node_parent,
+                                                                 b.leaf_parent, b.bounds, b.node_cell);
         e = cudaMemsetAsync(b.counters, 0, sizeof(int) * (size_t)(nt - 1), s);
         if (e != cudaSuccess) return e;
         refit_kernel<DIM><<<nblk(nt, 256), 256, 0, s>>>(vert, elem, b.vals_sorted, nt, b.node_child,
                                                         b.node_parent, b.leaf_parent, b.counters, b.nodes);
         finalize_kernel<DIM><<<nblk(n, 256), 256, 0, s>>>(vert, elem, b.vals_sorted, n, b.node_child,
-                                                          b.node_parent, nt - 1, b.nodes, b.prims, b.prim_elem);
+                                                          b.node_parent, nt - 1, b.nodes, b.prims, b.prim_elem,
+                                                          b.leaf_of_elem);
     } else {
         b.n_internal = nt;    // 1: a single-leaf node; 0: no tree
-        if (nt == 1) single_leaf_kernel<DIM><<<1, 1, 0, s>>>(vert, elem, b.vals_sorted, b.nodes);
+        if (nt == 1) single_leaf_kernel<DIM><<<1, 1, 0, s>>>(vert, elem, b.vals_sorted, b.nodes, b.leaf_parent,
+                                                             b.node_cell);
         finalize_kernel<DIM><<<nblk(n, 256), 256, 0, s>>>(vert, elem, b.vals_sorted, n, nullptr, nullptr, 0,
-                                                          b.nodes, b.prims, b.prim_elem);
+                                                          b.nodes, b.prims, b.prim_elem, b.leaf_of_elem);
     }
     return cudaGetLastError();
 }
@@ -569,14 +645,20 @@ static BvhView view_of(const BvhBuffers& b) {
     v.n_internal = b.n_internal;
     v.n_tree = b.n_tree;
     v.n_big = b.n_big;
+    v.climb = 0;
+    v.leaf_parent = b.leaf_parent;
+    v.node_cell = b.node_cell;
+    v.r_max = b.r_max;
     return v;
 }
 
-cudaError_t launch_closest(const BvhBuffers& b, int n, const float* p, float* dist, int* elem_out, float* bary,
-                           int* err, cudaStream_t s) {
+cudaError_t launch_closest(const BvhBuffers& b, int n, const float* p, const int* hint_elem, float* dist,
+                           int* elem_out, float* bary, int* err, DevCounters* ctr, int traversal, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    if (b.dim == 2) closest_kernel<2><<<nblk(n, 128), 128, 0, s>>>(view_of(b), b.prim_elem, n, p, dist, elem_out, bary, err);
-    else closest_kernel<3><<<nblk(n, 128), 128, 0, s>>>(view_of(b), b.prim_elem, n, p, dist, elem_out, bary, err);
+    BvhView v = view_of(b);
+    v.climb = traversal;
+    if (b.dim == 2) closest_kernel<2><<<nblk(n, 128), 128, 0, s>>>(v, b.prim_elem, b.leaf_of_elem, n, p, hint_elem, dist, elem_out, bary, err, ctr);
+    else closest_kernel<3><<<nblk(n, 128), 128, 0, s>>>(v, b.prim_elem, b.leaf_of_elem, n, p, hint_elem, dist, elem_out, bary, err, ctr);
     return cudaGetLastError();
 }
 

@@ -200,6 +200,10 @@ template <> struct BvhLayout<3> { static constexpr int kNodeF4 = 4; static const
 // n_tree + n_big) are outsized elements (much larger than the typical one,
 // such as an enclosing box) kept out of the tree so that their boxes do not
 // inflate every ancestor's: each query tests them first, by brute force.
+// For the hint-seeded ascent: each leaf's parent, and each internal node's
+// Morton cell (the box of centroids its key prefix admits; every element
+// outside the node's subtree has its centroid outside that box) together with
+// r_max, the largest distance from an element's box centre to its corners.
 struct BvhView {
     const float4* nodes;
     const float4* prims;
@@ -207,6 +211,10 @@ struct BvhView {
     int n_internal;   // internal nodes of the tree (0: no tree)
     int n_tree;       // leaves in the tree
     int n_big;        // outsized elements after the tree's leaves
+    int climb;        // 1: climb from a tree-leaf hint; 0: always search from the root
+    const int* leaf_parent;
+    const float* node_cell;   // 2*DIM floats per internal node: lo, hi
+    float r_max;
 };
 
 template <int DIM>
@@ -275,25 +283,16 @@ __device__ __forceinline__ float prim_box_dist2(const float4* __restrict__ prims
     return box_dist2<DIM>(q, lo, hi);
 }
 
-// Closest leaf to q.  On entry best2 / best hold an upper bound and its leaf
-// (a previous hit: any element's distance bounds the minimum), or kInf / -1.
-// Near-child-first descent; on the way back up, each parent is refetched and
-// its children re-ordered by the same box distances, so no stack is needed.
-// Returns false if the iteration bound was exceeded (never in a valid tree:
-// each internal node is entered at most three times).
+// Top-down search of the subtree under internal node `start` for a leaf
+// closer than best2: near-child-first descent; on the way back up each parent
+// is refetched and its children re-ordered by the same box distances, so no
+// stack is needed.  Returns when it climbs back out of `start`.  The budget
+// bounds the node fetches (each node is entered at most three times).
 template <int DIM>
-__device__ __forceinline__ bool closest_leaf(const BvhView& bvh, const float* q, float& best2, int& best,
-                                             unsigned& n_nodes, unsigned& n_prims) {
-    for (int p = bvh.n_tree; p < bvh.n_tree + bvh.n_big; ++p) {
-        if (prim_box_dist2<DIM>(bvh.prims, p, q) >= best2) continue;   // cannot be closer
-        ++n_prims;
-        const float dd = prim_dist2<DIM>(bvh.prims, p, q);
-        if (dd < best2) { best2 = dd; best = p; }
-    }
-    if (bvh.n_internal == 0) return true;
-    int node = bvh.root;
+__device__ __forceinline__ bool search_subtree(const BvhView& bvh, int start, const float* q, float& best2, int& best,
+                                               int& budget, unsigned& n_nodes, unsigned& n_prims) {
+    int node = start;
     int from = kFromParent;
-    int budget = 3 * bvh.n_internal + 8;
     for (;;) {
         if (--budget < 0) return false;
         ++n_nodes;
@@ -324,10 +323,68 @@ __device__ __forceinline__ bool closest_leaf(const BvhView& bvh, const float* q,
             break;
         }
         if (next != kFromParent) { from = kFromParent; node = next; continue; }
-        if (parent < 0) return true;
+        if (node == start) return true;
         from = node;
         node = parent;
     }
+}
+
+// Closest leaf to q.  On entry best2 / best hold an upper bound and its leaf
+// (the previous step's closest element: any element's distance bounds the
+// minimum), or kInf / -1.  Outsized elements are tested first.  With a tree
+// leaf as hint the search climbs from that leaf: at each ancestor the sibling
+// subtree is searched if its box is within the bound, and the climb stops once
+// the ball of radius best + r_max around q lies inside the ancestor's Morton
+// cell (no element outside the ancestor's subtree can then be closer).
+// Without one it searches the whole tree from the root.  Returns false if the
+// fetch budget was exceeded (never in a valid tree).
+template <int DIM>
+__device__ __forceinline__ bool closest_leaf(const BvhView& bvh, const float* q, float& best2, int& best,
+                                             unsigned& n_nodes, unsigned& n_prims) {
+    for (int p = bvh.n_tree; p < bvh.n_tree + bvh.n_big; ++p) {
+        if (prim_box_dist2<DIM>(bvh.prims, p, q) >= best2) continue;   // cannot be closer
+        ++n_prims;
+        const float dd = prim_dist2<DIM>(bvh.prims, p, q);
+        if (dd < best2) { best2 = dd; best = p; }
+    }
+    if (bvh.n_internal == 0) return true;
+    int budget = 4 * bvh.n_internal + 64;
+    if (!bvh.climb || best < 0 || best >= bvh.n_tree || !bvh.leaf_parent)
+        return search_subtree<DIM>(bvh, bvh.root, q, best2, best, budget, n_nodes, n_prims);
+    int child = ~best;
+    int node = __ldg(bvh.leaf_parent + best);
+    while (node >= 0) {
+        if (--budget < 0) return false;
+        ++n_nodes;
+        float lo0[DIM], hi0[DIM], lo1[DIM], hi1[DIM];
+        int c0, c1, parent;
+        load_node<DIM>(bvh.nodes, node, lo0, hi0, lo1, hi1, c0, c1, parent);
+        const bool from0 = (c0 == child);
+        const int sib = from0 ? c1 : c0;
+        if (sib != kEmptyChild) {
+            const float ds = from0 ? box_dist2<DIM>(q, lo1, hi1) : box_dist2<DIM>(q, lo0, hi0);
+            if (ds < best2) {
+                if (sib < 0) {
+                    ++n_prims;
+                    const float dd = prim_dist2<DIM>(bvh.prims, ~sib, q);
+                    if (dd < best2) { best2 = dd; best = ~sib; }
+                } else if (!search_subtree<DIM>(bvh, sib, q, best2, best, budget, n_nodes, n_prims)) {
+                    return false;
+                }
+            }
+        }
+        // stop when the ball around q, grown by r_max, lies inside this node's Morton cell
+        const float r = sqrtf(best2) + bvh.r_max;
+        const float* cell = bvh.node_cell + 2 * DIM * node;
+        bool inside = true;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k)
+            inside = inside && (q[k] - r >= __ldg(cell + k)) && (q[k] + r <= __ldg(cell + DIM + k));
+        if (inside) return true;
+        child = node;
+        node = parent;
+    }
+    return true;
 }
 
 }  // namespace dwos

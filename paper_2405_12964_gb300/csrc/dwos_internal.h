@@ -22,6 +22,10 @@ struct DevProblem {
     int n_internal;
     int n_tree;                 // leaves in the LBVH
     int n_big;                  // outsized elements after them
+    const int* leaf_parent;     // leaf -> parent node
+    const float* node_cell;     // Morton cell per internal node
+    float r_max;                // element radius bound for the cell test
+    int traversal;              // 0 root-down, 1 climb from the hint leaf
     int data_kind;              // 0 mapped, 1 field
     int differential;
     float field[10];            // c0, c(3), Axx Ayy Azz Axy Axz Ayz
@@ -65,6 +69,7 @@ struct BvhBuffers {
     float4* nodes = nullptr;      // max(1, n_elem-1) nodes
     float4* prims = nullptr;      // n_elem prims
     int* prim_elem = nullptr;     // n_elem
+    int* leaf_of_elem = nullptr;  // n_elem: element -> leaf
     // scratch
     unsigned int* keys = nullptr;
     unsigned int* keys_sorted = nullptr;
@@ -74,6 +79,8 @@ struct BvhBuffers {
     int* node_parent = nullptr;
     int* node_child = nullptr;    // 2 per internal node
     int* counters = nullptr;
+    float* node_cell = nullptr;      // Morton cell box per internal node
+    float r_max = 0.0f;              // largest element half box diagonal (tree elements)
     unsigned int* bounds = nullptr;  // 2*dim ordered-uint scene bounds
     float* stats = nullptr;          // size statistics + outsized count
     void* sort_tmp = nullptr;
@@ -87,8 +94,9 @@ cudaError_t bvh_build(BvhBuffers& b, int dim, const float* vert, const int* elem
                       cudaStream_t stream);
 
 // Batched queries through the BVH (bvh.cu).
-cudaError_t launch_closest(const BvhBuffers& b, int n, const float* p, float* dist, int* elem_out,
-                           float* bary, int* err, cudaStream_t stream);
+cudaError_t launch_closest(const BvhBuffers& b, int n, const float* p, const int* hint_elem, float* dist,
+                           int* elem_out, float* bary, int* err, DevCounters* counters, int traversal,
+                           cudaStream_t stream);
 cudaError_t launch_inside(const BvhBuffers& b, int n, const float* p, int* inside, cudaStream_t stream);
 cudaError_t launch_philox(int n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
                           cudaStream_t stream);

@@ -139,7 +139,8 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevPr
         const unsigned long long local = gw - P.work_begin;
 
         // ---- DistanceToBoundary, seeded with the previous closest element
-        BvhView bvh{P.nodes, P.prims, P.root, P.n_internal, P.n_tree, P.n_big};
+        BvhView bvh{P.nodes, P.prims, P.root, P.n_internal, P.n_tree, P.n_big, P.traversal, P.leaf_parent,
+                    P.node_cell, P.r_max};
         float best2 = kInf;
         int best = -1;
         if (hint >= 0) { best2 = prim_dist2<DIM>(P.prims, hint, x); best = hint; }

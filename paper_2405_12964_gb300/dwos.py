@@ -32,7 +32,7 @@ DEBUG_DTYPE = np.dtype([("dudn", "<f4"), ("n", "<f4", (3,)), ("u_off", "<f4"), (
 class Options(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_float), ("h", ctypes.c_float), ("K", ctypes.c_int), ("B", ctypes.c_int),
                 ("max_steps", ctypes.c_int), ("seed", ctypes.c_uint64), ("check_inside", ctypes.c_int),
-                ("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("smem_nodes", ctypes.c_int)]
+                ("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("traversal", ctypes.c_int)]
 
 
 class RunStats(ctypes.Structure):
@@ -69,6 +69,7 @@ _SIGS = {
     "dwos_walk_records": [_vp, _i, _vp, _i, _u64, _i, _vp, _vp, _vp, _i],
     "dwos_last_stats": [_vp, ctypes.POINTER(RunStats)],
     "dwos_closest_point": [_vp, _i, _vp, _vp, _vp, _vp, _i],
+    "dwos_closest_point_hint": [_vp, _i, _vp, _vp, _vp, _vp, _vp, _i],
     "dwos_inside": [_vp, _i, _vp, _vp, _i],
     "dwos_philox4x32_10": [_vp, _i, _vp, _vp, _vp, _i],
     "dwos_eval_static": [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp],
@@ -270,6 +271,18 @@ class Solver:
         self._check(lib().dwos_closest_point(self._h, n, _ptr(x), _ptr(d), _ptr(e), _ptr(b), MEM_DEVICE))
         return d, e, b
 
+    def closest_point_hint(self, p, hint_elem):
+        self._stream()
+        x = self._dev(p, torch.float32)
+        h = self._dev(hint_elem, torch.int32)
+        n = x.shape[0]
+        d = torch.empty(n, device=self.device, dtype=torch.float32)
+        e = torch.empty(n, device=self.device, dtype=torch.int32)
+        b = torch.empty(n, 2, device=self.device, dtype=torch.float32)
+        self._check(lib().dwos_closest_point_hint(self._h, n, _ptr(x), _ptr(h), _ptr(d), _ptr(e), _ptr(b),
+                                                  MEM_DEVICE))
+        return d, e, b
+
     def inside(self, p):
         self._stream()
         x = self._dev(p, torch.float32)
@@ -306,7 +319,7 @@ class DWoSFunction(torch.autograd.Function):
         ctx.bw = backward_walks
         ctx.base = backward_base
         ctx.save_for_backward(theta.detach().clone())
-        return out["u"].to(theta.dtype) if theta.dtype == torch.float64 else out["u"]
+        return out["u"].to(dtype=theta.dtype)     # on the solver's device
 
     @staticmethod
     def backward(ctx, grad_u):
@@ -314,7 +327,7 @@ class DWoSFunction(torch.autograd.Function):
         s = ctx.solver
         s.set_params(theta)
         g = s.vjp(ctx.xq, grad_u.detach().to(torch.float32), ctx.bw, walk_id_base=ctx.base)
-        return g.to(theta.dtype), None, None, None, None, None
+        return g.to(device=theta.device, dtype=theta.dtype), None, None, None, None, None
 
 
 def solve(theta, solver: Solver, xq, walks: int, backward_walks: Optional[int] = None,

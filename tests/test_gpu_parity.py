@@ -316,3 +316,34 @@ def test_capped_walks_are_counted(Solver):
     capped_o = (o["kind"] == oracle.KIND_CAPPED).sum()
     assert abs(int(st["capped"]) - int(capped_o)) <= 2
     assert ((g["trace"][:, 0] & 0x3FFFFFFF) <= 3).all()
+
+
+@pytest.mark.parametrize("traversal", [0, 1])
+@pytest.mark.parametrize("which", ["star", "sphere"])
+def test_hinted_closest_point_equals_unhinted(Solver, which, traversal):
+    # the walk seeds each query with the previous hit and climbs the BVH from it,
+    # stopping at the first Morton cell that contains the search ball; with any
+    # hint (good, random, or none) the distance must be the brute-force minimum
+    rng = np.random.default_rng(5)
+    if which == "star":
+        sc = scenes.star_box_scene()
+        p = rng.uniform(-0.99, 0.99, size=(4000, 2))
+    else:
+        sc = scenes.sh_sphere_scene(freq=40, n_query=8)
+        p = rng.uniform(-1.95, 1.95, size=(3000, 3))
+    s = Solver(0)
+    s.load_scene(sc, traversal=traversal)
+    d0, e0, _ = (t.cpu().numpy() for t in s.closest_point(p))
+    hints = {
+        "random": rng.integers(0, sc.elem.shape[0], size=len(p)),
+        "own": e0,
+        "none": np.full(len(p), -1),
+    }
+    # a nearby element: the closest element of a slightly moved point
+    d1, e1, _ = (t.cpu().numpy() for t in s.closest_point(p + 0.05 * rng.normal(size=p.shape)))
+    hints["near"] = e1
+    for name, h in hints.items():
+        d, e, b = (t.cpu().numpy() for t in s.closest_point_hint(p, h.astype(np.int32)))
+        assert np.allclose(d, d0, rtol=1e-6, atol=1e-7), (name, np.abs(d - d0).max())
+    do = oracle.closest_point(to_oracle(sc), p[:500])[0]
+    assert np.allclose(d0[:500], do, rtol=2e-5, atol=2e-6)
