@@ -39,6 +39,9 @@ WORKLOADS = {
     "c3": ("3D thermal design: 200k-triangle SH-perturbed icosphere (81 SH coefficients, g=1) in box "
            "[-2,2]^3 (g=0), sigma=1, source 0.5, 4096 points x 2048 differential walks, K=2 nested, "
            "gradient of 1/2 sum u^2 with U-statistics (B=8)"),
+    "c4": ("batched: 64 independent problems (32 2D star-in-box, 32 3D SH-sphere-in-box), elements "
+           "log-uniform 1e3-5e5, 16-4096 points, sigma log-uniform 0.01-100, 256-4096 walks/point, "
+           "16 shape params each; L2-loss gradients in one captured CUDA graph, autotuned walk pool"),
 }
 WORKLOAD = WORKLOADS["c2"]
 
@@ -176,6 +179,74 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batched(args):
+    """Config 4: the 64 problems as separate dwos_grad_l2 calls (the plain GPU
+    path) and as one batched, autotuned, graph-captured pass."""
+    import numpy as np
+    import torch
+    from paper_2405_12964_gb300 import build, scenes
+    build.build()
+    from paper_2405_12964_gb300.dwos import Batch, Solver
+    probs = scenes.batched_problems(64)
+    solvers = []
+    for sc in probs:
+        s = Solver(0)
+        s.load_scene(sc)
+        solvers.append(s)
+    xs = [torch.tensor(sc.query, dtype=torch.float32, device="cuda") for sc in probs]
+    us = [torch.tensor(sc.u_ref, dtype=torch.float32, device="cuda") for sc in probs]
+
+    def plain(i):
+        steps = 0
+        for k, (sc, s) in enumerate(zip(probs, solvers)):
+            s.grad_l2(xs[k], us[k], sc.walks, walk_id_base=(i + 1) << 32)
+        return steps
+
+    for i in range(args.warmup):
+        plain(i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_plain = []
+    for i in range(args.steps):
+        e0.record()
+        plain(100 + i)
+        e1.record()
+        torch.cuda.synchronize()
+        t_plain.append(e0.elapsed_time(e1))
+    b = Batch([(s, xs[k], sc.walks, us[k], 7 << 32) for k, (sc, s) in enumerate(zip(probs, solvers))])
+    b.autotune(reps=1)
+    b.capture()
+    for _ in range(args.warmup):
+        b.launch()
+    b.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for i in range(args.steps):
+        ev[i][0].record(b.stream)
+        b.launch()
+        ev[i][1].record(b.stream)
+    b.synchronize()
+    clk = clocks.stop()
+    t_b = [a.elapsed_time(c) for a, c in ev]
+    st = b.stats()
+    steps = st["steps_main"] + st["steps_nested"]
+    value = steps / (np.mean(t_b) / 1e3)
+    plain_value = steps / (np.mean(t_plain) / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": float(np.mean(t_b)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["c4"], "problems": len(probs),
+                       "walks": int(sum(sc.query.shape[0] * sc.walks for sc in probs)),
+                       "autotuned": {"2d": b.config(2), "3d": b.config(3)}},
+            "plain": {"value": plain_value, "ms_per_step": float(np.mean(t_plain)),
+                      "note": "same 64 problems as separate dwos_grad_l2 calls"},
+            "speedup_vs_plain": float(np.mean(t_plain) / np.mean(t_b)),
+            "walk_steps_per_step": steps, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -188,6 +259,8 @@ def main():
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "c4":
+        return run_batched(args)
 
     import numpy as np
     import torch

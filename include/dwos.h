@@ -232,6 +232,56 @@ dwos_status dwos_inside(dwos_ctx* ctx, int n, const float* p, int32_t* inside, i
 dwos_status dwos_philox4x32_10(dwos_ctx* ctx, int n, const uint32_t* ctr, const uint32_t* key,
                                uint32_t* out, int mem);
 
+/* ---- batched problems ----------------------------------------------------
+ * Many independent reverse-mode problems in one pass: each job is a
+ * dwos_grad_l2 (Sec. 4.3, U-statistic squared-loss gradient) on its own
+ * context (boundary, BVH, data, PDE and options of that context).  The jobs of
+ * one dimension share a persistent walk launch over a table of up to 64
+ * problem descriptors, so the tail of long walks is paid once per launch.  A
+ * pass enqueues only kernels and memsets on the batch's stream and can be
+ * captured into a CUDA graph.  Contexts must outlive the batch and must not be
+ * changed (boundary, parameters, data, options) while it is used; create a new
+ * batch after such changes.  All pointers in a job are device memory on the
+ * contexts' device, owned by the caller. */
+typedef struct dwos_batch dwos_batch;
+typedef struct {
+    dwos_ctx* ctx;          /* the problem */
+    int n_query;            /* >= 1 */
+    const float* xq;        /* n_query x dim query points */
+    int walks_per_point;    /* multiple of the context's B */
+    const float* uref;      /* n_query targets of the squared loss */
+    uint64_t walk_id_base;  /* Philox walk id of the job's first walk */
+    double* loss;           /* 1 value */
+    double* grad_param;     /* n_param values (may be NULL if n_param = 0) */
+    double* u_mean;         /* n_query values or NULL */
+} dwos_batch_job;
+
+/* Validate the jobs, run the inside test once (DWOS_ERR_OUTSIDE if a point is
+ * outside its domain), allocate every buffer a pass needs and build the
+ * descriptor tables.  stream: cudaStream_t of all passes (a non-default stream
+ * is needed for graph capture).  Synchronises. */
+dwos_status dwos_batch_create(dwos_batch** out, const dwos_batch_job* jobs, int n_jobs, void* stream);
+void dwos_batch_destroy(dwos_batch* b);
+const char* dwos_batch_last_error(const dwos_batch* b);
+/* Enqueue one pass: walks of every job, then each job's scatter, GEMV, mean
+ * and loss.  Asynchronous; allocates nothing; capturable. */
+dwos_status dwos_batch_run(dwos_batch* b);
+/* Capture one pass into a CUDA graph (replaces an earlier one). */
+dwos_status dwos_batch_capture(dwos_batch* b);
+/* Replay the captured graph on the batch's stream. */
+dwos_status dwos_batch_launch(dwos_batch* b);
+/* Time the walk launch of each dimension group over block size (128, 256),
+ * resident blocks per SM (1, 2, 4, ... up to the occupancy limit) and the
+ * distance-query search order (dwos_options.traversal 0 / 1), reps passes
+ * each, and keep the fastest; recaptures the graph if one exists.
+ * Synchronises. */
+dwos_status dwos_batch_autotune(dwos_batch* b, int reps);
+/* The configuration in use for dimension dim and, after autotuning, its walk time. */
+dwos_status dwos_batch_config(const dwos_batch* b, int dim, int* block_size, int* blocks_per_sm, int* traversal,
+                              float* walk_ms);
+/* Walk statistics of the last pass (summed over launches; synchronises). */
+dwos_status dwos_batch_stats(dwos_batch* b, dwos_run_stats* out);
+
 /* ---- allocation-free evaluation ------------------------------------------
  * The paper has no counterpart to this entry point.  It is dwos_eval for
  * callers that cannot allocate device memory during the call: code under a

@@ -1,0 +1,51 @@
+// Private: the context object behind the opaque dwos_ctx handle.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "dwos_internal.h"
+
+struct dwos_ctx {
+    int device = 0;
+    int n_sm = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    dwos_options opt{};
+
+
+    // boundary
+    int dim = 0, n_vert = 0, n_elem = 0, n_param = 0;
+    float* vert_ref = nullptr;   // n_vert*dim
+    float* vert = nullptr;       // current vertices
+    int* elem = nullptr;
+    float* jac = nullptr;        // n_vert*dim*n_param (or null)
+    float* theta = nullptr;      // n_param
+    float* g_vert = nullptr;     // n_vert
+    float* dg_vert = nullptr;    // n_vert*n_param or null
+    int data_kind = 0;
+    double field[10] = {0};
+    float sigma = 0.0f, f = 0.0f;
+    dwos::BvhBuffers bvh;
+    bool have_boundary = false;
+
+    // workspaces (grow-only)
+    dwos_record* rec = nullptr; size_t rec_cap = 0;
+    float* xq = nullptr; size_t xq_cap = 0;
+    int* valid = nullptr; size_t valid_cap = 0;
+    float* wvec = nullptr; size_t wvec_cap = 0;           // cotangent / uref
+    double* out = nullptr; size_t out_cap = 0;            // reduced outputs
+    double* acc_vert = nullptr; size_t acc_cap = 0;       // n_vert*dim + n_vert
+    uint32_t* trace = nullptr; size_t trace_cap = 0;
+    dwos_walk_debug* dbg = nullptr; size_t dbg_cap = 0;
+    float* misc_f = nullptr; size_t misc_f_cap = 0;
+    int* misc_i = nullptr; size_t misc_i_cap = 0;
+    uint32_t* misc_u = nullptr; size_t misc_u_cap = 0;
+    dwos::DevProblem* d_prob = nullptr;
+    dwos::DevCounters* d_ctr = nullptr;
+    int* d_err = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    bool timed = false;
+    unsigned long long launches = 0;   // kernels launched by this context
+    int last_blocks = 0;
+};

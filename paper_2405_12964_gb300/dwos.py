@@ -47,6 +47,12 @@ class DwosError(RuntimeError):
         self.status = status
 
 
+class BatchJob(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("n_query", ctypes.c_int), ("xq", ctypes.c_void_p),
+                ("walks_per_point", ctypes.c_int), ("uref", ctypes.c_void_p), ("walk_id_base", ctypes.c_uint64),
+                ("loss", ctypes.c_void_p), ("grad_param", ctypes.c_void_p), ("u_mean", ctypes.c_void_p)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
@@ -73,6 +79,14 @@ _SIGS = {
     "dwos_inside": [_vp, _i, _vp, _vp, _i],
     "dwos_philox4x32_10": [_vp, _i, _vp, _vp, _vp, _i],
     "dwos_eval_static": [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp],
+    "dwos_batch_create": [ctypes.POINTER(_vp), ctypes.POINTER(BatchJob), _i, _vp],
+    "dwos_batch_run": [_vp],
+    "dwos_batch_capture": [_vp],
+    "dwos_batch_launch": [_vp],
+    "dwos_batch_autotune": [_vp, _i],
+    "dwos_batch_config": [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
+                          ctypes.POINTER(ctypes.c_float)],
+    "dwos_batch_stats": [_vp, ctypes.POINTER(RunStats)],
 }
 
 
@@ -93,12 +107,17 @@ def lib():
         L.dwos_last_error.restype = ctypes.c_char_p
         L.dwos_default_options.argtypes = [ctypes.POINTER(Options)]
         L.dwos_default_options.restype = None
+        L.dwos_batch_destroy.argtypes = [_vp]
+        L.dwos_batch_destroy.restype = None
+        L.dwos_batch_last_error.argtypes = [_vp]
+        L.dwos_batch_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
 
 def exported_symbols():
-    return sorted(list(_SIGS) + ["dwos_destroy", "dwos_last_error", "dwos_default_options"])
+    return sorted(list(_SIGS) + ["dwos_destroy", "dwos_last_error", "dwos_default_options", "dwos_batch_destroy",
+                                 "dwos_batch_last_error"])
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -298,6 +317,76 @@ class Solver:
         out = torch.empty(n * 4, device=self.device, dtype=torch.int32)
         self._check(lib().dwos_philox4x32_10(self._h, n, _ptr(c), _ptr(k), _ptr(out), MEM_DEVICE))
         return out.cpu().numpy().view(np.uint32).reshape(n, 4)
+
+
+class Batch:
+    """Many reverse-mode problems in one pass (dwos_batch_*): each job is
+    (solver, xq, walks_per_point, uref, walk_id_base).  Outputs per job:
+    loss (1), grad (n_param), u_mean (n_query), FP64 device tensors.  All work
+    runs on the batch's own CUDA stream (`self.stream`)."""
+
+    def __init__(self, jobs, device: int = 0):
+        self.device = torch.device("cuda", device)
+        self.stream = torch.cuda.Stream(device=self.device)
+        self.solvers, self.keep, self.out = [], [], []
+        arr = (BatchJob * len(jobs))()
+        for k, (solver, xq, walks, uref, base) in enumerate(jobs):
+            x = solver._dev(xq, torch.float32)
+            ur = solver._dev(uref, torch.float32)
+            dd = dict(device=self.device, dtype=torch.float64)
+            o = {"loss": torch.zeros(1, **dd), "grad": torch.zeros(max(solver.n_param, 1), **dd),
+                 "u_mean": torch.zeros(x.shape[0], **dd)}
+            self.solvers.append(solver)
+            self.keep += [x, ur]
+            self.out.append(o)
+            arr[k] = BatchJob(solver._h.value, x.shape[0], x.data_ptr(), int(walks), ur.data_ptr(), int(base),
+                              o["loss"].data_ptr(), o["grad"].data_ptr(), o["u_mean"].data_ptr())
+        torch.cuda.synchronize(self.device)
+        self._h = ctypes.c_void_p()
+        st = lib().dwos_batch_create(ctypes.byref(self._h), arr, len(jobs), ctypes.c_void_p(self.stream.cuda_stream))
+        if st:
+            raise DwosError(st, lib().dwos_batch_last_error(None).decode())
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and h.value and _lib is not None:
+            _lib.dwos_batch_destroy(h)
+            self._h = ctypes.c_void_p()
+
+    def _check(self, st):
+        if st:
+            raise DwosError(st, lib().dwos_batch_last_error(self._h).decode())
+
+    def run(self):
+        self._check(lib().dwos_batch_run(self._h))
+
+    def capture(self):
+        self._check(lib().dwos_batch_capture(self._h))
+
+    def launch(self):
+        self._check(lib().dwos_batch_launch(self._h))
+
+    def autotune(self, reps: int = 2):
+        self._check(lib().dwos_batch_autotune(self._h, int(reps)))
+
+    def config(self, dim: int) -> dict:
+        bs, per, tr, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+        self._check(lib().dwos_batch_config(self._h, dim, ctypes.byref(bs), ctypes.byref(per), ctypes.byref(tr),
+                                            ctypes.byref(ms)))
+        return {"block_size": bs.value, "blocks_per_sm": per.value, "traversal": tr.value, "walk_ms": ms.value}
+
+    def stats(self) -> dict:
+        s = RunStats()
+        self._check(lib().dwos_batch_stats(self._h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in RunStats._fields_}
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def results(self):
+        self.synchronize()
+        return [{"loss": float(o["loss"][0]), "grad": o["grad"][:sv.n_param].cpu().numpy(),
+                 "u_mean": o["u_mean"].cpu().numpy()} for o, sv in zip(self.out, self.solvers)]
 
 
 class DWoSFunction(torch.autograd.Function):

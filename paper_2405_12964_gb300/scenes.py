@@ -335,3 +335,29 @@ def ball_scene(freq: int = 16, R: float = 1.0, sigma: float = 1.0, f: float = 0.
                f=f, eps=eps, h=h, K=K, query=q, walks=walks)
     sc.meta = {"R": R, "theta0": np.array([R])}
     return sc
+
+
+def batched_problems(n: int = 64, seed: int = GEOMETRY_SEED, scale: float = 1.0, max_elems: int = 500_000):
+    """Batched workload: n independent problems, half 2D star-in-box, half 3D
+    SH-sphere-in-box, with element counts log-uniform in [1e3, max_elems],
+    query counts log-uniform in [16, 4096] (times `scale`), sigma log-uniform in
+    [0.01, 100], walks per point 2^floor(U[8, 12]) (times `scale`, kept a
+    multiple of 8), and 16 shape parameters (Fourier k <= 8 in 2D, SH l <= 3 in
+    3D).  Each scene carries query points, walks and a target u_ref."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        n_el = int(np.exp(rng.uniform(np.log(1e3), np.log(max_elems))))
+        n_q = max(16, int(np.exp(rng.uniform(np.log(16), np.log(4096))) * scale))
+        sigma = float(np.exp(rng.uniform(np.log(0.01), np.log(100.0))))
+        walks = max(8, int(2 ** int(rng.uniform(8, 12.999)) * scale) // 8 * 8)
+        sub = int(rng.integers(0, 2 ** 31))
+        if i % 2 == 0:
+            sc = star_box_scene(n_seg=max(64, n_el - 4), n_modes=8, sigma=sigma, n_query=n_q, walks=walks, seed=sub)
+        else:
+            freq = max(7, int(round(np.sqrt(max(n_el - 12, 20) / 20.0))))
+            sc = sh_sphere_scene(freq=freq, lmax=3, coef_std=0.02, sigma=sigma, n_query=n_q, walks=walks, seed=sub)
+            sc.u_ref = np.zeros(n_q)
+        sc.name = f"batch{i:02d}_{sc.dim}d"
+        out.append(sc)
+    return out
