@@ -390,35 +390,64 @@ __device__ __forceinline__ bool seg_hits_box(const float* o, const float* inv, f
     return t0 <= t1;
 }
 
-// Ray parameter of the crossing with leaf p, or -1.
+// Ray parameter of the crossing with leaf p, or -1.  Watertight: a crossing
+// through a vertex or edge shared by two elements is counted exactly once.
+//  2D: crossing-number rule; each vertex's side of the ray's line is computed
+//      from that vertex alone, so both segments sharing it agree.
+//  3D: vertices are projected on the plane orthogonal to the ray (per-vertex
+//      arithmetic, identical in every triangle); the 2D edge functions are
+//      evaluated without contraction, so the two triangles of a shared edge get
+//      exactly opposite values, and a zero value is broken by the edge's
+//      direction, which the two triangles also see reversed.
+struct RayFrame {
+    float dir[3];
+    float e1[3], e2[3];   // 3D: orthonormal basis of the plane orthogonal to dir
+};
+
+__device__ __forceinline__ float side2(const float* o, const float* dir, float vx, float vy) {
+    return __fsub_rn(__fmul_rn(dir[0], __fsub_rn(vy, o[1])), __fmul_rn(dir[1], __fsub_rn(vx, o[0])));
+}
+
+__device__ __forceinline__ float edge_fn(float px, float py, float qx, float qy) {
+    return __fsub_rn(__fmul_rn(px, qy), __fmul_rn(py, qx));
+}
+
+__device__ __forceinline__ bool edge_positive(float px, float py, float qx, float qy) {
+    const float e = edge_fn(px, py, qx, qy);
+    if (e != 0.0f) return e > 0.0f;
+    return (qx > px) || (qx == px && qy > py);
+}
+
+__device__ __forceinline__ void project(const RayFrame& F, const float* o, float4 v, float& x, float& y, float& z) {
+    const float dx = __fsub_rn(v.x, o[0]), dy = __fsub_rn(v.y, o[1]), dz = __fsub_rn(v.z, o[2]);
+    x = __fadd_rn(__fadd_rn(__fmul_rn(dx, F.e1[0]), __fmul_rn(dy, F.e1[1])), __fmul_rn(dz, F.e1[2]));
+    y = __fadd_rn(__fadd_rn(__fmul_rn(dx, F.e2[0]), __fmul_rn(dy, F.e2[1])), __fmul_rn(dz, F.e2[2]));
+    z = __fadd_rn(__fadd_rn(__fmul_rn(dx, F.dir[0]), __fmul_rn(dy, F.dir[1])), __fmul_rn(dz, F.dir[2]));
+}
+
 template <int DIM>
-__device__ __forceinline__ float ray_prim_t(const float4* prims, int p, const float* o, const float* dir) {
+__device__ __forceinline__ float ray_prim_t(const float4* prims, int p, const float* o, const RayFrame& F) {
     if (DIM == 2) {
         const float4 s = prims[p];
-        const float ex = s.z - s.x, ey = s.w - s.y;
-        const float det = -dir[0] * ey + dir[1] * ex;
-        if (det == 0.0f) return -1.0f;
-        const float rx = s.x - o[0], ry = s.y - o[1];
-        const float t = (-rx * ey + ry * ex) / det;
-        const float u = (dir[0] * ry - dir[1] * rx) / det;
-        return (u >= 0.0f && u < 1.0f) ? t : -1.0f;
+        const float sa = side2(o, F.dir, s.x, s.y), sb = side2(o, F.dir, s.z, s.w);
+        if ((sa >= 0.0f) == (sb >= 0.0f)) return -1.0f;
+        const float lam = sa / (sa - sb);
+        const float ax = s.x - o[0], ay = s.y - o[1];
+        return (ax + lam * (s.z - s.x)) * F.dir[0] + (ay + lam * (s.w - s.y)) * F.dir[1];
     } else {
-        const float4 a = prims[3 * p], b = prims[3 * p + 1], c = prims[3 * p + 2];
-        const float e1[3] = {b.x - a.x, b.y - a.y, b.z - a.z};
-        const float e2[3] = {c.x - a.x, c.y - a.y, c.z - a.z};
-        const float pv[3] = {dir[1] * e2[2] - dir[2] * e2[1], dir[2] * e2[0] - dir[0] * e2[2],
-                             dir[0] * e2[1] - dir[1] * e2[0]};
-        const float det = e1[0] * pv[0] + e1[1] * pv[1] + e1[2] * pv[2];
-        if (det == 0.0f) return -1.0f;
-        const float inv = 1.0f / det;
-        const float tv[3] = {o[0] - a.x, o[1] - a.y, o[2] - a.z};
-        const float u = (tv[0] * pv[0] + tv[1] * pv[1] + tv[2] * pv[2]) * inv;
-        if (u < 0.0f || u > 1.0f) return -1.0f;
-        const float qv[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2],
-                             tv[0] * e1[1] - tv[1] * e1[0]};
-        const float v = (dir[0] * qv[0] + dir[1] * qv[1] + dir[2] * qv[2]) * inv;
-        if (v < 0.0f || u + v > 1.0f) return -1.0f;
-        return (e2[0] * qv[0] + e2[1] * qv[1] + e2[2] * qv[2]) * inv;
+        float ax, ay, az, bx, by, bz, cx, cy, cz;
+        project(F, o, prims[3 * p], ax, ay, az);
+        project(F, o, prims[3 * p + 1], bx, by, bz);
+        project(F, o, prims[3 * p + 2], cx, cy, cz);
+        // the projected origin is (0, 0): inside iff all edge functions share a sign
+        const bool pa = edge_positive(bx, by, cx, cy);   // edge b -> c (weight of a)
+        const bool pb = edge_positive(cx, cy, ax, ay);   // edge c -> a (weight of b)
+        const bool pc = edge_positive(ax, ay, bx, by);   // edge a -> b (weight of c)
+        if (!((pa && pb && pc) || (!pa && !pb && !pc))) return -1.0f;
+        const float wa = edge_fn(bx, by, cx, cy), wb = edge_fn(cx, cy, ax, ay), wc = edge_fn(ax, ay, bx, by);
+        const float den = wa + wb + wc;
+        if (den == 0.0f) return -1.0f;
+        return (wa * az + wb * bz + wc * cz) / den;
     }
 }
 
@@ -441,9 +470,17 @@ __global__ void inside_kernel(BvhView bvh, int n, const float* p, int* inside) {
     const int pt = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (pt >= n) return;    // whole warps exit together
-    float o[DIM], dir[DIM], inv[DIM];
-    if (DIM == 2) { dir[0] = 0.8191520443f; dir[1] = 0.5735764364f; }
-    else { dir[0] = 0.5144957554f; dir[1] = 0.6859943406f; dir[2] = 0.5144957554f; }
+    float o[DIM], inv[DIM];
+    RayFrame F;
+    if (DIM == 2) {
+        F.dir[0] = 0.8191520443f; F.dir[1] = 0.5735764364f; F.dir[2] = 0.0f;
+    } else {
+        // generic unit direction and an orthonormal basis of its normal plane
+        F.dir[0] = 0.5144957554f; F.dir[1] = 0.6859943406f; F.dir[2] = 0.5144957554f;
+        F.e1[0] = 0.7071067812f; F.e1[1] = 0.0f; F.e1[2] = -0.7071067812f;
+        F.e2[0] = -0.4850712500f; F.e2[1] = 0.7276068751f; F.e2[2] = -0.4850712500f;
+    }
+    const float* dir = F.dir;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) { o[k] = p[DIM * pt + k]; inv[k] = 1.0f / dir[k]; }
     // scene box: the root's two children and the outsized elements
@@ -477,7 +514,7 @@ __global__ void inside_kernel(BvhView bvh, int n, const float* p, int* inside) {
     const float tb = lane == 31 ? 2.0f * tmax : tmax * (float)(lane + 1) / 32.0f;
     int count = 0;
     for (int q = bvh.n_tree; q < bvh.n_tree + bvh.n_big; ++q) {
-        const float t = ray_prim_t<DIM>(bvh.prims, q, o, dir);
+        const float t = ray_prim_t<DIM>(bvh.prims, q, o, F);
         count += (t > 0.0f && t >= ta && t < tb) ? 1 : 0;
     }
     if (bvh.n_internal > 0) {
@@ -496,7 +533,7 @@ __global__ void inside_kernel(BvhView bvh, int n, const float* p, int* inside) {
                                              : seg_hits_box<DIM>(o, inv, ta, tb, lo1, hi1));
                 if (hit && c >= 0) { next = c; break; }
                 if (hit) {
-                    const float t = ray_prim_t<DIM>(bvh.prims, ~c, o, dir);
+                    const float t = ray_prim_t<DIM>(bvh.prims, ~c, o, F);
                     count += (t > 0.0f && t >= ta && t < tb) ? 1 : 0;
                 }
                 ++state;

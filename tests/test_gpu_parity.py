@@ -347,3 +347,22 @@ def test_hinted_closest_point_equals_unhinted(Solver, which, traversal):
         assert np.allclose(d, d0, rtol=1e-6, atol=1e-7), (name, np.abs(d - d0).max())
     do = oracle.closest_point(to_oracle(sc), p[:500])[0]
     assert np.allclose(d0[:500], do, rtol=2e-5, atol=2e-6)
+
+
+def test_inside_test_is_watertight_on_fine_boundaries(Solver):
+    # very short segments / small triangles: a ray through a shared vertex or
+    # edge must count one crossing, never zero or two
+    s = Solver(0)
+    st = scenes.star_box_scene(n_seg=400_000, n_query=2048)
+    s.load_scene(st)
+    assert np.all(s.inside(st.query).cpu().numpy() == 1)
+    rng = np.random.default_rng(9)
+    a = rng.uniform(0, 2 * np.pi, 4000)
+    inner = np.stack([0.1 * np.cos(a), 0.1 * np.sin(a)], 1)          # inside the star: outside Omega
+    assert np.all(s.inside(inner).cpu().numpy() == 0)
+    sp = scenes.sh_sphere_scene(freq=120, n_query=2048)
+    s.load_scene(sp)
+    assert np.all(s.inside(sp.query).cpu().numpy() == 1)
+    d = rng.normal(size=(4000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    assert np.all(s.inside(0.5 * d).cpu().numpy() == 0)
