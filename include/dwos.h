@@ -199,6 +199,22 @@ dwos_status dwos_grad_l2(dwos_ctx* ctx, int n_query, const float* xq, const floa
                          int walks_per_point, uint64_t walk_id_base, double* loss,
                          double* grad_param, double* grad_vert, int mem);
 
+/* dwos_grad_l2 with a control variate and training samples (device pointers
+ * only).  cv_grad (n_query x dim, or NULL) is the spatial gradient of a smooth
+ * surrogate of u at the query points (e.g. the learned network's,
+ * dwos_mlp_eval); each walk whose main walk takes its first step, from x0 to
+ * x1 = x0 + d w with w uniform on the sphere and independent of the roulette
+ * draw, contributes u - cv_grad(x0) . (x1 - x0) instead of u.  The subtracted
+ * term has mean zero, so the loss gradient stays unbiased for any surrogate
+ * (Sec. 4.3's U-statistic weights use the corrected u).  samples (4 floats per
+ * walk, or NULL): (x1, estimate of u at x1) for walks that moved, NaN x
+ * otherwise.  debug (or NULL): per-walk diagnostics (xbar, du/dn).  u_se_pair (2 x
+ * n_query, or NULL): per-point standard errors of u without and with the
+ * control variate.  Asynchronous. */
+dwos_status dwos_grad_l2_cv(dwos_ctx* ctx, int n_query, const float* xq, const float* uref, int walks_per_point,
+                            uint64_t walk_id_base, const float* cv_grad, float* samples, dwos_walk_debug* debug,
+                            double* loss, double* grad_param, double* u_se_pair);
+
 /* Raw per-walk records (n_query x walks_per_point rows, row p*W + w, Philox
  * walk id walk_id_base + p*W + w).  differential = 0 runs Algorithm 1 only
  * (record.u, record.elem, record.b*, meta; c = 0).  trace (optional,
@@ -281,6 +297,38 @@ dwos_status dwos_batch_config(const dwos_batch* b, int dim, int* block_size, int
                               float* walk_ms);
 /* Walk statistics of the last pass (summed over launches; synchronises). */
 dwos_status dwos_batch_stats(dwos_batch* b, dwos_run_stats* out);
+
+/* ---- learned control variate ---------------------------------------------
+ * The paper points to variance reduction for WoS (Sec. 2, Sec. 7) without
+ * fixing one; this network is the learned control variate of the 2D
+ * shape-from-diffusion workload.  Features (x, y, sin pi x, sin pi y,
+ * sin pi (x + y)) -> four tanh layers of 64 -> 8 linear outputs, of which
+ * output 0 estimates u and output 1 du/dn.  Training uses the tensor cores:
+ * every matrix-product input (weights, activations, deltas) is BF16, sums are
+ * FP32; parameters are FP32 with Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * Flat parameter layout: W1 (64 x 16), b1 (64), W2 (64 x 64), b2, W3, b3, W4,
+ * b4, W5 (8 x 64), b5 (8), W[out][in] row-major.  Loss: (1/n) sum_s sum_k
+ * mask[s][k] (out[s][k] - target[s][k])^2 over k in {0, 1}.  Points x,
+ * targets and masks are n x 2 row-major; `mem` applies to every pointer. */
+#define DWOS_MLP_NPARAM 14088
+typedef struct dwos_mlp dwos_mlp;
+dwos_status dwos_mlp_create(dwos_mlp** out, int device);   /* parameters zero */
+void dwos_mlp_destroy(dwos_mlp* mlp);
+const char* dwos_mlp_last_error(const dwos_mlp* mlp);
+dwos_status dwos_mlp_set_stream(dwos_mlp* mlp, void* stream);
+/* Load parameters (DWOS_MLP_NPARAM floats) and reset the Adam state. */
+dwos_status dwos_mlp_set_params(dwos_mlp* mlp, const float* params, int mem);
+dwos_status dwos_mlp_get_params(dwos_mlp* mlp, float* params, int mem);
+/* Loss and gradient (DWOS_MLP_NPARAM floats) on n samples, no update. */
+dwos_status dwos_mlp_loss_grad(dwos_mlp* mlp, int n, const float* x, const float* target, const float* mask,
+                               float* grad, double* loss, int mem);
+/* One Adam step with learning rate lr on n samples; loss (may be NULL) is the
+ * loss before the step. */
+dwos_status dwos_mlp_train_step(dwos_mlp* mlp, int n, const float* x, const float* target, const float* mask,
+                                float lr, double* loss, int mem);
+/* Output 0 (u), its gradient d u / d(x, y) (n x 2) and output 1 (du/dn) at n
+ * points, with the BF16 weights and FP32 activations; any output may be NULL. */
+dwos_status dwos_mlp_eval(dwos_mlp* mlp, int n, const float* x, float* u, float* grad_u, float* q, int mem);
 
 /* ---- allocation-free evaluation ------------------------------------------
  * The paper has no counterpart to this entry point.  It is dwos_eval for

@@ -392,6 +392,7 @@ static double sample_ball_radius(int dim, const Draws& r) {
 }
 
 struct PhaseResult {
+    double x1[3];      /* point after the first sphere step (NaN if the walk never moved) */
     double u;          /* estimate from this phase */
     int kind;          /* KIND_* */
     int steps;         /* distance queries */
@@ -405,6 +406,7 @@ struct PhaseResult {
  * recursed.  acc collects the source estimates S of every step. */
 static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_t walk_id, uint32_t phase) {
     PhaseResult res;
+    res.x1[0] = res.x1[1] = res.x1[2] = NAN;
     double x[3] = {x0[0], x0[1], s->dim == 3 ? x0[2] : 0.0};
     double acc = 0;
     for (int k = 0;; ++k) {
@@ -440,6 +442,7 @@ static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_
         double w[3];
         sample_sphere(s->dim, r0, w);
         for (int i = 0; i < s->dim; ++i) x[i] += d * w[i];
+        if (k == 0) for (int i = 0; i < 3; ++i) res.x1[i] = i < s->dim ? x[i] : 0.0;
     }
 }
 
@@ -455,6 +458,7 @@ typedef struct {
     double* xbar;      /* n * 3 */
     int* kind;         /* n * (K + 1) */
     int* steps;        /* n * (K + 1) */
+    double* x1;        /* n * 3: main walk's point after its first step (NaN if none) */
 } oracle_walk_out;
 
 /* Algorithm 2 (DiffWalkOnSpheres) extended, as Sec. 4.1 observation 2
@@ -471,6 +475,7 @@ static void run_one(const oracle_scene* s, const double* x0, uint64_t walk_id, i
     if (o->elem) o->elem[idx] = main.e;
     if (o->bary) { o->bary[2 * idx] = main.bary[0]; o->bary[2 * idx + 1] = main.bary[1]; }
     if (o->xbar) for (int i = 0; i < 3; ++i) o->xbar[3 * idx + i] = main.xbar[i];
+    if (o->x1) for (int i = 0; i < 3; ++i) o->x1[3 * idx + i] = main.x1[i];
     if (mode == 0) return;
     for (int j = 1; j <= s->K; ++j) {
         if (o->kind) o->kind[idx * slots + j] = -1;

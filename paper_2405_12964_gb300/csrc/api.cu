@@ -93,7 +93,8 @@ dwos_status rebuild(dwos_ctx* ctx) {
 // Shared front half of every walk-running call: validate, stage the query
 // points, optionally classify them, fill the problem descriptor, run the walks.
 dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsigned long long base,
-                      int differential, int mem, uint32_t* trace_dev, dwos_walk_debug* dbg_dev) {
+                      int differential, int mem, uint32_t* trace_dev, dwos_walk_debug* dbg_dev,
+                      float4* cv_sample = nullptr) {
     if (!ctx->have_boundary) return fail(ctx, DWOS_ERR_STATE, "no boundary: call dwos_set_boundary first");
     if (n_query < 0 || W < 1) return fail(ctx, DWOS_ERR_INVALID_ARG, "n_query must be >= 0 and walks_per_point >= 1");
     if (n_query > 0 && !xq) return fail(ctx, DWOS_ERR_INVALID_ARG, "xq is NULL");
@@ -148,6 +149,8 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     P.rec = ctx->rec;
     P.trace = trace_dev;
     P.dbg = dbg_dev;
+    P.cv_sample = cv_sample;
+    if (cv_sample) CK(cudaMemsetAsync(cv_sample, 0xff, sizeof(float4) * total, ctx->stream), "init samples");
     CK(cudaMemcpyAsync(ctx->d_prob, &P, sizeof(P), cudaMemcpyHostToDevice, ctx->stream), "copy problem");
     CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->stream), "reset counters");
     WalkLaunch L;
@@ -473,6 +476,57 @@ dwos_status dwos_grad_l2(dwos_ctx* ctx, int n_query, const float* xq, const floa
                          uint64_t walk_id_base, double* loss, double* grad_param, double* grad_vert, int mem) {
     if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
     return reverse_common(ctx, n_query, xq, uref, W, walk_id_base, 1, loss, grad_param, grad_vert, mem);
+}
+
+dwos_status dwos_grad_l2_cv(dwos_ctx* ctx, int n_query, const float* xq, const float* uref, int W,
+                            uint64_t walk_id_base, const float* cv_grad, float* samples, dwos_walk_debug* debug,
+                            double* loss, double* grad_param, double* u_var) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (n_query < 1 || !uref || !loss) return fail(ctx, DWOS_ERR_INVALID_ARG, "bad arguments");
+    if (ctx->n_param > 0 && !grad_param) return fail(ctx, DWOS_ERR_INVALID_ARG, "grad_param is NULL");
+    if (W % ctx->opt.B) return fail(ctx, DWOS_ERR_INVALID_ARG, "walks_per_point must be a multiple of B");
+    for (const void* p : {(const void*)xq, (const void*)uref, (const void*)cv_grad, (const void*)samples,
+                          (const void*)debug, (const void*)loss, (const void*)grad_param, (const void*)u_var})
+        if (dwos_status s = check_device_ptr(ctx, p, "argument")) return s;
+    if (dwos_status s = set_device(ctx)) return s;
+    const size_t total = (size_t)n_query * W;
+    float4* smp = reinterpret_cast<float4*>(samples);
+    if (!smp && cv_grad) {
+        CK(grow(ctx->misc_f, ctx->misc_f_cap, 4 * total), "alloc samples");
+        smp = reinterpret_cast<float4*>(ctx->misc_f);
+    }
+    if (dwos_status s = run_walks(ctx, n_query, xq, W, walk_id_base, 1, DWOS_MEM_DEVICE, nullptr, debug, smp)) return s;
+    const CvView cv{smp, cv_grad, ctx->xq, ctx->dim};
+    const CvView* cvp = cv_grad ? &cv : nullptr;
+    const int N = ctx->n_param;
+    CK(grow(ctx->wvec, ctx->wvec_cap, (size_t)n_query), "alloc weights");
+    CK(cudaMemcpyAsync(ctx->wvec, uref, sizeof(float) * n_query, cudaMemcpyDeviceToDevice, ctx->stream), "copy uref");
+    const size_t nacc = (size_t)ctx->n_vert * ctx->dim + (size_t)ctx->n_vert;
+    CK(grow(ctx->acc_vert, ctx->acc_cap, nacc), "alloc accumulators");
+    CK(cudaMemsetAsync(ctx->acc_vert, 0, nacc * sizeof(double), ctx->stream), "zero accumulators");
+    double* acc_g = ctx->dg_vert ? ctx->acc_vert + (size_t)ctx->n_vert * ctx->dim : nullptr;
+    CK(launch_scatter(ctx->rec, ctx->elem, ctx->dim, n_query, W, ctx->opt.B, 1, ctx->wvec, ctx->acc_vert, acc_g,
+                      ctx->stream, cvp), "scatter");
+    if (N > 0) {
+        CK(cudaMemsetAsync(grad_param, 0, (size_t)N * sizeof(double), ctx->stream), "zero grad");
+        CK(launch_gemv(ctx->jac, ctx->dg_vert, ctx->acc_vert, acc_g, ctx->n_vert, ctx->dim, N, grad_param,
+                       ctx->stream), "adjoint gemv");
+    }
+    CK(grow(ctx->out, ctx->out_cap, 2 * (size_t)n_query), "alloc outputs");
+    double* mean = ctx->out;
+    double* se = ctx->out + n_query;
+    CK(launch_reduce_u(ctx->rec, n_query, W, mean, se, ctx->stream, cvp), "reduce u");
+    CK(launch_loss(mean, ctx->wvec, n_query, loss, ctx->stream), "loss");
+    if (u_var) {   // per-point standard errors without and with the control variate
+        CK(launch_reduce_u(ctx->rec, n_query, W, mean, u_var, ctx->stream, nullptr), "reduce u");
+        CK(launch_reduce_u(ctx->rec, n_query, W, mean, u_var + n_query, ctx->stream, cvp), "reduce u");
+    }
+    ctx->launches += 4 + (N > 0) + (u_var ? 2 : 0);
+    if (samples) {
+        CK(launch_pack_samples(ctx->rec, smp, (long long)total, ctx->stream), "pack samples");
+        ctx->launches += 1;
+    }
+    return DWOS_OK;
 }
 
 dwos_status dwos_walk_records(dwos_ctx* ctx, int n_query, const float* xq, int W, uint64_t walk_id_base,

@@ -387,7 +387,9 @@ __device__ __forceinline__ bool seg_hits_box(const float* o, const float* inv, f
         t0 = fmaxf(t0, fminf(a, b));
         t1 = fminf(t1, fmaxf(a, b));
     }
-    return t0 <= t1;
+    // a prefilter only: a ray through a box corner (a shared vertex) must not be
+    // rejected by rounding, so the overlap test allows a small relative slack
+    return t0 <= t1 + 1e-5f * fmaxf(1.0f, fabsf(t1));
 }
 
 // Ray parameter of the crossing with leaf p, or -1.  Watertight: a crossing

@@ -49,6 +49,16 @@ struct DevProblem {
     dwos_record* rec;           // one per walk (local index p*W + w)
     uint32_t* trace;            // (K+1) per walk or null
     dwos_walk_debug* dbg;       // one per walk or null
+    float4* cv_sample;          // per walk: main walk's first-step point x1 and its source S0, or null
+};
+
+// Control variate applied by the estimator kernels: u - grad(x0) . (x1 - x0)
+// for walks whose main walk took its first step (cv_sample x is not NaN).
+struct CvView {
+    const float4* sample;       // per walk (x1, S0), NaN x when the walk did not move
+    const float* grad;          // n_query x dim
+    const float* xq;            // n_query x dim
+    int dim;
 };
 
 struct DevCounters {
@@ -117,14 +127,16 @@ int walk_max_blocks_per_sm(int dim, int block_size);
 
 // Estimator reductions (estimators.cu).
 cudaError_t launch_reduce_u(const dwos_record* rec, int n_points, int W, double* mean, double* se,
-                            cudaStream_t stream);
+                            cudaStream_t stream, const CvView* cv = nullptr);
+// per-walk training samples: s.w <- u - s.w (the estimate of u at x1) where x1 exists
+cudaError_t launch_pack_samples(const dwos_record* rec, float4* samples, long long n, cudaStream_t stream);
 cudaError_t launch_reduce_udot(const dwos_record* rec, const int* elem, const float* jac, const float* dg,
                                int dim, int n_param, int n_points, int W, double* mean, double* se,
                                cudaStream_t stream);
 // mode 0: VJP weights w_p / W;  mode 1: U-statistic L2 weights in batches of B.
 cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int n_points, int W, int B,
                            int mode, const float* cot_or_uref, double* acc_vert, double* acc_g,
-                           cudaStream_t stream);
+                           cudaStream_t stream, const CvView* cv = nullptr);
 cudaError_t launch_gemv(const float* jac, const float* dg, const double* acc_vert, const double* acc_g,
                         int n_vert, int dim, int n_param, double* grad, cudaStream_t stream);
 cudaError_t launch_loss(const double* mean, const float* uref, int n_points, double* loss,

@@ -25,11 +25,26 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-__global__ void reduce_u_kernel(const dwos_record* __restrict__ rec, int W, double* mean, double* se) {
+// u of walk i (of point p), with the control variate subtracted when one is given.
+__device__ __forceinline__ double walk_u(const dwos_record* __restrict__ rec, long long i, int p, const CvView cv) {
+    double u = rec[i].u;
+    if (cv.sample) {
+        const float4 s = cv.sample[i];
+        if (s.x == s.x) {
+            double dot = (double)cv.grad[p * cv.dim] * (s.x - cv.xq[p * cv.dim]) +
+                         (double)cv.grad[p * cv.dim + 1] * (s.y - cv.xq[p * cv.dim + 1]);
+            if (cv.dim == 3) dot += (double)cv.grad[p * 3 + 2] * (s.z - cv.xq[p * 3 + 2]);
+            u -= dot;
+        }
+    }
+    return u;
+}
+
+__global__ void reduce_u_kernel(const dwos_record* __restrict__ rec, int W, double* mean, double* se, CvView cv) {
     const int p = blockIdx.x;
     double s = 0.0, s2 = 0.0;
     for (int w = threadIdx.x; w < W; w += blockDim.x) {
-        const double u = rec[(size_t)p * W + w].u;
+        const double u = walk_u(rec, (long long)p * W + w, p, cv);
         s += u;
         s2 += u * u;
     }
@@ -135,7 +150,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
                                                       const int* __restrict__ elem, int n_points, int W, int B,
                                                       int mode, const float* __restrict__ cot_or_uref,
                                                       long long walks_per_block, double* __restrict__ acc_vert,
-                                                      double* __restrict__ acc_g) {
+                                                      double* __restrict__ acc_g, CvView cv) {
     __shared__ int keys[kSlots];
     __shared__ double vals[kSlots][DIM + 1];
     for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
@@ -154,6 +169,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
         if (valid) r = rec[i];
         else { r.u = 0.0f; r.elem = -1; r.b1 = 0.0f; r.b2 = 0.0f; r.c[0] = r.c[1] = r.c[2] = 0.0f; r.meta = 0; }
         const int p = valid ? (int)(i / W) : 0;
+        const double u = valid ? walk_u(rec, i, p, cv) : 0.0;
         double wt;
         if (mode == 0) {
             wt = valid ? (double)cot_or_uref[p] / W : 0.0;
@@ -161,10 +177,10 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
             // U-statistic weight, Eq. (ustatistics): u*udot is estimated by
             // sum_m udot_m (S - u_m)/(B(B-1)), uref*udot by uref sum_m udot_m / B;
             // each batch is one of W/B estimates of the point's derivative.
-            double S = r.u;
+            double S = u;
             for (int o = B >> 1; o > 0; o >>= 1) S += __shfl_xor_sync(kFull, S, o);
             const double ur = valid ? (double)cot_or_uref[p] : 0.0;
-            wt = ((S - (double)r.u) / ((double)B * (B - 1)) - ur / B) / (double)(W / B);
+            wt = ((S - u) / ((double)B * (B - 1)) - ur / B) / (double)(W / B);
         }
         const bool hit = valid && r.elem >= 0;
         const float wv[3] = {1.0f - r.b1 - r.b2, r.b1, r.b2};
@@ -270,9 +286,25 @@ __global__ void loss_kernel(const double* mean, const float* uref, int n, double
 
 }  // namespace
 
-cudaError_t launch_reduce_u(const dwos_record* rec, int n_points, int W, double* mean, double* se, cudaStream_t s) {
+cudaError_t launch_reduce_u(const dwos_record* rec, int n_points, int W, double* mean, double* se, cudaStream_t s,
+                            const CvView* cv) {
     if (n_points <= 0) return cudaSuccess;
-    reduce_u_kernel<<<n_points, 256, 0, s>>>(rec, W, mean, se);
+    const CvView none{nullptr, nullptr, nullptr, 2};
+    reduce_u_kernel<<<n_points, 256, 0, s>>>(rec, W, mean, se, cv ? *cv : none);
+    return cudaGetLastError();
+}
+
+__global__ void pack_samples_kernel(const dwos_record* __restrict__ rec, float4* __restrict__ samples, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float4 s = samples[i];
+    if (s.x == s.x) s.w = rec[i].u - s.w;
+    samples[i] = s;
+}
+
+cudaError_t launch_pack_samples(const dwos_record* rec, float4* samples, long long n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    pack_samples_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rec, samples, n);
     return cudaGetLastError();
 }
 
@@ -286,7 +318,10 @@ cudaError_t launch_reduce_udot(const dwos_record* rec, const int* elem, const fl
 }
 
 cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int n_points, int W, int B, int mode,
-                           const float* cot_or_uref, double* acc_vert, double* acc_g, cudaStream_t s) {
+                           const float* cot_or_uref, double* acc_vert, double* acc_g, cudaStream_t s,
+                           const CvView* cv) {
+    const CvView none{nullptr, nullptr, nullptr, dim};
+    const CvView c = cv ? *cv : none;
     const long long total = (long long)n_points * W;
     if (total <= 0) return cudaSuccess;
     const int bs = 256;
@@ -295,8 +330,8 @@ cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int
     per = ((per + bs - 1) / bs) * bs;
     if (per < bs) per = bs;
     const long long blocks = (total + per - 1) / per;
-    if (dim == 2) scatter_kernel<2><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, per, acc_vert, acc_g);
-    else scatter_kernel<3><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, per, acc_vert, acc_g);
+    if (dim == 2) scatter_kernel<2><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, per, acc_vert, acc_g, c);
+    else scatter_kernel<3><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, per, acc_vert, acc_g, c);
     return cudaGetLastError();
 }
 

@@ -203,6 +203,8 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevPr
                     x[DIM - 1] = fmaf(d, z, x[DIM - 1]);
                 }
                 hint = best;
+                if (phase == 0 && k_step == 0 && P.cv_sample)   // first step of the main walk
+                    P.cv_sample[local] = make_float4(x[0], x[1], DIM == 3 ? x[DIM - 1] : 0.0f, acc);
                 continue;
             }
         }

@@ -87,7 +87,16 @@ _SIGS = {
     "dwos_batch_config": [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                           ctypes.POINTER(ctypes.c_float)],
     "dwos_batch_stats": [_vp, ctypes.POINTER(RunStats)],
+    "dwos_grad_l2_cv": [_vp, _i, _vp, _vp, _i, _u64, _vp, _vp, _vp, _vp, _vp, _vp],
+    "dwos_mlp_create": [ctypes.POINTER(_vp), _i],
+    "dwos_mlp_set_stream": [_vp, _vp],
+    "dwos_mlp_set_params": [_vp, _vp, _i],
+    "dwos_mlp_get_params": [_vp, _vp, _i],
+    "dwos_mlp_loss_grad": [_vp, _i, _vp, _vp, _vp, _vp, _vp, _i],
+    "dwos_mlp_train_step": [_vp, _i, _vp, _vp, _vp, ctypes.c_float, _vp, _i],
+    "dwos_mlp_eval": [_vp, _i, _vp, _vp, _vp, _vp, _i],
 }
+MLP_NPARAM = 14088
 
 
 def lib():
@@ -111,13 +120,17 @@ def lib():
         L.dwos_batch_destroy.restype = None
         L.dwos_batch_last_error.argtypes = [_vp]
         L.dwos_batch_last_error.restype = ctypes.c_char_p
+        L.dwos_mlp_destroy.argtypes = [_vp]
+        L.dwos_mlp_destroy.restype = None
+        L.dwos_mlp_last_error.argtypes = [_vp]
+        L.dwos_mlp_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
 
 def exported_symbols():
     return sorted(list(_SIGS) + ["dwos_destroy", "dwos_last_error", "dwos_default_options", "dwos_batch_destroy",
-                                 "dwos_batch_last_error"])
+                                 "dwos_batch_last_error", "dwos_mlp_destroy", "dwos_mlp_last_error"])
 
 
 def _ptr(t: Optional[torch.Tensor]):
@@ -250,6 +263,30 @@ class Solver:
         self._check(lib().dwos_grad_l2(self._h, x.shape[0], _ptr(x), _ptr(ur), int(walks), int(walk_id_base),
                                        _ptr(loss), _ptr(g), _ptr(gv), MEM_DEVICE))
         return (loss, g[:self.n_param], gv) if vertex_grad else (loss, g[:self.n_param])
+
+    def grad_l2_cv(self, xq, uref, walks: int, walk_id_base: int = 0, cv_grad=None, samples: bool = False,
+                   debug: bool = False):
+        """dwos_grad_l2_cv: loss, gradient, per-point SE of u without / with the
+        control variate, and optionally the training samples and debug records."""
+        self._stream()
+        x = self._dev(xq, torch.float32)
+        ur = self._dev(uref, torch.float32)
+        n = x.shape[0]
+        cg = None if cv_grad is None else self._dev(cv_grad, torch.float32)
+        dd = dict(device=self.device, dtype=torch.float64)
+        loss = torch.empty(1, **dd)
+        g = torch.empty(max(self.n_param, 1), **dd)
+        se = torch.empty(2, n, **dd)
+        smp = torch.empty(n * int(walks), 4, device=self.device, dtype=torch.float32) if samples else None
+        dbg = torch.empty(n * int(walks) * 32, device=self.device, dtype=torch.uint8) if debug else None
+        self._check(lib().dwos_grad_l2_cv(self._h, n, _ptr(x), _ptr(ur), int(walks), int(walk_id_base), _ptr(cg),
+                                          _ptr(smp), _ptr(dbg), _ptr(loss), _ptr(g), _ptr(se)))
+        out = {"loss": loss, "grad": g[:self.n_param], "u_se": se[0], "u_se_cv": se[1]}
+        if samples:
+            out["samples"] = smp
+        if debug:
+            out["debug"] = dbg
+        return out
 
     def walk_records(self, xq, walks: int, walk_id_base: int = 0, differential: bool = True,
                      trace: bool = False, debug: bool = False):
@@ -387,6 +424,91 @@ class Batch:
         self.synchronize()
         return [{"loss": float(o["loss"][0]), "grad": o["grad"][:sv.n_param].cpu().numpy(),
                  "u_mean": o["u_mean"].cpu().numpy()} for o, sv in zip(self.out, self.solvers)]
+
+
+class ControlVariateNet:
+    """The control-variate network (dwos_mlp_*): 5 features -> 4 x 64 tanh ->
+    outputs (u, du/dn); trained with the library's tensor-core kernels."""
+
+    def __init__(self, device: int = 0, params=None, seed: int = 0):
+        self.device = torch.device("cuda", device)
+        self._h = ctypes.c_void_p()
+        st = lib().dwos_mlp_create(ctypes.byref(self._h), device)
+        if st:
+            raise DwosError(st, lib().dwos_mlp_last_error(None).decode())
+        if params is None:
+            params = init_mlp_params(seed)
+        self.set_params(params)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and h.value and _lib is not None:
+            _lib.dwos_mlp_destroy(h)
+            self._h = ctypes.c_void_p()
+
+    def _check(self, st):
+        if st:
+            raise DwosError(st, lib().dwos_mlp_last_error(self._h).decode())
+
+    def _stream(self):
+        self._check(lib().dwos_mlp_set_stream(self._h, ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)))
+
+    def _dev(self, a, dtype=torch.float32):
+        return torch.as_tensor(np.asarray(a) if not torch.is_tensor(a) else a).to(device=self.device,
+                                                                                     dtype=dtype).contiguous()
+
+    def set_params(self, p):
+        self._stream()
+        t = self._dev(p)
+        self._check(lib().dwos_mlp_set_params(self._h, _ptr(t), MEM_DEVICE))
+        torch.cuda.synchronize(self.device)
+
+    def params(self):
+        self._stream()
+        out = torch.empty(MLP_NPARAM, device=self.device, dtype=torch.float32)
+        self._check(lib().dwos_mlp_get_params(self._h, _ptr(out), MEM_DEVICE))
+        return out
+
+    def loss_grad(self, x, target, mask):
+        self._stream()
+        x, t, m = self._dev(x), self._dev(target), self._dev(mask)
+        g = torch.empty(MLP_NPARAM, device=self.device, dtype=torch.float32)
+        loss = torch.empty(1, device=self.device, dtype=torch.float64)
+        self._check(lib().dwos_mlp_loss_grad(self._h, x.shape[0], _ptr(x), _ptr(t), _ptr(m), _ptr(g), _ptr(loss),
+                                             MEM_DEVICE))
+        return loss, g
+
+    def train_step(self, x, target, mask, lr: float = 1e-3):
+        self._stream()
+        x, t, m = self._dev(x), self._dev(target), self._dev(mask)
+        loss = torch.empty(1, device=self.device, dtype=torch.float64)
+        self._check(lib().dwos_mlp_train_step(self._h, x.shape[0], _ptr(x), _ptr(t), _ptr(m), float(lr), _ptr(loss),
+                                              MEM_DEVICE))
+        return loss
+
+    def eval(self, x):
+        self._stream()
+        x = self._dev(x)
+        n = x.shape[0]
+        u = torch.empty(n, device=self.device, dtype=torch.float32)
+        gu = torch.empty(n, 2, device=self.device, dtype=torch.float32)
+        q = torch.empty(n, device=self.device, dtype=torch.float32)
+        self._check(lib().dwos_mlp_eval(self._h, n, _ptr(x), _ptr(u), _ptr(gu), _ptr(q), MEM_DEVICE))
+        return u, gu, q
+
+
+def init_mlp_params(seed: int = 0) -> np.ndarray:
+    """Xavier-uniform weights (unused input columns and output rows zero), zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for fan_out, fan_in, used_in, used_out in [(64, 16, 5, 64), (64, 64, 64, 64), (64, 64, 64, 64),
+                                               (64, 64, 64, 64), (8, 64, 64, 2)]:
+        lim = np.sqrt(6.0 / (fan_in + fan_out))
+        w = rng.uniform(-lim, lim, size=(fan_out, fan_in))
+        w[:, used_in:] = 0.0
+        w[used_out:, :] = 0.0
+        parts += [w.reshape(-1), np.zeros(fan_out)]
+    return np.concatenate(parts).astype(np.float32)
 
 
 class DWoSFunction(torch.autograd.Function):

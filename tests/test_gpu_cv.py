@@ -1,0 +1,107 @@
+"""Learned control variate on the 2D shape-from-diffusion geometry.
+
+The walk estimate of u at a query point x0 is corrected by the network's
+gradient: u - grad u~(x0) . (x1 - x0), where x1 is the main walk's first step
+(the direction is uniform and independent of the roulette draw), so the
+correction has mean zero for any network.  Checks: the per-walk corrected
+estimates and the U-statistic loss gradient equal the oracle's on the same
+walks and the same cv gradient; the correction is zero-mean; a network trained
+on the walks' own samples reduces the variance of u.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import estimators as est
+from paper_2405_12964_gb300 import scenes
+from tests.helpers import to_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_12964_gb300 import build
+    build.build()
+    from paper_2405_12964_gb300 import dwos
+    return torch, dwos
+
+
+def _corrected(o, xq, W, g):
+    x1 = o["x1"][:, :2]
+    moved = ~np.isnan(x1[:, 0])
+    p = np.repeat(np.arange(xq.shape[0]), W)
+    corr = np.zeros(len(p))
+    corr[moved] = ((x1[moved] - xq[p[moved]]) * g[p[moved]]).sum(1)
+    return o["u_hat"] - corr
+
+
+def test_cv_gradient_matches_oracle_on_the_same_walks(env):
+    torch, dwos = env
+    sc = scenes.star_box_scene(n_seg=1024, n_query=12, walks=64)
+    s = dwos.Solver(0)
+    s.load_scene(sc)
+    rng = np.random.default_rng(3)
+    g = rng.normal(size=(12, 2)).astype(np.float32)
+    out = s.grad_l2_cv(sc.query, sc.u_ref, sc.walks, walk_id_base=0, cv_grad=g, samples=True)
+    o = oracle.run_walks(to_oracle(sc), sc.query, sc.walks, differential=True)
+    uc = _corrected(o, sc.query, sc.walks, g.astype(np.float64))
+    go = est.grad_l2_ustat(uc, o["udot"], sc.u_ref, 12, sc.walks, 8)
+    gg = out["grad"].cpu().numpy()
+    assert np.allclose(gg, go, rtol=2e-3, atol=2e-3 * np.abs(go).max())
+    lo = est.loss_l2(uc, sc.u_ref, 12, sc.walks)
+    assert abs(float(out["loss"][0]) - lo) <= 1e-4 * abs(lo) + 1e-7
+    # samples: x1 and the estimate of u at x1 (u minus the first ball's source, zero here)
+    smp = out["samples"].cpu().numpy()
+    moved = ~np.isnan(o["x1"][:, 0])
+    assert np.array_equal(~np.isnan(smp[:, 0]), moved)
+    assert np.allclose(smp[moved, :2], o["x1"][moved, :2], atol=1e-5)
+    assert np.allclose(smp[moved, 3], o["u_hat"][moved], atol=1e-5)
+
+
+def test_correction_has_zero_mean(env):
+    torch, dwos = env
+    sc = scenes.star_box_scene(n_query=64, walks=4096)
+    s = dwos.Solver(0)
+    s.load_scene(sc)
+    rng = np.random.default_rng(4)
+    g = rng.normal(size=(64, 2)).astype(np.float32) * 3.0
+    out = s.grad_l2_cv(sc.query, sc.u_ref, sc.walks, cv_grad=g, samples=True)
+    smp = out["samples"].cpu().numpy()
+    W = sc.walks
+    moved = ~np.isnan(smp[:, 0])
+    p = np.repeat(np.arange(64), W)
+    corr = np.zeros(len(p))
+    corr[moved] = ((smp[moved, :2] - sc.query[p[moved]]) * g[p[moved]]).sum(1)
+    c = corr.reshape(64, W)
+    z = c.mean(1) / (c.std(1, ddof=1) / np.sqrt(W))
+    assert np.abs(z).max() < 4.5
+    assert abs(z.mean()) < 4.0 / np.sqrt(64)
+
+
+def test_trained_network_reduces_variance(env):
+    torch, dwos = env
+    sc = scenes.star_box_scene(n_query=256, walks=1024)
+    s = dwos.Solver(0)
+    s.load_scene(sc)
+    net = dwos.ControlVariateNet(seed=1)
+    # fit u on the walks' own first-step samples (x1, estimate of u at x1)
+    for it in range(6):
+        out = s.grad_l2_cv(sc.query, sc.u_ref, sc.walks, walk_id_base=(it + 1) << 24, samples=True)
+        smp = out["samples"]
+        ok = ~torch.isnan(smp[:, 0])
+        x = smp[ok, :2].contiguous()
+        t = torch.stack([smp[ok, 3], torch.zeros_like(smp[ok, 3])], 1).contiguous()
+        m = torch.stack([torch.ones_like(t[:, 0]), torch.zeros_like(t[:, 0])], 1).contiguous()
+        for _ in range(60):
+            net.train_step(x, t, m, lr=2e-3)
+    _, grad_u, _ = net.eval(sc.query)
+    plain = s.grad_l2_cv(sc.query, sc.u_ref, sc.walks, walk_id_base=99 << 24)
+    cv = s.grad_l2_cv(sc.query, sc.u_ref, sc.walks, walk_id_base=99 << 24, cv_grad=grad_u)
+    ratio = (cv["u_se_cv"] / plain["u_se"]).cpu().numpy() ** 2
+    assert np.median(ratio) < 0.8, np.median(ratio)
+    # same walks: the plain SE column of the CV call equals the plain call's
+    assert np.allclose(cv["u_se"].cpu().numpy(), plain["u_se"].cpu().numpy())
