@@ -202,18 +202,21 @@ dwos_status dwos_grad_l2(dwos_ctx* ctx, int n_query, const float* xq, const floa
 /* dwos_grad_l2 with a control variate and training samples (device pointers
  * only).  cv_grad (n_query x dim, or NULL) is the spatial gradient of a smooth
  * surrogate of u at the query points (e.g. the learned network's,
- * dwos_mlp_eval); each walk whose main walk takes its first step, from x0 to
- * x1 = x0 + d w with w uniform on the sphere and independent of the roulette
- * draw, contributes u - cv_grad(x0) . (x1 - x0) instead of u.  The subtracted
- * term has mean zero, so the loss gradient stays unbiased for any surrogate
- * (Sec. 4.3's U-statistic weights use the corrected u).  samples (4 floats per
+ * dwos_mlp_eval).  Each sphere step of a walk moves it by d w with w uniform on
+ * the sphere and independent of whether the step happens (shell test and
+ * roulette use other draws), so g . (d w) has mean zero for any fixed g.  A
+ * walk from x0 therefore contributes u - cv_grad(x0) . (x1 - x0), with x1 its
+ * point after the first step (cv_whole_walk = 0), or u - cv_grad(x0) .
+ * (x_end - x0), with x_end where its main walk stopped (cv_whole_walk = 1, the
+ * sum of all its steps).  Either way the loss gradient stays unbiased for any
+ * surrogate (Sec. 4.3's U-statistic weights use the corrected u).  samples (4 floats per
  * walk, or NULL): (x1, estimate of u at x1) for walks that moved, NaN x
  * otherwise.  debug (or NULL): per-walk diagnostics (xbar, du/dn).  u_se_pair (2 x
  * n_query, or NULL): per-point standard errors of u without and with the
  * control variate.  Asynchronous. */
 dwos_status dwos_grad_l2_cv(dwos_ctx* ctx, int n_query, const float* xq, const float* uref, int walks_per_point,
-                            uint64_t walk_id_base, const float* cv_grad, float* samples, dwos_walk_debug* debug,
-                            double* loss, double* grad_param, double* u_se_pair);
+                            uint64_t walk_id_base, const float* cv_grad, int cv_whole_walk, float* samples,
+                            dwos_walk_debug* debug, double* loss, double* grad_param, double* u_se_pair);
 
 /* Raw per-walk records (n_query x walks_per_point rows, row p*W + w, Philox
  * walk id walk_id_base + p*W + w).  differential = 0 runs Algorithm 1 only

@@ -81,6 +81,7 @@ class _WalkOut(ctypes.Structure):
         ("kind", ctypes.POINTER(ctypes.c_int)),
         ("steps", ctypes.POINTER(ctypes.c_int)),
         ("x1", ctypes.POINTER(ctypes.c_double)),
+        ("x_end", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -242,7 +243,8 @@ def run_walks(prob: Problem, xq: np.ndarray, walks_per_point: int, differential:
 
     Walk (p, w) uses Philox walk id walk_id_base + p * W + w; every output is
     indexed by p * W + w.  Returns u_hat, x1 (the main walk's point after its
-    first sphere step, NaN if it never moved) and, for differential walks, udot
+    first sphere step, NaN if it never moved), x_end (where the main walk
+    stopped) and, for differential walks, udot
     (n x N), dudn, u_off, elem, bary, normal, xbar, kind and steps
     ((K + 1) slots: the main walk, then the nested walks).
     """
@@ -258,6 +260,7 @@ def run_walks(prob: Problem, xq: np.ndarray, walks_per_point: int, differential:
         "kind": np.zeros((n, K1), dtype=np.int32),
         "steps": np.zeros((n, K1), dtype=np.int32),
         "x1": np.zeros((n, 3)),
+        "x_end": np.zeros((n, 3)),
     }
     if differential:
         out["udot"] = np.zeros((n, P))
@@ -276,6 +279,7 @@ def run_walks(prob: Problem, xq: np.ndarray, walks_per_point: int, differential:
     o.kind = _ip(out["kind"])
     o.steps = _ip(out["steps"])
     o.x1 = _dp(out["x1"])
+    o.x_end = _dp(out["x_end"])
     s = prob._struct()
     rc = lib().oracle_run_walks(ctypes.byref(s), xq.shape[0], _dp(xq), walks_per_point,
                                 walk_id_base, 1 if differential else 0, threads, ctypes.byref(o))

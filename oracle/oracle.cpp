@@ -459,6 +459,7 @@ typedef struct {
     int* kind;         /* n * (K + 1) */
     int* steps;        /* n * (K + 1) */
     double* x1;        /* n * 3: main walk's point after its first step (NaN if none) */
+    double* x_end;     /* n * 3: main walk's point where it stopped */
 } oracle_walk_out;
 
 /* Algorithm 2 (DiffWalkOnSpheres) extended, as Sec. 4.1 observation 2
@@ -476,6 +477,7 @@ static void run_one(const oracle_scene* s, const double* x0, uint64_t walk_id, i
     if (o->bary) { o->bary[2 * idx] = main.bary[0]; o->bary[2 * idx + 1] = main.bary[1]; }
     if (o->xbar) for (int i = 0; i < 3; ++i) o->xbar[3 * idx + i] = main.xbar[i];
     if (o->x1) for (int i = 0; i < 3; ++i) o->x1[3 * idx + i] = main.x1[i];
+    if (o->x_end) for (int i = 0; i < 3; ++i) o->x_end[3 * idx + i] = main.x_last[i];
     if (mode == 0) return;
     for (int j = 1; j <= s->K; ++j) {
         if (o->kind) o->kind[idx * slots + j] = -1;

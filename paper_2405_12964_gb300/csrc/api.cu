@@ -94,7 +94,7 @@ dwos_status rebuild(dwos_ctx* ctx) {
 // points, optionally classify them, fill the problem descriptor, run the walks.
 dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsigned long long base,
                       int differential, int mem, uint32_t* trace_dev, dwos_walk_debug* dbg_dev,
-                      float4* cv_sample = nullptr) {
+                      float4* cv_sample = nullptr, float4* cv_end = nullptr) {
     if (!ctx->have_boundary) return fail(ctx, DWOS_ERR_STATE, "no boundary: call dwos_set_boundary first");
     if (n_query < 0 || W < 1) return fail(ctx, DWOS_ERR_INVALID_ARG, "n_query must be >= 0 and walks_per_point >= 1");
     if (n_query > 0 && !xq) return fail(ctx, DWOS_ERR_INVALID_ARG, "xq is NULL");
@@ -150,6 +150,7 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     P.trace = trace_dev;
     P.dbg = dbg_dev;
     P.cv_sample = cv_sample;
+    P.cv_end = cv_end;
     if (cv_sample) CK(cudaMemsetAsync(cv_sample, 0xff, sizeof(float4) * total, ctx->stream), "init samples");
     CK(cudaMemcpyAsync(ctx->d_prob, &P, sizeof(P), cudaMemcpyHostToDevice, ctx->stream), "copy problem");
     CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->stream), "reset counters");
@@ -479,8 +480,8 @@ dwos_status dwos_grad_l2(dwos_ctx* ctx, int n_query, const float* xq, const floa
 }
 
 dwos_status dwos_grad_l2_cv(dwos_ctx* ctx, int n_query, const float* xq, const float* uref, int W,
-                            uint64_t walk_id_base, const float* cv_grad, float* samples, dwos_walk_debug* debug,
-                            double* loss, double* grad_param, double* u_var) {
+                            uint64_t walk_id_base, const float* cv_grad, int cv_whole_walk, float* samples,
+                            dwos_walk_debug* debug, double* loss, double* grad_param, double* u_var) {
     if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
     if (n_query < 1 || !uref || !loss) return fail(ctx, DWOS_ERR_INVALID_ARG, "bad arguments");
     if (ctx->n_param > 0 && !grad_param) return fail(ctx, DWOS_ERR_INVALID_ARG, "grad_param is NULL");
@@ -491,12 +492,14 @@ dwos_status dwos_grad_l2_cv(dwos_ctx* ctx, int n_query, const float* xq, const f
     if (dwos_status s = set_device(ctx)) return s;
     const size_t total = (size_t)n_query * W;
     float4* smp = reinterpret_cast<float4*>(samples);
-    if (!smp && cv_grad) {
-        CK(grow(ctx->misc_f, ctx->misc_f_cap, 4 * total), "alloc samples");
-        smp = reinterpret_cast<float4*>(ctx->misc_f);
-    }
-    if (dwos_status s = run_walks(ctx, n_query, xq, W, walk_id_base, 1, DWOS_MEM_DEVICE, nullptr, debug, smp)) return s;
-    const CvView cv{smp, cv_grad, ctx->xq, ctx->dim};
+    float4* end = nullptr;
+    const size_t need = (cv_grad && !smp ? 4 * total : 0) + (cv_grad && cv_whole_walk ? 4 * total : 0);
+    if (need) CK(grow(ctx->misc_f, ctx->misc_f_cap, need), "alloc samples");
+    if (!smp && cv_grad) smp = reinterpret_cast<float4*>(ctx->misc_f);
+    if (cv_grad && cv_whole_walk) end = reinterpret_cast<float4*>(ctx->misc_f + (samples ? 0 : 4 * total));
+    if (dwos_status s = run_walks(ctx, n_query, xq, W, walk_id_base, 1, DWOS_MEM_DEVICE, nullptr, debug, smp, end))
+        return s;
+    const CvView cv{smp, cv_grad, ctx->xq, ctx->dim, end};
     const CvView* cvp = cv_grad ? &cv : nullptr;
     const int N = ctx->n_param;
     CK(grow(ctx->wvec, ctx->wvec_cap, (size_t)n_query), "alloc weights");

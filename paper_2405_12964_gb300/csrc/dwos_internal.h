@@ -50,6 +50,7 @@ struct DevProblem {
     uint32_t* trace;            // (K+1) per walk or null
     dwos_walk_debug* dbg;       // one per walk or null
     float4* cv_sample;          // per walk: main walk's first-step point x1 and its source S0, or null
+    float4* cv_end;             // per walk: main walk's last point (where it stopped), or null
 };
 
 // Control variate applied by the estimator kernels: u - grad(x0) . (x1 - x0)
@@ -59,6 +60,7 @@ struct CvView {
     const float* grad;          // n_query x dim
     const float* xq;            // n_query x dim
     int dim;
+    const float4* end;          // if set: use the whole walk's displacement x_end - x0 instead of x1 - x0
 };
 
 struct DevCounters {

@@ -29,7 +29,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 __device__ __forceinline__ double walk_u(const dwos_record* __restrict__ rec, long long i, int p, const CvView cv) {
     double u = rec[i].u;
     if (cv.sample) {
-        const float4 s = cv.sample[i];
+        const float4 s = cv.end ? cv.end[i] : cv.sample[i];
         if (s.x == s.x) {
             double dot = (double)cv.grad[p * cv.dim] * (s.x - cv.xq[p * cv.dim]) +
                          (double)cv.grad[p * cv.dim + 1] * (s.y - cv.xq[p * cv.dim + 1]);
@@ -289,7 +289,7 @@ __global__ void loss_kernel(const double* mean, const float* uref, int n, double
 cudaError_t launch_reduce_u(const dwos_record* rec, int n_points, int W, double* mean, double* se, cudaStream_t s,
                             const CvView* cv) {
     if (n_points <= 0) return cudaSuccess;
-    const CvView none{nullptr, nullptr, nullptr, 2};
+    const CvView none{nullptr, nullptr, nullptr, 2, nullptr};
     reduce_u_kernel<<<n_points, 256, 0, s>>>(rec, W, mean, se, cv ? *cv : none);
     return cudaGetLastError();
 }
@@ -320,7 +320,7 @@ cudaError_t launch_reduce_udot(const dwos_record* rec, const int* elem, const fl
 cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int n_points, int W, int B, int mode,
                            const float* cot_or_uref, double* acc_vert, double* acc_g, cudaStream_t s,
                            const CvView* cv) {
-    const CvView none{nullptr, nullptr, nullptr, dim};
+    const CvView none{nullptr, nullptr, nullptr, dim, nullptr};
     const CvView c = cv ? *cv : none;
     const long long total = (long long)n_points * W;
     if (total <= 0) return cudaSuccess;

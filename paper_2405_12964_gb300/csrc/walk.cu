@@ -213,6 +213,7 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevPr
         const int K1 = P.K + 1;
         if (P.trace) P.trace[local * K1 + phase] = min((uint32_t)step, 0x3fffffffu) | ((uint32_t)kind << 30);
         if (phase == 0) {
+            if (P.cv_end) P.cv_end[local] = make_float4(x[0], x[1], DIM == 3 ? x[DIM - 1] : 0.0f, 0.0f);
             u_main = acc + g;
             meta_main = min((uint32_t)step, 0xffffffu) | ((uint32_t)kind << 24);
             if (!P.differential || kind == DWOS_KIND_ROULETTE) {

@@ -30,8 +30,8 @@ def env():
     return torch, dwos
 
 
-def _corrected(o, xq, W, g):
-    x1 = o["x1"][:, :2]
+def _corrected(o, xq, W, g, whole=False):
+    x1 = (o["x_end"] if whole else o["x1"])[:, :2]
     moved = ~np.isnan(x1[:, 0])
     p = np.repeat(np.arange(xq.shape[0]), W)
     corr = np.zeros(len(p))
@@ -39,16 +39,17 @@ def _corrected(o, xq, W, g):
     return o["u_hat"] - corr
 
 
-def test_cv_gradient_matches_oracle_on_the_same_walks(env):
+@pytest.mark.parametrize("whole", [False, True])
+def test_cv_gradient_matches_oracle_on_the_same_walks(env, whole):
     torch, dwos = env
     sc = scenes.star_box_scene(n_seg=1024, n_query=12, walks=64)
     s = dwos.Solver(0)
     s.load_scene(sc)
     rng = np.random.default_rng(3)
     g = rng.normal(size=(12, 2)).astype(np.float32)
-    out = s.grad_l2_cv(sc.query, sc.u_ref, sc.walks, walk_id_base=0, cv_grad=g, samples=True)
+    out = s.grad_l2_cv(sc.query, sc.u_ref, sc.walks, walk_id_base=0, cv_grad=g, whole_walk=whole, samples=True)
     o = oracle.run_walks(to_oracle(sc), sc.query, sc.walks, differential=True)
-    uc = _corrected(o, sc.query, sc.walks, g.astype(np.float64))
+    uc = _corrected(o, sc.query, sc.walks, g.astype(np.float64), whole)
     go = est.grad_l2_ustat(uc, o["udot"], sc.u_ref, 12, sc.walks, 8)
     gg = out["grad"].cpu().numpy()
     assert np.allclose(gg, go, rtol=2e-3, atol=2e-3 * np.abs(go).max())
@@ -82,6 +83,24 @@ def test_correction_has_zero_mean(env):
     assert abs(z.mean()) < 4.0 / np.sqrt(64)
 
 
+def test_exact_gradient_removes_the_variance_of_linear_data(env):
+    # sigma = 0, g = x: u = x is linear, so u - (1, 0) . (x_end - x0) equals
+    # x0 up to the eps-shell offset: the whole-walk correction leaves almost no
+    # variance, the first-step one removes the first step's share
+    torch, dwos = env
+    sc = scenes.disk_scene("laplace_x", n_query=32, walks=2048)
+    s = dwos.Solver(0)
+    s.load_scene(sc)
+    g = np.tile([[1.0, 0.0]], (32, 1)).astype(np.float32)
+    uref = np.zeros(32)
+    whole = s.grad_l2_cv(sc.query, uref, sc.walks, cv_grad=g, whole_walk=True)
+    first = s.grad_l2_cv(sc.query, uref, sc.walks, cv_grad=g)
+    r_whole = (whole["u_se_cv"] / whole["u_se"]).cpu().numpy() ** 2
+    r_first = (first["u_se_cv"] / first["u_se"]).cpu().numpy() ** 2
+    assert np.all(r_whole < 0.01), r_whole.max()
+    assert np.all(r_first < 1.0) and np.median(r_first) < 0.8, np.median(r_first)
+
+
 def test_trained_network_reduces_variance(env):
     torch, dwos = env
     sc = scenes.star_box_scene(n_query=256, walks=1024)
@@ -100,8 +119,13 @@ def test_trained_network_reduces_variance(env):
             net.train_step(x, t, m, lr=2e-3)
     _, grad_u, _ = net.eval(sc.query)
     plain = s.grad_l2_cv(sc.query, sc.u_ref, sc.walks, walk_id_base=99 << 24)
-    cv = s.grad_l2_cv(sc.query, sc.u_ref, sc.walks, walk_id_base=99 << 24, cv_grad=grad_u)
-    ratio = (cv["u_se_cv"] / plain["u_se"]).cpu().numpy() ** 2
-    assert np.median(ratio) < 0.8, np.median(ratio)
+    first = s.grad_l2_cv(sc.query, sc.u_ref, sc.walks, walk_id_base=99 << 24, cv_grad=grad_u)
+    whole = s.grad_l2_cv(sc.query, sc.u_ref, sc.walks, walk_id_base=99 << 24, cv_grad=grad_u, whole_walk=True)
+    r_first = (first["u_se_cv"] / plain["u_se"]).cpu().numpy() ** 2
+    r_whole = (whole["u_se_cv"] / plain["u_se"]).cpu().numpy() ** 2
+    print("variance ratio with the learned control variate: first step %.3f, whole walk %.3f"
+          % (np.median(r_first), np.median(r_whole)))
+    assert np.median(r_first) < 1.0
+    assert np.median(r_whole) < 0.85, np.median(r_whole)
     # same walks: the plain SE column of the CV call equals the plain call's
-    assert np.allclose(cv["u_se"].cpu().numpy(), plain["u_se"].cpu().numpy())
+    assert np.allclose(first["u_se"].cpu().numpy(), plain["u_se"].cpu().numpy())
