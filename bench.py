@@ -39,6 +39,9 @@ WORKLOADS = {
     "c3": ("3D thermal design: 200k-triangle SH-perturbed icosphere (81 SH coefficients, g=1) in box "
            "[-2,2]^3 (g=0), sigma=1, source 0.5, 4096 points x 2048 differential walks, K=2 nested, "
            "gradient of 1/2 sum u^2 with U-statistics (B=8)"),
+    "c5": ("learned control variate on the 2D shape-from-diffusion geometry: 200 Adam steps (lr 1e-3) "
+           "on 64 Fourier coefficients from a circle toward the star, walks/point annealed 256->1024, MLP "
+           "5->64x4->2 (BF16 tensor cores, FP32 accum) trained online on the walks' estimates"),
     "c4": ("batched: 64 independent problems (32 2D star-in-box, 32 3D SH-sphere-in-box), elements "
            "log-uniform 1e3-5e5, 16-4096 points, sigma log-uniform 0.01-100, 256-4096 walks/point, "
            "16 shape params each; L2-loss gradients in one captured CUDA graph, autotuned walk pool"),
@@ -247,6 +250,49 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def run_control_variate(args):
+    """Config 5: the same optimisation with and without the learned control
+    variate; variance reduction and gradient RMSE x seconds at equal walks."""
+    import numpy as np
+    import torch
+    from paper_2405_12964_gb300 import build, scenes
+    build.build()
+    from paper_2405_12964_gb300 import optimize
+    sc = scenes.star_box_scene()
+    target = sc.theta0.copy()
+    start = np.zeros_like(target)
+    steps = 200
+    th_p, hp, _ = optimize.run(sc, target, start, steps=steps, use_cv=False, seed=3)
+    th_c, hc, trainer = optimize.run(sc, target, start, steps=steps, use_cv=True, whole_walk=True, seed=3)
+    # gradient quality at the starting shape, equal walks per point
+    s_uref = None
+    from paper_2405_12964_gb300.dwos import Solver
+    s = Solver(0)
+    s.load_scene(sc)
+    s.set_boundary(sc.reference_vertices(), sc.elem, sc.jac)
+    s.set_dirichlet_mapped(sc.g_vert)
+    s.set_params(target)
+    xq = torch.tensor(sc.query, dtype=torch.float32, device="cuda")
+    s_uref = s.eval(xq, 16384)["u"].cpu().numpy()
+    mid = 0.5 * (start + target)
+    cvg = trainer.grad_at(xq)
+    rows = {}
+    for name, th in [("start", start), ("midway", mid)]:
+        plain = optimize.gradient_rmse_x_time(sc, th, s_uref, 1024, cv_grad=None)
+        cv = optimize.gradient_rmse_x_time(sc, th, s_uref, 1024, cv_grad=cvg, whole_walk=True)
+        rows[name] = {"plain": plain, "cv": cv, "rmse_x_seconds_ratio": cv["rmse_x_seconds"] / plain["rmse_x_seconds"]}
+    line = {"metric": METRIC, "value": rows["start"]["cv"]["rmse_x_seconds"], "unit": "gradient RMSE x s",
+            "higher_is_better": False, "n_gpus": 1, "steps": steps, "warmup": 0, "vs_baseline": None,
+            "dtype": "f32 walks, bf16 MLP", "data": "synthetic",
+            "config": {"workload": WORKLOADS["c5"]},
+            "plain_run": {"final_loss": hp.loss[-1], "theta_err": hp.theta_err[-1], "seconds": hp.seconds[-1]},
+            "cv_run": {"final_loss": hc.loss[-1], "theta_err": hc.theta_err[-1], "seconds": hc.seconds[-1],
+                       "median_var_ratio_last20": float(np.median(hc.var_ratio[-20:])),
+                       "mlp_loss_last": hc.mlp_loss[-1]},
+            "gradient_rmse_x_seconds": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -261,6 +307,8 @@ def main():
         return run_reference(args)
     if args.workload == "c4":
         return run_batched(args)
+    if args.workload == "c5":
+        return run_control_variate(args)
 
     import numpy as np
     import torch

@@ -1,0 +1,175 @@
+"""Gradient-based shape optimisation with differential walk on spheres.
+
+The loop of the paper's experiments (Sec. 5.2, Sec. 6): at each iteration,
+estimate dL/dtheta of L = 1/2 sum_p (u_p(theta) - uref_p)^2 with fresh walks
+(U-statistic product estimator, Sec. 4.3), and take an Adam step (Sec. 5: lr
+1e-3).  The number of walks per point follows the exponential annealing
+schedule of Eq. (update_rule), read with t/T in the exponent.
+
+Optionally a learned control variate (the library's tensor-core MLP) is trained
+online on the walks' own estimates: (x1, estimate of u at x1) for the u head and
+(xbar, du/dn) for the du/dn head, and its spatial gradient at the observation
+points is subtracted from every walk's estimate (dwos_grad_l2_cv), which keeps
+the gradient unbiased.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+import torch
+
+from . import dwos
+
+
+def wpp_schedule(t: int, T: int, wpp0: int, wppT: int, multiple: int = 8) -> int:
+    """Eq. (update_rule): WPP_t = WPP_0 exp(log(WPP_T / WPP_0) t / T), rounded to
+    a multiple of the U-statistic batch size."""
+    w = wpp0 * math.exp(math.log(wppT / wpp0) * t / max(T, 1))
+    return max(multiple, int(round(w / multiple)) * multiple)
+
+
+class Adam:
+    """Adam (Kingma & Ba 2015) on a parameter vector."""
+
+    def __init__(self, theta: np.ndarray, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+                 eps: float = 1e-8):
+        self.theta = np.array(theta, dtype=np.float64)
+        self.lr, self.b1, self.b2, self.eps = lr, beta1, beta2, eps
+        self.m = np.zeros_like(self.theta)
+        self.v = np.zeros_like(self.theta)
+        self.t = 0
+
+    def step(self, g: np.ndarray) -> np.ndarray:
+        self.t += 1
+        self.m = self.b1 * self.m + (1 - self.b1) * g
+        self.v = self.b2 * self.v + (1 - self.b2) * g * g
+        mh = self.m / (1 - self.b1 ** self.t)
+        vh = self.v / (1 - self.b2 ** self.t)
+        self.theta = self.theta - self.lr * mh / (np.sqrt(vh) + self.eps)
+        return self.theta
+
+
+@dataclass
+class History:
+    loss: List[float] = field(default_factory=list)
+    theta_err: List[float] = field(default_factory=list)
+    wpp: List[int] = field(default_factory=list)
+    seconds: List[float] = field(default_factory=list)
+    var_ratio: List[float] = field(default_factory=list)     # median per-point Var(u with CV) / Var(u)
+    mlp_loss: List[float] = field(default_factory=list)
+
+
+class ControlVariateTrainer:
+    """Online training of the control-variate network on walk samples."""
+
+    def __init__(self, device: int = 0, seed: int = 0, lr: float = 2e-3, iters: int = 20, max_samples: int = 65536):
+        self.net = dwos.ControlVariateNet(device, seed=seed)
+        self.lr, self.iters, self.max_samples = lr, iters, max_samples
+        self.rng = np.random.default_rng(seed)
+
+    def update(self, samples: torch.Tensor, debug: Optional[torch.Tensor]) -> float:
+        ok = ~torch.isnan(samples[:, 0])
+        xs = samples[ok, :2]
+        tu = samples[ok, 3]
+        parts_x = [xs]
+        parts_t = [torch.stack([tu, torch.zeros_like(tu)], 1)]
+        parts_m = [torch.stack([torch.ones_like(tu), torch.zeros_like(tu)], 1)]
+        if debug is not None:
+            rec = debug.view(torch.float32).view(-1, 8)      # dwos_walk_debug: dudn, n[3], u_off, xbar[3]
+            dudn, xb = rec[:, 0], rec[:, 5:7]
+            hit = (rec[:, 1] != 0) | (rec[:, 2] != 0)
+            parts_x.append(xb[hit])
+            parts_t.append(torch.stack([torch.zeros_like(dudn[hit]), dudn[hit]], 1))
+            parts_m.append(torch.stack([torch.zeros_like(dudn[hit]), torch.ones_like(dudn[hit])], 1))
+        x = torch.cat(parts_x)
+        t = torch.cat(parts_t)
+        m = torch.cat(parts_m)
+        if x.shape[0] > self.max_samples:
+            idx = torch.randperm(x.shape[0], device=x.device)[:self.max_samples]
+            x, t, m = x[idx], t[idx], m[idx]
+        loss = 0.0
+        for _ in range(self.iters):
+            loss = float(self.net.train_step(x.contiguous(), t.contiguous(), m.contiguous(), lr=self.lr)[0])
+        return loss
+
+    def grad_at(self, xq) -> torch.Tensor:
+        _, g, _ = self.net.eval(xq)
+        return g
+
+
+def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 200, lr: float = 1e-3,
+        wpp0: int = 256, wppT: int = 1024, use_cv: bool = False, whole_walk: bool = True, seed: int = 1,
+        device: int = 0, target_walks: int = 16384, trainer: Optional[ControlVariateTrainer] = None):
+    """Optimise theta to match the profile that theta_target produces at the
+    scene's observation points.  Returns (theta, History)."""
+    s = dwos.Solver(device)
+    s.load_scene(scene)
+    s.set_boundary(scene.reference_vertices(), scene.elem, scene.jac)
+    s.set_dirichlet_mapped(scene.g_vert, scene.dg_vert)
+    xq = torch.tensor(scene.query, dtype=torch.float32, device=s.device)
+    s.set_params(theta_target)
+    uref = s.eval(xq, target_walks)["u"].to(torch.float32)
+    opt = Adam(theta_start, lr=lr)
+    hist = History()
+    if use_cv and trainer is None:
+        trainer = ControlVariateTrainer(device, seed=seed)
+    total = 0.0
+    for it in range(steps):
+        W = wpp_schedule(it + 1, steps, wpp0, wppT)
+        s.set_params(opt.theta)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cv_grad = trainer.grad_at(xq) if use_cv else None
+        out = s.grad_l2_cv(xq, uref, W, walk_id_base=(seed << 40) + it * (1 << 28), cv_grad=cv_grad,
+                           whole_walk=whole_walk, samples=use_cv, debug=use_cv)
+        g = out["grad"].cpu().numpy()
+        if use_cv:
+            hist.mlp_loss.append(trainer.update(out["samples"], out["debug"]))
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        total += dt
+        opt.step(g)
+        hist.loss.append(float(out["loss"][0]))
+        hist.theta_err.append(float(np.linalg.norm(opt.theta - theta_target)))
+        hist.wpp.append(W)
+        hist.seconds.append(total)
+        if use_cv:
+            r = (out["u_se_cv"] / out["u_se"].clamp_min(1e-30)).cpu().numpy() ** 2
+            hist.var_ratio.append(float(np.median(r)))
+    return opt.theta, hist, trainer
+
+
+def gradient_rmse_x_time(scene, theta: np.ndarray, uref, walks: int, repeats: int = 16, cv_grad=None,
+                         whole_walk: bool = True, ref_walks: int = 65536, device: int = 0, seed: int = 5):
+    """RMSE of one gradient estimate (walks per point) against a reference
+    (ref_walks per point, plain estimator), times the seconds one estimate
+    takes: the figure that compares estimators at equal accuracy."""
+    s = dwos.Solver(device)
+    s.load_scene(scene)
+    s.set_boundary(scene.reference_vertices(), scene.elem, scene.jac)
+    s.set_dirichlet_mapped(scene.g_vert, scene.dg_vert)
+    s.set_params(theta)
+    xq = torch.tensor(scene.query, dtype=torch.float32, device=s.device)
+    ur = torch.as_tensor(uref, dtype=torch.float32, device=s.device)
+    ref = []
+    for r in range(4):
+        ref.append(s.grad_l2_cv(xq, ur, ref_walks // 4, walk_id_base=(7 << 44) + r * (1 << 34))["grad"].cpu().numpy())
+    g_ref = np.mean(ref, axis=0)
+    est, times = [], []
+    for r in range(repeats):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = s.grad_l2_cv(xq, ur, walks, walk_id_base=(seed << 44) + r * (1 << 30), cv_grad=cv_grad,
+                           whole_walk=whole_walk)
+        g = out["grad"].cpu().numpy()
+        times.append(time.perf_counter() - t0)
+        est.append(g)
+    E = np.array(est)
+    rmse = float(np.sqrt(np.mean((E - g_ref[None]) ** 2)))
+    sec = float(np.median(times))
+    return {"rmse": rmse, "seconds": sec, "rmse_x_seconds": rmse * sec,
+            "rel_rmse": rmse / float(np.sqrt(np.mean(g_ref ** 2)))}

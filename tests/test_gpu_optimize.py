@@ -1,0 +1,37 @@
+"""Shape optimisation loop (Sec. 5.2 / Sec. 6 setting) on the 2D
+shape-from-diffusion geometry, with and without the learned control variate."""
+import numpy as np
+import pytest
+
+from paper_2405_12964_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def opt():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_12964_gb300 import build
+    build.build()
+    from paper_2405_12964_gb300 import optimize
+    return optimize
+
+
+def test_wpp_schedule_follows_update_rule(opt):
+    assert opt.wpp_schedule(0, 100, 16, 256) == 16
+    assert opt.wpp_schedule(100, 100, 16, 256) == 256
+    assert opt.wpp_schedule(50, 100, 16, 256) == 64      # geometric midpoint
+
+
+@pytest.mark.parametrize("use_cv", [False, True])
+def test_optimisation_reduces_the_loss(opt, use_cv):
+    sc = scenes.star_box_scene(n_seg=1024, n_modes=4, coef_std=0.1, n_query=64)
+    target = sc.theta0.copy()
+    start = np.zeros_like(target)
+    theta, hist, _ = opt.run(sc, target, start, steps=60, lr=1e-2, wpp0=128, wppT=512, use_cv=use_cv, seed=2)
+    assert np.mean(hist.loss[-10:]) < 0.5 * np.mean(hist.loss[:5])
+    assert hist.theta_err[-1] < hist.theta_err[0]
+    if use_cv:
+        assert np.median(hist.var_ratio[-10:]) < 1.0
