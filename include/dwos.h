@@ -208,15 +208,23 @@ dwos_status dwos_grad_l2(dwos_ctx* ctx, int n_query, const float* xq, const floa
  * walk from x0 therefore contributes u - cv_grad(x0) . (x1 - x0), with x1 its
  * point after the first step (cv_whole_walk = 0), or u - cv_grad(x0) .
  * (x_end - x0), with x_end where its main walk stopped (cv_whole_walk = 1, the
- * sum of all its steps).  Either way the loss gradient stays unbiased for any
- * surrogate (Sec. 4.3's U-statistic weights use the corrected u).  samples (4 floats per
+ * sum of all its steps).  cv_elem (n_elem x 4 floats, 16-byte aligned, or
+ * NULL) holds per boundary element a surrogate of grad u there, split as
+ * (q, t0, t1, t2): grad u ~ q n + t with n the walk's oriented normal at the
+ * hit (q stands for du/dn, t for the tangential gradient of the data).  Each
+ * nested walk launched from x_off = xbar - h n at a shell hit on element e
+ * then contributes u - (q n + t) . (x_end - x_off) to the backward difference
+ * of Eq. (dudn_fd_estimate), again a zero-mean correction.
+ * Either way the loss gradient stays unbiased for any surrogate (Sec. 4.3's
+ * U-statistic weights use the corrected u).  samples (4 floats per
  * walk, or NULL): (x1, estimate of u at x1) for walks that moved, NaN x
  * otherwise.  debug (or NULL): per-walk diagnostics (xbar, du/dn).  u_se_pair (2 x
  * n_query, or NULL): per-point standard errors of u without and with the
  * control variate.  Asynchronous. */
 dwos_status dwos_grad_l2_cv(dwos_ctx* ctx, int n_query, const float* xq, const float* uref, int walks_per_point,
-                            uint64_t walk_id_base, const float* cv_grad, int cv_whole_walk, float* samples,
-                            dwos_walk_debug* debug, double* loss, double* grad_param, double* u_se_pair);
+                            uint64_t walk_id_base, const float* cv_grad, int cv_whole_walk, const float* cv_elem,
+                            float* samples, dwos_walk_debug* debug, double* loss, double* grad_param,
+                            double* u_se_pair);
 
 /* Raw per-walk records (n_query x walks_per_point rows, row p*W + w, Philox
  * walk id walk_id_base + p*W + w).  differential = 0 runs Algorithm 1 only

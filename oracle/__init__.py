@@ -65,6 +65,7 @@ class _Scene(ctypes.Structure):
         ("max_steps", ctypes.c_int),
         ("seed_lo", ctypes.c_uint32),
         ("seed_hi", ctypes.c_uint32),
+        ("cv_elem", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -151,6 +152,7 @@ class Problem:
     K: int = 1
     max_steps: int = 1 << 14
     seed: int = 0x12964
+    cv_elem: Optional[np.ndarray] = None      # (n_elem, 4): q, t of the nested walks' surrogate grad u = q n + t
     _keep: list = dc_field(default_factory=list, repr=False)
 
     @property
@@ -167,7 +169,8 @@ class Problem:
         jac = None if self.jac is None else np.ascontiguousarray(self.jac, dtype=np.float64)
         g = None if self.g_vert is None else np.ascontiguousarray(self.g_vert, dtype=np.float64)
         dg = None if self.dg_vert is None else np.ascontiguousarray(self.dg_vert, dtype=np.float64)
-        self._keep = [v, e, jac, g, dg]
+        cq = None if self.cv_elem is None else np.ascontiguousarray(self.cv_elem, dtype=np.float64).reshape(-1, 4)
+        self._keep = [v, e, jac, g, dg, cq]
         s = _Scene()
         s.dim = v.shape[1]
         s.n_vert = v.shape[0]
@@ -193,6 +196,7 @@ class Problem:
         s.max_steps = int(self.max_steps)
         s.seed_lo = self.seed & 0xFFFFFFFF
         s.seed_hi = (self.seed >> 32) & 0xFFFFFFFF
+        s.cv_elem = _dp(cq)
         return s
 
 

@@ -125,6 +125,8 @@ typedef struct {
     int max_steps;           /* distance queries per walk phase */
     uint32_t seed_lo;
     uint32_t seed_hi;
+    const double* cv_elem;   /* per element (q, t0, t1, t2): surrogate grad u = q n + t for the nested
+                                walks' control variate, or NULL */
 } oracle_scene;
 
 enum { KIND_SHELL = 0, KIND_ROULETTE = 1, KIND_CAPPED = 2 };
@@ -500,9 +502,14 @@ static void run_one(const oracle_scene* s, const double* x0, uint64_t walk_id, i
     double xoff[3] = {0, 0, 0};
     for (int i = 0; i < s->dim; ++i) xoff[i] = main.xbar[i] - s->h * n[i];
     double sum = 0;
+    const double* q_cv = s->cv_elem ? s->cv_elem + 4 * (size_t)main.e : NULL;
     for (int j = 1; j <= s->K; ++j) {
         PhaseResult nr = forward_walk(s, xoff, walk_id, (uint32_t)j);
-        sum += nr.u;
+        /* control variate: (q n + t) . (x_end - x_off) has mean zero */
+        double disp = 0;
+        if (q_cv)
+            for (int i = 0; i < s->dim; ++i) disp += (q_cv[0] * n[i] + q_cv[1 + i]) * (nr.x_last[i] - xoff[i]);
+        sum += nr.u - disp;
         if (o->kind) o->kind[idx * slots + j] = nr.kind;
         if (o->steps) o->steps[idx * slots + j] = nr.steps;
     }

@@ -94,7 +94,7 @@ dwos_status rebuild(dwos_ctx* ctx) {
 // points, optionally classify them, fill the problem descriptor, run the walks.
 dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsigned long long base,
                       int differential, int mem, uint32_t* trace_dev, dwos_walk_debug* dbg_dev,
-                      float4* cv_sample = nullptr, float4* cv_end = nullptr) {
+                      float4* cv_sample = nullptr, float4* cv_end = nullptr, const float4* cv_elem = nullptr) {
     if (!ctx->have_boundary) return fail(ctx, DWOS_ERR_STATE, "no boundary: call dwos_set_boundary first");
     if (n_query < 0 || W < 1) return fail(ctx, DWOS_ERR_INVALID_ARG, "n_query must be >= 0 and walks_per_point >= 1");
     if (n_query > 0 && !xq) return fail(ctx, DWOS_ERR_INVALID_ARG, "xq is NULL");
@@ -151,6 +151,7 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     P.dbg = dbg_dev;
     P.cv_sample = cv_sample;
     P.cv_end = cv_end;
+    P.cv_elem = cv_elem;
     if (cv_sample) CK(cudaMemsetAsync(cv_sample, 0xff, sizeof(float4) * total, ctx->stream), "init samples");
     CK(cudaMemcpyAsync(ctx->d_prob, &P, sizeof(P), cudaMemcpyHostToDevice, ctx->stream), "copy problem");
     CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->stream), "reset counters");
@@ -480,14 +481,16 @@ dwos_status dwos_grad_l2(dwos_ctx* ctx, int n_query, const float* xq, const floa
 }
 
 dwos_status dwos_grad_l2_cv(dwos_ctx* ctx, int n_query, const float* xq, const float* uref, int W,
-                            uint64_t walk_id_base, const float* cv_grad, int cv_whole_walk, float* samples,
-                            dwos_walk_debug* debug, double* loss, double* grad_param, double* u_var) {
+                            uint64_t walk_id_base, const float* cv_grad, int cv_whole_walk, const float* cv_elem,
+                            float* samples, dwos_walk_debug* debug, double* loss, double* grad_param,
+                            double* u_var) {
     if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
     if (n_query < 1 || !uref || !loss) return fail(ctx, DWOS_ERR_INVALID_ARG, "bad arguments");
     if (ctx->n_param > 0 && !grad_param) return fail(ctx, DWOS_ERR_INVALID_ARG, "grad_param is NULL");
     if (W % ctx->opt.B) return fail(ctx, DWOS_ERR_INVALID_ARG, "walks_per_point must be a multiple of B");
-    for (const void* p : {(const void*)xq, (const void*)uref, (const void*)cv_grad, (const void*)samples,
-                          (const void*)debug, (const void*)loss, (const void*)grad_param, (const void*)u_var})
+    for (const void* p : {(const void*)xq, (const void*)uref, (const void*)cv_grad, (const void*)cv_elem,
+                          (const void*)samples, (const void*)debug, (const void*)loss, (const void*)grad_param,
+                          (const void*)u_var})
         if (dwos_status s = check_device_ptr(ctx, p, "argument")) return s;
     if (dwos_status s = set_device(ctx)) return s;
     const size_t total = (size_t)n_query * W;
@@ -497,7 +500,8 @@ dwos_status dwos_grad_l2_cv(dwos_ctx* ctx, int n_query, const float* xq, const f
     if (need) CK(grow(ctx->misc_f, ctx->misc_f_cap, need), "alloc samples");
     if (!smp && cv_grad) smp = reinterpret_cast<float4*>(ctx->misc_f);
     if (cv_grad && cv_whole_walk) end = reinterpret_cast<float4*>(ctx->misc_f + (samples ? 0 : 4 * total));
-    if (dwos_status s = run_walks(ctx, n_query, xq, W, walk_id_base, 1, DWOS_MEM_DEVICE, nullptr, debug, smp, end))
+    if (dwos_status s = run_walks(ctx, n_query, xq, W, walk_id_base, 1, DWOS_MEM_DEVICE, nullptr, debug, smp, end,
+                                  reinterpret_cast<const float4*>(cv_elem)))
         return s;
     const CvView cv{smp, cv_grad, ctx->xq, ctx->dim, end};
     const CvView* cvp = cv_grad ? &cv : nullptr;

@@ -51,6 +51,7 @@ struct DevProblem {
     dwos_walk_debug* dbg;       // one per walk or null
     float4* cv_sample;          // per walk: main walk's first-step point x1 and its source S0, or null
     float4* cv_end;             // per walk: main walk's last point (where it stopped), or null
+    const float4* cv_elem;      // per element (q, t): surrogate grad u = q n + t for the nested walks' correction, or null
 };
 
 // Control variate applied by the estimator kernels: u - grad(x0) . (x1 - x0)

@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevPr
     float x[DIM], acc = 0.0f;
     // main-walk results kept while the nested walks run
     float u_main = 0.0f, g_main = 0.0f, b1 = 0.0f, b2 = 0.0f, sum_nested = 0.0f;
+    float4 q_cv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     int leaf_main = -1, e_main = -1;
     uint32_t meta_main = 0;
     float nrm[DIM], cb[DIM], xoff[DIM];
@@ -292,8 +293,15 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevPr
             for (int k = 0; k < DIM; ++k) xoff[k] = fmaf(-P.h, nrm[k], xbar[k]);
             g_main = g; b1 = w1; b2 = w2; leaf_main = best; e_main = e;
             sum_nested = 0.0f;
+            if (P.cv_elem) q_cv = __ldg(P.cv_elem + e);
         } else {
-            sum_nested += acc + g;
+            // nested control variate: (q n + t) . (x_end - x_off) has mean zero (every
+            // move's direction is uniform and independent of whether the move happens)
+            const float tv[3] = {q_cv.y, q_cv.z, q_cv.w};
+            float disp = 0.0f;
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) disp = fmaf(fmaf(q_cv.x, nrm[k], tv[k]), x[k] - xoff[k], disp);
+            sum_nested += acc + g - disp;
             if (phase == P.K) {   // Eq. (wos_deriv), shell case, with Eq. (dudn_fd_estimate)
                 const float u_off = sum_nested / (float)P.K;
                 const float dudn = (g_main - u_off) * P.inv_h;

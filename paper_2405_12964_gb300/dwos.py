@@ -87,7 +87,7 @@ _SIGS = {
     "dwos_batch_config": [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                           ctypes.POINTER(ctypes.c_float)],
     "dwos_batch_stats": [_vp, ctypes.POINTER(RunStats)],
-    "dwos_grad_l2_cv": [_vp, _i, _vp, _vp, _i, _u64, _vp, _i, _vp, _vp, _vp, _vp, _vp],
+    "dwos_grad_l2_cv": [_vp, _i, _vp, _vp, _i, _u64, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp],
     "dwos_mlp_create": [ctypes.POINTER(_vp), _i],
     "dwos_mlp_set_stream": [_vp, _vp],
     "dwos_mlp_set_params": [_vp, _vp, _i],
@@ -265,7 +265,7 @@ class Solver:
         return (loss, g[:self.n_param], gv) if vertex_grad else (loss, g[:self.n_param])
 
     def grad_l2_cv(self, xq, uref, walks: int, walk_id_base: int = 0, cv_grad=None, whole_walk: bool = False,
-                   samples: bool = False, debug: bool = False):
+                   cv_elem=None, samples: bool = False, debug: bool = False):
         """dwos_grad_l2_cv: loss, gradient, per-point SE of u without / with the
         control variate, and optionally the training samples and debug records."""
         self._stream()
@@ -273,6 +273,11 @@ class Solver:
         ur = self._dev(uref, torch.float32)
         n = x.shape[0]
         cg = None if cv_grad is None else self._dev(cv_grad, torch.float32)
+        cq = None
+        if cv_elem is not None:
+            cq = self._dev(cv_elem, torch.float32)
+            if cq.dim() != 2 or cq.shape[1] != 4:
+                raise ValueError("cv_elem must be (n_elem, 4): du/dn surrogate and tangential gradient")
         dd = dict(device=self.device, dtype=torch.float64)
         loss = torch.empty(1, **dd)
         g = torch.empty(max(self.n_param, 1), **dd)
@@ -280,7 +285,8 @@ class Solver:
         smp = torch.empty(n * int(walks), 4, device=self.device, dtype=torch.float32) if samples else None
         dbg = torch.empty(n * int(walks) * 32, device=self.device, dtype=torch.uint8) if debug else None
         self._check(lib().dwos_grad_l2_cv(self._h, n, _ptr(x), _ptr(ur), int(walks), int(walk_id_base), _ptr(cg),
-                                          1 if whole_walk else 0, _ptr(smp), _ptr(dbg), _ptr(loss), _ptr(g), _ptr(se)))
+                                          1 if whole_walk else 0, _ptr(cq), _ptr(smp), _ptr(dbg), _ptr(loss), _ptr(g),
+                                          _ptr(se)))
         out = {"loss": loss, "grad": g[:self.n_param], "u_se": se[0], "u_se_cv": se[1]}
         if samples:
             out["samples"] = smp

@@ -9,8 +9,10 @@ schedule of Eq. (update_rule), read with t/T in the exponent.
 Optionally a learned control variate (the library's tensor-core MLP) is trained
 online on the walks' own estimates: (x1, estimate of u at x1) for the u head and
 (xbar, du/dn) for the du/dn head, and its spatial gradient at the observation
-points is subtracted from every walk's estimate (dwos_grad_l2_cv), which keeps
-the gradient unbiased.
+points is subtracted from every walk's estimate (dwos_grad_l2_cv); the nested
+walks behind each du/dn estimate subtract (q n + t) . (x_end - x_off) with q the
+du/dn head at the element and t the data's tangential gradient.  Both
+corrections have mean zero, which keeps the gradient unbiased.
 """
 from __future__ import annotations
 
@@ -66,9 +68,11 @@ class History:
 class ControlVariateTrainer:
     """Online training of the control-variate network on walk samples."""
 
-    def __init__(self, device: int = 0, seed: int = 0, lr: float = 2e-3, iters: int = 20, max_samples: int = 65536):
+    def __init__(self, device: int = 0, seed: int = 0, lr: float = 2e-3, iters: int = 20, max_samples: int = 65536,
+                 q_weight: float = 0.05):
         self.net = dwos.ControlVariateNet(device, seed=seed)
         self.lr, self.iters, self.max_samples = lr, iters, max_samples
+        self.q_weight = q_weight     # du/dn targets carry 1/h-amplified noise: weight their loss down
         self.rng = np.random.default_rng(seed)
 
     def update(self, samples: torch.Tensor, debug: Optional[torch.Tensor]) -> float:
@@ -84,7 +88,7 @@ class ControlVariateTrainer:
             hit = (rec[:, 1] != 0) | (rec[:, 2] != 0)
             parts_x.append(xb[hit])
             parts_t.append(torch.stack([torch.zeros_like(dudn[hit]), dudn[hit]], 1))
-            parts_m.append(torch.stack([torch.zeros_like(dudn[hit]), torch.ones_like(dudn[hit])], 1))
+            parts_m.append(torch.stack([torch.zeros_like(dudn[hit]), torch.full_like(dudn[hit], self.q_weight)], 1))
         x = torch.cat(parts_x)
         t = torch.cat(parts_t)
         m = torch.cat(parts_m)
@@ -99,6 +103,44 @@ class ControlVariateTrainer:
     def grad_at(self, xq) -> torch.Tensor:
         _, g, _ = self.net.eval(xq)
         return g
+
+    def elem_table(self, vert: np.ndarray, elem: np.ndarray, g_vert: np.ndarray) -> np.ndarray:
+        """The nested walks' table: the du/dn head at each element's centre and
+        the data's tangential gradient (boundary at its current position)."""
+        centres = np.asarray(vert, dtype=np.float64)[elem].mean(axis=1)
+        _, _, q = self.net.eval(centres.astype(np.float32))
+        return nested_cv_table(vert, elem, g_vert, q)
+
+
+def tangential_gradient(vert: np.ndarray, elem: np.ndarray, g_vert: np.ndarray) -> np.ndarray:
+    """Per element, the surface gradient of the piecewise-linear data g (its
+    interpolant of the vertex values): (g1 - g0) / L^2 (v1 - v0) on a segment,
+    sum_i g_i grad lambda_i on a triangle.  Returns (n_elem, 3)."""
+    vert = np.asarray(vert, dtype=np.float64)
+    g = np.asarray(g_vert, dtype=np.float64)
+    out = np.zeros((elem.shape[0], 3))
+    if elem.shape[1] == 2:
+        d = vert[elem[:, 1]] - vert[elem[:, 0]]
+        out[:, :2] = ((g[elem[:, 1]] - g[elem[:, 0]]) / (d * d).sum(1))[:, None] * d
+        return out
+    a, b, c = vert[elem[:, 0]], vert[elem[:, 1]], vert[elem[:, 2]]
+    N = np.cross(b - a, c - a)
+    n2 = (N * N).sum(1)[:, None]
+    # grad lambda_i = N x (edge opposite i, walked a->b->c) / |N|^2
+    for gi, e in ((g[elem[:, 0]], c - b), (g[elem[:, 1]], a - c), (g[elem[:, 2]], b - a)):
+        out += gi[:, None] * np.cross(N, e) / n2
+    return out
+
+
+def nested_cv_table(vert: np.ndarray, elem: np.ndarray, g_vert: np.ndarray, q) -> np.ndarray:
+    """The nested walks' control-variate table (n_elem, 4): (q, t) with q a
+    du/dn surrogate per element and t the data's tangential gradient, so that
+    q n + t approximates grad u at the boundary (n the walk's oriented normal)."""
+    q = q.detach().cpu().numpy() if isinstance(q, torch.Tensor) else np.asarray(q)
+    tab = np.zeros((elem.shape[0], 4), dtype=np.float32)
+    tab[:, 0] = q
+    tab[:, 1:] = tangential_gradient(vert, elem, g_vert)
+    return tab
 
 
 def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 200, lr: float = 1e-3,
@@ -117,6 +159,7 @@ def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 2
     hist = History()
     if use_cv and trainer is None:
         trainer = ControlVariateTrainer(device, seed=seed)
+    vref = scene.reference_vertices()
     total = 0.0
     for it in range(steps):
         W = wpp_schedule(it + 1, steps, wpp0, wppT)
@@ -124,8 +167,10 @@ def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 2
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cv_grad = trainer.grad_at(xq) if use_cv else None
+        cv_elem = trainer.elem_table(vref + np.einsum("vkp,p->vk", scene.jac, opt.theta), scene.elem,
+                                     scene.g_vert) if use_cv else None
         out = s.grad_l2_cv(xq, uref, W, walk_id_base=(seed << 40) + it * (1 << 28), cv_grad=cv_grad,
-                           whole_walk=whole_walk, samples=use_cv, debug=use_cv)
+                           whole_walk=whole_walk, cv_elem=cv_elem, samples=use_cv, debug=use_cv)
         g = out["grad"].cpu().numpy()
         if use_cv:
             hist.mlp_loss.append(trainer.update(out["samples"], out["debug"]))
@@ -144,7 +189,8 @@ def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 2
 
 
 def gradient_rmse_x_time(scene, theta: np.ndarray, uref, walks: int, repeats: int = 16, cv_grad=None,
-                         whole_walk: bool = True, ref_walks: int = 65536, device: int = 0, seed: int = 5):
+                         whole_walk: bool = True, cv_elem=None, ref_walks: int = 65536, device: int = 0,
+                         seed: int = 5):
     """RMSE of one gradient estimate (walks per point) against a reference
     (ref_walks per point, plain estimator), times the seconds one estimate
     takes: the figure that compares estimators at equal accuracy."""
@@ -164,7 +210,7 @@ def gradient_rmse_x_time(scene, theta: np.ndarray, uref, walks: int, repeats: in
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         out = s.grad_l2_cv(xq, ur, walks, walk_id_base=(seed << 44) + r * (1 << 30), cv_grad=cv_grad,
-                           whole_walk=whole_walk)
+                           whole_walk=whole_walk, cv_elem=cv_elem)
         g = out["grad"].cpu().numpy()
         times.append(time.perf_counter() - t0)
         est.append(g)

@@ -129,3 +129,51 @@ def test_trained_network_reduces_variance(env):
     assert np.median(r_whole) < 0.85, np.median(r_whole)
     # same walks: the plain SE column of the CV call equals the plain call's
     assert np.allclose(first["u_se"].cpu().numpy(), plain["u_se"].cpu().numpy())
+
+
+def test_nested_cv_table_matches_oracle(env):
+    # the per-element table (q, t) corrects each nested walk by (q n + t) . (x_end - x_off)
+    torch, dwos = env
+    from tests.test_gpu_parity import branch_match
+    sc = scenes.star_box_scene(n_seg=1024, n_query=12, walks=64)
+    s = dwos.Solver(0)
+    s.load_scene(sc)
+    rng = np.random.default_rng(5)
+    tab = rng.normal(size=(sc.elem.shape[0], 4)).astype(np.float32)
+    g = rng.normal(size=(12, 2)).astype(np.float32)
+    recs = s.walk_records(sc.query, sc.walks, trace=True)         # the table changes no walk's path
+    out = s.grad_l2_cv(sc.query, sc.u_ref, sc.walks, cv_grad=g, whole_walk=True, cv_elem=tab, debug=True)
+    o = oracle.run_walks(to_oracle(sc, cv_elem=tab.astype(np.float64)), sc.query, sc.walks, differential=True)
+    same = branch_match(sc, recs, o)
+    assert same.mean() > 0.97
+    dd = out["debug"].view(torch.float32).view(-1, 8)[:, 0].cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(dd - o["dudn"])[same] <= 1e-3 * (1 + np.abs(o["dudn"][same])))
+    uc = _corrected(o, sc.query, sc.walks, g.astype(np.float64), True)
+    go = est.grad_l2_ustat(uc, o["udot"], sc.u_ref, 12, sc.walks, 8)
+    gg = out["grad"].cpu().numpy()
+    assert np.allclose(gg, go, rtol=2e-3, atol=2e-3 * np.abs(go).max())
+
+
+def test_exact_boundary_gradient_collapses_nested_variance(env):
+    # u = x: q = n_x and t = e_x - n_x n give grad u exactly; du/dn keeps only the eps-shell offset
+    torch, dwos = env
+    from paper_2405_12964_gb300.optimize import nested_cv_table
+    sc = scenes.disk_scene("laplace_x", n_query=32, walks=1024)
+    s = dwos.Solver(0)
+    s.load_scene(sc)
+    v, e = sc.vert, sc.elem
+    d = v[e[:, 1]] - v[e[:, 0]]
+    n = np.stack([d[:, 1], -d[:, 0]], 1) / np.linalg.norm(d, axis=1)[:, None]
+    n *= np.sign(((v[e[:, 0]] + v[e[:, 1]]) * n).sum(1))[:, None]
+    tab = nested_cv_table(v, e, v[:, 0], n[:, 0])
+    uref = np.zeros(32)
+    res = []
+    for t in (None, tab):
+        out = s.grad_l2_cv(sc.query, uref, sc.walks, cv_elem=t, debug=True)
+        rec = out["debug"].view(torch.float32).view(-1, 8).cpu().numpy().astype(np.float64)
+        hit = (rec[:, 1] != 0) | (rec[:, 2] != 0)
+        res.append(rec[hit, 0] - rec[hit, 1])                      # du/dn minus the closed form n_x
+    ratio = res[1].var() / res[0].var()
+    print("nested du/dn variance ratio with the exact table: %.2e" % ratio)
+    assert ratio < 0.01, ratio
+    assert abs(res[1].mean()) < 0.05
