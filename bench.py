@@ -306,6 +306,8 @@ def main():
     ap.add_argument("--walks", type=int, default=0, help="walks per point (0: the workload's)")
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--traversal", type=int, default=-1,
+                    help="closest-point search: 0 binary per lane, 1 climb, 2 32-wide warp-wide (-1: 2 in 3D, 0 in 2D)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -334,7 +336,8 @@ def main():
 
     sc = make_scene(args.workload, args.walks)
     s = Solver(local)
-    s.load_scene(sc)
+    trav = args.traversal if args.traversal >= 0 else (2 if sc.dim == 3 else 0)
+    s.load_scene(sc, traversal=trav)
     n_pts, W = sc.query.shape[0], sc.walks
     total = n_pts * W
     xq = torch.tensor(sc.query, dtype=torch.float32, device=dev)
@@ -396,9 +399,11 @@ def main():
     rmse = float(np.sqrt(np.mean((G - g_ref[None]) ** 2)))
     rel = rmse / float(np.sqrt(np.mean(g_ref ** 2)))
 
-    # roofline of the walk kernel: algorithmic bytes = BVH node fetches x 48 B
-    # + element tests x 16 B + one 32 B record per walk + 8 B query load per walk
-    node_b, prim_b = (48, 16) if sc.dim == 2 else (64, 48)
+    # roofline of the walk kernel: algorithmic bytes = BVH node fetches x node size
+    # (binary 48 / 64 B; 32-wide (2 dim + 1) x 128 B) + element tests x 16 / 48 B
+    # + one 32 B record per walk + 8 B query load per walk
+    node_b = (2 * sc.dim + 1) * 128 if trav == 2 else (48 if sc.dim == 2 else 64)
+    prim_b = 16 if sc.dim == 2 else 48
     alg_bytes = nodes * node_b + prims * prim_b + args.steps * total * (32 + 8)
     walk_s = sum(kernel_ms) / 1e3
     achieved = alg_bytes / walk_s / 1e9 / args.steps * args.steps
@@ -442,6 +447,8 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload], "points": n_pts, "walks_per_point": W, "K": sc.K, "B": sc.B,
                        "n_param": sc.n_param, "eps": sc.eps, "h": sc.h,
+                       "closest_point_search": {0: "binary LBVH, per lane", 1: "binary LBVH climbing from the hint",
+                                                2: "32-wide BVH, warp-wide"}[trav],
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": f"replicas x{world} (independent walk ranges, no collective)"},
             "gradient_estimates_per_s": world * total * args.steps / t,

@@ -25,6 +25,12 @@ dwos_status fail(dwos_ctx* c, dwos_status s, const std::string& msg) {
     return s;
 }
 
+// The search order a launch uses: the warp-wide one only where the tree supports it.
+int effective_traversal(const dwos_ctx* c) {
+    const int t = c->opt.traversal;
+    return (t == 2 && !c->bvh.wide_ok) ? 0 : t;
+}
+
 dwos_status cuda_fail(dwos_ctx* c, cudaError_t e, const char* where) {
     std::string m = std::string(where) + ": " + cudaGetErrorString(e);
     cudaGetLastError();
@@ -127,7 +133,9 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     P.leaf_parent = ctx->bvh.leaf_parent;
     P.node_cell = ctx->bvh.node_cell;
     P.r_max = ctx->bvh.r_max;
-    P.traversal = ctx->opt.traversal;
+    P.traversal = effective_traversal(ctx);
+    P.wnodes = ctx->bvh.wnodes;
+    P.n_wide = ctx->bvh.n_wide;
     P.data_kind = ctx->data_kind;
     P.differential = differential;
     for (int i = 0; i < 10; ++i) P.field[i] = (float)ctx->field[i];
@@ -160,6 +168,7 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     L.block_size = ctx->opt.block_size > 0 ? ctx->opt.block_size : 256;
     L.blocks_per_sm = ctx->opt.blocks_per_sm;
     L.n_sm = ctx->n_sm;
+    L.traversal = P.traversal;
     CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
     int blocks = 0;
     CK(launch_walks(L, ctx->d_prob, 1, total, ctx->d_ctr, ctx->stream, &blocks), "walk kernel");
@@ -269,7 +278,7 @@ dwos_status dwos_set_options(dwos_ctx* ctx, const dwos_options* o) {
     if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 256 || o->block_size % 32))
         return fail(ctx, DWOS_ERR_INVALID_ARG, "block_size must be 0 or a multiple of 32 in [32, 256]");
     if (o->blocks_per_sm < 0 || o->blocks_per_sm > 64) return fail(ctx, DWOS_ERR_INVALID_ARG, "blocks_per_sm must be in [0, 64]");
-    if (o->traversal < 0 || o->traversal > 1) return fail(ctx, DWOS_ERR_INVALID_ARG, "traversal must be 0 or 1");
+    if (o->traversal < 0 || o->traversal > 2) return fail(ctx, DWOS_ERR_INVALID_ARG, "traversal must be 0, 1 or 2");
     ctx->opt = *o;
     return DWOS_OK;
 }
@@ -607,7 +616,7 @@ static dwos_status closest_common(dwos_ctx* ctx, int n, const float* p, const in
     if (hint) { dh = ctx->misc_i + std::max(n, 1); CK(to_device(ctx, dh, hint, (size_t)n, mem), "copy hints"); }
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream), "reset");
     CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->stream), "reset counters");
-    CK(launch_closest(ctx->bvh, n, dp, dh, dd, ctx->misc_i, db, ctx->d_err, ctx->d_ctr, ctx->opt.traversal,
+    CK(launch_closest(ctx->bvh, n, dp, dh, dd, ctx->misc_i, db, ctx->d_err, ctx->d_ctr, effective_traversal(ctx),
                       ctx->stream), "closest point");
     ctx->launches += n > 0 ? 1 : 0;
     CK(from_device(ctx, dist, dd, n, mem), "copy");
@@ -755,7 +764,9 @@ extern "C" dwos_status dwos_eval_static(dwos_ctx* ctx, int n_query, const float*
     P.leaf_parent = ctx->bvh.leaf_parent;
     P.node_cell = ctx->bvh.node_cell;
     P.r_max = ctx->bvh.r_max;
-    P.traversal = ctx->opt.traversal;
+    P.traversal = effective_traversal(ctx);
+    P.wnodes = ctx->bvh.wnodes;
+    P.n_wide = ctx->bvh.n_wide;
     P.data_kind = ctx->data_kind;
     P.differential = diff;
     for (int i = 0; i < 10; ++i) P.field[i] = (float)ctx->field[i];
@@ -783,6 +794,7 @@ extern "C" dwos_status dwos_eval_static(dwos_ctx* ctx, int n_query, const float*
     L.block_size = ctx->opt.block_size > 0 ? ctx->opt.block_size : 256;
     L.blocks_per_sm = ctx->opt.blocks_per_sm;
     L.n_sm = ctx->n_sm;
+    L.traversal = P.traversal;
     int blocks = 0;
     CK(launch_walks(L, d_prob, 1, total, d_ctr, ctx->stream, &blocks), "walk kernel");
     CK(launch_reduce_u(d_rec, n_query, W, u_mean, u_se, ctx->stream), "reduce u");

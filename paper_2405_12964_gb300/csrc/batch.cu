@@ -95,6 +95,8 @@ void fill_problem(const dwos_ctx* c, const dwos_batch_job& j, dwos_record* rec, 
     P.node_cell = c->bvh.node_cell;
     P.r_max = c->bvh.r_max;
     P.traversal = traversal;
+    P.wnodes = c->bvh.wnodes;
+    P.n_wide = c->bvh.n_wide;
     P.data_kind = c->data_kind;
     P.differential = 1;
     for (int i = 0; i < 10; ++i) P.field[i] = (float)c->field[i];
@@ -117,11 +119,23 @@ void fill_problem(const dwos_ctx* c, const dwos_batch_job& j, dwos_record* rec, 
     P.rec = rec;
 }
 
+// The warp-wide search serves a launch only if every problem's tree supports it.
+bool wide_ok_dim(const dwos_batch* b, int dim) {
+    for (const auto& ch : b->chunks)
+        if (ch.dim == dim)
+            for (int ji : ch.jobs)
+                if (!b->jobs[ji].ctx->bvh.wide_ok) return false;
+    return true;
+}
+
 // Rewrite the descriptor tables (after an autotuner change of search order).
 dwos_status upload_tables(dwos_batch* b) {
+    for (int dim = 2; dim <= 3; ++dim)
+        if (b->trav[dim] == 2 && !wide_ok_dim(b, dim)) b->trav[dim] = 0;
     for (auto& ch : b->chunks) {
         std::vector<DevProblem> tab(ch.jobs.size());
         unsigned long long begin = 0;
+        b->cfg[ch.dim].traversal = b->trav[ch.dim];
         for (size_t k = 0; k < ch.jobs.size(); ++k) {
             const int ji = ch.jobs[k];
             const dwos_batch_job& j = b->jobs[ji];
@@ -311,15 +325,17 @@ dwos_status dwos_batch_autotune(dwos_batch* b, int reps) {
         float best = 1e30f;
         WalkLaunch best_cfg = b->cfg[dim];
         int best_trav = b->trav[dim];
-        for (int trav = 0; trav <= 1; ++trav) {
+        for (int trav = 0; trav <= 2; ++trav) {
+            if (trav == 2 && !wide_ok_dim(b, dim)) continue;
             b->trav[dim] = trav;
             if (dwos_status s = upload_tables(b)) return s;
             for (int bs : sizes) {
-                const int maxb = std::max(1, walk_max_blocks_per_sm(dim, bs));
+                const int maxb = std::max(1, walk_max_blocks_per_sm(dim, bs, trav));
                 for (int per = 1; per <= maxb; per = per < maxb ? std::min(maxb, per * 2) : maxb + 1) {
                     WalkLaunch L = b->cfg[dim];
                     L.block_size = bs;
                     L.blocks_per_sm = per;
+                    L.traversal = trav;
                     const WalkLaunch keep = b->cfg[dim];
                     b->cfg[dim] = L;
                     float t = 0.0f;

@@ -2,9 +2,11 @@
 //   element boxes + scene bounds -> Morton codes -> radix sort (CUB) ->
 //   binary radix tree (Karras, "Maximizing parallelism in the construction of
 //   BVHs, octrees and k-d trees", HPG 2012) -> bottom-up box refit with
-//   arrival counters -> leaf primitives written in Morton order.
+//   arrival counters -> leaf primitives written in Morton order -> 32-wide
+//   tree collapsed from the binary one five levels at a time.
 // Plus the batched closest-point, ray-parity inside test and Philox kernels.
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
 
 #include <cstring>
 
@@ -330,6 +332,74 @@ __global__ void single_leaf_kernel(const float* vert, const int* elem, const int
         make_float4(__int_as_float(~0), __int_as_float(kEmptyChild), __int_as_float(-1), 0.0f);
 }
 
+// ---- 32-wide tree -----------------------------------------------------------
+// Depth of every internal node; nodes at depths 0, 5, 10, ... root the wide
+// nodes (flag 1).
+__global__ void wide_depth_kernel(const int* node_parent, int n_int, int* depth, int* flag, int* winfo) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    int d = 0;
+    for (int a = node_parent[i]; a >= 0 && d <= n_int; a = node_parent[a]) ++d;
+    depth[i] = d;
+    flag[i] = (d % 5) == 0 ? 1 : 0;
+    atomicMax(winfo + 1, d);
+}
+
+__global__ void wide_count_kernel(const int* wid, const int* flag, int n_int, int* winfo) {
+    winfo[0] = wid[n_int - 1] + flag[n_int - 1];
+}
+
+// Children of one wide node: its binary subtree's frontier at relative depth
+// 5 (or leaves above it), left to right.  Each slot records the child's code
+// and where the binary tree keeps its box (parent node and side).
+__global__ void wide_fill_kernel(const int* node_child, const int* wid, const int* flag, int n_int, int* wsrc,
+                                 int* wcode) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_int || !flag[i]) return;
+    const int w = wid[i];
+    int st_node[8], st_rel[8], st_side[8], top = 0;   // pending binary children: parent, parent's depth, side
+    st_node[top] = i; st_rel[top] = 0; st_side[top] = 1; ++top;
+    st_node[top] = i; st_rel[top] = 0; st_side[top] = 0; ++top;
+    int cnt = 0;
+    while (top > 0) {
+        --top;
+        const int par = st_node[top], rel = st_rel[top], side = st_side[top];
+        const int c = node_child[2 * par + side];
+        if (c < 0 || rel + 1 == 5) {                 // a leaf, or the root of the next wide node
+            wcode[kWide * w + cnt] = c < 0 ? c : wid[c];
+            wsrc[kWide * w + cnt] = (par << 1) | side;
+            ++cnt;
+        } else {
+            st_node[top] = c; st_rel[top] = rel + 1; st_side[top] = 1; ++top;
+            st_node[top] = c; st_rel[top] = rel + 1; st_side[top] = 0; ++top;
+        }
+    }
+    for (; cnt < kWide; ++cnt) { wcode[kWide * w + cnt] = kEmptyChild; wsrc[kWide * w + cnt] = -1; }
+}
+
+// Child boxes gathered from the binary tree (its refit already ran) and codes.
+template <int DIM>
+__global__ void wide_refit_kernel(const float4* nodes, const int* wsrc, const int* wcode, int n_wide, float* wnodes) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n_wide * kWide) return;
+    const int w = t / kWide, j = t % kWide;
+    float* f = wnodes + (size_t)w * WideLayout<DIM>::kFloats;
+    const int src = wsrc[t];
+    float lo[DIM], hi[DIM];
+    if (src < 0) {
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) { lo[k] = kInf; hi[k] = -kInf; }
+    } else {
+        const float* b = reinterpret_cast<const float*>(nodes + BvhLayout<DIM>::kNodeF4 * (src >> 1)) +
+                         (DIM == 2 ? 4 : 6) * (src & 1);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) { lo[k] = b[k]; hi[k] = b[DIM + k]; }
+    }
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) { f[k * kWide + j] = lo[k]; f[(DIM + k) * kWide + j] = hi[k]; }
+    f[2 * DIM * kWide + j] = __int_as_float(wcode[t]);
+}
+
 // ---- queries --------------------------------------------------------------
 template <int DIM>
 __global__ void closest_kernel(BvhView bvh, const int* prim_elem, const int* leaf_of_elem, int n, const float* p,
@@ -355,6 +425,56 @@ __global__ void closest_kernel(BvhView bvh, const int* prim_elem, const int* lea
         atomicAdd(&ctr->nodes, (unsigned long long)nn);
         atomicAdd(&ctr->prims, (unsigned long long)np);
     }
+    float w1 = 0.0f, w2 = 0.0f;
+    if (best >= 0) {
+        if (DIM == 2) {
+            const float4 s = bvh.prims[best];
+            best2 = seg_closest(q, s.x, s.y, s.z, s.w, w1);
+        } else {
+            const float4 a = bvh.prims[3 * best], b = bvh.prims[3 * best + 1], c = bvh.prims[3 * best + 2];
+            best2 = tri_closest(q, make_float3(a.x, a.y, a.z), make_float3(b.x, b.y, b.z),
+                                make_float3(c.x, c.y, c.z), w1, w2);
+        }
+    }
+    dist[i] = sqrtf(best2);
+    elem_out[i] = best >= 0 ? prim_elem[best] : -1;
+    bary[2 * i] = w1;
+    bary[2 * i + 1] = w2;
+}
+
+// The same query with the warp-wide search of the 32-wide tree: all lanes of a
+// block take part (a lane past n only helps), so there is no early return.
+template <int DIM>
+__global__ void closest_wide_kernel(BvhView bvh, WideView wv, const int* prim_elem, const int* leaf_of_elem, int n,
+                                    const float* p, const int* hint_elem, float* dist, int* elem_out, float* bary,
+                                    int* err, DevCounters* ctr) {
+    extern __shared__ float2 wide_stack[];
+    float2* stk = wide_stack + (size_t)(threadIdx.x >> 5) * kWideStack;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool act = i < n;
+    float q[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) q[k] = act ? p[DIM * i + k] : 0.0f;
+    float best2 = kInf;
+    int best = -1;
+    unsigned nn = 0, np = 0;
+    if (act) {
+        if (hint_elem) {
+            const int h = hint_elem[i];
+            if (h >= 0 && h < bvh.n_tree + bvh.n_big) {
+                best = leaf_of_elem[h];
+                best2 = prim_dist2<DIM>(bvh.prims, best, q);
+            }
+        }
+        big_closest<DIM>(bvh.prims, bvh.n_tree, bvh.n_big, q, best2, best, np);
+    }
+    const int e = wide_closest<DIM>(wv, __ballot_sync(kWarpAll, act), q, best2, best, stk, nn, np);
+    if (e) atomicOr(err, 1);
+    if (ctr) {
+        atomicAdd(&ctr->nodes, (unsigned long long)nn);
+        atomicAdd(&ctr->prims, (unsigned long long)np);
+    }
+    if (!act) return;
     float w1 = 0.0f, w2 = 0.0f;
     if (best >= 0) {
         if (DIM == 2) {
@@ -594,9 +714,12 @@ cudaError_t bvh_reserve(BvhBuffers& b, int dim, int n_elem) {
     DW_TRY(cudaMalloc(&b.node_cell, sizeof(float) * 2 * dim * (size_t)n_int));
     DW_TRY(cudaMalloc(&b.bounds, sizeof(unsigned int) * 6));
     DW_TRY(cudaMalloc(&b.stats, sizeof(float) * 2 + sizeof(int) * 4));
-    size_t tmp = 0;
+    size_t tmp = 0, tmp_scan = 0;
     DW_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp, b.keys, b.keys_sorted, b.vals, b.vals_sorted, n_elem));
+    DW_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tmp_scan, b.counters, b.vals, n_int));
+    tmp = tmp > tmp_scan ? tmp : tmp_scan;
     DW_TRY(cudaMalloc(&b.sort_tmp, tmp));
+    DW_TRY(cudaMalloc(&b.winfo, sizeof(int) * 4));
 #undef DW_TRY
     b.sort_tmp_bytes = tmp;
     b.capacity = n_elem;
@@ -609,10 +732,52 @@ void bvh_free(BvhBuffers& b) {
     cudaFree(b.vals); cudaFree(b.vals_sorted); cudaFree(b.leaf_parent); cudaFree(b.node_parent);
     cudaFree(b.node_child); cudaFree(b.counters); cudaFree(b.bounds); cudaFree(b.stats); cudaFree(b.node_cell);
     cudaFree(b.sort_tmp);
+    cudaFree(b.wnodes); cudaFree(b.wsrc); cudaFree(b.winfo);
     b = BvhBuffers();
 }
 
 constexpr int kMaxBig = 64;
+
+// Collapse the binary tree (nt - 1 = n_internal >= 1 nodes, boxes refit) into
+// the 32-wide tree.  Scratch: vals (depth), counters (flags), keys (wide ids);
+// one host synchronisation reads the node count and the depth.
+template <int DIM>
+static cudaError_t build_wide(BvhBuffers& b, cudaStream_t s) {
+    const int n_int = b.n_internal;
+    int* depth = b.vals;
+    int* flag = b.counters;
+    int* wid = reinterpret_cast<int*>(b.keys);
+    cudaError_t e = cudaMemsetAsync(b.winfo, 0, sizeof(int) * 4, s);
+    if (e != cudaSuccess) return e;
+    wide_depth_kernel<<<nblk(n_int, 256), 256, 0, s>>>(b.node_parent, n_int, depth, flag, b.winfo);
+    size_t tmp = b.sort_tmp_bytes;
+    e = cub::DeviceScan::ExclusiveSum(b.sort_tmp, tmp, flag, wid, n_int, s);
+    if (e != cudaSuccess) return e;
+    wide_count_kernel<<<1, 1, 0, s>>>(wid, flag, n_int, b.winfo);
+    int info[2] = {0, 0};
+    e = cudaMemcpyAsync(info, b.winfo, sizeof(int) * 2, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    const int n_wide = info[0];
+    if (n_wide > b.wide_cap) {
+        cudaFree(b.wnodes); cudaFree(b.wsrc);
+        b.wnodes = nullptr; b.wsrc = nullptr; b.wide_cap = 0;
+        e = cudaMalloc(&b.wnodes, sizeof(float) * WideLayout<3>::kFloats * (size_t)n_wide);
+        if (e != cudaSuccess) return e;
+        e = cudaMalloc(&b.wsrc, sizeof(int) * 2 * kWide * (size_t)n_wide);   // sources, then codes
+        if (e != cudaSuccess) return e;
+        b.wide_cap = n_wide;
+    }
+    b.n_wide = n_wide;
+    b.wide_depth = info[1] / 5 + 1;
+    b.wide_ok = 31 * b.wide_depth + 1 <= kWideStack;
+    int* wcode = b.wsrc + kWide * (size_t)n_wide;
+    wide_fill_kernel<<<nblk(n_int, 128), 128, 0, s>>>(b.node_child, wid, flag, n_int, b.wsrc, wcode);
+    wide_refit_kernel<DIM><<<nblk((long long)n_wide * kWide, 256), 256, 0, s>>>(b.nodes, b.wsrc, wcode, n_wide,
+                                                                               b.wnodes);
+    return cudaGetLastError();
+}
 
 template <int DIM>
 static cudaError_t build_impl(BvhBuffers& b, const float* vert, const int* elem, int n, cudaStream_t s) {
@@ -660,7 +825,12 @@ static cudaError_t build_impl(BvhBuffers& b, const float* vert, const int* elem,
         finalize_kernel<DIM><<<nblk(n, 256), 256, 0, s>>>(vert, elem, b.vals_sorted, n, b.node_child,
                                                           b.node_parent, nt - 1, b.nodes, b.prims, b.prim_elem,
                                                           b.leaf_of_elem);
+        e = build_wide<DIM>(b, s);
+        if (e != cudaSuccess) return e;
     } else {
+        b.n_wide = 0;
+        b.wide_depth = 0;
+        b.wide_ok = true;     // nothing to search beyond the single leaf
         b.n_internal = nt;    // 1: a single-leaf node; 0: no tree
         if (nt == 1) single_leaf_kernel<DIM><<<1, 1, 0, s>>>(vert, elem, b.vals_sorted, b.nodes, b.leaf_parent,
                                                              b.node_cell);
@@ -695,7 +865,14 @@ cudaError_t launch_closest(const BvhBuffers& b, int n, const float* p, const int
                            int* elem_out, float* bary, int* err, DevCounters* ctr, int traversal, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     BvhView v = view_of(b);
-    v.climb = traversal;
+    if (traversal == 2 && b.wide_ok) {
+        const WideView wv{b.wnodes, b.prims, b.n_wide, b.n_tree};
+        const size_t smem = sizeof(float2) * kWideStack * (128 / 32);
+        if (b.dim == 2) closest_wide_kernel<2><<<nblk(n, 128), 128, smem, s>>>(v, wv, b.prim_elem, b.leaf_of_elem, n, p, hint_elem, dist, elem_out, bary, err, ctr);
+        else closest_wide_kernel<3><<<nblk(n, 128), 128, smem, s>>>(v, wv, b.prim_elem, b.leaf_of_elem, n, p, hint_elem, dist, elem_out, bary, err, ctr);
+        return cudaGetLastError();
+    }
+    v.climb = traversal == 1 ? 1 : 0;
     if (b.dim == 2) closest_kernel<2><<<nblk(n, 128), 128, 0, s>>>(v, b.prim_elem, b.leaf_of_elem, n, p, hint_elem, dist, elem_out, bary, err, ctr);
     else closest_kernel<3><<<nblk(n, 128), 128, 0, s>>>(v, b.prim_elem, b.leaf_of_elem, n, p, hint_elem, dist, elem_out, bary, err, ctr);
     return cudaGetLastError();

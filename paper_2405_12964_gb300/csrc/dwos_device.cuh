@@ -387,4 +387,127 @@ __device__ __forceinline__ bool closest_leaf(const BvhView& bvh, const float* q,
     return true;
 }
 
+// ---- 32-wide BVH searched by a whole warp ---------------------------------
+// The binary LBVH collapsed five levels at a time: a wide node holds up to 32
+// children in SoA order, lo[DIM][32], hi[DIM][32], code[32] (>= 0: wide node,
+// < 0: ~leaf, kEmptyChild: unused slot with an empty box), so that lane j of
+// a warp loads slot j of every array with one coalesced request per array.
+constexpr int kWide = 32;
+constexpr int kWideStack = 416;            // stack entries per warp: 31 x wide depth + 1 (checked at build)
+constexpr unsigned kWarpAll = 0xffffffffu;
+template <int DIM> struct WideLayout { static constexpr int kFloats = (2 * DIM + 1) * kWide; };
+
+struct WideView {
+    const float* wnodes;   // n_wide nodes of WideLayout<DIM>::kFloats floats, root first
+    const float4* prims;
+    int n_wide;
+    int n_tree;
+};
+
+// Closest tree leaf for every lane in `need`, one query at a time, with all
+// 32 lanes working on it: each lane takes one child slot of the current wide
+// node, leaf children are measured exactly in parallel and reduced with
+// shuffles (ties to the lower leaf index), and the inner children that can
+// still hold a closer leaf go on the warp's stack in shared memory, nearest
+// on top (depth-first, near child first, pruned by the running bound).
+// best2 / best hold each lane's bound on entry (kInf / -1 without one) and
+// the result on exit.  Called by all 32 lanes with the same `need` and each
+// lane's own view (lanes may belong to different problems).  Returns error
+// bits: 1 if a query popped more nodes than the tree has, 4 if the stack
+// would overflow (excluded by the build's depth check).
+template <int DIM>
+__device__ __forceinline__ int wide_closest(const WideView& mine, unsigned need, const float* q_lane, float& best2,
+                                            int& best, float2* stk, unsigned& n_nodes, unsigned& n_prims) {
+    const int lane = threadIdx.x & 31;
+    int err = 0;
+    while (need) {
+        const int src = __ffs(need) - 1;
+        need &= need - 1;
+        float q[DIM];
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) q[k] = __shfl_sync(kWarpAll, q_lane[k], src);
+        float b2 = __shfl_sync(kWarpAll, best2, src);
+        int bi = __shfl_sync(kWarpAll, best, src);
+        const float* wn = reinterpret_cast<const float*>(
+            __shfl_sync(kWarpAll, reinterpret_cast<unsigned long long>(mine.wnodes), src));
+        const float4* prims = reinterpret_cast<const float4*>(
+            __shfl_sync(kWarpAll, reinterpret_cast<unsigned long long>(mine.prims), src));
+        const int n_wide = __shfl_sync(kWarpAll, mine.n_wide, src);
+        const int n_tree = __shfl_sync(kWarpAll, mine.n_tree, src);
+        if (n_wide > 0) {
+            __syncwarp();
+            if (lane == 0) stk[0] = make_float2(0.0f, __int_as_float(0));
+            __syncwarp();
+            int top = 1;
+            int budget = n_wide;
+            while (top > 0) {
+                const float2 e = stk[top - 1];
+                --top;
+                if (!(e.x < b2)) continue;                     // pruned by a closer leaf found since
+                if (--budget < 0) { err |= 1; break; }
+                const float* f = wn + (size_t)__float_as_int(e.y) * WideLayout<DIM>::kFloats;
+                float lo[DIM], hi[DIM];
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) {
+                    lo[k] = __ldg(f + k * kWide + lane);
+                    hi[k] = __ldg(f + (DIM + k) * kWide + lane);
+                }
+                const int code = __float_as_int(__ldg(f + 2 * DIM * kWide + lane));
+                const float cd = box_dist2<DIM>(q, lo, hi);
+                if (lane == 0) ++n_nodes;
+                const bool leaf = code < 0 && cd < b2;
+                const unsigned lm = __ballot_sync(kWarpAll, leaf);
+                if (lm) {
+                    float dd = kInf;
+                    int pi = 0x7fffffff;
+                    if (leaf) { pi = ~code; dd = prim_dist2<DIM>(prims, pi, q); }
+                    if (lane == 0) n_prims += __popc(lm);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const float od = __shfl_xor_sync(kWarpAll, dd, o);
+                        const int op = __shfl_xor_sync(kWarpAll, pi, o);
+                        if (od < dd || (od == dd && op < pi)) { dd = od; pi = op; }
+                    }
+                    if (dd < b2) { b2 = dd; bi = pi; }
+                }
+                const bool inner = code >= 0 && code != kEmptyChild && cd < b2;
+                const unsigned im = __ballot_sync(kWarpAll, inner);
+                if (im) {
+                    const int cnt = __popc(im);
+                    if (top + cnt > kWideStack) { err |= 4; break; }
+                    // stack position from the bottom: how many pushed siblings are farther
+                    int rank = 0;
+                    for (unsigned m = im; m; m &= m - 1) {
+                        const int j = __ffs(m) - 1;
+                        const float dj = __shfl_sync(kWarpAll, cd, j);
+                        rank += (dj > cd || (dj == cd && j > lane)) ? 1 : 0;
+                    }
+                    __syncwarp();
+                    if (inner) stk[top + rank] = make_float2(cd, __int_as_float(code));
+                    top += cnt;
+                    __syncwarp();
+                }
+            }
+        } else if (n_tree == 1) {
+            const float dd = prim_dist2<DIM>(prims, 0, q);
+            if (lane == 0) ++n_prims;
+            if (dd < b2) { b2 = dd; bi = 0; }
+        }
+        if (lane == src) { best2 = b2; best = bi; }
+    }
+    return err;
+}
+
+// Outsized elements (kept out of the tree) against one lane's query.
+template <int DIM>
+__device__ __forceinline__ void big_closest(const float4* __restrict__ prims, int n_tree, int n_big, const float* q,
+                                            float& best2, int& best, unsigned& n_prims) {
+    for (int p = n_tree; p < n_tree + n_big; ++p) {
+        if (prim_box_dist2<DIM>(prims, p, q) >= best2) continue;
+        ++n_prims;
+        const float dd = prim_dist2<DIM>(prims, p, q);
+        if (dd < best2) { best2 = dd; best = p; }
+    }
+}
+
 }  // namespace dwos

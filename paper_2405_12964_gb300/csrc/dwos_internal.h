@@ -25,7 +25,9 @@ struct DevProblem {
     const int* leaf_parent;     // leaf -> parent node
     const float* node_cell;     // Morton cell per internal node
     float r_max;                // element radius bound for the cell test
-    int traversal;              // 0 root-down, 1 climb from the hint leaf
+    int traversal;              // 0 root-down, 1 climb from the hint leaf, 2 warp-wide over the 32-wide tree
+    const float* wnodes;        // 32-wide tree (SoA nodes), root first
+    int n_wide;                 // its node count
     int data_kind;              // 0 mapped, 1 field
     int differential;
     float field[10];            // c0, c(3), Axx Ayy Azz Axy Axz Ayz
@@ -99,6 +101,12 @@ struct BvhBuffers {
     void* sort_tmp = nullptr;
     size_t sort_tmp_bytes = 0;
     int capacity = 0;
+    // 32-wide tree collapsed from the binary one (rebuilt with it)
+    float* wnodes = nullptr;         // n_wide x WideLayout<dim>::kFloats
+    int* wsrc = nullptr;             // per slot: (binary parent << 1 | side) of the child's box, -1 unused
+    int* winfo = nullptr;            // device: n_wide, max binary depth
+    int n_wide = 0, wide_depth = 0, wide_cap = 0;
+    bool wide_ok = false;            // the warp-wide search fits its stack on this tree
 };
 
 cudaError_t bvh_reserve(BvhBuffers& b, int dim, int n_elem);
@@ -122,11 +130,12 @@ struct WalkLaunch {
     int block_size;
     int blocks_per_sm;
     int n_sm;
+    int traversal = 0;          // 2: warp-wide search (every problem of the launch has wide_ok)
 };
 cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_probs,
                          unsigned long long total_work, DevCounters* d_counters, cudaStream_t stream,
                          int* blocks_used);
-int walk_max_blocks_per_sm(int dim, int block_size);
+int walk_max_blocks_per_sm(int dim, int block_size, int traversal = 0);
 
 // Estimator reductions (estimators.cu).
 cudaError_t launch_reduce_u(const dwos_record* rec, int n_points, int W, double* mean, double* se,

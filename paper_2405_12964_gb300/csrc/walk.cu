@@ -68,11 +68,22 @@ struct WarpStats {
     unsigned nodes = 0, prims = 0;
 };
 
+// Dynamic shared memory: the problem descriptors, then (warp-wide search only)
+// one traversal stack per warp.
+__host__ __device__ inline size_t walk_smem_bytes(int n_probs, int block_size, int traversal) {
+    size_t b = (sizeof(DevProblem) * (size_t)n_probs + 15) & ~(size_t)15;
+    if (traversal == 2) b += sizeof(float2) * kWideStack * (size_t)(block_size / 32);
+    return b;
+}
+
 template <int DIM>
 __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevProblem* __restrict__ g_probs, int n_probs,
-                                                   unsigned long long total, DevCounters* __restrict__ ctr) {
+                                                   unsigned long long total, DevCounters* __restrict__ ctr,
+                                                   int wide) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DevProblem* sp = reinterpret_cast<DevProblem*>(smem_raw);
+    float2* stk = reinterpret_cast<float2*>(smem_raw + walk_smem_bytes(n_probs, 0, 0)) +
+                  (size_t)(threadIdx.x >> 5) * kWideStack;
     {
         const int words = (int)(sizeof(DevProblem) / sizeof(int)) * n_probs;
         const int* src = reinterpret_cast<const int*>(g_probs);
@@ -134,19 +145,30 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevPr
             }
         }
         if (!__any_sync(kFull, active)) break;
+
+        // ---- DistanceToBoundary, seeded with the previous closest element
+        float best2 = kInf;
+        int best = -1;
+        if (wide) {   // all lanes search the 32-wide tree together, one lane's query at a time
+            const DevProblem& Pw = sp[prob];
+            if (active) {
+                if (hint >= 0) { best2 = prim_dist2<DIM>(Pw.prims, hint, x); best = hint; ++st.prims; }
+                big_closest<DIM>(Pw.prims, Pw.n_tree, Pw.n_big, x, best2, best, st.prims);
+            }
+            const WideView wv{Pw.wnodes, Pw.prims, Pw.n_wide, Pw.n_tree};
+            error |= wide_closest<DIM>(wv, __ballot_sync(kFull, active), x, best2, best, stk, st.nodes, st.prims) & 1;
+        }
         if (!active) continue;
 
         const DevProblem& P = sp[prob];
         const unsigned long long local = gw - P.work_begin;
-
-        // ---- DistanceToBoundary, seeded with the previous closest element
-        BvhView bvh{P.nodes, P.prims, P.root, P.n_internal, P.n_tree, P.n_big, P.traversal, P.leaf_parent,
-                    P.node_cell, P.r_max};
-        float best2 = kInf;
-        int best = -1;
-        if (hint >= 0) { best2 = prim_dist2<DIM>(P.prims, hint, x); best = hint; }
-        if (hint >= 0) ++st.prims;
-        if (!closest_leaf<DIM>(bvh, x, best2, best, st.nodes, st.prims)) error |= 1;
+        if (!wide) {
+            BvhView bvh{P.nodes, P.prims, P.root, P.n_internal, P.n_tree, P.n_big, P.traversal, P.leaf_parent,
+                        P.node_cell, P.r_max};
+            if (hint >= 0) { best2 = prim_dist2<DIM>(P.prims, hint, x); best = hint; }
+            if (hint >= 0) ++st.prims;
+            if (!closest_leaf<DIM>(bvh, x, best2, best, st.nodes, st.prims)) error |= 1;
+        }
         const float d = sqrtf(best2);
         const uint32_t k_step = (uint32_t)step;
         ++step;
@@ -361,9 +383,9 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevPr
 
 }  // namespace
 
-int walk_max_blocks_per_sm(int dim, int block_size) {
+int walk_max_blocks_per_sm(int dim, int block_size, int traversal) {
     int n = 0;
-    const size_t smem = sizeof(DevProblem);
+    const size_t smem = walk_smem_bytes(1, block_size, traversal);
     if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<2>, block_size, smem);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<3>, block_size, smem);
     return n;
@@ -374,16 +396,29 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
     if (n_probs < 1 || n_probs > kMaxProblems) return cudaErrorInvalidValue;
     if (total == 0) { if (blocks_used) *blocks_used = 0; return cudaSuccess; }
     const int bs = L.block_size;
-    int per_sm = L.blocks_per_sm > 0 ? L.blocks_per_sm : walk_max_blocks_per_sm(L.dim, bs);
+    int per_sm = L.blocks_per_sm > 0 ? L.blocks_per_sm : walk_max_blocks_per_sm(L.dim, bs, L.traversal);
     if (per_sm < 1) per_sm = 1;
     long long blocks = (long long)per_sm * L.n_sm;
     const long long need = (long long)((total + bs - 1) / bs);
     if (blocks > need) blocks = need;
     if (blocks < 1) blocks = 1;
     if (blocks_used) *blocks_used = (int)blocks;
-    const size_t smem = sizeof(DevProblem) * (size_t)n_probs;
-    if (L.dim == 2) walk_kernel<2><<<(int)blocks, bs, smem, stream>>>(d_probs, n_probs, total, d_counters);
-    else walk_kernel<3><<<(int)blocks, bs, smem, stream>>>(d_probs, n_probs, total, d_counters);
+    if (bs % 32 != 0) return cudaErrorInvalidValue;
+    const int wide = L.traversal == 2 ? 1 : 0;
+    const size_t smem = walk_smem_bytes(n_probs, bs, L.traversal);
+    if (L.dim == 2) {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(walk_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        walk_kernel<2><<<(int)blocks, bs, smem, stream>>>(d_probs, n_probs, total, d_counters, wide);
+    } else {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(walk_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        walk_kernel<3><<<(int)blocks, bs, smem, stream>>>(d_probs, n_probs, total, d_counters, wide);
+    }
     return cudaGetLastError();
 }
 

@@ -108,8 +108,9 @@ def test_philox_bit_exact(Solver):
         assert np.array_equal(got[i], oracle.philox4x32_10(ctrs[i], key))
 
 
+@pytest.mark.parametrize("traversal", [0, 2])
 @pytest.mark.parametrize("which", ["disk", "star", "sphere", "ball_small"])
-def test_closest_point_matches_brute_force(Solver, which):
+def test_closest_point_matches_brute_force(Solver, which, traversal):
     rng = np.random.default_rng(1)
     if which == "disk":
         sc = scenes.disk_scene("screened_1")
@@ -124,7 +125,7 @@ def test_closest_point_matches_brute_force(Solver, which):
         sc = scenes.ball_scene(freq=3)
         p = rng.uniform(-1.2, 1.2, size=(2000, 3))
     s = Solver(0)
-    s.load_scene(sc)
+    s.load_scene(sc, traversal=traversal)
     d, e, b = (t.cpu().numpy() for t in s.closest_point(p))
     do, xo, eo, bo = oracle.closest_point(to_oracle(sc), p)
     assert np.allclose(d, do, rtol=2e-5, atol=2e-6)
@@ -170,19 +171,38 @@ def test_disk_per_walk_replay(Solver, variant):
     check_walks(sc, g, o)
 
 
-def test_star_box_per_walk_replay_with_nested_walks(Solver):
+@pytest.mark.parametrize("traversal", [0, 2])
+def test_star_box_per_walk_replay_with_nested_walks(Solver, traversal):
     sc = scenes.star_box_scene(n_seg=4096, n_query=24)
-    s, g, o = run_pair(Solver, sc, 32, K=2)
+    s, g, o = run_pair(Solver, sc, 32, K=2, traversal=traversal)
     same = check_walks(sc, g, o)
     # debug outputs: du/dn and the oracle's agree on matching walks
     dd = g["debug"]["dudn"].astype(np.float64)
     assert np.all(np.abs(dd - o["dudn"])[same] <= 1e-3 * (1 + np.abs(o["dudn"][same])))
 
 
-def test_sphere_3d_per_walk_replay_with_source(Solver):
+@pytest.mark.parametrize("traversal", [0, 2])
+def test_sphere_3d_per_walk_replay_with_source(Solver, traversal):
     sc = scenes.sh_sphere_scene(freq=16, n_query=12, K=2)
-    s, g, o = run_pair(Solver, sc, 24)
+    s, g, o = run_pair(Solver, sc, 24, traversal=traversal)
     check_walks(sc, g, o, max_flip=0.02)
+
+
+def test_warp_wide_search_is_the_one_that_ran(Solver):
+    # same walks, same results; the 32-wide tree needs far fewer node visits
+    sc = scenes.sh_sphere_scene(freq=40, n_query=64)
+    out, nodes = [], []
+    for t in (0, 2):
+        s = Solver(0)
+        s.load_scene(sc, traversal=t)
+        out.append(s.walk_records(sc.query, 64)["rec"])
+        st = s.stats()
+        nodes.append(st["nodes_visited"] / (st["steps_main"] + st["steps_nested"]))
+    same = out[0]["elem"] == out[1]["elem"]
+    assert same.mean() > 0.99
+    assert np.allclose(out[0]["u"][same], out[1]["u"][same], rtol=1e-5, atol=1e-6)
+    print("node visits per query: binary %.1f, 32-wide %.1f" % tuple(nodes))
+    assert nodes[1] < 0.5 * nodes[0]
 
 
 def test_forward_only_walks_match(Solver):
@@ -318,7 +338,7 @@ def test_capped_walks_are_counted(Solver):
     assert ((g["trace"][:, 0] & 0x3FFFFFFF) <= 3).all()
 
 
-@pytest.mark.parametrize("traversal", [0, 1])
+@pytest.mark.parametrize("traversal", [0, 1, 2])
 @pytest.mark.parametrize("which", ["star", "sphere"])
 def test_hinted_closest_point_equals_unhinted(Solver, which, traversal):
     # the walk seeds each query with the previous hit and climbs the BVH from it,
