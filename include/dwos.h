@@ -100,12 +100,18 @@ typedef struct {
                            bits 24-25: its termination kind */
 } dwos_record;
 
-/* Optional per-walk diagnostics of a differential walk (32 bytes). */
+/* Optional per-walk diagnostics of a differential walk (48 bytes).  With a
+ * nested control-variate table (q, t) at the main walk's element e,
+ * u_off = u_plain - q disp_n - disp_t; without one u_off = u_plain. */
 typedef struct {
-    float dudn;         /* (g(xbar) - mean nested estimate) / h */
+    float dudn;         /* (g(xbar) - u_off) / h */
     float n[3];         /* oriented normal at xbar */
-    float u_off;        /* mean of the K nested estimates at xbar - h n */
+    float u_off;        /* mean of the K nested estimates at x_off = xbar - h n (corrected) */
     float xbar[3];      /* closest boundary point where the main walk stopped */
+    float u_plain;      /* mean of the K nested estimates, uncorrected */
+    float disp_n;       /* mean over the nested walks of n . (x_end - x_off) */
+    float disp_t;       /* mean over the nested walks of t . (x_end - x_off) (0 without a table) */
+    int32_t elem;       /* the main walk's terminal element, -1 if none */
 } dwos_walk_debug;
 
 typedef struct {

@@ -83,6 +83,9 @@ class _WalkOut(ctypes.Structure):
         ("steps", ctypes.POINTER(ctypes.c_int)),
         ("x1", ctypes.POINTER(ctypes.c_double)),
         ("x_end", ctypes.POINTER(ctypes.c_double)),
+        ("u_plain", ctypes.POINTER(ctypes.c_double)),
+        ("disp_n", ctypes.POINTER(ctypes.c_double)),
+        ("disp_t", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -249,7 +252,9 @@ def run_walks(prob: Problem, xq: np.ndarray, walks_per_point: int, differential:
     indexed by p * W + w.  Returns u_hat, x1 (the main walk's point after its
     first sphere step, NaN if it never moved), x_end (where the main walk
     stopped) and, for differential walks, udot
-    (n x N), dudn, u_off, elem, bary, normal, xbar, kind and steps
+    (n x N), dudn, u_off, u_plain, disp_n, disp_t (the nested walks' mean
+    estimate without the control variate and their mean normal / tangential
+    displacements), elem, bary, normal, xbar, kind and steps
     ((K + 1) slots: the main walk, then the nested walks).
     """
     xq = np.ascontiguousarray(xq, dtype=np.float64).reshape(-1, prob.dim)
@@ -271,6 +276,9 @@ def run_walks(prob: Problem, xq: np.ndarray, walks_per_point: int, differential:
         out["dudn"] = np.zeros(n)
         out["u_off"] = np.zeros(n)
         out["normal"] = np.zeros((n, 3))
+        out["u_plain"] = np.zeros(n)
+        out["disp_n"] = np.zeros(n)
+        out["disp_t"] = np.zeros(n)
     o = _WalkOut()
     o.u_hat = _dp(out["u_hat"])
     o.udot = _dp(out.get("udot")) if P > 0 and differential else None
@@ -284,6 +292,9 @@ def run_walks(prob: Problem, xq: np.ndarray, walks_per_point: int, differential:
     o.steps = _ip(out["steps"])
     o.x1 = _dp(out["x1"])
     o.x_end = _dp(out["x_end"])
+    o.u_plain = _dp(out.get("u_plain"))
+    o.disp_n = _dp(out.get("disp_n"))
+    o.disp_t = _dp(out.get("disp_t"))
     s = prob._struct()
     rc = lib().oracle_run_walks(ctypes.byref(s), xq.shape[0], _dp(xq), walks_per_point,
                                 walk_id_base, 1 if differential else 0, threads, ctypes.byref(o))

@@ -462,6 +462,9 @@ typedef struct {
     int* steps;        /* n * (K + 1) */
     double* x1;        /* n * 3: main walk's point after its first step (NaN if none) */
     double* x_end;     /* n * 3: main walk's point where it stopped */
+    double* u_plain;   /* n: mean of the nested estimates without the control variate */
+    double* disp_n;    /* n: mean over the nested walks of n . (x_end - x_off) */
+    double* disp_t;    /* n: mean over the nested walks of t . (x_end - x_off) (0 without a table) */
 } oracle_walk_out;
 
 /* Algorithm 2 (DiffWalkOnSpheres) extended, as Sec. 4.1 observation 2
@@ -488,6 +491,9 @@ static void run_one(const oracle_scene* s, const double* x0, uint64_t walk_id, i
     if (o->udot) for (int j = 0; j < P; ++j) o->udot[idx * P + j] = 0;
     if (o->dudn) o->dudn[idx] = 0;
     if (o->u_off) o->u_off[idx] = 0;
+    if (o->u_plain) o->u_plain[idx] = 0;
+    if (o->disp_n) o->disp_n[idx] = 0;
+    if (o->disp_t) o->disp_t[idx] = 0;
     if (o->normal) for (int i = 0; i < 3; ++i) o->normal[3 * idx + i] = 0;
     if (main.kind == KIND_ROULETTE) return;   /* Algorithm 2: roulette returns 0 */
 
@@ -501,15 +507,21 @@ static void run_one(const oracle_scene* s, const double* x0, uint64_t walk_id, i
     /* offset point and nested forward walks */
     double xoff[3] = {0, 0, 0};
     for (int i = 0; i < s->dim; ++i) xoff[i] = main.xbar[i] - s->h * n[i];
-    double sum = 0;
+    double sum = 0, sum_plain = 0, sum_dn = 0, sum_dt = 0;
     const double* q_cv = s->cv_elem ? s->cv_elem + 4 * (size_t)main.e : NULL;
     for (int j = 1; j <= s->K; ++j) {
         PhaseResult nr = forward_walk(s, xoff, walk_id, (uint32_t)j);
         /* control variate: (q n + t) . (x_end - x_off) has mean zero */
-        double disp = 0;
-        if (q_cv)
-            for (int i = 0; i < s->dim; ++i) disp += (q_cv[0] * n[i] + q_cv[1 + i]) * (nr.x_last[i] - xoff[i]);
+        double disp = 0, dn = 0, dt = 0;
+        for (int i = 0; i < s->dim; ++i) dn += n[i] * (nr.x_last[i] - xoff[i]);
+        if (q_cv) {
+            for (int i = 0; i < s->dim; ++i) dt += q_cv[1 + i] * (nr.x_last[i] - xoff[i]);
+            disp = q_cv[0] * dn + dt;
+        }
         sum += nr.u - disp;
+        sum_plain += nr.u;
+        sum_dn += dn;
+        sum_dt += dt;
         if (o->kind) o->kind[idx * slots + j] = nr.kind;
         if (o->steps) o->steps[idx * slots + j] = nr.steps;
     }
@@ -518,6 +530,9 @@ static void run_one(const oracle_scene* s, const double* x0, uint64_t walk_id, i
     double dudn = (g - ubar) / s->h;     /* Eq. (dudn_fd_estimate) */
     if (o->dudn) o->dudn[idx] = dudn;
     if (o->u_off) o->u_off[idx] = ubar;
+    if (o->u_plain) o->u_plain[idx] = sum_plain / s->K;
+    if (o->disp_n) o->disp_n[idx] = sum_dn / s->K;
+    if (o->disp_t) o->disp_t[idx] = sum_dt / s->K;
     if (o->normal) for (int i = 0; i < 3; ++i) o->normal[3 * idx + i] = n[i];
 
     if (!o->udot || P == 0) return;

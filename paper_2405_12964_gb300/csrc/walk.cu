@@ -63,8 +63,8 @@ __device__ __forceinline__ void leaf_geometry(const float4* __restrict__ prims, 
     }
 }
 
-struct WarpStats {
-    unsigned long long steps_main = 0, steps_nested = 0, capped = 0;
+struct WarpStats {             // per lane; summed over the warp in 64 bits at the end
+    unsigned steps_main = 0, steps_nested = 0, capped = 0;
     unsigned nodes = 0, prims = 0;
 };
 
@@ -76,10 +76,11 @@ __host__ __device__ inline size_t walk_smem_bytes(int n_probs, int block_size, i
     return b;
 }
 
-template <int DIM>
-__global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevProblem* __restrict__ g_probs, int n_probs,
-                                                   unsigned long long total, DevCounters* __restrict__ ctr,
-                                                   int wide) {
+template <int DIM, bool WIDE>
+__global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
+    walk_kernel(const DevProblem* __restrict__ g_probs, int n_probs, unsigned long long total,
+                DevCounters* __restrict__ ctr) {
+    constexpr bool wide = WIDE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DevProblem* sp = reinterpret_cast<DevProblem*>(smem_raw);
     float2* stk = reinterpret_cast<float2*>(smem_raw + walk_smem_bytes(n_probs, 0, 0)) +
@@ -102,8 +103,8 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevPr
     int prob = 0, phase = 0, step = 0, hint = -1;
     float x[DIM], acc = 0.0f;
     // main-walk results kept while the nested walks run
-    float u_main = 0.0f, g_main = 0.0f, b1 = 0.0f, b2 = 0.0f, sum_nested = 0.0f;
-    float4 q_cv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    float u_main = 0.0f, g_main = 0.0f, b1 = 0.0f, b2 = 0.0f;
+    float sum_plain = 0.0f, sum_dn = 0.0f, sum_dt = 0.0f;   // nested walks: estimates, n / t displacements
     int leaf_main = -1, e_main = -1;
     uint32_t meta_main = 0;
     float nrm[DIM], cb[DIM], xoff[DIM];
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevPr
                     } else {
 #pragma unroll
                         for (int k = 0; k < DIM; ++k) x[k] = __ldg(P.xq + (size_t)DIM * point + k);
-                        phase = 0; step = 0; hint = -1; acc = 0.0f; sum_nested = 0.0f;
+                        phase = 0; step = 0; hint = -1; acc = 0.0f;
                         active = true;
                     }
                 } else {
@@ -253,6 +254,8 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevPr
                         dwos_walk_debug z;
                         z.dudn = 0.0f; z.u_off = 0.0f;
                         for (int k = 0; k < 3; ++k) { z.n[k] = 0.0f; z.xbar[k] = k < DIM ? xbar[k] * (kind != DWOS_KIND_ROULETTE) : 0.0f; }
+                        z.u_plain = 0.0f; z.disp_n = 0.0f; z.disp_t = 0.0f;
+                        z.elem = kind == DWOS_KIND_ROULETTE ? -1 : e;
                         P.dbg[local] = z;
                     }
                 }
@@ -314,18 +317,27 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevPr
 #pragma unroll
             for (int k = 0; k < DIM; ++k) xoff[k] = fmaf(-P.h, nrm[k], xbar[k]);
             g_main = g; b1 = w1; b2 = w2; leaf_main = best; e_main = e;
-            sum_nested = 0.0f;
-            if (P.cv_elem) q_cv = __ldg(P.cv_elem + e);
+            sum_plain = 0.0f; sum_dn = 0.0f; sum_dt = 0.0f;
         } else {
             // nested control variate: (q n + t) . (x_end - x_off) has mean zero (every
             // move's direction is uniform and independent of whether the move happens)
-            const float tv[3] = {q_cv.y, q_cv.z, q_cv.w};
-            float disp = 0.0f;
+            float dn = 0.0f, dt = 0.0f;
 #pragma unroll
-            for (int k = 0; k < DIM; ++k) disp = fmaf(fmaf(q_cv.x, nrm[k], tv[k]), x[k] - xoff[k], disp);
-            sum_nested += acc + g - disp;
+            for (int k = 0; k < DIM; ++k) dn = fmaf(nrm[k], x[k] - xoff[k], dn);
+            float q = 0.0f;
+            if (P.cv_elem) {
+                const float4 qc = __ldg(P.cv_elem + e_main);
+                const float tv[3] = {qc.y, qc.z, qc.w};
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) dt = fmaf(tv[k], x[k] - xoff[k], dt);
+                q = qc.x;
+            }
+            sum_plain += acc + g;
+            sum_dn += dn;
+            sum_dt += dt;
             if (phase == P.K) {   // Eq. (wos_deriv), shell case, with Eq. (dudn_fd_estimate)
-                const float u_off = sum_nested / (float)P.K;
+                const float inv_k = 1.0f / (float)P.K;
+                const float u_off = (sum_plain - fmaf(q, sum_dn, sum_dt)) * inv_k;
                 const float dudn = (g_main - u_off) * P.inv_h;
                 dwos_record r;
                 r.u = u_main;
@@ -344,6 +356,10 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevPr
                         z.n[k] = k < DIM ? nrm[k] : 0.0f;
                         z.xbar[k] = k < DIM ? fmaf(P.h, nrm[k], xoff[k]) : 0.0f;
                     }
+                    z.u_plain = sum_plain * inv_k;
+                    z.disp_n = sum_dn * inv_k;
+                    z.disp_t = sum_dt * inv_k;
+                    z.elem = e_main;
                     P.dbg[local] = z;
                 }
                 active = false;
@@ -360,10 +376,11 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevPr
     }
 
     // ---- statistics: one atomic per warp
+    unsigned long long sm = st.steps_main, sn = st.steps_nested, sc = st.capped;
     for (int o = 16; o > 0; o >>= 1) {
-        st.steps_main += __shfl_xor_sync(kFull, st.steps_main, o);
-        st.steps_nested += __shfl_xor_sync(kFull, st.steps_nested, o);
-        st.capped += __shfl_xor_sync(kFull, st.capped, o);
+        sm += __shfl_xor_sync(kFull, sm, o);
+        sn += __shfl_xor_sync(kFull, sn, o);
+        sc += __shfl_xor_sync(kFull, sc, o);
         error |= __shfl_xor_sync(kFull, error, o);
     }
     unsigned long long nodes = st.nodes, prims = st.prims;
@@ -372,11 +389,11 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevPr
         prims += __shfl_xor_sync(kFull, prims, o);
     }
     if (lane == 0) {
-        atomicAdd(&ctr->steps_main, st.steps_main);
-        atomicAdd(&ctr->steps_nested, st.steps_nested);
+        atomicAdd(&ctr->steps_main, sm);
+        atomicAdd(&ctr->steps_nested, sn);
         atomicAdd(&ctr->nodes, nodes);
         atomicAdd(&ctr->prims, prims);
-        if (st.capped) atomicAdd(&ctr->capped, st.capped);
+        if (sc) atomicAdd(&ctr->capped, sc);
         if (error) atomicOr(&ctr->error, error);
     }
 }
@@ -386,8 +403,13 @@ __global__ void __launch_bounds__(256, DIM == 2 ? 4 : 3) walk_kernel(const DevPr
 int walk_max_blocks_per_sm(int dim, int block_size, int traversal) {
     int n = 0;
     const size_t smem = walk_smem_bytes(1, block_size, traversal);
-    if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<2>, block_size, smem);
-    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<3>, block_size, smem);
+    if (traversal == 2) {
+        if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<2, true>, block_size, smem);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<3, true>, block_size, smem);
+    } else {
+        if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<2, false>, block_size, smem);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<3, false>, block_size, smem);
+    }
     return n;
 }
 
@@ -404,22 +426,17 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
     if (blocks < 1) blocks = 1;
     if (blocks_used) *blocks_used = (int)blocks;
     if (bs % 32 != 0) return cudaErrorInvalidValue;
-    const int wide = L.traversal == 2 ? 1 : 0;
     const size_t smem = walk_smem_bytes(n_probs, bs, L.traversal);
-    if (L.dim == 2) {
+    auto go = [&](auto kernel) -> cudaError_t {
         if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(walk_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        walk_kernel<2><<<(int)blocks, bs, smem, stream>>>(d_probs, n_probs, total, d_counters, wide);
-    } else {
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(walk_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-        }
-        walk_kernel<3><<<(int)blocks, bs, smem, stream>>>(d_probs, n_probs, total, d_counters, wide);
-    }
-    return cudaGetLastError();
+        kernel<<<(int)blocks, bs, smem, stream>>>(d_probs, n_probs, total, d_counters);
+        return cudaGetLastError();
+    };
+    if (L.traversal == 2) return L.dim == 2 ? go(walk_kernel<2, true>) : go(walk_kernel<3, true>);
+    return L.dim == 2 ? go(walk_kernel<2, false>) : go(walk_kernel<3, false>);
 }
 
 }  // namespace dwos

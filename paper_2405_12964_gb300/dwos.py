@@ -26,7 +26,8 @@ STATUS = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "STEP_LIMIT", 5: "T
 
 RECORD_DTYPE = np.dtype([("u", "<f4"), ("elem", "<i4"), ("b1", "<f4"), ("b2", "<f4"),
                          ("c", "<f4", (3,)), ("meta", "<u4")])
-DEBUG_DTYPE = np.dtype([("dudn", "<f4"), ("n", "<f4", (3,)), ("u_off", "<f4"), ("xbar", "<f4", (3,))])
+DEBUG_DTYPE = np.dtype([("dudn", "<f4"), ("n", "<f4", (3,)), ("u_off", "<f4"), ("xbar", "<f4", (3,)),
+                        ("u_plain", "<f4"), ("disp_n", "<f4"), ("disp_t", "<f4"), ("elem", "<i4")])
 
 
 class Options(ctypes.Structure):
@@ -283,7 +284,7 @@ class Solver:
         g = torch.empty(max(self.n_param, 1), **dd)
         se = torch.empty(2, n, **dd)
         smp = torch.empty(n * int(walks), 4, device=self.device, dtype=torch.float32) if samples else None
-        dbg = torch.empty(n * int(walks) * 32, device=self.device, dtype=torch.uint8) if debug else None
+        dbg = torch.empty(n * int(walks) * DEBUG_DTYPE.itemsize, device=self.device, dtype=torch.uint8) if debug else None
         self._check(lib().dwos_grad_l2_cv(self._h, n, _ptr(x), _ptr(ur), int(walks), int(walk_id_base), _ptr(cg),
                                           1 if whole_walk else 0, _ptr(cq), _ptr(smp), _ptr(dbg), _ptr(loss), _ptr(g),
                                           _ptr(se)))
@@ -303,7 +304,7 @@ class Solver:
         rec = torch.empty(n * 32, device=self.device, dtype=torch.uint8)
         K1 = self.opt.K + 1
         tr = torch.empty(n * K1, device=self.device, dtype=torch.int32) if trace else None
-        db = torch.empty(n * 32, device=self.device, dtype=torch.uint8) if debug else None
+        db = torch.empty(n * DEBUG_DTYPE.itemsize, device=self.device, dtype=torch.uint8) if debug else None
         self._check(lib().dwos_walk_records(self._h, x.shape[0], _ptr(x), int(walks), int(walk_id_base),
                                             1 if differential else 0, _ptr(rec), _ptr(tr), _ptr(db), MEM_DEVICE))
         self.sync()

@@ -7,8 +7,9 @@ estimate dL/dtheta of L = 1/2 sum_p (u_p(theta) - uref_p)^2 with fresh walks
 schedule of Eq. (update_rule), read with t/T in the exponent.
 
 Optionally a learned control variate (the library's tensor-core MLP) is trained
-online on the walks' own estimates: (x1, estimate of u at x1) for the u head and
-(xbar, du/dn) for the du/dn head, and its spatial gradient at the observation
+online on the walks' own estimates: (x1, estimate of u at x1) for the u head,
+and for the du/dn head the nested walks' estimates and displacements (a
+variance-minimising least-squares fit), and its spatial gradient at the observation
 points is subtracted from every walk's estimate (dwos_grad_l2_cv); the nested
 walks behind each du/dn estimate subtract (q n + t) . (x_end - x_off) with q the
 du/dn head at the element and t the data's tangential gradient.  Both
@@ -69,10 +70,10 @@ class ControlVariateTrainer:
     """Online training of the control-variate network on walk samples."""
 
     def __init__(self, device: int = 0, seed: int = 0, lr: float = 2e-3, iters: int = 20, max_samples: int = 65536,
-                 q_weight: float = 0.05):
+                 q_weight: float = 0.2):
         self.net = dwos.ControlVariateNet(device, seed=seed)
         self.lr, self.iters, self.max_samples = lr, iters, max_samples
-        self.q_weight = q_weight     # du/dn targets carry 1/h-amplified noise: weight their loss down
+        self.q_weight = q_weight     # weight of the du/dn head's (normalised) variance loss against the u head's
         self.rng = np.random.default_rng(seed)
 
     def update(self, samples: torch.Tensor, debug: Optional[torch.Tensor]) -> float:
@@ -83,12 +84,22 @@ class ControlVariateTrainer:
         parts_t = [torch.stack([tu, torch.zeros_like(tu)], 1)]
         parts_m = [torch.stack([torch.ones_like(tu), torch.zeros_like(tu)], 1)]
         if debug is not None:
-            rec = debug.view(torch.float32).view(-1, 8)      # dwos_walk_debug: dudn, n[3], u_off, xbar[3]
-            dudn, xb = rec[:, 0], rec[:, 5:7]
-            hit = (rec[:, 1] != 0) | (rec[:, 2] != 0)
-            parts_x.append(xb[hit])
-            parts_t.append(torch.stack([torch.zeros_like(dudn[hit]), dudn[hit]], 1))
-            parts_m.append(torch.stack([torch.zeros_like(dudn[hit]), torch.full_like(dudn[hit], self.q_weight)], 1))
+            # dwos_walk_debug: dudn, n[3], u_off, xbar[3], u_plain, disp_n, disp_t, elem
+            rec = debug.view(torch.float32).view(-1, 12)
+            xb, u_plain, dn, dt = rec[:, 5:7], rec[:, 8], rec[:, 9], rec[:, 10]
+            hit = ((rec[:, 1] != 0) | (rec[:, 2] != 0)) & (dn.abs() > 1e-7)
+            if bool(hit.any()):
+                # The du/dn head q weights the nested walks' normal displacement; the
+                # corrected nested mean u_plain - disp_t - q disp_n keeps its mean for
+                # any q and has the least variance where q minimises
+                # E[(u_plain - disp_t - q disp_n)^2] = E[disp_n^2 (q - (u_plain - disp_t) / disp_n)^2]:
+                # a weighted least-squares fit (the normal derivative itself where u is
+                # linear on the scale of the nested walks).
+                d, y = dn[hit], (u_plain[hit] - dt[hit]) / dn[hit]
+                w = torch.sqrt(self.q_weight / (d * d).mean()) * d.abs()
+                parts_x.append(xb[hit])
+                parts_t.append(torch.stack([torch.zeros_like(y), y], 1))
+                parts_m.append(torch.stack([torch.zeros_like(w), w], 1))
         x = torch.cat(parts_x)
         t = torch.cat(parts_t)
         m = torch.cat(parts_m)

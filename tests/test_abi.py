@@ -54,7 +54,7 @@ def test_default_options_and_null_context_errors(libdwos):
 def test_record_layouts_are_32_bytes():
     from paper_2405_12964_gb300 import dwos
     assert dwos.RECORD_DTYPE.itemsize == 32
-    assert dwos.DEBUG_DTYPE.itemsize == 32
+    assert dwos.DEBUG_DTYPE.itemsize == 48
     assert ctypes.sizeof(dwos.Options) == 48
 
 

@@ -146,7 +146,7 @@ def test_nested_cv_table_matches_oracle(env):
     o = oracle.run_walks(to_oracle(sc, cv_elem=tab.astype(np.float64)), sc.query, sc.walks, differential=True)
     same = branch_match(sc, recs, o)
     assert same.mean() > 0.97
-    dbg = out["debug"].view(torch.float32).view(-1, 8).cpu().numpy().astype(np.float64)
+    dbg = out["debug"].view(torch.float32).view(-1, 12).cpu().numpy().astype(np.float64)
     dd = dbg[:, 0]
     # The correction is continuous in the walk positions, so unlike u (piecewise-constant
     # data) it also shows how far the FP32 walk drifted from the FP64 one.  The ball-step map
@@ -167,6 +167,14 @@ def test_nested_cv_table_matches_oracle(env):
           % (tight.sum(), tight.size, ok[tight].mean(), np.median(err[tight]), (err / tol)[tight].max()))
     assert ok[tight].mean() >= 0.98
     assert np.median(err[tight]) < 1e-4
+    # the record's parts: uncorrected nested mean and the mean displacements
+    pos = 2e-6 + 5e-7 * nested_steps.sum(1)
+    for name, col, scale in (("u_plain", 8, 1e-5), ("disp_n", 9, 0.0), ("disp_t", 10, 0.0)):
+        lim = scale + pos * (gmax if name == "disp_t" else 1.0)
+        okp = np.abs(dbg[:, col] - o[name]) <= lim
+        assert okp[tight].mean() >= 0.98, name
+    elem_gpu = out["debug"].view(torch.int32).view(-1, 12)[:, 11].cpu().numpy()
+    assert np.array_equal(elem_gpu[same], o["elem"][same])
     uc = _corrected(o, sc.query, sc.walks, g.astype(np.float64), True)
     go = est.grad_l2_ustat(uc, o["udot"], sc.u_ref, 12, sc.walks, 8)
     gg = out["grad"].cpu().numpy()
@@ -189,7 +197,7 @@ def test_exact_boundary_gradient_collapses_nested_variance(env):
     res = []
     for t in (None, tab):
         out = s.grad_l2_cv(sc.query, uref, sc.walks, cv_elem=t, debug=True)
-        rec = out["debug"].view(torch.float32).view(-1, 8).cpu().numpy().astype(np.float64)
+        rec = out["debug"].view(torch.float32).view(-1, 12).cpu().numpy().astype(np.float64)
         hit = (rec[:, 1] != 0) | (rec[:, 2] != 0)
         res.append(rec[hit, 0] - rec[hit, 1])                      # du/dn minus the closed form n_x
     ratio = res[1].var() / res[0].var()

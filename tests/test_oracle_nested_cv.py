@@ -59,6 +59,11 @@ def test_nested_correction_has_zero_mean():
     o1, _ = _dudn(sc, W, tab)
     # identical walks: u and the boundary hits do not change, only du/dn
     assert np.array_equal(o0["u_hat"], o1["u_hat"]) and np.array_equal(o0["elem"], o1["elem"])
+    # the corrected nested mean is the uncorrected one minus the table's terms
+    assert np.array_equal(o0["u_plain"], o1["u_plain"]) and np.array_equal(o0["disp_n"], o1["disp_n"])
+    assert np.allclose(o0["u_off"], o0["u_plain"]) and np.all(o0["disp_t"] == 0)
+    q = np.where(hit, tab[np.maximum(o1["elem"], 0), 0], 0.0)
+    assert np.allclose(o1["u_off"], o1["u_plain"] - q * o1["disp_n"] - o1["disp_t"], atol=1e-12)
     d = (o1["dudn"] - o0["dudn"])[hit]
     assert d.std() > 1.0                       # the correction is not trivially zero
     z = d.mean() / (d.std(ddof=1) / np.sqrt(d.size))
