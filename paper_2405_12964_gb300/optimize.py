@@ -70,8 +70,9 @@ class ControlVariateTrainer:
     """Online training of the control-variate network on walk samples."""
 
     def __init__(self, device: int = 0, seed: int = 0, lr: float = 2e-3, iters: int = 20, max_samples: int = 65536,
-                 q_weight: float = 0.2):
+                 q_weight: float = 0.2, h: float = 0.02):
         self.net = dwos.ControlVariateNet(device, seed=seed)
+        self.h = h                   # the solver's offset distance (du/dn = (g - u_off) / h)
         self.lr, self.iters, self.max_samples = lr, iters, max_samples
         self.q_weight = q_weight     # weight of the du/dn head's (normalised) variance loss against the u head's
         self.rng = np.random.default_rng(seed)
@@ -86,17 +87,21 @@ class ControlVariateTrainer:
         if debug is not None:
             # dwos_walk_debug: dudn, n[3], u_off, xbar[3], u_plain, disp_n, disp_t, elem
             rec = debug.view(torch.float32).view(-1, 12)
-            xb, u_plain, dn, dt = rec[:, 5:7], rec[:, 8], rec[:, 9], rec[:, 10]
+            dudn, u_off, xb, u_plain, dn, dt = rec[:, 0], rec[:, 4], rec[:, 5:7], rec[:, 8], rec[:, 9], rec[:, 10]
             hit = ((rec[:, 1] != 0) | (rec[:, 2] != 0)) & (dn.abs() > 1e-7)
             if bool(hit.any()):
                 # The du/dn head q weights the nested walks' normal displacement; the
                 # corrected nested mean u_plain - disp_t - q disp_n keeps its mean for
                 # any q and has the least variance where q minimises
-                # E[(u_plain - disp_t - q disp_n)^2] = E[disp_n^2 (q - (u_plain - disp_t) / disp_n)^2]:
-                # a weighted least-squares fit (the normal derivative itself where u is
-                # linear on the scale of the nested walks).
-                d, y = dn[hit], (u_plain[hit] - dt[hit]) / dn[hit]
-                w = torch.sqrt(self.q_weight / (d * d).mean()) * d.abs()
+                # E[(r - q disp_n)^2], r = u_plain - g(xbar) - disp_t, i.e. the
+                # least-squares fit of r / disp_n with weights disp_n^2 (the normal
+                # derivative itself where u is linear on the scale of the nested walks).
+                # Centring on g = u_off + h du/dn keeps the fit's noise at Var(u).
+                g = u_off[hit] + self.h * dudn[hit]
+                d = dn[hit]
+                r = u_plain[hit] - g - dt[hit]
+                y = r / d
+                w = torch.sqrt(self.q_weight / (r * r).mean().clamp_min(1e-12)) * d.abs()
                 parts_x.append(xb[hit])
                 parts_t.append(torch.stack([torch.zeros_like(y), y], 1))
                 parts_m.append(torch.stack([torch.zeros_like(w), w], 1))
@@ -169,7 +174,7 @@ def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 2
     opt = Adam(theta_start, lr=lr)
     hist = History()
     if use_cv and trainer is None:
-        trainer = ControlVariateTrainer(device, seed=seed)
+        trainer = ControlVariateTrainer(device, seed=seed, h=scene.h)
     vref = scene.reference_vertices()
     total = 0.0
     for it in range(steps):
