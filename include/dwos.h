@@ -55,7 +55,7 @@ typedef enum {
     DWOS_ERR_CUDA = 2,            /* a CUDA runtime call failed */
     DWOS_ERR_OOM = 3,             /* device allocation failed */
     DWOS_ERR_STEP_LIMIT = 4,      /* a traversal exceeded its iteration bound */
-    DWOS_ERR_TIMEOUT = 5,         /* reserved for bounded device waits */
+    DWOS_ERR_TIMEOUT = 5,         /* a bounded device wait ran out (the kernel gave up instead of hanging) */
     DWOS_ERR_NOT_IMPLEMENTED = 6,
     DWOS_ERR_STATE = 7,           /* call order: e.g. eval before set_boundary */
     DWOS_ERR_OUTSIDE = 8          /* a query point lies outside Omega */
@@ -320,9 +320,11 @@ dwos_status dwos_batch_stats(dwos_batch* b, dwos_run_stats* out);
  * fixing one; this network is the learned control variate of the 2D
  * shape-from-diffusion workload.  Features (x, y, sin pi x, sin pi y,
  * sin pi (x + y)) -> four tanh layers of 64 -> 8 linear outputs, of which
- * output 0 estimates u and output 1 du/dn.  Training uses the tensor cores:
- * every matrix-product input (weights, activations, deltas) is BF16, sums are
- * FP32; parameters are FP32 with Adam (beta1 0.9, beta2 0.999, eps 1e-8).
+ * output 0 estimates u and output 1 du/dn.  Training and evaluation run on
+ * the tensor cores (tcgen05, accumulators in TMEM): every matrix-product input
+ * (weights, activations, deltas) is BF16, sums are FP32, biases, tanh and the
+ * loss FP32, and tanh' = 1 - a^2 uses the activation as stored (BF16);
+ * parameters are FP32 with Adam (beta1 0.9, beta2 0.999, eps 1e-8).
  * Flat parameter layout: W1 (64 x 16), b1 (64), W2 (64 x 64), b2, W3, b3, W4,
  * b4, W5 (8 x 64), b5 (8), W[out][in] row-major.  Loss: (1/n) sum_s sum_k
  * mask[s][k] (out[s][k] - target[s][k])^2 over k in {0, 1}.  Points x,
@@ -343,9 +345,15 @@ dwos_status dwos_mlp_loss_grad(dwos_mlp* mlp, int n, const float* x, const float
  * loss before the step. */
 dwos_status dwos_mlp_train_step(dwos_mlp* mlp, int n, const float* x, const float* target, const float* mask,
                                 float lr, double* loss, int mem);
-/* Output 0 (u), its gradient d u / d(x, y) (n x 2) and output 1 (du/dn) at n
- * points, with the BF16 weights and FP32 activations; any output may be NULL. */
+/* Output 0 (u), its gradient d u / d(x, y) (n x 2, the backward pass of
+ * output 0 in the same arithmetic) and output 1 (du/dn) at n points; any
+ * output may be NULL. */
 dwos_status dwos_mlp_eval(dwos_mlp* mlp, int n, const float* x, float* u, float* grad_u, float* q, int mem);
+
+/* Wait for the network's queued work and report a tensor-core product that did
+ * not complete within its bounded wait (DWOS_ERR_TIMEOUT; the kernels give up
+ * instead of hanging).  Calls with host buffers check this themselves. */
+dwos_status dwos_mlp_sync(dwos_mlp* mlp);
 
 /* ---- allocation-free evaluation ------------------------------------------
  * The paper has no counterpart to this entry point.  It is dwos_eval for

@@ -6,7 +6,10 @@ four tanh hidden layers of width 64 and a linear output layer of width 8, of
 which outputs 0 (u) and 1 (du/dn) are used.  Tensor-core arithmetic: every
 matrix-product input (weights, layer inputs, back-propagated deltas) is
 rounded to BF16 (round to nearest even); sums are exact here (FP64) and FP32 on
-the GPU; biases, activations and tanh' = 1 - a^2 stay in full precision.
+the GPU; biases, tanh and the loss stay in full precision, and tanh' = 1 - a^2
+is taken from the activation as stored for the next product (BF16).  The
+evaluation (u, its (x, y) gradient and du/dn) follows the same rules: the
+gradient is the backward pass of output 0 through the same rounded products.
 
 Flat parameter layout (FP32 master copy, 14088 values):
     W1 (64 x 16), b1 (64), W2 (64 x 64), b2, W3, b3, W4, b4, W5 (8 x 64), b5 (8)
@@ -94,7 +97,7 @@ def loss_and_grad(params, x, target, mask, rounding: bool = True):
     g["b5"] = delta.sum(0)
     back = r(delta) @ r(P["W5"])                             # (n, 64)
     for l in range(4, 0, -1):
-        d = back * (1.0 - a[l] ** 2)
+        d = back * (1.0 - r(a[l]) ** 2)
         g[f"W{l}"] = r(d).T @ r(a[l - 1])
         g[f"b{l}"] = d.sum(0)
         if l > 1:
@@ -112,19 +115,18 @@ def adam(params, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
 
 
 def eval_u(params, x, rounding: bool = True):
-    """Evaluation precision (BF16 weights, full-precision activations): u head,
-    its gradient with respect to (x, y), and the du/dn head."""
-    bf16_ = bf16 if rounding else _ident
-    P = {k: (bf16_(v) if k.startswith("W") else v) for k, v in unpack(params).items()}
+    """Evaluation: u head, its gradient with respect to (x, y), and the du/dn
+    head, in the training arithmetic (rounding=False: the exact network)."""
+    r = bf16 if rounding else _ident
+    P = unpack(params)
     x = np.asarray(x, dtype=np.float64)
-    f = features(x)
-    a = [f]
-    for l in range(1, 5):
-        a.append(np.tanh(a[-1] @ P[f"W{l}"].T + P[f"b{l}"]))
-    out = a[-1] @ P["W5"].T + P["b5"]
-    back = np.tile(P["W5"][0], (x.shape[0], 1))              # d u / d a4
+    out, a = forward(params, x, rounding)
+    back = np.zeros((x.shape[0], 8))
+    back[:, 0] = 1.0                                         # d u / d out
+    back = r(back) @ r(P["W5"])                              # d u / d a4
     for l in range(4, 0, -1):
-        back = (back * (1.0 - a[l] ** 2)) @ P[f"W{l}"]        # d u / d a_{l-1}
+        d = back * (1.0 - r(a[l]) ** 2)                      # d u / d z_l
+        back = r(d) @ r(P[f"W{l}"])                          # d u / d a_{l-1}
     df = back[:, :5]
     c0, c1, c01 = np.pi * np.cos(np.pi * x[:, 0]), np.pi * np.cos(np.pi * x[:, 1]), np.pi * np.cos(np.pi * (x[:, 0] + x[:, 1]))
     gx = df[:, 0] + df[:, 2] * c0 + df[:, 4] * c01

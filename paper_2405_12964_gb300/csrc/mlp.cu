@@ -1,12 +1,24 @@
 // Control-variate network: features (x, y, sin pi x, sin pi y, sin pi (x+y))
-// -> 4 x 64 tanh -> 8 linear outputs (0: u, 1: du/dn).  Training runs on the
-// tensor cores (mma.sync m16n8k16, BF16 inputs, FP32 accumulation): forward
-// products, the back-propagated deltas and the weight gradients.  Parameters
-// are kept in FP32 (Adam) and copied to BF16 for the products.  Evaluation of
-// u, its spatial gradient and the du/dn head is a scalar FP32 kernel with the
-// BF16 weights (it runs on a few thousand query points).
+// -> 4 x 64 tanh -> 8 linear outputs (0: u, 1: du/dn), trained and evaluated
+// on the 5th-generation tensor cores.
 //
-// Flat parameter layout: W1 (64 x 16), b1 (64), W2 (64 x 64), b2, W3, b3,
+// One persistent kernel (128 threads, one CTA per SM) walks over tiles of 128
+// samples; thread r owns sample row r, which is also TMEM lane r.  Operands
+// live in shared memory as BF16 in the canonical no-swizzle core-matrix
+// layout (8 rows x 16 bytes per 128-byte core matrix), the products are
+// tcgen05.mma (kind::f16, BF16 in, FP32 accumulate) issued by one thread and
+// tracked by an mbarrier, and results come back with tcgen05.ld:
+//   forward     D[128 x 64]  = A_{l-1}[128 x K] W_l^T        (A, B K-major)
+//   backward    D[128 x 64]  = delta_l[128 x K] W_l           (B MN-major: W as stored)
+//   weight grad dW_l[out x in+1] += delta_l^T A_{l-1}          (A, B MN-major)
+// Each activation tile carries a constant-1 column, so the same product also
+// accumulates the bias gradient.  Weight gradients stay in TMEM across all
+// of a CTA's tiles and are written once per CTA; a second kernel sums the CTA
+// partials in a fixed order (no atomics).  The BF16 weight image is copied
+// into shared memory with one bulk asynchronous copy.  Evaluation runs the
+// forward pass and the backward pass of output 0 (d u / d x) the same way.
+//
+// Flat FP32 parameter layout: W1 (64 x 16), b1 (64), W2 (64 x 64), b2, W3, b3,
 // W4, b4, W5 (8 x 64), b5 (8); W[out][in] row-major.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -20,47 +32,152 @@ namespace {
 
 constexpr int H = 64;            // hidden width
 constexpr int IN = 16;           // padded input width
-constexpr int OUT = 8;           // padded output width
+constexpr int OUT = 8;           // output width
+constexpr int OUTP = 16;         // output rows padded for the N = 16 product
 constexpr int NP = DWOS_MLP_NPARAM;
+constexpr int TILE = 128;        // samples per tile (the MMA's M)
+constexpr int THREADS = 128;
 // offsets of W_l and b_l (l = 1..5) in the flat parameter vector
 __host__ __device__ constexpr int off_w(int l) { return l == 1 ? 0 : 1088 + (l - 2) * 4160; }
 __host__ __device__ constexpr int off_b(int l) { return l == 1 ? 1024 : (l == 5 ? 14080 : 1088 + (l - 2) * 4160 + 4096); }
 static_assert(off_b(5) + 8 == DWOS_MLP_NPARAM, "parameter layout");
-constexpr int WARPS = 4;
-constexpr int TILE = 16;                 // samples per warp
-constexpr int BS = WARPS * TILE;         // samples per block
 
-// BF16 weight copies: forward operand W[out][in] and backward operand W^T[in][out_pad]
-struct Bf16Weights {
-    __nv_bfloat16 w1[H * IN];
+// Element offset of (row, col) in a BF16 tile of C columns, canonical
+// no-swizzle layout: core matrix (row / 8, col / 8) is 64 contiguous elements,
+// row-major inside (16 bytes per row); core matrices of one 8-row group are
+// consecutive along the columns (128 bytes apart), groups are C * 16 bytes apart.
+__host__ __device__ constexpr int core_off(int row, int col, int C) {
+    return ((row >> 3) * (C >> 3) + (col >> 3)) * 64 + (row & 7) * 8 + (col & 7);
+}
+
+// BF16 weight image, in the shared-memory layout (one bulk copy).
+struct WImage {
+    __nv_bfloat16 w1[H * IN];        // 64 x 16
     __nv_bfloat16 w2[H * H], w3[H * H], w4[H * H];
-    __nv_bfloat16 w5[OUT * H];
-    __nv_bfloat16 t2[H * H], t3[H * H], t4[H * H];   // t_l[in][out] = W_l[out][in]
-    __nv_bfloat16 t5[H * 16];                        // W5^T padded to 16 outputs
+    __nv_bfloat16 w5[OUTP * H];      // 16 x 64, rows 8..15 zero
+};
+static_assert(sizeof(WImage) % 16 == 0, "bulk copy size");
+
+constexpr int C0 = 32;           // input tile: 16 features, the constant 1 at column 16, zeros
+constexpr int CA = 80;           // hidden tiles: 64 activations, the constant 1 at column 64, zeros
+constexpr int CD = 128;          // delta tile: 64 (or 16) deltas, zeros (rows of the M = 128 weight-gradient product)
+
+struct __align__(1024) Smem {
+    WImage w;                                   // 28672 B
+    __nv_bfloat16 a0[TILE * C0];                // 8 KB
+    __nv_bfloat16 a[4][TILE * CA];              // 4 x 20 KB
+    __nv_bfloat16 d[TILE * CD];                 // 32 KB
+    float bias[4 * H + OUT];
+    unsigned long long bar_load, bar_mma;
+    uint32_t tmem_base;
+    int fail;
 };
 
-struct Smem {
-    Bf16Weights w;
-    float act[5][BS * H];     // layer inputs: act[0] = features (IN wide, stride H), act[l] = a_l
-    float delta[BS * H];      // current layer's delta
-    float loss[WARPS];
-};
+// TMEM columns (512 allocated)
+constexpr uint32_t T_SCR = 0;                   // 64: forward / backward products
+// dW_l with its bias column (32, 80, 80, 80, 80 columns) for l = 1..5
+__host__ __device__ constexpr uint32_t t_dw(int l) { return l == 1 ? 64u : 96u + 80u * (uint32_t)(l - 2); }
+constexpr uint32_t TMEM_COLS = 512;
+
+// ---- PTX wrappers -------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Instruction descriptor, kind::f16: D F32 (bits 4-5 = 1), A and B BF16 (bits
+// 7-9, 10-12 = 1), A / B major-ness (bits 15, 16: 0 K-major, 1 MN-major),
+// N >> 3 (bits 17-22), M >> 4 (bits 24-28).
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool a_mn, bool b_mn) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((a_mn ? 1u : 0u) << 15) | ((b_mn ? 1u : 0u) << 16) |
+           ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading-dimension
+// byte offset (between core matrices along K for K-major operands, along the
+// 8-element K groups for MN-major ones), stride byte offset (the other
+// direction), all >> 4; bit 46 set (descriptor version of this architecture).
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// K-major view of a tile with C columns, K step ks (16 columns)
+__device__ __forceinline__ uint64_t kmajor(const __nv_bfloat16* tile, int C, int ks) {
+    return sdesc(smem_u32(tile) + ks * 256, 128, (C / 8) * 128);
+}
+// MN-major view of a tile with C columns (MN = columns, K = rows), K step ks (16 rows)
+__device__ __forceinline__ uint64_t mnmajor(const __nv_bfloat16* tile, int C, int ks) {
+    return sdesc(smem_u32(tile) + ks * 2 * (C / 8) * 128, (C / 8) * 128, 128);
+}
+
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        :: "r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void bar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bounded wait: false if the phase never completed.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
+    for (int i = 0; i < (1 << 24); ++i)
+        if (bar_try(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 :: "r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
 
 __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t*>(&v);
 }
-
-__device__ __forceinline__ uint32_t ld2(const __nv_bfloat16* p) {   // two adjacent BF16
-    return *reinterpret_cast<const uint32_t*>(p);
+// write 8 values (one core-matrix row) of row r, column chunk cc of a tile with C columns
+__device__ __forceinline__ void put8(__nv_bfloat16* tile, int C, int r, int cc, const float* v) {
+    uint4 q;
+    q.x = pack2(v[0], v[1]); q.y = pack2(v[2], v[3]); q.z = pack2(v[4], v[5]); q.w = pack2(v[6], v[7]);
+    *reinterpret_cast<uint4*>(tile + core_off(r, cc * 8, C)) = q;
 }
-
-__device__ __forceinline__ void mma(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+__device__ __forceinline__ void get8(const __nv_bfloat16* tile, int C, int r, int cc, float* v) {
+    const uint4 q = *reinterpret_cast<const uint4*>(tile + core_off(r, cc * 8, C));
+    const uint32_t w[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&w[i]);
+        v[2 * i] = __low2float(b);
+        v[2 * i + 1] = __high2float(b);
+    }
 }
 
 __device__ __forceinline__ void feats(float x, float y, float* f) {
@@ -71,219 +188,254 @@ __device__ __forceinline__ void feats(float x, float y, float* f) {
     f[4] = sinpif(x + y);
 }
 
-// Masked-MSE gradient over n samples, accumulated into grad (FP32, zeroed by the
-// caller) and loss (FP64 sum).
-__global__ void __launch_bounds__(WARPS * 32) train_kernel(const Bf16Weights* __restrict__ gw,
-                                                           const float* __restrict__ params, int n,
-                                                           const float* __restrict__ x, const float* __restrict__ target,
-                                                           const float* __restrict__ mask, float* __restrict__ grad,
-                                                           double* __restrict__ loss) {
-    extern __shared__ __align__(16) unsigned char raw[];
+enum Mode { kTrain = 0, kEval = 1 };
+
+// mode kTrain: masked-MSE loss (sum over this CTA's samples, FP64, one atomic
+// per warp) and the CTA's gradient partial (NP floats at part + blockIdx.x * NP).
+// mode kEval: u, d u / d (x, y) and du/dn per sample.
+template <int MODE>
+__global__ void __launch_bounds__(THREADS, 1)
+    mlp_kernel(const WImage* __restrict__ wimg, const float* __restrict__ params, int n,
+               const float* __restrict__ x, const float* __restrict__ target, const float* __restrict__ mask,
+               float* __restrict__ part, double* __restrict__ loss, float* __restrict__ u_out,
+               float* __restrict__ g_out, float* __restrict__ q_out, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char raw[];
     Smem& S = *reinterpret_cast<Smem*>(raw);
-    {
-        const int words = sizeof(Bf16Weights) / 4;
-        const int* src = reinterpret_cast<const int*>(gw);
-        int* dst = reinterpret_cast<int*>(&S.w);
-        for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+    const int r = threadIdx.x;                 // sample row and TMEM lane
+    const int warp = r >> 5;
+    const uint32_t bar_load = smem_u32(&S.bar_load), bar_mma = smem_u32(&S.bar_mma);
+    if (r == 0) {
+        bar_init(bar_load, 1);
+        bar_init(bar_mma, 1);
+        S.fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int g = lane >> 2, t = lane & 3;
-    const int s0 = blockIdx.x * BS + warp * TILE;       // first sample of this warp
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     :: "r"(smem_u32(&S.tmem_base)), "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    // constants: biases; zero the columns of the tiles that no tile overwrites
+    for (int i = r; i < 4 * H + OUT; i += THREADS)
+        S.bias[i] = params[i < 4 * H ? off_b(1 + i / H) + i % H : off_b(5) + (i - 4 * H)];
+    {
+        const float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        const float one[8] = {1, 0, 0, 0, 0, 0, 0, 0};
+        put8(S.a0, C0, r, 2, one);
+        put8(S.a0, C0, r, 3, z);
+        for (int l = 0; l < 4; ++l) {
+            put8(S.a[l], CA, r, 8, one);
+            put8(S.a[l], CA, r, 9, z);
+        }
+        for (int cc = 0; cc < CD / 8; ++cc) put8(S.d, CD, r, cc, z);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = S.tmem_base;
+    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+    if (r == 0) {
+        bar_expect_tx(bar_load, sizeof(WImage));
+        bulk_g2s(smem_u32(&S.w), wimg, sizeof(WImage), bar_load);
+    }
+    bool ok = bar_wait(bar_load, 0);
+    ok = !__syncthreads_or(!ok);
+    uint32_t phase = 0;
+    const __nv_bfloat16* W[6] = {nullptr, S.w.w1, S.w.w2, S.w.w3, S.w.w4, S.w.w5};
+    const int CW[6] = {0, IN, H, H, H, H};     // columns of W_l (its K in the forward product)
     const float inv_n = 1.0f / (float)n;
+    float loss_acc = 0.0f;
+    const int n_tiles = (n + TILE - 1) / TILE;
 
-    // ---- features of rows g and g + 8
-    float fr[2][5];
-    bool valid[2];
-    for (int h = 0; h < 2; ++h) {
-        const int s = s0 + g + 8 * h;
-        valid[h] = s < n;
-        if (valid[h]) feats(x[2 * s], x[2 * s + 1], fr[h]);
-        else for (int k = 0; k < 5; ++k) fr[h][k] = 0.0f;
-    }
-    __syncthreads();
-    // store features (FP32) for the first layer's weight gradient
-    if (t == 0) {
-        for (int h = 0; h < 2; ++h) {
-            float* row = S.act[0] + (warp * TILE + g + 8 * h) * H;
-            for (int k = 0; k < IN; ++k) row[k] = k < 5 ? fr[h][k] : 0.0f;
-        }
-    }
-    // A fragment of the features (K = 16): columns 2t, 2t+1 and 2t+8, 2t+9
-    uint32_t a[4][4];
-    {
-        auto fv = [&](int h, int c) { return c < 5 ? fr[h][c] : 0.0f; };
-        a[0][0] = pack2(fv(0, 2 * t), fv(0, 2 * t + 1));
-        a[0][1] = pack2(fv(1, 2 * t), fv(1, 2 * t + 1));
-        a[0][2] = pack2(fv(0, 2 * t + 8), fv(0, 2 * t + 9));
-        a[0][3] = pack2(fv(1, 2 * t + 8), fv(1, 2 * t + 9));
-    }
-    const __nv_bfloat16* Wf[5] = {S.w.w1, S.w.w2, S.w.w3, S.w.w4, S.w.w5};
-    float acc[8][4];
-    // ---- forward: four tanh layers
-    for (int l = 1; l <= 4; ++l) {
-        const int kin = l == 1 ? IN : H;
-        const __nv_bfloat16* W = Wf[l - 1];
-        const float* b = params + off_b(l);
-        for (int nt = 0; nt < 8; ++nt) {
-            const float b0 = b[nt * 8 + 2 * t], b1 = b[nt * 8 + 2 * t + 1];
-            acc[nt][0] = b0; acc[nt][1] = b1; acc[nt][2] = b0; acc[nt][3] = b1;
-        }
-        for (int kt = 0; kt < kin / 16; ++kt)
-            for (int nt = 0; nt < 8; ++nt) {
-                const __nv_bfloat16* wr = W + (nt * 8 + g) * kin + kt * 16 + 2 * t;
-                mma(acc[nt], a[kt], ld2(wr), ld2(wr + 8));
-            }
-        float* A = S.act[l];
-        for (int nt = 0; nt < 8; ++nt) {
-            for (int i = 0; i < 4; ++i) acc[nt][i] = tanhf(acc[nt][i]);
-            const int c = nt * 8 + 2 * t;
-            A[(warp * TILE + g) * H + c] = acc[nt][0];
-            A[(warp * TILE + g) * H + c + 1] = acc[nt][1];
-            A[(warp * TILE + g + 8) * H + c] = acc[nt][2];
-            A[(warp * TILE + g + 8) * H + c + 1] = acc[nt][3];
-        }
-        for (int kt = 0; kt < 4; ++kt) {
-            a[kt][0] = pack2(acc[2 * kt][0], acc[2 * kt][1]);
-            a[kt][1] = pack2(acc[2 * kt][2], acc[2 * kt][3]);
-            a[kt][2] = pack2(acc[2 * kt + 1][0], acc[2 * kt + 1][1]);
-            a[kt][3] = pack2(acc[2 * kt + 1][2], acc[2 * kt + 1][3]);
-        }
-    }
-    // ---- output layer (one n-tile of 8) and the loss delta
-    float o[4];
-    {
-        const float* b = params + off_b(5);
-        o[0] = b[2 * t]; o[1] = b[2 * t + 1]; o[2] = b[2 * t]; o[3] = b[2 * t + 1];
-        for (int kt = 0; kt < 4; ++kt) {
-            const __nv_bfloat16* wr = S.w.w5 + g * H + kt * 16 + 2 * t;
-            mma(o, a[kt], ld2(wr), ld2(wr + 8));
-        }
-    }
-    float d5[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    float lsum = 0.0f;
-    if (t == 0) {
-        for (int h = 0; h < 2; ++h) {
-            const int s = s0 + g + 8 * h;
-            if (!valid[h]) continue;
-            for (int k = 0; k < 2; ++k) {
-                const float m = mask[2 * s + k];
-                const float e = m * (o[2 * h + k] - target[2 * s + k]);
-                lsum += e * e;
-                d5[2 * h + k] = 2.0f * e * inv_n;
-            }
-        }
-    }
-    for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
-    if (lane == 0) atomicAdd(loss, (double)lsum * (double)inv_n);
-
-    // delta of the output layer to shared memory: delta[s][0..7]
-    __syncthreads();
-    {
-        float* D = S.delta;
-        D[(warp * TILE + g) * H + 2 * t] = d5[0];
-        D[(warp * TILE + g) * H + 2 * t + 1] = d5[1];
-        D[(warp * TILE + g + 8) * H + 2 * t] = d5[2];
-        D[(warp * TILE + g + 8) * H + 2 * t + 1] = d5[3];
-    }
-    __syncthreads();
-
-    // Weight gradient dW[out][in] = sum_s bf16(delta[s][out]) bf16(act[s][in]) over the block's
-    // samples (K = 64), plus db[out] = sum_s delta[s][out].  Rows beyond `outs` are zero.
-    auto weight_grad = [&](int l, int outs, int ins) {
-        const float* D = S.delta;
-        const float* A = S.act[l - 1];
-        const int mtiles = (outs + 15) / 16, ntiles = ins / 8;
-        for (int pair = warp; pair < mtiles * ntiles; pair += WARPS) {
-            const int mt = pair / ntiles, nt = pair % ntiles;
-            float c[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-            for (int kt = 0; kt < BS / 16; ++kt) {
-                const int sa = kt * 16 + 2 * t;
-                const int r0 = mt * 16 + g, r1 = r0 + 8;
-                auto dv = [&](int s, int r) { return r < outs ? D[s * H + r] : 0.0f; };
-                uint32_t af[4] = {pack2(dv(sa, r0), dv(sa + 1, r0)), pack2(dv(sa, r1), dv(sa + 1, r1)),
-                                  pack2(dv(sa + 8, r0), dv(sa + 9, r0)), pack2(dv(sa + 8, r1), dv(sa + 9, r1))};
-                const int col = nt * 8 + g;
-                const uint32_t b0 = pack2(A[sa * H + col], A[(sa + 1) * H + col]);
-                const uint32_t b1 = pack2(A[(sa + 8) * H + col], A[(sa + 9) * H + col]);
-                mma(c, af, b0, b1);
-            }
-            float* gW = grad + off_w(l);
-            const int r0 = mt * 16 + g, c0 = nt * 8 + 2 * t;
-            if (r0 < outs) { atomicAdd(gW + r0 * ins + c0, c[0]); atomicAdd(gW + r0 * ins + c0 + 1, c[1]); }
-            if (r0 + 8 < outs) { atomicAdd(gW + (r0 + 8) * ins + c0, c[2]); atomicAdd(gW + (r0 + 8) * ins + c0 + 1, c[3]); }
-        }
-        for (int r = threadIdx.x; r < outs; r += blockDim.x) {
-            float sb = 0.0f;
-            for (int s = 0; s < BS; ++s) sb += D[s * H + r];
-            atomicAdd(grad + off_b(l) + r, sb);
-        }
+    // thread 0 commits the issued products; everyone waits; false if any wait failed
+    auto sync_mma = [&]() -> bool {
+        if (r == 0) mma_commit(bar_mma);
+        const bool got = bar_wait(bar_mma, phase);
+        phase ^= 1u;
+        fence_after();
+        return !__syncthreads_or(!got);
     };
-    weight_grad(5, OUT, H);
+    auto publish = [&]() {     // smem written by the threads -> visible to the next products
+        fence_async_smem();
+        fence_before();
+        __syncthreads();
+        fence_after();
+    };
 
-    // ---- backward through the hidden layers
-    // delta_l = (delta_{l+1} W_{l+1}) * (1 - a_l^2); the product uses W^T[in][out] as B
-    uint32_t da[4][4];
-    da[0][0] = pack2(d5[0], d5[1]);
-    da[0][1] = pack2(d5[2], d5[3]);
-    da[0][2] = 0u;
-    da[0][3] = 0u;
-    int ktiles = 1;
-    const __nv_bfloat16* Wt[6] = {nullptr, nullptr, S.w.t2, S.w.t3, S.w.t4, S.w.t5};
-    for (int l = 4; l >= 1; --l) {
-        const __nv_bfloat16* T = Wt[l + 1];
-        const int kout = l == 4 ? 16 : H;       // padded width of layer l+1's outputs
-        float dd[8][4];
-        for (int nt = 0; nt < 8; ++nt) {
-            dd[nt][0] = dd[nt][1] = dd[nt][2] = dd[nt][3] = 0.0f;
-            for (int kt = 0; kt < ktiles; ++kt) {
-                const __nv_bfloat16* tr = T + (nt * 8 + g) * kout + kt * 16 + 2 * t;
-                mma(dd[nt], da[kt], ld2(tr), ld2(tr + 8));
+    int tiles_done = 0;
+    for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x, ++tiles_done) {
+        const int s = tile * TILE + r;
+        const bool valid = s < n;
+        float px = 0.0f, py = 0.0f;
+        if (valid) { px = x[2 * s]; py = x[2 * s + 1]; }
+        {
+            float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            if (valid) feats(px, py, f);
+            const float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            put8(S.a0, C0, r, 0, f);
+            put8(S.a0, C0, r, 1, z);
+        }
+        publish();
+        // ---- forward: four tanh layers
+        for (int l = 1; l <= 4 && ok; ++l) {
+            const __nv_bfloat16* A = l == 1 ? S.a0 : S.a[l - 2];
+            const int CAin = l == 1 ? C0 : CA;
+            if (r == 0) {
+                fence_after();
+                for (int ks = 0; ks < CW[l] / 16; ++ks)
+                    mma(tmem + T_SCR, kmajor(A, CAin, ks), kmajor(W[l], CW[l], ks), idesc_bf16(128, 64, false, false),
+                        ks > 0 ? 1u : 0u);
+            }
+            ok = sync_mma();
+            if (!ok) break;
+            for (int c16 = 0; c16 < 4; ++c16) {
+                float v[16];
+                tmem_ld16(lane_addr + T_SCR + 16 * c16, v);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = tanhf(v[i] + S.bias[(l - 1) * H + 16 * c16 + i]);
+                put8(S.a[l - 1], CA, r, 2 * c16, v);
+                put8(S.a[l - 1], CA, r, 2 * c16 + 1, v + 8);
+            }
+            publish();
+        }
+        if (!ok) break;
+        // ---- output layer
+        if (r == 0) {
+            fence_after();
+            for (int ks = 0; ks < 4; ++ks)
+                mma(tmem + T_SCR, kmajor(S.a[3], CA, ks), kmajor(S.w.w5, H, ks), idesc_bf16(128, 16, false, false),
+                    ks > 0 ? 1u : 0u);
+        }
+        ok = sync_mma();
+        if (!ok) break;
+        {
+            float o[16];
+            tmem_ld16(lane_addr + T_SCR, o);
+            float d5[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) d5[i] = 0.0f;
+            if (MODE == kTrain) {
+                if (valid)
+                    for (int k = 0; k < 2; ++k) {
+                        const float e = mask[2 * s + k] * (o[k] + S.bias[4 * H + k] - target[2 * s + k]);
+                        loss_acc += e * e;
+                        d5[k] = 2.0f * e * inv_n;
+                    }
+            } else {
+                if (valid) {
+                    if (u_out) u_out[s] = o[0] + S.bias[4 * H];
+                    if (q_out) q_out[s] = o[1] + S.bias[4 * H + 1];
+                }
+                d5[0] = 1.0f;        // d u / d out
+            }
+            put8(S.d, CD, r, 0, d5);
+            put8(S.d, CD, r, 1, d5 + 8);
+        }
+        publish();
+        // ---- backward: weight gradients (training) and the deltas
+        for (int l = 5; l >= 1 && ok; --l) {
+            const __nv_bfloat16* Ain = l == 1 ? S.a0 : S.a[l - 2];
+            const int CAin = l == 1 ? C0 : CA;
+            const bool delta_product = l > 1 || MODE == kEval;
+            if (r == 0) {
+                fence_after();
+                if (MODE == kTrain)
+                    for (int ks = 0; ks < TILE / 16; ++ks)
+                        mma(tmem + t_dw(l), mnmajor(S.d, CD, ks), mnmajor(Ain, CAin, ks),
+                            idesc_bf16(128, CAin, true, true), (tiles_done > 0 || ks > 0) ? 1u : 0u);
+                if (delta_product) {
+                    const int kout = l == 5 ? OUTP : H;  // K of the product: layer l's outputs
+                    const int nin = l == 1 ? IN : H;     // N: its inputs
+                    for (int ks = 0; ks < kout / 16; ++ks)
+                        mma(tmem + T_SCR, kmajor(S.d, CD, ks), mnmajor(W[l], CW[l], ks),
+                            idesc_bf16(128, nin, false, true), ks > 0 ? 1u : 0u);
+                }
+            }
+            ok = sync_mma();
+            if (!ok) break;
+            if (l > 1) {
+                // delta_{l-1} = (delta_l W_l) * (1 - a_{l-1}^2), a as stored (BF16)
+                for (int c16 = 0; c16 < 4; ++c16) {
+                    float v[16], a[16];
+                    tmem_ld16(lane_addr + T_SCR + 16 * c16, v);
+                    get8(S.a[l - 2], CA, r, 2 * c16, a);
+                    get8(S.a[l - 2], CA, r, 2 * c16 + 1, a + 8);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) v[i] *= 1.0f - a[i] * a[i];
+                    put8(S.d, CD, r, 2 * c16, v);
+                    put8(S.d, CD, r, 2 * c16 + 1, v + 8);
+                }
+                publish();
+            } else if (MODE == kEval) {
+                float df[16];
+                tmem_ld16(lane_addr + T_SCR, df);       // d u / d features
+                if (valid && g_out) {
+                    const float c0 = 3.14159265358979f * cospif(px), c1 = 3.14159265358979f * cospif(py);
+                    const float c01 = 3.14159265358979f * cospif(px + py);
+                    g_out[2 * s] = df[0] + df[2] * c0 + df[4] * c01;
+                    g_out[2 * s + 1] = df[1] + df[3] * c1 + df[4] * c01;
+                }
+                fence_before();
+                __syncthreads();
+                fence_after();
             }
         }
-        __syncthreads();     // the previous weight gradient has finished reading S.delta
-        const float* A = S.act[l];
-        float* D = S.delta;
-        for (int nt = 0; nt < 8; ++nt) {
-            const int c = nt * 8 + 2 * t;
-            const int ra = (warp * TILE + g) * H, rb = (warp * TILE + g + 8) * H;
-            dd[nt][0] *= 1.0f - A[ra + c] * A[ra + c];
-            dd[nt][1] *= 1.0f - A[ra + c + 1] * A[ra + c + 1];
-            dd[nt][2] *= 1.0f - A[rb + c] * A[rb + c];
-            dd[nt][3] *= 1.0f - A[rb + c + 1] * A[rb + c + 1];
-            D[ra + c] = dd[nt][0];
-            D[ra + c + 1] = dd[nt][1];
-            D[rb + c] = dd[nt][2];
-            D[rb + c + 1] = dd[nt][3];
-        }
-        for (int kt = 0; kt < 4; ++kt) {
-            da[kt][0] = pack2(dd[2 * kt][0], dd[2 * kt][1]);
-            da[kt][1] = pack2(dd[2 * kt][2], dd[2 * kt][3]);
-            da[kt][2] = pack2(dd[2 * kt + 1][0], dd[2 * kt + 1][1]);
-            da[kt][3] = pack2(dd[2 * kt + 1][2], dd[2 * kt + 1][3]);
-        }
-        ktiles = 4;
-        __syncthreads();
-        weight_grad(l, H, l == 1 ? IN : H);
     }
+
+    if (MODE == kTrain && ok) {
+        for (int off = 16; off > 0; off >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
+        if ((r & 31) == 0 && loss_acc != 0.0f) atomicAdd(loss, (double)loss_acc * (double)inv_n);
+        // the CTA's weight and bias gradients: rows (outputs) are TMEM lanes 0..63
+        float* P = part + (size_t)blockIdx.x * NP;
+        for (int l = 1; l <= 5; ++l) {
+            const int outs = l == 5 ? OUT : H, ins = l == 1 ? IN : H;
+            const int ncol = l == 1 ? C0 : CA;
+            for (int c16 = 0; c16 < ncol / 16; ++c16) {
+                float v[16];
+                tmem_ld16(lane_addr + t_dw(l) + 16 * c16, v);     // warp-wide: every warp loads
+                if (r < outs)
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const int c = 16 * c16 + i;
+                        if (c < ins) P[off_w(l) + r * ins + c] = v[i];
+                        else if (c == ins) P[off_b(l) + r] = v[i];
+                    }
+            }
+        }
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS));
+    if (r == 0 && !ok) atomicOr(err, 1);
 }
 
-// BF16 copies (and transposes) of the FP32 parameters.
-__global__ void convert_kernel(const float* __restrict__ p, Bf16Weights* __restrict__ w) {
+// Sum of the CTA partials, in CTA order (deterministic).
+__global__ void reduce_parts_kernel(const float* __restrict__ part, int n_parts, float* __restrict__ grad) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < H * IN) w->w1[i] = __float2bfloat16_rn(p[off_w(1) + i]);
-    if (i < H * H) {
-        const int o = i / H, in = i % H;
-        w->w2[i] = __float2bfloat16_rn(p[off_w(2) + i]);
-        w->w3[i] = __float2bfloat16_rn(p[off_w(3) + i]);
-        w->w4[i] = __float2bfloat16_rn(p[off_w(4) + i]);
-        w->t2[in * H + o] = __float2bfloat16_rn(p[off_w(2) + i]);
-        w->t3[in * H + o] = __float2bfloat16_rn(p[off_w(3) + i]);
-        w->t4[in * H + o] = __float2bfloat16_rn(p[off_w(4) + i]);
+    if (i >= NP) return;
+    float s = 0.0f;
+    for (int c = 0; c < n_parts; ++c) s += part[(size_t)c * NP + i];
+    grad[i] = s;
+}
+
+// BF16 weight image in the shared-memory layout.
+__global__ void convert_kernel(const float* __restrict__ p, WImage* __restrict__ w) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < H * IN) {
+        const int o = i / IN, c = i % IN;
+        w->w1[core_off(o, c, IN)] = __float2bfloat16_rn(p[off_w(1) + i]);
     }
-    if (i < OUT * H) w->w5[i] = __float2bfloat16_rn(p[off_w(5) + i]);
-    if (i < H * 16) {
-        const int in = i / 16, o = i % 16;
-        w->t5[i] = __float2bfloat16_rn(o < OUT ? p[off_w(5) + o * H + in] : 0.0f);
+    if (i < H * H) {
+        const int o = i / H, c = i % H;
+        w->w2[core_off(o, c, H)] = __float2bfloat16_rn(p[off_w(2) + i]);
+        w->w3[core_off(o, c, H)] = __float2bfloat16_rn(p[off_w(3) + i]);
+        w->w4[core_off(o, c, H)] = __float2bfloat16_rn(p[off_w(4) + i]);
+    }
+    if (i < OUTP * H) {
+        const int o = i / H, c = i % H;
+        w->w5[core_off(o, c, H)] = __float2bfloat16_rn(o < OUT ? p[off_w(5) + o * H + c] : 0.0f);
     }
 }
 
@@ -300,60 +452,6 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
     p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-// u head, d u / d(x, y) and the du/dn head at n points (scalar FP32, BF16 weights).
-__global__ void eval_kernel(const Bf16Weights* __restrict__ w, const float* __restrict__ params, int n,
-                            const float* __restrict__ x, float* __restrict__ u, float* __restrict__ gu,
-                            float* __restrict__ q) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float f[5];
-    feats(x[2 * i], x[2 * i + 1], f);
-    float a[5][H];
-    for (int o = 0; o < H; ++o) {
-        float s = params[off_b(1) + o];
-        for (int k = 0; k < 5; ++k) s = fmaf(__bfloat162float(w->w1[o * IN + k]), f[k], s);
-        a[1][o] = tanhf(s);
-    }
-    const __nv_bfloat16* Wl[5] = {nullptr, nullptr, w->w2, w->w3, w->w4};
-    for (int l = 2; l <= 4; ++l)
-        for (int o = 0; o < H; ++o) {
-            float s = params[off_b(l) + o];
-            for (int k = 0; k < H; ++k) s = fmaf(__bfloat162float(Wl[l][o * H + k]), a[l - 1][k], s);
-            a[l][o] = tanhf(s);
-        }
-    float out0 = params[off_b(5)], out1 = params[off_b(5) + 1];
-    for (int k = 0; k < H; ++k) {
-        out0 = fmaf(__bfloat162float(w->w5[k]), a[4][k], out0);
-        out1 = fmaf(__bfloat162float(w->w5[H + k]), a[4][k], out1);
-    }
-    // d u / d a_l, back to the features
-    float back[H], nb[H];
-    for (int k = 0; k < H; ++k) back[k] = __bfloat162float(w->w5[k]) * (1.0f - a[4][k] * a[4][k]);
-    for (int l = 4; l >= 2; --l) {
-        for (int k = 0; k < H; ++k) {
-            float s = 0.0f;
-            for (int o = 0; o < H; ++o) s = fmaf(back[o], __bfloat162float(Wl[l][o * H + k]), s);
-            nb[k] = s * (1.0f - a[l - 1][k] * a[l - 1][k]);
-        }
-        for (int k = 0; k < H; ++k) back[k] = nb[k];
-    }
-    float df[5];
-    for (int k = 0; k < 5; ++k) {
-        float s = 0.0f;
-        for (int o = 0; o < H; ++o) s = fmaf(back[o], __bfloat162float(w->w1[o * IN + k]), s);
-        df[k] = s;
-    }
-    const float px = x[2 * i], py = x[2 * i + 1];
-    const float c0 = 3.14159265358979f * cospif(px), c1 = 3.14159265358979f * cospif(py);
-    const float c01 = 3.14159265358979f * cospif(px + py);
-    if (u) u[i] = out0;
-    if (q) q[i] = out1;
-    if (gu) {
-        gu[2 * i] = df[0] + df[2] * c0 + df[4] * c01;
-        gu[2 * i + 1] = df[1] + df[3] * c1 + df[4] * c01;
-    }
-}
-
 }  // namespace
 
 struct dwos_mlp {
@@ -365,7 +463,10 @@ struct dwos_mlp {
     float* m = nullptr;          // Adam moments
     float* v = nullptr;
     double* loss = nullptr;
-    Bf16Weights* w = nullptr;
+    WImage* w = nullptr;         // BF16 weight image
+    float* part = nullptr;       // per-CTA gradient partials (n_sm x NP)
+    int* dflag = nullptr;        // device flag: a bounded wait ran out
+    int n_sm = 0;
     float* scratch = nullptr;    // staging for host inputs
     size_t scratch_cap = 0;
     long long step = 0;
@@ -411,12 +512,27 @@ dwos_status stage(dwos_mlp* mlp, int mem, size_t n_floats, const float* const* i
     return DWOS_OK;
 }
 
+int grid_for(const dwos_mlp* mlp, int n) {
+    const int tiles = (n + TILE - 1) / TILE;
+    return tiles < mlp->n_sm ? tiles : mlp->n_sm;
+}
+
+dwos_status check_err(dwos_mlp* mlp) {
+    int e = 0;
+    MK(cudaMemcpyAsync(&e, mlp->dflag, sizeof(int), cudaMemcpyDeviceToHost, mlp->stream), "read flag");
+    MK(cudaStreamSynchronize(mlp->stream), "synchronize");
+    if (e) return mfail(mlp, DWOS_ERR_TIMEOUT, "a tensor-core product did not complete in time");
+    return DWOS_OK;
+}
+
 dwos_status grads(dwos_mlp* mlp, int n, const float* x, const float* t, const float* mk) {
-    MK(cudaMemsetAsync(mlp->g, 0, sizeof(float) * NP, mlp->stream), "zero grad");
     MK(cudaMemsetAsync(mlp->loss, 0, sizeof(double), mlp->stream), "zero loss");
-    const int blocks = (n + BS - 1) / BS;
-    train_kernel<<<blocks, WARPS * 32, sizeof(Smem), mlp->stream>>>(mlp->w, mlp->p, n, x, t, mk, mlp->g, mlp->loss);
+    const int grid = grid_for(mlp, n);
+    mlp_kernel<kTrain><<<grid, THREADS, sizeof(Smem), mlp->stream>>>(mlp->w, mlp->p, n, x, t, mk, mlp->part,
+                                                                     mlp->loss, nullptr, nullptr, nullptr, mlp->dflag);
     MK(cudaGetLastError(), "train kernel");
+    reduce_parts_kernel<<<(NP + 255) / 256, 256, 0, mlp->stream>>>(mlp->part, grid, mlp->g);
+    MK(cudaGetLastError(), "reduce");
     return DWOS_OK;
 }
 
@@ -435,11 +551,18 @@ dwos_status dwos_mlp_create(dwos_mlp** out, int device) {
     if (e == cudaSuccess) e = cudaMalloc(&mlp->m, sizeof(float) * NP);
     if (e == cudaSuccess) e = cudaMalloc(&mlp->v, sizeof(float) * NP);
     if (e == cudaSuccess) e = cudaMalloc(&mlp->loss, sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&mlp->w, sizeof(Bf16Weights));
+    if (e == cudaSuccess) e = cudaMalloc(&mlp->w, sizeof(WImage));
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&mlp->n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaMalloc(&mlp->part, sizeof(float) * NP * (size_t)(mlp->n_sm > 0 ? mlp->n_sm : 1));
+    if (e == cudaSuccess) e = cudaMalloc(&mlp->dflag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(mlp->dflag, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(mlp->w, 0, sizeof(WImage));
     if (e == cudaSuccess) e = cudaMemset(mlp->p, 0, sizeof(float) * NP);
     if (e == cudaSuccess) e = cudaMemset(mlp->m, 0, sizeof(float) * NP);
     if (e == cudaSuccess) e = cudaMemset(mlp->v, 0, sizeof(float) * NP);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(mlp_kernel<kTrain>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)sizeof(Smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(mlp_kernel<kEval>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    (int)sizeof(Smem));
     if (e != cudaSuccess) {
         g_mlp_err = std::string("mlp setup: ") + cudaGetErrorString(e);
@@ -456,7 +579,7 @@ void dwos_mlp_destroy(dwos_mlp* mlp) {
     cudaSetDevice(mlp->device);
     if (mlp->stream) cudaStreamSynchronize(mlp->stream);
     for (void* p : {(void*)mlp->p, (void*)mlp->g, (void*)mlp->m, (void*)mlp->v, (void*)mlp->loss, (void*)mlp->w,
-                    (void*)mlp->scratch})
+                    (void*)mlp->scratch, (void*)mlp->part, (void*)mlp->dflag})
         if (p) cudaFree(p);
     delete mlp;
 }
@@ -505,7 +628,7 @@ dwos_status dwos_mlp_loss_grad(dwos_mlp* mlp, int n, const float* x, const float
     const cudaMemcpyKind k = mem == DWOS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     if (grad) MK(cudaMemcpyAsync(grad, mlp->g, sizeof(float) * NP, k, mlp->stream), "copy grad");
     if (loss) MK(cudaMemcpyAsync(loss, mlp->loss, sizeof(double), k, mlp->stream), "copy loss");
-    if (mem == DWOS_MEM_HOST) MK(cudaStreamSynchronize(mlp->stream), "synchronize");
+    if (mem == DWOS_MEM_HOST) return check_err(mlp);
     return DWOS_OK;
 }
 
@@ -529,7 +652,7 @@ dwos_status dwos_mlp_train_step(dwos_mlp* mlp, int n, const float* x, const floa
     if (loss) MK(cudaMemcpyAsync(loss, mlp->loss, sizeof(double),
                                  mem == DWOS_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                  mlp->stream), "copy loss");
-    if (mem == DWOS_MEM_HOST) MK(cudaStreamSynchronize(mlp->stream), "synchronize");
+    if (mem == DWOS_MEM_HOST) return check_err(mlp);
     return DWOS_OK;
 }
 
@@ -546,15 +669,22 @@ dwos_status dwos_mlp_eval(dwos_mlp* mlp, int n, const float* x, float* u, float*
         dg = du + n;
         dq = dg + 2 * (size_t)n;
     }
-    eval_kernel<<<(n + 63) / 64, 64, 0, mlp->stream>>>(mlp->w, mlp->p, n, d[0], du, dg, dq);
+    mlp_kernel<kEval><<<grid_for(mlp, n), THREADS, sizeof(Smem), mlp->stream>>>(
+        mlp->w, mlp->p, n, d[0], nullptr, nullptr, nullptr, nullptr, du, dg, dq, mlp->dflag);
     MK(cudaGetLastError(), "eval");
     if (mem == DWOS_MEM_HOST) {
         if (u) MK(cudaMemcpyAsync(u, du, sizeof(float) * n, cudaMemcpyDeviceToHost, mlp->stream), "copy");
         if (grad_u) MK(cudaMemcpyAsync(grad_u, dg, sizeof(float) * 2 * n, cudaMemcpyDeviceToHost, mlp->stream), "copy");
         if (q) MK(cudaMemcpyAsync(q, dq, sizeof(float) * n, cudaMemcpyDeviceToHost, mlp->stream), "copy");
-        MK(cudaStreamSynchronize(mlp->stream), "synchronize");
+        return check_err(mlp);
     }
     return DWOS_OK;
+}
+
+dwos_status dwos_mlp_sync(dwos_mlp* mlp) {
+    if (!mlp) return mfail(nullptr, DWOS_ERR_INVALID_ARG, "mlp is NULL");
+    MK(cudaSetDevice(mlp->device), "cudaSetDevice");
+    return check_err(mlp);
 }
 
 }  // extern "C"

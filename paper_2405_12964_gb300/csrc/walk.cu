@@ -68,11 +68,27 @@ struct WarpStats {             // per lane; summed over the warp in 64 bits at t
     unsigned nodes = 0, prims = 0;
 };
 
+// What a walk keeps from the end of its main walk until its last nested walk
+// ends (read and written only at phase changes).  The warp-wide kernel keeps
+// it in shared memory (an odd word count per thread: no bank conflicts) to
+// leave the registers to the search; the per-lane kernels keep it in registers.
+template <int DIM>
+struct PhaseState {
+    float u_main, g_main, b1, b2;
+    float sum_plain, sum_dn, sum_dt;     // nested walks: estimates, n / t displacements
+    float nrm[DIM], cb[DIM], xoff[DIM];
+    int leaf_main, e_main;
+    uint32_t meta_main;
+    uint32_t pad[DIM == 2 ? 1 : 2];      // 17 / 21 words
+};
+
 // Dynamic shared memory: the problem descriptors, then (warp-wide search only)
-// one traversal stack per warp.
-__host__ __device__ inline size_t walk_smem_bytes(int n_probs, int block_size, int traversal) {
+// one traversal stack per warp and the threads' phase states.
+__host__ __device__ inline size_t walk_smem_bytes(int n_probs, int block_size, int traversal, int dim = 3) {
     size_t b = (sizeof(DevProblem) * (size_t)n_probs + 15) & ~(size_t)15;
-    if (traversal == 2) b += sizeof(float2) * kWideStack * (size_t)(block_size / 32);
+    if (traversal == 2)
+        b += sizeof(float2) * kWideStack * (size_t)(block_size / 32) +
+             (dim == 2 ? sizeof(PhaseState<2>) : sizeof(PhaseState<3>)) * (size_t)block_size;
     return b;
 }
 
@@ -83,8 +99,11 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
     constexpr bool wide = WIDE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DevProblem* sp = reinterpret_cast<DevProblem*>(smem_raw);
-    float2* stk = reinterpret_cast<float2*>(smem_raw + walk_smem_bytes(n_probs, 0, 0)) +
-                  (size_t)(threadIdx.x >> 5) * kWideStack;
+    float2* stk_base = reinterpret_cast<float2*>(smem_raw + walk_smem_bytes(n_probs, 0, 0));
+    float2* stk = stk_base + (size_t)(threadIdx.x >> 5) * kWideStack;
+    PhaseState<DIM> ps_reg;
+    PhaseState<DIM>& S = WIDE ? reinterpret_cast<PhaseState<DIM>*>(stk_base + (size_t)(blockDim.x >> 5) * kWideStack)[threadIdx.x]
+                              : ps_reg;
     {
         const int words = (int)(sizeof(DevProblem) / sizeof(int)) * n_probs;
         const int* src = reinterpret_cast<const int*>(g_probs);
@@ -103,13 +122,11 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
     int prob = 0, phase = 0, step = 0, hint = -1;
     float x[DIM], acc = 0.0f;
     // main-walk results kept while the nested walks run
-    float u_main = 0.0f, g_main = 0.0f, b1 = 0.0f, b2 = 0.0f;
-    float sum_plain = 0.0f, sum_dn = 0.0f, sum_dt = 0.0f;   // nested walks: estimates, n / t displacements
-    int leaf_main = -1, e_main = -1;
-    uint32_t meta_main = 0;
-    float nrm[DIM], cb[DIM], xoff[DIM];
+    S.u_main = 0.0f; S.g_main = 0.0f; S.b1 = 0.0f; S.b2 = 0.0f;
+    S.sum_plain = 0.0f; S.sum_dn = 0.0f; S.sum_dt = 0.0f;
+    S.leaf_main = -1; S.e_main = -1; S.meta_main = 0;
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) { x[k] = 0.0f; nrm[k] = 0.0f; cb[k] = 0.0f; xoff[k] = 0.0f; }
+    for (int k = 0; k < DIM; ++k) { x[k] = 0.0f; S.nrm[k] = 0.0f; S.cb[k] = 0.0f; S.xoff[k] = 0.0f; }
 
     for (;;) {
         // ---- refill idle lanes with consecutive walk indices (one atomic per warp)
@@ -238,15 +255,15 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
         if (P.trace) P.trace[local * K1 + phase] = min((uint32_t)step, 0x3fffffffu) | ((uint32_t)kind << 30);
         if (phase == 0) {
             if (P.cv_end) P.cv_end[local] = make_float4(x[0], x[1], DIM == 3 ? x[DIM - 1] : 0.0f, 0.0f);
-            u_main = acc + g;
-            meta_main = min((uint32_t)step, 0xffffffu) | ((uint32_t)kind << 24);
+            S.u_main = acc + g;
+            S.meta_main = min((uint32_t)step, 0xffffffu) | ((uint32_t)kind << 24);
             if (!P.differential || kind == DWOS_KIND_ROULETTE) {
                 dwos_record r;
-                r.u = u_main;
+                r.u = S.u_main;
                 r.elem = kind == DWOS_KIND_ROULETTE ? -1 : e;
                 r.b1 = w1; r.b2 = w2;
                 r.c[0] = 0.0f; r.c[1] = 0.0f; r.c[2] = 0.0f;
-                r.meta = meta_main;
+                r.meta = S.meta_main;
                 P.rec[local] = r;
                 if (P.differential) {
                     if (P.trace) for (int j = 1; j < K1; ++j) P.trace[local * K1 + j] = 0xffffffffu;
@@ -267,21 +284,21 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
             if (DIM == 2) {
                 const float tx = vb[0] - va[0], ty = vb[1] - va[1];
                 const float inv = rsqrtf(tx * tx + ty * ty);
-                nrm[0] = ty * inv;
-                nrm[1] = -tx * inv;
+                S.nrm[0] = ty * inv;
+                S.nrm[1] = -tx * inv;
             } else {
                 const float e1[3] = {vb[0] - va[0], vb[1] - va[1], vb[2] - va[2]};
                 const float e2[3] = {vc[0] - va[0], vc[1] - va[1], vc[2] - va[2]};
                 const float cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
                                      e1[0] * e2[1] - e1[1] * e2[0]};
                 const float inv = rsqrtf(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]);
-                nrm[0] = cr[0] * inv; nrm[1] = cr[1] * inv; nrm[DIM - 1] = cr[2] * inv;
+                S.nrm[0] = cr[0] * inv; S.nrm[1] = cr[1] * inv; S.nrm[DIM - 1] = cr[2] * inv;
             }
 #pragma unroll
-            for (int k = 0; k < DIM; ++k) side = fmaf(nrm[k], xbar[k] - x[k], side);
+            for (int k = 0; k < DIM; ++k) side = fmaf(S.nrm[k], xbar[k] - x[k], side);
             if (side < 0.0f) {
 #pragma unroll
-                for (int k = 0; k < DIM; ++k) nrm[k] = -nrm[k];
+                for (int k = 0; k < DIM; ++k) S.nrm[k] = -S.nrm[k];
             }
             // boundary-data part of c: (dg/dn) n for field data (Eq. boundary_deriv_restricted),
             // -grad_Gamma(g) for mapped data (Eq. boundary_deriv_mapped with dg/dn = 0)
@@ -290,17 +307,17 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
                 field_value<DIM>(P.field, xbar, gr);
                 float dgdn = 0.0f;
 #pragma unroll
-                for (int k = 0; k < DIM; ++k) dgdn = fmaf(nrm[k], gr[k], dgdn);
+                for (int k = 0; k < DIM; ++k) dgdn = fmaf(S.nrm[k], gr[k], dgdn);
 #pragma unroll
-                for (int k = 0; k < DIM; ++k) cb[k] = dgdn * nrm[k];
+                for (int k = 0; k < DIM; ++k) S.cb[k] = dgdn * S.nrm[k];
             } else {
                 const int* ev = P.elem + (size_t)DIM * e;
                 const float g0 = __ldg(P.g_vert + ev[0]);
                 if (DIM == 2) {
                     const float tx = vb[0] - va[0], ty = vb[1] - va[1];
                     const float s = (__ldg(P.g_vert + ev[1]) - g0) / (tx * tx + ty * ty);
-                    cb[0] = -s * tx;
-                    cb[1] = -s * ty;
+                    S.cb[0] = -s * tx;
+                    S.cb[1] = -s * ty;
                 } else {
                     const float e1[3] = {vb[0] - va[0], vb[1] - va[1], vb[2] - va[2]};
                     const float e2[3] = {vc[0] - va[0], vc[1] - va[1], vc[2] - va[2]};
@@ -311,55 +328,55 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
                     const float det = g11 * g22 - g12 * g12;
                     const float a1 = (g22 * r1 - g12 * r2) / det, a2 = (g11 * r2 - g12 * r1) / det;
 #pragma unroll
-                    for (int k = 0; k < DIM; ++k) cb[k] = -(a1 * e1[k] + a2 * e2[k]);
+                    for (int k = 0; k < DIM; ++k) S.cb[k] = -(a1 * e1[k] + a2 * e2[k]);
                 }
             }
 #pragma unroll
-            for (int k = 0; k < DIM; ++k) xoff[k] = fmaf(-P.h, nrm[k], xbar[k]);
-            g_main = g; b1 = w1; b2 = w2; leaf_main = best; e_main = e;
-            sum_plain = 0.0f; sum_dn = 0.0f; sum_dt = 0.0f;
+            for (int k = 0; k < DIM; ++k) S.xoff[k] = fmaf(-P.h, S.nrm[k], xbar[k]);
+            S.g_main = g; S.b1 = w1; S.b2 = w2; S.leaf_main = best; S.e_main = e;
+            S.sum_plain = 0.0f; S.sum_dn = 0.0f; S.sum_dt = 0.0f;
         } else {
             // nested control variate: (q n + t) . (x_end - x_off) has mean zero (every
             // move's direction is uniform and independent of whether the move happens)
             float dn = 0.0f, dt = 0.0f;
 #pragma unroll
-            for (int k = 0; k < DIM; ++k) dn = fmaf(nrm[k], x[k] - xoff[k], dn);
+            for (int k = 0; k < DIM; ++k) dn = fmaf(S.nrm[k], x[k] - S.xoff[k], dn);
             float q = 0.0f;
             if (P.cv_elem) {
-                const float4 qc = __ldg(P.cv_elem + e_main);
+                const float4 qc = __ldg(P.cv_elem + S.e_main);
                 const float tv[3] = {qc.y, qc.z, qc.w};
 #pragma unroll
-                for (int k = 0; k < DIM; ++k) dt = fmaf(tv[k], x[k] - xoff[k], dt);
+                for (int k = 0; k < DIM; ++k) dt = fmaf(tv[k], x[k] - S.xoff[k], dt);
                 q = qc.x;
             }
-            sum_plain += acc + g;
-            sum_dn += dn;
-            sum_dt += dt;
+            S.sum_plain += acc + g;
+            S.sum_dn += dn;
+            S.sum_dt += dt;
             if (phase == P.K) {   // Eq. (wos_deriv), shell case, with Eq. (dudn_fd_estimate)
                 const float inv_k = 1.0f / (float)P.K;
-                const float u_off = (sum_plain - fmaf(q, sum_dn, sum_dt)) * inv_k;
-                const float dudn = (g_main - u_off) * P.inv_h;
+                const float u_off = (S.sum_plain - fmaf(q, S.sum_dn, S.sum_dt)) * inv_k;
+                const float dudn = (S.g_main - u_off) * P.inv_h;
                 dwos_record r;
-                r.u = u_main;
-                r.elem = e_main;
-                r.b1 = b1; r.b2 = b2;
-                r.c[0] = cb[0] - dudn * nrm[0];
-                r.c[1] = cb[1] - dudn * nrm[1];
-                r.c[2] = DIM == 3 ? cb[DIM - 1] - dudn * nrm[DIM - 1] : 0.0f;
-                r.meta = meta_main;
+                r.u = S.u_main;
+                r.elem = S.e_main;
+                r.b1 = S.b1; r.b2 = S.b2;
+                r.c[0] = S.cb[0] - dudn * S.nrm[0];
+                r.c[1] = S.cb[1] - dudn * S.nrm[1];
+                r.c[2] = DIM == 3 ? S.cb[DIM - 1] - dudn * S.nrm[DIM - 1] : 0.0f;
+                r.meta = S.meta_main;
                 P.rec[local] = r;
                 if (P.dbg) {
                     dwos_walk_debug z;
                     z.dudn = dudn;
                     z.u_off = u_off;
                     for (int k = 0; k < 3; ++k) {
-                        z.n[k] = k < DIM ? nrm[k] : 0.0f;
-                        z.xbar[k] = k < DIM ? fmaf(P.h, nrm[k], xoff[k]) : 0.0f;
+                        z.n[k] = k < DIM ? S.nrm[k] : 0.0f;
+                        z.xbar[k] = k < DIM ? fmaf(P.h, S.nrm[k], S.xoff[k]) : 0.0f;
                     }
-                    z.u_plain = sum_plain * inv_k;
-                    z.disp_n = sum_dn * inv_k;
-                    z.disp_t = sum_dt * inv_k;
-                    z.elem = e_main;
+                    z.u_plain = S.sum_plain * inv_k;
+                    z.disp_n = S.sum_dn * inv_k;
+                    z.disp_t = S.sum_dt * inv_k;
+                    z.elem = S.e_main;
                     P.dbg[local] = z;
                 }
                 active = false;
@@ -370,9 +387,9 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
         ++phase;
         step = 0;
         acc = 0.0f;
-        hint = leaf_main;
+        hint = S.leaf_main;
 #pragma unroll
-        for (int k = 0; k < DIM; ++k) x[k] = xoff[k];
+        for (int k = 0; k < DIM; ++k) x[k] = S.xoff[k];
     }
 
     // ---- statistics: one atomic per warp
@@ -402,7 +419,7 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
 
 int walk_max_blocks_per_sm(int dim, int block_size, int traversal) {
     int n = 0;
-    const size_t smem = walk_smem_bytes(1, block_size, traversal);
+    const size_t smem = walk_smem_bytes(1, block_size, traversal, dim);
     if (traversal == 2) {
         if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<2, true>, block_size, smem);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<3, true>, block_size, smem);
@@ -426,7 +443,7 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
     if (blocks < 1) blocks = 1;
     if (blocks_used) *blocks_used = (int)blocks;
     if (bs % 32 != 0) return cudaErrorInvalidValue;
-    const size_t smem = walk_smem_bytes(n_probs, bs, L.traversal);
+    const size_t smem = walk_smem_bytes(n_probs, bs, L.traversal, L.dim);
     auto go = [&](auto kernel) -> cudaError_t {
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -96,6 +96,7 @@ _SIGS = {
     "dwos_mlp_loss_grad": [_vp, _i, _vp, _vp, _vp, _vp, _vp, _i],
     "dwos_mlp_train_step": [_vp, _i, _vp, _vp, _vp, ctypes.c_float, _vp, _i],
     "dwos_mlp_eval": [_vp, _i, _vp, _vp, _vp, _vp, _i],
+    "dwos_mlp_sync": [_vp],
 }
 MLP_NPARAM = 14088
 
@@ -435,7 +436,8 @@ class Batch:
 
 class ControlVariateNet:
     """The control-variate network (dwos_mlp_*): 5 features -> 4 x 64 tanh ->
-    outputs (u, du/dn); trained with the library's tensor-core kernels."""
+    outputs (u, du/dn); trained and evaluated with the library's tcgen05
+    tensor-core kernel."""
 
     def __init__(self, device: int = 0, params=None, seed: int = 0):
         self.device = torch.device("cuda", device)
@@ -469,6 +471,11 @@ class ControlVariateNet:
         t = self._dev(p)
         self._check(lib().dwos_mlp_set_params(self._h, _ptr(t), MEM_DEVICE))
         torch.cuda.synchronize(self.device)
+
+    def sync(self):
+        """Wait for queued work; raises if a tensor-core product timed out."""
+        self._stream()
+        self._check(lib().dwos_mlp_sync(self._h))
 
     def params(self):
         self._stream()

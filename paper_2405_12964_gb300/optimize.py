@@ -111,10 +111,10 @@ class ControlVariateTrainer:
         if x.shape[0] > self.max_samples:
             idx = torch.randperm(x.shape[0], device=x.device)[:self.max_samples]
             x, t, m = x[idx], t[idx], m[idx]
-        loss = 0.0
-        for _ in range(self.iters):
-            loss = float(self.net.train_step(x.contiguous(), t.contiguous(), m.contiguous(), lr=self.lr)[0])
-        return loss
+        losses = [self.net.train_step(x.contiguous(), t.contiguous(), m.contiguous(), lr=self.lr)
+                  for _ in range(self.iters)]
+        self.net.sync()
+        return float(losses[-1][0])
 
     def grad_at(self, xq) -> torch.Tensor:
         _, g, _ = self.net.eval(xq)

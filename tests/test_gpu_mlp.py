@@ -28,8 +28,10 @@ def _data(n, seed):
     return x, t, m
 
 
-@pytest.mark.parametrize("n", [64, 1000])
+@pytest.mark.parametrize("n", [64, 1000, 50000])
 def test_loss_and_gradient_match_reference(net_cls, n):
+    # 64: one partial tile; 1000: eight tiles; 50000: more tiles than CTAs, so each
+    # CTA accumulates several tiles' weight gradients in TMEM
     p = ref.init_params(1) * 2.0
     net = net_cls.ControlVariateNet(params=p.astype(np.float32))
     x, t, m = _data(n, 2)
@@ -66,9 +68,12 @@ def test_eval_matches_reference(net_cls):
     x = rng.uniform(-0.95, 0.95, size=(300, 2)).astype(np.float32)
     u, gu, q = (a.cpu().numpy() for a in net.eval(x))
     ur, gr, qr = ref.eval_u(p, x)
-    assert np.allclose(u, ur, rtol=1e-4, atol=1e-5)
-    assert np.allclose(q, qr, rtol=1e-4, atol=1e-5)
-    assert np.allclose(gu, gr, rtol=1e-3, atol=1e-4)
+    # same BF16 rounding on both sides; FP32 accumulation order can move an
+    # activation across a BF16 rounding boundary (2^-8 relative) now and then
+    for got, want, tol in ((u, ur, 2e-3), (q, qr, 2e-3), (gu, gr, 5e-3)):
+        scale = np.abs(want).max()
+        assert np.abs(got - want).max() <= tol * scale, np.abs(got - want).max() / scale
+        assert np.median(np.abs(got - want)) <= 1e-4 * scale
 
 
 def test_training_fits_a_smooth_field(net_cls):
