@@ -275,14 +275,11 @@ def run_control_variate(args):
     xq = torch.tensor(sc.query, dtype=torch.float32, device="cuda")
     s_uref = s.eval(xq, 16384)["u"].cpu().numpy()
     mid = 0.5 * (start + target)
-    cvg = trainer.grad_at(xq)
-    vref = sc.reference_vertices()
     rows = {}
     for name, th in [("start", start), ("midway", mid)]:
-        table = trainer.elem_table(vref + np.einsum("vkp,p->vk", sc.jac, th), sc.elem, sc.g_vert)
-        plain = optimize.gradient_rmse_x_time(sc, th, s_uref, 1024, cv_grad=None)
-        cv = optimize.gradient_rmse_x_time(sc, th, s_uref, 1024, cv_grad=cvg, whole_walk=True, cv_elem=table)
-        nested = optimize.gradient_rmse_x_time(sc, th, s_uref, 1024, cv_grad=None, cv_elem=table)
+        plain = optimize.gradient_rmse_x_time(sc, th, s_uref, 1024)
+        cv = optimize.gradient_rmse_x_time(sc, th, s_uref, 1024, net=trainer.net, whole_walk=True)
+        nested = optimize.gradient_rmse_x_time(sc, th, s_uref, 1024, net=trainer.net, main=False)
         rows[name] = {"plain": plain, "cv": cv, "nested_only": nested,
                       "rmse_x_seconds_ratio": cv["rmse_x_seconds"] / plain["rmse_x_seconds"]}
     line = {"metric": METRIC, "value": rows["start"]["cv"]["rmse_x_seconds"], "unit": "gradient RMSE x s",

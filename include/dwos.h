@@ -48,6 +48,7 @@ extern "C" {
 #endif
 
 typedef struct dwos_ctx dwos_ctx;
+typedef struct dwos_mlp dwos_mlp;       /* the control-variate network (below) */
 
 typedef enum {
     DWOS_OK = 0,
@@ -232,6 +233,15 @@ dwos_status dwos_grad_l2_cv(dwos_ctx* ctx, int n_query, const float* xq, const f
                             float* samples, dwos_walk_debug* debug, double* loss, double* grad_param,
                             double* u_se_pair);
 
+/* The nested walks' control-variate table for dwos_grad_l2_cv (2D boundaries):
+ * table (device, n_elem x 4 floats, 16-byte aligned) receives per element
+ * (q, t0, t1, 0) with q the network's du/dn head (output 1) at the element's
+ * centre and t the tangential gradient of the Dirichlet data on the element
+ * ((g1 - g0) / |d|^2 d for vertex data, grad g minus its normal part at the
+ * centre for field data), all at the current vertices.  Runs on the context's
+ * stream (the network's stream is set to it).  Asynchronous. */
+dwos_status dwos_cv_table(dwos_ctx* ctx, dwos_mlp* mlp, float* table);
+
 /* Raw per-walk records (n_query x walks_per_point rows, row p*W + w, Philox
  * walk id walk_id_base + p*W + w).  differential = 0 runs Algorithm 1 only
  * (record.u, record.elem, record.b*, meta; c = 0).  trace (optional,
@@ -330,7 +340,6 @@ dwos_status dwos_batch_stats(dwos_batch* b, dwos_run_stats* out);
  * mask[s][k] (out[s][k] - target[s][k])^2 over k in {0, 1}.  Points x,
  * targets and masks are n x 2 row-major; `mem` applies to every pointer. */
 #define DWOS_MLP_NPARAM 14088
-typedef struct dwos_mlp dwos_mlp;
 dwos_status dwos_mlp_create(dwos_mlp** out, int device);   /* parameters zero */
 void dwos_mlp_destroy(dwos_mlp* mlp);
 const char* dwos_mlp_last_error(const dwos_mlp* mlp);

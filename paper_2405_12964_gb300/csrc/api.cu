@@ -545,6 +545,78 @@ dwos_status dwos_grad_l2_cv(dwos_ctx* ctx, int n_query, const float* xq, const f
     return DWOS_OK;
 }
 
+namespace {
+
+// Element centres of a 2D boundary (current vertices).
+__global__ void cv_centres_kernel(const float* __restrict__ vert, const int* __restrict__ elem, int n_elem,
+                                  float* __restrict__ centres) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_elem) return;
+    const int a = elem[2 * e], b = elem[2 * e + 1];
+    centres[2 * e] = 0.5f * (vert[2 * a] + vert[2 * b]);
+    centres[2 * e + 1] = 0.5f * (vert[2 * a + 1] + vert[2 * b + 1]);
+}
+
+struct FieldCoef { float c[10]; };
+
+// (q, t) per element: q as given, t the tangential gradient of the Dirichlet
+// data on the element: (g1 - g0) / |d|^2 d for mapped vertex data (d = v1 - v0),
+// grad g - (grad g . n) n at the centre for field data.
+__global__ void cv_table_kernel(const float* __restrict__ vert, const int* __restrict__ elem,
+                                const float* __restrict__ g_vert, int data_kind, FieldCoef fc,
+                                const float* __restrict__ q, int n_elem, float4* __restrict__ table) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_elem) return;
+    const int a = elem[2 * e], b = elem[2 * e + 1];
+    const float dx = vert[2 * b] - vert[2 * a], dy = vert[2 * b + 1] - vert[2 * a + 1];
+    const float l2 = dx * dx + dy * dy;
+    float tx = 0.0f, ty = 0.0f;
+    if (l2 > 0.0f) {
+        if (data_kind == 1) {
+            const float X = 0.5f * (vert[2 * a] + vert[2 * b]), Y = 0.5f * (vert[2 * a + 1] + vert[2 * b + 1]);
+            const float gx = fc.c[1] + 2.0f * (fc.c[4] * X + fc.c[7] * Y);
+            const float gy = fc.c[2] + 2.0f * (fc.c[7] * X + fc.c[5] * Y);
+            const float s = (gx * dx + gy * dy) / l2;      // projection on the segment's direction
+            tx = s * dx;
+            ty = s * dy;
+        } else {
+            const float s = (g_vert[b] - g_vert[a]) / l2;
+            tx = s * dx;
+            ty = s * dy;
+        }
+    }
+    table[e] = make_float4(q[e], tx, ty, 0.0f);
+}
+
+}  // namespace
+
+dwos_status dwos_cv_table(dwos_ctx* ctx, dwos_mlp* mlp, float* table) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (!mlp || !table) return fail(ctx, DWOS_ERR_INVALID_ARG, "NULL argument");
+    if (!ctx->have_boundary) return fail(ctx, DWOS_ERR_STATE, "no boundary: call dwos_set_boundary first");
+    if (ctx->dim != 2) return fail(ctx, DWOS_ERR_NOT_IMPLEMENTED, "the control-variate network is two-dimensional");
+    if (dwos_status s = check_device_ptr(ctx, table, "table")) return s;
+    if (dwos_status s = set_device(ctx)) return s;
+    const int n = ctx->n_elem;
+    CK(grow(ctx->misc_f, ctx->misc_f_cap, 3 * (size_t)n), "alloc");
+    float* centres = ctx->misc_f;
+    float* q = centres + 2 * (size_t)n;
+    const int blocks = (n + 255) / 256;
+    cv_centres_kernel<<<blocks, 256, 0, ctx->stream>>>(ctx->vert, ctx->elem, n, centres);
+    CK(cudaGetLastError(), "centres");
+    if (dwos_status s = dwos_mlp_set_stream(mlp, ctx->stream))
+        return fail(ctx, s, std::string("network: ") + dwos_mlp_last_error(mlp));
+    if (dwos_status s = dwos_mlp_eval(mlp, n, centres, nullptr, nullptr, q, DWOS_MEM_DEVICE))
+        return fail(ctx, s, std::string("network: ") + dwos_mlp_last_error(mlp));
+    FieldCoef fc;
+    for (int i = 0; i < 10; ++i) fc.c[i] = (float)ctx->field[i];
+    cv_table_kernel<<<blocks, 256, 0, ctx->stream>>>(ctx->vert, ctx->elem, ctx->g_vert, ctx->data_kind, fc, q, n,
+                                                     reinterpret_cast<float4*>(table));
+    CK(cudaGetLastError(), "table");
+    ctx->launches += 3;
+    return DWOS_OK;
+}
+
 dwos_status dwos_walk_records(dwos_ctx* ctx, int n_query, const float* xq, int W, uint64_t walk_id_base,
                               int differential, dwos_record* records, uint32_t* trace, dwos_walk_debug* debug,
                               int mem) {

@@ -408,8 +408,9 @@ struct WideView {
 // 32 lanes working on it: each lane takes one child slot of the current wide
 // node, leaf children are measured exactly in parallel and reduced with
 // shuffles (ties to the lower leaf index), and the inner children that can
-// still hold a closer leaf go on the warp's stack in shared memory, nearest
-// on top (depth-first, near child first, pruned by the running bound).
+// still hold a closer leaf go on the warp's stack in shared memory with the
+// nearest on top (depth-first, nearest child first, the others in Morton
+// order, all pruned by the running bound when popped).
 // best2 / best hold each lane's bound on entry (kInf / -1 without one) and
 // the result on exit.  Called by all 32 lanes with the same `need` and each
 // lane's own view (lanes may belong to different problems).  Returns error
@@ -475,15 +476,22 @@ __device__ __forceinline__ int wide_closest(const WideView& mine, unsigned need,
                 if (im) {
                     const int cnt = __popc(im);
                     if (top + cnt > kWideStack) { err |= 4; break; }
-                    // stack position from the bottom: how many pushed siblings are farther
-                    int rank = 0;
-                    for (unsigned m = im; m; m &= m - 1) {
-                        const int j = __ffs(m) - 1;
-                        const float dj = __shfl_sync(kWarpAll, cd, j);
-                        rank += (dj > cd || (dj == cd && j > lane)) ? 1 : 0;
+                    // the nearest child goes on top (popped next); its siblings below it in
+                    // lane order, which is the Morton order of the subtrees
+                    float md = inner ? cd : kInf;
+                    int ml = inner ? lane : 32;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const float od = __shfl_xor_sync(kWarpAll, md, o);
+                        const int ol = __shfl_xor_sync(kWarpAll, ml, o);
+                        if (od < md || (od == md && ol < ml)) { md = od; ml = ol; }
                     }
+                    const unsigned rest = im & ~(1u << ml);
                     __syncwarp();
-                    if (inner) stk[top + rank] = make_float2(cd, __int_as_float(code));
+                    if (inner) {
+                        const int pos = lane == ml ? cnt - 1 : __popc(rest & ((1u << lane) - 1u));
+                        stk[top + pos] = make_float2(cd, __int_as_float(code));
+                    }
                     top += cnt;
                     __syncwarp();
                 }

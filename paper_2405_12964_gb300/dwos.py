@@ -97,6 +97,7 @@ _SIGS = {
     "dwos_mlp_train_step": [_vp, _i, _vp, _vp, _vp, ctypes.c_float, _vp, _i],
     "dwos_mlp_eval": [_vp, _i, _vp, _vp, _vp, _vp, _i],
     "dwos_mlp_sync": [_vp],
+    "dwos_cv_table": [_vp, _vp, _vp],
 }
 MLP_NPARAM = 14088
 
@@ -193,7 +194,7 @@ class Solver:
         P = 0 if j is None else j.shape[2]
         self._check(lib().dwos_set_boundary(self._h, dim, v.shape[0], _ptr(v), e.shape[0], _ptr(e), P, _ptr(j),
                                             MEM_DEVICE))
-        self.dim, self.n_vert, self.n_param = dim, v.shape[0], P
+        self.dim, self.n_vert, self.n_param, self.n_elem = dim, v.shape[0], P, e.shape[0]
 
     def set_params(self, theta):
         self._stream()
@@ -294,6 +295,15 @@ class Solver:
             out["samples"] = smp
         if debug:
             out["debug"] = dbg
+        return out
+
+    def cv_table(self, net: "ControlVariateNet") -> torch.Tensor:
+        """The nested walks' control-variate table (n_elem, 4) on the device:
+        the network's du/dn head at each element's centre and the data's
+        tangential gradient (dwos_cv_table)."""
+        self._stream()
+        out = torch.empty(self.n_elem, 4, device=self.device, dtype=torch.float32)
+        self._check(lib().dwos_cv_table(self._h, net._h, _ptr(out)))
         return out
 
     def walk_records(self, xq, walks: int, walk_id_base: int = 0, differential: bool = True,

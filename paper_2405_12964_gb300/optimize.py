@@ -69,7 +69,7 @@ class History:
 class ControlVariateTrainer:
     """Online training of the control-variate network on walk samples."""
 
-    def __init__(self, device: int = 0, seed: int = 0, lr: float = 2e-3, iters: int = 20, max_samples: int = 65536,
+    def __init__(self, device: int = 0, seed: int = 0, lr: float = 2e-3, iters: int = 10, max_samples: int = 65536,
                  q_weight: float = 0.2, h: float = 0.02):
         self.net = dwos.ControlVariateNet(device, seed=seed)
         self.h = h                   # the solver's offset distance (du/dn = (g - u_off) / h)
@@ -78,41 +78,46 @@ class ControlVariateTrainer:
         self.rng = np.random.default_rng(seed)
 
     def update(self, samples: torch.Tensor, debug: Optional[torch.Tensor]) -> float:
-        ok = ~torch.isnan(samples[:, 0])
-        xs = samples[ok, :2]
-        tu = samples[ok, 3]
-        parts_x = [xs]
-        parts_t = [torch.stack([tu, torch.zeros_like(tu)], 1)]
-        parts_m = [torch.stack([torch.ones_like(tu), torch.zeros_like(tu)], 1)]
+        """Train on one gradient step's walks.  Fixed-size tensors with zero
+        weights for unusable rows keep the host out of the loop (no sync)."""
+        xs = samples[:, :2]
+        ok = ~torch.isnan(xs[:, 0])
+        zero = torch.zeros_like(samples[:, 0])
+        parts_x = [torch.where(ok[:, None], xs, torch.zeros_like(xs))]
+        parts_t = [torch.stack([torch.where(ok, samples[:, 3], zero), zero], 1)]
+        parts_m = [torch.stack([ok.to(zero.dtype), zero], 1)]
         if debug is not None:
             # dwos_walk_debug: dudn, n[3], u_off, xbar[3], u_plain, disp_n, disp_t, elem
             rec = debug.view(torch.float32).view(-1, 12)
             dudn, u_off, xb, u_plain, dn, dt = rec[:, 0], rec[:, 4], rec[:, 5:7], rec[:, 8], rec[:, 9], rec[:, 10]
             hit = ((rec[:, 1] != 0) | (rec[:, 2] != 0)) & (dn.abs() > 1e-7)
-            if bool(hit.any()):
-                # The du/dn head q weights the nested walks' normal displacement; the
-                # corrected nested mean u_plain - disp_t - q disp_n keeps its mean for
-                # any q and has the least variance where q minimises
-                # E[(r - q disp_n)^2], r = u_plain - g(xbar) - disp_t, i.e. the
-                # least-squares fit of r / disp_n with weights disp_n^2 (the normal
-                # derivative itself where u is linear on the scale of the nested walks).
-                # Centring on g = u_off + h du/dn keeps the fit's noise at Var(u).
-                g = u_off[hit] + self.h * dudn[hit]
-                d = dn[hit]
-                r = u_plain[hit] - g - dt[hit]
-                y = r / d
-                w = torch.sqrt(self.q_weight / (r * r).mean().clamp_min(1e-12)) * d.abs()
-                parts_x.append(xb[hit])
-                parts_t.append(torch.stack([torch.zeros_like(y), y], 1))
-                parts_m.append(torch.stack([torch.zeros_like(w), w], 1))
+            # The du/dn head q weights the nested walks' normal displacement; the
+            # corrected nested mean u_plain - disp_t - q disp_n keeps its mean for
+            # any q and has the least variance where q minimises
+            # E[(r - q disp_n)^2], r = u_plain - g(xbar) - disp_t, i.e. the
+            # least-squares fit of r / disp_n with weights disp_n^2 (the normal
+            # derivative itself where u is linear on the scale of the nested walks).
+            # Centring on g = u_off + h du/dn keeps the fit's noise at Var(u).
+            hf = hit.to(zero.dtype)
+            g = u_off + self.h * dudn
+            r = (u_plain - g - dt) * hf
+            d = torch.where(hit, dn, torch.ones_like(dn))
+            y = r / d
+            r2 = (r * r).sum() / hf.sum().clamp_min(1.0)
+            w = torch.sqrt(self.q_weight / r2.clamp_min(1e-12)) * dn.abs() * hf
+            parts_x.append(torch.where(hit[:, None], xb, torch.zeros_like(xb)))
+            parts_t.append(torch.stack([zero, y], 1))
+            parts_m.append(torch.stack([zero, w], 1))
         x = torch.cat(parts_x)
         t = torch.cat(parts_t)
         m = torch.cat(parts_m)
-        if x.shape[0] > self.max_samples:
-            idx = torch.randperm(x.shape[0], device=x.device)[:self.max_samples]
-            x, t, m = x[idx], t[idx], m[idx]
-        losses = [self.net.train_step(x.contiguous(), t.contiguous(), m.contiguous(), lr=self.lr)
-                  for _ in range(self.iters)]
+        n = x.shape[0]
+        if n > self.max_samples:            # a strided subset with a random offset
+            stride = (n + self.max_samples - 1) // self.max_samples
+            off = int(self.rng.integers(stride))
+            x, t, m = x[off::stride], t[off::stride], m[off::stride]
+        x, t, m = x.contiguous(), t.contiguous(), m.contiguous()
+        losses = [self.net.train_step(x, t, m, lr=self.lr) for _ in range(self.iters)]
         self.net.sync()
         return float(losses[-1][0])
 
@@ -120,12 +125,7 @@ class ControlVariateTrainer:
         _, g, _ = self.net.eval(xq)
         return g
 
-    def elem_table(self, vert: np.ndarray, elem: np.ndarray, g_vert: np.ndarray) -> np.ndarray:
-        """The nested walks' table: the du/dn head at each element's centre and
-        the data's tangential gradient (boundary at its current position)."""
-        centres = np.asarray(vert, dtype=np.float64)[elem].mean(axis=1)
-        _, _, q = self.net.eval(centres.astype(np.float32))
-        return nested_cv_table(vert, elem, g_vert, q)
+
 
 
 def tangential_gradient(vert: np.ndarray, elem: np.ndarray, g_vert: np.ndarray) -> np.ndarray:
@@ -175,7 +175,6 @@ def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 2
     hist = History()
     if use_cv and trainer is None:
         trainer = ControlVariateTrainer(device, seed=seed, h=scene.h)
-    vref = scene.reference_vertices()
     total = 0.0
     for it in range(steps):
         W = wpp_schedule(it + 1, steps, wpp0, wppT)
@@ -183,8 +182,7 @@ def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 2
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         cv_grad = trainer.grad_at(xq) if use_cv else None
-        cv_elem = trainer.elem_table(vref + np.einsum("vkp,p->vk", scene.jac, opt.theta), scene.elem,
-                                     scene.g_vert) if use_cv else None
+        cv_elem = s.cv_table(trainer.net) if use_cv else None
         out = s.grad_l2_cv(xq, uref, W, walk_id_base=(seed << 40) + it * (1 << 28), cv_grad=cv_grad,
                            whole_walk=whole_walk, cv_elem=cv_elem, samples=use_cv, debug=use_cv)
         g = out["grad"].cpu().numpy()
@@ -204,12 +202,14 @@ def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 2
     return opt.theta, hist, trainer
 
 
-def gradient_rmse_x_time(scene, theta: np.ndarray, uref, walks: int, repeats: int = 16, cv_grad=None,
-                         whole_walk: bool = True, cv_elem=None, ref_walks: int = 65536, device: int = 0,
-                         seed: int = 5):
+def gradient_rmse_x_time(scene, theta: np.ndarray, uref, walks: int, repeats: int = 16, net=None,
+                         whole_walk: bool = True, nested: bool = True, main: bool = True, ref_walks: int = 65536,
+                         device: int = 0, seed: int = 5):
     """RMSE of one gradient estimate (walks per point) against a reference
     (ref_walks per point, plain estimator), times the seconds one estimate
-    takes: the figure that compares estimators at equal accuracy."""
+    takes: the figure that compares estimators at equal accuracy.  With a
+    control-variate network the timed region includes its inference (the
+    gradient at the points and the nested table), not its training."""
     s = dwos.Solver(device)
     s.load_scene(scene)
     s.set_boundary(scene.reference_vertices(), scene.elem, scene.jac)
@@ -225,6 +225,8 @@ def gradient_rmse_x_time(scene, theta: np.ndarray, uref, walks: int, repeats: in
     for r in range(repeats):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        cv_grad = net.eval(xq)[1] if (net is not None and main) else None
+        cv_elem = s.cv_table(net) if (net is not None and nested) else None
         out = s.grad_l2_cv(xq, ur, walks, walk_id_base=(seed << 44) + r * (1 << 30), cv_grad=cv_grad,
                            whole_walk=whole_walk, cv_elem=cv_elem)
         g = out["grad"].cpu().numpy()

@@ -204,3 +204,20 @@ def test_exact_boundary_gradient_collapses_nested_variance(env):
     print("nested du/dn variance ratio with the exact table: %.2e" % ratio)
     assert ratio < 0.01, ratio
     assert abs(res[1].mean()) < 0.05
+
+
+def test_cv_table_matches_host_reference(env):
+    # dwos_cv_table: the du/dn head at element centres and the data's tangential gradient
+    torch, dwos = env
+    from paper_2405_12964_gb300.optimize import nested_cv_table
+    net = dwos.ControlVariateNet(seed=3)
+    s = dwos.Solver(0)
+    for sc, g in ((scenes.star_box_scene(n_seg=1024, n_query=8), None),
+                  (scenes.disk_scene("laplace_x", n_query=8), "x")):
+        s.load_scene(sc)
+        tab = s.cv_table(net).cpu().numpy()
+        centres = (0.5 * (sc.vert[sc.elem[:, 0]] + sc.vert[sc.elem[:, 1]])).astype(np.float32)
+        q = net.eval(centres)[2].cpu().numpy()
+        g_vert = sc.vert[:, 0] if g == "x" else sc.g_vert       # g = x is linear: its tangential gradient is exact
+        ref = nested_cv_table(sc.vert, sc.elem, g_vert, q)
+        assert np.allclose(tab, ref, rtol=1e-4, atol=1e-5), np.abs(tab - ref).max()
