@@ -62,6 +62,42 @@ def make_scene(name: str, walks: int = 0):
     return sc
 
 
+TRAFFIC_SOURCES = ["walk.cu", "dwos_device.cuh", "dwos_internal.h", "bvh.cu"]
+
+
+def kernel_source_hash() -> str:
+    """SHA-256 over the walk kernel's sources (the build's inputs for it)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2405_12964_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def measured_traffic(kernel: str, workload: str):
+    """DRAM bytes per walk-step of `kernel` on `workload` from a committed ncu
+    summary (a line 'traffic: kernel=... workload=... dram_bytes=... walk_steps=...
+    source_sha256=...' under profiles/), or None if there is none or the
+    kernel's sources changed since it was captured."""
+    d = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(d):
+        return None
+    want = kernel_source_hash()
+    for name in sorted(os.listdir(d)):
+        if not name.endswith((".md", ".txt")):
+            continue
+        with open(os.path.join(d, name)) as fh:
+            for line in fh:
+                line = line.strip().strip("`")
+                if not line.startswith("traffic:"):
+                    continue
+                kv = dict(t.split("=", 1) for t in line[len("traffic:"):].split() if "=" in t)
+                if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("source_sha256") == want:
+                    return float(kv["dram_bytes"]) / float(kv["walk_steps"])
+    return None
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -264,6 +300,9 @@ def run_control_variate(args):
     steps = 200
     th_p, hp, _ = optimize.run(sc, target, start, steps=steps, use_cv=False, seed=3)
     th_c, hc, trainer = optimize.run(sc, target, start, steps=steps, use_cv=True, whole_walk=True, seed=3)
+    # equal wall time: the plain optimiser gets the seconds the CV run took (training included)
+    steps_eq = max(steps, int(round(steps * hc.seconds[-1] / max(hp.seconds[-1], 1e-9))))
+    th_e, he, _ = optimize.run(sc, target, start, steps=steps_eq, use_cv=False, seed=3)
     # gradient quality at the starting shape, equal walks per point
     s_uref = None
     from paper_2405_12964_gb300.dwos import Solver
@@ -275,6 +314,13 @@ def run_control_variate(args):
     xq = torch.tensor(sc.query, dtype=torch.float32, device="cuda")
     s_uref = s.eval(xq, 16384)["u"].cpu().numpy()
     mid = 0.5 * (start + target)
+
+    def true_loss(theta):          # the loss of a final shape, from 16384 walks per point
+        s.set_params(theta)
+        u = s.eval(xq, 16384)["u"].cpu().numpy()
+        s.set_params(target)
+        return float(0.5 * np.sum((u - s_uref) ** 2))
+
     rows = {}
     for name, th in [("start", start), ("midway", mid)]:
         plain = optimize.gradient_rmse_x_time(sc, th, s_uref, 1024)
@@ -286,10 +332,14 @@ def run_control_variate(args):
             "higher_is_better": False, "n_gpus": 1, "steps": steps, "warmup": 0, "vs_baseline": None,
             "dtype": "f32 walks, bf16 MLP", "data": "synthetic",
             "config": {"workload": WORKLOADS["c5"]},
-            "plain_run": {"final_loss": hp.loss[-1], "theta_err": hp.theta_err[-1], "seconds": hp.seconds[-1]},
-            "cv_run": {"final_loss": hc.loss[-1], "theta_err": hc.theta_err[-1], "seconds": hc.seconds[-1],
-                       "median_var_ratio_last20": float(np.median(hc.var_ratio[-20:])),
+            "plain_run": {"steps": steps, "final_loss": true_loss(th_p), "theta_err": hp.theta_err[-1],
+                          "seconds": hp.seconds[-1]},
+            "cv_run": {"steps": steps, "final_loss": true_loss(th_c), "theta_err": hc.theta_err[-1],
+                       "seconds": hc.seconds[-1], "median_var_ratio_last20": float(np.median(hc.var_ratio[-20:])),
                        "mlp_loss_last": hc.mlp_loss[-1]},
+            "plain_run_equal_time": {"steps": steps_eq, "final_loss": true_loss(th_e), "theta_err": he.theta_err[-1],
+                                     "seconds": he.seconds[-1]},
+            "final_loss_note": "1/2 sum (u - u_target)^2 of the final shape, u from 16384 walks per point",
             "gradient_rmse_x_seconds": rows}
     print(json.dumps(line), flush=True)
 
@@ -405,6 +455,8 @@ def main():
     walk_s = sum(kernel_ms) / 1e3
     achieved = alg_bytes / walk_s / 1e9 / args.steps * args.steps
     hbm, src = peaks()
+    kname = f"walk_kernel<{sc.dim},{'true' if trav == 2 else 'false'}>"
+    traffic_per_step = measured_traffic(kname, args.workload)
 
     e2e = None
     if rank == 0:
@@ -452,8 +504,13 @@ def main():
             "grad_rmse": rmse, "grad_rel_rmse": rel, "grad_rmse_x_seconds": rmse * (ms_per_step / 1e3),
             "walk_steps_per_step": steps_done / args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                         "frac": achieved / hbm, "traffic": None,
-                         "kernel": f"walk_kernel<{sc.dim}>", "peak_source": src,
+                         "frac": achieved / hbm,
+                         "traffic": (None if traffic_per_step is None
+                                     else traffic_per_step * steps_done / args.steps),
+                         "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
+                                            "scaled to this launch's walk-steps" if traffic_per_step is not None
+                                            else "no ncu capture of the current kernel sources"),
+                         "kernel": kname, "peak_source": src,
                          "bytes_per_walk_step": alg_bytes / max(steps_done, 1),
                          "walk_kernel_ms": walk_s * 1e3 / args.steps},
             "cpu_baseline": cpu, "e2e": e2e,
