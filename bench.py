@@ -503,6 +503,8 @@ def main():
             "gradient_estimates_per_s": world * total * args.steps / t,
             "grad_rmse": rmse, "grad_rel_rmse": rel, "grad_rmse_x_seconds": rmse * (ms_per_step / 1e3),
             "walk_steps_per_step": steps_done / args.steps,
+            "closest_point_search": {"nodes_per_query": nodes / max(steps_done, 1),
+                                     "element_tests_per_query": prims / max(steps_done, 1)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
                          "traffic": (None if traffic_per_step is None

@@ -161,9 +161,11 @@ def nested_cv_table(vert: np.ndarray, elem: np.ndarray, g_vert: np.ndarray, q) -
 
 def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 200, lr: float = 1e-3,
         wpp0: int = 256, wppT: int = 1024, use_cv: bool = False, whole_walk: bool = True, seed: int = 1,
-        device: int = 0, target_walks: int = 16384, trainer: Optional[ControlVariateTrainer] = None):
+        device: int = 0, target_walks: int = 16384, trainer: Optional[ControlVariateTrainer] = None,
+        train_every: int = 1):
     """Optimise theta to match the profile that theta_target produces at the
-    scene's observation points.  Returns (theta, History)."""
+    scene's observation points (the network, if any, is trained on every
+    train_every-th step's walks).  Returns (theta, History, trainer)."""
     s = dwos.Solver(device)
     s.load_scene(scene)
     s.set_boundary(scene.reference_vertices(), scene.elem, scene.jac)
@@ -183,10 +185,11 @@ def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 2
         t0 = time.perf_counter()
         cv_grad = trainer.grad_at(xq) if use_cv else None
         cv_elem = s.cv_table(trainer.net) if use_cv else None
+        train = use_cv and it % train_every == 0
         out = s.grad_l2_cv(xq, uref, W, walk_id_base=(seed << 40) + it * (1 << 28), cv_grad=cv_grad,
-                           whole_walk=whole_walk, cv_elem=cv_elem, samples=use_cv, debug=use_cv)
+                           whole_walk=whole_walk, cv_elem=cv_elem, samples=train, debug=train)
         g = out["grad"].cpu().numpy()
-        if use_cv:
+        if train:
             hist.mlp_loss.append(trainer.update(out["samples"], out["debug"]))
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
