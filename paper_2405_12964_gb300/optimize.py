@@ -69,7 +69,7 @@ class History:
 class ControlVariateTrainer:
     """Online training of the control-variate network on walk samples."""
 
-    def __init__(self, device: int = 0, seed: int = 0, lr: float = 2e-3, iters: int = 10, max_samples: int = 65536,
+    def __init__(self, device: int = 0, seed: int = 0, lr: float = 2e-3, iters: int = 4, max_samples: int = 65536,
                  q_weight: float = 0.2, h: float = 0.02):
         self.net = dwos.ControlVariateNet(device, seed=seed)
         self.h = h                   # the solver's offset distance (du/dn = (g - u_off) / h)
