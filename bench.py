@@ -232,7 +232,7 @@ def run_batched(args):
     solvers = []
     for sc in probs:
         s = Solver(0)
-        s.load_scene(sc)
+        s.load_scene(sc)           # automatic search order: warp-wide for the 3D problems
         solvers.append(s)
     xs = [torch.tensor(sc.query, dtype=torch.float32, device="cuda") for sc in probs]
     us = [torch.tensor(sc.u_ref, dtype=torch.float32, device="cuda") for sc in probs]

@@ -78,9 +78,12 @@ typedef struct {
     int check_inside;   /* 1: reject query points outside Omega (ray parity) */
     int block_size;     /* walk-kernel threads per block; 0 = library default */
     int blocks_per_sm;  /* resident walk blocks per SM; 0 = occupancy maximum */
-    int traversal;      /* distance-query search order: 0 = from the root, bounded by
-                           the previous step's element; 1 = climbing from that
-                           element's leaf with the Morton-cell stop test */
+    int traversal;      /* distance-query search order: 0 = binary tree from the root,
+                           one query per lane, bounded by the previous step's
+                           element; 1 = climbing from that element's leaf with
+                           the Morton-cell stop test; 2 = the 32-wide tree
+                           searched by a whole warp, one query at a time;
+                           -1 = automatic (2 for triangles, 0 for segments) */
 } dwos_options;
 
 /* Per-walk record of a differential walk (32 bytes).  For a walk that reaches
@@ -144,7 +147,7 @@ const char* dwos_last_error(const dwos_ctx* ctx);
 dwos_status dwos_sync(dwos_ctx* ctx);
 
 /* Fill *opt with the defaults: eps 1e-3, h 1e-2, K 1, B 8, max_steps 16384,
- * seed 0x12964, check_inside 1, automatic launch shape, traversal 0. */
+ * seed 0x12964, check_inside 1, automatic launch shape, traversal -1 (automatic). */
 void dwos_default_options(dwos_options* opt);
 /* Validate and store options (eps > 0, h > 0, K >= 1, B in {2,4,8,16,32},
  * 1 <= max_steps < 2^24). */
@@ -315,7 +318,7 @@ dwos_status dwos_batch_capture(dwos_batch* b);
 dwos_status dwos_batch_launch(dwos_batch* b);
 /* Time the walk launch of each dimension group over block size (128, 256),
  * resident blocks per SM (1, 2, 4, ... up to the occupancy limit) and the
- * distance-query search order (dwos_options.traversal 0 / 1), reps passes
+ * distance-query search order (dwos_options.traversal 0 / 1 / 2), reps passes
  * each, and keep the fastest; recaptures the graph if one exists.
  * Synchronises. */
 dwos_status dwos_batch_autotune(dwos_batch* b, int reps);

@@ -27,7 +27,8 @@ dwos_status fail(dwos_ctx* c, dwos_status s, const std::string& msg) {
 
 // The search order a launch uses: the warp-wide one only where the tree supports it.
 int effective_traversal(const dwos_ctx* c) {
-    const int t = c->opt.traversal;
+    int t = c->opt.traversal;
+    if (t < 0) t = c->dim == 3 ? 2 : 0;
     return (t == 2 && !c->bvh.wide_ok) ? 0 : t;
 }
 
@@ -204,7 +205,7 @@ void dwos_default_options(dwos_options* o) {
     o->check_inside = 1;
     o->block_size = 0;
     o->blocks_per_sm = 0;
-    o->traversal = 0;
+    o->traversal = -1;
 }
 
 dwos_status dwos_create(dwos_ctx** out, int device) {
@@ -278,7 +279,8 @@ dwos_status dwos_set_options(dwos_ctx* ctx, const dwos_options* o) {
     if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 256 || o->block_size % 32))
         return fail(ctx, DWOS_ERR_INVALID_ARG, "block_size must be 0 or a multiple of 32 in [32, 256]");
     if (o->blocks_per_sm < 0 || o->blocks_per_sm > 64) return fail(ctx, DWOS_ERR_INVALID_ARG, "blocks_per_sm must be in [0, 64]");
-    if (o->traversal < 0 || o->traversal > 2) return fail(ctx, DWOS_ERR_INVALID_ARG, "traversal must be 0, 1 or 2");
+    if (o->traversal < -1 || o->traversal > 2)
+        return fail(ctx, DWOS_ERR_INVALID_ARG, "traversal must be -1 (automatic), 0, 1 or 2");
     ctx->opt = *o;
     return DWOS_OK;
 }
