@@ -44,6 +44,7 @@ WORKLOADS = {
            "5->64x4->2 (tcgen05 BF16 products, FP32 accumulation in TMEM) trained online on the walks' "
            "estimates (4 Adam iterations per step); value = gradient RMSE x seconds of one estimate at "
            "1024 walks/point, the network's inference inside the timed region"),
+    "ablation": "estimator ablation (product estimators, du/dn estimators, K, h) on the 2D workload",
     "c4": ("batched: 64 independent problems (32 2D star-in-box, 32 3D SH-sphere-in-box), elements "
            "log-uniform 1e3-5e5, 16-4096 points, sigma log-uniform 0.01-100, 256-4096 walks/point, "
            "16 shape params each; L2-loss gradients in one captured CUDA graph, autotuned walk pool"),
@@ -354,6 +355,62 @@ def run_control_variate(args):
     print(json.dumps(line), flush=True)
 
 
+def run_ablation(args):
+    """Estimator ablation on the 2D shape-from-diffusion workload at the star
+    (Sec. 5.3, Fig. ablation): gradient RMSE against a 64x-walk reference,
+    bias (the mean of the repeats against it) and seconds per estimate for
+    the product estimators (U-statistic, correlated, uncorrelated), the two
+    du/dn estimators (backward difference, ball gradient), K and h."""
+    import numpy as np
+    import torch
+    from paper_2405_12964_gb300 import build, scenes
+    build.build()
+    from paper_2405_12964_gb300.dwos import Solver
+    sc = scenes.star_box_scene()
+    W, R = 1024, 16
+    xq = torch.tensor(sc.query, dtype=torch.float32, device="cuda")
+    uref = torch.tensor(sc.u_ref, dtype=torch.float32, device="cuda")
+    s = Solver(0)
+    s.load_scene(sc)
+    ref = np.mean([s.grad_l2(xq, uref, 16384, walk_id_base=(3 << 44) + r * (1 << 30))[1].cpu().numpy()
+                   for r in range(4)], axis=0)
+    variants = [("ustat, backward difference, K=2, h=10 eps", dict(), "ustat"),
+                ("ustat, backward difference, K=1", dict(K=1), "ustat"),
+                ("ustat, backward difference, K=4", dict(K=4), "ustat"),
+                ("ustat, backward difference, h=5 eps", dict(h=5 * sc.eps), "ustat"),
+                ("ustat, backward difference, h=20 eps", dict(h=20 * sc.eps), "ustat"),
+                ("ustat, ball gradient, K=2", dict(dudn_estimator=1), "ustat"),
+                ("correlated product", dict(), "correlated"),
+                ("uncorrelated product", dict(), "uncorrelated")]
+    rows = []
+    for name, opt, product in variants:
+        s.load_scene(sc, **opt)
+        s.grad_l2_product(xq, uref, W, product=product, walk_id_base=1 << 46)   # warm-up
+        est, times = [], []
+        for r in range(R):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g = s.grad_l2_product(xq, uref, W, product=product, walk_id_base=(5 << 44) + r * (1 << 30))[1]
+            g = g.cpu().numpy()
+            times.append(time.perf_counter() - t0)
+            est.append(g)
+        E = np.array(est)
+        rmse = float(np.sqrt(np.mean((E - ref[None]) ** 2)))
+        bias = float(np.sqrt(np.mean((E.mean(0) - ref) ** 2)))
+        sec = float(np.median(times))
+        rows.append({"variant": name, "rmse": rmse, "bias_of_mean": bias,
+                     "bias_se": float(np.sqrt(np.mean(E.var(0, ddof=1) / R))),
+                     "seconds": sec, "rmse_x_seconds": rmse * sec})
+    line = {"metric": METRIC, "value": rows[0]["rmse_x_seconds"], "unit": "gradient RMSE x s",
+            "higher_is_better": False, "n_gpus": 1, "steps": R, "warmup": 1, "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "estimator ablation on the 2D shape-from-diffusion workload: 256 points x "
+                                   "1024 walks per estimate, 16 repeats per variant, reference = U-statistic "
+                                   "backward-difference gradient at 65536 walks per point"},
+            "ablation": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -372,6 +429,8 @@ def main():
         return run_batched(args)
     if args.workload == "c5":
         return run_control_variate(args)
+    if args.workload == "ablation":
+        return run_ablation(args)
 
     import numpy as np
     import torch

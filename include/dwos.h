@@ -84,6 +84,14 @@ typedef struct {
                            the Morton-cell stop test; 2 = the 32-wide tree
                            searched by a whole warp, one query at a time;
                            -1 = automatic (2 for triangles, 0 for segments) */
+    int dudn_estimator; /* du/dn at a shell hit from the K nested walks: 0 = backward
+                           difference (g(xbar) - mean u(xbar - h n)) / h, Eq.
+                           (dudn_fd_estimate); 1 = ball gradient at x_off = xbar - h n:
+                           each nested walk first moves to y uniform on the sphere of
+                           radius R = d(x_off) (no source, no roulette) and
+                           contributes F(R) (n_y . n) u(y), Eq. (dudn_mc_estimate) with
+                           F = d / R for sigma = 0, k / I1(kR) (2D) and k / i1(kR)
+                           (3D, spherical) for k = sqrt(sigma) > 0 */
 } dwos_options;
 
 /* Per-walk record of a differential walk (32 bytes).  For a walk that reaches
@@ -147,7 +155,8 @@ const char* dwos_last_error(const dwos_ctx* ctx);
 dwos_status dwos_sync(dwos_ctx* ctx);
 
 /* Fill *opt with the defaults: eps 1e-3, h 1e-2, K 1, B 8, max_steps 16384,
- * seed 0x12964, check_inside 1, automatic launch shape, traversal -1 (automatic). */
+ * seed 0x12964, check_inside 1, automatic launch shape, traversal -1 (automatic),
+ * dudn_estimator 0. */
 void dwos_default_options(dwos_options* opt);
 /* Validate and store options (eps > 0, h > 0, K >= 1, B in {2,4,8,16,32},
  * 1 <= max_steps < 2^24). */
@@ -208,6 +217,16 @@ dwos_status dwos_vjp(dwos_ctx* ctx, int n_query, const float* xq, const float* w
 dwos_status dwos_grad_l2(dwos_ctx* ctx, int n_query, const float* xq, const float* uref,
                          int walks_per_point, uint64_t walk_id_base, double* loss,
                          double* grad_param, double* grad_vert, int mem);
+
+/* The same squared-loss gradient with a choice of product estimator for
+ * u udot (Sec. 4.3): product 0 = U-statistic (as dwos_grad_l2), 1 =
+ * correlated (Eq. correlated_product: mean u and mean udot of all W walks;
+ * biased), 2 = uncorrelated (Eq. uncorrelated_product: u from walks
+ * 0 .. W/2 - 1 of each point, udot from the others; W even).  The loss is
+ * always that of the mean of all W walks. */
+dwos_status dwos_grad_l2_product(dwos_ctx* ctx, int n_query, const float* xq, const float* uref,
+                                 int walks_per_point, uint64_t walk_id_base, int product, double* loss,
+                                 double* grad_param, double* grad_vert, int mem);
 
 /* dwos_grad_l2 with a control variate and training samples (device pointers
  * only).  cv_grad (n_query x dim, or NULL) is the spatial gradient of a smooth

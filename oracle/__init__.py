@@ -66,6 +66,7 @@ class _Scene(ctypes.Structure):
         ("seed_lo", ctypes.c_uint32),
         ("seed_hi", ctypes.c_uint32),
         ("cv_elem", ctypes.POINTER(ctypes.c_double)),
+        ("dudn_mode", ctypes.c_int),
     ]
 
 
@@ -110,6 +111,8 @@ def lib():
             L.oracle_source_weight.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_double]
             L.oracle_source_weight.restype = ctypes.c_double
+            L.oracle_gradient_factor.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+            L.oracle_gradient_factor.restype = ctypes.c_double
             L.oracle_closest_point.argtypes = [ctypes.POINTER(_Scene), ctypes.c_int, dp, dp, dp,
                                                ip, dp]
             L.oracle_closest_point.restype = ctypes.c_int
@@ -156,6 +159,7 @@ class Problem:
     max_steps: int = 1 << 14
     seed: int = 0x12964
     cv_elem: Optional[np.ndarray] = None      # (n_elem, 4): q, t of the nested walks' surrogate grad u = q n + t
+    dudn_mode: int = 0                        # 0: backward difference (Eq. dudn_fd_estimate), 1: ball gradient
     _keep: list = dc_field(default_factory=list, repr=False)
 
     @property
@@ -200,6 +204,7 @@ class Problem:
         s.seed_lo = self.seed & 0xFFFFFFFF
         s.seed_hi = (self.seed >> 32) & 0xFFFFFFFF
         s.cv_elem = _dp(cq)
+        s.dudn_mode = int(self.dudn_mode)
         return s
 
 
@@ -222,6 +227,11 @@ def alpha(dim: int, sigma: float, d: float) -> float:
 def source_weight(dim: int, sigma: float, d: float, rho: float) -> float:
     """|B(d)| * G_d(rho d): Algorithm 1's source weight per unit source."""
     return lib().oracle_source_weight(dim, sigma, d, rho)
+
+
+def gradient_factor(dim: int, sigma: float, R: float) -> float:
+    """F with grad u(c) = F E[n_y u(y)] over the sphere of radius R about c."""
+    return lib().oracle_gradient_factor(dim, sigma, R)
 
 
 def closest_point(prob: Problem, pts: np.ndarray):

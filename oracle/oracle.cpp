@@ -127,6 +127,8 @@ typedef struct {
     uint32_t seed_hi;
     const double* cv_elem;   /* per element (q, t0, t1, t2): surrogate grad u = q n + t for the nested
                                 walks' control variate, or NULL */
+    int dudn_mode;           /* 0: backward difference, Eq. (dudn_fd_estimate); 1: ball gradient at the
+                                offset point, Eq. (dudn_mc_estimate) */
 } oracle_scene;
 
 enum { KIND_SHELL = 0, KIND_ROULETTE = 1, KIND_CAPPED = 2 };
@@ -376,6 +378,21 @@ double oracle_source_weight(int dim, double sigma, double d, double rho) {
     return vol * G;
 }
 
+/* Gradient of a solution of -Lap u + sigma u = 0 at the centre of a ball of
+ * radius R from its values on the sphere: grad u(c) = F E[n_y u(y)], y
+ * uniform.  Writing u's l = 1 part as f(r) cos t, the gradient at c is f'(0)
+ * and E[n_y u(y)] = f(R) / d; with f = I1(k r) (2D) or i1(k r) = (k r cosh k r
+ * - sinh k r) / (k r)^2 (3D), f'(0) = k / d, so F = k / f(R); sigma = 0 gives
+ * F = d / R (the mean-value property). */
+double oracle_gradient_factor(int dim, double sigma, double R) {
+    if (sigma <= 0) return dim / R;
+    double k = std::sqrt(sigma), z = k * R;
+    if (dim == 2) return k / std::cyl_bessel_i(1.0, z);
+    double i1 = z < 1e-2 ? z / 3 + z * z * z / 30 + std::pow(z, 5) / 840
+                         : (z * std::cosh(z) - std::sinh(z)) / (z * z);
+    return k / i1;
+}
+
 /* Uniform direction on the unit circle / sphere and uniform point in the ball. */
 static void sample_sphere(int dim, const Draws& r, double* w) {
     if (dim == 2) {
@@ -402,13 +419,19 @@ struct PhaseResult {
     double bary[2];
     double xbar[3];
     double x_last[3];  /* walk point at termination */
+    double ball_w;     /* ball-gradient weight F(R) (omega . n) of the first move, 0 if none */
 };
 
 /* Algorithm 1 (WalkOnSpheres) with Russian roulette, iterated instead of
- * recursed.  acc collects the source estimates S of every step. */
-static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_t walk_id, uint32_t phase) {
+ * recursed.  acc collects the source estimates S of every step.  With
+ * ball_n (the ball-gradient estimator of Eq. dudn_mc_estimate at x0) the
+ * first move is the gradient sample: no source, no roulette, and the weight
+ * F(R) (omega . ball_n) is returned with the walk's estimate at y. */
+static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_t walk_id, uint32_t phase,
+                                const double* ball_n = NULL) {
     PhaseResult res;
     res.x1[0] = res.x1[1] = res.x1[2] = NAN;
+    res.ball_w = 0;
     double x[3] = {x0[0], x0[1], s->dim == 3 ? x0[2] : 0.0};
     double acc = 0;
     for (int k = 0;; ++k) {
@@ -425,14 +448,15 @@ static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_
             for (int i = 0; i < 3; ++i) { res.xbar[i] = xbar[i]; res.x_last[i] = x[i]; }
             return res;
         }
-        if (s->f != 0) {
+        const bool ball = ball_n && k == 0;
+        if (s->f != 0 && !ball) {
             Draws rb = draw(s->seed_lo, s->seed_hi, walk_id, (uint32_t)k, phase, 1);
             double rho = sample_ball_radius(s->dim, rb);
             acc += oracle_source_weight(s->dim, s->sigma, d, rho) * s->f;
         }
         Draws r0 = draw(s->seed_lo, s->seed_hi, walk_id, (uint32_t)k, phase, 0);
         double alpha = oracle_alpha(s->dim, s->sigma, d);
-        if (alpha < r0.u[2]) {
+        if (!ball && alpha < r0.u[2]) {
             res.u = acc;
             res.kind = KIND_ROULETTE;
             res.steps = k + 1;
@@ -444,6 +468,11 @@ static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_
         double w[3];
         sample_sphere(s->dim, r0, w);
         for (int i = 0; i < s->dim; ++i) x[i] += d * w[i];
+        if (ball) {
+            double on = 0;
+            for (int i = 0; i < s->dim; ++i) on += w[i] * ball_n[i];
+            res.ball_w = oracle_gradient_factor(s->dim, s->sigma, d) * on;
+        }
         if (k == 0) for (int i = 0; i < 3; ++i) res.x1[i] = i < s->dim ? x[i] : 0.0;
     }
 }
@@ -507,10 +536,10 @@ static void run_one(const oracle_scene* s, const double* x0, uint64_t walk_id, i
     /* offset point and nested forward walks */
     double xoff[3] = {0, 0, 0};
     for (int i = 0; i < s->dim; ++i) xoff[i] = main.xbar[i] - s->h * n[i];
-    double sum = 0, sum_plain = 0, sum_dn = 0, sum_dt = 0;
+    double sum = 0, sum_plain = 0, sum_dn = 0, sum_dt = 0, sum_ball = 0;
     const double* q_cv = s->cv_elem ? s->cv_elem + 4 * (size_t)main.e : NULL;
     for (int j = 1; j <= s->K; ++j) {
-        PhaseResult nr = forward_walk(s, xoff, walk_id, (uint32_t)j);
+        PhaseResult nr = forward_walk(s, xoff, walk_id, (uint32_t)j, s->dudn_mode == 1 ? n : NULL);
         /* control variate: (q n + t) . (x_end - x_off) has mean zero */
         double disp = 0, dn = 0, dt = 0;
         for (int i = 0; i < s->dim; ++i) dn += n[i] * (nr.x_last[i] - xoff[i]);
@@ -520,6 +549,7 @@ static void run_one(const oracle_scene* s, const double* x0, uint64_t walk_id, i
         }
         sum += nr.u - disp;
         sum_plain += nr.u;
+        sum_ball += nr.ball_w * nr.u;
         sum_dn += dn;
         sum_dt += dt;
         if (o->kind) o->kind[idx * slots + j] = nr.kind;
@@ -527,7 +557,8 @@ static void run_one(const oracle_scene* s, const double* x0, uint64_t walk_id, i
     }
     double ubar = sum / s->K;
     double g = dirichlet_value(s, main.e, main.bary, main.xbar);
-    double dudn = (g - ubar) / s->h;     /* Eq. (dudn_fd_estimate) */
+    double dudn = s->dudn_mode == 1 ? sum_ball / s->K   /* Eq. (dudn_mc_estimate) */
+                                    : (g - ubar) / s->h;  /* Eq. (dudn_fd_estimate) */
     if (o->dudn) o->dudn[idx] = dudn;
     if (o->u_off) o->u_off[idx] = ubar;
     if (o->u_plain) o->u_plain[idx] = sum_plain / s->K;

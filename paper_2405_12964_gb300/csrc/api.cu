@@ -147,6 +147,7 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     P.inv_h = 1.0f / ctx->opt.h;
     P.K = ctx->opt.K;
     P.max_steps = ctx->opt.max_steps;
+    P.dudn_mode = ctx->opt.dudn_estimator;
     P.seed_lo = (uint32_t)ctx->opt.seed;
     P.seed_hi = (uint32_t)(ctx->opt.seed >> 32);
     P.xq = ctx->xq;
@@ -206,6 +207,7 @@ void dwos_default_options(dwos_options* o) {
     o->block_size = 0;
     o->blocks_per_sm = 0;
     o->traversal = -1;
+    o->dudn_estimator = 0;
 }
 
 dwos_status dwos_create(dwos_ctx** out, int device) {
@@ -279,6 +281,8 @@ dwos_status dwos_set_options(dwos_ctx* ctx, const dwos_options* o) {
     if (o->block_size != 0 && (o->block_size < 32 || o->block_size > 256 || o->block_size % 32))
         return fail(ctx, DWOS_ERR_INVALID_ARG, "block_size must be 0 or a multiple of 32 in [32, 256]");
     if (o->blocks_per_sm < 0 || o->blocks_per_sm > 64) return fail(ctx, DWOS_ERR_INVALID_ARG, "blocks_per_sm must be in [0, 64]");
+    if (o->dudn_estimator < 0 || o->dudn_estimator > 1)
+        return fail(ctx, DWOS_ERR_INVALID_ARG, "dudn_estimator must be 0 or 1");
     if (o->traversal < -1 || o->traversal > 2)
         return fail(ctx, DWOS_ERR_INVALID_ARG, "traversal must be -1 (automatic), 0, 1 or 2");
     ctx->opt = *o;
@@ -427,16 +431,17 @@ dwos_status dwos_eval(dwos_ctx* ctx, int n_query, const float* xq, int W, double
     return DWOS_OK;
 }
 
+// mode 0: VJP with cotangent wv; 1: squared-loss gradient, U-statistic product; 2: correlated
+// product; 3: uncorrelated product (wv = uref for modes 1-3).
 static dwos_status reverse_common(dwos_ctx* ctx, int n_query, const float* xq, const float* wv, int W,
                                   unsigned long long base, int mode, double* loss, double* grad_param,
                                   double* grad_vert, int mem) {
     if (dwos_status s = check_mem(ctx, mem)) return s;
     if (!wv && n_query > 0) return fail(ctx, DWOS_ERR_INVALID_ARG, mode ? "uref is NULL" : "w is NULL");
     if (ctx->n_param > 0 && !grad_param) return fail(ctx, DWOS_ERR_INVALID_ARG, "grad_param is NULL");
-    if (mode == 1) {
-        if (W % ctx->opt.B) return fail(ctx, DWOS_ERR_INVALID_ARG, "walks_per_point must be a multiple of B");
-        if (!loss) return fail(ctx, DWOS_ERR_INVALID_ARG, "loss is NULL");
-    }
+    if (mode == 1 && W % ctx->opt.B) return fail(ctx, DWOS_ERR_INVALID_ARG, "walks_per_point must be a multiple of B");
+    if (mode == 3 && (W < 2 || W % 2)) return fail(ctx, DWOS_ERR_INVALID_ARG, "walks_per_point must be even");
+    if (mode >= 1 && !loss) return fail(ctx, DWOS_ERR_INVALID_ARG, "loss is NULL");
     if (mem == DWOS_MEM_HOST && wv && !finite_all(wv, n_query)) return fail(ctx, DWOS_ERR_INVALID_ARG, "weights must be finite");
     if (mem == DWOS_MEM_DEVICE)
         for (const void* p : {(const void*)wv, (const void*)loss, (const void*)grad_param, (const void*)grad_vert})
@@ -450,11 +455,17 @@ static dwos_status reverse_common(dwos_ctx* ctx, int n_query, const float* xq, c
     CK(grow(ctx->acc_vert, ctx->acc_cap, nacc), "alloc accumulators");
     CK(cudaMemsetAsync(ctx->acc_vert, 0, nacc * sizeof(double), ctx->stream), "zero accumulators");
     double* acc_g = ctx->dg_vert ? ctx->acc_vert + (size_t)ctx->n_vert * ctx->dim : nullptr;
-    CK(launch_scatter(ctx->rec, ctx->elem, ctx->dim, n_query, W, ctx->opt.B, mode, ctx->wvec, ctx->acc_vert, acc_g,
-                      ctx->stream), "scatter");
-    ctx->launches += n_query > 0 ? 1 : 0;
-    const size_t need = (size_t)n_query + (size_t)std::max(N, 1) + 1;
+    const size_t need = 2 * (size_t)n_query + (size_t)std::max(N, 1) + 1;
     CK(grow(ctx->out, ctx->out_cap, need), "alloc outputs");
+    double* d_umean = ctx->out + std::max(N, 1) + n_query + 1;   // per-point mean for the product weights
+    if (mode == 2 || mode == 3) {
+        CK(launch_reduce_u(ctx->rec, n_query, W, d_umean, nullptr, ctx->stream, nullptr, mode == 3 ? W / 2 : W),
+           "reduce u");
+        ctx->launches += n_query > 0 ? 1 : 0;
+    }
+    CK(launch_scatter(ctx->rec, ctx->elem, ctx->dim, n_query, W, ctx->opt.B, mode, ctx->wvec, ctx->acc_vert, acc_g,
+                      ctx->stream, nullptr, d_umean), "scatter");
+    ctx->launches += n_query > 0 ? 1 : 0;
     double* d_grad = mem == DWOS_MEM_DEVICE ? grad_param : ctx->out;
     if (N > 0) {
         CK(cudaMemsetAsync(d_grad, 0, (size_t)N * sizeof(double), ctx->stream), "zero grad");
@@ -462,7 +473,7 @@ static dwos_status reverse_common(dwos_ctx* ctx, int n_query, const float* xq, c
         ctx->launches += 1;
     }
     double* d_loss = nullptr;
-    if (mode == 1) {
+    if (mode >= 1) {
         double* d_mean = ctx->out + std::max(N, 1);
         CK(launch_reduce_u(ctx->rec, n_query, W, d_mean, nullptr, ctx->stream), "reduce u");
         d_loss = mem == DWOS_MEM_DEVICE ? loss : ctx->out + std::max(N, 1) + n_query;
@@ -473,10 +484,19 @@ static dwos_status reverse_common(dwos_ctx* ctx, int n_query, const float* xq, c
         CK(from_device(ctx, grad_vert, ctx->acc_vert, (size_t)ctx->n_vert * ctx->dim, mem), "copy vertex gradient");
     if (mem == DWOS_MEM_HOST) {
         if (N > 0) CK(from_device(ctx, grad_param, ctx->out, N, mem), "copy grad");
-        if (mode == 1) CK(from_device(ctx, loss, d_loss, 1, mem), "copy loss");
+        if (mode >= 1) CK(from_device(ctx, loss, d_loss, 1, mem), "copy loss");
         return finish_sync(ctx);
     }
     return DWOS_OK;
+}
+
+dwos_status dwos_grad_l2_product(dwos_ctx* ctx, int n_query, const float* xq, const float* uref, int W,
+                                 uint64_t walk_id_base, int product, double* loss, double* grad_param,
+                                 double* grad_vert, int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (product < 0 || product > 2) return fail(ctx, DWOS_ERR_INVALID_ARG, "product must be 0, 1 or 2");
+    const int mode = product == 0 ? 1 : product + 1;
+    return reverse_common(ctx, n_query, xq, uref, W, walk_id_base, mode, loss, grad_param, grad_vert, mem);
 }
 
 dwos_status dwos_vjp(dwos_ctx* ctx, int n_query, const float* xq, const float* w, int W,
@@ -496,6 +516,8 @@ dwos_status dwos_grad_l2_cv(dwos_ctx* ctx, int n_query, const float* xq, const f
                             float* samples, dwos_walk_debug* debug, double* loss, double* grad_param,
                             double* u_var) {
     if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (cv_elem && ctx->opt.dudn_estimator != 0)
+        return fail(ctx, DWOS_ERR_INVALID_ARG, "the nested table corrects the backward-difference du/dn estimator");
     if (n_query < 1 || !uref || !loss) return fail(ctx, DWOS_ERR_INVALID_ARG, "bad arguments");
     if (ctx->n_param > 0 && !grad_param) return fail(ctx, DWOS_ERR_INVALID_ARG, "grad_param is NULL");
     if (W % ctx->opt.B) return fail(ctx, DWOS_ERR_INVALID_ARG, "walks_per_point must be a multiple of B");
@@ -851,6 +873,7 @@ extern "C" dwos_status dwos_eval_static(dwos_ctx* ctx, int n_query, const float*
     P.inv_h = 1.0f / ctx->opt.h;
     P.K = ctx->opt.K;
     P.max_steps = ctx->opt.max_steps;
+    P.dudn_mode = ctx->opt.dudn_estimator;
     P.seed_lo = (uint32_t)ctx->opt.seed;
     P.seed_hi = (uint32_t)(ctx->opt.seed >> 32);
     P.xq = xq;

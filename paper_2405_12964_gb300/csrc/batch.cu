@@ -107,6 +107,7 @@ void fill_problem(const dwos_ctx* c, const dwos_batch_job& j, dwos_record* rec, 
     P.inv_h = 1.0f / c->opt.h;
     P.K = c->opt.K;
     P.max_steps = c->opt.max_steps;
+    P.dudn_mode = c->opt.dudn_estimator;
     P.seed_lo = (uint32_t)c->opt.seed;
     P.seed_hi = (uint32_t)(c->opt.seed >> 32);
     P.xq = j.xq;

@@ -387,6 +387,24 @@ __device__ __forceinline__ bool closest_leaf(const BvhView& bvh, const float* q,
     return true;
 }
 
+// Factor of the ball gradient estimator behind Eq. (dudn_mc_estimate): for
+// -Lap u + k^2 u = 0 in a ball of radius R about c and y uniform on its
+// sphere, grad u(c) = F(R) E[n_y u(y)].  The l = 1 solutions u = I1(kr) cos t
+// (2D) and i1(kr) cos t (3D, i1 the modified spherical Bessel function) give
+// F = k / I1(kR) and k / i1(kR); both tend to d / R as k -> 0.
+template <int DIM>
+__device__ __forceinline__ float gradient_factor(float k, float R) {
+    const float z = k * R;
+    if (DIM == 2) return k > 0.0f ? k / cyl_bessel_i1f(z) : 2.0f / R;
+    if (!(k > 0.0f)) return 3.0f / R;
+    if (z < 0.5f) {            // i1(z) = z/3 + z^3/30 + z^5/840 + z^7/45360 + ...
+        const float z2 = z * z;
+        return k / (z * (1.0f / 3.0f + z2 * (1.0f / 30.0f + z2 * (1.0f / 840.0f + z2 * (1.0f / 45360.0f)))));
+    }
+    if (z < 20.0f) return k * z * z / (z * coshf(z) - sinhf(z));
+    return 2.0f * k * z * z * expf(-z) / (z - 1.0f);   // i1(z) = e^z (z - 1) / (2 z^2) + O(e^-z)
+}
+
 // ---- 32-wide BVH searched by a whole warp ---------------------------------
 // The binary LBVH collapsed five levels at a time: a wide node holds up to 32
 // children in SoA order, lo[DIM][32], hi[DIM][32], code[32] (>= 0: wide node,

@@ -38,6 +38,7 @@ struct DevProblem {
     float inv_h;
     int K;
     int max_steps;
+    int dudn_mode;              // 0 backward difference (Eq. dudn_fd_estimate), 1 ball gradient (Eq. dudn_mc_estimate)
     uint32_t seed_lo, seed_hi;
     // work
     const float* xq;            // n_query x dim
@@ -138,17 +139,20 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
 int walk_max_blocks_per_sm(int dim, int block_size, int traversal = 0);
 
 // Estimator reductions (estimators.cu).
+// mean / SE of the first `used` (0: all W) walks of each point
 cudaError_t launch_reduce_u(const dwos_record* rec, int n_points, int W, double* mean, double* se,
-                            cudaStream_t stream, const CvView* cv = nullptr);
+                            cudaStream_t stream, const CvView* cv = nullptr, int used = 0);
 // per-walk training samples: s.w <- u - s.w (the estimate of u at x1) where x1 exists
 cudaError_t launch_pack_samples(const dwos_record* rec, float4* samples, long long n, cudaStream_t stream);
 cudaError_t launch_reduce_udot(const dwos_record* rec, const int* elem, const float* jac, const float* dg,
                                int dim, int n_param, int n_points, int W, double* mean, double* se,
                                cudaStream_t stream);
-// mode 0: VJP weights w_p / W;  mode 1: U-statistic L2 weights in batches of B.
+// mode 0: VJP weights w_p / W;  1: U-statistic L2 weights in batches of B;  2: correlated
+// product (umean = mean u of all W walks);  3: uncorrelated product (umean = mean u of the
+// first W/2 walks, weights on the other W/2).
 cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int n_points, int W, int B,
                            int mode, const float* cot_or_uref, double* acc_vert, double* acc_g,
-                           cudaStream_t stream, const CvView* cv = nullptr);
+                           cudaStream_t stream, const CvView* cv = nullptr, const double* umean = nullptr);
 cudaError_t launch_gemv(const float* jac, const float* dg, const double* acc_vert, const double* acc_g,
                         int n_vert, int dim, int n_param, double* grad, cudaStream_t stream);
 cudaError_t launch_loss(const double* mean, const float* uref, int n_points, double* loss,

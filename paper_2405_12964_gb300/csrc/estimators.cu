@@ -40,10 +40,12 @@ __device__ __forceinline__ double walk_u(const dwos_record* __restrict__ rec, lo
     return u;
 }
 
-__global__ void reduce_u_kernel(const dwos_record* __restrict__ rec, int W, double* mean, double* se, CvView cv) {
+// Mean (and standard error) of the first `used` walks of each point's W.
+__global__ void reduce_u_kernel(const dwos_record* __restrict__ rec, int W, int used, double* mean, double* se,
+                                CvView cv) {
     const int p = blockIdx.x;
     double s = 0.0, s2 = 0.0;
-    for (int w = threadIdx.x; w < W; w += blockDim.x) {
+    for (int w = threadIdx.x; w < used; w += blockDim.x) {
         const double u = walk_u(rec, (long long)p * W + w, p, cv);
         s += u;
         s2 += u * u;
@@ -61,11 +63,11 @@ __global__ void reduce_u_kernel(const dwos_record* __restrict__ rec, int W, doub
         s = warp_sum(s);
         s2 = warp_sum(s2);
         if (lane == 0) {
-            const double m = s / W;
+            const double m = s / used;
             mean[p] = m;
             if (se) {
-                const double var = W > 1 ? fmax(s2 - W * m * m, 0.0) / (W - 1) : 0.0;
-                se[p] = sqrt(var / W);
+                const double var = used > 1 ? fmax(s2 - used * m * m, 0.0) / (used - 1) : 0.0;
+                se[p] = sqrt(var / used);
             }
         }
     }
@@ -149,6 +151,7 @@ template <int DIM>
 __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restrict__ rec,
                                                       const int* __restrict__ elem, int n_points, int W, int B,
                                                       int mode, const float* __restrict__ cot_or_uref,
+                                                      const double* __restrict__ umean,
                                                       long long walks_per_block, double* __restrict__ acc_vert,
                                                       double* __restrict__ acc_g, CvView cv) {
     __shared__ int keys[kSlots];
@@ -173,6 +176,14 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
         double wt;
         if (mode == 0) {
             wt = valid ? (double)cot_or_uref[p] / W : 0.0;
+        } else if (mode == 2) {
+            // correlated product, Eq. (correlated_product): (mean u - uref) mean udot, all W walks
+            wt = valid ? (umean[p] - (double)cot_or_uref[p]) / W : 0.0;
+        } else if (mode == 3) {
+            // uncorrelated product, Eq. (uncorrelated_product): u from the first W/2 walks,
+            // udot from the other W/2
+            const int M = W / 2;
+            wt = (valid && (int)(i % W) >= M) ? (umean[p] - (double)cot_or_uref[p]) / M : 0.0;
         } else {
             // U-statistic weight, Eq. (ustatistics): u*udot is estimated by
             // sum_m udot_m (S - u_m)/(B(B-1)), uref*udot by uref sum_m udot_m / B;
@@ -287,10 +298,10 @@ __global__ void loss_kernel(const double* mean, const float* uref, int n, double
 }  // namespace
 
 cudaError_t launch_reduce_u(const dwos_record* rec, int n_points, int W, double* mean, double* se, cudaStream_t s,
-                            const CvView* cv) {
+                            const CvView* cv, int used) {
     if (n_points <= 0) return cudaSuccess;
     const CvView none{nullptr, nullptr, nullptr, 2, nullptr};
-    reduce_u_kernel<<<n_points, 256, 0, s>>>(rec, W, mean, se, cv ? *cv : none);
+    reduce_u_kernel<<<n_points, 256, 0, s>>>(rec, W, used > 0 && used <= W ? used : W, mean, se, cv ? *cv : none);
     return cudaGetLastError();
 }
 
@@ -319,7 +330,7 @@ cudaError_t launch_reduce_udot(const dwos_record* rec, const int* elem, const fl
 
 cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int n_points, int W, int B, int mode,
                            const float* cot_or_uref, double* acc_vert, double* acc_g, cudaStream_t s,
-                           const CvView* cv) {
+                           const CvView* cv, const double* umean) {
     const CvView none{nullptr, nullptr, nullptr, dim, nullptr};
     const CvView c = cv ? *cv : none;
     const long long total = (long long)n_points * W;
@@ -330,8 +341,8 @@ cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int
     per = ((per + bs - 1) / bs) * bs;
     if (per < bs) per = bs;
     const long long blocks = (total + per - 1) / per;
-    if (dim == 2) scatter_kernel<2><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, per, acc_vert, acc_g, c);
-    else scatter_kernel<3><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, per, acc_vert, acc_g, c);
+    if (dim == 2) scatter_kernel<2><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, umean, per, acc_vert, acc_g, c);
+    else scatter_kernel<3><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, umean, per, acc_vert, acc_g, c);
     return cudaGetLastError();
 }
 

@@ -76,10 +76,11 @@ template <int DIM>
 struct PhaseState {
     float u_main, g_main, b1, b2;
     float sum_plain, sum_dn, sum_dt;     // nested walks: estimates, n / t displacements
+    float sum_ball, w_ball;              // ball-gradient estimator: weighted sum, this nested walk's weight
     float nrm[DIM], cb[DIM], xoff[DIM];
     int leaf_main, e_main;
     uint32_t meta_main;
-    uint32_t pad[DIM == 2 ? 1 : 2];      // 17 / 21 words
+    uint32_t pad[DIM == 2 ? 1 : 2];      // 19 / 23 words
 };
 
 // Dynamic shared memory: the problem descriptors, then (warp-wide search only)
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
     float x[DIM], acc = 0.0f;
     // main-walk results kept while the nested walks run
     S.u_main = 0.0f; S.g_main = 0.0f; S.b1 = 0.0f; S.b2 = 0.0f;
-    S.sum_plain = 0.0f; S.sum_dn = 0.0f; S.sum_dt = 0.0f;
+    S.sum_plain = 0.0f; S.sum_dn = 0.0f; S.sum_dt = 0.0f; S.sum_ball = 0.0f; S.w_ball = 0.0f;
     S.leaf_main = -1; S.e_main = -1; S.meta_main = 0;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) { x[k] = 0.0f; S.nrm[k] = 0.0f; S.cb[k] = 0.0f; S.xoff[k] = 0.0f; }
@@ -220,28 +221,37 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
             }
         } else {
             const unsigned long long wid = P.walk_id_base + local;
-            if (P.f != 0.0f) {   // source estimate of this ball (Algorithm 1, S-hat)
+            // ball-gradient estimator: a nested walk's first move samples y on the sphere
+            // about the offset point (no source, no roulette) and weighs the estimate at y
+            const bool ball = P.dudn_mode == 1 && phase > 0 && k_step == 0;
+            if (P.f != 0.0f && !ball) {   // source estimate of this ball (Algorithm 1, S-hat)
                 const U4 r1 = draw_block(P.seed_lo, P.seed_hi, wid, k_step, (uint32_t)phase, 1u);
                 acc = fmaf(source_weight<DIM>(P.sqrt_sigma, d, u01(r1.z)), P.f, acc);
             }
             const U4 r0 = draw_block(P.seed_lo, P.seed_hi, wid, k_step, (uint32_t)phase, 0u);
-            if (roulette_stops<DIM>(P.sqrt_sigma, d, u01(r0.z))) {
+            if (!ball && roulette_stops<DIM>(P.sqrt_sigma, d, u01(r0.z))) {
                 kind = DWOS_KIND_ROULETTE;
             } else {   // next point on the sphere of radius d
+                float om[3];
                 if (DIM == 2) {
                     float s, c;
                     sincospif(2.0f * u01(r0.x), &s, &c);
-                    x[0] = fmaf(d, c, x[0]);
-                    x[1] = fmaf(d, s, x[1]);
+                    om[0] = c; om[1] = s; om[2] = 0.0f;
                 } else {
                     const float u0 = u01(r0.x);
                     const float z = 1.0f - 2.0f * u0;
                     const float sth = 2.0f * sqrtf(u0 * (1.0f - u0));
                     float s, c;
                     sincospif(2.0f * u01(r0.y), &s, &c);
-                    x[0] = fmaf(d * sth, c, x[0]);
-                    x[1] = fmaf(d * sth, s, x[1]);
-                    x[DIM - 1] = fmaf(d, z, x[DIM - 1]);
+                    om[0] = sth * c; om[1] = sth * s; om[2] = z;
+                }
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) x[k] = fmaf(d, om[k], x[k]);
+                if (ball) {
+                    float on = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) on = fmaf(om[k], S.nrm[k], on);
+                    S.w_ball = gradient_factor<DIM>(P.sqrt_sigma, d) * on;
                 }
                 hint = best;
                 if (phase == 0 && k_step == 0 && P.cv_sample)   // first step of the main walk
@@ -334,7 +344,7 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
 #pragma unroll
             for (int k = 0; k < DIM; ++k) S.xoff[k] = fmaf(-P.h, S.nrm[k], xbar[k]);
             S.g_main = g; S.b1 = w1; S.b2 = w2; S.leaf_main = best; S.e_main = e;
-            S.sum_plain = 0.0f; S.sum_dn = 0.0f; S.sum_dt = 0.0f;
+            S.sum_plain = 0.0f; S.sum_dn = 0.0f; S.sum_dt = 0.0f; S.sum_ball = 0.0f; S.w_ball = 0.0f;
         } else {
             // nested control variate: (q n + t) . (x_end - x_off) has mean zero (every
             // move's direction is uniform and independent of whether the move happens)
@@ -352,10 +362,12 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
             S.sum_plain += acc + g;
             S.sum_dn += dn;
             S.sum_dt += dt;
-            if (phase == P.K) {   // Eq. (wos_deriv), shell case, with Eq. (dudn_fd_estimate)
+            S.sum_ball = fmaf(S.w_ball, acc + g, S.sum_ball);   // zero unless the ball estimator moved
+            S.w_ball = 0.0f;
+            if (phase == P.K) {   // Eq. (wos_deriv), shell case, with Eq. (dudn_fd_estimate) or (dudn_mc_estimate)
                 const float inv_k = 1.0f / (float)P.K;
                 const float u_off = (S.sum_plain - fmaf(q, S.sum_dn, S.sum_dt)) * inv_k;
-                const float dudn = (S.g_main - u_off) * P.inv_h;
+                const float dudn = P.dudn_mode == 1 ? S.sum_ball * inv_k : (S.g_main - u_off) * P.inv_h;
                 dwos_record r;
                 r.u = S.u_main;
                 r.elem = S.e_main;

@@ -33,7 +33,8 @@ DEBUG_DTYPE = np.dtype([("dudn", "<f4"), ("n", "<f4", (3,)), ("u_off", "<f4"), (
 class Options(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_float), ("h", ctypes.c_float), ("K", ctypes.c_int), ("B", ctypes.c_int),
                 ("max_steps", ctypes.c_int), ("seed", ctypes.c_uint64), ("check_inside", ctypes.c_int),
-                ("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("traversal", ctypes.c_int)]
+                ("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int), ("traversal", ctypes.c_int),
+                ("dudn_estimator", ctypes.c_int)]
 
 
 class RunStats(ctypes.Structure):
@@ -73,6 +74,7 @@ _SIGS = {
     "dwos_eval": [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp, _i],
     "dwos_vjp": [_vp, _i, _vp, _vp, _i, _u64, _vp, _vp, _i],
     "dwos_grad_l2": [_vp, _i, _vp, _vp, _i, _u64, _vp, _vp, _vp, _i],
+    "dwos_grad_l2_product": [_vp, _i, _vp, _vp, _i, _u64, _i, _vp, _vp, _vp, _i],
     "dwos_walk_records": [_vp, _i, _vp, _i, _u64, _i, _vp, _vp, _vp, _i],
     "dwos_last_stats": [_vp, ctypes.POINTER(RunStats)],
     "dwos_closest_point": [_vp, _i, _vp, _vp, _vp, _vp, _i],
@@ -266,6 +268,20 @@ class Solver:
         self._check(lib().dwos_grad_l2(self._h, x.shape[0], _ptr(x), _ptr(ur), int(walks), int(walk_id_base),
                                        _ptr(loss), _ptr(g), _ptr(gv), MEM_DEVICE))
         return (loss, g[:self.n_param], gv) if vertex_grad else (loss, g[:self.n_param])
+
+    def grad_l2_product(self, xq, uref, walks: int, product: str = "ustat", walk_id_base: int = 0):
+        """dwos_grad_l2_product: the squared-loss gradient with the U-statistic
+        ("ustat"), correlated ("correlated") or uncorrelated ("uncorrelated")
+        product estimator.  Returns (loss, grad) as device FP64 tensors."""
+        code = {"ustat": 0, "correlated": 1, "uncorrelated": 2}[product]
+        self._stream()
+        x = self._dev(xq, torch.float32)
+        u = self._dev(uref, torch.float32)
+        loss = torch.empty(1, device=self.device, dtype=torch.float64)
+        g = torch.empty(max(self.n_param, 1), device=self.device, dtype=torch.float64)
+        self._check(lib().dwos_grad_l2_product(self._h, x.shape[0], _ptr(x), _ptr(u), int(walks), int(walk_id_base),
+                                               code, _ptr(loss), _ptr(g), None, MEM_DEVICE))
+        return loss, g[:self.n_param]
 
     def grad_l2_cv(self, xq, uref, walks: int, walk_id_base: int = 0, cv_grad=None, whole_walk: bool = False,
                    cv_elem=None, samples: bool = False, debug: bool = False):

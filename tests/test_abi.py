@@ -51,11 +51,16 @@ def test_default_options_and_null_context_errors(libdwos):
     assert L.dwos_last_error(None)
 
 
-def test_record_layouts_are_32_bytes():
+def test_record_layouts_match_the_header():
     from paper_2405_12964_gb300 import dwos
     assert dwos.RECORD_DTYPE.itemsize == 32
     assert dwos.DEBUG_DTYPE.itemsize == 48
-    assert ctypes.sizeof(dwos.Options) == 48
+    assert ctypes.sizeof(dwos.Options) == 56
+    # the library's defaults land in the binding's fields (same layout on both sides)
+    o = dwos.Options()
+    dwos.lib().dwos_default_options(ctypes.byref(o))
+    assert o.K == 1 and o.B == 8 and o.seed == 0x12964 and o.check_inside == 1
+    assert o.traversal == -1 and o.dudn_estimator == 0 and o.block_size == 0
 
 
 def test_product_path_does_not_import_the_oracle():

@@ -74,6 +74,8 @@ def run_pair(Solver, sc, W, differential=True, base=0, **opt):
     s.load_scene(sc, **opt)
     g = s.walk_records(sc.query, W, walk_id_base=base, differential=differential, trace=True, debug=True)
     over = {k: v for k, v in opt.items() if k in ("eps", "h", "K", "max_steps", "seed")}
+    if "dudn_estimator" in opt:
+        over["dudn_mode"] = opt["dudn_estimator"]
     o = oracle.run_walks(to_oracle(sc, **over), sc.query, W, differential=differential, walk_id_base=base)
     return s, g, o
 
@@ -181,6 +183,22 @@ def test_star_box_per_walk_replay_with_nested_walks(Solver, traversal):
     assert np.all(np.abs(dd - o["dudn"])[same] <= 1e-3 * (1 + np.abs(o["dudn"][same])))
 
 
+@pytest.mark.parametrize("which", ["star", "sphere"])
+def test_ball_gradient_estimator_replay(Solver, which):
+    # Eq. (dudn_mc_estimate): each nested walk's first move samples the sphere about
+    # the offset point (no roulette, no source) and weighs the estimate at y
+    if which == "star":
+        sc = scenes.star_box_scene(n_seg=4096, n_query=16)
+        s, g, o = run_pair(Solver, sc, 32, K=2, dudn_estimator=1)
+    else:
+        sc = scenes.sh_sphere_scene(freq=16, n_query=12, K=2)
+        s, g, o = run_pair(Solver, sc, 24, dudn_estimator=1)
+    same = check_walks(sc, g, o, max_flip=0.02)
+    dd = g["debug"]["dudn"].astype(np.float64)
+    assert np.all(np.abs(dd - o["dudn"])[same] <= 1e-3 * (1 + np.abs(o["dudn"][same])))
+    assert np.abs(o["dudn"][same]).max() > 0
+
+
 @pytest.mark.parametrize("traversal", [0, 2])
 def test_sphere_3d_per_walk_replay_with_source(Solver, traversal):
     sc = scenes.sh_sphere_scene(freq=16, n_query=12, K=2)
@@ -260,6 +278,27 @@ def test_grad_l2_and_vjp_match_oracle_estimators(Solver):
     gv = s.vjp(sc.query, w, sc.walks, walk_id_base=0).cpu().numpy()
     vo = est.vjp(o["udot"], w, 16, sc.walks)
     assert np.allclose(gv, vo, rtol=2e-3, atol=2e-3 * np.abs(vo).max())
+
+
+def test_product_estimators_match_oracle(Solver):
+    # Sec. 4.3: U-statistic (= dwos_grad_l2), correlated and uncorrelated products on the same walks
+    sc = scenes.star_box_scene(n_seg=1024, n_query=16, walks=64)
+    s = Solver(0)
+    s.load_scene(sc, K=2)
+    uref = sc.u_ref
+    o = oracle.run_walks(to_oracle(sc, K=2), sc.query, sc.walks, differential=True)
+    want = {"ustat": est.grad_l2_ustat(o["u_hat"], o["udot"], uref, 16, sc.walks, 8),
+            "correlated": est.grad_l2_correlated(o["u_hat"], o["udot"], uref, 16, sc.walks),
+            "uncorrelated": est.grad_l2_uncorrelated(o["u_hat"], o["udot"], uref, 16, sc.walks)}
+    lo = est.loss_l2(o["u_hat"], uref, 16, sc.walks)
+    for name, go in want.items():
+        loss, g = (t.cpu().numpy() for t in s.grad_l2_product(sc.query, uref, sc.walks, product=name))
+        scale = np.abs(go).max()
+        assert np.allclose(g, go, rtol=2e-3, atol=2e-3 * scale), (name, np.abs(g - go).max() / scale)
+        assert abs(loss[0] - lo) <= 1e-4 * abs(lo) + 1e-7
+    g1 = s.grad_l2(sc.query, uref, sc.walks)[1].cpu().numpy()
+    g2 = s.grad_l2_product(sc.query, uref, sc.walks, product="ustat")[1].cpu().numpy()
+    assert np.array_equal(g1, g2)
 
 
 def test_vertex_gradient_chains_to_parameters(Solver):
