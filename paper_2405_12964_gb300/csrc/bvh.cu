@@ -379,7 +379,8 @@ __global__ void wide_fill_kernel(const int* node_child, const int* wid, const in
 
 // Child boxes gathered from the binary tree (its refit already ran) and codes.
 template <int DIM>
-__global__ void wide_refit_kernel(const float4* nodes, const int* wsrc, const int* wcode, int n_wide, float* wnodes) {
+__global__ void wide_refit_kernel(const float4* nodes, const float4* prims, const int* wsrc, const int* wcode,
+                                  int n_wide, float* wnodes) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_wide * kWide) return;
     const int w = t / kWide, j = t % kWide;
@@ -397,7 +398,27 @@ __global__ void wide_refit_kernel(const float4* nodes, const int* wsrc, const in
     }
 #pragma unroll
     for (int k = 0; k < DIM; ++k) { f[k * kWide + j] = lo[k]; f[(DIM + k) * kWide + j] = hi[k]; }
-    f[2 * DIM * kWide + j] = __int_as_float(wcode[t]);
+    const int code = wcode[t];
+    f[2 * DIM * kWide + j] = __int_as_float(code);
+    // a leaf child's vertices (the element in Morton order), zeros otherwise
+    float v[DIM * DIM];
+#pragma unroll
+    for (int k = 0; k < DIM * DIM; ++k) v[k] = 0.0f;
+    if (code < 0) {
+        const int p = ~code;
+        if constexpr (DIM == 2) {
+            const float4 sgm = prims[p];
+            v[0] = sgm.x; v[1] = sgm.y; v[2] = sgm.z; v[3] = sgm.w;
+        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float4 a = prims[3 * p + c];
+                v[3 * c] = a.x; v[3 * c + 1] = a.y; v[3 * c + 2] = a.z;
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < DIM * DIM; ++k) f[WideLayout<DIM>::kVtx + k * kWide + j] = v[k];
 }
 
 // ---- queries --------------------------------------------------------------
@@ -774,8 +795,8 @@ static cudaError_t build_wide(BvhBuffers& b, cudaStream_t s) {
     b.wide_ok = 31 * b.wide_depth + 1 <= kWideStack;
     int* wcode = b.wsrc + kWide * (size_t)n_wide;
     wide_fill_kernel<<<nblk(n_int, 128), 128, 0, s>>>(b.node_child, wid, flag, n_int, b.wsrc, wcode);
-    wide_refit_kernel<DIM><<<nblk((long long)n_wide * kWide, 256), 256, 0, s>>>(b.nodes, b.wsrc, wcode, n_wide,
-                                                                               b.wnodes);
+    wide_refit_kernel<DIM><<<nblk((long long)n_wide * kWide, 256), 256, 0, s>>>(b.nodes, b.prims, b.wsrc, wcode,
+                                                                               n_wide, b.wnodes);
     return cudaGetLastError();
 }
 

@@ -408,12 +408,18 @@ __device__ __forceinline__ float gradient_factor(float k, float R) {
 // ---- 32-wide BVH searched by a whole warp ---------------------------------
 // The binary LBVH collapsed five levels at a time: a wide node holds up to 32
 // children in SoA order, lo[DIM][32], hi[DIM][32], code[32] (>= 0: wide node,
-// < 0: ~leaf, kEmptyChild: unused slot with an empty box), so that lane j of
-// a warp loads slot j of every array with one coalesced request per array.
+// < 0: ~leaf, kEmptyChild: unused slot with an empty box) and, for leaf
+// children, the element's vertices vtx[DIM * DIM][32] (segment a, b or
+// triangle a, b, c), so that lane j of a warp loads slot j of every array with
+// one coalesced request per array, and a visit needs one round trip to memory
+// whether its children are nodes or elements.
 constexpr int kWide = 32;
 constexpr int kWideStack = 416;            // stack entries per warp: 31 x wide depth + 1 (checked at build)
 constexpr unsigned kWarpAll = 0xffffffffu;
-template <int DIM> struct WideLayout { static constexpr int kFloats = (2 * DIM + 1) * kWide; };
+template <int DIM> struct WideLayout {
+    static constexpr int kVtx = (2 * DIM + 1) * kWide;              // offset of the vertex arrays
+    static constexpr int kFloats = (2 * DIM + 1 + DIM * DIM) * kWide;
+};
 
 struct WideView {
     const float* wnodes;   // n_wide nodes of WideLayout<DIM>::kFloats floats, root first
@@ -428,7 +434,8 @@ struct WideView {
 // shuffles (ties to the lower leaf index), and the inner children that can
 // still hold a closer leaf go on the warp's stack in shared memory with the
 // nearest on top (depth-first, nearest child first, the others in Morton
-// order, all pruned by the running bound when popped).
+// order, all pruned by the running bound when popped).  n_nodes counts node
+// visits (a leaf child's vertices come with its node).
 // best2 / best hold each lane's bound on entry (kInf / -1 without one) and
 // the result on exit.  Called by all 32 lanes with the same `need` and each
 // lane's own view (lanes may belong to different problems).  Returns error
@@ -465,13 +472,15 @@ __device__ __forceinline__ int wide_closest(const WideView& mine, unsigned need,
                 if (!(e.x < b2)) continue;                     // pruned by a closer leaf found since
                 if (--budget < 0) { err |= 1; break; }
                 const float* f = wn + (size_t)__float_as_int(e.y) * WideLayout<DIM>::kFloats;
-                float lo[DIM], hi[DIM];
+                float lo[DIM], hi[DIM], vt[DIM * DIM];
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) {
                     lo[k] = __ldg(f + k * kWide + lane);
                     hi[k] = __ldg(f + (DIM + k) * kWide + lane);
                 }
                 const int code = __float_as_int(__ldg(f + 2 * DIM * kWide + lane));
+#pragma unroll
+                for (int k = 0; k < DIM * DIM; ++k) vt[k] = __ldg(f + WideLayout<DIM>::kVtx + k * kWide + lane);
                 const float cd = box_dist2<DIM>(q, lo, hi);
                 if (lane == 0) ++n_nodes;
                 const bool leaf = code < 0 && cd < b2;
@@ -479,8 +488,17 @@ __device__ __forceinline__ int wide_closest(const WideView& mine, unsigned need,
                 if (lm) {
                     float dd = kInf;
                     int pi = 0x7fffffff;
-                    if (leaf) { pi = ~code; dd = prim_dist2<DIM>(prims, pi, q); }
-                    if (lane == 0) n_prims += __popc(lm);
+                    if (leaf) {
+                        pi = ~code;
+                        if (DIM == 2) {
+                            float t;
+                            dd = seg_closest(q, vt[0], vt[1], vt[2], vt[3], t);
+                        } else {
+                            float w1, w2;
+                            dd = tri_closest(q, make_float3(vt[0], vt[1], vt[2]), make_float3(vt[3], vt[4], vt[5]),
+                                             make_float3(vt[6], vt[7], vt[8]), w1, w2);
+                        }
+                    }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) {
                         const float od = __shfl_xor_sync(kWarpAll, dd, o);
