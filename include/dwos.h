@@ -264,6 +264,12 @@ dwos_status dwos_grad_l2_cv(dwos_ctx* ctx, int n_query, const float* xq, const f
  * stream (the network's stream is set to it).  Asynchronous. */
 dwos_status dwos_cv_table(dwos_ctx* ctx, dwos_mlp* mlp, float* table);
 
+/* Sizes of the acceleration structures built by dwos_set_boundary /
+ * dwos_set_params: info[0..5] = elements, elements in the binary tree,
+ * outsized elements kept out of it, binary inner nodes, 32-wide nodes, levels
+ * of the 32-wide tree.  Synchronous (host array). */
+dwos_status dwos_bvh_info(const dwos_ctx* ctx, int32_t* info);
+
 /* Raw per-walk records (n_query x walks_per_point rows, row p*W + w, Philox
  * walk id walk_id_base + p*W + w).  differential = 0 runs Algorithm 1 only
  * (record.u, record.elem, record.b*, meta; c = 0).  trace (optional,

@@ -614,6 +614,18 @@ __global__ void cv_table_kernel(const float* __restrict__ vert, const int* __res
 
 }  // namespace
 
+dwos_status dwos_bvh_info(const dwos_ctx* ctx, int32_t* info) {
+    if (!ctx || !info) return fail(nullptr, DWOS_ERR_INVALID_ARG, "NULL argument");
+    if (!ctx->have_boundary) return fail(const_cast<dwos_ctx*>(ctx), DWOS_ERR_STATE, "no boundary");
+    info[0] = ctx->n_elem;
+    info[1] = ctx->bvh.n_tree;
+    info[2] = ctx->bvh.n_big;
+    info[3] = ctx->bvh.n_internal;
+    info[4] = ctx->bvh.n_wide;
+    info[5] = ctx->bvh.wide_depth;
+    return DWOS_OK;
+}
+
 dwos_status dwos_cv_table(dwos_ctx* ctx, dwos_mlp* mlp, float* table) {
     if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
     if (!mlp || !table) return fail(ctx, DWOS_ERR_INVALID_ARG, "NULL argument");

@@ -9,6 +9,8 @@
 #include <cub/device/device_scan.cuh>
 
 #include <cstring>
+#include <utility>
+#include <vector>
 
 #include "dwos_device.cuh"
 #include "dwos_internal.h"
@@ -333,48 +335,79 @@ __global__ void single_leaf_kernel(const float* vert, const int* elem, const int
 }
 
 // ---- 32-wide tree -----------------------------------------------------------
-// Depth of every internal node; nodes at depths 0, 5, 10, ... root the wide
-// nodes (flag 1).
-__global__ void wide_depth_kernel(const int* node_parent, int n_int, int* depth, int* flag, int* winfo) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_int) return;
-    int d = 0;
-    for (int a = node_parent[i]; a >= 0 && d <= n_int; a = node_parent[a]) ++d;
-    depth[i] = d;
-    flag[i] = (d % 5) == 0 ? 1 : 0;
-    atomicMax(winfo + 1, d);
+// Built top-down, one level per launch: a wide node starts from its binary
+// root's two children and keeps opening the inner child with the largest box
+// (surface area in 3D, perimeter in 2D) until it holds 32 children or only
+// leaves; its inner children become the next level's wide nodes.
+
+template <int DIM>
+__device__ __forceinline__ float child_area(const float4* nodes, int parent, int side) {
+    const float* b = reinterpret_cast<const float*>(nodes + BvhLayout<DIM>::kNodeF4 * parent) + (DIM == 2 ? 4 : 6) * side;
+    const float ex = b[DIM] - b[0], ey = b[DIM + 1] - b[1];
+    if (DIM == 2) return ex + ey;
+    const float ez = b[DIM + 2] - b[2];
+    return ex * ey + ey * ez + ez * ex;
 }
 
-__global__ void wide_count_kernel(const int* wid, const int* flag, int n_int, int* winfo) {
-    winfo[0] = wid[n_int - 1] + flag[n_int - 1];
-}
-
-// Children of one wide node: its binary subtree's frontier at relative depth
-// 5 (or leaves above it), left to right.  Each slot records the child's code
-// and where the binary tree keeps its box (parent node and side).
-__global__ void wide_fill_kernel(const int* node_child, const int* wid, const int* flag, int n_int, int* wsrc,
-                                 int* wcode) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_int || !flag[i]) return;
-    const int w = wid[i];
-    int st_node[8], st_rel[8], st_side[8], top = 0;   // pending binary children: parent, parent's depth, side
-    st_node[top] = i; st_rel[top] = 0; st_side[top] = 1; ++top;
-    st_node[top] = i; st_rel[top] = 0; st_side[top] = 0; ++top;
+// Frontier of each wide node of this level (in order), and its inner-child count.
+template <int DIM>
+__global__ void wide_level_kernel(const float4* nodes, const int* node_child, const int* roots, int m,
+                                  int* fr_code, int* fr_src, int* n_inner) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= m) return;
+    const int r = roots[w];
+    int code[kWide], src[kWide];
+    float area[kWide];
     int cnt = 0;
-    while (top > 0) {
-        --top;
-        const int par = st_node[top], rel = st_rel[top], side = st_side[top];
-        const int c = node_child[2 * par + side];
-        if (c < 0 || rel + 1 == 5) {                 // a leaf, or the root of the next wide node
-            wcode[kWide * w + cnt] = c < 0 ? c : wid[c];
-            wsrc[kWide * w + cnt] = (par << 1) | side;
-            ++cnt;
+    for (int side = 0; side < 2; ++side) {
+        code[cnt] = node_child[2 * r + side];
+        src[cnt] = (r << 1) | side;
+        area[cnt] = child_area<DIM>(nodes, r, side);
+        ++cnt;
+    }
+    while (cnt < kWide) {
+        int pick = -1;
+        float best = -1.0f;
+        for (int i = 0; i < cnt; ++i)
+            if (code[i] >= 0 && area[i] > best) { best = area[i]; pick = i; }
+        if (pick < 0) break;
+        const int c = code[pick];
+        for (int i = cnt; i > pick + 1; --i) { code[i] = code[i - 1]; src[i] = src[i - 1]; area[i] = area[i - 1]; }
+        for (int side = 0; side < 2; ++side) {
+            code[pick + side] = node_child[2 * c + side];
+            src[pick + side] = (c << 1) | side;
+            area[pick + side] = child_area<DIM>(nodes, c, side);
+        }
+        ++cnt;
+    }
+    int inner = 0;
+    for (int i = 0; i < kWide; ++i) {
+        const bool used = i < cnt;
+        fr_code[kWide * w + i] = used ? code[i] : kEmptyChild;
+        fr_src[kWide * w + i] = used ? src[i] : -1;
+        inner += (used && code[i] >= 0) ? 1 : 0;
+    }
+    n_inner[w] = inner;
+}
+
+// Wide-node codes of the inner children (the next level, numbered after
+// next_base in order) and the next level's binary roots.
+__global__ void wide_assign_kernel(const int* fr_code, const int* fr_src, const int* offset, int m, int next_base,
+                                   int* wcode, int* wsrc, int* next_roots) {
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= m) return;
+    int k = offset[w];
+    for (int i = 0; i < kWide; ++i) {
+        const int c = fr_code[kWide * w + i];
+        wsrc[kWide * w + i] = fr_src[kWide * w + i];
+        if (c >= 0 && c != kEmptyChild) {
+            next_roots[k] = c;
+            wcode[kWide * w + i] = next_base + k;
+            ++k;
         } else {
-            st_node[top] = c; st_rel[top] = rel + 1; st_side[top] = 1; ++top;
-            st_node[top] = c; st_rel[top] = rel + 1; st_side[top] = 0; ++top;
+            wcode[kWide * w + i] = c;
         }
     }
-    for (; cnt < kWide; ++cnt) { wcode[kWide * w + cnt] = kEmptyChild; wsrc[kWide * w + cnt] = -1; }
 }
 
 // Child boxes gathered from the binary tree (its refit already ran) and codes.
@@ -735,12 +768,9 @@ cudaError_t bvh_reserve(BvhBuffers& b, int dim, int n_elem) {
     DW_TRY(cudaMalloc(&b.node_cell, sizeof(float) * 2 * dim * (size_t)n_int));
     DW_TRY(cudaMalloc(&b.bounds, sizeof(unsigned int) * 6));
     DW_TRY(cudaMalloc(&b.stats, sizeof(float) * 2 + sizeof(int) * 4));
-    size_t tmp = 0, tmp_scan = 0;
+    size_t tmp = 0;
     DW_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tmp, b.keys, b.keys_sorted, b.vals, b.vals_sorted, n_elem));
-    DW_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tmp_scan, b.counters, b.vals, n_int));
-    tmp = tmp > tmp_scan ? tmp : tmp_scan;
     DW_TRY(cudaMalloc(&b.sort_tmp, tmp));
-    DW_TRY(cudaMalloc(&b.winfo, sizeof(int) * 4));
 #undef DW_TRY
     b.sort_tmp_bytes = tmp;
     b.capacity = n_elem;
@@ -753,51 +783,97 @@ void bvh_free(BvhBuffers& b) {
     cudaFree(b.vals); cudaFree(b.vals_sorted); cudaFree(b.leaf_parent); cudaFree(b.node_parent);
     cudaFree(b.node_child); cudaFree(b.counters); cudaFree(b.bounds); cudaFree(b.stats); cudaFree(b.node_cell);
     cudaFree(b.sort_tmp);
-    cudaFree(b.wnodes); cudaFree(b.wsrc); cudaFree(b.winfo);
+    cudaFree(b.wnodes); cudaFree(b.wsrc);
     b = BvhBuffers();
 }
 
 constexpr int kMaxBig = 64;
 
-// Collapse the binary tree (nt - 1 = n_internal >= 1 nodes, boxes refit) into
-// the 32-wide tree.  Scratch: vals (depth), counters (flags), keys (wide ids);
-// one host synchronisation reads the node count and the depth.
+// Collapse the binary tree (n_internal >= 1 nodes, boxes refit) into the
+// 32-wide tree, level by level (one host synchronisation per level reads the
+// next level's size).  Nodes are numbered in level order, the root first.
 template <int DIM>
 static cudaError_t build_wide(BvhBuffers& b, cudaStream_t s) {
     const int n_int = b.n_internal;
-    int* depth = b.vals;
-    int* flag = b.counters;
-    int* wid = reinterpret_cast<int*>(b.keys);
-    cudaError_t e = cudaMemsetAsync(b.winfo, 0, sizeof(int) * 4, s);
-    if (e != cudaSuccess) return e;
-    wide_depth_kernel<<<nblk(n_int, 256), 256, 0, s>>>(b.node_parent, n_int, depth, flag, b.winfo);
-    size_t tmp = b.sort_tmp_bytes;
-    e = cub::DeviceScan::ExclusiveSum(b.sort_tmp, tmp, flag, wid, n_int, s);
-    if (e != cudaSuccess) return e;
-    wide_count_kernel<<<1, 1, 0, s>>>(wid, flag, n_int, b.winfo);
-    int info[2] = {0, 0};
-    e = cudaMemcpyAsync(info, b.winfo, sizeof(int) * 2, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) return e;
-    e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return e;
-    const int n_wide = info[0];
+    cudaError_t e = cudaSuccess;
+    std::vector<int*> lv_code, lv_src;      // per level: final codes and sources of its nodes
+    std::vector<int> lv_m;
+    int* roots = nullptr;
+    int* next = nullptr;
+    int* fr_code = nullptr;
+    int* fr_src = nullptr;
+    int* n_inner = nullptr;
+    int* offset = nullptr;
+    int m = 1, base = 0, depth = 0;
+    auto cleanup = [&]() {
+        for (int* p : lv_code) cudaFree(p);
+        for (int* p : lv_src) cudaFree(p);
+        cudaFree(roots); cudaFree(next); cudaFree(fr_code); cudaFree(fr_src); cudaFree(n_inner); cudaFree(offset);
+    };
+#define DW_W(x) do { e = (x); if (e != cudaSuccess) { cleanup(); return e; } } while (0)
+    DW_W(cudaMalloc(&roots, sizeof(int)));
+    DW_W(cudaMemsetAsync(roots, 0, sizeof(int), s));          // the binary root is node 0
+    while (m > 0) {
+        if (++depth > 64) { cleanup(); return cudaErrorInvalidValue; }   // a 64-level wide tree cannot happen
+        int *lc = nullptr, *ls = nullptr;
+        DW_W(cudaMalloc(&lc, sizeof(int) * kWide * (size_t)m));
+        lv_code.push_back(lc);
+        DW_W(cudaMalloc(&ls, sizeof(int) * kWide * (size_t)m));
+        lv_src.push_back(ls);
+        lv_m.push_back(m);
+        cudaFree(fr_code); cudaFree(fr_src); cudaFree(n_inner); cudaFree(offset);
+        fr_code = fr_src = n_inner = offset = nullptr;
+        DW_W(cudaMalloc(&fr_code, sizeof(int) * kWide * (size_t)m));
+        DW_W(cudaMalloc(&fr_src, sizeof(int) * kWide * (size_t)m));
+        DW_W(cudaMalloc(&n_inner, sizeof(int) * ((size_t)m + 1)));
+        DW_W(cudaMalloc(&offset, sizeof(int) * ((size_t)m + 1)));
+        wide_level_kernel<DIM><<<nblk(m, 128), 128, 0, s>>>(b.nodes, b.node_child, roots, m, fr_code, fr_src, n_inner);
+        DW_W(cudaMemsetAsync(n_inner + m, 0, sizeof(int), s));
+        size_t tmp = 0;
+        DW_W(cub::DeviceScan::ExclusiveSum(nullptr, tmp, n_inner, offset, m + 1, s));
+        void* tmp_buf = nullptr;
+        DW_W(cudaMalloc(&tmp_buf, tmp));
+        e = cub::DeviceScan::ExclusiveSum(tmp_buf, tmp, n_inner, offset, m + 1, s);
+        int next_m = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&next_m, offset + m, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(tmp_buf);
+        if (e != cudaSuccess) { cleanup(); return e; }
+        cudaFree(next);
+        next = nullptr;
+        if (next_m > 0) DW_W(cudaMalloc(&next, sizeof(int) * (size_t)next_m));
+        wide_assign_kernel<<<nblk(m, 128), 128, 0, s>>>(fr_code, fr_src, offset, m, base + m, lc, ls, next);
+        DW_W(cudaGetLastError());
+        base += m;
+        m = next_m;
+        std::swap(roots, next);
+    }
+    const int n_wide = base;
     if (n_wide > b.wide_cap) {
         cudaFree(b.wnodes); cudaFree(b.wsrc);
         b.wnodes = nullptr; b.wsrc = nullptr; b.wide_cap = 0;
-        e = cudaMalloc(&b.wnodes, sizeof(float) * WideLayout<3>::kFloats * (size_t)n_wide);
-        if (e != cudaSuccess) return e;
-        e = cudaMalloc(&b.wsrc, sizeof(int) * 2 * kWide * (size_t)n_wide);   // sources, then codes
-        if (e != cudaSuccess) return e;
+        DW_W(cudaMalloc(&b.wnodes, sizeof(float) * WideLayout<3>::kFloats * (size_t)n_wide));
+        DW_W(cudaMalloc(&b.wsrc, sizeof(int) * 2 * kWide * (size_t)n_wide));   // sources, then codes
         b.wide_cap = n_wide;
     }
     b.n_wide = n_wide;
-    b.wide_depth = info[1] / 5 + 1;
+    b.wide_depth = depth;
     b.wide_ok = 31 * b.wide_depth + 1 <= kWideStack;
     int* wcode = b.wsrc + kWide * (size_t)n_wide;
-    wide_fill_kernel<<<nblk(n_int, 128), 128, 0, s>>>(b.node_child, wid, flag, n_int, b.wsrc, wcode);
+    size_t at = 0;
+    for (size_t l = 0; l < lv_m.size(); ++l) {
+        const size_t n = kWide * (size_t)lv_m[l];
+        DW_W(cudaMemcpyAsync(b.wsrc + at, lv_src[l], sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+        DW_W(cudaMemcpyAsync(wcode + at, lv_code[l], sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
+        at += n;
+    }
     wide_refit_kernel<DIM><<<nblk((long long)n_wide * kWide, 256), 256, 0, s>>>(b.nodes, b.prims, b.wsrc, wcode,
                                                                                n_wide, b.wnodes);
-    return cudaGetLastError();
+    DW_W(cudaGetLastError());
+    DW_W(cudaStreamSynchronize(s));      // the level buffers are freed next
+    cleanup();
+#undef DW_W
+    return cudaSuccess;
 }
 
 template <int DIM>

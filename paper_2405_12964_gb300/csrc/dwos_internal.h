@@ -102,10 +102,10 @@ struct BvhBuffers {
     void* sort_tmp = nullptr;
     size_t sort_tmp_bytes = 0;
     int capacity = 0;
-    // 32-wide tree collapsed from the binary one (rebuilt with it)
+    // 32-wide tree collapsed from the binary one (rebuilt with it): each wide node opens
+    // its largest inner child until it has 32 children; nodes in level order
     float* wnodes = nullptr;         // n_wide x WideLayout<dim>::kFloats
     int* wsrc = nullptr;             // per slot: (binary parent << 1 | side) of the child's box, -1 unused
-    int* winfo = nullptr;            // device: n_wide, max binary depth
     int n_wide = 0, wide_depth = 0, wide_cap = 0;
     bool wide_ok = false;            // the warp-wide search fits its stack on this tree
 };

@@ -100,6 +100,7 @@ _SIGS = {
     "dwos_mlp_eval": [_vp, _i, _vp, _vp, _vp, _vp, _i],
     "dwos_mlp_sync": [_vp],
     "dwos_cv_table": [_vp, _vp, _vp],
+    "dwos_bvh_info": [_vp, _vp],
 }
 MLP_NPARAM = 14088
 
@@ -312,6 +313,12 @@ class Solver:
         if debug:
             out["debug"] = dbg
         return out
+
+    def bvh_info(self) -> dict:
+        info = (ctypes.c_int32 * 6)()
+        self._check(lib().dwos_bvh_info(self._h, info))
+        keys = ("n_elem", "n_tree", "n_big", "n_internal", "n_wide", "wide_depth")
+        return dict(zip(keys, [int(v) for v in info]))
 
     def cv_table(self, net: "ControlVariateNet") -> torch.Tensor:
         """The nested walks' control-variate table (n_elem, 4) on the device:

@@ -216,6 +216,10 @@ def test_warp_wide_search_is_the_one_that_ran(Solver):
         out.append(s.walk_records(sc.query, 64)["rec"])
         st = s.stats()
         nodes.append(st["nodes_visited"] / (st["steps_main"] + st["steps_nested"]))
+    info = s.bvh_info()
+    fill = (info["n_wide"] - 1 + info["n_tree"]) / (32.0 * info["n_wide"])
+    print("32-wide tree: %d nodes, %d levels, %.2f of the child slots used" % (info["n_wide"], info["wide_depth"], fill))
+    assert info["n_tree"] + info["n_big"] == info["n_elem"] and fill > 0.5
     same = out[0]["elem"] == out[1]["elem"]
     assert same.mean() > 0.99
     assert np.allclose(out[0]["u"][same], out[1]["u"][same], rtol=1e-5, atol=1e-6)
