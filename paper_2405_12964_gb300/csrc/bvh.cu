@@ -214,7 +214,7 @@ __device__ void morton_cell(unsigned int key, int p, const unsigned int* bounds,
 
 template <int DIM>
 __global__ void radix_tree_kernel(const unsigned int* keys, int n, int* node_child, int* node_parent,
-                                  int* leaf_parent, const unsigned int* bounds, float* node_cell) {
+                                  int* leaf_parent, const unsigned int* bounds, float* node_cell, int* node_count) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n - 1) return;
     const int dir = (delta(keys, n, i, i + 1) - delta(keys, n, i, i - 1)) >= 0 ? 1 : -1;
@@ -233,6 +233,7 @@ __global__ void radix_tree_kernel(const unsigned int* keys, int n, int* node_chi
     } while (t > 1);
     const int split = i + s * dir + min(dir, 0);
     const int first = min(i, j), last = max(i, j);
+    node_count[i] = last - first + 1;               // leaves under node i
     int left, right;
     if (first == split) { left = ~split; leaf_parent[split] = i; }
     else { left = split; node_parent[split] = i; }
@@ -336,38 +337,27 @@ __global__ void single_leaf_kernel(const float* vert, const int* elem, const int
 
 // ---- 32-wide tree -----------------------------------------------------------
 // Built top-down, one level per launch: a wide node starts from its binary
-// root's two children and keeps opening the inner child with the largest box
-// (surface area in 3D, perimeter in 2D) until it holds 32 children or only
-// leaves; its inner children become the next level's wide nodes.
-
-template <int DIM>
-__device__ __forceinline__ float child_area(const float4* nodes, int parent, int side) {
-    const float* b = reinterpret_cast<const float*>(nodes + BvhLayout<DIM>::kNodeF4 * parent) + (DIM == 2 ? 4 : 6) * side;
-    const float ex = b[DIM] - b[0], ey = b[DIM + 1] - b[1];
-    if (DIM == 2) return ex + ey;
-    const float ez = b[DIM + 2] - b[2];
-    return ex * ey + ey * ez + ez * ex;
-}
+// root's two children and keeps opening the inner child with the most leaves
+// under it until it holds 32 children or only leaves; its inner children
+// become the next level's wide nodes.  (Opening by box size instead leaves
+// many small inner children behind, each a nearly empty wide node.)
 
 // Frontier of each wide node of this level (in order), and its inner-child count.
-template <int DIM>
-__global__ void wide_level_kernel(const float4* nodes, const int* node_child, const int* roots, int m,
+__global__ void wide_level_kernel(const int* node_child, const int* node_count, const int* roots, int m,
                                   int* fr_code, int* fr_src, int* n_inner) {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
     if (w >= m) return;
     const int r = roots[w];
-    int code[kWide], src[kWide];
-    float area[kWide];
+    int code[kWide], src[kWide], area[kWide];
     int cnt = 0;
     for (int side = 0; side < 2; ++side) {
         code[cnt] = node_child[2 * r + side];
         src[cnt] = (r << 1) | side;
-        area[cnt] = child_area<DIM>(nodes, r, side);
+        area[cnt] = code[cnt] >= 0 ? node_count[code[cnt]] : 1;
         ++cnt;
     }
     while (cnt < kWide) {
-        int pick = -1;
-        float best = -1.0f;
+        int pick = -1, best = 0;
         for (int i = 0; i < cnt; ++i)
             if (code[i] >= 0 && area[i] > best) { best = area[i]; pick = i; }
         if (pick < 0) break;
@@ -376,7 +366,7 @@ __global__ void wide_level_kernel(const float4* nodes, const int* node_child, co
         for (int side = 0; side < 2; ++side) {
             code[pick + side] = node_child[2 * c + side];
             src[pick + side] = (c << 1) | side;
-            area[pick + side] = child_area<DIM>(nodes, c, side);
+            area[pick + side] = code[pick + side] >= 0 ? node_count[code[pick + side]] : 1;
         }
         ++cnt;
     }
@@ -765,6 +755,7 @@ cudaError_t bvh_reserve(BvhBuffers& b, int dim, int n_elem) {
     DW_TRY(cudaMalloc(&b.node_parent, sizeof(int) * (size_t)n_int));
     DW_TRY(cudaMalloc(&b.node_child, sizeof(int) * 2 * (size_t)n_int));
     DW_TRY(cudaMalloc(&b.counters, sizeof(int) * (size_t)n_int));
+    DW_TRY(cudaMalloc(&b.node_count, sizeof(int) * (size_t)n_int));
     DW_TRY(cudaMalloc(&b.node_cell, sizeof(float) * 2 * dim * (size_t)n_int));
     DW_TRY(cudaMalloc(&b.bounds, sizeof(unsigned int) * 6));
     DW_TRY(cudaMalloc(&b.stats, sizeof(float) * 2 + sizeof(int) * 4));
@@ -783,7 +774,7 @@ void bvh_free(BvhBuffers& b) {
     cudaFree(b.vals); cudaFree(b.vals_sorted); cudaFree(b.leaf_parent); cudaFree(b.node_parent);
     cudaFree(b.node_child); cudaFree(b.counters); cudaFree(b.bounds); cudaFree(b.stats); cudaFree(b.node_cell);
     cudaFree(b.sort_tmp);
-    cudaFree(b.wnodes); cudaFree(b.wsrc);
+    cudaFree(b.wnodes); cudaFree(b.wsrc); cudaFree(b.node_count);
     b = BvhBuffers();
 }
 
@@ -827,7 +818,8 @@ static cudaError_t build_wide(BvhBuffers& b, cudaStream_t s) {
         DW_W(cudaMalloc(&fr_src, sizeof(int) * kWide * (size_t)m));
         DW_W(cudaMalloc(&n_inner, sizeof(int) * ((size_t)m + 1)));
         DW_W(cudaMalloc(&offset, sizeof(int) * ((size_t)m + 1)));
-        wide_level_kernel<DIM><<<nblk(m, 128), 128, 0, s>>>(b.nodes, b.node_child, roots, m, fr_code, fr_src, n_inner);
+        wide_level_kernel<<<nblk(m, 128), 128, 0, s>>>(b.node_child, b.node_count, roots, m, fr_code, fr_src,
+                                                       n_inner);
         DW_W(cudaMemsetAsync(n_inner + m, 0, sizeof(int), s));
         size_t tmp = 0;
         DW_W(cub::DeviceScan::ExclusiveSum(nullptr, tmp, n_inner, offset, m + 1, s));
@@ -914,7 +906,8 @@ static cudaError_t build_impl(BvhBuffers& b, const float* vert, const int* elem,
     if (nt >= 2) {
         b.n_internal = nt - 1;
         radix_tree_kernel<DIM><<<nblk(nt - 1, 256), 256, 0, s>>>(b.keys_sorted, nt, b.node_child, b.node_parent,
-                                                                 b.leaf_parent, b.bounds, b.node_cell);
+                                                                 b.leaf_parent, b.bounds, b.node_cell,
+                                                                 b.node_count);
         e = cudaMemsetAsync(b.counters, 0, sizeof(int) * (size_t)(nt - 1), s);
         if (e != cudaSuccess) return e;
         refit_kernel<DIM><<<nblk(nt, 256), 256, 0, s>>>(vert, elem, b.vals_sorted, nt, b.node_child,
