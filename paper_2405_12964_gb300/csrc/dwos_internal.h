@@ -95,7 +95,7 @@ struct BvhBuffers {
     int* node_parent = nullptr;
     int* node_child = nullptr;    // 2 per internal node
     int* counters = nullptr;
-    int* node_count = nullptr;       // leaves under each internal node
+    int* node_count = nullptr;       // per internal node: leaves under it; then (second half) its first leaf
     float* node_cell = nullptr;      // Morton cell box per internal node
     float r_max = 0.0f;              // largest element half box diagonal (tree elements)
     unsigned int* bounds = nullptr;  // 2*dim ordered-uint scene bounds
@@ -103,8 +103,7 @@ struct BvhBuffers {
     void* sort_tmp = nullptr;
     size_t sort_tmp_bytes = 0;
     int capacity = 0;
-    // 32-wide tree collapsed from the binary one (rebuilt with it): each wide node opens
-    // its inner child with the most leaves until it has 32 children; nodes in level order
+    // 32-wide tree collapsed from the binary one (rebuilt with it), nodes in level order
     float* wnodes = nullptr;         // n_wide x WideLayout<dim>::kFloats
     int* wsrc = nullptr;             // per slot: (binary parent << 1 | side) of the child's box, -1 unused
     int n_wide = 0, wide_depth = 0, wide_cap = 0;
