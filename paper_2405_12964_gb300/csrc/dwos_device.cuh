@@ -414,7 +414,7 @@ __device__ __forceinline__ float gradient_factor(float k, float R) {
 // one coalesced request per array, and a visit needs one round trip to memory
 // whether its children are nodes or elements.
 constexpr int kWide = 32;
-constexpr int kWideStack = 416;            // stack entries per warp: 31 x wide depth + 1 (checked at build)
+constexpr int kWideStack = 224;            // stack entries per warp: 31 x wide depth + 1 (checked at build): depth <= 7
 constexpr unsigned kWarpAll = 0xffffffffu;
 template <int DIM> struct WideLayout {
     static constexpr int kVtx = (2 * DIM + 1) * kWide;              // offset of the vertex arrays
