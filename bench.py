@@ -526,6 +526,8 @@ def main():
     walk_s = sum(kernel_ms) / 1e3
     achieved = alg_bytes / walk_s / 1e9 / args.steps * args.steps
     hbm, src = peaks()
+    from paper_2405_12964_gb300.dwos import probe_l2_read
+    l2 = probe_l2_read(local)
     kname = f"walk_kernel<{sc.dim},{'true' if trav == 2 else 'false'}>"
     traffic_per_step = measured_traffic(kname, args.workload)
 
@@ -585,7 +587,10 @@ def main():
                                             else "no ncu capture of the current kernel sources"),
                          "kernel": kname, "peak_source": src,
                          "bytes_per_walk_step": alg_bytes / max(steps_done, 1),
-                         "walk_kernel_ms": walk_s * 1e3 / args.steps},
+                         "walk_kernel_ms": walk_s * 1e3 / args.steps,
+                         "l2": {"peak": l2, "unit": "GB/s", "frac": achieved / l2,
+                                "peak_source": "measured in this run: 32 MB L2-resident buffer read 50 times "
+                                               "(dwos_probe_l2_read)"}},
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(launches),
             "clocks": clk,

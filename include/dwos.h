@@ -264,6 +264,12 @@ dwos_status dwos_grad_l2_cv(dwos_ctx* ctx, int n_query, const float* xq, const f
  * stream (the network's stream is set to it).  Asynchronous. */
 dwos_status dwos_cv_table(dwos_ctx* ctx, dwos_mlp* mlp, float* table);
 
+/* Measurement helper (not part of the method): read bandwidth of an
+ * L2-resident buffer of `bytes` bytes on `device`, read `reps` times by a
+ * coalesced grid-stride kernel; the roof against which the walk kernel's
+ * tree traffic (which stays on chip) is compared.  Synchronous. */
+dwos_status dwos_probe_l2_read(int device, size_t bytes, int reps, double* gbs);
+
 /* Sizes of the acceleration structures built by dwos_set_boundary /
  * dwos_set_params: info[0..5] = elements, elements in the binary tree,
  * outsized elements kept out of it, binary inner nodes, 32-wide nodes, levels

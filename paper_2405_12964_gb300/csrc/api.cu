@@ -614,6 +614,54 @@ __global__ void cv_table_kernel(const float* __restrict__ vert, const int* __res
 
 }  // namespace
 
+namespace {
+// Reads `words` float4 of an L2-resident buffer `reps` times (grid-stride,
+// coalesced) and folds them into one value so the loads cannot be dropped.
+__global__ void l2_read_kernel(const float4* __restrict__ buf, size_t words, int reps, float* sink) {
+    float acc = 0.0f;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (int r = 0; r < reps; ++r)
+        for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += stride) {
+            const float4 v = __ldcg(buf + i);
+            acc += v.x + v.y + v.z + v.w;
+        }
+    if (acc == 1.2345e-30f) *sink = acc;
+}
+}  // namespace
+
+dwos_status dwos_probe_l2_read(int device, size_t bytes, int reps, double* gbs) {
+    if (!gbs || bytes < 16 || reps < 1) return fail(nullptr, DWOS_ERR_INVALID_ARG, "bad arguments");
+    cudaError_t e = cudaSetDevice(device);
+    if (e != cudaSuccess) return fail(nullptr, DWOS_ERR_CUDA, cudaGetErrorString(e));
+    int n_sm = 0;
+    cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, device);
+    const size_t words = bytes / 16;
+    float4* buf = nullptr;
+    float* sink = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    float ms = 0.0f;
+    e = cudaMalloc(&buf, words * 16);
+    if (e == cudaSuccess) e = cudaMalloc(&sink, sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(buf, 0, words * 16);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) {
+        l2_read_kernel<<<n_sm * 8, 256>>>(buf, words, 1, sink);           // bring the buffer into L2
+        cudaEventRecord(a);
+        l2_read_kernel<<<n_sm * 8, 256>>>(buf, words, reps, sink);
+        cudaEventRecord(b);
+        e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(buf);
+    cudaFree(sink);
+    if (e != cudaSuccess) return fail(nullptr, DWOS_ERR_CUDA, cudaGetErrorString(e));
+    *gbs = (double)words * 16.0 * reps / (ms * 1e-3) / 1e9;
+    return DWOS_OK;
+}
+
 dwos_status dwos_bvh_info(const dwos_ctx* ctx, int32_t* info) {
     if (!ctx || !info) return fail(nullptr, DWOS_ERR_INVALID_ARG, "NULL argument");
     if (!ctx->have_boundary) return fail(const_cast<dwos_ctx*>(ctx), DWOS_ERR_STATE, "no boundary");

@@ -101,6 +101,7 @@ _SIGS = {
     "dwos_mlp_sync": [_vp],
     "dwos_cv_table": [_vp, _vp, _vp],
     "dwos_bvh_info": [_vp, _vp],
+    "dwos_probe_l2_read": [_i, ctypes.c_size_t, _i, _vp],
 }
 MLP_NPARAM = 14088
 
@@ -542,6 +543,15 @@ class ControlVariateNet:
         q = torch.empty(n, device=self.device, dtype=torch.float32)
         self._check(lib().dwos_mlp_eval(self._h, n, _ptr(x), _ptr(u), _ptr(gu), _ptr(q), MEM_DEVICE))
         return u, gu, q
+
+
+def probe_l2_read(device: int = 0, nbytes: int = 32 << 20, reps: int = 50) -> float:
+    """Measured read bandwidth (GB/s) of an L2-resident buffer (dwos_probe_l2_read)."""
+    out = ctypes.c_double()
+    st = lib().dwos_probe_l2_read(device, nbytes, reps, ctypes.byref(out))
+    if st:
+        raise DwosError(st, lib().dwos_last_error(None).decode())
+    return out.value
 
 
 def init_mlp_params(seed: int = 0) -> np.ndarray:
