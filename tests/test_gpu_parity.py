@@ -302,7 +302,7 @@ def test_product_estimators_match_oracle(Solver):
         assert abs(loss[0] - lo) <= 1e-4 * abs(lo) + 1e-7
     g1 = s.grad_l2(sc.query, uref, sc.walks)[1].cpu().numpy()
     g2 = s.grad_l2_product(sc.query, uref, sc.walks, product="ustat")[1].cpu().numpy()
-    assert np.array_equal(g1, g2)
+    assert np.allclose(g1, g2, rtol=1e-9, atol=1e-12 * np.abs(g1).max())     # FP64 atomics: order may differ
 
 
 def test_vertex_gradient_chains_to_parameters(Solver):
