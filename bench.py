@@ -485,7 +485,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    steps_done = nodes = prims = leaf_nodes = 0
+    steps_done = nodes = prims = 0
     kernel_ms = []
     grads = []
     for i in range(args.steps):
@@ -497,7 +497,6 @@ def main():
         steps_done += st["steps_main"] + st["steps_nested"]
         nodes += st["nodes_visited"]
         prims += st["prims_tested"]
-        leaf_nodes += st["leaf_node_visits"]
         kernel_ms.append(st["kernel_ms"])
         grads.append(g.cpu().numpy())
     torch.cuda.synchronize()
@@ -517,15 +516,13 @@ def main():
     rel = rmse / float(np.sqrt(np.mean(g_ref ** 2)))
 
     # roofline of the walk kernel: algorithmic bytes = BVH node fetches x node size
-    # (binary 48 / 64 B; 32-wide (2 dim + 1) x 128 B, plus dim^2 x 128 B of leaf
-    # vertices on the visits to nodes with leaf children)
+    # (binary 48 / 64 B; 32-wide (2 dim + 1 + dim^2) x 128 B, leaf vertices included)
     # + element fetches outside the nodes (the previous step's element, outsized
     # elements; all element tests of the binary search) x 16 / 48 B
     # + one 32 B record per walk + 8 B query load per walk
-    node_b = (2 * sc.dim + 1) * 128 if trav == 2 else (48 if sc.dim == 2 else 64)
+    node_b = (2 * sc.dim + 1 + sc.dim * sc.dim) * 128 if trav == 2 else (48 if sc.dim == 2 else 64)
     prim_b = 16 if sc.dim == 2 else 48
-    alg_bytes = (nodes * node_b + leaf_nodes * sc.dim * sc.dim * 128 + prims * prim_b
-                 + args.steps * total * (32 + 8))
+    alg_bytes = nodes * node_b + prims * prim_b + args.steps * total * (32 + 8)
     walk_s = sum(kernel_ms) / 1e3
     achieved = alg_bytes / walk_s / 1e9 / args.steps * args.steps
     hbm, src = peaks()
@@ -580,7 +577,6 @@ def main():
             "grad_rmse": rmse, "grad_rel_rmse": rel, "grad_rmse_x_seconds": rmse * (ms_per_step / 1e3),
             "walk_steps_per_step": steps_done / args.steps,
             "closest_point_search": {"nodes_per_query": nodes / max(steps_done, 1),
-                                     "leaf_node_visits_per_query": leaf_nodes / max(steps_done, 1),
                                      "element_fetches_per_query": prims / max(steps_done, 1)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,

@@ -136,7 +136,6 @@ typedef struct {
     uint64_t launches;      /* kernels this context has launched since creation */
     float kernel_ms;        /* device time of the last walk kernel (0 if unknown) */
     int blocks;             /* thread blocks of the last walk kernel */
-    uint64_t leaf_node_visits; /* 32-wide node visits that also read their leaf children's vertices */
 } dwos_run_stats;
 
 /* ---- context ------------------------------------------------------------ */

@@ -744,7 +744,6 @@ dwos_status dwos_last_stats(dwos_ctx* ctx, dwos_run_stats* out) {
     out->capped = c.capped;
     out->nodes_visited = c.nodes;
     out->prims_tested = c.prims;
-    out->leaf_node_visits = c.leaf_nodes;
     out->launches = ctx->launches;
     out->blocks = ctx->last_blocks;
     float ms = 0.0f;

@@ -387,7 +387,6 @@ dwos_status dwos_batch_stats(dwos_batch* b, dwos_run_stats* out) {
         out->capped += c.capped;
         out->nodes_visited += c.nodes;
         out->prims_tested += c.prims;
-        out->leaf_node_visits += c.leaf_nodes;
         if (c.error & 1) return bfail(b, DWOS_ERR_STEP_LIMIT, "BVH traversal exceeded its iteration bound");
     }
     return DWOS_OK;

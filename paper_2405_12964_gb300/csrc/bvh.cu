@@ -420,21 +420,6 @@ __global__ void wide_assign_kernel(const int* fr_code, const int* fr_src, const 
     }
 }
 
-// Flag the inner child codes whose wide node has leaf children (kHasLeaves).
-__global__ void wide_has_leaf_kernel(const int* wcode, int n_wide, int* has_leaf) {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= n_wide) return;
-    int h = 0;
-    for (int i = 0; i < kWide; ++i) h |= wcode[kWide * w + i] < 0 ? 1 : 0;
-    has_leaf[w] = h;
-}
-__global__ void wide_flag_kernel(int* wcode, int n_slots, const int* has_leaf) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_slots) return;
-    const int c = wcode[t];
-    if (c >= 0 && c != kEmptyChild && has_leaf[c]) wcode[t] = c | kHasLeaves;
-}
-
 // Child boxes gathered from the binary tree (its refit already ran) and codes.
 template <int DIM>
 __global__ void wide_refit_kernel(const float4* nodes, const float4* prims, const int* wsrc, const int* wcode,
@@ -536,7 +521,7 @@ __global__ void closest_wide_kernel(BvhView bvh, WideView wv, const int* prim_el
     for (int k = 0; k < DIM; ++k) q[k] = act ? p[DIM * i + k] : 0.0f;
     float best2 = kInf;
     int best = -1;
-    unsigned nn = 0, np = 0, nl = 0;
+    unsigned nn = 0, np = 0;
     if (act) {
         if (hint_elem) {
             const int h = hint_elem[i];
@@ -547,12 +532,11 @@ __global__ void closest_wide_kernel(BvhView bvh, WideView wv, const int* prim_el
         }
         big_closest<DIM>(bvh.prims, bvh.n_tree, bvh.n_big, q, best2, best, np);
     }
-    const int e = wide_closest<DIM>(wv, __ballot_sync(kWarpAll, act), q, best2, best, stk, nn, nl);
+    const int e = wide_closest<DIM>(wv, __ballot_sync(kWarpAll, act), q, best2, best, stk, nn, np);
     if (e) atomicOr(err, 1);
     if (ctr) {
         atomicAdd(&ctr->nodes, (unsigned long long)nn);
         atomicAdd(&ctr->prims, (unsigned long long)np);
-        atomicAdd(&ctr->leaf_nodes, (unsigned long long)nl);
     }
     if (!act) return;
     float w1 = 0.0f, w2 = 0.0f;
@@ -895,11 +879,6 @@ static cudaError_t build_wide(BvhBuffers& b, cudaStream_t s) {
         DW_W(cudaMemcpyAsync(wcode + at, lv_code[l], sizeof(int) * n, cudaMemcpyDeviceToDevice, s));
         at += n;
     }
-    int* has_leaf = nullptr;
-    DW_W(cudaMalloc(&has_leaf, sizeof(int) * (size_t)n_wide));
-    lv_code.push_back(has_leaf);         // freed with the level buffers
-    wide_has_leaf_kernel<<<nblk(n_wide, 128), 128, 0, s>>>(wcode, n_wide, has_leaf);
-    wide_flag_kernel<<<nblk((long long)n_wide * kWide, 256), 256, 0, s>>>(wcode, n_wide * kWide, has_leaf);
     wide_refit_kernel<DIM><<<nblk((long long)n_wide * kWide, 256), 256, 0, s>>>(b.nodes, b.prims, b.wsrc, wcode,
                                                                                n_wide, b.wnodes);
     DW_W(cudaGetLastError());

@@ -412,14 +412,10 @@ __device__ __forceinline__ float gradient_factor(float k, float R) {
 // children, the element's vertices vtx[DIM * DIM][32] (segment a, b or
 // triangle a, b, c), so that lane j of a warp loads slot j of every array with
 // one coalesced request per array, and a visit needs one round trip to memory
-// whether its children are nodes or elements.  An inner child's code carries
-// kHasLeaves when that node has leaf children; other nodes skip the vertex
-// arrays (7 of 16 arrays in 3D).
+// whether its children are nodes or elements.
 constexpr int kWide = 32;
 constexpr int kWideStack = 224;            // stack entries per warp: 31 x wide depth + 1 (checked at build): depth <= 7
 constexpr unsigned kWarpAll = 0xffffffffu;
-constexpr int kHasLeaves = 1 << 30;         // inner child code flag: that wide node has leaf children
-constexpr int kNodeMask = kHasLeaves - 1;
 template <int DIM> struct WideLayout {
     static constexpr int kVtx = (2 * DIM + 1) * kWide;              // offset of the vertex arrays
     static constexpr int kFloats = (2 * DIM + 1 + DIM * DIM) * kWide;
@@ -439,7 +435,7 @@ struct WideView {
 // still hold a closer leaf go on the warp's stack in shared memory with the
 // nearest on top (depth-first, nearest child first, the others in Morton
 // order, all pruned by the running bound when popped).  n_nodes counts node
-// visits, n_leaf_nodes those that also read leaf children's vertices.
+// visits (a leaf child's vertices come with its node).
 // best2 / best hold each lane's bound on entry (kInf / -1 without one) and
 // the result on exit.  Called by all 32 lanes with the same `need` and each
 // lane's own view (lanes may belong to different problems).  Returns error
@@ -447,7 +443,7 @@ struct WideView {
 // would overflow (excluded by the build's depth check).
 template <int DIM>
 __device__ __forceinline__ int wide_closest(const WideView& mine, unsigned need, const float* q_lane, float& best2,
-                                            int& best, float2* stk, unsigned& n_nodes, unsigned& n_leaf_nodes) {
+                                            int& best, float2* stk, unsigned& n_nodes, unsigned& n_prims) {
     const int lane = threadIdx.x & 31;
     int err = 0;
     while (need) {
@@ -466,7 +462,7 @@ __device__ __forceinline__ int wide_closest(const WideView& mine, unsigned need,
         const int n_tree = __shfl_sync(kWarpAll, mine.n_tree, src);
         if (n_wide > 0) {
             __syncwarp();
-            if (lane == 0) stk[0] = make_float2(0.0f, __int_as_float(kHasLeaves));   // the root, read in full
+            if (lane == 0) stk[0] = make_float2(0.0f, __int_as_float(0));
             __syncwarp();
             int top = 1;
             int budget = n_wide;
@@ -475,8 +471,7 @@ __device__ __forceinline__ int wide_closest(const WideView& mine, unsigned need,
                 --top;
                 if (!(e.x < b2)) continue;                     // pruned by a closer leaf found since
                 if (--budget < 0) { err |= 1; break; }
-                const int tag = __float_as_int(e.y);
-                const float* f = wn + (size_t)(tag & kNodeMask) * WideLayout<DIM>::kFloats;
+                const float* f = wn + (size_t)__float_as_int(e.y) * WideLayout<DIM>::kFloats;
                 float lo[DIM], hi[DIM], vt[DIM * DIM];
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) {
@@ -484,14 +479,8 @@ __device__ __forceinline__ int wide_closest(const WideView& mine, unsigned need,
                     hi[k] = __ldg(f + (DIM + k) * kWide + lane);
                 }
                 const int code = __float_as_int(__ldg(f + 2 * DIM * kWide + lane));
-                if (tag & kHasLeaves) {
-                    if (lane == 0) ++n_leaf_nodes;
 #pragma unroll
-                    for (int k = 0; k < DIM * DIM; ++k) vt[k] = __ldg(f + WideLayout<DIM>::kVtx + k * kWide + lane);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < DIM * DIM; ++k) vt[k] = 0.0f;
-                }
+                for (int k = 0; k < DIM * DIM; ++k) vt[k] = __ldg(f + WideLayout<DIM>::kVtx + k * kWide + lane);
                 const float cd = box_dist2<DIM>(q, lo, hi);
                 if (lane == 0) ++n_nodes;
                 const bool leaf = code < 0 && cd < b2;
@@ -545,6 +534,7 @@ __device__ __forceinline__ int wide_closest(const WideView& mine, unsigned need,
             }
         } else if (n_tree == 1) {
             const float dd = prim_dist2<DIM>(prims, 0, q);
+            if (lane == 0) ++n_prims;
             if (dd < b2) { b2 = dd; bi = 0; }
         }
         if (lane == src) { best2 = b2; best = bi; }

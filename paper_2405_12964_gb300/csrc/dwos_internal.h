@@ -74,7 +74,6 @@ struct DevCounters {
     unsigned long long capped;
     unsigned long long nodes;   // BVH node fetches
     unsigned long long prims;   // element distance tests
-    unsigned long long leaf_nodes;   // 32-wide node visits that also read leaf vertices
     int error;                  // bit 0: traversal bound exceeded, bit 1: query outside Omega
     int pad[3];
 };

@@ -65,7 +65,7 @@ __device__ __forceinline__ void leaf_geometry(const float4* __restrict__ prims, 
 
 struct WarpStats {             // per lane; summed over the warp in 64 bits at the end
     unsigned steps_main = 0, steps_nested = 0, capped = 0;
-    unsigned nodes = 0, prims = 0, leaf_nodes = 0;
+    unsigned nodes = 0, prims = 0;
 };
 
 // What a walk keeps from the end of its main walk until its last nested walk
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
                 big_closest<DIM>(Pw.prims, Pw.n_tree, Pw.n_big, x, best2, best, st.prims);
             }
             const WideView wv{Pw.wnodes, Pw.prims, Pw.n_wide, Pw.n_tree};
-            error |= wide_closest<DIM>(wv, __ballot_sync(kFull, active), x, best2, best, stk, st.nodes, st.leaf_nodes) & 1;
+            error |= wide_closest<DIM>(wv, __ballot_sync(kFull, active), x, best2, best, stk, st.nodes, st.prims) & 1;
         }
         if (!active) continue;
 
@@ -412,18 +412,16 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
         sc += __shfl_xor_sync(kFull, sc, o);
         error |= __shfl_xor_sync(kFull, error, o);
     }
-    unsigned long long nodes = st.nodes, prims = st.prims, leaf_nodes = st.leaf_nodes;
+    unsigned long long nodes = st.nodes, prims = st.prims;
     for (int o = 16; o > 0; o >>= 1) {
         nodes += __shfl_xor_sync(kFull, nodes, o);
         prims += __shfl_xor_sync(kFull, prims, o);
-        leaf_nodes += __shfl_xor_sync(kFull, leaf_nodes, o);
     }
     if (lane == 0) {
         atomicAdd(&ctr->steps_main, sm);
         atomicAdd(&ctr->steps_nested, sn);
         atomicAdd(&ctr->nodes, nodes);
         atomicAdd(&ctr->prims, prims);
-        if (leaf_nodes) atomicAdd(&ctr->leaf_nodes, leaf_nodes);
         if (sc) atomicAdd(&ctr->capped, sc);
         if (error) atomicOr(&ctr->error, error);
     }
