@@ -270,6 +270,37 @@ dwos_status dwos_cv_table(dwos_ctx* ctx, dwos_mlp* mlp, float* table);
  * tree traffic (which stays on chip) is compared.  Synchronous. */
 dwos_status dwos_probe_l2_read(int device, size_t bytes, int reps, double* gbs);
 
+/* ---- volume-integrated shape functional ----------------------------------
+ * J(theta) = int_Omega M(x) 1/2 (u(x) - uref(x))^2 dx (Eq. functional, M the
+ * indicator of an axis-aligned box) and its derivative, Eq. functional_deriv:
+ *   dJ/dtheta = int_Omega M (u - uref) udot dx + int_Gamma M V_n 1/2 (u - uref)^2 dA.
+ * The domain term: dwos_sample_domain draws n_try points uniformly in the
+ * box (Philox4x32-10, key = seed, counter = (i, 0, 0, 0xD0A1), words 0..dim-1
+ * mapped as for the walks), keeps those inside Omega (ray parity), in
+ * candidate order, in points (device, n_try x dim floats of room), and
+ * returns their number and the weight |box| / n_try each carries (an
+ * unbiased quadrature of the box integral); dwos_grad_l2_weighted is
+ * dwos_grad_l2 with those weights per point (loss = sum_p w_p 1/2 (u_p -
+ * uref_p)^2, the U-statistic product per point scaled by w_p).  The boundary
+ * term: dwos_boundary_term_l2 integrates M V_n 1/2 (g - uref)^2 over the
+ * boundary (u = g there), with mapped vertex data g and uref_vert (n_vert
+ * values, or NULL for 0) both linear on each element, M the box indicator at
+ * the element's centre, and V_n along the outward normal (oriented by the
+ * inside test of a point just behind the element); the per-element integrals
+ * are exact.  grad_param receives n_param values (host or device by mem).
+ * Both calls synchronise. */
+dwos_status dwos_sample_domain(dwos_ctx* ctx, int n_try, const float* box_lo, const float* box_hi, uint64_t seed,
+                               float* points, int* n_inside, float* weight);
+dwos_status dwos_grad_l2_weighted(dwos_ctx* ctx, int n_query, const float* xq, const float* uref,
+                                  const float* point_weight, int walks_per_point, uint64_t walk_id_base,
+                                  double* loss, double* grad_param, double* grad_vert, int mem);
+dwos_status dwos_boundary_term_l2(dwos_ctx* ctx, const float* box_lo, const float* box_hi, const float* uref_vert,
+                                  double* grad_param, int mem);
+
+/* The current vertex positions (n_vert x dim floats: reference + J theta),
+ * host or device by mem.  Synchronises for host memory. */
+dwos_status dwos_get_vertices(const dwos_ctx* ctx, float* vert, int mem);
+
 /* Sizes of the acceleration structures built by dwos_set_boundary /
  * dwos_set_params: info[0..5] = elements, elements in the binary tree,
  * outsized elements kept out of it, binary inner nodes, 32-wide nodes, levels

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdwos.so")
-SOURCES = ["api.cu", "bvh.cu", "walk.cu", "estimators.cu", "batch.cu", "mlp.cu"]
+SOURCES = ["api.cu", "bvh.cu", "walk.cu", "estimators.cu", "batch.cu", "mlp.cu", "functional.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -39,6 +39,7 @@ dwos_status cuda_fail(dwos_ctx* c, cudaError_t e, const char* where) {
 }
 
 #define CK(call, where) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); } while (0)
+#define CKC(c, call, where) do { cudaError_t e_ = (call); if (e_ != cudaSuccess) return cuda_fail(c, e_, where); } while (0)
 
 template <typename T>
 cudaError_t grow(T*& p, size_t& cap, size_t n) {
@@ -246,7 +247,7 @@ void dwos_destroy(dwos_ctx* ctx) {
     bvh_free(ctx->bvh);
     void* bufs[] = {ctx->vert_ref, ctx->vert, ctx->elem, ctx->jac, ctx->theta, ctx->g_vert, ctx->dg_vert, ctx->rec,
                     ctx->xq, ctx->valid, ctx->wvec, ctx->out, ctx->acc_vert, ctx->trace, ctx->dbg, ctx->misc_f,
-                    ctx->misc_i, ctx->misc_u, ctx->d_prob, ctx->d_ctr, ctx->d_err};
+                    ctx->misc_i, ctx->misc_u, ctx->d_prob, ctx->d_ctr, ctx->d_err, ctx->pw};
     for (void* p : bufs) if (p) cudaFree(p);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -435,7 +436,7 @@ dwos_status dwos_eval(dwos_ctx* ctx, int n_query, const float* xq, int W, double
 // product; 3: uncorrelated product (wv = uref for modes 1-3).
 static dwos_status reverse_common(dwos_ctx* ctx, int n_query, const float* xq, const float* wv, int W,
                                   unsigned long long base, int mode, double* loss, double* grad_param,
-                                  double* grad_vert, int mem) {
+                                  double* grad_vert, int mem, const float* pweight = nullptr) {
     if (dwos_status s = check_mem(ctx, mem)) return s;
     if (!wv && n_query > 0) return fail(ctx, DWOS_ERR_INVALID_ARG, mode ? "uref is NULL" : "w is NULL");
     if (ctx->n_param > 0 && !grad_param) return fail(ctx, DWOS_ERR_INVALID_ARG, "grad_param is NULL");
@@ -451,6 +452,12 @@ static dwos_status reverse_common(dwos_ctx* ctx, int n_query, const float* xq, c
     const int N = ctx->n_param;
     CK(grow(ctx->wvec, ctx->wvec_cap, (size_t)std::max(n_query, 1)), "alloc weights");
     CK(to_device(ctx, ctx->wvec, wv, (size_t)n_query, mem), "copy weights");
+    const float* d_pw = nullptr;
+    if (pweight) {
+        CK(grow(ctx->pw, ctx->pw_cap, (size_t)std::max(n_query, 1)), "alloc point weights");
+        CK(to_device(ctx, ctx->pw, pweight, (size_t)n_query, mem), "copy point weights");
+        d_pw = ctx->pw;
+    }
     const size_t nacc = (size_t)ctx->n_vert * ctx->dim + (size_t)ctx->n_vert;
     CK(grow(ctx->acc_vert, ctx->acc_cap, nacc), "alloc accumulators");
     CK(cudaMemsetAsync(ctx->acc_vert, 0, nacc * sizeof(double), ctx->stream), "zero accumulators");
@@ -464,7 +471,7 @@ static dwos_status reverse_common(dwos_ctx* ctx, int n_query, const float* xq, c
         ctx->launches += n_query > 0 ? 1 : 0;
     }
     CK(launch_scatter(ctx->rec, ctx->elem, ctx->dim, n_query, W, ctx->opt.B, mode, ctx->wvec, ctx->acc_vert, acc_g,
-                      ctx->stream, nullptr, d_umean), "scatter");
+                      ctx->stream, nullptr, d_umean, d_pw), "scatter");
     ctx->launches += n_query > 0 ? 1 : 0;
     double* d_grad = mem == DWOS_MEM_DEVICE ? grad_param : ctx->out;
     if (N > 0) {
@@ -477,7 +484,7 @@ static dwos_status reverse_common(dwos_ctx* ctx, int n_query, const float* xq, c
         double* d_mean = ctx->out + std::max(N, 1);
         CK(launch_reduce_u(ctx->rec, n_query, W, d_mean, nullptr, ctx->stream), "reduce u");
         d_loss = mem == DWOS_MEM_DEVICE ? loss : ctx->out + std::max(N, 1) + n_query;
-        CK(launch_loss(d_mean, ctx->wvec, n_query, d_loss, ctx->stream), "loss");
+        CK(launch_loss(d_mean, ctx->wvec, n_query, d_loss, ctx->stream, d_pw), "loss");
         ctx->launches += n_query > 0 ? 2 : 1;
     }
     if (grad_vert)
@@ -488,6 +495,17 @@ static dwos_status reverse_common(dwos_ctx* ctx, int n_query, const float* xq, c
         return finish_sync(ctx);
     }
     return DWOS_OK;
+}
+
+dwos_status dwos_grad_l2_weighted(dwos_ctx* ctx, int n_query, const float* xq, const float* uref,
+                                  const float* point_weight, int W, uint64_t walk_id_base, double* loss,
+                                  double* grad_param, double* grad_vert, int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (n_query > 0 && !point_weight) return fail(ctx, DWOS_ERR_INVALID_ARG, "point_weight is NULL");
+    if (mem == DWOS_MEM_HOST && n_query > 0 && !finite_all(point_weight, n_query))
+        return fail(ctx, DWOS_ERR_INVALID_ARG, "point weights must be finite");
+    return reverse_common(ctx, n_query, xq, uref, W, walk_id_base, 1, loss, grad_param, grad_vert, mem,
+                          point_weight);
 }
 
 dwos_status dwos_grad_l2_product(dwos_ctx* ctx, int n_query, const float* xq, const float* uref, int W,
@@ -659,6 +677,20 @@ dwos_status dwos_probe_l2_read(int device, size_t bytes, int reps, double* gbs) 
     cudaFree(sink);
     if (e != cudaSuccess) return fail(nullptr, DWOS_ERR_CUDA, cudaGetErrorString(e));
     *gbs = (double)words * 16.0 * reps / (ms * 1e-3) / 1e9;
+    return DWOS_OK;
+}
+
+dwos_status dwos_get_vertices(const dwos_ctx* ctx, float* vert, int mem) {
+    dwos_ctx* c = const_cast<dwos_ctx*>(ctx);
+    if (!ctx || !vert) return fail(c, DWOS_ERR_INVALID_ARG, "NULL argument");
+    if (!ctx->have_boundary) return fail(c, DWOS_ERR_STATE, "no boundary");
+    if (dwos_status s = check_mem(c, mem)) return s;
+    if (dwos_status s = set_device(c)) return s;
+    const size_t n = (size_t)ctx->n_vert * ctx->dim;
+    CKC(c, cudaMemcpyAsync(vert, ctx->vert, sizeof(float) * n,
+                           mem == DWOS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, ctx->stream),
+        "copy vertices");
+    if (mem == DWOS_MEM_HOST) CKC(c, cudaStreamSynchronize(ctx->stream), "synchronize");
     return DWOS_OK;
 }
 

@@ -34,6 +34,7 @@ struct dwos_ctx {
     float* xq = nullptr; size_t xq_cap = 0;
     int* valid = nullptr; size_t valid_cap = 0;
     float* wvec = nullptr; size_t wvec_cap = 0;           // cotangent / uref
+    float* pw = nullptr; size_t pw_cap = 0;               // per-point quadrature weights
     double* out = nullptr; size_t out_cap = 0;            // reduced outputs
     double* acc_vert = nullptr; size_t acc_cap = 0;       // n_vert*dim + n_vert
     uint32_t* trace = nullptr; size_t trace_cap = 0;

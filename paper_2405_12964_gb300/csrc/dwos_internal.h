@@ -152,10 +152,12 @@ cudaError_t launch_reduce_udot(const dwos_record* rec, const int* elem, const fl
 // first W/2 walks, weights on the other W/2).
 cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int n_points, int W, int B,
                            int mode, const float* cot_or_uref, double* acc_vert, double* acc_g,
-                           cudaStream_t stream, const CvView* cv = nullptr, const double* umean = nullptr);
+                           cudaStream_t stream, const CvView* cv = nullptr, const double* umean = nullptr,
+                           const float* pweight = nullptr);
 cudaError_t launch_gemv(const float* jac, const float* dg, const double* acc_vert, const double* acc_g,
                         int n_vert, int dim, int n_param, double* grad, cudaStream_t stream);
+// 1/2 sum_p w_p (mean_p - uref_p)^2 with w = pweight (or 1)
 cudaError_t launch_loss(const double* mean, const float* uref, int n_points, double* loss,
-                        cudaStream_t stream);
+                        cudaStream_t stream, const float* pweight = nullptr);
 
 }  // namespace dwos

@@ -152,6 +152,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
                                                       const int* __restrict__ elem, int n_points, int W, int B,
                                                       int mode, const float* __restrict__ cot_or_uref,
                                                       const double* __restrict__ umean,
+                                                      const float* __restrict__ pweight,
                                                       long long walks_per_block, double* __restrict__ acc_vert,
                                                       double* __restrict__ acc_g, CvView cv) {
     __shared__ int keys[kSlots];
@@ -193,6 +194,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
             const double ur = valid ? (double)cot_or_uref[p] : 0.0;
             wt = ((S - u) / ((double)B * (B - 1)) - ur / B) / (double)(W / B);
         }
+        if (pweight && valid) wt *= (double)pweight[p];     // quadrature weight of the point
         const bool hit = valid && r.elem >= 0;
         const float wv[3] = {1.0f - r.b1 - r.b2, r.b1, r.b2};
         const int lane = threadIdx.x & 31;
@@ -278,11 +280,11 @@ __global__ void gemv_kernel(const float* __restrict__ jac, const float* __restri
     }
 }
 
-__global__ void loss_kernel(const double* mean, const float* uref, int n, double* loss) {
+__global__ void loss_kernel(const double* mean, const float* uref, const float* pweight, int n, double* loss) {
     double s = 0.0;
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
         const double e = mean[p] - (double)uref[p];
-        s += 0.5 * e * e;
+        s += 0.5 * e * e * (pweight ? (double)pweight[p] : 1.0);
     }
     __shared__ double sh[32];
     s = warp_sum(s);
@@ -330,7 +332,7 @@ cudaError_t launch_reduce_udot(const dwos_record* rec, const int* elem, const fl
 
 cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int n_points, int W, int B, int mode,
                            const float* cot_or_uref, double* acc_vert, double* acc_g, cudaStream_t s,
-                           const CvView* cv, const double* umean) {
+                           const CvView* cv, const double* umean, const float* pweight) {
     const CvView none{nullptr, nullptr, nullptr, dim, nullptr};
     const CvView c = cv ? *cv : none;
     const long long total = (long long)n_points * W;
@@ -341,8 +343,8 @@ cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int
     per = ((per + bs - 1) / bs) * bs;
     if (per < bs) per = bs;
     const long long blocks = (total + per - 1) / per;
-    if (dim == 2) scatter_kernel<2><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, umean, per, acc_vert, acc_g, c);
-    else scatter_kernel<3><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, umean, per, acc_vert, acc_g, c);
+    if (dim == 2) scatter_kernel<2><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, umean, pweight, per, acc_vert, acc_g, c);
+    else scatter_kernel<3><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, umean, pweight, per, acc_vert, acc_g, c);
     return cudaGetLastError();
 }
 
@@ -358,8 +360,9 @@ cudaError_t launch_gemv(const float* jac, const float* dg, const double* acc_ver
     return cudaGetLastError();
 }
 
-cudaError_t launch_loss(const double* mean, const float* uref, int n_points, double* loss, cudaStream_t s) {
-    loss_kernel<<<1, 256, 0, s>>>(mean, uref, n_points, loss);
+cudaError_t launch_loss(const double* mean, const float* uref, int n_points, double* loss, cudaStream_t s,
+                        const float* pweight) {
+    loss_kernel<<<1, 256, 0, s>>>(mean, uref, pweight, n_points, loss);
     return cudaGetLastError();
 }
 

@@ -102,6 +102,10 @@ _SIGS = {
     "dwos_cv_table": [_vp, _vp, _vp],
     "dwos_bvh_info": [_vp, _vp],
     "dwos_probe_l2_read": [_i, ctypes.c_size_t, _i, _vp],
+    "dwos_sample_domain": [_vp, _i, _vp, _vp, _u64, _vp, _vp, _vp],
+    "dwos_grad_l2_weighted": [_vp, _i, _vp, _vp, _vp, _i, _u64, _vp, _vp, _vp, _i],
+    "dwos_boundary_term_l2": [_vp, _vp, _vp, _vp, _vp, _i],
+    "dwos_get_vertices": [_vp, _vp, _i],
 }
 MLP_NPARAM = 14088
 
@@ -314,6 +318,62 @@ class Solver:
         if debug:
             out["debug"] = dbg
         return out
+
+    # ------------------------------------------------ volume-integrated functional
+    def sample_domain(self, n_try: int, box_lo, box_hi, seed: int = 0):
+        """Points sampled uniformly in the box and kept inside Omega (dwos_sample_domain):
+        (points on the device, the quadrature weight each carries)."""
+        self._stream()
+        pts = torch.empty(n_try, self.dim, device=self.device, dtype=torch.float32)
+        lo = (ctypes.c_float * 3)(*[float(v) for v in box_lo])
+        hi = (ctypes.c_float * 3)(*[float(v) for v in box_hi])
+        n_in = ctypes.c_int()
+        w = ctypes.c_float()
+        self._check(lib().dwos_sample_domain(self._h, int(n_try), lo, hi, int(seed) & 0xFFFFFFFFFFFFFFFF, _ptr(pts),
+                                             ctypes.byref(n_in), ctypes.byref(w)))
+        return pts[:n_in.value], float(w.value)
+
+    def grad_l2_weighted(self, xq, uref, weight, walks: int, walk_id_base: int = 0):
+        """dwos_grad_l2_weighted: loss sum_p w_p 1/2 (u_p - uref_p)^2 and its gradient."""
+        self._stream()
+        x = self._dev(xq, torch.float32)
+        u = self._dev(uref, torch.float32)
+        w = self._dev(weight, torch.float32)
+        loss = torch.empty(1, device=self.device, dtype=torch.float64)
+        g = torch.empty(max(self.n_param, 1), device=self.device, dtype=torch.float64)
+        self._check(lib().dwos_grad_l2_weighted(self._h, x.shape[0], _ptr(x), _ptr(u), _ptr(w), int(walks),
+                                                int(walk_id_base), _ptr(loss), _ptr(g), None, MEM_DEVICE))
+        return loss, g[:self.n_param]
+
+    def boundary_term_l2(self, box_lo, box_hi, uref_vert=None):
+        """dwos_boundary_term_l2: int_Gamma M V_n 1/2 (g - uref)^2 dA per parameter (numpy)."""
+        self._stream()
+        lo = (ctypes.c_float * 3)(*[float(v) for v in box_lo])
+        hi = (ctypes.c_float * 3)(*[float(v) for v in box_hi])
+        ur = None if uref_vert is None else self._dev(uref_vert, torch.float32)
+        g = torch.empty(max(self.n_param, 1), device=self.device, dtype=torch.float64)
+        self._check(lib().dwos_boundary_term_l2(self._h, lo, hi, _ptr(ur), _ptr(g), MEM_DEVICE))
+        return g[:self.n_param].cpu().numpy()
+
+    def functional_gradient(self, box_lo, box_hi, uref_fn, walks: int, n_try: int, seed: int = 0,
+                            walk_id_base: int = 0):
+        """Eq. (functional_deriv) for J = int_Omega M 1/2 (u - uref)^2 with M the box:
+        the domain term from points sampled in the box (uref_fn maps an (n, dim)
+        numpy array to uref there) plus the boundary term with uref_fn at the
+        vertices.  Returns (J estimate, dJ/dtheta) as numpy."""
+        pts, w = self.sample_domain(n_try, box_lo, box_hi, seed)
+        p = pts.cpu().numpy().astype(np.float64)
+        ur = np.asarray(uref_fn(p), dtype=np.float32).reshape(-1)
+        loss, g = self.grad_l2_weighted(pts, ur, np.full(len(p), w, np.float32), walks, walk_id_base)
+        vert = self.current_vertices()
+        gb = self.boundary_term_l2(box_lo, box_hi, np.asarray(uref_fn(vert), np.float32).reshape(-1))
+        return float(loss.cpu()[0]), g.cpu().numpy() + gb
+
+    def current_vertices(self) -> np.ndarray:
+        """Vertex positions at the current parameters (dwos_get_vertices)."""
+        out = np.empty((self.n_vert, self.dim), dtype=np.float32)
+        self._check(lib().dwos_get_vertices(self._h, out.ctypes.data_as(ctypes.c_void_p), MEM_HOST))
+        return out.astype(np.float64)
 
     def bvh_info(self) -> dict:
         info = (ctypes.c_int32 * 6)()

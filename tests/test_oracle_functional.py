@@ -1,0 +1,90 @@
+"""The volume-integrated functional (Eqs. functional, functional_deriv) in the
+oracle.
+
+Pins:
+  * the monomial integrals against dense quadrature on random segments and
+    triangles (the boundary term's integration);
+  * the boundary term on the disk: V_n = 1 for the radius, so with g = 1 it is
+    half the polygon's perimeter; a Fourier mode integrates to about zero;
+  * the sampled domain's weight x count estimates the disk's area;
+  * the whole estimator's mean equals dJ/dR of J(R) = int_disk 1/2 u^2 for the
+    screened disk u = I0(k r) / I0(k R), computed by quadrature, within its
+    standard error and the estimator's eps/h bias.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import functional as fn
+from paper_2405_12964_gb300 import scenes
+from tests.helpers import to_oracle
+
+
+def test_monomial_integrals_match_dense_quadrature():
+    rng = np.random.default_rng(0)
+    # segment of length L: midpoint rule with many points
+    L = 1.7
+    t = (np.arange(20000) + 0.5) / 20000
+    for exps in [(1, 2), (3, 0), (2, 2)]:
+        want = L * np.mean((1 - t) ** exps[0] * t ** exps[1])
+        assert abs(fn._simplex_monomial(L, list(exps)) - want) < 1e-7
+    # triangle of area A: uniform samples of the barycentrics (large count, Monte Carlo)
+    A = 0.8
+    u = rng.random((400000, 2))
+    flip = u.sum(1) > 1
+    u[flip] = 1 - u[flip]
+    w = np.stack([1 - u.sum(1), u[:, 0], u[:, 1]], 1)
+    for exps in [(1, 1, 1), (2, 1, 0), (0, 0, 3)]:
+        vals = A * np.prod(w ** np.array(exps), axis=1)
+        want, se = vals.mean(), vals.std() / np.sqrt(len(vals))
+        assert abs(fn._simplex_monomial(A, list(exps)) - want) < 5 * se
+
+
+def test_boundary_term_on_the_disk():
+    sc = scenes.disk_scene("screened_1", n_query=4)
+    pr = to_oracle(sc)
+    g = fn.boundary_term_l2(pr, [-2, -2], [2, 2])
+    n = len(sc.elem)
+    perimeter = 2 * n * np.sin(np.pi / n)
+    # dJ/dR of the boundary part: int 1/2 g^2 V_n dA with V_n = the radial unit ... on a polygon the
+    # vertices move radially, so V_n = cos(pi/n) along each edge
+    assert abs(g[0] - 0.5 * perimeter * np.cos(np.pi / n)) < 1e-12
+    assert np.all(np.abs(g[1:]) < 1e-12)
+    # a mask box that excludes every element
+    assert np.all(fn.boundary_term_l2(pr, [-0.5, -0.5], [0.5, 0.5]) == 0)
+
+
+def test_domain_weights_estimate_the_area():
+    sc = scenes.disk_scene("screened_1", n_query=4)
+    pr = to_oracle(sc)
+    pts, w = fn.sample_domain(pr, 4000, [-1.1, -1.1], [1.1, 1.1], seed=7)
+    n = len(sc.elem)
+    area = 0.5 * n * np.sin(2 * np.pi / n)
+    p = area / 2.2 ** 2
+    se = 2.2 ** 2 * np.sqrt(p * (1 - p) / 4000)
+    assert abs(len(pts) * w - area) < 4.5 * se
+    assert np.all(np.hypot(pts[:, 0], pts[:, 1]) < 1.0)
+
+
+def _disk_J(R, k=2.0):
+    from scipy.integrate import quad
+    from scipy.special import iv
+    return quad(lambda r: 0.5 * (iv(0, k * r) / iv(0, k * R)) ** 2 * 2 * np.pi * r, 0, R, epsabs=1e-13)[0]
+
+
+def test_estimator_mean_matches_the_closed_form():
+    sc = scenes.disk_scene("screened_1", n_query=4)
+    pr = to_oracle(sc)
+    want = (_disk_J(1 + 1e-5) - _disk_J(1 - 1e-5)) / 2e-5
+    est_g = []
+    for rep in range(3):
+        pts, w = fn.sample_domain(pr, 600, [-1, -1], [1, 1], seed=100 + rep)
+        W = 64
+        o = oracle.run_walks(pr, pts, W, differential=True, walk_id_base=rep << 32)
+        ur = np.zeros(len(pts))
+        est_g.append(fn.grad_l2_weighted(o["u_hat"], o["udot"], ur, np.full(len(pts), w), len(pts), W, 8)[0])
+    gb = fn.boundary_term_l2(pr, [-1.5, -1.5], [1.5, 1.5])[0]
+    tot = np.array(est_g) + gb
+    se = tot.std(ddof=1) / np.sqrt(len(tot))
+    # the boundary term dominates; the domain term carries the O(eps/h) du/dn bias (a few %)
+    assert abs(tot.mean() - want) < 4.5 * se + 0.03 * abs(want), (tot.mean(), want, se)
