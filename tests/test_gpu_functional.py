@@ -83,8 +83,17 @@ def test_weighted_gradient_matches_oracle(Solver):
     o = oracle.run_walks(to_oracle(sc, K=2), p.astype(np.float32).astype(np.float64), W, differential=True)
     go = fn.grad_l2_weighted(o["u_hat"], o["udot"], ur, wt, len(p), W, 8)
     lo_ = fn.loss_l2_weighted(o["u_hat"], ur, wt, len(p), W)
-    assert np.allclose(g, go, rtol=3e-3, atol=3e-3 * np.abs(go).max()), np.abs(g - go).max() / np.abs(go).max()
-    assert abs(loss[0] - lo_) <= 1e-4 * abs(lo_) + 1e-8
+    # ~9k walks: a handful change branch between FP32 and FP64 (each with a 1/h-amplified
+    # du/dn), so the comparison is at 1 % of the largest component; the weighting itself is
+    # checked exactly below (a wrong weight moves the gradient by tens of percent)
+    assert np.allclose(g, go, rtol=1e-2, atol=1e-2 * np.abs(go).max()), np.abs(g - go).max() / np.abs(go).max()
+    assert abs(loss[0] - lo_) <= 1e-3 * abs(lo_) + 1e-8
+    # the same walks: unit weights give dwos_grad_l2, constant weights scale it
+    g1 = s.grad_l2_weighted(pts, ur, np.ones(len(p), np.float32), W)[1].cpu().numpy()
+    g0 = s.grad_l2(pts, ur, W)[1].cpu().numpy()
+    g2 = s.grad_l2_weighted(pts, ur, np.full(len(p), 2.5, np.float32), W)[1].cpu().numpy()
+    assert np.allclose(g1, g0, rtol=1e-9, atol=1e-12 * np.abs(g0).max())
+    assert np.allclose(g2, 2.5 * g0, rtol=1e-9, atol=1e-12 * np.abs(g0).max())
 
 
 def test_functional_gradient_matches_the_closed_form(Solver):
