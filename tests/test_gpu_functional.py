@@ -112,4 +112,6 @@ def test_functional_gradient_matches_the_closed_form(Solver):
     vals = np.array(vals)
     se = vals.std(ddof=1) / np.sqrt(len(vals))
     print("dJ/dR: estimate %.4f +- %.4f, closed form %.4f" % (vals.mean(), se, want))
-    assert abs(vals.mean() - want) < 4.5 * se + 0.03 * abs(want)
+    # boundary part pi (exact); the domain part carries the eps/h bias of the du/dn estimate
+    # (Sec. 5.3; 4.4 % low at eps/h = 0.1 in the oracle): budget 6 % of it
+    assert abs(vals.mean() - want) < 4.5 * se + 0.06 * abs(want - np.pi)

@@ -227,6 +227,23 @@ def test_warp_wide_search_is_the_one_that_ran(Solver):
     assert nodes[1] < 0.5 * nodes[0]
 
 
+def test_replay_from_points_at_and_near_the_shell(Solver):
+    # query points at 0.5, 2 and 5 eps from the boundary (inside): the first query may end the
+    # walk at once; u and udot must still match the oracle walk for walk
+    sc = scenes.disk_scene("screened_1", n_query=4)
+    n = len(sc.elem)
+    apothem = np.cos(np.pi / n)
+    t = (np.arange(48) + 0.37) * (2 * np.pi / 48)        # off the polygon's vertex rays (exact ties)
+    q = []
+    for dd in (0.5, 2.0, 5.0):
+        r = apothem - dd * sc.eps
+        q.append(np.stack([r * np.cos(t), r * np.sin(t)], 1))
+    sc.query = np.concatenate(q)
+    s, g, o = run_pair(Solver, sc, 32)
+    same = check_walks(sc, g, o, max_flip=0.02)
+    print("near-shell replay: %.4f of walks on the same branch" % same.mean())
+
+
 def test_forward_only_walks_match(Solver):
     sc = scenes.ball_scene(freq=8, n_query=10, sigma=2.0, f=0.7)
     s, g, o = run_pair(Solver, sc, 64, differential=False)

@@ -9,7 +9,9 @@ Pins:
   * the sampled domain's weight x count estimates the disk's area;
   * the whole estimator's mean equals dJ/dR of J(R) = int_disk 1/2 u^2 for the
     screened disk u = I0(k r) / I0(k R), computed by quadrature, within its
-    standard error and the estimator's eps/h bias.
+    standard error and the estimator's eps/h bias (Sec. 5.3): the domain term
+    comes out 4.4 % low at eps/h = 0.1 (2.8 % with eps and h four times
+    smaller, 14 % at eps/h = 0.4), so the budget is 6 % of the domain term.
 """
 import numpy as np
 import pytest
@@ -77,14 +79,15 @@ def test_estimator_mean_matches_the_closed_form():
     pr = to_oracle(sc)
     want = (_disk_J(1 + 1e-5) - _disk_J(1 - 1e-5)) / 2e-5
     est_g = []
-    for rep in range(3):
-        pts, w = fn.sample_domain(pr, 600, [-1, -1], [1, 1], seed=100 + rep)
+    for rep in range(8):
+        pts, w = fn.sample_domain(pr, 1500, [-1, -1], [1, 1], seed=100 + rep)
         W = 64
         o = oracle.run_walks(pr, pts, W, differential=True, walk_id_base=rep << 32)
         ur = np.zeros(len(pts))
         est_g.append(fn.grad_l2_weighted(o["u_hat"], o["udot"], ur, np.full(len(pts), w), len(pts), W, 8)[0])
     gb = fn.boundary_term_l2(pr, [-1.5, -1.5], [1.5, 1.5])[0]
+    # the boundary term is exact here: pi (g = 1, V_n = 1 on the unit circle, to the polygon's sagitta)
+    assert abs(gb - np.pi) < 2e-3
     tot = np.array(est_g) + gb
     se = tot.std(ddof=1) / np.sqrt(len(tot))
-    # the boundary term dominates; the domain term carries the O(eps/h) du/dn bias (a few %)
-    assert abs(tot.mean() - want) < 4.5 * se + 0.03 * abs(want), (tot.mean(), want, se)
+    assert abs(tot.mean() - want) < 4.5 * se + 0.06 * abs(want - gb), (tot.mean(), want, se)
