@@ -431,10 +431,10 @@ dwos_status dwos_mlp_sync(dwos_mlp* mlp);
 
 /* ---- allocation-free evaluation ------------------------------------------
  * The paper has no counterpart to this entry point.  It is dwos_eval for
- * callers that cannot allocate device memory during the call: code under a
- * stream capture in global mode, where cudaMalloc is not permitted; hosts
- * whose device memory belongs to another allocator or a fixed budget; loops
- * that cannot afford cudaMalloc's implicit device synchronisation.
+ * callers that cannot allocate device memory during the call: hosts whose
+ * device memory belongs to another allocator (a framework's caching pool) or
+ * to a fixed budget set aside at start-up, and loops that cannot afford the
+ * implicit device synchronisation that cudaMalloc and cudaFree bring.
  *
  * It runs the same kernels as dwos_eval (inside test if enabled, walks with
  * walk id p * W + w, per-point reductions) but keeps all scratch in one fixed

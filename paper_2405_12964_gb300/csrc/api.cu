@@ -869,11 +869,10 @@ dwos_status dwos_philox4x32_10(dwos_ctx* ctx, int n, const uint32_t* ctr, const 
 // ---------------------------------------------------------------------------
 // Allocation-free evaluation.
 //
-// Some callers cannot allocate device memory while they call us: code running
-// under a stream capture in global mode (where cudaMalloc is not permitted),
-// hosts whose memory is owned by another allocator (a framework's caching
-// pool, a fixed device budget), or latency-sensitive loops where the implicit
-// device synchronisation of cudaMalloc is unacceptable.  dwos_eval_static
+// Some callers cannot allocate device memory while they call us: hosts whose
+// memory is owned by another allocator (a framework's caching pool, a fixed
+// device budget set aside at start-up), or latency-sensitive loops where the
+// implicit device synchronisation of cudaMalloc / cudaFree is unacceptable.  dwos_eval_static
 // serves them: it runs the same walk, inside-test and reduction kernels as
 // dwos_eval, but every byte of scratch (problem descriptor, counters, inside
 // flags, per-walk records) lives in the fixed array below, so the call itself

@@ -1,8 +1,9 @@
 """dwos_eval_static: the allocation-free variant of dwos_eval.
 
-Callers under a global-mode stream capture, or whose device memory belongs to
-another allocator, cannot let a library call cudaMalloc; this entry point keeps
-its scratch in a fixed array inside the library.  It must return what
+Callers whose device memory belongs to another allocator or a fixed budget,
+or whose loops cannot absorb cudaMalloc's implicit synchronisation, cannot let
+a library allocate; this entry point keeps its scratch in a fixed array inside
+the library.  It must return what
 dwos_eval returns for the same walks, call after call (the array is reused and
 keeps the previous call's contents), and refuse requests larger than its
 array.  This file is collected last on purpose.
