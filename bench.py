@@ -421,7 +421,8 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--traversal", type=int, default=-1,
-                    help="closest-point search: 0 binary per lane, 1 climb, 2 32-wide warp-wide (-1: 2 in 3D, 0 in 2D)")
+                    help="closest-point search: 0 binary per lane, 1 climb, 2 32-wide warp-wide, 3 hybrid "
+                         "(0 while a warp is full, 2 in the tail; -1: 2 in 3D, 3 in 2D)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -452,7 +453,7 @@ def main():
 
     sc = make_scene(args.workload, args.walks)
     s = Solver(local)
-    trav = args.traversal if args.traversal >= 0 else (2 if sc.dim == 3 else 0)
+    trav = args.traversal if args.traversal >= 0 else (2 if sc.dim == 3 else 3)
     s.load_scene(sc, traversal=trav)
     n_pts, W = sc.query.shape[0], sc.walks
     total = n_pts * W
@@ -485,7 +486,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    steps_done = nodes = prims = 0
+    steps_done = nodes = wnodes = prims = 0
     kernel_ms = []
     grads = []
     for i in range(args.steps):
@@ -496,6 +497,7 @@ def main():
         st = s.stats()                             # synchronises; outside the events
         steps_done += st["steps_main"] + st["steps_nested"]
         nodes += st["nodes_visited"]
+        wnodes += st["wide_nodes_visited"]
         prims += st["prims_tested"]
         kernel_ms.append(st["kernel_ms"])
         grads.append(g.cpu().numpy())
@@ -515,20 +517,21 @@ def main():
     rmse = float(np.sqrt(np.mean((G - g_ref[None]) ** 2)))
     rel = rmse / float(np.sqrt(np.mean(g_ref ** 2)))
 
-    # roofline of the walk kernel: algorithmic bytes = BVH node fetches x node size
-    # (binary 48 / 64 B; 32-wide (2 dim + 1 + dim^2) x 128 B, leaf vertices included)
+    # roofline of the walk kernel: algorithmic bytes = binary node fetches x 48 / 64 B
+    # + 32-wide node visits x (2 dim + 1 + dim^2) x 128 B (leaf vertices included)
     # + element fetches outside the nodes (the previous step's element, outsized
     # elements; all element tests of the binary search) x 16 / 48 B
     # + one 32 B record per walk + 8 B query load per walk
-    node_b = (2 * sc.dim + 1 + sc.dim * sc.dim) * 128 if trav == 2 else (48 if sc.dim == 2 else 64)
+    node_b = 48 if sc.dim == 2 else 64
+    wide_b = (2 * sc.dim + 1 + sc.dim * sc.dim) * 128
     prim_b = 16 if sc.dim == 2 else 48
-    alg_bytes = nodes * node_b + prims * prim_b + args.steps * total * (32 + 8)
+    alg_bytes = nodes * node_b + wnodes * wide_b + prims * prim_b + args.steps * total * (32 + 8)
     walk_s = sum(kernel_ms) / 1e3
     achieved = alg_bytes / walk_s / 1e9 / args.steps * args.steps
     hbm, src = peaks()
     from paper_2405_12964_gb300.dwos import probe_l2_read
     l2 = probe_l2_read(local)
-    kname = f"walk_kernel<{sc.dim},{'true' if trav == 2 else 'false'}>"
+    kname = f"walk_kernel<{sc.dim},{'true' if trav in (2, 3) else 'false'}>"
     traffic_per_step = measured_traffic(kname, args.workload)
 
     e2e = None
@@ -570,13 +573,16 @@ def main():
             "config": {"workload": WORKLOADS[args.workload], "points": n_pts, "walks_per_point": W, "K": sc.K, "B": sc.B,
                        "n_param": sc.n_param, "eps": sc.eps, "h": sc.h,
                        "closest_point_search": {0: "binary LBVH, per lane", 1: "binary LBVH climbing from the hint",
-                                                2: "32-wide BVH, warp-wide"}[trav],
+                                                2: "32-wide BVH, warp-wide",
+                                                3: "binary LBVH per lane while >= 24 lanes of a warp are busy, "
+                                                   "32-wide warp-wide below"}[trav],
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": f"replicas x{world} (independent walk ranges, no collective)"},
             "gradient_estimates_per_s": world * total * args.steps / t,
             "grad_rmse": rmse, "grad_rel_rmse": rel, "grad_rmse_x_seconds": rmse * (ms_per_step / 1e3),
             "walk_steps_per_step": steps_done / args.steps,
             "closest_point_search": {"nodes_per_query": nodes / max(steps_done, 1),
+                                     "wide_nodes_per_query": wnodes / max(steps_done, 1),
                                      "element_fetches_per_query": prims / max(steps_done, 1)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,

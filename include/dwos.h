@@ -83,7 +83,10 @@ typedef struct {
                            element; 1 = climbing from that element's leaf with
                            the Morton-cell stop test; 2 = the 32-wide tree
                            searched by a whole warp, one query at a time;
-                           -1 = automatic (2 for triangles, 0 for segments) */
+                           3 = per warp: order 0 while at least 24 of its lanes
+                           have a walk, order 2 below (the tail of a launch);
+                           -1 = automatic (2 for triangles, 3 for segments;
+                           orders 2 and 3 fall back to 0 without a 32-wide tree) */
     int dudn_estimator; /* du/dn at a shell hit from the K nested walks: 0 = backward
                            difference (g(xbar) - mean u(xbar - h n)) / h, Eq.
                            (dudn_fd_estimate); 1 = ball gradient at x_off = xbar - h n:
@@ -131,11 +134,12 @@ typedef struct {
     uint64_t steps_nested;  /* distance queries of nested forward walks */
     uint64_t walks;         /* main walks run */
     uint64_t capped;        /* walk phases that hit max_steps */
-    uint64_t nodes_visited; /* BVH node fetches made by the distance queries */
+    uint64_t nodes_visited; /* binary BVH node fetches made by the distance queries */
     uint64_t prims_tested;  /* element distance tests made by the distance queries */
     uint64_t launches;      /* kernels this context has launched since creation */
     float kernel_ms;        /* device time of the last walk kernel (0 if unknown) */
     int blocks;             /* thread blocks of the last walk kernel */
+    uint64_t wide_nodes_visited; /* 32-wide node visits (search orders 2 and 3) */
 } dwos_run_stats;
 
 /* ---- context ------------------------------------------------------------ */
@@ -380,7 +384,7 @@ dwos_status dwos_batch_capture(dwos_batch* b);
 dwos_status dwos_batch_launch(dwos_batch* b);
 /* Time the walk launch of each dimension group over block size (128, 256),
  * resident blocks per SM (1, 2, 4, ... up to the occupancy limit) and the
- * distance-query search order (dwos_options.traversal 0 / 1 / 2), reps passes
+ * distance-query search order (dwos_options.traversal 0 to 3), reps passes
  * each, and keep the fastest; recaptures the graph if one exists.
  * Synchronises. */
 dwos_status dwos_batch_autotune(dwos_batch* b, int reps);

@@ -28,8 +28,8 @@ dwos_status fail(dwos_ctx* c, dwos_status s, const std::string& msg) {
 // The search order a launch uses: the warp-wide one only where the tree supports it.
 int effective_traversal(const dwos_ctx* c) {
     int t = c->opt.traversal;
-    if (t < 0) t = c->dim == 3 ? 2 : 0;
-    return (t == 2 && !c->bvh.wide_ok) ? 0 : t;
+    if (t < 0) t = c->dim == 3 ? 2 : 3;
+    return ((t == 2 || t == 3) && !c->bvh.wide_ok) ? 0 : t;
 }
 
 dwos_status cuda_fail(dwos_ctx* c, cudaError_t e, const char* where) {
@@ -284,8 +284,8 @@ dwos_status dwos_set_options(dwos_ctx* ctx, const dwos_options* o) {
     if (o->blocks_per_sm < 0 || o->blocks_per_sm > 64) return fail(ctx, DWOS_ERR_INVALID_ARG, "blocks_per_sm must be in [0, 64]");
     if (o->dudn_estimator < 0 || o->dudn_estimator > 1)
         return fail(ctx, DWOS_ERR_INVALID_ARG, "dudn_estimator must be 0 or 1");
-    if (o->traversal < -1 || o->traversal > 2)
-        return fail(ctx, DWOS_ERR_INVALID_ARG, "traversal must be -1 (automatic), 0, 1 or 2");
+    if (o->traversal < -1 || o->traversal > 3)
+        return fail(ctx, DWOS_ERR_INVALID_ARG, "traversal must be -1 (automatic), 0, 1, 2 or 3");
     ctx->opt = *o;
     return DWOS_OK;
 }
@@ -776,6 +776,7 @@ dwos_status dwos_last_stats(dwos_ctx* ctx, dwos_run_stats* out) {
     out->capped = c.capped;
     out->nodes_visited = c.nodes;
     out->prims_tested = c.prims;
+    out->wide_nodes_visited = c.wnodes;
     out->launches = ctx->launches;
     out->blocks = ctx->last_blocks;
     float ms = 0.0f;
@@ -884,6 +885,7 @@ constexpr size_t kStaticHeader = 4096;     // problem descriptor + counters
 constexpr size_t kStaticFlags = (size_t)DWOS_STATIC_MAX_WALKS * sizeof(int);
 constexpr size_t kStaticBytes = kStaticHeader + kStaticFlags + (size_t)DWOS_STATIC_MAX_WALKS * sizeof(dwos_record);
 static_assert(sizeof(DevProblem) + sizeof(DevCounters) <= kStaticHeader, "static header too small");
+static_assert(sizeof(DevProblem) <= 2048, "the counters sit 2048 bytes into the header");
 
 // Held by every GPU that loads the library, until the process exits.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];

@@ -48,7 +48,7 @@ struct dwos_batch {
     double* means = nullptr;            // per job: n_query doubles
     std::vector<size_t> mean_off;
     WalkLaunch cfg[4];                  // per dimension (index 2 and 3)
-    int trav[4] = {0, 0, 0, 2};         // per dimension: warp-wide search for triangles
+    int trav[4] = {0, 0, 3, 2};         // per dimension: hybrid for segments, warp-wide for triangles
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -132,7 +132,7 @@ bool wide_ok_dim(const dwos_batch* b, int dim) {
 // Rewrite the descriptor tables (after an autotuner change of search order).
 dwos_status upload_tables(dwos_batch* b) {
     for (int dim = 2; dim <= 3; ++dim)
-        if (b->trav[dim] == 2 && !wide_ok_dim(b, dim)) b->trav[dim] = 0;
+        if ((b->trav[dim] == 2 || b->trav[dim] == 3) && !wide_ok_dim(b, dim)) b->trav[dim] = 0;
     for (auto& ch : b->chunks) {
         std::vector<DevProblem> tab(ch.jobs.size());
         unsigned long long begin = 0;
@@ -326,8 +326,8 @@ dwos_status dwos_batch_autotune(dwos_batch* b, int reps) {
         float best = 1e30f;
         WalkLaunch best_cfg = b->cfg[dim];
         int best_trav = b->trav[dim];
-        for (int trav = 0; trav <= 2; ++trav) {
-            if (trav == 2 && !wide_ok_dim(b, dim)) continue;
+        for (int trav = 0; trav <= 3; ++trav) {
+            if ((trav == 2 || trav == 3) && !wide_ok_dim(b, dim)) continue;
             b->trav[dim] = trav;
             if (dwos_status s = upload_tables(b)) return s;
             for (int bs : sizes) {
@@ -387,6 +387,7 @@ dwos_status dwos_batch_stats(dwos_batch* b, dwos_run_stats* out) {
         out->capped += c.capped;
         out->nodes_visited += c.nodes;
         out->prims_tested += c.prims;
+        out->wide_nodes_visited += c.wnodes;
         if (c.error & 1) return bfail(b, DWOS_ERR_STEP_LIMIT, "BVH traversal exceeded its iteration bound");
     }
     return DWOS_OK;

@@ -535,7 +535,7 @@ __global__ void closest_wide_kernel(BvhView bvh, WideView wv, const int* prim_el
     const int e = wide_closest<DIM>(wv, __ballot_sync(kWarpAll, act), q, best2, best, stk, nn, np);
     if (e) atomicOr(err, 1);
     if (ctr) {
-        atomicAdd(&ctr->nodes, (unsigned long long)nn);
+        atomicAdd(&ctr->wnodes, (unsigned long long)nn);
         atomicAdd(&ctr->prims, (unsigned long long)np);
     }
     if (!act) return;

@@ -25,7 +25,8 @@ struct DevProblem {
     const int* leaf_parent;     // leaf -> parent node
     const float* node_cell;     // Morton cell per internal node
     float r_max;                // element radius bound for the cell test
-    int traversal;              // 0 root-down, 1 climb from the hint leaf, 2 warp-wide over the 32-wide tree
+    int traversal;              // 0 root-down, 1 climb from the hint leaf, 2 warp-wide over the 32-wide tree,
+                                // 3 root-down per lane while a warp has many busy lanes, warp-wide below
     const float* wnodes;        // 32-wide tree (SoA nodes), root first
     int n_wide;                 // its node count
     int data_kind;              // 0 mapped, 1 field
@@ -44,7 +45,7 @@ struct DevProblem {
     const float* xq;            // n_query x dim
     const int* valid;           // n_query inside flags, or null (no check)
     int walks;                  // walks per point
-    int pad0;
+    int lane_min;               // order 3: busy lanes from which a warp searches per lane (0: kHybridLaneMin)
     unsigned long long walk_id_base;
     unsigned long long work_begin;   // first global work index of this problem
     unsigned long long work_end;
@@ -72,10 +73,11 @@ struct DevCounters {
     unsigned long long steps_main;
     unsigned long long steps_nested;
     unsigned long long capped;
-    unsigned long long nodes;   // BVH node fetches
+    unsigned long long nodes;   // binary BVH node fetches
     unsigned long long prims;   // element distance tests
+    unsigned long long wnodes;  // 32-wide node visits
     int error;                  // bit 0: traversal bound exceeded, bit 1: query outside Omega
-    int pad[3];
+    int pad[1];
 };
 
 // BVH build (bvh.cu).  All pointers are device pointers; work on `stream`.
@@ -131,7 +133,7 @@ struct WalkLaunch {
     int block_size;
     int blocks_per_sm;
     int n_sm;
-    int traversal = 0;          // 2: warp-wide search (every problem of the launch has wide_ok)
+    int traversal = 0;          // 2, 3: warp-wide search (every problem of the launch has wide_ok)
 };
 cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_probs,
                          unsigned long long total_work, DevCounters* d_counters, cudaStream_t stream,

@@ -25,6 +25,10 @@ namespace {
 
 constexpr int kMaxProblems = 64;
 constexpr unsigned kFull = 0xffffffffu;
+// Search order 3: a warp with at least this many busy lanes searches the binary
+// tree one query per lane (its lanes' searches overlap); with fewer, in the tail
+// of the launch, it searches the 32-wide tree together, one query at a time.
+constexpr int kHybridLaneMin = 24;
 
 template <int DIM>
 __device__ __forceinline__ float field_value(const float* c, const float* x, float* grad) {
@@ -65,7 +69,7 @@ __device__ __forceinline__ void leaf_geometry(const float4* __restrict__ prims, 
 
 struct WarpStats {             // per lane; summed over the warp in 64 bits at the end
     unsigned steps_main = 0, steps_nested = 0, capped = 0;
-    unsigned nodes = 0, prims = 0;
+    unsigned nodes = 0, prims = 0, wnodes = 0;
 };
 
 // What a walk keeps from the end of its main walk until its last nested walk
@@ -87,7 +91,7 @@ struct PhaseState {
 // one traversal stack per warp and the threads' phase states.
 __host__ __device__ inline size_t walk_smem_bytes(int n_probs, int block_size, int traversal, int dim = 3) {
     size_t b = (sizeof(DevProblem) * (size_t)n_probs + 15) & ~(size_t)15;
-    if (traversal == 2)
+    if (traversal == 2 || traversal == 3)
         b += sizeof(float2) * kWideStack * (size_t)(block_size / 32) +
              (dim == 2 ? sizeof(PhaseState<2>) : sizeof(PhaseState<3>)) * (size_t)block_size;
     return b;
@@ -168,22 +172,29 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
         // ---- DistanceToBoundary, seeded with the previous closest element
         float best2 = kInf;
         int best = -1;
-        if (wide) {   // all lanes search the 32-wide tree together, one lane's query at a time
-            const DevProblem& Pw = sp[prob];
-            if (active) {
-                if (hint >= 0) { best2 = prim_dist2<DIM>(Pw.prims, hint, x); best = hint; ++st.prims; }
-                big_closest<DIM>(Pw.prims, Pw.n_tree, Pw.n_big, x, best2, best, st.prims);
+        bool lane_search = !wide;
+        if (wide) {
+            const unsigned busy = __ballot_sync(kFull, active);
+            // order 3 (the same for every problem of a launch): per-lane search while the warp is full
+            if (sp[0].traversal == 3)
+                lane_search = __popc(busy) >= (sp[0].lane_min > 0 ? sp[0].lane_min : kHybridLaneMin);
+            if (!lane_search) {   // all lanes search the 32-wide tree together, one lane's query at a time
+                const DevProblem& Pw = sp[prob];
+                if (active) {
+                    if (hint >= 0) { best2 = prim_dist2<DIM>(Pw.prims, hint, x); best = hint; ++st.prims; }
+                    big_closest<DIM>(Pw.prims, Pw.n_tree, Pw.n_big, x, best2, best, st.prims);
+                }
+                const WideView wv{Pw.wnodes, Pw.prims, Pw.n_wide, Pw.n_tree};
+                error |= wide_closest<DIM>(wv, busy, x, best2, best, stk, st.wnodes, st.prims) & 1;
             }
-            const WideView wv{Pw.wnodes, Pw.prims, Pw.n_wide, Pw.n_tree};
-            error |= wide_closest<DIM>(wv, __ballot_sync(kFull, active), x, best2, best, stk, st.nodes, st.prims) & 1;
         }
         if (!active) continue;
 
         const DevProblem& P = sp[prob];
         const unsigned long long local = gw - P.work_begin;
-        if (!wide) {
-            BvhView bvh{P.nodes, P.prims, P.root, P.n_internal, P.n_tree, P.n_big, P.traversal, P.leaf_parent,
-                        P.node_cell, P.r_max};
+        if (lane_search) {
+            BvhView bvh{P.nodes, P.prims, P.root, P.n_internal, P.n_tree, P.n_big, P.traversal == 1,
+                        P.leaf_parent, P.node_cell, P.r_max};
             if (hint >= 0) { best2 = prim_dist2<DIM>(P.prims, hint, x); best = hint; }
             if (hint >= 0) ++st.prims;
             if (!closest_leaf<DIM>(bvh, x, best2, best, st.nodes, st.prims)) error |= 1;
@@ -412,16 +423,18 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
         sc += __shfl_xor_sync(kFull, sc, o);
         error |= __shfl_xor_sync(kFull, error, o);
     }
-    unsigned long long nodes = st.nodes, prims = st.prims;
+    unsigned long long nodes = st.nodes, prims = st.prims, wnodes = st.wnodes;
     for (int o = 16; o > 0; o >>= 1) {
         nodes += __shfl_xor_sync(kFull, nodes, o);
         prims += __shfl_xor_sync(kFull, prims, o);
+        wnodes += __shfl_xor_sync(kFull, wnodes, o);
     }
     if (lane == 0) {
         atomicAdd(&ctr->steps_main, sm);
         atomicAdd(&ctr->steps_nested, sn);
         atomicAdd(&ctr->nodes, nodes);
         atomicAdd(&ctr->prims, prims);
+        if (wnodes) atomicAdd(&ctr->wnodes, wnodes);
         if (sc) atomicAdd(&ctr->capped, sc);
         if (error) atomicOr(&ctr->error, error);
     }
@@ -432,7 +445,7 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
 int walk_max_blocks_per_sm(int dim, int block_size, int traversal) {
     int n = 0;
     const size_t smem = walk_smem_bytes(1, block_size, traversal, dim);
-    if (traversal == 2) {
+    if (traversal == 2 || traversal == 3) {
         if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<2, true>, block_size, smem);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<3, true>, block_size, smem);
     } else {
@@ -464,7 +477,7 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
         kernel<<<(int)blocks, bs, smem, stream>>>(d_probs, n_probs, total, d_counters);
         return cudaGetLastError();
     };
-    if (L.traversal == 2) return L.dim == 2 ? go(walk_kernel<2, true>) : go(walk_kernel<3, true>);
+    if (L.traversal == 2 || L.traversal == 3) return L.dim == 2 ? go(walk_kernel<2, true>) : go(walk_kernel<3, true>);
     return L.dim == 2 ? go(walk_kernel<2, false>) : go(walk_kernel<3, false>);
 }
 

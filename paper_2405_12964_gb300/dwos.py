@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
 class RunStats(ctypes.Structure):
     _fields_ = [("steps_main", ctypes.c_uint64), ("steps_nested", ctypes.c_uint64), ("walks", ctypes.c_uint64),
                 ("capped", ctypes.c_uint64), ("nodes_visited", ctypes.c_uint64), ("prims_tested", ctypes.c_uint64),
-                ("launches", ctypes.c_uint64), ("kernel_ms", ctypes.c_float), ("blocks", ctypes.c_int)]
+                ("launches", ctypes.c_uint64), ("kernel_ms", ctypes.c_float), ("blocks", ctypes.c_int),
+                ("wide_nodes_visited", ctypes.c_uint64)]
 
 
 class DwosError(RuntimeError):

@@ -110,7 +110,7 @@ def test_philox_bit_exact(Solver):
         assert np.array_equal(got[i], oracle.philox4x32_10(ctrs[i], key))
 
 
-@pytest.mark.parametrize("traversal", [0, 2])
+@pytest.mark.parametrize("traversal", [0, 2, 3])
 @pytest.mark.parametrize("which", ["disk", "star", "sphere", "ball_small"])
 def test_closest_point_matches_brute_force(Solver, which, traversal):
     rng = np.random.default_rng(1)
@@ -173,7 +173,7 @@ def test_disk_per_walk_replay(Solver, variant):
     check_walks(sc, g, o)
 
 
-@pytest.mark.parametrize("traversal", [0, 2])
+@pytest.mark.parametrize("traversal", [0, 2, 3])
 def test_star_box_per_walk_replay_with_nested_walks(Solver, traversal):
     sc = scenes.star_box_scene(n_seg=4096, n_query=24)
     s, g, o = run_pair(Solver, sc, 32, K=2, traversal=traversal)
@@ -199,7 +199,7 @@ def test_ball_gradient_estimator_replay(Solver, which):
     assert np.abs(o["dudn"][same]).max() > 0
 
 
-@pytest.mark.parametrize("traversal", [0, 2])
+@pytest.mark.parametrize("traversal", [0, 2, 3])
 def test_sphere_3d_per_walk_replay_with_source(Solver, traversal):
     sc = scenes.sh_sphere_scene(freq=16, n_query=12, K=2)
     s, g, o = run_pair(Solver, sc, 24, traversal=traversal)
@@ -215,7 +215,7 @@ def test_warp_wide_search_is_the_one_that_ran(Solver):
         s.load_scene(sc, traversal=t)
         out.append(s.walk_records(sc.query, 64)["rec"])
         st = s.stats()
-        nodes.append(st["nodes_visited"] / (st["steps_main"] + st["steps_nested"]))
+        nodes.append((st["nodes_visited"] + st["wide_nodes_visited"]) / (st["steps_main"] + st["steps_nested"]))
     info = s.bvh_info()
     fill = (info["n_wide"] - 1 + info["n_tree"]) / (32.0 * info["n_wide"])
     print("32-wide tree: %d nodes, %d levels, %.2f of the child slots used" % (info["n_wide"], info["wide_depth"], fill))
@@ -225,6 +225,23 @@ def test_warp_wide_search_is_the_one_that_ran(Solver):
     assert np.allclose(out[0]["u"][same], out[1]["u"][same], rtol=1e-5, atol=1e-6)
     print("node visits per query: binary %.1f, 32-wide %.1f" % tuple(nodes))
     assert nodes[1] < 0.5 * nodes[0]
+
+
+def test_hybrid_search_switches_trees_and_keeps_the_walks(Solver):
+    # order 3: full warps search the binary tree per lane, the launch's tail the 32-wide
+    # tree; the closest element, hence every walk, is the same as with order 0
+    sc = scenes.star_box_scene(n_query=32, walks=256)
+    out, st = [], []
+    for t in (0, 3):
+        s = Solver(0)
+        s.load_scene(sc, traversal=t)
+        out.append(s.walk_records(sc.query, sc.walks)["rec"])
+        st.append(s.stats())
+    # a small launch: each lane gets about one walk, so both trees see part of the queries
+    assert st[0]["wide_nodes_visited"] == 0 and st[1]["wide_nodes_visited"] > 0 and st[1]["nodes_visited"] > 0
+    same = out[0]["elem"] == out[1]["elem"]
+    assert same.mean() > 0.99
+    assert np.allclose(out[0]["u"][same], out[1]["u"][same], rtol=1e-5, atol=1e-6)
 
 
 def test_replay_from_points_at_and_near_the_shell(Solver):
@@ -398,7 +415,7 @@ def test_capped_walks_are_counted(Solver):
     assert ((g["trace"][:, 0] & 0x3FFFFFFF) <= 3).all()
 
 
-@pytest.mark.parametrize("traversal", [0, 1, 2])
+@pytest.mark.parametrize("traversal", [0, 1, 2, 3])
 @pytest.mark.parametrize("which", ["star", "sphere"])
 def test_hinted_closest_point_equals_unhinted(Solver, which, traversal):
     # the walk seeds each query with the previous hit and climbs the BVH from it,
