@@ -421,8 +421,9 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--traversal", type=int, default=-1,
-                    help="closest-point search: 0 binary per lane, 1 climb, 2 32-wide warp-wide, 3 hybrid "
-                         "(0 while a warp is full, 2 in the tail; -1: 2 in 3D, 3 in 2D)")
+                    help="closest-point search: 0 binary per lane, 1 climb, 2 32-wide warp-wide, 3 routed "
+                         "(only queries that reach inside the binary root's child boxes are searched, warp-wide; "
+                         "-1: 3)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -453,7 +454,7 @@ def main():
 
     sc = make_scene(args.workload, args.walks)
     s = Solver(local)
-    trav = args.traversal if args.traversal >= 0 else (2 if sc.dim == 3 else 3)
+    trav = args.traversal if args.traversal >= 0 else 3
     s.load_scene(sc, traversal=trav)
     n_pts, W = sc.query.shape[0], sc.walks
     total = n_pts * W
@@ -574,8 +575,8 @@ def main():
                        "n_param": sc.n_param, "eps": sc.eps, "h": sc.h,
                        "closest_point_search": {0: "binary LBVH, per lane", 1: "binary LBVH climbing from the hint",
                                                 2: "32-wide BVH, warp-wide",
-                                                3: "binary LBVH per lane while >= 24 lanes of a warp are busy, "
-                                                   "32-wide warp-wide below"}[trav],
+                                                3: "routed: binary-root test per query, then the 32-wide BVH "
+                                                   "warp-wide for the queries that need the tree"}[trav],
                        "l2": "flushed between timed steps (256 MB write outside the events)",
                        "parallelism": f"replicas x{world} (independent walk ranges, no collective)"},
             "gradient_estimates_per_s": world * total * args.steps / t,

@@ -83,10 +83,13 @@ typedef struct {
                            element; 1 = climbing from that element's leaf with
                            the Morton-cell stop test; 2 = the 32-wide tree
                            searched by a whole warp, one query at a time;
-                           3 = per warp: order 0 while at least 24 of its lanes
-                           have a walk, order 2 below (the tail of a launch);
-                           -1 = automatic (2 for triangles, 3 for segments;
-                           orders 2 and 3 fall back to 0 without a 32-wide tree) */
+                           3 = routed: after the seed and the outsized elements,
+                           a query whose bound excludes both child boxes of the
+                           binary root needs no tree search; the others are
+                           searched as in order 2 (for segments, as in order 0
+                           when more than 16 lanes of a warp need one at once);
+                           -1 = automatic (3; orders 2 and 3 fall back to 0
+                           without a 32-wide tree) */
     int dudn_estimator; /* du/dn at a shell hit from the K nested walks: 0 = backward
                            difference (g(xbar) - mean u(xbar - h n)) / h, Eq.
                            (dudn_fd_estimate); 1 = ball gradient at x_off = xbar - h n:

@@ -28,7 +28,7 @@ dwos_status fail(dwos_ctx* c, dwos_status s, const std::string& msg) {
 // The search order a launch uses: the warp-wide one only where the tree supports it.
 int effective_traversal(const dwos_ctx* c) {
     int t = c->opt.traversal;
-    if (t < 0) t = c->dim == 3 ? 2 : 3;
+    if (t < 0) t = 3;
     return ((t == 2 || t == 3) && !c->bvh.wide_ok) ? 0 : t;
 }
 

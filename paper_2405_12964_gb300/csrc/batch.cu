@@ -48,7 +48,7 @@ struct dwos_batch {
     double* means = nullptr;            // per job: n_query doubles
     std::vector<size_t> mean_off;
     WalkLaunch cfg[4];                  // per dimension (index 2 and 3)
-    int trav[4] = {0, 0, 3, 2};         // per dimension: hybrid for segments, warp-wide for triangles
+    int trav[4] = {0, 0, 3, 3};         // per dimension: routed search (order 3)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

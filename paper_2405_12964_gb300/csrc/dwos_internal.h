@@ -26,7 +26,8 @@ struct DevProblem {
     const float* node_cell;     // Morton cell per internal node
     float r_max;                // element radius bound for the cell test
     int traversal;              // 0 root-down, 1 climb from the hint leaf, 2 warp-wide over the 32-wide tree,
-                                // 3 root-down per lane while a warp has many busy lanes, warp-wide below
+                                // 3 routed: no tree search if the binary root's child boxes are outside the
+                                // bound, else warp-wide (per lane when many lanes need one in a step)
     const float* wnodes;        // 32-wide tree (SoA nodes), root first
     int n_wide;                 // its node count
     int data_kind;              // 0 mapped, 1 field
@@ -45,7 +46,7 @@ struct DevProblem {
     const float* xq;            // n_query x dim
     const int* valid;           // n_query inside flags, or null (no check)
     int walks;                  // walks per point
-    int lane_min;               // order 3: busy lanes from which a warp searches per lane (0: kHybridLaneMin)
+    int wide_max;               // order 3: most tree searches per warp step done warp-wide (0: the default)
     unsigned long long walk_id_base;
     unsigned long long work_begin;   // first global work index of this problem
     unsigned long long work_end;

@@ -25,10 +25,13 @@ namespace {
 
 constexpr int kMaxProblems = 64;
 constexpr unsigned kFull = 0xffffffffu;
-// Search order 3: a warp with at least this many busy lanes searches the binary
-// tree one query per lane (its lanes' searches overlap); with fewer, in the tail
-// of the launch, it searches the 32-wide tree together, one query at a time.
-constexpr int kHybridLaneMin = 24;
+// Search order 3 routes each query by the binary root's two child boxes: most
+// queries (closer to an outsized element, or to their seed, than to any tree
+// box) need no tree search at all; the few that do are searched by the whole
+// warp over the 32-wide tree, one at a time, unless more than this many lanes
+// of the warp need one in the same step, when each searches the binary tree.
+constexpr int kRouteWideMax2 = 16;   // segments
+constexpr int kRouteWideMax3 = 32;   // triangles: the per-lane binary search never pays
 
 template <int DIM>
 __device__ __forceinline__ float field_value(const float* c, const float* x, float* grad) {
@@ -173,19 +176,39 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
         float best2 = kInf;
         int best = -1;
         bool lane_search = !wide;
+        bool seeded = false;   // hint and outsized elements already tested
         if (wide) {
-            const unsigned busy = __ballot_sync(kFull, active);
-            // order 3 (the same for every problem of a launch): per-lane search while the warp is full
-            if (sp[0].traversal == 3)
-                lane_search = __popc(busy) >= (sp[0].lane_min > 0 ? sp[0].lane_min : kHybridLaneMin);
-            if (!lane_search) {   // all lanes search the 32-wide tree together, one lane's query at a time
-                const DevProblem& Pw = sp[prob];
+            const DevProblem& Pw = sp[prob];
+            if (active) {
+                if (hint >= 0) { best2 = prim_dist2<DIM>(Pw.prims, hint, x); best = hint; ++st.prims; }
+                big_closest<DIM>(Pw.prims, Pw.n_tree, Pw.n_big, x, best2, best, st.prims);
+                seeded = true;
+            }
+            unsigned need = __ballot_sync(kFull, active);
+            if (sp[0].traversal == 3) {   // the same order for every problem of a launch
+                // route: only queries with a root child box inside the bound need the tree
+                bool desc = false;
                 if (active) {
-                    if (hint >= 0) { best2 = prim_dist2<DIM>(Pw.prims, hint, x); best = hint; ++st.prims; }
-                    big_closest<DIM>(Pw.prims, Pw.n_tree, Pw.n_big, x, best2, best, st.prims);
+                    if (Pw.n_internal > 0) {
+                        float lo0[DIM], hi0[DIM], lo1[DIM], hi1[DIM];
+                        int c0, c1, parent;
+                        load_node<DIM>(Pw.nodes, Pw.root, lo0, hi0, lo1, hi1, c0, c1, parent);
+                        ++st.nodes;
+                        desc = box_dist2<DIM>(x, lo0, hi0) < best2 || box_dist2<DIM>(x, lo1, hi1) < best2;
+                    } else {
+                        desc = Pw.n_tree > 0;
+                    }
                 }
+                need = __ballot_sync(kFull, desc);
+                const int wide_max = sp[0].wide_max > 0 ? sp[0].wide_max : (DIM == 2 ? kRouteWideMax2 : kRouteWideMax3);
+                if (__popc(need) > wide_max) {   // many searches this step: one per lane, in parallel
+                    lane_search = desc;
+                    need = 0;
+                }
+            }
+            if (need) {   // all lanes search the 32-wide tree together, one lane's query at a time
                 const WideView wv{Pw.wnodes, Pw.prims, Pw.n_wide, Pw.n_tree};
-                error |= wide_closest<DIM>(wv, busy, x, best2, best, stk, st.wnodes, st.prims) & 1;
+                error |= wide_closest<DIM>(wv, need, x, best2, best, stk, st.wnodes, st.prims) & 1;
             }
         }
         if (!active) continue;
@@ -193,10 +216,9 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
         const DevProblem& P = sp[prob];
         const unsigned long long local = gw - P.work_begin;
         if (lane_search) {
-            BvhView bvh{P.nodes, P.prims, P.root, P.n_internal, P.n_tree, P.n_big, P.traversal == 1,
+            BvhView bvh{P.nodes, P.prims, P.root, P.n_internal, P.n_tree, seeded ? 0 : P.n_big, P.traversal == 1,
                         P.leaf_parent, P.node_cell, P.r_max};
-            if (hint >= 0) { best2 = prim_dist2<DIM>(P.prims, hint, x); best = hint; }
-            if (hint >= 0) ++st.prims;
+            if (!seeded && hint >= 0) { best2 = prim_dist2<DIM>(P.prims, hint, x); best = hint; ++st.prims; }
             if (!closest_leaf<DIM>(bvh, x, best2, best, st.nodes, st.prims)) error |= 1;
         }
         const float d = sqrtf(best2);

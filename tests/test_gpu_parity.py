@@ -227,8 +227,9 @@ def test_warp_wide_search_is_the_one_that_ran(Solver):
     assert nodes[1] < 0.5 * nodes[0]
 
 
-def test_hybrid_search_switches_trees_and_keeps_the_walks(Solver):
-    # order 3: full warps search the binary tree per lane, the launch's tail the 32-wide
+def test_routed_search_skips_the_tree_and_keeps_the_walks(Solver):
+    # order 3: every query tests the binary root's two child boxes against its bound (one
+    # node visit); only the queries that reach inside them are searched, over the 32-wide
     # tree; the closest element, hence every walk, is the same as with order 0
     sc = scenes.star_box_scene(n_query=32, walks=256)
     out, st = [], []
@@ -237,8 +238,11 @@ def test_hybrid_search_switches_trees_and_keeps_the_walks(Solver):
         s.load_scene(sc, traversal=t)
         out.append(s.walk_records(sc.query, sc.walks)["rec"])
         st.append(s.stats())
-    # a small launch: each lane gets about one walk, so both trees see part of the queries
-    assert st[0]["wide_nodes_visited"] == 0 and st[1]["wide_nodes_visited"] > 0 and st[1]["nodes_visited"] > 0
+    steps = [x["steps_main"] + x["steps_nested"] for x in st]
+    assert st[0]["wide_nodes_visited"] == 0 and st[1]["wide_nodes_visited"] > 0
+    assert st[1]["nodes_visited"] >= steps[1]
+    # most queries stop at the root test: far fewer node visits than the per-lane search
+    assert st[1]["wide_nodes_visited"] < 0.25 * steps[1]
     same = out[0]["elem"] == out[1]["elem"]
     assert same.mean() > 0.99
     assert np.allclose(out[0]["u"][same], out[1]["u"][same], rtol=1e-5, atol=1e-6)
