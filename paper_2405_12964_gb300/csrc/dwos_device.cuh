@@ -487,9 +487,7 @@ __device__ __forceinline__ int wide_closest(const WideView& mine, unsigned need,
                 const unsigned lm = __ballot_sync(kWarpAll, leaf);
                 if (lm) {
                     float dd = kInf;
-                    int pi = 0x7fffffff;
                     if (leaf) {
-                        pi = ~code;
                         if (DIM == 2) {
                             float t;
                             dd = seg_closest(q, vt[0], vt[1], vt[2], vt[3], t);
@@ -499,29 +497,25 @@ __device__ __forceinline__ int wide_closest(const WideView& mine, unsigned need,
                                              make_float3(vt[6], vt[7], vt[8]), w1, w2);
                         }
                     }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const float od = __shfl_xor_sync(kWarpAll, dd, o);
-                        const int op = __shfl_xor_sync(kWarpAll, pi, o);
-                        if (od < dd || (od == dd && op < pi)) { dd = od; pi = op; }
-                    }
-                    if (dd < b2) { b2 = dd; bi = pi; }
+                    // warp argmin, ties to the lower leaf index: squared distances are >= 0 (or
+                    // +inf), so their bit patterns order like the values and one integer
+                    // reduction finds the minimum; a second one picks the tied leaf
+                    const unsigned bits = __float_as_uint(dd);
+                    const unsigned mbits = __reduce_min_sync(kWarpAll, bits);
+                    const unsigned pi = __reduce_min_sync(kWarpAll, leaf && bits == mbits ? (unsigned)~code : 0xffffffffu);
+                    const float md = __uint_as_float(mbits);
+                    if (md < b2) { b2 = md; bi = (int)pi; }
                 }
                 const bool inner = code >= 0 && code != kEmptyChild && cd < b2;
                 const unsigned im = __ballot_sync(kWarpAll, inner);
                 if (im) {
                     const int cnt = __popc(im);
                     if (top + cnt > kWideStack) { err |= 4; break; }
-                    // the nearest child goes on top (popped next); its siblings below it in
-                    // lane order, which is the Morton order of the subtrees
-                    float md = inner ? cd : kInf;
-                    int ml = inner ? lane : 32;
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const float od = __shfl_xor_sync(kWarpAll, md, o);
-                        const int ol = __shfl_xor_sync(kWarpAll, ml, o);
-                        if (od < md || (od == md && ol < ml)) { md = od; ml = ol; }
-                    }
+                    // the nearest child (ties to the lower lane) goes on top (popped next); its
+                    // siblings below it in lane order, which is the Morton order of the subtrees
+                    const unsigned cbits = inner ? __float_as_uint(cd) : 0xffffffffu;
+                    const unsigned mc = __reduce_min_sync(kWarpAll, cbits);
+                    const int ml = __ffs(__ballot_sync(kWarpAll, inner && cbits == mc)) - 1;
                     const unsigned rest = im & ~(1u << ml);
                     __syncwarp();
                     if (inner) {
