@@ -247,7 +247,7 @@ void dwos_destroy(dwos_ctx* ctx) {
     bvh_free(ctx->bvh);
     void* bufs[] = {ctx->vert_ref, ctx->vert, ctx->elem, ctx->jac, ctx->theta, ctx->g_vert, ctx->dg_vert, ctx->rec,
                     ctx->xq, ctx->valid, ctx->wvec, ctx->out, ctx->acc_vert, ctx->trace, ctx->dbg, ctx->misc_f,
-                    ctx->misc_i, ctx->misc_u, ctx->d_prob, ctx->d_ctr, ctx->d_err, ctx->pw};
+                    ctx->misc_i, ctx->misc_u, ctx->d_prob, ctx->d_ctr, ctx->d_err, ctx->pw, ctx->vert_active};
     for (void* p : bufs) if (p) cudaFree(p);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -331,6 +331,7 @@ dwos_status dwos_set_boundary(dwos_ctx* ctx, int dim, int n_vert, const float* v
     CK(cudaMemsetAsync(ctx->theta, 0, (size_t)std::max(n_param, 1) * sizeof(float), ctx->stream), "zero theta");
     ctx->dim = dim; ctx->n_vert = n_vert; ctx->n_elem = n_elem; ctx->n_param = n_param;
     ctx->data_kind = 0;
+    ctx->active_stale = true;
     std::memset(ctx->field, 0, sizeof(ctx->field));
     if (dwos_status s = rebuild(ctx)) return s;
     CK(cudaStreamSynchronize(ctx->stream), "BVH build");
@@ -372,6 +373,7 @@ dwos_status dwos_set_dirichlet_mapped(dwos_ctx* ctx, const float* g_vert, const 
         CK(to_device(ctx, ctx->dg_vert, dg_vert, (size_t)ctx->n_vert * ctx->n_param, mem), "copy dg");
     }
     ctx->data_kind = 0;
+    ctx->active_stale = true;
     return DWOS_OK;
 }
 
@@ -381,6 +383,7 @@ dwos_status dwos_set_dirichlet_field(dwos_ctx* ctx, const double* coeffs) {
     for (int i = 0; i < 10; ++i) if (!std::isfinite(coeffs[i])) return fail(ctx, DWOS_ERR_INVALID_ARG, "coeffs must be finite");
     std::memcpy(ctx->field, coeffs, sizeof(ctx->field));
     ctx->data_kind = 1;
+    ctx->active_stale = true;
     return DWOS_OK;
 }
 
@@ -432,6 +435,19 @@ dwos_status dwos_eval(dwos_ctx* ctx, int n_query, const float* xq, int W, double
     return DWOS_OK;
 }
 
+// Per-vertex flags: a nonzero Jacobian or dg row (recomputed after the boundary or the
+// data changed).  The scatter skips unflagged vertices when only the parameter gradient
+// is wanted: their accumulators meet zero rows in the adjoint GEMV.
+static dwos_status ensure_vert_active(dwos_ctx* ctx) {
+    if (!ctx->active_stale && ctx->vert_active) return DWOS_OK;
+    CK(grow(ctx->vert_active, ctx->vert_active_cap, (size_t)std::max(ctx->n_vert, 1)), "alloc vertex flags");
+    CK(launch_vertex_active(ctx->jac, ctx->dg_vert, ctx->n_vert, ctx->dim, ctx->n_param, ctx->vert_active,
+                            ctx->stream), "vertex flags");
+    ctx->launches += 1;
+    ctx->active_stale = false;
+    return DWOS_OK;
+}
+
 // mode 0: VJP with cotangent wv; 1: squared-loss gradient, U-statistic product; 2: correlated
 // product; 3: uncorrelated product (wv = uref for modes 1-3).
 static dwos_status reverse_common(dwos_ctx* ctx, int n_query, const float* xq, const float* wv, int W,
@@ -470,8 +486,13 @@ static dwos_status reverse_common(dwos_ctx* ctx, int n_query, const float* xq, c
            "reduce u");
         ctx->launches += n_query > 0 ? 1 : 0;
     }
+    const unsigned char* active = nullptr;   // every vertex when the vertex gradient is returned
+    if (!grad_vert) {
+        if (dwos_status s = ensure_vert_active(ctx)) return s;
+        active = ctx->vert_active;
+    }
     CK(launch_scatter(ctx->rec, ctx->elem, ctx->dim, n_query, W, ctx->opt.B, mode, ctx->wvec, ctx->acc_vert, acc_g,
-                      ctx->stream, nullptr, d_umean, d_pw), "scatter");
+                      ctx->stream, nullptr, d_umean, d_pw, active), "scatter");
     ctx->launches += n_query > 0 ? 1 : 0;
     double* d_grad = mem == DWOS_MEM_DEVICE ? grad_param : ctx->out;
     if (N > 0) {
@@ -563,8 +584,9 @@ dwos_status dwos_grad_l2_cv(dwos_ctx* ctx, int n_query, const float* xq, const f
     CK(grow(ctx->acc_vert, ctx->acc_cap, nacc), "alloc accumulators");
     CK(cudaMemsetAsync(ctx->acc_vert, 0, nacc * sizeof(double), ctx->stream), "zero accumulators");
     double* acc_g = ctx->dg_vert ? ctx->acc_vert + (size_t)ctx->n_vert * ctx->dim : nullptr;
+    if (dwos_status s = ensure_vert_active(ctx)) return s;
     CK(launch_scatter(ctx->rec, ctx->elem, ctx->dim, n_query, W, ctx->opt.B, 1, ctx->wvec, ctx->acc_vert, acc_g,
-                      ctx->stream, cvp), "scatter");
+                      ctx->stream, cvp, nullptr, nullptr, ctx->vert_active), "scatter");
     if (N > 0) {
         CK(cudaMemsetAsync(grad_param, 0, (size_t)N * sizeof(double), ctx->stream), "zero grad");
         CK(launch_gemv(ctx->jac, ctx->dg_vert, ctx->acc_vert, acc_g, ctx->n_vert, ctx->dim, N, grad_param,

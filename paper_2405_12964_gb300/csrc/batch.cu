@@ -47,6 +47,8 @@ struct dwos_batch {
     std::vector<size_t> acc_off;
     double* means = nullptr;            // per job: n_query doubles
     std::vector<size_t> mean_off;
+    unsigned char* active = nullptr;    // per job: n_vert vertex flags (nonzero Jacobian / dg row)
+    std::vector<size_t> active_off;
     WalkLaunch cfg[4];                  // per dimension (index 2 and 3)
     int trav[4] = {0, 0, 3, 3};         // per dimension: routed search (order 3)
     cudaGraph_t graph = nullptr;
@@ -222,6 +224,19 @@ dwos_status dwos_batch_create(dwos_batch** out, const dwos_batch_job* jobs, int 
     if ((e = cudaMalloc(&b->rec, sizeof(dwos_record) * n_rec)) != cudaSuccess) return bail(bcuda(b, e, "alloc records"));
     if ((e = cudaMalloc(&b->acc, sizeof(double) * n_acc)) != cudaSuccess) return bail(bcuda(b, e, "alloc accumulators"));
     if ((e = cudaMalloc(&b->means, sizeof(double) * n_mean)) != cudaSuccess) return bail(bcuda(b, e, "alloc means"));
+    // vertices with zero Jacobian and dg rows cannot reach a job's parameter gradient: the
+    // scatter skips them (the batch returns no vertex gradients)
+    {
+        size_t n_act = 0;
+        for (auto& j : b->jobs) { b->active_off.push_back(n_act); n_act += (size_t)std::max(j.ctx->n_vert, 1); }
+        if ((e = cudaMalloc(&b->active, n_act)) != cudaSuccess) return bail(bcuda(b, e, "alloc vertex flags"));
+        for (int i = 0; i < n_jobs; ++i) {
+            const dwos_ctx* c = b->jobs[i].ctx;
+            if ((e = launch_vertex_active(c->jac, c->dg_vert, c->n_vert, c->dim, c->n_param, b->active + b->active_off[i],
+                                          b->stream)) != cudaSuccess)
+                return bail(bcuda(b, e, "vertex flags"));
+        }
+    }
     // chunks of up to 64 problems per dimension
     for (int dim = 2; dim <= 3; ++dim) {
         std::vector<int> ids;
@@ -257,6 +272,7 @@ void dwos_batch_destroy(dwos_batch* b) {
     cudaFree(b->rec);
     cudaFree(b->acc);
     cudaFree(b->means);
+    cudaFree(b->active);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
     delete b;
@@ -276,8 +292,8 @@ dwos_status dwos_batch_run(dwos_batch* b) {
         double* acc_g = c->dg_vert ? acc + (size_t)c->n_vert * c->dim : nullptr;
         const dwos_record* rec = b->rec + b->rec_off[i];
         BK(cudaMemsetAsync(acc, 0, nacc * sizeof(double), b->stream), "zero accumulators");
-        BK(launch_scatter(rec, c->elem, c->dim, j.n_query, j.walks_per_point, c->opt.B, 1, j.uref, acc, acc_g, b->stream),
-           "scatter");
+        BK(launch_scatter(rec, c->elem, c->dim, j.n_query, j.walks_per_point, c->opt.B, 1, j.uref, acc, acc_g, b->stream,
+                          nullptr, nullptr, nullptr, b->active + b->active_off[i]), "scatter");
         if (c->n_param > 0) {
             BK(cudaMemsetAsync(j.grad_param, 0, sizeof(double) * c->n_param, b->stream), "zero grad");
             BK(launch_gemv(c->jac, c->dg_vert, acc, acc_g, c->n_vert, c->dim, c->n_param, j.grad_param, b->stream), "gemv");

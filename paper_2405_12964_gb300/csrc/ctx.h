@@ -23,6 +23,8 @@ struct dwos_ctx {
     float* theta = nullptr;      // n_param
     float* g_vert = nullptr;     // n_vert
     float* dg_vert = nullptr;    // n_vert*n_param or null
+    unsigned char* vert_active = nullptr; size_t vert_active_cap = 0;   // vertex has a nonzero Jacobian / dg row
+    bool active_stale = true;    // vert_active must be recomputed (Jacobian or data changed)
     int data_kind = 0;
     double field[10] = {0};
     float sigma = 0.0f, f = 0.0f;

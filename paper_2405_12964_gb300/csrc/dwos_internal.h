@@ -153,10 +153,15 @@ cudaError_t launch_reduce_udot(const dwos_record* rec, const int* elem, const fl
 // mode 0: VJP weights w_p / W;  1: U-statistic L2 weights in batches of B;  2: correlated
 // product (umean = mean u of all W walks);  3: uncorrelated product (umean = mean u of the
 // first W/2 walks, weights on the other W/2).
+// active (optional, one byte per vertex): scatter only into vertices whose flag is set
+// (the others have zero Jacobian and dg rows, so they cannot reach the parameter gradient).
 cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int n_points, int W, int B,
                            int mode, const float* cot_or_uref, double* acc_vert, double* acc_g,
                            cudaStream_t stream, const CvView* cv = nullptr, const double* umean = nullptr,
-                           const float* pweight = nullptr);
+                           const float* pweight = nullptr, const unsigned char* active = nullptr);
+// out[v] = 1 if vertex v has a nonzero entry in its Jacobian rows (dim x n_param) or its dg row.
+cudaError_t launch_vertex_active(const float* jac, const float* dg, int n_vert, int dim, int n_param,
+                                 unsigned char* out, cudaStream_t stream);
 cudaError_t launch_gemv(const float* jac, const float* dg, const double* acc_vert, const double* acc_g,
                         int n_vert, int dim, int n_param, double* grad, cudaStream_t stream);
 // 1/2 sum_p w_p (mean_p - uref_p)^2 with w = pweight (or 1)

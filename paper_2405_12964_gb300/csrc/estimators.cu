@@ -147,20 +147,23 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
 
 constexpr int kProbes = 8;
 
-template <int DIM>
+// G: the data-derivative sums s_v (acc_g) are wanted too (DIM + 1 values per vertex, else DIM).
+template <int DIM, bool G>
 __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restrict__ rec,
                                                       const int* __restrict__ elem, int n_points, int W, int B,
                                                       int mode, const float* __restrict__ cot_or_uref,
                                                       const double* __restrict__ umean,
                                                       const float* __restrict__ pweight,
+                                                      const unsigned char* __restrict__ active,
                                                       long long walks_per_block, double* __restrict__ acc_vert,
                                                       double* __restrict__ acc_g, CvView cv) {
+    constexpr int NV = G ? DIM + 1 : DIM;
     __shared__ int keys[kSlots];
-    __shared__ double vals[kSlots][DIM + 1];
+    __shared__ double vals[kSlots][NV];
     for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
         keys[i] = -1;
 #pragma unroll
-        for (int k = 0; k <= DIM; ++k) vals[i][k] = 0.0;
+        for (int k = 0; k < NV; ++k) vals[i][k] = 0.0;
     }
     __syncthreads();
     const long long total = (long long)n_points * W;
@@ -200,22 +203,24 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
         const int lane = threadIdx.x & 31;
 #pragma unroll
         for (int sidx = 0; sidx < DIM; ++sidx) {
-            const int vid = hit ? __ldg(elem + DIM * r.elem + sidx) : -1;
-            const double ws = hit ? wt * (double)wv[sidx] : 0.0;
-            double val[DIM + 1];
+            int vid = hit ? __ldg(elem + DIM * r.elem + sidx) : -1;
+            if (active && vid >= 0 && !__ldg(active + vid)) vid = -1;   // cannot reach the gradient
+            if (!__any_sync(kFull, vid >= 0)) continue;
+            const double ws = vid >= 0 ? wt * (double)wv[sidx] : 0.0;
+            double val[NV];
 #pragma unroll
             for (int k = 0; k < DIM; ++k) val[k] = ws * (double)r.c[k];
-            val[DIM] = ws;
+            if (G) val[NV - 1] = ws;
             // sum over the lanes that hold the same vertex: a log-step tree over
             // each peer group (lane of rank j adds the partial sum of rank j + off)
             const unsigned peers = __match_any_sync(kFull, vid);
-            if (__any_sync(kFull, __popc(peers) > 1)) {
+            if (__any_sync(kFull, vid >= 0 && __popc(peers) > 1)) {
                 const int rank = __popc(peers & ((1u << lane) - 1u));
                 for (int off = 1; off < 32; off <<= 1) {
                     const int src = nth_set_bit(peers, rank + off);
                     const bool has = src >= 0;
 #pragma unroll
-                    for (int k = 0; k <= DIM; ++k) {
+                    for (int k = 0; k < NV; ++k) {
                         const double t = __shfl_sync(kFull, val[k], has ? src : lane);
                         if (has) val[k] += t;
                     }
@@ -229,14 +234,14 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
                 const int prev = atomicCAS(&keys[slot], -1, vid);
                 if (prev == -1 || prev == vid) {
 #pragma unroll
-                    for (int k = 0; k <= DIM; ++k) atomicAdd(&vals[slot][k], val[k]);
+                    for (int k = 0; k < NV; ++k) atomicAdd(&vals[slot][k], val[k]);
                     done = true;
                 }
             }
             if (!done) {
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) atomicAdd(acc_vert + (size_t)vid * DIM + k, val[k]);
-                if (acc_g) atomicAdd(acc_g + vid, val[DIM]);
+                if (G) atomicAdd(acc_g + vid, val[NV - 1]);
             }
         }
     }
@@ -246,8 +251,24 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
         if (vid < 0) continue;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) atomicAdd(acc_vert + (size_t)vid * DIM + k, vals[i][k]);
-        if (acc_g) atomicAdd(acc_g + vid, vals[i][DIM]);
+        if (G) atomicAdd(acc_g + vid, vals[i][NV - 1]);
     }
+}
+
+__global__ void vertex_active_kernel(const float* __restrict__ jac, const float* __restrict__ dg, int n_vert,
+                                     int dim, int n_param, unsigned char* __restrict__ out) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= n_vert) return;
+    bool any = false;
+    if (jac) {
+        const float* row = jac + (size_t)v * dim * n_param;
+        for (int i = 0; i < dim * n_param && !any; ++i) any = row[i] != 0.0f;
+    }
+    if (dg) {
+        const float* row = dg + (size_t)v * n_param;
+        for (int i = 0; i < n_param && !any; ++i) any = row[i] != 0.0f;
+    }
+    out[v] = any ? 1 : 0;
 }
 
 // grad[j] += sum over rows r (= vertex*dim + k) of J[r][j] a[r], plus sum_v dg[v][j] s[v].
@@ -330,9 +351,18 @@ cudaError_t launch_reduce_udot(const dwos_record* rec, const int* elem, const fl
     return cudaGetLastError();
 }
 
+cudaError_t launch_vertex_active(const float* jac, const float* dg, int n_vert, int dim, int n_param,
+                                 unsigned char* out, cudaStream_t s) {
+    if (n_vert <= 0) return cudaSuccess;
+    vertex_active_kernel<<<(n_vert + 255) / 256, 256, 0, s>>>(n_param > 0 ? jac : nullptr, n_param > 0 ? dg : nullptr,
+                                                              n_vert, dim, n_param, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int n_points, int W, int B, int mode,
                            const float* cot_or_uref, double* acc_vert, double* acc_g, cudaStream_t s,
-                           const CvView* cv, const double* umean, const float* pweight) {
+                           const CvView* cv, const double* umean, const float* pweight,
+                           const unsigned char* active) {
     const CvView none{nullptr, nullptr, nullptr, dim, nullptr};
     const CvView c = cv ? *cv : none;
     const long long total = (long long)n_points * W;
@@ -343,8 +373,12 @@ cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int
     per = ((per + bs - 1) / bs) * bs;
     if (per < bs) per = bs;
     const long long blocks = (total + per - 1) / per;
-    if (dim == 2) scatter_kernel<2><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, umean, pweight, per, acc_vert, acc_g, c);
-    else scatter_kernel<3><<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, umean, pweight, per, acc_vert, acc_g, c);
+    auto go = [&](auto kernel) {
+        kernel<<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, umean, pweight, active,
+                                              per, acc_vert, acc_g, c);
+    };
+    if (dim == 2) { if (acc_g) go(scatter_kernel<2, true>); else go(scatter_kernel<2, false>); }
+    else { if (acc_g) go(scatter_kernel<3, true>); else go(scatter_kernel<3, false>); }
     return cudaGetLastError();
 }
 
