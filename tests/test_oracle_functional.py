@@ -91,3 +91,97 @@ def test_estimator_mean_matches_the_closed_form():
     tot = np.array(est_g) + gb
     se = tot.std(ddof=1) / np.sqrt(len(tot))
     assert abs(tot.mean() - want) < 4.5 * se + 0.06 * abs(want - gb), (tot.mean(), want, se)
+
+
+# ---- boundary loss of the general functional (App. C) ----------------------
+
+def _perturbed(pr, sc, delta):
+    """The oracle problem at theta = delta (vertices v + J delta, data g + dg delta)."""
+    v = np.asarray(sc.vert, dtype=np.float64) + np.einsum("vkp,p->vk", np.asarray(sc.jac, dtype=np.float64), delta)
+    g = np.asarray(sc.g_vert, dtype=np.float64)
+    if sc.dg_vert is not None:
+        g = g + np.asarray(sc.dg_vert, dtype=np.float64) @ delta
+    return to_oracle(sc, vert=v, g_vert=g)
+
+
+def test_boundary_loss_on_the_polygon():
+    # g = 1 on a regular 128-gon of radius R: J_b = 1/2 perimeter = 128 R sin(pi/128), linear in R;
+    # the Fourier modes change the perimeter only at second order
+    sc = scenes.disk_scene("screened_1", n_query=4)
+    pr = to_oracle(sc)
+    n = len(sc.elem)
+    loss, g = fn.boundary_loss_l2(pr, [-2, -2], [2, 2])
+    assert abs(loss - n * np.sin(np.pi / n)) < 1e-12
+    assert abs(g[0] - n * np.sin(np.pi / n)) < 1e-12
+    assert np.all(np.abs(g[1:]) < 1e-12)
+    # a target equal to the data gives zero; a mask box around no element gives zero
+    ub = np.asarray(sc.g_vert, dtype=np.float64)
+    l0, g0 = fn.boundary_loss_l2(pr, [-2, -2], [2, 2], ub)
+    assert l0 == 0.0 and np.all(g0 == 0.0)
+    lm, gm = fn.boundary_loss_l2(pr, [-0.5, -0.5], [0.5, 0.5])
+    assert lm == 0.0 and np.all(gm == 0.0)
+    # the right half-plane box keeps the elements whose centres have x >= 0: half of them
+    lh, _ = fn.boundary_loss_l2(pr, [0.0, -2], [2, 2])
+    assert abs(lh - 0.5 * loss) < 1e-12
+
+
+def test_boundary_loss_on_the_sphere():
+    # unperturbed SH sphere (radius 1) with g = 1, target 0, mask around the sphere only:
+    # J_b = A / 2 with A the mesh's area; the l = 0 coefficient moves every sphere vertex by
+    # Y00 along its radius, and A scales as R^2, so dJ_b/dc00 = A Y00
+    sc = scenes.sh_sphere_scene(freq=6, n_query=4, coeffs=np.zeros(81))
+    pr = to_oracle(sc)
+    loss, g = fn.boundary_loss_l2(pr, [-1.5] * 3, [1.5] * 3)
+    vert, elem = np.asarray(sc.vert, dtype=np.float64), np.asarray(sc.elem)
+    sph = np.all(np.abs(vert[elem].mean(axis=1)) <= 1.5, axis=1)
+    tri = vert[elem[sph]]
+    area = 0.5 * np.linalg.norm(np.cross(tri[:, 1] - tri[:, 0], tri[:, 2] - tri[:, 0]), axis=1).sum()
+    y00 = 0.5 / np.sqrt(np.pi)
+    assert abs(loss - 0.5 * area) < 1e-12 * area
+    assert abs(g[0] - area * y00) < 1e-10 * area
+
+
+def test_boundary_loss_gradient_matches_central_differences():
+    # a small star in its box, random per-vertex data with a data derivative, a random target
+    # and a mask that cuts through both the star and the box: the gradient equals central
+    # differences of the value (a separate formula: no derivative code involved)
+    rng = np.random.default_rng(5)
+    sc = scenes.star_box_scene(n_seg=96, n_query=4)
+    nv, N = len(sc.vert), sc.jac.shape[2]
+    sc.g_vert = rng.uniform(0.0, 1.0, nv)
+    sc.dg_vert = rng.normal(0.0, 0.3, (nv, N))
+    ub = rng.uniform(0.0, 1.0, nv)
+    lo, hi = [-0.9, -1.2], [1.2, 0.25]
+    pr = _perturbed(None, sc, np.zeros(N))
+    loss, g = fn.boundary_loss_l2(pr, lo, hi, ub)
+    assert abs(loss - fn.boundary_loss_l2_value(pr, lo, hi, ub)) < 1e-14
+    h = 1e-6
+    fd = np.zeros(N)
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = h
+        fd[j] = (fn.boundary_loss_l2_value(_perturbed(None, sc, e), lo, hi, ub)
+                 - fn.boundary_loss_l2_value(_perturbed(None, sc, -e), lo, hi, ub)) / (2 * h)
+    assert np.abs(g).max() > 1e-3
+    assert np.allclose(g, fd, rtol=1e-6, atol=1e-8 * np.abs(g).max())
+
+
+def test_boundary_loss_gradient_matches_central_differences_3d():
+    rng = np.random.default_rng(6)
+    sc = scenes.sh_sphere_scene(freq=4, lmax=3, n_query=4)
+    nv, N = len(sc.vert), sc.jac.shape[2]
+    sc.g_vert = rng.uniform(0.0, 1.0, nv)
+    sc.dg_vert = rng.normal(0.0, 0.3, (nv, N))
+    ub = rng.uniform(0.0, 1.0, nv)
+    lo, hi = [-2.5, -0.3, -2.5], [0.4, 2.5, 2.5]
+    pr = _perturbed(None, sc, np.zeros(N))
+    loss, g = fn.boundary_loss_l2(pr, lo, hi, ub)
+    h = 1e-6
+    fd = np.zeros(N)
+    for j in range(N):
+        e = np.zeros(N)
+        e[j] = h
+        fd[j] = (fn.boundary_loss_l2_value(_perturbed(None, sc, e), lo, hi, ub)
+                 - fn.boundary_loss_l2_value(_perturbed(None, sc, -e), lo, hi, ub)) / (2 * h)
+    assert np.abs(g).max() > 1e-3
+    assert np.allclose(g, fd, rtol=1e-6, atol=1e-8 * np.abs(g).max())
