@@ -304,6 +304,24 @@ dwos_status dwos_grad_l2_weighted(dwos_ctx* ctx, int n_query, const float* xq, c
 dwos_status dwos_boundary_term_l2(dwos_ctx* ctx, const float* box_lo, const float* box_hi, const float* uref_vert,
                                   double* grad_param, int mem);
 
+/* ---- boundary loss of the general shape functional ------------------------
+ * App. C, Eq. general_functional: J_b(theta) = int_Gamma m(y) l_b(u(y)) dA
+ * with l_b(u) = 1/2 (u - ub)^2, m the indicator of an axis-aligned box (taken
+ * at each element's centre and held fixed) and ub_vert the target per vertex
+ * (n_vert values, host or device by mem, or NULL for 0).  On a Dirichlet
+ * boundary u = g, and the du/dn terms of Eq. general_functional_deriv cancel
+ * against udot = gdot - V_n du/dn (Eq. bvp_deriv), so no walk is needed: the
+ * call returns J_b and its exact derivative for mapped vertex data g, linear
+ * on each element, through the element measures (the discrete mean-curvature
+ * term; vertices move by the Jacobian given to dwos_set_boundary) and through
+ * dg/dtheta (dwos_set_dirichlet_mapped).  loss receives 1 value and
+ * grad_param n_param values (host or device by mem).  Field data:
+ * DWOS_ERR_NOT_IMPLEMENTED.  Synchronises.  With dwos_sample_domain,
+ * dwos_grad_l2_weighted and dwos_boundary_term_l2 this gives the derivative
+ * of the whole general functional. */
+dwos_status dwos_boundary_loss_l2(dwos_ctx* ctx, const float* box_lo, const float* box_hi, const float* ub_vert,
+                                  double* loss, double* grad_param, int mem);
+
 /* The current vertex positions (n_vert x dim floats: reference + J theta),
  * host or device by mem.  Synchronises for host memory. */
 dwos_status dwos_get_vertices(const dwos_ctx* ctx, float* vert, int mem);

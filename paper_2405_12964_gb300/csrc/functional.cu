@@ -142,6 +142,84 @@ __global__ void boundary_term_kernel(const float* vert, const int* elem, int n_e
         for (int k = 0; k < DIM; ++k) atomicAdd(acc + (size_t)DIM * ev[a] + k, sgn * wsum[a] * n[k]);
 }
 
+// Boundary loss of the general shape functional (App. C), for mapped vertex data:
+//     J_b = sum_e m_e int_e 1/2 (g - ub)^2 dA,
+// m_e the box indicator at the element's centre.  On a Dirichlet boundary the
+// du/dn terms of Eq. (general_functional_deriv) cancel (udot = gdot - V_n du/dn
+// there, Eq. bvp_deriv), so its derivative is that of this sum: the element
+// measure's gradient (the discrete form of the mean-curvature term) times the
+// element's mean of 1/2 (g - ub)^2, plus |e| int w_a (g - ub) dg_a/dtheta.  Per
+// element, exactly (g and ub linear, so the mean is a quadratic form with the
+// weights (1 + delta_ab) / (n (n + 1)), n = DIM vertices):
+//     acc_vert[a] += m_e Q_e d|e|/dv_a,   acc_g[a] += m_e |e| sum_b d_b (1 + delta_ab) / (n (n + 1)),
+//     loss += m_e |e| Q_e,                Q_e = 1/2 sum_ab d_a d_b (1 + delta_ab) / (n (n + 1)).
+template <int DIM>
+__global__ void boundary_loss_kernel(const float* vert, const int* elem, int n_elem, const float* g_vert,
+                                     const float* ub_vert, Box box, double* acc_vert, double* acc_g,
+                                     double* loss) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    double part = 0.0;
+    if (e < n_elem) {
+        const int* ev = elem + DIM * e;
+        double v[3][3] = {{0}};
+        for (int a = 0; a < DIM; ++a)
+            for (int k = 0; k < DIM; ++k) v[a][k] = vert[DIM * ev[a] + k];
+        bool in_box = true;
+        for (int k = 0; k < DIM; ++k) {
+            float c = 0.0f;
+            for (int a = 0; a < DIM; ++a) c += vert[DIM * ev[a] + k] / DIM;
+            in_box = in_box && c >= box.lo[k] && c <= box.hi[k];
+        }
+        double meas = 0.0, dm[3][3] = {{0}};
+        if (DIM == 2) {
+            const double tx = v[1][0] - v[0][0], ty = v[1][1] - v[0][1];
+            meas = sqrt(tx * tx + ty * ty);
+            if (meas > 0.0) {
+                dm[0][0] = -tx / meas; dm[0][1] = -ty / meas;
+                dm[1][0] = tx / meas;  dm[1][1] = ty / meas;
+            }
+        } else {
+            const double e1[3] = {v[1][0] - v[0][0], v[1][1] - v[0][1], v[1][2] - v[0][2]};
+            const double e2[3] = {v[2][0] - v[0][0], v[2][1] - v[0][1], v[2][2] - v[0][2]};
+            const double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+            const double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+            meas = 0.5 * nn;
+            if (nn > 0.0) {
+                const double h[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+                // dA/dv_a = 1/2 nhat x (v_{a+2} - v_{a+1}), a cyclic
+                for (int a = 0; a < 3; ++a) {
+                    const double* p = v[(a + 1) % 3];
+                    const double* q = v[(a + 2) % 3];
+                    const double r[3] = {q[0] - p[0], q[1] - p[1], q[2] - p[2]};
+                    dm[a][0] = 0.5 * (h[1] * r[2] - h[2] * r[1]);
+                    dm[a][1] = 0.5 * (h[2] * r[0] - h[0] * r[2]);
+                    dm[a][2] = 0.5 * (h[0] * r[1] - h[1] * r[0]);
+                }
+            }
+        }
+        if (in_box && meas > 0.0) {
+            double d[3] = {0, 0, 0};
+            for (int a = 0; a < DIM; ++a) d[a] = (double)g_vert[ev[a]] - (ub_vert ? (double)ub_vert[ev[a]] : 0.0);
+            const double wn = 1.0 / (DIM * (DIM + 1));
+            double q = 0.0, wa[3] = {0, 0, 0};
+            for (int a = 0; a < DIM; ++a)
+                for (int b = 0; b < DIM; ++b) {
+                    const double c = (a == b ? 2.0 : 1.0) * wn;
+                    q += 0.5 * d[a] * d[b] * c;
+                    wa[a] += d[b] * c;
+                }
+            part = meas * q;
+            for (int a = 0; a < DIM; ++a) {
+                for (int k = 0; k < DIM; ++k) atomicAdd(acc_vert + (size_t)DIM * ev[a] + k, q * dm[a][k]);
+                if (acc_g) atomicAdd(acc_g + ev[a], meas * wa[a]);
+            }
+        }
+    }
+    // the loss: one FP64 atomic per warp
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0 && part != 0.0) atomicAdd(loss, part);
+}
+
 dwos_status ffail(dwos_ctx* c, dwos_status s, const std::string& m) {
     c->err = m;
     return s;
@@ -267,6 +345,55 @@ dwos_status dwos_boundary_term_l2(dwos_ctx* ctx, const float* box_lo, const floa
     cleanup();
     FK(e, "boundary term");
     ctx->launches += 4;
+    return DWOS_OK;
+}
+
+dwos_status dwos_boundary_loss_l2(dwos_ctx* ctx, const float* box_lo, const float* box_hi, const float* ub_vert,
+                                  double* loss, double* grad_param, int mem) {
+    if (!ctx) return DWOS_ERR_INVALID_ARG;
+    if (!ctx->have_boundary) return ffail(ctx, DWOS_ERR_STATE, "no boundary: call dwos_set_boundary first");
+    if (!box_ok(ctx, box_lo, box_hi) || !loss || (ctx->n_param > 0 && !grad_param) ||
+        (mem != DWOS_MEM_HOST && mem != DWOS_MEM_DEVICE))
+        return ffail(ctx, DWOS_ERR_INVALID_ARG, "bad arguments");
+    if (ctx->data_kind != 0)
+        return ffail(ctx, DWOS_ERR_NOT_IMPLEMENTED, "the boundary loss is implemented for mapped (per-vertex) data");
+    FK(cudaSetDevice(ctx->device), "cudaSetDevice");
+    const int dim = ctx->dim, ne = ctx->n_elem, nv = ctx->n_vert, N = ctx->n_param;
+    const cudaMemcpyKind out_kind = mem == DWOS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    cudaStream_t s = ctx->stream;
+    Box box{};
+    for (int k = 0; k < dim; ++k) { box.lo[k] = box_lo[k]; box.hi[k] = box_hi[k]; }
+    float* ub = nullptr;
+    double* acc = nullptr;       // n_vert * dim position sums, then n_vert data sums, then the loss
+    double* grad = nullptr;
+    auto cleanup = [&]() { cudaFree(ub); cudaFree(acc); cudaFree(grad); };
+    const size_t nacc = (size_t)nv * dim + nv + 1;
+    cudaError_t e = cudaMalloc(&acc, sizeof(double) * nacc);
+    if (e == cudaSuccess) e = cudaMalloc(&grad, sizeof(double) * (size_t)(N > 0 ? N : 1));
+    if (e == cudaSuccess && ub_vert) {
+        e = cudaMalloc(&ub, sizeof(float) * (size_t)nv);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(ub, ub_vert, sizeof(float) * nv,
+                                mem == DWOS_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, sizeof(double) * nacc, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(grad, 0, sizeof(double) * (size_t)(N > 0 ? N : 1), s);
+    double* acc_g = ctx->dg_vert ? acc + (size_t)nv * dim : nullptr;
+    double* d_loss = acc + (size_t)nv * dim + nv;
+    if (e == cudaSuccess) {
+        if (dim == 2)
+            boundary_loss_kernel<2><<<nblk(ne, 256), 256, 0, s>>>(ctx->vert, ctx->elem, ne, ctx->g_vert, ub, box, acc, acc_g, d_loss);
+        else
+            boundary_loss_kernel<3><<<nblk(ne, 256), 256, 0, s>>>(ctx->vert, ctx->elem, ne, ctx->g_vert, ub, box, acc, acc_g, d_loss);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && N > 0) e = launch_gemv(ctx->jac, ctx->dg_vert, acc, acc_g, nv, dim, N, grad, s);
+    if (e == cudaSuccess && N > 0) e = cudaMemcpyAsync(grad_param, grad, sizeof(double) * N, out_kind, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(loss, d_loss, sizeof(double), out_kind, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    FK(e, "boundary loss");
+    ctx->launches += N > 0 ? 2 : 1;
     return DWOS_OK;
 }
 

@@ -106,6 +106,7 @@ _SIGS = {
     "dwos_sample_domain": [_vp, _i, _vp, _vp, _u64, _vp, _vp, _vp],
     "dwos_grad_l2_weighted": [_vp, _i, _vp, _vp, _vp, _i, _u64, _vp, _vp, _vp, _i],
     "dwos_boundary_term_l2": [_vp, _vp, _vp, _vp, _vp, _i],
+    "dwos_boundary_loss_l2": [_vp, _vp, _vp, _vp, _vp, _vp, _i],
     "dwos_get_vertices": [_vp, _vp, _i],
 }
 MLP_NPARAM = 14088
@@ -355,6 +356,26 @@ class Solver:
         g = torch.empty(max(self.n_param, 1), device=self.device, dtype=torch.float64)
         self._check(lib().dwos_boundary_term_l2(self._h, lo, hi, _ptr(ur), _ptr(g), MEM_DEVICE))
         return g[:self.n_param].cpu().numpy()
+
+    def boundary_loss_l2(self, box_lo, box_hi, ub_vert=None):
+        """dwos_boundary_loss_l2: (J_b, dJ_b/dtheta) of int_Gamma m 1/2 (g - ub)^2 dA (numpy)."""
+        self._stream()
+        lo = (ctypes.c_float * 3)(*[float(v) for v in box_lo])
+        hi = (ctypes.c_float * 3)(*[float(v) for v in box_hi])
+        ub = None if ub_vert is None else self._dev(ub_vert, torch.float32)
+        loss = torch.empty(1, device=self.device, dtype=torch.float64)
+        g = torch.empty(max(self.n_param, 1), device=self.device, dtype=torch.float64)
+        self._check(lib().dwos_boundary_loss_l2(self._h, lo, hi, _ptr(ub), _ptr(loss), _ptr(g), MEM_DEVICE))
+        return float(loss.cpu()[0]), g[:self.n_param].cpu().numpy()
+
+    def general_functional_gradient(self, box_lo, box_hi, uref_fn, walks: int, n_try: int, bbox_lo, bbox_hi,
+                                    ub_vert=None, seed: int = 0, walk_id_base: int = 0):
+        """Eq. (general_functional_deriv): the volume part of functional_gradient (mask box
+        box_lo / box_hi, target uref_fn) plus the boundary loss int_Gamma m 1/2 (g - ub)^2 dA
+        with m the box bbox_lo / bbox_hi and ub per vertex.  Returns (J estimate, dJ/dtheta)."""
+        jv, gv = self.functional_gradient(box_lo, box_hi, uref_fn, walks, n_try, seed, walk_id_base)
+        jb, gb = self.boundary_loss_l2(bbox_lo, bbox_hi, ub_vert)
+        return jv + jb, gv + gb
 
     def functional_gradient(self, box_lo, box_hi, uref_fn, walks: int, n_try: int, seed: int = 0,
                             walk_id_base: int = 0):

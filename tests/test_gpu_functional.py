@@ -115,3 +115,67 @@ def test_functional_gradient_matches_the_closed_form(Solver):
     # boundary part pi (exact); the domain part carries the eps/h bias of the du/dn estimate
     # (Sec. 5.3; 4.4 % low at eps/h = 0.1 in the oracle): budget 6 % of it
     assert abs(vals.mean() - want) < 4.5 * se + 0.06 * abs(want - np.pi)
+
+
+def _f32(a):
+    return None if a is None else np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("which", ["star", "sphere"])
+def test_boundary_loss_matches_oracle(Solver, which):
+    # App. C's boundary loss, exact on both sides: the GPU (FP64 from the FP32 inputs) against
+    # the oracle on the same FP32-rounded vertices, Jacobian, data, data derivative and target
+    rng = np.random.default_rng(11)
+    if which == "star":
+        sc, lo, hi = scenes.star_box_scene(n_seg=1024, n_query=4), [-0.83, -1.31], [1.27, 0.217]
+    else:
+        sc, lo, hi = scenes.sh_sphere_scene(freq=12, lmax=4, n_query=4), [-2.5, -0.31, -2.5], [0.43, 2.5, 2.5]
+    nv, N = len(sc.vert), sc.jac.shape[2]
+    sc.g_vert = rng.uniform(0.0, 1.0, nv)
+    sc.dg_vert = rng.normal(0.0, 0.3, (nv, N))
+    ub = rng.uniform(0.0, 1.0, nv).astype(np.float32)
+    s = Solver(0)
+    s.load_scene(sc)
+    loss, g = s.boundary_loss_l2(lo, hi, ub)
+    pr = to_oracle(sc, vert=_f32(sc.vert), jac=_f32(sc.jac), g_vert=_f32(sc.g_vert), dg_vert=_f32(sc.dg_vert))
+    want_loss, want_g = fn.boundary_loss_l2(pr, lo, hi, ub.astype(np.float64))
+    assert want_loss > 0 and np.abs(want_g).max() > 0
+    assert abs(loss - want_loss) <= 1e-9 * want_loss
+    assert np.allclose(g, want_g, rtol=1e-8, atol=1e-10 * np.abs(want_g).max())
+    # without a target and without a data derivative
+    s.set_dirichlet_mapped(sc.g_vert)
+    loss0, g0 = s.boundary_loss_l2(lo, hi)
+    pr0 = to_oracle(sc, vert=_f32(sc.vert), jac=_f32(sc.jac), g_vert=_f32(sc.g_vert), dg_vert=None)
+    wl0, wg0 = fn.boundary_loss_l2(pr0, lo, hi)
+    assert abs(loss0 - wl0) <= 1e-9 * wl0
+    assert np.allclose(g0, wg0, rtol=1e-8, atol=1e-10 * np.abs(wg0).max())
+
+
+def test_boundary_loss_rejects_field_data_and_bad_boxes(Solver):
+    from paper_2405_12964_gb300.dwos import DwosError
+    sc = scenes.disk_scene("laplace_x", n_query=4)
+    s = Solver(0)
+    s.load_scene(sc)
+    with pytest.raises(DwosError, match="NOT_IMPLEMENTED|mapped"):
+        s.boundary_loss_l2([-2, -2], [2, 2])
+    sc = scenes.disk_scene("screened_1", n_query=4)
+    s.load_scene(sc)
+    with pytest.raises(DwosError, match="INVALID_ARG|bad arguments"):
+        s.boundary_loss_l2([1, -2], [-1, 2])
+
+
+def test_general_functional_gradient_is_the_sum_of_its_parts(Solver):
+    sc = scenes.disk_scene("screened_1", n_query=4)
+    s = Solver(0)
+    s.load_scene(sc)
+    uref = lambda p: 0.2 * p[:, 0]
+    ub = np.full(len(sc.vert), 0.25, np.float32)
+    j, g = s.general_functional_gradient([-1, -1], [1, 1], uref, 64, 2000, [-2, -2], [2, 2], ub, seed=3)
+    jv, gv = s.functional_gradient([-1, -1], [1, 1], uref, 64, 2000, seed=3)
+    jb, gb = s.boundary_loss_l2([-2, -2], [2, 2], ub)
+    assert abs(j - (jv + jb)) <= 1e-12 * abs(j)
+    assert np.allclose(g, gv + gb, rtol=1e-12, atol=1e-15)
+    # g = 1, ub = 1/4 on the 128-gon: J_b = 1/2 (3/4)^2 perimeter, dJ_b/dR = J_b
+    n = len(sc.elem)
+    assert abs(jb - 0.5 * 0.75 ** 2 * 2 * n * np.sin(np.pi / n)) < 1e-6 * jb
+    assert abs(gb[0] - jb) < 1e-6 * jb
