@@ -132,18 +132,26 @@ __device__ __forceinline__ float source_weight(float k, float d, float u) {
 // projection, so the squared distance is stationary in the weights there and
 // their ulp-level errors only reach d^2 at second order.
 // ---------------------------------------------------------------------------
+// Every product is rounded explicitly (fmaf, __fmul_rn), so that the compiler
+// cannot contract the expressions differently where it inlines them: a leaf's
+// distance is then the same bits in every search path, and ties between
+// elements (a shared vertex) resolve the same way whichever path found them.
 __device__ __forceinline__ float seg_closest(const float* q, float ax, float ay, float bx, float by,
                                              float& t_out) {
     const float ex = bx - ax, ey = by - ay;
     const float px = q[0] - ax, py = q[1] - ay;
-    const float len2 = ex * ex + ey * ey;
+    const float len2 = fmaf(ex, ex, __fmul_rn(ey, ey));
     // fast division: the distance is quadratic in t at its minimum, so an
     // ulp-level error in t does not move d^2 beyond rounding
-    float t = len2 > 0.0f ? __fdividef(px * ex + py * ey, len2) : 0.0f;
+    float t = len2 > 0.0f ? __fdividef(fmaf(px, ex, __fmul_rn(py, ey)), len2) : 0.0f;
     t = fminf(fmaxf(t, 0.0f), 1.0f);
-    const float dx = px - t * ex, dy = py - t * ey;
+    const float dx = fmaf(-t, ex, px), dy = fmaf(-t, ey, py);
     t_out = t;
-    return dx * dx + dy * dy;
+    return fmaf(dx, dx, __fmul_rn(dy, dy));
+}
+
+__device__ __forceinline__ float dot3_rn(float ax, float ay, float az, float bx, float by, float bz) {
+    return fmaf(ax, bx, fmaf(ay, by, __fmul_rn(az, bz)));
 }
 
 __device__ __forceinline__ float tri_closest(const float* q, const float3 a, const float3 b, const float3 c,
@@ -151,17 +159,17 @@ __device__ __forceinline__ float tri_closest(const float* q, const float3 a, con
     const float3 ab = make_float3(b.x - a.x, b.y - a.y, b.z - a.z);
     const float3 ac = make_float3(c.x - a.x, c.y - a.y, c.z - a.z);
     const float3 ap = make_float3(q[0] - a.x, q[1] - a.y, q[2] - a.z);
-    const float d1 = ab.x * ap.x + ab.y * ap.y + ab.z * ap.z;
-    const float d2 = ac.x * ap.x + ac.y * ap.y + ac.z * ap.z;
+    const float d1 = dot3_rn(ab.x, ab.y, ab.z, ap.x, ap.y, ap.z);
+    const float d2 = dot3_rn(ac.x, ac.y, ac.z, ap.x, ap.y, ap.z);
     const float3 bp = make_float3(q[0] - b.x, q[1] - b.y, q[2] - b.z);
-    const float d3 = ab.x * bp.x + ab.y * bp.y + ab.z * bp.z;
-    const float d4 = ac.x * bp.x + ac.y * bp.y + ac.z * bp.z;
+    const float d3 = dot3_rn(ab.x, ab.y, ab.z, bp.x, bp.y, bp.z);
+    const float d4 = dot3_rn(ac.x, ac.y, ac.z, bp.x, bp.y, bp.z);
     const float3 cp = make_float3(q[0] - c.x, q[1] - c.y, q[2] - c.z);
-    const float d5 = ab.x * cp.x + ab.y * cp.y + ab.z * cp.z;
-    const float d6 = ac.x * cp.x + ac.y * cp.y + ac.z * cp.z;
-    const float vc = d1 * d4 - d3 * d2;
-    const float vb = d5 * d2 - d1 * d6;
-    const float va = d3 * d6 - d5 * d4;
+    const float d5 = dot3_rn(ab.x, ab.y, ab.z, cp.x, cp.y, cp.z);
+    const float d6 = dot3_rn(ac.x, ac.y, ac.z, cp.x, cp.y, cp.z);
+    const float vc = fmaf(d1, d4, -__fmul_rn(d3, d2));
+    const float vb = fmaf(d5, d2, -__fmul_rn(d1, d6));
+    const float va = fmaf(d3, d6, -__fmul_rn(d5, d4));
     float s, t;
     if (d1 <= 0.0f && d2 <= 0.0f) { s = 0.0f; t = 0.0f; }                          // vertex a
     else if (d3 >= 0.0f && d4 <= d3) { s = 1.0f; t = 0.0f; }                        // vertex b
@@ -173,14 +181,14 @@ __device__ __forceinline__ float tri_closest(const float* q, const float3 a, con
         s = 1.0f - u; t = u;
     } else {                                                                          // face
         const float inv = __fdividef(1.0f, va + vb + vc);
-        s = vb * inv; t = vc * inv;
+        s = __fmul_rn(vb, inv); t = __fmul_rn(vc, inv);
     }
-    const float rx = ap.x - s * ab.x - t * ac.x;
-    const float ry = ap.y - s * ab.y - t * ac.y;
-    const float rz = ap.z - s * ab.z - t * ac.z;
+    const float rx = fmaf(-t, ac.x, fmaf(-s, ab.x, ap.x));
+    const float ry = fmaf(-t, ac.y, fmaf(-s, ab.y, ap.y));
+    const float rz = fmaf(-t, ac.z, fmaf(-s, ab.z, ap.z));
     w1 = s;
     w2 = t;
-    return rx * rx + ry * ry + rz * rz;
+    return dot3_rn(rx, ry, rz, rx, ry, rz);
 }
 
 // ---------------------------------------------------------------------------
@@ -283,6 +291,21 @@ __device__ __forceinline__ float prim_box_dist2(const float4* __restrict__ prims
     return box_dist2<DIM>(q, lo, hi);
 }
 
+// Ties between equally distant leaves (a query whose closest point is a vertex
+// shared by two elements) go to the lower leaf index, and a box exactly at the
+// bound is still searched, so that every search order, seed and schedule picks
+// the same element.
+__device__ __forceinline__ bool closer(float d, int p, float best2, int best) {
+    return d < best2 || (d == best2 && d < kInf && (unsigned)p < (unsigned)best);
+}
+
+// A box is searched while its squared distance is within the bound up to a
+// relative 1e-5: the computed distance of a box can round above the computed
+// distance of an element inside it, and a tied element must not be pruned.
+__device__ __forceinline__ bool within(float box_d2, float best2) {
+    return box_d2 <= best2 * 1.00001f;
+}
+
 // Top-down search of the subtree under internal node `start` for a leaf
 // closer than best2: near-child-first descent; on the way back up each parent
 // is refetched and its children re-ordered by the same box distances, so no
@@ -308,14 +331,14 @@ __device__ __forceinline__ bool search_subtree(const BvhView& bvh, int start, co
         int next = kFromParent;
         for (;;) {
             int cand = kFromParent;
-            if (state == 0) { if (dn < best2) cand = nearc; else state = 2; }
-            if (state == 1) { if (df < best2) cand = farc; }
+            if (state == 0) { if (within(dn, best2)) cand = nearc; else state = 2; }
+            if (state == 1) { if (within(df, best2)) cand = farc; }
             if (cand == kFromParent) break;
             if (cand < 0) {                       // leaf: test in place
                 const int p = ~cand;
                 ++n_prims;
                 const float dd = prim_dist2<DIM>(bvh.prims, p, q);
-                if (dd < best2) { best2 = dd; best = p; }
+                if (closer(dd, p, best2, best)) { best2 = dd; best = p; }
                 state = (state == 0) ? 1 : 2;
                 continue;
             }
@@ -342,10 +365,10 @@ template <int DIM>
 __device__ __forceinline__ bool closest_leaf(const BvhView& bvh, const float* q, float& best2, int& best,
                                              unsigned& n_nodes, unsigned& n_prims) {
     for (int p = bvh.n_tree; p < bvh.n_tree + bvh.n_big; ++p) {
-        if (prim_box_dist2<DIM>(bvh.prims, p, q) >= best2) continue;   // cannot be closer
+        if (!within(prim_box_dist2<DIM>(bvh.prims, p, q), best2)) continue;   // cannot be closer
         ++n_prims;
         const float dd = prim_dist2<DIM>(bvh.prims, p, q);
-        if (dd < best2) { best2 = dd; best = p; }
+        if (closer(dd, p, best2, best)) { best2 = dd; best = p; }
     }
     if (bvh.n_internal == 0) return true;
     int budget = 4 * bvh.n_internal + 64;
@@ -363,11 +386,11 @@ __device__ __forceinline__ bool closest_leaf(const BvhView& bvh, const float* q,
         const int sib = from0 ? c1 : c0;
         if (sib != kEmptyChild) {
             const float ds = from0 ? box_dist2<DIM>(q, lo1, hi1) : box_dist2<DIM>(q, lo0, hi0);
-            if (ds < best2) {
+            if (within(ds, best2)) {
                 if (sib < 0) {
                     ++n_prims;
                     const float dd = prim_dist2<DIM>(bvh.prims, ~sib, q);
-                    if (dd < best2) { best2 = dd; best = ~sib; }
+                    if (closer(dd, ~sib, best2, best)) { best2 = dd; best = ~sib; }
                 } else if (!search_subtree<DIM>(bvh, sib, q, best2, best, budget, n_nodes, n_prims)) {
                     return false;
                 }
@@ -469,7 +492,7 @@ __device__ __forceinline__ int wide_closest(const WideView& mine, unsigned need,
             while (top > 0) {
                 const float2 e = stk[top - 1];
                 --top;
-                if (!(e.x < b2)) continue;                     // pruned by a closer leaf found since
+                if (!within(e.x, b2)) continue;                // pruned by a closer leaf found since
                 if (--budget < 0) { err |= 1; break; }
                 const float* f = wn + (size_t)__float_as_int(e.y) * WideLayout<DIM>::kFloats;
                 float lo[DIM], hi[DIM], vt[DIM * DIM];
@@ -483,7 +506,7 @@ __device__ __forceinline__ int wide_closest(const WideView& mine, unsigned need,
                 for (int k = 0; k < DIM * DIM; ++k) vt[k] = __ldg(f + WideLayout<DIM>::kVtx + k * kWide + lane);
                 const float cd = box_dist2<DIM>(q, lo, hi);
                 if (lane == 0) ++n_nodes;
-                const bool leaf = code < 0 && cd < b2;
+                const bool leaf = code < 0 && within(cd, b2);
                 const unsigned lm = __ballot_sync(kWarpAll, leaf);
                 if (lm) {
                     float dd = kInf;
@@ -504,9 +527,9 @@ __device__ __forceinline__ int wide_closest(const WideView& mine, unsigned need,
                     const unsigned mbits = __reduce_min_sync(kWarpAll, bits);
                     const unsigned pi = __reduce_min_sync(kWarpAll, leaf && bits == mbits ? (unsigned)~code : 0xffffffffu);
                     const float md = __uint_as_float(mbits);
-                    if (md < b2) { b2 = md; bi = (int)pi; }
+                    if (closer(md, (int)pi, b2, bi)) { b2 = md; bi = (int)pi; }
                 }
-                const bool inner = code >= 0 && code != kEmptyChild && cd < b2;
+                const bool inner = code >= 0 && code != kEmptyChild && within(cd, b2);
                 const unsigned im = __ballot_sync(kWarpAll, inner);
                 if (im) {
                     const int cnt = __popc(im);
@@ -529,7 +552,7 @@ __device__ __forceinline__ int wide_closest(const WideView& mine, unsigned need,
         } else if (n_tree == 1) {
             const float dd = prim_dist2<DIM>(prims, 0, q);
             if (lane == 0) ++n_prims;
-            if (dd < b2) { b2 = dd; bi = 0; }
+            if (closer(dd, 0, b2, bi)) { b2 = dd; bi = 0; }
         }
         if (lane == src) { best2 = b2; best = bi; }
     }
@@ -541,10 +564,10 @@ template <int DIM>
 __device__ __forceinline__ void big_closest(const float4* __restrict__ prims, int n_tree, int n_big, const float* q,
                                             float& best2, int& best, unsigned& n_prims) {
     for (int p = n_tree; p < n_tree + n_big; ++p) {
-        if (prim_box_dist2<DIM>(prims, p, q) >= best2) continue;
+        if (!within(prim_box_dist2<DIM>(prims, p, q), best2)) continue;
         ++n_prims;
         const float dd = prim_dist2<DIM>(prims, p, q);
-        if (dd < best2) { best2 = dd; best = p; }
+        if (closer(dd, p, best2, best)) { best2 = dd; best = p; }
     }
 }
 

@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
                         int c0, c1, parent;
                         load_node<DIM>(Pw.nodes, Pw.root, lo0, hi0, lo1, hi1, c0, c1, parent);
                         ++st.nodes;
-                        desc = box_dist2<DIM>(x, lo0, hi0) < best2 || box_dist2<DIM>(x, lo1, hi1) < best2;
+                        desc = within(box_dist2<DIM>(x, lo0, hi0), best2) || within(box_dist2<DIM>(x, lo1, hi1), best2);
                     } else {
                         desc = Pw.n_tree > 0;
                     }

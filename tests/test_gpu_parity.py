@@ -467,3 +467,20 @@ def test_inside_test_is_watertight_on_fine_boundaries(Solver):
     d = rng.normal(size=(4000, 3))
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     assert np.all(s.inside(0.5 * d).cpu().numpy() == 0)
+
+
+def test_walks_do_not_depend_on_search_order_or_schedule(Solver):
+    # walks that end at a vertex shared by two segments tie exactly; the search breaks the tie
+    # the same way in every order (lower leaf index, boxes searched up to a 1e-5 margin over
+    # the bound), so the records are bit-identical across orders and repeated runs
+    sc = scenes.star_box_scene(n_seg=1024, n_query=4)
+    s = Solver(0)
+    s.load_scene(sc, K=2)
+    pts, _ = s.sample_domain(200, [-0.8, -0.8], [0.8, 0.8], seed=5)
+    recs = []
+    for t in (0, 2, 3, 3):
+        s = Solver(0)
+        s.load_scene(sc, K=2, traversal=t)
+        recs.append(s.walk_records(pts, 64)["rec"].view(np.uint32))
+    for r in recs[1:]:
+        assert np.array_equal(recs[0], r)
