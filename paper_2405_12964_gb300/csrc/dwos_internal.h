@@ -46,7 +46,7 @@ struct DevProblem {
     const float* xq;            // n_query x dim
     const int* valid;           // n_query inside flags, or null (no check)
     int walks;                  // walks per point
-    int wide_max;               // order 3: most tree searches per warp step done warp-wide (0: the default)
+    int pad0;
     unsigned long long walk_id_base;
     unsigned long long work_begin;   // first global work index of this problem
     unsigned long long work_end;

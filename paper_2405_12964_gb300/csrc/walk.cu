@@ -200,8 +200,7 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
                     }
                 }
                 need = __ballot_sync(kFull, desc);
-                const int wide_max = sp[0].wide_max > 0 ? sp[0].wide_max : (DIM == 2 ? kRouteWideMax2 : kRouteWideMax3);
-                if (__popc(need) > wide_max) {   // many searches this step: one per lane, in parallel
+                if (__popc(need) > (DIM == 2 ? kRouteWideMax2 : kRouteWideMax3)) {   // many searches this step: one per lane, in parallel
                     lane_search = desc;
                     need = 0;
                 }
