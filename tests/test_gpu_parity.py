@@ -484,3 +484,20 @@ def test_walks_do_not_depend_on_search_order_or_schedule(Solver):
         recs.append(s.walk_records(pts, 64)["rec"].view(np.uint32))
     for r in recs[1:]:
         assert np.array_equal(recs[0], r)
+
+
+def test_routed_search_per_lane_branch_on_a_disk(Solver):
+    # on the 128-gon every element is in the tree, so every query reaches inside the root's
+    # boxes and full warps take order 3's per-lane branch (more than 16 lanes need a search);
+    # the walks must equal those of the per-lane (0) and warp-wide (2) orders bit for bit
+    sc = scenes.disk_scene("screened_1", n_query=64)
+    recs, st = [], []
+    for t in (0, 2, 3):
+        s = Solver(0)
+        s.load_scene(sc, traversal=t)
+        recs.append(s.walk_records(sc.query, 512)["rec"].view(np.uint32))
+        st.append(s.stats())
+    steps = st[2]["steps_main"] + st[2]["steps_nested"]
+    # one root test per query, plus the per-lane branch's binary fetches
+    assert st[2]["nodes_visited"] > 2 * steps
+    assert np.array_equal(recs[0], recs[1]) and np.array_equal(recs[0], recs[2])
