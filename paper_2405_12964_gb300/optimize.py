@@ -79,7 +79,14 @@ class ControlVariateTrainer:
 
     def update(self, samples: torch.Tensor, debug: Optional[torch.Tensor]) -> float:
         """Train on one gradient step's walks.  Fixed-size tensors with zero
-        weights for unusable rows keep the host out of the loop (no sync)."""
+        weights for unusable rows keep the host out of the loop (no sync).
+        The rows (one per walk for the u head, one per walk for the du/dn head)
+        are thinned to at most max_samples by a common stride with a random
+        offset before any other work."""
+        n_rows = samples.shape[0] * (2 if debug is not None else 1)
+        stride = max(1, (n_rows + self.max_samples - 1) // self.max_samples)
+        off = int(self.rng.integers(stride))
+        samples = samples[off::stride]
         xs = samples[:, :2]
         ok = ~torch.isnan(xs[:, 0])
         zero = torch.zeros_like(samples[:, 0])
@@ -88,8 +95,9 @@ class ControlVariateTrainer:
         parts_m = [torch.stack([ok.to(zero.dtype), zero], 1)]
         if debug is not None:
             # dwos_walk_debug: dudn, n[3], u_off, xbar[3], u_plain, disp_n, disp_t, elem
-            rec = debug.view(torch.float32).view(-1, 12)
+            rec = debug.view(torch.float32).view(-1, 12)[off::stride]
             dudn, u_off, xb, u_plain, dn, dt = rec[:, 0], rec[:, 4], rec[:, 5:7], rec[:, 8], rec[:, 9], rec[:, 10]
+            zero = torch.zeros_like(dudn)
             hit = ((rec[:, 1] != 0) | (rec[:, 2] != 0)) & (dn.abs() > 1e-7)
             # The du/dn head q weights the nested walks' normal displacement; the
             # corrected nested mean u_plain - disp_t - q disp_n keeps its mean for
@@ -108,15 +116,9 @@ class ControlVariateTrainer:
             parts_x.append(torch.where(hit[:, None], xb, torch.zeros_like(xb)))
             parts_t.append(torch.stack([zero, y], 1))
             parts_m.append(torch.stack([zero, w], 1))
-        x = torch.cat(parts_x)
-        t = torch.cat(parts_t)
-        m = torch.cat(parts_m)
-        n = x.shape[0]
-        if n > self.max_samples:            # a strided subset with a random offset
-            stride = (n + self.max_samples - 1) // self.max_samples
-            off = int(self.rng.integers(stride))
-            x, t, m = x[off::stride], t[off::stride], m[off::stride]
-        x, t, m = x.contiguous(), t.contiguous(), m.contiguous()
+        x = torch.cat(parts_x).contiguous()
+        t = torch.cat(parts_t).contiguous()
+        m = torch.cat(parts_m).contiguous()
         losses = [self.net.train_step(x, t, m, lr=self.lr) for _ in range(self.iters)]
         self.net.sync()
         return float(losses[-1][0])
