@@ -1,5 +1,6 @@
 """Shape optimisation loop (Sec. 5.2 / Sec. 6 setting) on the 2D
-shape-from-diffusion geometry, with and without the learned control variate."""
+shape-from-diffusion geometry, with and without the learned control variate,
+and on the 3D thermal-design geometry."""
 import numpy as np
 import pytest
 
@@ -38,3 +39,14 @@ def test_optimisation_reduces_the_loss(opt, use_cv):
     assert np.all(np.isfinite(theta)) and hist.theta_err[-1] < 2.0 * hist.theta_err[0]
     if use_cv:
         assert np.median(hist.var_ratio[-10:]) < 1.0
+
+
+def test_optimisation_reduces_the_loss_in_3d(opt):
+    # the same loop on the 3D thermal-design geometry (SH sphere in a box), plain estimator:
+    # start from the unit sphere, target a perturbed one (l <= 2), observations in the box
+    sc = scenes.sh_sphere_scene(freq=12, lmax=2, coef_std=0.08, n_query=64)
+    target = sc.theta0.copy()
+    start = np.zeros_like(target)
+    theta, hist, _ = opt.run(sc, target, start, steps=40, lr=2e-2, wpp0=64, wppT=256, use_cv=False, seed=4)
+    assert np.mean(hist.loss[-8:]) < 0.5 * np.mean(hist.loss[:4])
+    assert np.all(np.isfinite(theta))
