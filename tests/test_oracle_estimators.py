@@ -65,3 +65,21 @@ def test_uncorrelated_and_vjp_definitions():
     assert np.allclose(g, want)
     w = rng.normal(size=P)
     assert np.allclose(est.vjp(ud, w, P, W), sum(w[p] * ud[p * W:(p + 1) * W].mean(0) for p in range(P)))
+
+
+def test_small_cases_worked_by_hand():
+    # one point, two walks: u = (1, 3), udot = (2, 4), target 1, all values worked out by hand
+    u = np.array([1.0, 3.0])
+    ud = np.array([[2.0], [4.0]])
+    # sample mean 2; sample standard deviation (n - 1 = 1) sqrt(2); standard error sqrt(2) / sqrt(2) = 1
+    m, se = est.point_mean_se(u, 1, 2)
+    assert m[0] == 2.0 and abs(se[0] - 1.0) < 1e-15
+    # loss: 1/2 (2 - 1)^2 = 1/2
+    assert est.loss_l2(u, [1.0], 1, 2) == 0.5
+    # correlated product: (mean u - target) mean udot = (2 - 1) * 3 = 3
+    assert est.grad_l2_correlated(u, ud, [1.0], 1, 2)[0] == 3.0
+    # uncorrelated product: u from walk 1, udot from walk 2: (1 - 1) * 4 = 0; with target 0: 1 * 4
+    assert est.grad_l2_uncorrelated(u, ud, [1.0], 1, 2)[0] == 0.0
+    assert est.grad_l2_uncorrelated(u, ud, [0.0], 1, 2)[0] == 4.0
+    # U-statistic, one batch of B = 2: (udot_1 u_2 + udot_2 u_1) / 2 - target mean udot = (6 + 4) / 2 - 3 = 2
+    assert est.grad_l2_ustat(u, ud, [1.0], 1, 2, 2)[0] == 2.0
