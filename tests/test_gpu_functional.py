@@ -179,3 +179,25 @@ def test_general_functional_gradient_is_the_sum_of_its_parts(Solver):
     n = len(sc.elem)
     assert abs(jb - 0.5 * 0.75 ** 2 * 2 * n * np.sin(np.pi / n)) < 1e-6 * jb
     assert abs(gb[0] - jb) < 1e-6 * jb
+
+
+def test_boundary_loss_with_host_buffers(Solver):
+    # the same call through the C ABI with host target, loss and gradient buffers (mem = host)
+    import ctypes
+    from paper_2405_12964_gb300 import dwos
+    sc = scenes.star_box_scene(n_seg=512, n_query=4)
+    s = Solver(0)
+    s.load_scene(sc)
+    ub = np.linspace(0.0, 1.0, len(sc.vert)).astype(np.float32)
+    lo, hi = [-0.7, -1.5], [1.5, 0.4]
+    loss_d, g_d = s.boundary_loss_l2(lo, hi, ub)
+    lo_c = (ctypes.c_float * 3)(*lo, 0.0)
+    hi_c = (ctypes.c_float * 3)(*hi, 0.0)
+    loss_h = np.zeros(1, np.float64)
+    g_h = np.zeros(s.n_param, np.float64)
+    st = dwos.lib().dwos_boundary_loss_l2(s._h, lo_c, hi_c, ub.ctypes.data_as(ctypes.c_void_p),
+                                         loss_h.ctypes.data_as(ctypes.c_void_p),
+                                         g_h.ctypes.data_as(ctypes.c_void_p), dwos.MEM_HOST)
+    assert st == 0, dwos.lib().dwos_last_error(s._h).decode()
+    assert abs(loss_h[0] - loss_d) <= 1e-12 * loss_d
+    assert np.allclose(g_h, g_d, rtol=1e-12, atol=1e-15)
