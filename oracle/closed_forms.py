@@ -65,6 +65,35 @@ def disk_mapped_cos(x, R: float, n_modes: int = 8):
     return u, out
 
 
+def disk_mapped_linear(x, R: float, c: float, s: float, n_modes: int = 8):
+    """Disk, sigma = 0, mapped data g(t) = c cos t + s sin t whose two
+    coefficients are themselves parameters (Eq. boundary_deriv_mapped with a
+    nonzero data derivative): theta = [R, a_1..a_M, b_1..b_M, c, s].
+    u = (c x + s y) / R is harmonic with these boundary values, so
+      du/dc = x / R,  du/ds = y / R  (the data term alone: V_n = 0 for them),
+      du/dR = -(c x + s y) / R^2,
+    and a_m, b_m move the boundary by V_n = cos mt, sin mt, giving the boundary
+    value -V_n du/dn = -V_n (c cos t + s sin t) / R extended harmonically:
+      du/da_m = -(1/2R) [c (p cos(m+1)th + q cos(m-1)th) + s (p sin(m+1)th - q sin(m-1)th)]
+      du/db_m = -(1/2R) [c (p sin(m+1)th + q sin(m-1)th) + s (q cos(m-1)th - p cos(m+1)th)]
+    with p = (r/R)^(m+1), q = (r/R)^|m-1|."""
+    r, th = polar(x)
+    M = n_modes
+    u = r * (c * np.cos(th) + s * np.sin(th)) / R
+    out = np.zeros((r.size, 1 + 2 * M + 2))
+    out[:, 0] = -u / R
+    for m in range(1, M + 1):
+        p = (r / R) ** (m + 1)
+        q = (r / R) ** abs(m - 1)
+        out[:, m] = -(c * (p * np.cos((m + 1) * th) + q * np.cos((m - 1) * th))
+                      + s * (p * np.sin((m + 1) * th) - q * np.sin((m - 1) * th))) / (2 * R)
+        out[:, M + m] = -(c * (p * np.sin((m + 1) * th) + q * np.sin((m - 1) * th))
+                          + s * (q * np.cos((m - 1) * th) - p * np.cos((m + 1) * th))) / (2 * R)
+    out[:, 2 * M + 1] = r * np.cos(th) / R
+    out[:, 2 * M + 2] = r * np.sin(th) / R
+    return u, out
+
+
 def harmonic_field(x, field):
     """u = g for restricted data g = c0 + c.x + x^T A x with trace(A) = 0, sigma = 0,
     f = 0, on any domain; du/dtheta = 0 for every shape parameter."""

@@ -351,6 +351,9 @@ double oracle_alpha(int dim, double sigma, double d) {
     return kd / std::sinh(kd);
 }
 
+/* The modified Bessel function K0 from the C++17 special-function library. */
+double oracle_bessel_k0(double x) { return std::cyl_bessel_k(0.0, x); }
+
 /* |B(d)| * G_d(r) with r = rho * d: the source weight of Algorithm 1 per unit f. */
 double oracle_source_weight(int dim, double sigma, double d, double rho) {
     double r = rho * d;

@@ -118,10 +118,26 @@ def disk_scene(variant: str = "laplace_x", n_seg: int = 128, R: float = 1.0, n_m
     variant 'laplace_x': sigma = 0, restricted data g = x  (u = x, du/dtheta = 0)
     variant 'screened_1': sigma = 4, g = 1  (u = I0(2r)/I0(2R))
     variant 'mapped_cos': sigma = 0, mapped data g_v = cos t_v  (u = x/R)
+    variant 'mapped_data': sigma = 0, mapped data g_v = c cos t_v + s sin t_v with
+        c = 1, s = 0.5 appended to theta as boundary-data parameters:
+        theta = [R, a_1..a_8, b_1..b_8, c, s], dg_v/dc = cos t_v, dg_v/ds = sin t_v
+        and no vertex motion for c and s (u = (c x + s y)/R)
     """
     t, vert, elem = radial_polygon(n_seg, lambda t: np.full_like(t, R))
     jac = fourier_jacobian(t, 1.0, n_modes, with_radius=True)
     q = disk_points(n_query, 0.9 * R, seed)
+    if variant == "mapped_data":
+        c, s = 1.0, 0.5
+        jac = np.concatenate([jac, np.zeros((n_seg, 2, 2))], axis=2)
+        dg = np.zeros((n_seg, jac.shape[2]))
+        dg[:, -2] = np.cos(t)
+        dg[:, -1] = np.sin(t)
+        sc = Scene("disk_mapped_data", vert, elem, jac, data="mapped", g_vert=c * np.cos(t) + s * np.sin(t),
+                   dg_vert=dg, sigma=0.0)
+        sc.eps, sc.h, sc.K, sc.query, sc.walks = eps, h, K, q, walks
+        sc.meta = {"R": R, "t": t, "n_modes": n_modes, "c": c, "s": s,
+                   "theta0": np.concatenate([[R], np.zeros(2 * n_modes), [c, s]])}
+        return sc
     if variant == "laplace_x":
         sc = Scene("disk_laplace_x", vert, elem, jac, data="field", field=_field(c=(1.0, 0.0, 0.0)),
                    sigma=0.0)

@@ -103,6 +103,32 @@ def test_disk_mapped_data_closed_form():
     _check(r["du"], r["du_se"], du, 0.08, 0.01)
 
 
+def test_disk_mapped_data_parameters_closed_form():
+    # Eq. (boundary_deriv_mapped) with a nonzero data derivative: g = c cos t + s sin t
+    # with c, s parameters; du/dc = x/R and du/ds = y/R come from the sum over the hit
+    # element's vertices of w_a dg_a/dtheta alone.  A dropped weight, a transposed
+    # [parameter][vertex] index or a sign error in that sum breaks these two columns.
+    sc = scenes.disk_scene("mapped_data", n_query=12)
+    r = _run(sc, 8192)
+    u, du = cf.disk_mapped_linear(sc.query, 1.0, sc.meta["c"], sc.meta["s"])
+    _check(r["u"], r["u_se"], u, 2e-3, 1e-3)
+    # the data columns carry no 1/h noise: a tight bias budget (polygon interpolation)
+    _check(r["du"][:, -2:], r["du_se"][:, -2:], du[:, -2:], 4e-3, 1e-3)
+    _check(r["du"], r["du_se"], du, 0.08, 0.01)
+    # the data columns are the dg term alone, walk by walk: each equals the hit
+    # element's interpolated cos / sin (V_n = 0 for c and s)
+    o = r["out"]
+    hit = o["elem"] >= 0
+    e = o["elem"][hit]
+    w1 = o["bary"][hit, 0]
+    t = sc.meta["t"]
+    a, b = sc.elem[e, 0], sc.elem[e, 1]
+    want_c = (1 - w1) * np.cos(t[a]) + w1 * np.cos(t[b])
+    want_s = (1 - w1) * np.sin(t[a]) + w1 * np.sin(t[b])
+    assert np.allclose(o["udot"][hit, -2], want_c, atol=1e-12)
+    assert np.allclose(o["udot"][hit, -1], want_s, atol=1e-12)
+
+
 def test_disk_source_closed_forms():
     for sigma, f, g in [(0.0, 1.0, 0.5), (3.0, 2.0, 1.0)]:
         sc = scenes.disk_scene("screened_1", n_query=8)
