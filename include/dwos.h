@@ -195,6 +195,13 @@ dwos_status dwos_set_dirichlet_mapped(dwos_ctx* ctx, const float* g_vert, const 
 dwos_status dwos_set_dirichlet_field(dwos_ctx* ctx, const double* coeffs);
 /* Screening sigma >= 0 and constant source f (of -Lap u + sigma u = f). */
 dwos_status dwos_set_pde(dwos_ctx* ctx, float sigma, float f);
+/* Bound on the BVH node fetches (binary nodes, or 32-wide node visits) that one
+ * distance query of a walk may make; 0 (the default) keeps the trees' own
+ * bounds, which a valid tree never reaches.  A query that exceeds the bound
+ * keeps the closest element it has found, its walk continues, and the call
+ * reports DWOS_ERR_STEP_LIMIT (at once for host outputs, else at dwos_sync).
+ * It exists to exercise that failure path without a fault.  max_fetches >= 0. */
+dwos_status dwos_set_traversal_budget(dwos_ctx* ctx, int max_fetches);
 
 /* ---- estimators --------------------------------------------------------- */
 
@@ -364,6 +371,22 @@ dwos_status dwos_inside(dwos_ctx* ctx, int n, const float* p, int32_t* inside, i
  * Philox(ctr[4i..4i+3], key[0..1]) for i < n.  ctx selects the device. */
 dwos_status dwos_philox4x32_10(dwos_ctx* ctx, int n, const uint32_t* ctr, const uint32_t* key,
                                uint32_t* out, int mem);
+/* The two ball weights of a walk step (Sec. 3.3.1, Algorithm 1), evaluated on
+ * the device exactly as the walk kernel does, for n pairs (d[i], u[i]) with
+ * d > 0 the ball radius and u in (0, 1) the uniform that places the source
+ * sample at r = d u^(1/dim): source[i] = |B(d)| G_d(r), the source estimate
+ * per unit f, and alpha[i] = P(d) |dB(d)|, the Russian-roulette survival
+ * probability; G and P are the screened Green's function and Poisson kernel
+ * of the ball for k = sqrt(sigma) (2D: G = (K0(kr) - K0(kd) I0(kr)/I0(kd)) /
+ * 2 pi, alpha = 1 / I0(kd); 3D: G = sinh(k(d - r)) / (4 pi r sinh kd),
+ * alpha = kd / sinh kd; the Laplace limits at sigma = 0).  Either output may
+ * be NULL.  Inputs and outputs are host or device memory by mem; sizes n. */
+dwos_status dwos_ball_weights(dwos_ctx* ctx, int dim, float sigma, int n, const float* d, const float* u,
+                              float* source, float* alpha, int mem);
+/* The modified Bessel function K0(x), x > 0, as the 2D source weight evaluates
+ * it (the polynomial approximations 9.8.5 and 9.8.6 of Abramowitz & Stegun in
+ * FP32): out[i] = K0(x[i]) for i < n, host or device memory by mem. */
+dwos_status dwos_bessel_k0(dwos_ctx* ctx, int n, const float* x, float* out, int mem);
 
 /* ---- batched problems ----------------------------------------------------
  * Many independent reverse-mode problems in one pass: each job is a
@@ -414,6 +437,15 @@ dwos_status dwos_batch_config(const dwos_batch* b, int dim, int* block_size, int
                               float* walk_ms);
 /* Walk statistics of the last pass (summed over launches; synchronises). */
 dwos_status dwos_batch_stats(dwos_batch* b, dwos_run_stats* out);
+/* enable = 1: later passes also write each walk's trace ((K + 1) words per
+ * walk, the layout of dwos_walk_records); 0: stop.  Allocates (or frees) the
+ * trace buffer and recaptures the graph if one exists.  Synchronises. */
+dwos_status dwos_batch_trace(dwos_batch* b, int enable);
+/* The per-walk records of job `job` from the last pass (n_query x
+ * walks_per_point rows, row p*W + w, Philox walk id walk_id_base + p*W + w,
+ * layout of dwos_record) and, if trace is not NULL, its traces (traces must be
+ * on).  Host or device memory by mem.  Synchronises the batch's stream. */
+dwos_status dwos_batch_records(dwos_batch* b, int job, dwos_record* records, uint32_t* trace, int mem);
 
 /* ---- learned control variate ---------------------------------------------
  * The paper points to variance reduction for WoS (Sec. 2, Sec. 7) without
@@ -451,8 +483,15 @@ dwos_status dwos_mlp_eval(dwos_mlp* mlp, int n, const float* x, float* u, float*
 
 /* Wait for the network's queued work and report a tensor-core product that did
  * not complete within its bounded wait (DWOS_ERR_TIMEOUT; the kernels give up
- * instead of hanging).  Calls with host buffers check this themselves. */
+ * instead of hanging).  Calls with host buffers check this themselves.  The
+ * failure is reported once; the next call starts clean. */
 dwos_status dwos_mlp_sync(dwos_mlp* mlp);
+/* The bounded-wait failure path without a fault: a kernel waits, with the
+ * training kernel's bounded mbarrier wait, on a barrier that nothing arrives
+ * at (no copy or product is issued), gives up after `polls` tries (1 ..
+ * 2^24) and raises the network's timeout flag.  Returns DWOS_ERR_TIMEOUT, as
+ * a stalled product would; the network stays usable.  Synchronises. */
+dwos_status dwos_mlp_wait_probe(dwos_mlp* mlp, int polls);
 
 /* ---- allocation-free evaluation ------------------------------------------
  * The paper has no counterpart to this entry point.  It is dwos_eval for
@@ -472,8 +511,10 @@ dwos_status dwos_mlp_sync(dwos_mlp* mlp);
  *    device (outputs as in dwos_eval; du_mean / du_se may be NULL);
  *  - the boundary, data and options must already be set on the context (those
  *    calls do allocate);
- *  - the first call on a device looks up the array's device address (once per
- *    device); make that first call before any stream capture;
+ *  - the first call on a device does a one-time set-up: it looks up the
+ *    array's device address, with that device current; make that first call
+ *    before any stream capture begins.  The address belongs to the device's
+ *    primary context, so a cudaDeviceReset in the process invalidates it;
  *  - all calls, from every context in the process, share the one array, which
  *    keeps the previous call's contents (the counters are cleared by each
  *    call): calls whose work overlaps on the GPU race and must be ordered by

@@ -11,6 +11,10 @@ Contents
                    an independent Philox4x32-10 (ctypes-loaded from liboracle.so)
   estimators.py    per-point means, the product estimators of Sec. 4.3, VJPs
   closed_forms.py  exact disk / ball solutions used to pin the oracle
+  cv.py            the nested walks' control-variate table (tangential data gradient)
+  mlp.py           the control-variate network with BF16 product operands, and
+                   error bounds for an FP32-accumulating implementation
+  functional.py    the volume-integrated and boundary shape functionals
 """
 from __future__ import annotations
 
@@ -111,6 +115,8 @@ def lib():
             L.oracle_source_weight.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_double]
             L.oracle_source_weight.restype = ctypes.c_double
+            L.oracle_bessel_k0.argtypes = [ctypes.c_double]
+            L.oracle_bessel_k0.restype = ctypes.c_double
             L.oracle_gradient_factor.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
             L.oracle_gradient_factor.restype = ctypes.c_double
             L.oracle_closest_point.argtypes = [ctypes.POINTER(_Scene), ctypes.c_int, dp, dp, dp,
@@ -227,6 +233,11 @@ def alpha(dim: int, sigma: float, d: float) -> float:
 def source_weight(dim: int, sigma: float, d: float, rho: float) -> float:
     """|B(d)| * G_d(rho d): Algorithm 1's source weight per unit source."""
     return lib().oracle_source_weight(dim, sigma, d, rho)
+
+
+def bessel_k0(x: float) -> float:
+    """K0(x) from std::cyl_bessel_k (the library routine the source weight uses)."""
+    return lib().oracle_bessel_k0(float(x))
 
 
 def gradient_factor(dim: int, sigma: float, R: float) -> float:

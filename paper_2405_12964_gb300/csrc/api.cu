@@ -154,6 +154,7 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     P.xq = ctx->xq;
     P.valid = valid;
     P.walks = W;
+    P.node_budget = ctx->node_budget;
     P.walk_id_base = base;
     P.work_begin = 0;
     P.work_end = total;
@@ -187,9 +188,53 @@ dwos_status finish_sync(dwos_ctx* ctx) {
     CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     DevCounters c;
     CK(cudaMemcpy(&c, ctx->d_ctr, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
+    if (c.error & 4) return fail(ctx, DWOS_ERR_INVALID_ARG, "a query point is not finite");
     if (c.error & 2) return fail(ctx, DWOS_ERR_OUTSIDE, "a query point lies outside the domain");
     if (c.error & 1) return fail(ctx, DWOS_ERR_STEP_LIMIT, "BVH traversal exceeded its iteration bound");
     return DWOS_OK;
+}
+
+// An element whose normal the walks cannot form: the squared length of a
+// segment, or of a triangle's edge cross product, is zero (or not finite) in
+// the FP32 arithmetic the walk kernel uses for it.
+__host__ __device__ inline bool degenerate_element(int dim, const float* a, const float* b, const float* c) {
+    float n2;
+    if (dim == 2) {
+        const float tx = b[0] - a[0], ty = b[1] - a[1];
+        n2 = tx * tx + ty * ty;
+    } else {
+        const float e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+        const float e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+        const float cr[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        n2 = cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2];
+    }
+    return !(n2 > 0.0f && n2 < __builtin_inff());
+}
+
+// Checks of boundary arrays that live on the device: bit 0 a vertex or Jacobian
+// entry is not finite, bit 1 an element's vertex id is out of range, bit 2 an
+// element is degenerate.
+__global__ void validate_boundary_kernel(int dim, int n_vert, const float* __restrict__ vert, int n_elem,
+                                         const int* __restrict__ elem, long long n_jac,
+                                         const float* __restrict__ jac, int* __restrict__ flags) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int bad = 0;
+    for (long long i = i0; i < (long long)n_vert * dim; i += stride)
+        if (!isfinite(vert[i])) bad |= 1;
+    for (long long i = i0; i < n_jac; i += stride)
+        if (!isfinite(jac[i])) bad |= 1;
+    for (long long e = i0; e < n_elem; e += stride) {
+        const int* ev = elem + (size_t)dim * e;
+        bool in_range = true;
+        for (int k = 0; k < dim; ++k) in_range = in_range && ev[k] >= 0 && ev[k] < n_vert;
+        if (!in_range) { bad |= 2; continue; }
+        const float* a = vert + (size_t)dim * ev[0];
+        const float* b = vert + (size_t)dim * ev[1];
+        const float* c = dim == 3 ? vert + (size_t)dim * ev[2] : a;
+        if (degenerate_element(dim, a, b, c)) bad |= 4;
+    }
+    if (bad) atomicOr(flags, bad);
 }
 
 }  // namespace
@@ -303,6 +348,14 @@ dwos_status dwos_set_boundary(dwos_ctx* ctx, int dim, int n_vert, const float* v
         if (!finite_all(vert_ref, (size_t)n_vert * dim)) return fail(ctx, DWOS_ERR_INVALID_ARG, "vertices must be finite");
         for (long long i = 0; i < (long long)n_elem * dim; ++i)
             if (elem[i] < 0 || elem[i] >= n_vert) return fail(ctx, DWOS_ERR_INVALID_ARG, "element vertex id out of range");
+        for (long long e = 0; e < n_elem; ++e) {
+            const int32_t* ev = elem + (size_t)dim * e;
+            const float* a = vert_ref + (size_t)dim * ev[0];
+            const float* b = vert_ref + (size_t)dim * ev[1];
+            if (degenerate_element(dim, a, b, dim == 3 ? vert_ref + (size_t)dim * ev[2] : a))
+                return fail(ctx, DWOS_ERR_INVALID_ARG, "element " + std::to_string(e) +
+                                                           " is degenerate (zero length or area)");
+        }
         if (n_param > 0 && !finite_all(vert_jac, (size_t)n_vert * dim * n_param))
             return fail(ctx, DWOS_ERR_INVALID_ARG, "Jacobian must be finite");
     } else {
@@ -327,6 +380,22 @@ dwos_status dwos_set_boundary(dwos_ctx* ctx, int dim, int n_vert, const float* v
     CK(cudaMemcpyAsync(ctx->vert, ctx->vert_ref, nv * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream), "copy vertices");
     CK(to_device(ctx, ctx->elem, elem, (size_t)n_elem * dim, mem), "copy elements");
     if (n_param > 0) CK(to_device(ctx, ctx->jac, vert_jac, nv * n_param, mem), "copy Jacobian");
+    if (mem == DWOS_MEM_DEVICE) {   // the host checks above, run on the device copies
+        CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream), "reset flag");
+        const long long work = std::max<long long>((long long)n_elem, (long long)nv * std::max(n_param, 1));
+        const int blocks = (int)std::min<long long>((work + 255) / 256, 4096);
+        validate_boundary_kernel<<<blocks, 256, 0, ctx->stream>>>(dim, n_vert, ctx->vert_ref, n_elem, ctx->elem,
+                                                                 n_param > 0 ? (long long)nv * n_param : 0, ctx->jac,
+                                                                 ctx->d_err);
+        CK(cudaGetLastError(), "validate boundary");
+        int flags = 0;
+        CK(cudaMemcpyAsync(&flags, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "read flag");
+        CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+        ctx->launches += 1;
+        if (flags & 1) return fail(ctx, DWOS_ERR_INVALID_ARG, "vertices and Jacobian must be finite");
+        if (flags & 2) return fail(ctx, DWOS_ERR_INVALID_ARG, "element vertex id out of range");
+        if (flags & 4) return fail(ctx, DWOS_ERR_INVALID_ARG, "an element is degenerate (zero length or area)");
+    }
     CK(cudaMemsetAsync(ctx->g_vert, 0, (size_t)n_vert * sizeof(float), ctx->stream), "zero data");
     CK(cudaMemsetAsync(ctx->theta, 0, (size_t)std::max(n_param, 1) * sizeof(float), ctx->stream), "zero theta");
     ctx->dim = dim; ctx->n_vert = n_vert; ctx->n_elem = n_elem; ctx->n_param = n_param;
@@ -393,6 +462,13 @@ dwos_status dwos_set_pde(dwos_ctx* ctx, float sigma, float f) {
     if (!std::isfinite(f)) return fail(ctx, DWOS_ERR_INVALID_ARG, "f must be finite");
     ctx->sigma = sigma;
     ctx->f = f;
+    return DWOS_OK;
+}
+
+dwos_status dwos_set_traversal_budget(dwos_ctx* ctx, int max_fetches) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (max_fetches < 0) return fail(ctx, DWOS_ERR_INVALID_ARG, "max_fetches must be >= 0");
+    ctx->node_budget = max_fetches;
     return DWOS_OK;
 }
 
@@ -887,6 +963,46 @@ dwos_status dwos_philox4x32_10(dwos_ctx* ctx, int n, const uint32_t* ctr, const 
     return DWOS_OK;
 }
 
+dwos_status dwos_ball_weights(dwos_ctx* ctx, int dim, float sigma, int n, const float* d, const float* u,
+                              float* source, float* alpha, int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (dwos_status s = check_mem(ctx, mem)) return s;
+    if (dim != 2 && dim != 3) return fail(ctx, DWOS_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (!(sigma >= 0.0f) || !std::isfinite(sigma)) return fail(ctx, DWOS_ERR_INVALID_ARG, "sigma must be finite and >= 0");
+    if (n < 0 || (n > 0 && (!d || !u || (!source && !alpha)))) return fail(ctx, DWOS_ERR_INVALID_ARG, "bad arguments");
+    if (dwos_status s = set_device(ctx)) return s;
+    if (n == 0) return DWOS_OK;
+    CK(grow(ctx->misc_f, ctx->misc_f_cap, 4 * (size_t)n), "alloc");
+    float* dd = ctx->misc_f;
+    float* du = dd + n;
+    float* ds = du + n;
+    float* da = ds + n;
+    CK(to_device(ctx, dd, d, (size_t)n, mem), "copy d");
+    CK(to_device(ctx, du, u, (size_t)n, mem), "copy u");
+    CK(launch_ball_weights(dim, std::sqrt(sigma), n, dd, du, source ? ds : nullptr, alpha ? da : nullptr,
+                           ctx->stream), "ball weights");
+    ctx->launches += 1;
+    if (source) CK(from_device(ctx, source, ds, (size_t)n, mem), "copy source weights");
+    if (alpha) CK(from_device(ctx, alpha, da, (size_t)n, mem), "copy recursive weights");
+    if (mem == DWOS_MEM_HOST) CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    return DWOS_OK;
+}
+
+dwos_status dwos_bessel_k0(dwos_ctx* ctx, int n, const float* x, float* out, int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (dwos_status s = check_mem(ctx, mem)) return s;
+    if (n < 0 || (n > 0 && (!x || !out))) return fail(ctx, DWOS_ERR_INVALID_ARG, "bad arguments");
+    if (dwos_status s = set_device(ctx)) return s;
+    if (n == 0) return DWOS_OK;
+    CK(grow(ctx->misc_f, ctx->misc_f_cap, 2 * (size_t)n), "alloc");
+    CK(to_device(ctx, ctx->misc_f, x, (size_t)n, mem), "copy x");
+    CK(launch_bessel_k0(n, ctx->misc_f, ctx->misc_f + n, ctx->stream), "K0");
+    ctx->launches += 1;
+    CK(from_device(ctx, out, ctx->misc_f + n, (size_t)n, mem), "copy K0");
+    if (mem == DWOS_MEM_HOST) CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    return DWOS_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
@@ -903,11 +1019,14 @@ dwos_status dwos_philox4x32_10(dwos_ctx* ctx, int n, const uint32_t* ctr, const 
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr size_t kStaticHeader = 4096;     // problem descriptor + counters
+constexpr size_t kStaticHeader = 4096;     // problem descriptor (offset 0) + counters (offset 2048)
+constexpr size_t kStaticCounters = 2048;
+// One inside flag per query point; n_query reaches DWOS_STATIC_MAX_WALKS when
+// walks_per_point = 1, so the region is sized for that worst case.
 constexpr size_t kStaticFlags = (size_t)DWOS_STATIC_MAX_WALKS * sizeof(int);
 constexpr size_t kStaticBytes = kStaticHeader + kStaticFlags + (size_t)DWOS_STATIC_MAX_WALKS * sizeof(dwos_record);
-static_assert(sizeof(DevProblem) + sizeof(DevCounters) <= kStaticHeader, "static header too small");
-static_assert(sizeof(DevProblem) <= 2048, "the counters sit 2048 bytes into the header");
+static_assert(sizeof(DevProblem) <= kStaticCounters, "the problem descriptor must end before the counters");
+static_assert(kStaticCounters + sizeof(DevCounters) <= kStaticHeader, "the counters must fit in the header");
 
 // Held by every GPU that loads the library, until the process exits.
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
@@ -917,6 +1036,8 @@ void* g_static_addr[64] = {nullptr};
 
 // Device address of the scratch array on ctx's device (looked up once per
 // device, with that device current; the host-side symbol is not an address).
+// The address belongs to the device's primary context: a cudaDeviceReset in
+// the caller's process ends that context, and the cached address with it.
 dwos_status static_scratch(dwos_ctx* ctx, unsigned char** out) {
     if (ctx->device < 0 || ctx->device >= 64) return fail(ctx, DWOS_ERR_INVALID_ARG, "device index too large");
     std::lock_guard<std::mutex> lock(g_static_mutex);
@@ -929,6 +1050,13 @@ dwos_status static_scratch(dwos_ctx* ctx, unsigned char** out) {
     }
     *out = static_cast<unsigned char*>(g_static_addr[ctx->device]);
     return DWOS_OK;
+}
+
+// Stores the walk launch's problem descriptor into the scratch array: the
+// descriptor travels as a kernel argument (copied at launch), so nothing is read
+// from the host stack after the call returns.
+__global__ void store_problem_kernel(DevProblem P, DevProblem* dst) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *dst = P;
 }
 
 }  // namespace
@@ -952,7 +1080,7 @@ extern "C" dwos_status dwos_eval_static(dwos_ctx* ctx, int n_query, const float*
     unsigned char* base = nullptr;
     if (dwos_status s = static_scratch(ctx, &base)) return s;
     DevProblem* d_prob = reinterpret_cast<DevProblem*>(base);
-    DevCounters* d_ctr = reinterpret_cast<DevCounters*>(base + 2048);
+    DevCounters* d_ctr = reinterpret_cast<DevCounters*>(base + kStaticCounters);
     int* d_valid = reinterpret_cast<int*>(base + kStaticHeader);
     dwos_record* d_rec = reinterpret_cast<dwos_record*>(base + kStaticHeader + kStaticFlags);
     const int diff = du_mean ? 1 : 0;
@@ -994,11 +1122,13 @@ extern "C" dwos_status dwos_eval_static(dwos_ctx* ctx, int n_query, const float*
     P.xq = xq;
     P.valid = valid;
     P.walks = W;
+    P.node_budget = ctx->node_budget;
     P.walk_id_base = 0;
     P.work_begin = 0;
     P.work_end = total;
     P.rec = d_rec;
-    CK(cudaMemcpyAsync(d_prob, &P, sizeof(P), cudaMemcpyHostToDevice, ctx->stream), "copy problem");
+    store_problem_kernel<<<1, 32, 0, ctx->stream>>>(P, d_prob);
+    CK(cudaGetLastError(), "store problem");
     // the array keeps the previous call's contents: the work counter and statistics start at zero
     CK(cudaMemsetAsync(d_ctr, 0, sizeof(DevCounters), ctx->stream), "reset counters");
     WalkLaunch L;

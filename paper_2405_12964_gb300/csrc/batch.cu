@@ -43,6 +43,8 @@ struct dwos_batch {
     std::vector<Chunk> chunks;
     dwos_record* rec = nullptr;
     std::vector<size_t> rec_off;
+    uint32_t* trace = nullptr;          // per job: (K + 1) words per walk, when traces are on
+    std::vector<size_t> trace_off;
     double* acc = nullptr;              // per job: n_vert*dim + n_vert doubles
     std::vector<size_t> acc_off;
     double* means = nullptr;            // per job: n_query doubles
@@ -81,8 +83,8 @@ bool on_device(const void* p, int dev) {
     return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
 
-void fill_problem(const dwos_ctx* c, const dwos_batch_job& j, dwos_record* rec, unsigned long long begin,
-                  int traversal, DevProblem& P) {
+void fill_problem(const dwos_ctx* c, const dwos_batch_job& j, dwos_record* rec, uint32_t* trace,
+                  unsigned long long begin, int traversal, DevProblem& P) {
     std::memset(&P, 0, sizeof(P));
     P.nodes = c->bvh.nodes;
     P.prims = c->bvh.prims;
@@ -115,11 +117,13 @@ void fill_problem(const dwos_ctx* c, const dwos_batch_job& j, dwos_record* rec, 
     P.xq = j.xq;
     P.valid = nullptr;     // checked once at creation
     P.walks = j.walks_per_point;
+    P.node_budget = c->node_budget;
     P.walk_id_base = j.walk_id_base;
     const unsigned long long n = (unsigned long long)j.n_query * (unsigned long long)j.walks_per_point;
     P.work_begin = begin;
     P.work_end = begin + n;
     P.rec = rec;
+    P.trace = trace;
 }
 
 // The warp-wide search serves a launch only if every problem's tree supports it.
@@ -142,7 +146,8 @@ dwos_status upload_tables(dwos_batch* b) {
         for (size_t k = 0; k < ch.jobs.size(); ++k) {
             const int ji = ch.jobs[k];
             const dwos_batch_job& j = b->jobs[ji];
-            fill_problem(j.ctx, j, b->rec + b->rec_off[ji], begin, b->trav[ch.dim], tab[k]);
+            fill_problem(j.ctx, j, b->rec + b->rec_off[ji], b->trace ? b->trace + b->trace_off[ji] : nullptr, begin,
+                         b->trav[ch.dim], tab[k]);
             begin = tab[k].work_end;
         }
         BK(cudaMemcpy(ch.d_probs, tab.data(), sizeof(DevProblem) * tab.size(), cudaMemcpyHostToDevice), "upload table");
@@ -270,6 +275,7 @@ void dwos_batch_destroy(dwos_batch* b) {
     if (b->graph) cudaGraphDestroy(b->graph);
     for (auto& ch : b->chunks) { cudaFree(ch.d_probs); cudaFree(ch.d_ctr); }
     cudaFree(b->rec);
+    cudaFree(b->trace);
     cudaFree(b->acc);
     cudaFree(b->means);
     cudaFree(b->active);
@@ -389,6 +395,46 @@ dwos_status dwos_batch_config(const dwos_batch* b, int dim, int* block_size, int
     return DWOS_OK;
 }
 
+dwos_status dwos_batch_trace(dwos_batch* b, int enable) {
+    if (!b) return bfail(nullptr, DWOS_ERR_INVALID_ARG, "batch is NULL");
+    BK(cudaSetDevice(b->device), "cudaSetDevice");
+    BK(cudaStreamSynchronize(b->stream), "synchronize");
+    if (enable && !b->trace) {
+        size_t n = 0;
+        b->trace_off.clear();
+        for (auto& j : b->jobs) {
+            b->trace_off.push_back(n);
+            n += (size_t)j.n_query * j.walks_per_point * (size_t)(j.ctx->opt.K + 1);
+        }
+        BK(cudaMalloc(&b->trace, sizeof(uint32_t) * std::max<size_t>(n, 1)), "alloc traces");
+        BK(cudaMemset(b->trace, 0xff, sizeof(uint32_t) * std::max<size_t>(n, 1)), "init traces");
+    } else if (!enable && b->trace) {
+        cudaFree(b->trace);
+        b->trace = nullptr;
+    }
+    if (dwos_status s = upload_tables(b)) return s;
+    if (b->exec) return dwos_batch_capture(b);
+    return DWOS_OK;
+}
+
+dwos_status dwos_batch_records(dwos_batch* b, int job, dwos_record* records, uint32_t* trace, int mem) {
+    if (!b) return bfail(nullptr, DWOS_ERR_INVALID_ARG, "batch is NULL");
+    if (job < 0 || job >= (int)b->jobs.size()) return bfail(b, DWOS_ERR_INVALID_ARG, "job index out of range");
+    if (mem != DWOS_MEM_HOST && mem != DWOS_MEM_DEVICE) return bfail(b, DWOS_ERR_INVALID_ARG, "bad mem flag");
+    if (!records) return bfail(b, DWOS_ERR_INVALID_ARG, "records is NULL");
+    if (trace && !b->trace) return bfail(b, DWOS_ERR_STATE, "traces are off: call dwos_batch_trace(b, 1) first");
+    BK(cudaSetDevice(b->device), "cudaSetDevice");
+    const dwos_batch_job& j = b->jobs[job];
+    const size_t n = (size_t)j.n_query * j.walks_per_point;
+    const cudaMemcpyKind k = mem == DWOS_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice;
+    BK(cudaMemcpyAsync(records, b->rec + b->rec_off[job], sizeof(dwos_record) * n, k, b->stream), "copy records");
+    if (trace)
+        BK(cudaMemcpyAsync(trace, b->trace + b->trace_off[job], sizeof(uint32_t) * n * (j.ctx->opt.K + 1), k,
+                           b->stream), "copy traces");
+    BK(cudaStreamSynchronize(b->stream), "synchronize");
+    return DWOS_OK;
+}
+
 dwos_status dwos_batch_stats(dwos_batch* b, dwos_run_stats* out) {
     if (!b || !out) return bfail(b, DWOS_ERR_INVALID_ARG, "NULL argument");
     BK(cudaSetDevice(b->device), "cudaSetDevice");
@@ -404,6 +450,7 @@ dwos_status dwos_batch_stats(dwos_batch* b, dwos_run_stats* out) {
         out->nodes_visited += c.nodes;
         out->prims_tested += c.prims;
         out->wide_nodes_visited += c.wnodes;
+        if (c.error & 4) return bfail(b, DWOS_ERR_INVALID_ARG, "a query point is not finite");
         if (c.error & 1) return bfail(b, DWOS_ERR_STEP_LIMIT, "BVH traversal exceeded its iteration bound");
     }
     return DWOS_OK;

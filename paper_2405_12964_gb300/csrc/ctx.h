@@ -12,6 +12,7 @@ struct dwos_ctx {
     cudaStream_t stream = nullptr;
     std::string err;
     dwos_options opt{};
+    int node_budget = 0;         // node fetches per distance query (0: the tree's own bound)
 
 
     // boundary

@@ -223,6 +223,7 @@ struct BvhView {
     const int* leaf_parent;
     const float* node_cell;   // 2*DIM floats per internal node: lo, hi
     float r_max;
+    int budget = 0;           // node fetches allowed per query; 0: 4 x the inner nodes + 64
 };
 
 template <int DIM>
@@ -371,7 +372,7 @@ __device__ __forceinline__ bool closest_leaf(const BvhView& bvh, const float* q,
         if (closer(dd, p, best2, best)) { best2 = dd; best = p; }
     }
     if (bvh.n_internal == 0) return true;
-    int budget = 4 * bvh.n_internal + 64;
+    int budget = bvh.budget > 0 ? bvh.budget : 4 * bvh.n_internal + 64;
     if (!bvh.climb || best < 0 || best >= bvh.n_tree || !bvh.leaf_parent)
         return search_subtree<DIM>(bvh, bvh.root, q, best2, best, budget, n_nodes, n_prims);
     int child = ~best;
@@ -449,6 +450,7 @@ struct WideView {
     const float4* prims;
     int n_wide;
     int n_tree;
+    int budget = 0;        // wide-node visits allowed per query; 0: the tree's node count
 };
 
 // Closest tree leaf for every lane in `need`, one query at a time, with all
@@ -483,12 +485,13 @@ __device__ __forceinline__ int wide_closest(const WideView& mine, unsigned need,
             __shfl_sync(kWarpAll, reinterpret_cast<unsigned long long>(mine.prims), src));
         const int n_wide = __shfl_sync(kWarpAll, mine.n_wide, src);
         const int n_tree = __shfl_sync(kWarpAll, mine.n_tree, src);
+        const int cap = __shfl_sync(kWarpAll, mine.budget, src);
         if (n_wide > 0) {
             __syncwarp();
             if (lane == 0) stk[0] = make_float2(0.0f, __int_as_float(0));
             __syncwarp();
             int top = 1;
-            int budget = n_wide;
+            int budget = cap > 0 ? cap : n_wide;
             while (top > 0) {
                 const float2 e = stk[top - 1];
                 --top;

@@ -46,7 +46,7 @@ struct DevProblem {
     const float* xq;            // n_query x dim
     const int* valid;           // n_query inside flags, or null (no check)
     int walks;                  // walks per point
-    int pad0;
+    int node_budget;            // node fetches one distance query may make (0: the tree's own bound)
     unsigned long long walk_id_base;
     unsigned long long work_begin;   // first global work index of this problem
     unsigned long long work_end;
@@ -77,7 +77,8 @@ struct DevCounters {
     unsigned long long nodes;   // binary BVH node fetches
     unsigned long long prims;   // element distance tests
     unsigned long long wnodes;  // 32-wide node visits
-    int error;                  // bit 0: traversal bound exceeded, bit 1: query outside Omega
+    int error;                  // bit 0: traversal bound exceeded, bit 1: query outside Omega,
+                                // bit 2: query point not finite
     int pad[1];
 };
 
@@ -140,6 +141,11 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
                          unsigned long long total_work, DevCounters* d_counters, cudaStream_t stream,
                          int* blocks_used);
 int walk_max_blocks_per_sm(int dim, int block_size, int traversal = 0);
+// The walk step's ball weights (source factor for uniform u, recursive weight) and the
+// K0 of the 2D source weight, evaluated as the walk kernel evaluates them (walk.cu).
+cudaError_t launch_ball_weights(int dim, float k, int n, const float* d, const float* u, float* src, float* alpha,
+                                cudaStream_t stream);
+cudaError_t launch_bessel_k0(int n, const float* x, float* out, cudaStream_t stream);
 
 // Estimator reductions (estimators.cu).
 // mean / SE of the first `used` (0: all W) walks of each point

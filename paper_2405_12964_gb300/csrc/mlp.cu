@@ -132,9 +132,9 @@ __device__ __forceinline__ bool bar_try(uint32_t bar, uint32_t parity) {
         : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
     return ok != 0;
 }
-// Bounded wait: false if the phase never completed.
-__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity) {
-    for (int i = 0; i < (1 << 24); ++i)
+// Bounded wait: false if the phase never completed within `polls` tries.
+__device__ __forceinline__ bool bar_wait(uint32_t bar, uint32_t parity, int polls = 1 << 24) {
+    for (int i = 0; i < polls; ++i)
         if (bar_try(bar, parity)) return true;
     return false;
 }
@@ -411,6 +411,23 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (r == 0 && !ok) atomicOr(err, 1);
 }
 
+// The failure path of the bounded wait, without a fault: thread 0 initialises an
+// mbarrier that nothing ever arrives at (no copy or product is issued, so nothing
+// is in flight), every thread waits on it with the training kernel's bar_wait and
+// gives up after `polls` tries, and the give-up is reported through the same flag.
+__global__ void wait_probe_kernel(int polls, int* __restrict__ err) {
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t b = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        bar_init(b, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool got = bar_wait(b, 0, polls);
+    if (!__syncthreads_or(!got)) return;
+    if (threadIdx.x == 0) atomicOr(err, 1);
+}
+
 // Sum of the CTA partials, in CTA order (deterministic).
 __global__ void reduce_parts_kernel(const float* __restrict__ part, int n_parts, float* __restrict__ grad) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -521,7 +538,10 @@ dwos_status check_err(dwos_mlp* mlp) {
     int e = 0;
     MK(cudaMemcpyAsync(&e, mlp->dflag, sizeof(int), cudaMemcpyDeviceToHost, mlp->stream), "read flag");
     MK(cudaStreamSynchronize(mlp->stream), "synchronize");
-    if (e) return mfail(mlp, DWOS_ERR_TIMEOUT, "a tensor-core product did not complete in time");
+    if (e) {   // reported once: the next call starts with a clear flag
+        MK(cudaMemsetAsync(mlp->dflag, 0, sizeof(int), mlp->stream), "reset flag");
+        return mfail(mlp, DWOS_ERR_TIMEOUT, "a bounded wait on the tensor-core kernel's mbarrier ran out");
+    }
     return DWOS_OK;
 }
 
@@ -684,6 +704,16 @@ dwos_status dwos_mlp_eval(dwos_mlp* mlp, int n, const float* x, float* u, float*
 dwos_status dwos_mlp_sync(dwos_mlp* mlp) {
     if (!mlp) return mfail(nullptr, DWOS_ERR_INVALID_ARG, "mlp is NULL");
     MK(cudaSetDevice(mlp->device), "cudaSetDevice");
+    return check_err(mlp);
+}
+
+dwos_status dwos_mlp_wait_probe(dwos_mlp* mlp, int polls) {
+    if (!mlp) return mfail(nullptr, DWOS_ERR_INVALID_ARG, "mlp is NULL");
+    if (polls < 1 || polls > (1 << 24)) return mfail(mlp, DWOS_ERR_INVALID_ARG, "polls must be in [1, 2^24]");
+    MK(cudaSetDevice(mlp->device), "cudaSetDevice");
+    if (dwos_status s = check_err(mlp)) return s;     // earlier work first
+    wait_probe_kernel<<<1, 128, 0, mlp->stream>>>(polls, mlp->dflag);
+    MK(cudaGetLastError(), "wait probe");
     return check_err(mlp);
 }
 

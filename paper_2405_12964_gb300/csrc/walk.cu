@@ -152,16 +152,20 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
                     const DevProblem& P = sp[prob];
                     const unsigned long long local = gw - P.work_begin;
                     const int point = (int)(local / (unsigned long long)P.walks);
-                    if (P.valid && !__ldg(P.valid + point)) {
-                        // query point outside Omega: NaN record, error bit 2, next walk
+                    bool finite = true;
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) {
+                        x[k] = __ldg(P.xq + (size_t)DIM * point + k);
+                        finite = finite && isfinite(x[k]);
+                    }
+                    if (!finite || (P.valid && !__ldg(P.valid + point))) {
+                        // query point not finite (error bit 4) or outside Omega (bit 2): NaN record, next walk
                         dwos_record r;
                         r.u = __int_as_float(0x7fc00000); r.elem = -1; r.b1 = 0.0f; r.b2 = 0.0f;
                         r.c[0] = 0.0f; r.c[1] = 0.0f; r.c[2] = 0.0f; r.meta = 0;
                         P.rec[local] = r;
-                        error |= 2;
+                        error |= finite ? 2 : 4;
                     } else {
-#pragma unroll
-                        for (int k = 0; k < DIM; ++k) x[k] = __ldg(P.xq + (size_t)DIM * point + k);
                         phase = 0; step = 0; hint = -1; acc = 0.0f;
                         active = true;
                     }
@@ -206,7 +210,7 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
                 }
             }
             if (need) {   // all lanes search the 32-wide tree together, one lane's query at a time
-                const WideView wv{Pw.wnodes, Pw.prims, Pw.n_wide, Pw.n_tree};
+                const WideView wv{Pw.wnodes, Pw.prims, Pw.n_wide, Pw.n_tree, Pw.node_budget};
                 error |= wide_closest<DIM>(wv, need, x, best2, best, stk, st.wnodes, st.prims) & 1;
             }
         }
@@ -216,7 +220,7 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
         const unsigned long long local = gw - P.work_begin;
         if (lane_search) {
             BvhView bvh{P.nodes, P.prims, P.root, P.n_internal, P.n_tree, seeded ? 0 : P.n_big, P.traversal == 1,
-                        P.leaf_parent, P.node_cell, P.r_max};
+                        P.leaf_parent, P.node_cell, P.r_max, P.node_budget};
             if (!seeded && hint >= 0) { best2 = prim_dist2<DIM>(P.prims, hint, x); best = hint; ++st.prims; }
             if (!closest_leaf<DIM>(bvh, x, best2, best, st.nodes, st.prims)) error |= 1;
         }
@@ -461,7 +465,39 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
     }
 }
 
+// The ball weights of one walk step, exactly as the walk kernel evaluates them:
+// the source factor |B(d)| G_d(r) for the ball sample drawn from the uniform u,
+// and the recursive weight alpha(d).
+template <int DIM>
+__global__ void ball_weights_kernel(float k, int n, const float* __restrict__ d, const float* __restrict__ u,
+                                    float* __restrict__ src, float* __restrict__ alpha) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (src) src[i] = source_weight<DIM>(k, d[i], u[i]);
+    if (alpha) alpha[i] = recursive_weight<DIM>(k, d[i]);
+}
+
+__global__ void bessel_k0_kernel(int n, const float* __restrict__ x, float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = bessel_k0(x[i]);
+}
+
 }  // namespace
+
+cudaError_t launch_ball_weights(int dim, float k, int n, const float* d, const float* u, float* src, float* alpha,
+                                cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (n + 255) / 256;
+    if (dim == 2) ball_weights_kernel<2><<<blocks, 256, 0, stream>>>(k, n, d, u, src, alpha);
+    else ball_weights_kernel<3><<<blocks, 256, 0, stream>>>(k, n, d, u, src, alpha);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bessel_k0(int n, const float* x, float* out, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    bessel_k0_kernel<<<(n + 255) / 256, 256, 0, stream>>>(n, x, out);
+    return cudaGetLastError();
+}
 
 int walk_max_blocks_per_sm(int dim, int block_size, int traversal) {
     int n = 0;

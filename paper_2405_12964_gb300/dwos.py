@@ -82,6 +82,8 @@ _SIGS = {
     "dwos_closest_point_hint": [_vp, _i, _vp, _vp, _vp, _vp, _vp, _i],
     "dwos_inside": [_vp, _i, _vp, _vp, _i],
     "dwos_philox4x32_10": [_vp, _i, _vp, _vp, _vp, _i],
+    "dwos_ball_weights": [_vp, _i, ctypes.c_float, _i, _vp, _vp, _vp, _vp, _i],
+    "dwos_bessel_k0": [_vp, _i, _vp, _vp, _i],
     "dwos_eval_static": [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp],
     "dwos_batch_create": [ctypes.POINTER(_vp), ctypes.POINTER(BatchJob), _i, _vp],
     "dwos_batch_run": [_vp],
@@ -91,6 +93,8 @@ _SIGS = {
     "dwos_batch_config": [_vp, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i),
                           ctypes.POINTER(ctypes.c_float)],
     "dwos_batch_stats": [_vp, ctypes.POINTER(RunStats)],
+    "dwos_batch_trace": [_vp, _i],
+    "dwos_batch_records": [_vp, _i, _vp, _vp, _i],
     "dwos_grad_l2_cv": [_vp, _i, _vp, _vp, _i, _u64, _vp, _i, _vp, _vp, _vp, _vp, _vp, _vp],
     "dwos_mlp_create": [ctypes.POINTER(_vp), _i],
     "dwos_mlp_set_stream": [_vp, _vp],
@@ -100,6 +104,8 @@ _SIGS = {
     "dwos_mlp_train_step": [_vp, _i, _vp, _vp, _vp, ctypes.c_float, _vp, _i],
     "dwos_mlp_eval": [_vp, _i, _vp, _vp, _vp, _vp, _i],
     "dwos_mlp_sync": [_vp],
+    "dwos_mlp_wait_probe": [_vp, _i],
+    "dwos_set_traversal_budget": [_vp, _i],
     "dwos_cv_table": [_vp, _vp, _vp],
     "dwos_bvh_info": [_vp, _vp],
     "dwos_probe_l2_read": [_i, ctypes.c_size_t, _i, _vp],
@@ -223,6 +229,10 @@ class Solver:
 
     def set_pde(self, sigma: float, f: float = 0.0):
         self._check(lib().dwos_set_pde(self._h, float(sigma), float(f)))
+
+    def set_traversal_budget(self, max_fetches: int):
+        """dwos_set_traversal_budget: node fetches one distance query may make (0: default)."""
+        self._check(lib().dwos_set_traversal_budget(self._h, int(max_fetches)))
 
     def load_scene(self, sc, **opt):
         """Set boundary, data, PDE and the scene's eps / h / K / B / seed."""
@@ -479,6 +489,27 @@ class Solver:
         self._check(lib().dwos_philox4x32_10(self._h, n, _ptr(c), _ptr(k), _ptr(out), MEM_DEVICE))
         return out.cpu().numpy().view(np.uint32).reshape(n, 4)
 
+    def ball_weights(self, dim: int, sigma: float, d, u):
+        """(source factor |B(d)| G_d(r), recursive weight alpha) per (d, u) pair,
+        as the walk kernel evaluates them (dwos_ball_weights); numpy float32."""
+        self._stream()
+        dt = self._dev(d, torch.float32)
+        ut = self._dev(u, torch.float32)
+        n = dt.numel()
+        src = torch.empty(n, device=self.device, dtype=torch.float32)
+        al = torch.empty(n, device=self.device, dtype=torch.float32)
+        self._check(lib().dwos_ball_weights(self._h, int(dim), float(sigma), n, _ptr(dt), _ptr(ut), _ptr(src),
+                                            _ptr(al), MEM_DEVICE))
+        return src.cpu().numpy(), al.cpu().numpy()
+
+    def bessel_k0(self, x):
+        """K0(x) as the 2D source weight evaluates it (dwos_bessel_k0); numpy float32."""
+        self._stream()
+        xt = self._dev(x, torch.float32)
+        out = torch.empty(xt.numel(), device=self.device, dtype=torch.float32)
+        self._check(lib().dwos_bessel_k0(self._h, xt.numel(), _ptr(xt), _ptr(out), MEM_DEVICE))
+        return out.cpu().numpy()
+
 
 class Batch:
     """Many reverse-mode problems in one pass (dwos_batch_*): each job is
@@ -489,7 +520,7 @@ class Batch:
     def __init__(self, jobs, device: int = 0):
         self.device = torch.device("cuda", device)
         self.stream = torch.cuda.Stream(device=self.device)
-        self.solvers, self.keep, self.out = [], [], []
+        self.solvers, self.keep, self.out, self.walks = [], [], [], []
         arr = (BatchJob * len(jobs))()
         for k, (solver, xq, walks, uref, base) in enumerate(jobs):
             x = solver._dev(xq, torch.float32)
@@ -498,6 +529,7 @@ class Batch:
             o = {"loss": torch.zeros(1, **dd), "grad": torch.zeros(max(solver.n_param, 1), **dd),
                  "u_mean": torch.zeros(x.shape[0], **dd)}
             self.solvers.append(solver)
+            self.walks.append(int(walks))
             self.keep += [x, ur]
             self.out.append(o)
             arr[k] = BatchJob(solver._h.value, x.shape[0], x.data_ptr(), int(walks), ur.data_ptr(), int(base),
@@ -543,6 +575,22 @@ class Batch:
 
     def synchronize(self):
         self.stream.synchronize()
+
+    def trace(self, enable: bool = True):
+        """dwos_batch_trace: write per-walk traces in later passes."""
+        self._check(lib().dwos_batch_trace(self._h, 1 if enable else 0))
+
+    def records(self, job: int, trace: bool = False):
+        """Records (numpy RECORD_DTYPE, row p * W + w) and optionally traces ((K + 1) uint32
+        per walk) of job `job` from the last pass (dwos_batch_records)."""
+        sv = self.solvers[job]
+        n = int(self.keep[2 * job].shape[0]) * int(self.walks[job])
+        rec = np.empty(n, dtype=RECORD_DTYPE)
+        K1 = sv.opt.K + 1
+        tr = np.empty(n * K1, dtype=np.uint32) if trace else None
+        self._check(lib().dwos_batch_records(self._h, int(job), rec.ctypes.data_as(ctypes.c_void_p),
+                                             None if tr is None else tr.ctypes.data_as(ctypes.c_void_p), MEM_HOST))
+        return (rec, tr.reshape(n, K1)) if trace else rec
 
     def results(self):
         self.synchronize()
@@ -592,6 +640,11 @@ class ControlVariateNet:
         """Wait for queued work; raises if a tensor-core product timed out."""
         self._stream()
         self._check(lib().dwos_mlp_sync(self._h))
+
+    def wait_probe(self, polls: int):
+        """dwos_mlp_wait_probe: a bounded wait that runs out (raises DwosError TIMEOUT)."""
+        self._stream()
+        self._check(lib().dwos_mlp_wait_probe(self._h, int(polls)))
 
     def params(self):
         self._stream()

@@ -80,21 +80,52 @@ def run_pair(Solver, sc, W, differential=True, base=0, **opt):
     return s, g, o
 
 
-def check_walks(sc, g, o, differential=True, max_flip=0.01):
+def check_walks(sc, g, o, differential=True, max_flip=0.01, u_scale=0.0):
+    """Per-walk agreement on walks whose branch matches.  u_scale: the size of
+    the Dirichlet data when it varies continuously along the boundary.  An FP32
+    walk ends up to about 1e-4 away from its FP64 replay after tens of steps,
+    which moves g(xbar) by |grad g| times that, whatever u's own size (u
+    crosses zero where the data does): the 1e-4 bound is then relative to
+    |u| + u_scale."""
     same = branch_match(sc, g, o, differential)
     frac_flip = 1 - same.mean()
     assert frac_flip <= max_flip, f"{frac_flip:.4f} of walks changed branch"
     ug = g["rec"]["u"].astype(np.float64)
     uo = o["u_hat"]
     err = np.abs(ug - uo)[same]
-    assert np.all(err <= 1e-4 * np.abs(uo[same]) + 1e-5), err.max()
+    assert np.all(err <= 1e-4 * (np.abs(uo[same]) + u_scale) + 1e-5), err.max()
     if differential and sc.n_param:
         dg = gpu_udot(sc, g["rec"])
         do = o["udot"]
         e2 = np.abs(dg - do)[same]
-        tol = 1e-3 * (1 + np.abs(do[same]))
+        tol = 1e-3 * (1 + np.abs(do[same])) + drift_allowance(sc, g["rec"], o)[same]
         assert np.all(e2 <= tol), (e2 / tol).max()
     return same
+
+
+def drift_allowance(sc, rec, o):
+    """What the FP32 end-point drift can move in udot on a matching branch: the
+    vertex weights w_i of the hit element differ between the FP32 walk and its
+    FP64 replay by the measured |dw_i|, and udot is linear in them with
+    coefficients c . J[v_i] + dg[v_i] (see dwos_record).  On short elements a
+    1e-4 drift moves w by a few percent, which matters for data derivatives that
+    vary from vertex to vertex (random dg); smooth Jacobians hardly see it."""
+    n, P = rec.shape[0], sc.n_param
+    out = np.zeros((n, P))
+    hit = (rec["elem"] >= 0) & (o["elem"] >= 0) & (rec["elem"] == o["elem"])
+    e = rec["elem"][hit]
+    wg = np.stack([1 - rec["b1"][hit] - rec["b2"][hit], rec["b1"][hit], rec["b2"][hit]], 1).astype(np.float64)
+    wo = np.stack([1 - o["bary"][hit, 0] - o["bary"][hit, 1], o["bary"][hit, 0], o["bary"][hit, 1]], 1)
+    c = np.abs(rec["c"][hit].astype(np.float64)[:, :sc.dim])
+    acc = np.zeros((hit.sum(), P))
+    for i in range(sc.dim):
+        v = sc.elem[e, i]
+        coef = np.einsum("mk,mkp->mp", c, np.abs(sc.jac[v]))
+        if sc.dg_vert is not None:
+            coef = coef + np.abs(sc.dg_vert[v])
+        acc += np.abs(wg[:, i] - wo[:, i])[:, None] * coef
+    out[hit] = acc
+    return out
 
 
 def test_philox_bit_exact(Solver):

@@ -70,3 +70,68 @@ def test_adjoint_gradient_matches_central_differences(setup):
     print("fd     ", np.round(mf, 4), "+-", np.round(sf, 4))
     assert cos > 0.95, cos
     assert np.all(z < 4.0), z
+
+
+def test_adjoint_matches_central_differences_at_full_size():
+    # The 3D thermal workload at its stated size: the 200,000-triangle icosphere
+    # perturbed by real SH with l <= 8 (81 coefficients, N(0, 0.01^2)), central
+    # differences with h = 1e-3 on every coefficient under common random numbers
+    # (the same seed and walk ids on both sides of each difference), against the
+    # adjoint of DWoSFunction.  Fewer query points than the workload's 4096: 256.
+    # Both estimates repeat 16 times with independent seeds; each coefficient is
+    # compared against the combined standard error (15 degrees of freedom: a
+    # threshold of 5 leaves a 1.6e-4 false-alarm rate per coefficient, about 1 %
+    # over 81) plus a bias budget (10 % of the finite difference for the
+    # eps-shell / backward-difference bias of Sec. 5.3, 2 % of the largest
+    # component).  Most coefficients are below the finite differences' noise
+    # (h = 1e-3 makes each difference a rare-jump estimate with variance of order
+    # 1/h; at this size the differences resolve the l = 0 coefficient), so the
+    # test also requires the adjoint to agree in sign with every coefficient the
+    # differences resolve, and the mean of z^2 over all 81 to stay near 1.
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2405_12964_gb300 import build
+    build.build()
+    from paper_2405_12964_gb300 import dwos
+    sc = scenes.sh_sphere_scene(n_query=256)
+    assert len(sc.elem) >= 200_000 and sc.n_param == 81
+    s = dwos.Solver(0)
+    s.load_scene(sc)
+    s.set_boundary(sc.reference_vertices(), sc.elem, sc.jac)
+    s.set_dirichlet_mapped(sc.g_vert)
+    xq = torch.tensor(sc.query, dtype=torch.float32, device="cuda")
+    R, W, h, P = 16, 1024, 1e-3, sc.n_param
+    g_adj, g_fd = [], []
+    for r in range(R):
+        s.set_options(seed=0x12964 + 31 * r)
+        th = torch.tensor(sc.theta0, dtype=torch.float64).requires_grad_(True)
+        u = dwos.solve(th, s, xq, W, backward_walks=W, backward_base=(1 << 40) + r * (1 << 32))
+        u.mean().backward()
+        g_adj.append(th.grad.numpy().copy())
+        fd = np.zeros(P)
+        for j in range(P):
+            Ls = []
+            for sgn in (1.0, -1.0):
+                tj = sc.theta0.copy()
+                tj[j] += sgn * h
+                s.set_params(tj)
+                Ls.append(float(s.eval(xq, W)["u"].mean()))
+            fd[j] = (Ls[0] - Ls[1]) / (2 * h)
+        g_fd.append(fd)
+    s.set_options(seed=0x12964)
+    A, F = np.array(g_adj), np.array(g_fd)
+    ma, mf = A.mean(0), F.mean(0)
+    sa, sf = A.std(0, ddof=1) / np.sqrt(R), F.std(0, ddof=1) / np.sqrt(R)
+    scale = np.abs(mf).max()
+    z = np.abs(ma - mf) / np.sqrt(sa ** 2 + sf ** 2 + (0.1 * np.abs(mf)) ** 2 + (0.02 * scale) ** 2)
+    cos = float(ma @ mf / (np.linalg.norm(ma) * np.linalg.norm(mf)))
+    print("full size: cos %.4f, max z %.2f, mean z^2 %.2f, median SE adjoint %.2e, FD %.2e"
+          % (cos, z.max(), np.mean(z ** 2), np.median(sa), np.median(sf)))
+    for j in np.argsort(-np.abs(mf))[:8]:
+        print("  c%02d adjoint %+.5f +- %.5f   FD %+.5f +- %.5f" % (j, ma[j], sa[j], mf[j], sf[j]))
+    assert np.all(z < 5.0), (np.argmax(z), z.max())
+    assert np.mean(z ** 2) < 2.0, np.mean(z ** 2)
+    resolved = np.abs(mf) > 4 * sf
+    assert resolved.sum() >= 1 and resolved[0], resolved.sum()
+    assert np.all(np.sign(ma[resolved]) == np.sign(mf[resolved]))

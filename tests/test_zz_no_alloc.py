@@ -6,7 +6,10 @@ a library allocate; this entry point keeps its scratch in a fixed array inside
 the library.  It must return what
 dwos_eval returns for the same walks, call after call (the array is reused and
 keeps the previous call's contents), and refuse requests larger than its
-array.  This file is collected last on purpose.
+array.  The file name sorts last so that pytest collects it last: a run that
+stops at the first failure (-x) has then already run every other test.  The
+tests depend on no earlier test: they pass alone in a fresh process, and after
+the rest of the suite, whatever the array held before.
 """
 import ctypes
 
