@@ -1,6 +1,13 @@
 """The control-variate network's tensor-core kernels against the FP64
-reference (oracle/mlp.py) on the same parameters: loss and gradient, Adam
-steps, evaluation of u, d u / d x and du/dn; and that training fits."""
+reference (oracle/mlp.py: the network with BF16 product operands, exact
+otherwise) on the same parameters: loss and gradient, Adam steps, evaluation
+of u, d u / d x and du/dn; and that training fits.
+
+Loss, gradient and evaluation are compared element by element against the
+bounds oracle/mlp.py derives for an implementation that accumulates in FP32,
+evaluates tanh and the features in FP32, stores BF16 product operands and takes
+tanh' from the stored activation (kernel_grad_bound, eval_bound): every weight
+and bias of every layer must lie within its own bound."""
 import numpy as np
 import pytest
 
@@ -36,29 +43,39 @@ def test_loss_and_gradient_match_reference(net_cls, n):
     net = net_cls.ControlVariateNet(params=p.astype(np.float32))
     x, t, m = _data(n, 2)
     loss, g = net.loss_grad(x, t, m)
-    Lr, Gr = ref.loss_and_grad(p, x, t, m)
+    Lr, Gr, E, EL = ref.kernel_grad_bound(p, x.astype(np.float64), t, m)
     g = g.cpu().numpy().astype(np.float64)
-    assert abs(float(loss[0]) - Lr) <= 1e-4 * abs(Lr)
-    assert np.linalg.norm(g - Gr) <= 2e-3 * np.linalg.norm(Gr), np.linalg.norm(g - Gr) / np.linalg.norm(Gr)
-    # per-layer agreement
-    G, R = ref.unpack(g), ref.unpack(Gr)
-    for k in R:
-        assert np.linalg.norm(G[k] - R[k]) <= 5e-3 * np.linalg.norm(R[k]) + 1e-9, k
+    assert abs(float(loss[0]) - Lr) <= EL, (float(loss[0]), Lr, EL)
+    G, R, B = ref.unpack(g), ref.unpack(Gr), ref.unpack(E)
+    for k in R:          # every weight and bias of every layer
+        ratio = np.abs(G[k] - R[k]) / np.maximum(B[k], 1e-300)
+        assert np.all(np.abs(G[k] - R[k]) <= B[k]), (k, ratio.max(), np.unravel_index(np.argmax(ratio), ratio.shape))
+    used = np.abs(Gr) > 1e-2 * np.abs(Gr).max()
+    print("n=%d: max |gpu - ref| / bound %.3f; median bound / |ref| %.4f"
+          % (n, (np.abs(g - Gr) / np.maximum(E, 1e-300)).max(), np.median(E[used] / np.abs(Gr[used]))))
 
 
 def test_adam_steps_match_reference(net_cls):
+    # Adam on its own: the oracle's Adam applied to the gradient the network's kernel
+    # returns at the same parameters (the kernel is deterministic: fixed-order partial
+    # sums, so train_step sees the same gradient as loss_grad).  The gradient itself is
+    # checked against the definition above.  Tolerance: FP32 evaluation of the update
+    # (about ten roundings of a value of size <= lr / (1 - beta1^t)) and the FP32 store
+    # of the parameters.
     p = ref.init_params(3)
     net = net_cls.ControlVariateNet(params=p.astype(np.float32))
     x, t, m = _data(512, 4)
+    lr = 1e-3
     mom, vel = np.zeros_like(p), np.zeros_like(p)
     q = p.copy()
     for it in range(1, 4):
-        net.train_step(x, t, m, lr=1e-3)
-        _, Gr = ref.loss_and_grad(q, x, t, m)
-        q, mom, vel = ref.adam(q, Gr, mom, vel, it, 1e-3)
-        q = q.astype(np.float32).astype(np.float64)
-    got = net.params().cpu().numpy().astype(np.float64)
-    assert np.abs(got - q).max() <= 3e-5, np.abs(got - q).max()
+        g = net.loss_grad(x, t, m)[1].cpu().numpy().astype(np.float64)
+        net.train_step(x, t, m, lr=lr)
+        q, mom, vel = ref.adam(q, g, mom, vel, it, lr)
+        got = net.params().cpu().numpy().astype(np.float64)
+        tol = 4.0 * np.abs(q) * 2.0 ** -24 + 20 * 2.0 ** -24 * lr / (1 - 0.9 ** it)
+        assert np.all(np.abs(got - q) <= tol), (it, (np.abs(got - q) / tol).max())
+        q = got
 
 
 def test_eval_matches_reference(net_cls):
@@ -67,13 +84,10 @@ def test_eval_matches_reference(net_cls):
     rng = np.random.default_rng(6)
     x = rng.uniform(-0.95, 0.95, size=(300, 2)).astype(np.float32)
     u, gu, q = (a.cpu().numpy() for a in net.eval(x))
-    ur, gr, qr = ref.eval_u(p, x)
-    # same BF16 rounding on both sides; FP32 accumulation order can move an
-    # activation across a BF16 rounding boundary (2^-8 relative) now and then
-    for got, want, tol in ((u, ur, 2e-3), (q, qr, 2e-3), (gu, gr, 5e-3)):
-        scale = np.abs(want).max()
-        assert np.abs(got - want).max() <= tol * scale, np.abs(got - want).max() / scale
-        assert np.median(np.abs(got - want)) <= 1e-4 * scale
+    (ur, gr, qr), (Eu, Eg, Eq) = ref.eval_bound(p, x.astype(np.float64))
+    for name, got, want, E in (("u", u, ur, Eu), ("du/dn", q, qr, Eq), ("grad u", gu, gr, Eg)):
+        err = np.abs(got.astype(np.float64) - want)
+        assert np.all(err <= E), (name, (err / E).max())
 
 
 def test_training_fits_a_smooth_field(net_cls):
