@@ -128,39 +128,6 @@ class ControlVariateTrainer:
         return g
 
 
-
-
-def tangential_gradient(vert: np.ndarray, elem: np.ndarray, g_vert: np.ndarray) -> np.ndarray:
-    """Per element, the surface gradient of the piecewise-linear data g (its
-    interpolant of the vertex values): (g1 - g0) / L^2 (v1 - v0) on a segment,
-    sum_i g_i grad lambda_i on a triangle.  Returns (n_elem, 3)."""
-    vert = np.asarray(vert, dtype=np.float64)
-    g = np.asarray(g_vert, dtype=np.float64)
-    out = np.zeros((elem.shape[0], 3))
-    if elem.shape[1] == 2:
-        d = vert[elem[:, 1]] - vert[elem[:, 0]]
-        out[:, :2] = ((g[elem[:, 1]] - g[elem[:, 0]]) / (d * d).sum(1))[:, None] * d
-        return out
-    a, b, c = vert[elem[:, 0]], vert[elem[:, 1]], vert[elem[:, 2]]
-    N = np.cross(b - a, c - a)
-    n2 = (N * N).sum(1)[:, None]
-    # grad lambda_i = N x (edge opposite i, walked a->b->c) / |N|^2
-    for gi, e in ((g[elem[:, 0]], c - b), (g[elem[:, 1]], a - c), (g[elem[:, 2]], b - a)):
-        out += gi[:, None] * np.cross(N, e) / n2
-    return out
-
-
-def nested_cv_table(vert: np.ndarray, elem: np.ndarray, g_vert: np.ndarray, q) -> np.ndarray:
-    """The nested walks' control-variate table (n_elem, 4): (q, t) with q a
-    du/dn surrogate per element and t the data's tangential gradient, so that
-    q n + t approximates grad u at the boundary (n the walk's oriented normal)."""
-    q = q.detach().cpu().numpy() if isinstance(q, torch.Tensor) else np.asarray(q)
-    tab = np.zeros((elem.shape[0], 4), dtype=np.float32)
-    tab[:, 0] = q
-    tab[:, 1:] = tangential_gradient(vert, elem, g_vert)
-    return tab
-
-
 def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 200, lr: float = 1e-3,
         wpp0: int = 256, wppT: int = 1024, use_cv: bool = False, whole_walk: bool = True, seed: int = 1,
         device: int = 0, target_walks: int = 16384, trainer: Optional[ControlVariateTrainer] = None,

@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle.cv import nested_cv_table
 from oracle import estimators as est
 from paper_2405_12964_gb300 import scenes
 from tests.helpers import to_oracle
@@ -184,7 +185,6 @@ def test_nested_cv_table_matches_oracle(env):
 def test_exact_boundary_gradient_collapses_nested_variance(env):
     # u = x: q = n_x and t = e_x - n_x n give grad u exactly; du/dn keeps only the eps-shell offset
     torch, dwos = env
-    from paper_2405_12964_gb300.optimize import nested_cv_table
     sc = scenes.disk_scene("laplace_x", n_query=32, walks=1024)
     s = dwos.Solver(0)
     s.load_scene(sc)
@@ -209,7 +209,6 @@ def test_exact_boundary_gradient_collapses_nested_variance(env):
 def test_cv_table_matches_host_reference(env):
     # dwos_cv_table: the du/dn head at element centres and the data's tangential gradient
     torch, dwos = env
-    from paper_2405_12964_gb300.optimize import nested_cv_table
     net = dwos.ControlVariateNet(seed=3)
     s = dwos.Solver(0)
     for sc, g in ((scenes.star_box_scene(n_seg=1024, n_query=8), None),

@@ -8,6 +8,7 @@ import oracle
 from oracle import functional as fn
 from paper_2405_12964_gb300 import scenes
 from tests.helpers import to_oracle
+from tests.test_gpu_parity import branch_match, gpu_udot
 
 pytestmark = pytest.mark.gpu
 
@@ -81,13 +82,19 @@ def test_weighted_gradient_matches_oracle(Solver):
     W = 64
     loss, g = (t.cpu().numpy() for t in s.grad_l2_weighted(pts, ur, wt, W))
     o = oracle.run_walks(to_oracle(sc, K=2), p.astype(np.float32).astype(np.float64), W, differential=True)
-    go = fn.grad_l2_weighted(o["u_hat"], o["udot"], ur, wt, len(p), W, 8)
-    lo_ = fn.loss_l2_weighted(o["u_hat"], ur, wt, len(p), W)
-    # ~9k walks: a handful change branch between FP32 and FP64 (each with a 1/h-amplified
-    # du/dn), so the comparison is at 1 % of the largest component; the weighting itself is
-    # checked exactly below (a wrong weight moves the gradient by tens of percent)
-    assert np.allclose(g, go, rtol=1e-2, atol=1e-2 * np.abs(go).max()), np.abs(g - go).max() / np.abs(go).max()
-    assert abs(loss[0] - lo_) <= 1e-3 * abs(lo_) + 1e-8
+    # ~9k walks: a handful change branch between FP32 and FP64, each with a 1/h-amplified
+    # du/dn.  As in the per-walk tests, those walks are identified by their branch (steps and
+    # termination per phase, terminal element) and enter the oracle's estimator with the
+    # GPU's own per-walk values; every other walk is the oracle's
+    rec = s.walk_records(pts, W, trace=True)
+    same = branch_match(sc, rec, o)
+    assert same.mean() >= 0.99, same.mean()
+    u_w = np.where(same, o["u_hat"], rec["rec"]["u"].astype(np.float64))
+    ud_w = np.where(same[:, None], o["udot"], gpu_udot(sc, rec["rec"]))
+    go = fn.grad_l2_weighted(u_w, ud_w, ur, wt, len(p), W, 8)
+    lo_ = fn.loss_l2_weighted(u_w, ur, wt, len(p), W)
+    assert np.allclose(g, go, rtol=3e-3, atol=3e-3 * np.abs(go).max()), np.abs(g - go).max() / np.abs(go).max()
+    assert abs(loss[0] - lo_) <= 1e-4 * abs(lo_) + 1e-8
     # the same walks: unit weights give dwos_grad_l2, constant weights scale it
     g1 = s.grad_l2_weighted(pts, ur, np.ones(len(p), np.float32), W)[1].cpu().numpy()
     g0 = s.grad_l2(pts, ur, W)[1].cpu().numpy()

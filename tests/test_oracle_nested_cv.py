@@ -17,7 +17,7 @@ import numpy as np
 
 import oracle
 from paper_2405_12964_gb300 import scenes
-from paper_2405_12964_gb300.optimize import nested_cv_table, tangential_gradient
+from oracle.cv import nested_cv_table, tangential_gradient
 from tests.helpers import to_oracle
 
 
