@@ -278,6 +278,25 @@ dwos_status dwos_grad_l2_cv(dwos_ctx* ctx, int n_query, const float* xq, const f
  * stream (the network's stream is set to it).  Asynchronous. */
 dwos_status dwos_cv_table(dwos_ctx* ctx, dwos_mlp* mlp, float* table);
 
+/* Training rows for the control-variate network (dwos_mlp_train_step) from
+ * one dwos_grad_l2_cv call's per-walk outputs, all device memory: samples
+ * (n_walks x 4 floats, the call's `samples`) and debug (n_walks records, or
+ * NULL).  The walks offset, offset + stride, ... are used (R = ceil((n_walks -
+ * offset) / stride) of them).  Rows 0 .. R-1 train output 0 (u) at the main
+ * walk's first-step point x1 on its estimate of u there (mask 0 where the walk
+ * never moved).  With debug, rows R .. 2R-1 train output 1 (du/dn) at the hit
+ * point xbar on r / disp_n with r = u_plain - g(xbar) - disp_t and g(xbar) =
+ * u_off + h du/dn (h the context's offset option): the weighted least-squares
+ * fit, weight |disp_n|, of the slope that minimises the variance of the nested
+ * walks' corrected mean, the weights scaled by sqrt(q_weight / mean r^2) over
+ * the hit walks so that both heads' losses have comparable size; rows of walks
+ * that did not reach the shell have mask 0.  x, target and mask receive
+ * 2 x (rows) floats each (room for 2R rows); *n_rows (host) the row count.
+ * Asynchronous on the context's stream. */
+dwos_status dwos_cv_training_set(dwos_ctx* ctx, long long n_walks, const float* samples, const dwos_walk_debug* debug,
+                                 long long stride, long long offset, float q_weight, float* x, float* target,
+                                 float* mask, long long* n_rows);
+
 /* Measurement helper (not part of the method): read bandwidth of an
  * L2-resident buffer of `bytes` bytes on `device`, read `reps` times by a
  * coalesced grid-stride kernel; the roof against which the walk kernel's

@@ -292,7 +292,8 @@ void dwos_destroy(dwos_ctx* ctx) {
     bvh_free(ctx->bvh);
     void* bufs[] = {ctx->vert_ref, ctx->vert, ctx->elem, ctx->jac, ctx->theta, ctx->g_vert, ctx->dg_vert, ctx->rec,
                     ctx->xq, ctx->valid, ctx->wvec, ctx->out, ctx->acc_vert, ctx->trace, ctx->dbg, ctx->misc_f,
-                    ctx->misc_i, ctx->misc_u, ctx->d_prob, ctx->d_ctr, ctx->d_err, ctx->pw, ctx->vert_active};
+                    ctx->misc_i, ctx->misc_u, ctx->d_prob, ctx->d_ctr, ctx->d_err, ctx->pw, ctx->vert_active,
+                    ctx->misc_d};
     for (void* p : bufs) if (p) cudaFree(p);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -828,6 +829,26 @@ dwos_status dwos_cv_table(dwos_ctx* ctx, dwos_mlp* mlp, float* table) {
                                                      reinterpret_cast<float4*>(table));
     CK(cudaGetLastError(), "table");
     ctx->launches += 3;
+    return DWOS_OK;
+}
+
+dwos_status dwos_cv_training_set(dwos_ctx* ctx, long long n_walks, const float* samples, const dwos_walk_debug* debug,
+                                 long long stride, long long offset, float q_weight, float* x, float* target,
+                                 float* mask, long long* n_rows) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (n_walks < 0 || stride < 1 || offset < 0 || (n_walks > 0 && offset >= n_walks))
+        return fail(ctx, DWOS_ERR_INVALID_ARG, "need n_walks >= 0, stride >= 1 and 0 <= offset < n_walks");
+    if (!samples || !x || !target || !mask || !n_rows) return fail(ctx, DWOS_ERR_INVALID_ARG, "NULL argument");
+    if (!(q_weight >= 0.0f) || !std::isfinite(q_weight)) return fail(ctx, DWOS_ERR_INVALID_ARG, "q_weight must be >= 0");
+    for (const void* p : {(const void*)samples, (const void*)debug, (const void*)x, (const void*)target, (const void*)mask})
+        if (dwos_status s = check_device_ptr(ctx, p, "argument")) return s;
+    if (dwos_status s = set_device(ctx)) return s;
+    const long long rows = n_walks > 0 ? (n_walks - offset + stride - 1) / stride : 0;
+    *n_rows = rows * (debug ? 2 : 1);
+    CK(grow(ctx->misc_d, ctx->misc_d_cap, 2), "alloc");
+    CK(launch_cv_rows(reinterpret_cast<const float4*>(samples), debug, rows, offset, stride, ctx->opt.h, q_weight, x,
+                      target, mask, ctx->misc_d, ctx->stream), "training rows");
+    ctx->launches += debug ? 2 : 1;
     return DWOS_OK;
 }
 

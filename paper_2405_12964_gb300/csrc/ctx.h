@@ -45,6 +45,7 @@ struct dwos_ctx {
     float* misc_f = nullptr; size_t misc_f_cap = 0;
     int* misc_i = nullptr; size_t misc_i_cap = 0;
     uint32_t* misc_u = nullptr; size_t misc_u_cap = 0;
+    double* misc_d = nullptr; size_t misc_d_cap = 0;
     dwos::DevProblem* d_prob = nullptr;
     dwos::DevCounters* d_ctr = nullptr;
     int* d_err = nullptr;

@@ -151,6 +151,10 @@ cudaError_t launch_bessel_k0(int n, const float* x, float* out, cudaStream_t str
 // mean / SE of the first `used` (0: all W) walks of each point
 cudaError_t launch_reduce_u(const dwos_record* rec, int n_points, int W, double* mean, double* se,
                             cudaStream_t stream, const CvView* cv = nullptr, int used = 0);
+// the control-variate network's training rows from thinned walks (see dwos_cv_training_set)
+cudaError_t launch_cv_rows(const float4* samples, const dwos_walk_debug* dbg, long long n_rows, long long off,
+                           long long stride, float h, float q_weight, float* x, float* t, float* m, double* acc,
+                           cudaStream_t stream);
 // per-walk training samples: s.w <- u - s.w (the estimate of u at x1) where x1 exists
 cudaError_t launch_pack_samples(const dwos_record* rec, float4* samples, long long n, cudaStream_t stream);
 cudaError_t launch_reduce_udot(const dwos_record* rec, const int* elem, const float* jac, const float* dg,

@@ -336,6 +336,81 @@ __global__ void pack_samples_kernel(const dwos_record* __restrict__ rec, float4*
     samples[i] = s;
 }
 
+// Training rows of the control-variate network from one gradient step's walks,
+// thinned to the walks off, off + stride, ...  Row r < n_rows (walk i = off + r
+// stride) trains the u head on (x1, estimate of u at x1) where the main walk
+// moved; row n_rows + r trains the du/dn head at the walk's hit point xbar on
+// y = r_i / disp_n with r_i = u_plain - g(xbar) - disp_t and g(xbar) = u_off +
+// h du/dn, the least-squares fit of the nested walks' normal displacement
+// (weight |disp_n|, scaled afterwards).  Accumulates sum r_i^2 and the hit
+// count for that scale.
+__global__ void cv_rows_kernel(const float4* __restrict__ samples, const dwos_walk_debug* __restrict__ dbg,
+                               long long n_rows, long long off, long long stride, float h, float* __restrict__ x,
+                               float* __restrict__ t, float* __restrict__ m, double* __restrict__ acc) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double r2 = 0.0, cnt = 0.0;
+    if (r < n_rows) {
+        const long long i = off + r * stride;
+        const float4 s = samples[i];
+        const bool ok = s.x == s.x;
+        x[2 * r] = ok ? s.x : 0.0f;
+        x[2 * r + 1] = ok ? s.y : 0.0f;
+        t[2 * r] = ok ? s.w : 0.0f;
+        t[2 * r + 1] = 0.0f;
+        m[2 * r] = ok ? 1.0f : 0.0f;
+        m[2 * r + 1] = 0.0f;
+        if (dbg) {
+            const dwos_walk_debug d = dbg[i];
+            const bool hit = (d.n[0] != 0.0f || d.n[1] != 0.0f) && fabsf(d.disp_n) > 1e-7f;
+            const float g = d.u_off + h * d.dudn;
+            const float res = hit ? d.u_plain - g - d.disp_t : 0.0f;
+            const long long q = n_rows + r;
+            x[2 * q] = hit ? d.xbar[0] : 0.0f;
+            x[2 * q + 1] = hit ? d.xbar[1] : 0.0f;
+            t[2 * q] = 0.0f;
+            t[2 * q + 1] = hit ? res / d.disp_n : 0.0f;
+            m[2 * q] = 0.0f;
+            m[2 * q + 1] = hit ? fabsf(d.disp_n) : 0.0f;     // times the scale below
+            r2 = (double)res * res;
+            cnt = hit ? 1.0 : 0.0;
+        }
+    }
+    if (!dbg) return;
+    for (int o = 16; o > 0; o >>= 1) {
+        r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+        cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if ((threadIdx.x & 31) == 0 && cnt > 0.0) {
+        atomicAdd(acc, r2);
+        atomicAdd(acc + 1, cnt);
+    }
+}
+
+// du/dn rows' weights times sqrt(q_weight / mean r^2): the two heads' losses on
+// a common scale whatever the size of the nested residuals.
+__global__ void cv_scale_kernel(long long n_rows, float q_weight, const double* __restrict__ acc,
+                                float* __restrict__ m) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rows) return;
+    const double mean_r2 = acc[0] / fmax(acc[1], 1.0);
+    const float scale = (float)sqrt((double)q_weight / fmax(mean_r2, 1e-12));
+    m[2 * (n_rows + r) + 1] *= scale;
+}
+
+cudaError_t launch_cv_rows(const float4* samples, const dwos_walk_debug* dbg, long long n_rows, long long off,
+                           long long stride, float h, float q_weight, float* x, float* t, float* m, double* acc,
+                           cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    if (dbg) {
+        cudaError_t e = cudaMemsetAsync(acc, 0, 2 * sizeof(double), s);
+        if (e != cudaSuccess) return e;
+    }
+    const unsigned blocks = (unsigned)((n_rows + 255) / 256);
+    cv_rows_kernel<<<blocks, 256, 0, s>>>(samples, dbg, n_rows, off, stride, h, x, t, m, acc);
+    if (dbg) cv_scale_kernel<<<blocks, 256, 0, s>>>(n_rows, q_weight, acc, m);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pack_samples(const dwos_record* rec, float4* samples, long long n, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     pack_samples_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(rec, samples, n);

@@ -107,6 +107,8 @@ _SIGS = {
     "dwos_mlp_wait_probe": [_vp, _i],
     "dwos_set_traversal_budget": [_vp, _i],
     "dwos_cv_table": [_vp, _vp, _vp],
+    "dwos_cv_training_set": [_vp, ctypes.c_longlong, _vp, _vp, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_float,
+                             _vp, _vp, _vp, ctypes.POINTER(ctypes.c_longlong)],
     "dwos_bvh_info": [_vp, _vp],
     "dwos_probe_l2_read": [_i, ctypes.c_size_t, _i, _vp],
     "dwos_sample_domain": [_vp, _i, _vp, _vp, _u64, _vp, _vp, _vp],
@@ -421,6 +423,22 @@ class Solver:
         out = torch.empty(self.n_elem, 4, device=self.device, dtype=torch.float32)
         self._check(lib().dwos_cv_table(self._h, net._h, _ptr(out)))
         return out
+
+    def cv_training_set(self, samples: torch.Tensor, debug: Optional[torch.Tensor], stride: int, offset: int,
+                        q_weight: float):
+        """dwos_cv_training_set: (x, target, mask) device tensors of the network's
+        training rows from a grad_l2_cv call's samples / debug records."""
+        self._stream()
+        n = samples.shape[0]
+        rows = (n - offset + stride - 1) // stride * (2 if debug is not None else 1)
+        x = torch.empty(rows, 2, device=self.device, dtype=torch.float32)
+        t = torch.empty(rows, 2, device=self.device, dtype=torch.float32)
+        m = torch.empty(rows, 2, device=self.device, dtype=torch.float32)
+        got = ctypes.c_longlong()
+        self._check(lib().dwos_cv_training_set(self._h, n, _ptr(samples), _ptr(debug), int(stride), int(offset),
+                                               float(q_weight), _ptr(x), _ptr(t), _ptr(m), ctypes.byref(got)))
+        assert got.value == rows
+        return x, t, m
 
     def walk_records(self, xq, walks: int, walk_id_base: int = 0, differential: bool = True,
                      trace: bool = False, debug: bool = False):

@@ -77,51 +77,25 @@ class ControlVariateTrainer:
         self.q_weight = q_weight     # weight of the du/dn head's (normalised) variance loss against the u head's
         self.rng = np.random.default_rng(seed)
 
-    def update(self, samples: torch.Tensor, debug: Optional[torch.Tensor]) -> float:
-        """Train on one gradient step's walks.  Fixed-size tensors with zero
-        weights for unusable rows keep the host out of the loop (no sync).
-        The rows (one per walk for the u head, one per walk for the du/dn head)
-        are thinned to at most max_samples by a common stride with a random
-        offset before any other work."""
+    def update(self, solver: "dwos.Solver", samples: torch.Tensor, debug: Optional[torch.Tensor]) -> torch.Tensor:
+        """Train on one gradient step's walks.  The training rows (one per walk
+        for the u head, one per walk for the du/dn head, thinned to at most
+        max_samples by a common stride with a random offset) are built on the
+        device by dwos_cv_training_set: the u head learns the walks' estimates
+        at their first-step points; the du/dn head learns, at each hit point,
+        the slope q that minimises the variance of the corrected nested mean
+        u_plain - disp_t - q disp_n (a least-squares fit of r / disp_n with
+        weights disp_n^2, r = u_plain - g(xbar) - disp_t; centring on g keeps
+        the fit's noise at Var(u)).  Returns the last iteration's loss as a
+        device tensor: nothing here waits for the GPU."""
         n_rows = samples.shape[0] * (2 if debug is not None else 1)
         stride = max(1, (n_rows + self.max_samples - 1) // self.max_samples)
         off = int(self.rng.integers(stride))
-        samples = samples[off::stride]
-        xs = samples[:, :2]
-        ok = ~torch.isnan(xs[:, 0])
-        zero = torch.zeros_like(samples[:, 0])
-        parts_x = [torch.where(ok[:, None], xs, torch.zeros_like(xs))]
-        parts_t = [torch.stack([torch.where(ok, samples[:, 3], zero), zero], 1)]
-        parts_m = [torch.stack([ok.to(zero.dtype), zero], 1)]
-        if debug is not None:
-            # dwos_walk_debug: dudn, n[3], u_off, xbar[3], u_plain, disp_n, disp_t, elem
-            rec = debug.view(torch.float32).view(-1, 12)[off::stride]
-            dudn, u_off, xb, u_plain, dn, dt = rec[:, 0], rec[:, 4], rec[:, 5:7], rec[:, 8], rec[:, 9], rec[:, 10]
-            zero = torch.zeros_like(dudn)
-            hit = ((rec[:, 1] != 0) | (rec[:, 2] != 0)) & (dn.abs() > 1e-7)
-            # The du/dn head q weights the nested walks' normal displacement; the
-            # corrected nested mean u_plain - disp_t - q disp_n keeps its mean for
-            # any q and has the least variance where q minimises
-            # E[(r - q disp_n)^2], r = u_plain - g(xbar) - disp_t, i.e. the
-            # least-squares fit of r / disp_n with weights disp_n^2 (the normal
-            # derivative itself where u is linear on the scale of the nested walks).
-            # Centring on g = u_off + h du/dn keeps the fit's noise at Var(u).
-            hf = hit.to(zero.dtype)
-            g = u_off + self.h * dudn
-            r = (u_plain - g - dt) * hf
-            d = torch.where(hit, dn, torch.ones_like(dn))
-            y = r / d
-            r2 = (r * r).sum() / hf.sum().clamp_min(1.0)
-            w = torch.sqrt(self.q_weight / r2.clamp_min(1e-12)) * dn.abs() * hf
-            parts_x.append(torch.where(hit[:, None], xb, torch.zeros_like(xb)))
-            parts_t.append(torch.stack([zero, y], 1))
-            parts_m.append(torch.stack([zero, w], 1))
-        x = torch.cat(parts_x).contiguous()
-        t = torch.cat(parts_t).contiguous()
-        m = torch.cat(parts_m).contiguous()
-        losses = [self.net.train_step(x, t, m, lr=self.lr) for _ in range(self.iters)]
-        self.net.sync()
-        return float(losses[-1][0])
+        x, t, m = solver.cv_training_set(samples, debug, stride, off, self.q_weight)
+        loss = None
+        for _ in range(self.iters):
+            loss = self.net.train_step(x, t, m, lr=self.lr)
+        return loss
 
     def grad_at(self, xq) -> torch.Tensor:
         _, g, _ = self.net.eval(xq)
@@ -159,7 +133,7 @@ def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 2
                            whole_walk=whole_walk, cv_elem=cv_elem, samples=train, debug=train)
         g = out["grad"].cpu().numpy()
         if train:
-            hist.mlp_loss.append(trainer.update(out["samples"], out["debug"]))
+            hist.mlp_loss.append(trainer.update(s, out["samples"], out["debug"]))
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         total += dt
@@ -171,6 +145,9 @@ def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 2
         if use_cv:
             r = (out["u_se_cv"] / out["u_se"].clamp_min(1e-30)).cpu().numpy() ** 2
             hist.var_ratio.append(float(np.median(r)))
+    if use_cv:
+        trainer.net.sync()                               # reports a timed-out tensor-core wait, if any
+        hist.mlp_loss = [float(l[0]) for l in hist.mlp_loss]
     return opt.theta, hist, trainer
 
 

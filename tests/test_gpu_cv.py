@@ -220,3 +220,44 @@ def test_cv_table_matches_host_reference(env):
         g_vert = sc.vert[:, 0] if g == "x" else sc.g_vert       # g = x is linear: its tangential gradient is exact
         ref = nested_cv_table(sc.vert, sc.elem, g_vert, q)
         assert np.allclose(tab, ref, rtol=1e-4, atol=1e-5), np.abs(tab - ref).max()
+
+
+def test_cv_training_set_matches_its_definition(env):
+    # dwos_cv_training_set: the network's training rows built on the device from one
+    # dwos_grad_l2_cv call's per-walk samples and debug records, against the rows
+    # written out here from the same per-walk values
+    torch, dwos = env
+    sc = scenes.star_box_scene(n_seg=1024, n_query=16, walks=64)
+    s = dwos.Solver(0)
+    s.load_scene(sc)
+    net = dwos.ControlVariateNet(seed=2)
+    xq = torch.tensor(sc.query, dtype=torch.float32, device="cuda")
+    out = s.grad_l2_cv(xq, sc.u_ref, sc.walks, cv_grad=net.eval(xq)[1], whole_walk=True, cv_elem=s.cv_table(net),
+                       samples=True, debug=True)
+    smp = out["samples"].cpu().numpy().astype(np.float64)
+    dbg = out["debug"].view(torch.float32).view(-1, 12).cpu().numpy().astype(np.float64)
+    n = smp.shape[0]
+    for stride, off, qw in ((1, 0, 0.2), (3, 2, 0.5)):
+        x, t, m = (a.cpu().numpy().astype(np.float64) for a in s.cv_training_set(out["samples"], out["debug"],
+                                                                                 stride, off, qw))
+        idx = np.arange(off, n, stride)
+        R = len(idx)
+        assert x.shape == (2 * R, 2)
+        sm, d = smp[idx], dbg[idx]
+        ok = ~np.isnan(sm[:, 0])
+        assert np.array_equal(x[:R][ok], sm[ok, :2]) and np.all(x[:R][~ok] == 0)
+        assert np.array_equal(t[:R, 0][ok], sm[ok, 3]) and np.all(t[:R, 1] == 0)
+        assert np.array_equal(m[:R, 0], ok.astype(float)) and np.all(m[:R, 1] == 0)
+        dudn, nx, ny, u_off, xb, u_plain, dn, dt = d[:, 0], d[:, 1], d[:, 2], d[:, 4], d[:, 5:7], d[:, 8], d[:, 9], d[:, 10]
+        hit = ((nx != 0) | (ny != 0)) & (np.abs(dn) > 1e-7)
+        res = np.where(hit, u_plain - (u_off + sc.h * dudn) - dt, 0.0)
+        y = np.where(hit, res / np.where(hit, dn, 1.0), 0.0)
+        scale = np.sqrt(qw / max((res ** 2).sum() / max(hit.sum(), 1), 1e-12))
+        assert np.array_equal(x[R:][hit], xb[hit]) and np.all(x[R:][~hit] == 0)
+        assert np.all(t[R:, 0] == 0) and np.all(m[R:, 0] == 0)
+        # the kernel forms the residual in FP32: a few roundings of the terms it subtracts
+        tol_y = 4 * 2.0 ** -24 * (np.abs(u_plain) + np.abs(u_off) + np.abs(sc.h * dudn) + np.abs(dt)) \
+            / np.where(hit, np.abs(dn), 1.0) + 1e-6 * np.abs(y)
+        assert np.all(np.abs(t[R:, 1] - y) <= tol_y), (np.abs(t[R:, 1] - y) / tol_y).max()
+        assert np.allclose(m[R:, 1], scale * np.abs(dn) * hit, rtol=1e-4, atol=0)
+        assert hit.sum() > 0.1 * R
