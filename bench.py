@@ -11,6 +11,12 @@ nested walks per second, whole job), ms per step, gradient estimates/s,
 gradient RMSE x seconds, the walk kernel's roofline entry, the oracle's CPU
 baseline on a bounded sample, the end-to-end figure through the C ABI with
 host buffers, launch count and SM clocks sampled during the timed region.
+After the C2 figures, and outside their timed region, the same line carries
+the other configurations' headline figures (about a minute in all; skip with
+--no-extras): "c3" walk-steps/s of the 200k-triangle 3D workload, "c4" the
+64-problem batch against the same problems as separate calls, "c5" the
+learned control variate against the plain estimator (equal-time final
+losses over three seeds, gradient RMSE x seconds per estimate).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 """
@@ -226,9 +232,10 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batched(args):
+def batched_summary(steps: int, warmup: int):
     """Config 4: the 64 problems as separate dwos_grad_l2 calls (the plain GPU
-    path) and as one batched, autotuned, graph-captured pass."""
+    path) and as one batched, autotuned, graph-captured pass (walk-steps/s of
+    each, the speed-up, the autotuned launch shapes, clocks)."""
     import numpy as np
     import torch
     from paper_2405_12964_gb300 import build, scenes
@@ -244,17 +251,15 @@ def run_batched(args):
     us = [torch.tensor(sc.u_ref, dtype=torch.float32, device="cuda") for sc in probs]
 
     def plain(i):
-        steps = 0
         for k, (sc, s) in enumerate(zip(probs, solvers)):
             s.grad_l2(xs[k], us[k], sc.walks, walk_id_base=(i + 1) << 32)
-        return steps
 
-    for i in range(args.warmup):
+    for i in range(warmup):
         plain(i)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t_plain = []
-    for i in range(args.steps):
+    for i in range(steps):
         e0.record()
         plain(100 + i)
         e1.record()
@@ -263,14 +268,14 @@ def run_batched(args):
     b = Batch([(s, xs[k], sc.walks, us[k], 7 << 32) for k, (sc, s) in enumerate(zip(probs, solvers))])
     b.autotune(reps=1)
     b.capture()
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         b.launch()
     b.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
     time.sleep(0.3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for i in range(args.steps):
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
         ev[i][0].record(b.stream)
         b.launch()
         ev[i][1].record(b.stream)
@@ -278,45 +283,46 @@ def run_batched(args):
     clk = clocks.stop()
     t_b = [a.elapsed_time(c) for a, c in ev]
     st = b.stats()
-    steps = st["steps_main"] + st["steps_nested"]
-    value = steps / (np.mean(t_b) / 1e3)
-    plain_value = steps / (np.mean(t_plain) / 1e3)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": float(np.mean(t_b)), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS["c4"], "problems": len(probs),
-                       "walks": int(sum(sc.query.shape[0] * sc.walks for sc in probs)),
-                       "autotuned": {"2d": b.config(2), "3d": b.config(3)}},
-            "plain": {"value": plain_value, "ms_per_step": float(np.mean(t_plain)),
-                      "note": "same 64 problems as separate dwos_grad_l2 calls"},
-            "speedup_vs_plain": float(np.mean(t_plain) / np.mean(t_b)),
-            "walk_steps_per_step": steps, "clocks": clk}
+    walk_steps = st["steps_main"] + st["steps_nested"]
+    return {"workload": WORKLOADS["c4"], "problems": len(probs),
+            "walks": int(sum(sc.query.shape[0] * sc.walks for sc in probs)),
+            "value": walk_steps / (np.mean(t_b) / 1e3), "unit": UNIT, "ms_per_pass": float(np.mean(t_b)),
+            "plain": {"value": walk_steps / (np.mean(t_plain) / 1e3), "ms_per_pass": float(np.mean(t_plain)),
+                      "note": "the same 64 problems as separate dwos_grad_l2 calls"},
+            "speedup_vs_plain": float(np.mean(t_plain) / np.mean(t_b)), "walk_steps_per_pass": walk_steps,
+            "autotuned": {"2d": b.config(2), "3d": b.config(3)}, "steps": steps, "warmup": warmup, "clocks": clk}
+
+
+def run_batched(args):
+    r = batched_summary(args.steps, args.warmup)
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_pass"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["c4"], "problems": r["problems"], "walks": r["walks"],
+                       "autotuned": r["autotuned"]},
+            "plain": r["plain"], "speedup_vs_plain": r["speedup_vs_plain"],
+            "walk_steps_per_step": r["walk_steps_per_pass"], "clocks": r["clocks"]}
     print(json.dumps(line), flush=True)
 
 
-def run_control_variate(args):
-    """Config 5: the same optimisation with and without the learned control
-    variate; variance reduction and gradient RMSE x seconds at equal walks."""
+def control_variate_summary(seeds=(3, 4, 5), steps: int = 200):
+    """Config 5: the optimisation of the 2D shape-from-diffusion workload with
+    and without the learned control variate, per seed: final losses of the CV
+    run, of a plain run of the same number of steps and of a plain run given
+    the CV run's wall time (training included); and the gradient RMSE x seconds
+    of one estimate (network inference timed) at the start shape and midway."""
     import numpy as np
     import torch
     from paper_2405_12964_gb300 import build, scenes
     build.build()
     from paper_2405_12964_gb300 import optimize
+    from paper_2405_12964_gb300.dwos import Solver
     sc = scenes.star_box_scene()
     target = sc.theta0.copy()
     start = np.zeros_like(target)
-    steps = 200
     # warm-up (module loading and first-use costs of both paths stay out of the timed runs)
     optimize.run(sc, target, start, steps=3, use_cv=False, seed=99)
     optimize.run(sc, target, start, steps=3, use_cv=True, whole_walk=True, seed=99)
-    th_p, hp, _ = optimize.run(sc, target, start, steps=steps, use_cv=False, seed=3)
-    th_c, hc, trainer = optimize.run(sc, target, start, steps=steps, use_cv=True, whole_walk=True, seed=3)
-    # equal wall time: the plain optimiser gets the seconds the CV run took (training included)
-    steps_eq = max(steps, int(round(steps * hc.seconds[-1] / max(hp.seconds[-1], 1e-9))))
-    th_e, he, _ = optimize.run(sc, target, start, steps=steps_eq, use_cv=False, seed=3)
-    # gradient quality at the starting shape, equal walks per point
-    s_uref = None
-    from paper_2405_12964_gb300.dwos import Solver
     s = Solver(0)
     s.load_scene(sc)
     s.set_boundary(sc.reference_vertices(), sc.elem, sc.jac)
@@ -324,7 +330,6 @@ def run_control_variate(args):
     s.set_params(target)
     xq = torch.tensor(sc.query, dtype=torch.float32, device="cuda")
     s_uref = s.eval(xq, 16384)["u"].cpu().numpy()
-    mid = 0.5 * (start + target)
 
     def true_loss(theta):          # the loss of a final shape, from 16384 walks per point
         s.set_params(theta)
@@ -332,27 +337,85 @@ def run_control_variate(args):
         s.set_params(target)
         return float(0.5 * np.sum((u - s_uref) ** 2))
 
+    clocks = ClockSampler(0)
+    clocks.start()
+    runs, trainer = [], None
+    for seed in seeds:
+        th_p, hp, _ = optimize.run(sc, target, start, steps=steps, use_cv=False, seed=seed)
+        th_c, hc, trainer = optimize.run(sc, target, start, steps=steps, use_cv=True, whole_walk=True, seed=seed)
+        # equal wall time: the plain optimiser gets the seconds the CV run took (training included)
+        steps_eq = max(steps, int(round(steps * hc.seconds[-1] / max(hp.seconds[-1], 1e-9))))
+        th_e, he, _ = optimize.run(sc, target, start, steps=steps_eq, use_cv=False, seed=seed)
+        lc, lp, le = true_loss(th_c), true_loss(th_p), true_loss(th_e)
+        runs.append({"seed": seed, "cv": {"final_loss": lc, "seconds": hc.seconds[-1],
+                                          "median_var_ratio_last20": float(np.median(hc.var_ratio[-20:]))},
+                     "plain": {"final_loss": lp, "seconds": hp.seconds[-1]},
+                     "plain_equal_time": {"final_loss": le, "seconds": he.seconds[-1], "steps": steps_eq},
+                     "ratio_cv_over_plain_equal_time": lc / le})
+    clk = clocks.stop()
+    ratios = np.array([r["ratio_cv_over_plain_equal_time"] for r in runs])
+    mid = 0.5 * (start + target)
     rows = {}
     for name, th in [("start", start), ("midway", mid)]:
         plain = optimize.gradient_rmse_x_time(sc, th, s_uref, 1024)
         cv = optimize.gradient_rmse_x_time(sc, th, s_uref, 1024, net=trainer.net, whole_walk=True)
-        nested = optimize.gradient_rmse_x_time(sc, th, s_uref, 1024, net=trainer.net, main=False)
-        rows[name] = {"plain": plain, "cv": cv, "nested_only": nested,
-                      "rmse_x_seconds_ratio": cv["rmse_x_seconds"] / plain["rmse_x_seconds"]}
-    line = {"metric": METRIC, "value": rows["start"]["cv"]["rmse_x_seconds"], "unit": "gradient RMSE x s",
-            "higher_is_better": False, "n_gpus": 1, "steps": steps, "warmup": 0, "vs_baseline": None,
-            "dtype": "f32 walks, bf16 MLP", "data": "synthetic",
-            "config": {"workload": WORKLOADS["c5"]},
-            "plain_run": {"steps": steps, "final_loss": true_loss(th_p), "theta_err": hp.theta_err[-1],
-                          "seconds": hp.seconds[-1]},
-            "cv_run": {"steps": steps, "final_loss": true_loss(th_c), "theta_err": hc.theta_err[-1],
-                       "seconds": hc.seconds[-1], "median_var_ratio_last20": float(np.median(hc.var_ratio[-20:])),
-                       "mlp_loss_last": hc.mlp_loss[-1]},
-            "plain_run_equal_time": {"steps": steps_eq, "final_loss": true_loss(th_e), "theta_err": he.theta_err[-1],
-                                     "seconds": he.seconds[-1]},
+        rows[name] = {"plain": plain, "cv": cv, "rmse_x_seconds_ratio": cv["rmse_x_seconds"] / plain["rmse_x_seconds"]}
+    return {"workload": WORKLOADS["c5"], "steps": steps, "runs": runs,
+            "equal_time_final_loss_ratio": {"geometric_mean": float(np.exp(np.mean(np.log(ratios)))),
+                                            "min": float(ratios.min()), "max": float(ratios.max()),
+                                            "seeds": list(seeds)},
             "final_loss_note": "1/2 sum (u - u_target)^2 of the final shape, u from 16384 walks per point",
-            "gradient_rmse_x_seconds": rows}
+            "gradient_rmse_x_seconds": rows, "clocks": clk}
+
+
+def run_control_variate(args):
+    r = control_variate_summary()
+    line = {"metric": METRIC, "value": r["gradient_rmse_x_seconds"]["start"]["cv"]["rmse_x_seconds"],
+            "unit": "gradient RMSE x s", "higher_is_better": False, "n_gpus": 1, "steps": r["steps"], "warmup": 0,
+            "vs_baseline": None, "dtype": "f32 walks, bf16 MLP", "data": "synthetic",
+            "config": {"workload": WORKLOADS["c5"]}}
+    line.update({k: v for k, v in r.items() if k != "workload"})
     print(json.dumps(line), flush=True)
+
+
+def thermal_summary(steps: int, warmup: int):
+    """Config 3 at its stated size: walk-steps/s of the U-statistic gradient of
+    1/2 sum u^2 over 4096 points x 2048 differential walks on the 200k-triangle
+    SH sphere (inputs resident, L2 flushed between timed steps)."""
+    import numpy as np
+    import torch
+    from paper_2405_12964_gb300 import build
+    build.build()
+    from paper_2405_12964_gb300.dwos import Solver
+    sc = make_scene("c3")
+    s = Solver(0)
+    s.load_scene(sc, traversal=3)
+    xq = torch.tensor(sc.query, dtype=torch.float32, device="cuda")
+    uref = torch.tensor(sc.u_ref, dtype=torch.float32, device="cuda")
+    total = sc.query.shape[0] * sc.walks
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for i in range(warmup):
+        s.grad_l2(xq, uref, sc.walks, walk_id_base=(i + 1) * total)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    t, walk_steps, kms = [], 0, []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for i in range(steps):
+        flush.fill_(float(i))
+        e0.record()
+        s.grad_l2(xq, uref, sc.walks, walk_id_base=(warmup + i + 1) * total)
+        e1.record()
+        st = s.stats()
+        t.append(e0.elapsed_time(e1))
+        walk_steps += st["steps_main"] + st["steps_nested"]
+        kms.append(st["kernel_ms"])
+    clk = clocks.stop()
+    return {"workload": WORKLOADS["c3"], "value": walk_steps / (sum(t) / 1e3), "unit": UNIT,
+            "ms_per_step": float(np.mean(t)), "walk_kernel_ms": float(np.mean(kms)),
+            "walk_steps_per_step": walk_steps / steps, "elements": int(len(sc.elem)), "steps": steps,
+            "warmup": warmup, "clocks": clk}
 
 
 def run_ablation(args):
@@ -420,6 +483,8 @@ def main():
     ap.add_argument("--walks", type=int, default=0, help="walks per point (0: the workload's)")
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the C3 / C4 / C5 summaries that the default line carries after the C2 figures")
     ap.add_argument("--traversal", type=int, default=-1,
                     help="closest-point search: 0 binary per lane, 1 climb, 2 32-wide warp-wide, 3 routed "
                          "(only queries that reach inside the binary root's child boxes are searched, warp-wide; "
@@ -585,8 +650,13 @@ def main():
             "closest_point_search": {"nodes_per_query": nodes / max(steps_done, 1),
                                      "wide_nodes_per_query": wnodes / max(steps_done, 1),
                                      "element_fetches_per_query": prims / max(steps_done, 1)},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "roofline": {"bound": "latency", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm,
+                         "bound_note": ("ncu: dependent-instruction and L1/L2 latency (fixed-latency and "
+                                        "long-scoreboard stalls, about a third of the warp slots active); the "
+                                        "tree bytes come from L1/L2, DRAM sees under 0.01 % of them, so the frac "
+                                        "against the HBM copy peak is a bandwidth-equivalent figure, not a "
+                                        "binding roof"),
                          "traffic": (None if traffic_per_step is None
                                      else traffic_per_step * steps_done / args.steps),
                          "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch, "
@@ -602,6 +672,13 @@ def main():
             "gpu_launches": int(launches),
             "clocks": clk,
         }
+        if world == 1 and not args.no_extras and args.workload == "c2":
+            # the other configurations' headline figures, measured after the C2 timed region
+            t_x = time.perf_counter()
+            line["c3"] = thermal_summary(steps=5, warmup=2)
+            line["c4"] = batched_summary(steps=3, warmup=2)
+            line["c5"] = control_variate_summary()
+            line["extras_seconds"] = time.perf_counter() - t_x
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
