@@ -71,6 +71,7 @@ class _Scene(ctypes.Structure):
         ("seed_hi", ctypes.c_uint32),
         ("cv_elem", ctypes.POINTER(ctypes.c_double)),
         ("dudn_mode", ctypes.c_int),
+        ("neumann", ctypes.POINTER(ctypes.c_int)),
     ]
 
 
@@ -115,6 +116,8 @@ def lib():
             L.oracle_source_weight.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                ctypes.c_double]
             L.oracle_source_weight.restype = ctypes.c_double
+            L.oracle_star_weight.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
+            L.oracle_star_weight.restype = ctypes.c_double
             L.oracle_bessel_k0.argtypes = [ctypes.c_double]
             L.oracle_bessel_k0.restype = ctypes.c_double
             L.oracle_gradient_factor.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
@@ -166,6 +169,7 @@ class Problem:
     seed: int = 0x12964
     cv_elem: Optional[np.ndarray] = None      # (n_elem, 4): q, t of the nested walks' surrogate grad u = q n + t
     dudn_mode: int = 0                        # 0: backward difference (Eq. dudn_fd_estimate), 1: ball gradient
+    neumann: Optional[np.ndarray] = None      # (n_elem,) flags: 1 for elements of the reflecting Neumann part
     _keep: list = dc_field(default_factory=list, repr=False)
 
     @property
@@ -183,7 +187,8 @@ class Problem:
         g = None if self.g_vert is None else np.ascontiguousarray(self.g_vert, dtype=np.float64)
         dg = None if self.dg_vert is None else np.ascontiguousarray(self.dg_vert, dtype=np.float64)
         cq = None if self.cv_elem is None else np.ascontiguousarray(self.cv_elem, dtype=np.float64).reshape(-1, 4)
-        self._keep = [v, e, jac, g, dg, cq]
+        nm = None if self.neumann is None else np.ascontiguousarray(self.neumann, dtype=np.int32)
+        self._keep = [v, e, jac, g, dg, cq, nm]
         s = _Scene()
         s.dim = v.shape[1]
         s.n_vert = v.shape[0]
@@ -211,6 +216,7 @@ class Problem:
         s.seed_hi = (self.seed >> 32) & 0xFFFFFFFF
         s.cv_elem = _dp(cq)
         s.dudn_mode = int(self.dudn_mode)
+        s.neumann = _ip(nm)
         return s
 
 
@@ -233,6 +239,11 @@ def alpha(dim: int, sigma: float, d: float) -> float:
 def source_weight(dim: int, sigma: float, d: float, rho: float) -> float:
     """|B(d)| * G_d(rho d): Algorithm 1's source weight per unit source."""
     return lib().oracle_source_weight(dim, sigma, d, rho)
+
+
+def star_weight(dim: int, sigma: float, t: float, R: float) -> float:
+    """Survival weight of a walk-on-stars step of length t in the ball of radius R."""
+    return lib().oracle_star_weight(dim, sigma, t, R)
 
 
 def bessel_k0(x: float) -> float:

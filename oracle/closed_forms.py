@@ -134,3 +134,54 @@ def expected_exit_weight(dim: int, sigma: float, d: float) -> float:
     k = np.sqrt(sigma) * d
     alpha = 1.0 / iv(0, k) if dim == 2 else k / np.sinh(k)
     return (1.0 - alpha) / sigma
+
+
+# ----------------------------------------------- mixed Dirichlet-Neumann boundaries
+def quarter_disk(x, data: str):
+    """Quarter disk, Dirichlet arc r = R, reflecting Neumann radii on the axes,
+    sigma = 0, R = 1: u = x^2 - y^2 (harmonic, zero normal derivative on both
+    axes).  theta = [R] scales the domain: for field data g = x^2 - y^2 the
+    solution does not change (du/dR = 0); for mapped data g = cos 2t,
+    u = (r/R)^2 cos 2 phi, du/dR = -2 (x^2 - y^2)."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    u = x[:, 0] ** 2 - x[:, 1] ** 2
+    du = np.zeros_like(u) if data == "field" else -2.0 * u
+    return u, du[:, None]
+
+
+def strip(x, sigma: float, f: float = 0.0, g: float = 1.0):
+    """Rectangle with Dirichlet sides x = -1 and x = L (data g) and reflecting
+    Neumann top and bottom: u depends on x alone, -u'' + sigma u = f.
+      sigma > 0, f = 0: u = g cosh(k (x - c)) / cosh(k (L - c)), c = (L - 1)/2,
+                        du/dL = -(g k / 2) sinh(k (x + 1)) / cosh(k)^2 at L = 1
+      sigma = 0:        u = g + f (x + 1)(L - x) / 2, du/dL = f (x + 1) / 2."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))[:, 0]
+    if sigma > 0:
+        if f != 0:
+            raise ValueError("strip: sigma > 0 with a source is not tabulated")
+        k = np.sqrt(sigma)
+        u = g * np.cosh(k * x) / np.cosh(k)
+        du = -g * 0.5 * k * np.sinh(k * (x + 1)) / np.cosh(k) ** 2
+    else:
+        u = g + f * (x + 1) * (1 - x) / 2
+        du = f * (x + 1) / 2
+    return u, du[:, None]
+
+
+def slit_sqrt(x):
+    """Unit disk cut along [0, 1) x {0} (reflecting on both sides), sigma = 0,
+    Dirichlet data cos(t / 2) on the circle: u = sqrt(r) cos(phi / 2) with phi
+    in (0, 2 pi) measured from the slit (harmonic, zero normal derivative on
+    both faces of the slit, equal to the data on the circle)."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    r = np.hypot(x[:, 0], x[:, 1])
+    phi = np.mod(np.arctan2(x[:, 1], x[:, 0]), 2 * np.pi)
+    return np.sqrt(r) * np.cos(phi / 2)
+
+
+def cube_linear(x):
+    """Cube with Dirichlet faces x = -1 (g = -1) and x = X (g = 1), reflecting
+    Neumann elsewhere, sigma = 0: u = 2 (x + 1) / (X + 1) - 1, so at X = 1
+    u = x and du/dX = -(x + 1) / 2."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    return x[:, 0].copy(), (-(x[:, 0] + 1) / 2)[:, None]

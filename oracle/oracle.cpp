@@ -35,6 +35,11 @@
  *  - A walk phase is capped at max_steps distance queries: the last allowed
  *    query treats the walk as if it had reached the shell at its current
  *    closest point (kind CAPPED).  The paper sets no cap.
+ *  - Mixed Dirichlet-Neumann boundaries (Sec. 3.4, Eq. mixed_bvp, with Robin
+ *    coefficient 0 and zero Neumann data, as in the thermal design of
+ *    Sec. 6.3): the walks are walks on stars (see wost_walk below), and the
+ *    differential walk nests at the Dirichlet shell only (Sec. 4.2, Eq.
+ *    mixed_bvp_deriv).  The star radius is at least eps.
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), keyed by
  * the seed; counter = (walk id lo, walk id hi, step, (phase << 8) | block).
@@ -45,6 +50,8 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <map>
+#include <utility>
 #include <vector>
 #include <algorithm>
 #ifdef _OPENMP
@@ -129,6 +136,8 @@ typedef struct {
                                 walks' control variate, or NULL */
     int dudn_mode;           /* 0: backward difference, Eq. (dudn_fd_estimate); 1: ball gradient at the
                                 offset point, Eq. (dudn_mc_estimate) */
+    const int* neumann;      /* n_elem flags, 1: element of the (reflecting) Neumann boundary; NULL: all
+                                elements are Dirichlet */
 } oracle_scene;
 
 enum { KIND_SHELL = 0, KIND_ROULETTE = 1, KIND_CAPPED = 2 };
@@ -214,13 +223,15 @@ static double closest_on_triangle(const double* p, const double* a, const double
     return dd;
 }
 
-/* DistanceToBoundary (Algorithm 1): brute force over every element.  Ties go
- * to the smaller element index (strict < keeps the first minimum). */
+/* DistanceToBoundary (Algorithm 1): brute force over every element (every
+ * Dirichlet element when the scene has a Neumann part).  Ties go to the
+ * smaller element index (strict < keeps the first minimum). */
 static double closest_point(const oracle_scene* s, const double* p, double* xbar, int* e_out, double* bary) {
     double best = INFINITY;
     int best_e = -1;
     double bx[3] = {0, 0, 0}, bb[2] = {0, 0};
     for (int e = 0; e < s->n_elem; ++e) {
+        if (s->neumann && s->neumann[e]) continue;
         double xb[3] = {0, 0, 0}, b2[2];
         double d2;
         if (s->dim == 2) {
@@ -480,6 +491,254 @@ static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_
     }
 }
 
+/* ---------------------------------------------------------------------------
+ * Walk on stars for a boundary split into a Dirichlet part and a reflecting
+ * Neumann part (Sec. 3.4, Eq. mixed_bvp with Robin coefficient 0 and zero
+ * Neumann data; the estimator of Walk on Stars, Sawhney et al. 2023, restated
+ * here).  From a point x the walk uses the star-shaped region St(x, R): the
+ * points of the ball B(x, R) that x sees without crossing the Neumann part.
+ * R must keep St free of Dirichlet boundary (R <= distance to it) and every
+ * ray from x must cross the Neumann part at most once inside B(x, R), which
+ * holds when R is at most the distance to the closest silhouette point of the
+ * Neumann part seen from x: a point where a ray from x grazes it (a vertex
+ * whose two segments lie on the same side of the ray in 2D; an edge whose two
+ * triangles lie on the same side of the plane through x and the edge in 3D)
+ * or where it ends.  The radius is R = max(min(d_D, d_sil), eps).
+ * One step: a direction v uniform on the sphere (reflected into the inward
+ * half-space when x lies on the Neumann part), the ray x + t v up to the first
+ * Neumann hit within R; the walk moves to the hit point (and is then on the
+ * Neumann part) or to x + R v.  Its weight is the Poisson kernel of the ball
+ * at that distance per unit solid angle, |S^(d-1)| t^(d-1) |G_R'(t)| with
+ * G_R the ball's Green's function: 1 for sigma = 0 and alpha(R) at t = R, so
+ * Russian roulette uses it as the survival probability.  The source term
+ * samples a point of the ball as in Algorithm 1 and counts it only if x sees
+ * it.  The walk ends in the eps-shell of the Dirichlet part.
+ * ------------------------------------------------------------------------- */
+struct Adjacency {
+    /* per element and per endpoint (2D) / per edge ab, bc, ca (3D): the vertex of the
+       Neumann neighbour across it (its other vertex / the vertex opposite the shared
+       edge), -1 where the Neumann part ends */
+    std::vector<int> other;
+};
+
+static Adjacency build_adjacency(const oracle_scene* s) {
+    Adjacency a;
+    a.other.assign((size_t)s->n_elem * s->dim, -1);
+    if (!s->neumann) return a;
+    if (s->dim == 2) {
+        std::map<int, std::vector<int>> at;     /* vertex -> Neumann segments containing it */
+        for (int e = 0; e < s->n_elem; ++e)
+            if (s->neumann[e]) for (int j = 0; j < 2; ++j) at[s->elem[2 * e + j]].push_back(e);
+        for (int e = 0; e < s->n_elem; ++e) {
+            if (!s->neumann[e]) continue;
+            for (int j = 0; j < 2; ++j) {
+                const int v = s->elem[2 * e + j];
+                for (int f : at[v])
+                    if (f != e) { a.other[2 * (size_t)e + j] = s->elem[2 * f] == v ? s->elem[2 * f + 1] : s->elem[2 * f]; break; }
+            }
+        }
+    } else {
+        std::map<std::pair<int, int>, std::vector<int>> at;   /* edge -> Neumann triangles containing it */
+        auto key = [](int p, int q) { return p < q ? std::make_pair(p, q) : std::make_pair(q, p); };
+        for (int e = 0; e < s->n_elem; ++e) {
+            if (!s->neumann[e]) continue;
+            const int* t = s->elem + 3 * e;
+            for (int j = 0; j < 3; ++j) at[key(t[j], t[(j + 1) % 3])].push_back(e);
+        }
+        for (int e = 0; e < s->n_elem; ++e) {
+            if (!s->neumann[e]) continue;
+            const int* t = s->elem + 3 * e;
+            for (int j = 0; j < 3; ++j) {
+                for (int f : at[key(t[j], t[(j + 1) % 3])]) {
+                    if (f == e) continue;
+                    const int* u = s->elem + 3 * f;
+                    for (int i = 0; i < 3; ++i)
+                        if (u[i] != t[j] && u[i] != t[(j + 1) % 3]) a.other[3 * (size_t)e + j] = u[i];
+                    break;
+                }
+            }
+        }
+    }
+    return a;
+}
+
+static double cross2(const double* a, const double* b) { return a[0] * b[1] - a[1] * b[0]; }
+
+static double det3(const double* a, const double* b, const double* c) {
+    return a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) + a[2] * (b[0] * c[1] - b[1] * c[0]);
+}
+
+/* Distance from x to the closest silhouette point of the Neumann part. */
+static double silhouette_distance(const oracle_scene* s, const Adjacency& adj, const double* x) {
+    double best = INFINITY;
+    const int d = s->dim;
+    for (int e = 0; e < s->n_elem; ++e) {
+        if (!s->neumann[e]) continue;
+        const int* el = s->elem + (size_t)d * e;
+        if (d == 2) {
+            for (int j = 0; j < 2; ++j) {
+                const double* v = s->vert + 2 * el[j];
+                const double* w = s->vert + 2 * el[1 - j];
+                const int nb = adj.other[2 * (size_t)e + j];
+                const double rv[2] = {v[0] - x[0], v[1] - x[1]};
+                bool sil = nb < 0;
+                if (!sil) {
+                    const double* z = s->vert + 2 * nb;
+                    const double rw[2] = {w[0] - x[0], w[1] - x[1]}, rz[2] = {z[0] - x[0], z[1] - x[1]};
+                    sil = cross2(rv, rw) * cross2(rv, rz) >= 0;
+                }
+                if (sil) best = std::min(best, std::sqrt(rv[0] * rv[0] + rv[1] * rv[1]));
+            }
+        } else {
+            for (int j = 0; j < 3; ++j) {
+                const double* a = s->vert + 3 * el[j];
+                const double* b = s->vert + 3 * el[(j + 1) % 3];
+                const double* c = s->vert + 3 * el[(j + 2) % 3];
+                const int nb = adj.other[3 * (size_t)e + j];
+                const double ra[3] = {a[0] - x[0], a[1] - x[1], a[2] - x[2]};
+                const double rb[3] = {b[0] - x[0], b[1] - x[1], b[2] - x[2]};
+                bool sil = nb < 0;
+                if (!sil) {
+                    const double* z = s->vert + 3 * nb;
+                    const double rc[3] = {c[0] - x[0], c[1] - x[1], c[2] - x[2]};
+                    const double rz[3] = {z[0] - x[0], z[1] - x[1], z[2] - x[2]};
+                    sil = det3(ra, rb, rc) * det3(ra, rb, rz) >= 0;
+                }
+                if (!sil) continue;
+                /* distance from x to the segment ab */
+                const double ab[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+                const double len2 = dot3(ab, ab);
+                double t = len2 > 0 ? -dot3(ra, ab) / len2 : 0.0;
+                t = std::min(1.0, std::max(0.0, t));
+                double off[3];
+                for (int i = 0; i < 3; ++i) off[i] = a[i] + t * ab[i] - x[i];
+                best = std::min(best, std::sqrt(dot3(off, off)));
+            }
+        }
+    }
+    return best;
+}
+
+/* First crossing of the ray x + t v (0 < t < tmax) with a Neumann element other
+ * than `skip`; returns t (INFINITY if none) and the element. */
+static double ray_neumann(const oracle_scene* s, const double* x, const double* v, double tmax, int skip, int* e_out) {
+    double best = INFINITY;
+    *e_out = -1;
+    for (int e = 0; e < s->n_elem; ++e) {
+        if (!s->neumann[e] || e == skip) continue;
+        const int* el = s->elem + (size_t)s->dim * e;
+        double t;
+        if (s->dim == 2) {
+            const double* a = s->vert + 2 * el[0];
+            const double* b = s->vert + 2 * el[1];
+            const double ab[2] = {b[0] - a[0], b[1] - a[1]}, ax[2] = {a[0] - x[0], a[1] - x[1]};
+            const double den = cross2(v, ab);
+            if (den == 0) continue;
+            t = cross2(ax, ab) / den;
+            const double u = cross2(ax, v) / den;
+            if (!(u >= 0 && u <= 1)) continue;
+        } else {
+            const double* a = s->vert + 3 * el[0];
+            const double* b = s->vert + 3 * el[1];
+            const double* c = s->vert + 3 * el[2];
+            double e1[3], e2[3], tv[3];
+            for (int i = 0; i < 3; ++i) { e1[i] = b[i] - a[i]; e2[i] = c[i] - a[i]; tv[i] = x[i] - a[i]; }
+            const double p[3] = {v[1] * e2[2] - v[2] * e2[1], v[2] * e2[0] - v[0] * e2[2], v[0] * e2[1] - v[1] * e2[0]};
+            const double det = dot3(e1, p);
+            if (det == 0) continue;
+            const double u = dot3(tv, p) / det;
+            if (!(u >= 0 && u <= 1)) continue;
+            const double q[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2], tv[0] * e1[1] - tv[1] * e1[0]};
+            const double w = dot3(v, q) / det;
+            if (!(w >= 0 && u + w <= 1)) continue;
+            t = dot3(e2, q) / det;
+        }
+        if (t > 0 && t < tmax && t < best) { best = t; *e_out = e; }
+    }
+    return best;
+}
+
+/* Survival weight of a star step of length t inside the ball of radius R:
+ * |S^(d-1)| t^(d-1) |G_R'(t)| for the screened ball Green's function G_R. */
+double oracle_star_weight(int dim, double sigma, double t, double R) {
+    if (sigma <= 0) return 1.0;
+    const double k = std::sqrt(sigma);
+    if (dim == 2)
+        return k * t * (std::cyl_bessel_k(1.0, k * t)
+                        + std::cyl_bessel_i(1.0, k * t) * std::cyl_bessel_k(0.0, k * R) / std::cyl_bessel_i(0.0, k * R));
+    return (k * t * std::cosh(k * (R - t)) + std::sinh(k * (R - t))) / std::sinh(k * R);
+}
+
+static PhaseResult wost_walk(const oracle_scene* s, const Adjacency& adj, const double* x0, uint64_t walk_id,
+                             uint32_t phase) {
+    PhaseResult res;
+    res.x1[0] = res.x1[1] = res.x1[2] = NAN;
+    res.ball_w = 0;
+    const int d = s->dim;
+    double x[3] = {x0[0], x0[1], d == 3 ? x0[2] : 0.0};
+    double acc = 0;
+    int on = -1;                       /* the Neumann element the walk sits on, -1 inside */
+    double n_on[3] = {0, 0, 0};        /* its normal, out of the domain */
+    for (int k = 0;; ++k) {
+        double xbar[3] = {0, 0, 0}, bary[2];
+        int e;
+        const double dD = closest_point(s, x, xbar, &e, bary);
+        const bool shell = dD < s->eps;
+        if (shell || k + 1 >= s->max_steps) {
+            res.u = acc + dirichlet_value(s, e, bary, xbar);
+            res.kind = shell ? KIND_SHELL : KIND_CAPPED;
+            res.steps = k + 1;
+            res.e = e;
+            res.bary[0] = bary[0]; res.bary[1] = bary[1];
+            for (int i = 0; i < 3; ++i) { res.xbar[i] = xbar[i]; res.x_last[i] = x[i]; }
+            return res;
+        }
+        const double R = std::max(std::min(dD, silhouette_distance(s, adj, x)), s->eps);
+        if (s->f != 0) {   /* source: a point of the ball, counted if x sees it */
+            Draws rb = draw(s->seed_lo, s->seed_hi, walk_id, (uint32_t)k, phase, 1);
+            double w[3];
+            sample_sphere(d, rb, w);
+            if (on >= 0 && dot3(w, n_on) > 0) for (int i = 0; i < 3; ++i) w[i] = -w[i];
+            const double rho = sample_ball_radius(d, rb);
+            int e2;
+            if (ray_neumann(s, x, w, rho * R, on, &e2) >= rho * R)
+                acc += oracle_source_weight(d, s->sigma, R, rho) * s->f;
+        }
+        Draws r0 = draw(s->seed_lo, s->seed_hi, walk_id, (uint32_t)k, phase, 0);
+        double v[3];
+        sample_sphere(d, r0, v);
+        if (on >= 0 && dot3(v, n_on) > 0) for (int i = 0; i < 3; ++i) v[i] = -v[i];
+        int he;
+        const double th = ray_neumann(s, x, v, R, on, &he);
+        const double t = th < R ? th : R;
+        if (oracle_star_weight(d, s->sigma, t, R) < r0.u[2]) {
+            res.u = acc;
+            res.kind = KIND_ROULETTE;
+            res.steps = k + 1;
+            res.e = -1;
+            res.bary[0] = res.bary[1] = 0;
+            for (int i = 0; i < 3; ++i) { res.xbar[i] = 0; res.x_last[i] = x[i]; }
+            return res;
+        }
+        for (int i = 0; i < d; ++i) x[i] += t * v[i];
+        if (th < R) {
+            on = he;
+            element_normal(s, he, n_on);
+            if (dot3(n_on, v) < 0) for (int i = 0; i < 3; ++i) n_on[i] = -n_on[i];
+        } else {
+            on = -1;
+        }
+        if (k == 0) for (int i = 0; i < 3; ++i) res.x1[i] = i < d ? x[i] : 0.0;
+    }
+}
+
+/* One phase of a walk: walk on spheres, or walk on stars with a Neumann part. */
+static PhaseResult phase_walk(const oracle_scene* s, const Adjacency* adj, const double* x0, uint64_t walk_id,
+                              uint32_t phase, const double* ball_n) {
+    if (s->neumann) return wost_walk(s, *adj, x0, walk_id, phase);
+    return forward_walk(s, x0, walk_id, phase, ball_n);
+}
+
 /* Per-walk outputs; any pointer may be NULL. */
 typedef struct {
     double* u_hat;     /* n: forward estimate of u at the query point */
@@ -502,11 +761,11 @@ typedef struct {
 /* Algorithm 2 (DiffWalkOnSpheres) extended, as Sec. 4.1 observation 2
  * describes, to also return u from the same path (source sum + g(xbar)).
  * With mode 0 only Algorithm 1 runs (no nested walks, no derivative). */
-static void run_one(const oracle_scene* s, const double* x0, uint64_t walk_id, int mode,
+static void run_one(const oracle_scene* s, const Adjacency* adj, const double* x0, uint64_t walk_id, int mode,
                     const oracle_walk_out* o, size_t idx) {
     int P = s->n_param;
     int slots = s->K + 1;
-    PhaseResult main = forward_walk(s, x0, walk_id, 0);
+    PhaseResult main = phase_walk(s, adj, x0, walk_id, 0, NULL);
     if (o->u_hat) o->u_hat[idx] = main.u;
     if (o->kind) { o->kind[idx * slots] = main.kind; }
     if (o->steps) { o->steps[idx * slots] = main.steps; }
@@ -542,7 +801,7 @@ static void run_one(const oracle_scene* s, const double* x0, uint64_t walk_id, i
     double sum = 0, sum_plain = 0, sum_dn = 0, sum_dt = 0, sum_ball = 0;
     const double* q_cv = s->cv_elem ? s->cv_elem + 4 * (size_t)main.e : NULL;
     for (int j = 1; j <= s->K; ++j) {
-        PhaseResult nr = forward_walk(s, xoff, walk_id, (uint32_t)j, s->dudn_mode == 1 ? n : NULL);
+        PhaseResult nr = phase_walk(s, adj, xoff, walk_id, (uint32_t)j, s->dudn_mode == 1 ? n : NULL);
         /* control variate: (q n + t) . (x_end - x_off) has mean zero */
         double disp = 0, dn = 0, dt = 0;
         for (int i = 0; i < s->dim; ++i) dn += n[i] * (nr.x_last[i] - xoff[i]);
@@ -618,6 +877,8 @@ int oracle_run_walks(const oracle_scene* s, int n_query, const double* xq, int w
     if (!s || !xq || !o || n_query < 0 || walks_per_point < 0) return 1;
     if (s->dim != 2 && s->dim != 3) return 1;
     if (mode == 1 && s->K < 1) return 1;
+    if (s->neumann && s->dudn_mode != 0) return 1;   /* the ball-gradient estimator needs a ball in the domain */
+    const Adjacency adj = build_adjacency(s);
     long long total = (long long)n_query * walks_per_point;
 #ifdef _OPENMP
     int nt = n_threads > 0 ? n_threads : omp_get_max_threads();
@@ -625,7 +886,7 @@ int oracle_run_walks(const oracle_scene* s, int n_query, const double* xq, int w
 #endif
     for (long long i = 0; i < total; ++i) {
         long long p = i / walks_per_point;
-        run_one(s, xq + (size_t)p * s->dim, walk_id_base + (uint64_t)i, mode, o, (size_t)i);
+        run_one(s, &adj, xq + (size_t)p * s->dim, walk_id_base + (uint64_t)i, mode, o, (size_t)i);
     }
     (void)n_threads;
     return 0;

@@ -11,6 +11,8 @@ Scenes (all seeds fixed; geometry seed 0x2405):
   disk_scene       128-gon of radius R with radial Fourier parameters
   star_box_scene   star-shaped emitter inside the box [-1, 1]^2
   sh_sphere_scene  SH-perturbed icosphere inside the box [-2, 2]^3
+  mixed boundaries (a Dirichlet part and a reflecting Neumann part):
+  quarter_disk_scene, strip_scene, slit_disk_scene, cube_neumann_scene
 """
 from __future__ import annotations
 
@@ -55,6 +57,7 @@ class Scene:
     u_ref: Optional[np.ndarray] = None
     seed: int = PHILOX_SEED
     meta: dict = dc_field(default_factory=dict)
+    neumann: Optional[np.ndarray] = None     # (n_elem,) int32 flags: 1 = reflecting Neumann element
 
     @property
     def dim(self) -> int:
@@ -377,3 +380,129 @@ def batched_problems(n: int = 64, seed: int = GEOMETRY_SEED, scale: float = 1.0,
         sc.name = f"batch{i:02d}_{sc.dim}d"
         out.append(sc)
     return out
+
+
+# ------------------------------------------------------------- mixed boundaries
+def _polyline(points):
+    """Vertices of consecutive point lists joined end to start (a closed loop)."""
+    v = np.concatenate(points, axis=0)
+    n = v.shape[0]
+    e = np.stack([np.arange(n), (np.arange(n) + 1) % n], 1).astype(np.int32)
+    return v, e
+
+
+def quarter_disk_scene(data: str = "field", n_arc: int = 128, n_axis: int = 16, n_query: int = 12,
+                       walks: int = 1024, eps: float = 1e-3, h: float = 1e-2, K: int = 1,
+                       seed: int = GEOMETRY_SEED) -> Scene:
+    """Quarter disk {r < R, 0 < angle < pi/2}, R = 1: the arc (n_arc segments) is
+    Dirichlet, the two radii on the axes (n_axis segments each) reflecting
+    Neumann.  theta = [R] scales every vertex (the arc moves along its normal,
+    the radii along themselves).  data 'field': g = x^2 - y^2 (restricted);
+    'mapped': g_v = cos 2 t_v on the arc."""
+    t = 0.5 * np.pi * np.arange(n_arc + 1) / n_arc
+    arc = np.stack([np.cos(t), np.sin(t)], 1)                       # (1, 0) .. (0, 1)
+    yv = 1.0 - np.arange(1, n_axis + 1) / n_axis                    # (0, y) down to the origin
+    xv = np.arange(1, n_axis) / n_axis                              # (x, 0) up to (1, 0), excluded
+    vert, elem = _polyline([arc, np.stack([0 * yv, yv], 1), np.stack([xv, 0 * xv], 1)])
+    neumann = np.zeros(len(elem), np.int32)
+    neumann[n_arc:] = 1
+    jac = vert[:, :, None].copy()
+    ang = np.arctan2(vert[:, 1], vert[:, 0])
+    rng = np.random.default_rng(seed)
+    r = 0.15 + 0.7 * rng.random(n_query)
+    a = 0.1 + (0.5 * np.pi - 0.2) * rng.random(n_query)
+    q = np.stack([r * np.cos(a), r * np.sin(a)], 1)
+    if data == "field":
+        sc = Scene("quarter_disk_field", vert, elem, jac, data="field",
+                   field=_field(A=(1.0, -1.0, 0.0, 0.0, 0.0, 0.0)), sigma=0.0)
+    else:
+        sc = Scene("quarter_disk_mapped", vert, elem, jac, data="mapped", g_vert=np.cos(2 * ang), sigma=0.0)
+    sc.eps, sc.h, sc.K, sc.query, sc.walks, sc.neumann = eps, h, K, q, walks, neumann
+    sc.meta = {"theta0": np.array([1.0])}
+    return sc
+
+
+def strip_scene(sigma: float = 4.0, f: float = 0.0, g: float = 1.0, half: float = 0.5, n_side: int = 16,
+                n_tb: int = 32, n_query: int = 12, walks: int = 1024, eps: float = 1e-3, h: float = 1e-2,
+                K: int = 1, seed: int = GEOMETRY_SEED) -> Scene:
+    """Rectangle [-1, 1] x [-half, half]: the sides x = -1 and x = L (L = 1) are
+    Dirichlet with mapped data g, the bottom and top reflecting Neumann.
+    theta = [L] moves the right side (its vertices, the corners included, move
+    in x; the top and bottom stretch along themselves)."""
+    bx = -1.0 + 2.0 * np.arange(n_tb) / n_tb
+    ry = -half + 2 * half * np.arange(n_side) / n_side
+    vert, elem = _polyline([np.stack([bx, np.full(n_tb, -half)], 1), np.stack([np.ones(n_side), ry], 1),
+                            np.stack([-bx, np.full(n_tb, half)], 1), np.stack([-np.ones(n_side), -ry], 1)])
+    neumann = np.zeros(len(elem), np.int32)
+    neumann[:n_tb] = 1
+    neumann[n_tb + n_side:2 * n_tb + n_side] = 1
+    jac = np.zeros((len(vert), 2, 1))
+    jac[np.isclose(vert[:, 0], 1.0), 0, 0] = 1.0
+    rng = np.random.default_rng(seed)
+    q = np.stack([rng.uniform(-0.9, 0.9, n_query), rng.uniform(-0.8 * half, 0.8 * half, n_query)], 1)
+    sc = Scene("strip", vert, elem, jac, data="mapped", g_vert=np.full(len(vert), g), sigma=sigma, f=f)
+    sc.eps, sc.h, sc.K, sc.query, sc.walks, sc.neumann = eps, h, K, q, walks, neumann
+    sc.meta = {"theta0": np.array([1.0]), "g": g}
+    return sc
+
+
+def slit_disk_scene(n_circle: int = 256, n_slit: int = 32, n_query: int = 12, walks: int = 1024,
+                    eps: float = 1e-3, seed: int = GEOMETRY_SEED) -> Scene:
+    """Unit disk cut along the slit [0, 1) x {0}: the circle is Dirichlet with
+    mapped data g(t) = cos(t / 2), t in [0, 2 pi] (the vertex at (1, 0) is
+    doubled so that the data can jump there), the slit is a reflecting
+    Neumann boundary seen from both sides, open at the origin.  No shape
+    parameters."""
+    t = 2 * np.pi * np.arange(n_circle + 1) / n_circle
+    circ = np.stack([np.cos(t), np.sin(t)], 1)
+    sv = np.stack([np.arange(n_slit + 1) / n_slit, np.zeros(n_slit + 1)], 1)
+    vert = np.concatenate([circ, sv], 0)
+    ce = np.stack([np.arange(n_circle), np.arange(1, n_circle + 1)], 1)
+    se = n_circle + 1 + np.stack([np.arange(n_slit), np.arange(1, n_slit + 1)], 1)
+    elem = np.concatenate([ce, se], 0).astype(np.int32)
+    neumann = np.concatenate([np.zeros(n_circle), np.ones(n_slit)]).astype(np.int32)
+    g = np.concatenate([np.cos(t / 2), np.zeros(n_slit + 1)])
+    rng = np.random.default_rng(seed)
+    r = 0.25 + 0.55 * rng.random(n_query)
+    a = 0.3 + (2 * np.pi - 0.6) * rng.random(n_query)
+    q = np.stack([r * np.cos(a), r * np.sin(a)], 1)
+    sc = Scene("slit_disk", vert, elem, None, data="mapped", g_vert=g, sigma=0.0)
+    sc.eps, sc.query, sc.walks, sc.neumann = eps, q, walks, neumann
+    return sc
+
+
+def cube_neumann_scene(m: int = 4, n_query: int = 8, walks: int = 1024, eps: float = 1e-3, h: float = 1e-2,
+                       K: int = 1, sigma: float = 0.0, seed: int = GEOMETRY_SEED) -> Scene:
+    """Cube [-1, 1]^3, each face split into 2 m^2 triangles: the faces x = -1 and
+    x = X (X = 1) are Dirichlet with mapped data g = x (-1 and 1), the other
+    four reflecting Neumann.  theta = [X] moves the face x = X (its vertices
+    move in x; the side faces stretch along themselves)."""
+    pts, tris, flags = [], [], []
+    u = np.linspace(-1.0, 1.0, m + 1)
+    for axis in range(3):
+        for sgn in (-1.0, 1.0):
+            a, b = [k for k in range(3) if k != axis]
+            base = sum(len(p) for p in pts)
+            P = np.zeros(((m + 1) ** 2, 3))
+            P[:, axis] = sgn
+            P[:, a] = np.repeat(u, m + 1)
+            P[:, b] = np.tile(u, m + 1)
+            pts.append(P)
+            for i in range(m):
+                for j in range(m):
+                    p0 = base + i * (m + 1) + j
+                    tris += [(p0, p0 + m + 1, p0 + 1), (p0 + 1, p0 + m + 1, p0 + m + 2)]
+                    flags += [0 if axis == 0 else 1] * 2
+    flat = np.concatenate(pts, 0)
+    key = np.round(flat * 1e6).astype(np.int64)
+    _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    vert = flat[first]
+    elem = inv.reshape(-1)[np.array(tris)].astype(np.int32)
+    jac = np.zeros((len(vert), 3, 1))
+    jac[np.isclose(vert[:, 0], 1.0), 0, 0] = 1.0
+    rng = np.random.default_rng(seed)
+    q = rng.uniform(-0.8, 0.8, size=(n_query, 3))
+    sc = Scene("cube_neumann", vert, elem, jac, data="mapped", g_vert=vert[:, 0].copy(), sigma=sigma)
+    sc.eps, sc.h, sc.K, sc.query, sc.walks, sc.neumann = eps, h, K, q, walks, np.array(flags, np.int32)
+    sc.meta = {"theta0": np.array([1.0])}
+    return sc

@@ -1,0 +1,114 @@
+"""Pins for the oracle's walk on stars (mixed Dirichlet / reflecting Neumann
+boundaries; Sec. 3.4, Eq. mixed_bvp with Robin coefficient 0 and zero Neumann
+data) and its differential walk, which nests at the Dirichlet shell only
+(Sec. 4.2, Eq. mixed_bvp_deriv).
+
+* The step weight is the flux of the ball's Green's function per unit solid
+  angle: checked against the Green's function itself (finite differences of
+  the oracle's source weight), not a retyped formula.
+* Closed forms: a quarter disk (u = x^2 - y^2, Neumann radii; du/dR for field
+  and mapped data), a screened strip (u = cosh(kx)/cosh(k), Neumann top and
+  bottom; du/dL of the moving side), a strip with a source, a slit disk
+  (u = sqrt(r) cos(phi/2), discontinuous across a two-sided Neumann slit with
+  an open end: a walk that stepped across the slit, as it would with a radius
+  not bounded by the slit's silhouette, lands on the other side's data), and a
+  cube with four Neumann faces (u = x, du/dX of the moving face).
+* Walks never end on the Neumann part.
+Tolerances: 3.5 SE + a bias budget (polygon / mesh, eps-shell and the O(h)
+backward difference of Sec. 5.3).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closed_forms as cf
+from oracle import estimators as est
+from paper_2405_12964_gb300 import scenes
+from tests.helpers import to_oracle
+
+Z = 3.5
+
+
+def _check(mean, se, exact, rel_bias, abs_bias=0.0):
+    ok = np.abs(mean - exact) <= Z * se + rel_bias * np.abs(exact) + abs_bias
+    assert ok.all(), (np.round(np.abs(mean - exact) / (se + 1e-300), 2), mean, exact)
+
+
+def _run(sc, W, differential=True, **over):
+    out = oracle.run_walks(to_oracle(sc, **over), sc.query, W, differential=differential)
+    n = sc.query.shape[0]
+    m, se = est.point_mean_se(out["u_hat"], n, W)
+    res = {"u": m, "u_se": se, "out": out}
+    if differential:
+        res["du"], res["du_se"] = est.point_mean_se(out["udot"], n, W)
+    return res
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("sigma", [0.0, 0.5, 9.0])
+def test_star_weight_is_the_flux_of_the_ball_green_function(dim, sigma):
+    R = 0.7
+    vol = np.pi * R ** 2 if dim == 2 else 4.0 / 3.0 * np.pi * R ** 3
+    area = lambda r: 2 * np.pi * r if dim == 2 else 4 * np.pi * r * r
+    G = lambda r: oracle.source_weight(dim, sigma, R, r / R) / vol
+    for t in (0.05, 0.2, 0.45, 0.69):
+        hh = 1e-6
+        flux = -(G(t + hh) - G(t - hh)) / (2 * hh) * area(t)
+        assert abs(oracle.star_weight(dim, sigma, t, R) - flux) < 1e-6
+    assert abs(oracle.star_weight(dim, sigma, R, R) - oracle.alpha(dim, sigma, R)) < 1e-12
+    assert abs(oracle.star_weight(dim, sigma, 1e-7, R) - 1.0) < 1e-5
+    if sigma == 0:
+        assert oracle.star_weight(dim, sigma, 0.3, R) == 1.0
+
+
+@pytest.mark.parametrize("data", ["field", "mapped"])
+def test_quarter_disk_closed_form(data):
+    sc = scenes.quarter_disk_scene(data, n_query=8)
+    r = _run(sc, 4096)
+    u, du = cf.quarter_disk(sc.query, data)
+    _check(r["u"], r["u_se"], u, 3e-3, 2e-3)
+    _check(r["du"], r["du_se"], du, 0.08, 0.02)
+    o = r["out"]
+    # walks end on the Dirichlet arc (elements 0 .. 127), never on the Neumann radii
+    assert np.all(o["elem"][o["kind"][:, 0] == oracle.KIND_SHELL] < 128)
+    # the data-independent part: with field data the two halves of udot cancel
+    if data == "field":
+        assert np.abs(o["dudn"]).mean() > 0.3
+
+
+def test_screened_strip_closed_form():
+    sc = scenes.strip_scene(sigma=4.0, n_query=8)
+    r = _run(sc, 4096)
+    u, du = cf.strip(sc.query, 4.0)
+    _check(r["u"], r["u_se"], u, 3e-3, 1e-3)
+    _check(r["du"], r["du_se"], du, 0.08, 0.01)
+    assert (r["out"]["kind"][:, 0] == oracle.KIND_ROULETTE).any()
+
+
+def test_strip_with_source_closed_form():
+    # the source samples a point of the star, counted only where the walk sees it
+    sc = scenes.strip_scene(sigma=0.0, f=2.0, g=0.5, n_query=8)
+    r = _run(sc, 4096)
+    u, du = cf.strip(sc.query, 0.0, f=2.0, g=0.5)
+    _check(r["u"], r["u_se"], u, 4e-3, 2e-3)
+    _check(r["du"], r["du_se"], du, 0.08, 0.02)
+
+
+def test_slit_disk_needs_the_silhouette_bound():
+    sc = scenes.slit_disk_scene(n_query=10)
+    r = _run(sc, 4096, differential=False)
+    _check(r["u"], r["u_se"], cf.slit_sqrt(sc.query), 0.0, 8e-3)
+    # walks above and below the slit see different data: the values straddle zero
+    assert (r["u"] > 0.2).any() and (r["u"] < -0.2).any()
+
+
+def test_cube_with_neumann_faces_closed_form():
+    sc = scenes.cube_neumann_scene(n_query=6)
+    r = _run(sc, 2048)
+    u, du = cf.cube_linear(sc.query)
+    _check(r["u"], r["u_se"], u, 0.0, 4e-3)
+    _check(r["du"], r["du_se"], du, 0.08, 0.02)
+    o = r["out"]
+    dirichlet = np.nonzero(sc.neumann == 0)[0]
+    hit = o["kind"][:, 0] == oracle.KIND_SHELL
+    assert np.isin(o["elem"][hit], dirichlet).all()
