@@ -195,6 +195,33 @@ dwos_status dwos_set_dirichlet_mapped(dwos_ctx* ctx, const float* g_vert, const 
 dwos_status dwos_set_dirichlet_field(dwos_ctx* ctx, const double* coeffs);
 /* Screening sigma >= 0 and constant source f (of -Lap u + sigma u = f). */
 dwos_status dwos_set_pde(dwos_ctx* ctx, float sigma, float f);
+/* Mixed Dirichlet / Neumann boundary (Sec. 3.4, Eq. mixed_bvp with Robin
+ * coefficient 0 and zero Neumann data: a reflecting boundary, as in the
+ * paper's thermal design, Sec. 6.3).  flags (n_elem int32, host or device by
+ * mem): 1 marks an element of the Neumann part, 0 of the Dirichlet part; NULL
+ * or all zeros makes every element Dirichlet again.  The Dirichlet part must
+ * not be empty.  With a Neumann part every walk-running call (dwos_eval,
+ * dwos_vjp, dwos_grad_l2, dwos_grad_l2_product, dwos_walk_records) runs walks
+ * on stars (Sawhney et al. 2023): from x the walk takes the star-shaped
+ * region of the ball of radius R = max(min(distance to the Dirichlet part,
+ * distance to the closest Neumann silhouette point), eps) that x sees without
+ * crossing the Neumann part, moves along a uniform direction (into the
+ * domain's half-space when x lies on the Neumann part) to the first Neumann
+ * crossing or the sphere, survives Russian roulette with probability
+ * |S| t^(d-1) |G_R'(t)| for the step length t, and counts a source sample of
+ * the ball where x sees it; walks end in the eps-shell of the Dirichlet part
+ * only.  The differential walk nests there (Sec. 4.2, Eq. mixed_bvp_deriv):
+ * the Neumann part contributes no boundary term, and its vertices' motion
+ * (for instance the tangential stretch of a side next to a moving Dirichlet
+ * part) enters only through the geometry.  Query points must lie in the
+ * interior.  Records number elements as the input does.  Not available with
+ * a Neumann part: the ball-gradient du/dn estimator, control variates,
+ * batches, dwos_eval_static and the shape-functional calls
+ * (DWOS_ERR_NOT_IMPLEMENTED / DWOS_ERR_INVALID_ARG).  dwos_closest_point
+ * then answers for the Dirichlet part, dwos_inside for the whole boundary.
+ * Builds a BVH for each part; dwos_set_params rebuilds both.  Synchronises. */
+dwos_status dwos_set_neumann(dwos_ctx* ctx, const int32_t* flags, int mem);
+
 /* Bound on the BVH node fetches (binary nodes, or 32-wide node visits) that one
  * distance query of a walk may make; 0 (the default) keeps the trees' own
  * bounds, which a valid tree never reaches.  A query that exceeds the bound
@@ -402,10 +429,17 @@ dwos_status dwos_philox4x32_10(dwos_ctx* ctx, int n, const uint32_t* ctr, const 
  * be NULL.  Inputs and outputs are host or device memory by mem; sizes n. */
 dwos_status dwos_ball_weights(dwos_ctx* ctx, int dim, float sigma, int n, const float* d, const float* u,
                               float* source, float* alpha, int mem);
-/* The modified Bessel function K0(x), x > 0, as the 2D source weight evaluates
- * it (the polynomial approximations 9.8.5 and 9.8.6 of Abramowitz & Stegun in
- * FP32): out[i] = K0(x[i]) for i < n, host or device memory by mem. */
+/* The modified Bessel functions K0(x) and K1(x), x > 0, as the 2D source
+ * weight and the walk-on-stars step weight evaluate them (the polynomial
+ * approximations 9.8.5-9.8.8 of Abramowitz & Stegun in FP32): out[i] =
+ * K0(x[i]) or K1(x[i]) for i < n, host or device memory by mem. */
 dwos_status dwos_bessel_k0(dwos_ctx* ctx, int n, const float* x, float* out, int mem);
+dwos_status dwos_bessel_k1(dwos_ctx* ctx, int n, const float* x, float* out, int mem);
+/* The walk-on-stars step's survival weight |S^(d-1)| t^(d-1) |G_R'(t)| for
+ * n pairs (t[i], R[i]), 0 < t <= R, evaluated as the walk kernel does
+ * (see dwos_set_neumann). */
+dwos_status dwos_star_weight(dwos_ctx* ctx, int dim, float sigma, int n, const float* t, const float* R, float* out,
+                             int mem);
 
 /* ---- batched problems ----------------------------------------------------
  * Many independent reverse-mode problems in one pass: each job is a

@@ -503,7 +503,18 @@ static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_
  * Neumann part seen from x: a point where a ray from x grazes it (a vertex
  * whose two segments lie on the same side of the ray in 2D; an edge whose two
  * triangles lie on the same side of the plane through x and the edge in 3D)
- * or where it ends.  The radius is R = max(min(d_D, d_sil), eps).
+ * or where it ends.  The radius is R = max(min(d_D, d_sil), eps).  A side
+ * test whose cross product (triple product in 3D) is within a relative 1e-4
+ * of zero counts as collinear (coplanar): where the boundary runs straight on
+ * through a vertex (or flat across an edge), seen from a point on its own line
+ * (plane), the vertex (edge) is no silhouette; where one side is collinear and
+ * the other turns away, it is one.  This keeps walks that sit on a flat
+ * Neumann side from taking every vertex of that side as a silhouette.
+ * A ray meets an element where its barycentric coordinates lie within 1e-5
+ * of the element (so that no ray slips between two neighbours).  The offset
+ * point xbar - h n of the differential walk is mirrored across the Neumann
+ * part where the segment from xbar to it crosses that part (next to a
+ * Dirichlet-Neumann junction): across a reflecting boundary u extends evenly.
  * One step: a direction v uniform on the sphere (reflected into the inward
  * half-space when x lies on the Neumann part), the ray x + t v up to the first
  * Neumann hit within R; the walk moves to the hit point (and is then on the
@@ -564,6 +575,16 @@ static Adjacency build_adjacency(const oracle_scene* s) {
 
 static double cross2(const double* a, const double* b) { return a[0] * b[1] - a[1] * b[0]; }
 
+/* Silhouette rule from the two side tests s1, s2 and their scales m1, m2 (the
+ * products of the lengths involved): a side test within a relative 1e-4 of
+ * zero counts as collinear / coplanar. */
+static bool silhouette_rule(double s1, double m1, double s2, double m2) {
+    const bool c1 = std::fabs(s1) <= 1e-4 * m1, c2 = std::fabs(s2) <= 1e-4 * m2;
+    if (c1 && c2) return false;      /* the boundary runs straight on through it */
+    if (c1 || c2) return true;       /* one side along the line of sight, the other turns */
+    return s1 * s2 > 0;              /* both neighbours on the same side */
+}
+
 static double det3(const double* a, const double* b, const double* c) {
     return a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) + a[2] * (b[0] * c[1] - b[1] * c[0]);
 }
@@ -585,7 +606,9 @@ static double silhouette_distance(const oracle_scene* s, const Adjacency& adj, c
                 if (!sil) {
                     const double* z = s->vert + 2 * nb;
                     const double rw[2] = {w[0] - x[0], w[1] - x[1]}, rz[2] = {z[0] - x[0], z[1] - x[1]};
-                    sil = cross2(rv, rw) * cross2(rv, rz) >= 0;
+                    const double lv = std::hypot(rv[0], rv[1]);
+                    sil = silhouette_rule(cross2(rv, rw), lv * std::hypot(rw[0], rw[1]),
+                                          cross2(rv, rz), lv * std::hypot(rz[0], rz[1]));
                 }
                 if (sil) best = std::min(best, std::sqrt(rv[0] * rv[0] + rv[1] * rv[1]));
             }
@@ -602,7 +625,11 @@ static double silhouette_distance(const oracle_scene* s, const Adjacency& adj, c
                     const double* z = s->vert + 3 * nb;
                     const double rc[3] = {c[0] - x[0], c[1] - x[1], c[2] - x[2]};
                     const double rz[3] = {z[0] - x[0], z[1] - x[1], z[2] - x[2]};
-                    sil = det3(ra, rb, rc) * det3(ra, rb, rz) >= 0;
+                    const double n[3] = {ra[1] * rb[2] - ra[2] * rb[1], ra[2] * rb[0] - ra[0] * rb[2],
+                                         ra[0] * rb[1] - ra[1] * rb[0]};
+                    const double ln = std::sqrt(dot3(n, n));
+                    sil = silhouette_rule(det3(ra, rb, rc), ln * std::sqrt(dot3(rc, rc)),
+                                          det3(ra, rb, rz), ln * std::sqrt(dot3(rz, rz)));
                 }
                 if (!sil) continue;
                 /* distance from x to the segment ab */
@@ -636,7 +663,7 @@ static double ray_neumann(const oracle_scene* s, const double* x, const double* 
             if (den == 0) continue;
             t = cross2(ax, ab) / den;
             const double u = cross2(ax, v) / den;
-            if (!(u >= 0 && u <= 1)) continue;
+            if (!(u >= -1e-5 && u <= 1 + 1e-5)) continue;
         } else {
             const double* a = s->vert + 3 * el[0];
             const double* b = s->vert + 3 * el[1];
@@ -647,10 +674,10 @@ static double ray_neumann(const oracle_scene* s, const double* x, const double* 
             const double det = dot3(e1, p);
             if (det == 0) continue;
             const double u = dot3(tv, p) / det;
-            if (!(u >= 0 && u <= 1)) continue;
+            if (!(u >= -1e-5 && u <= 1 + 1e-5)) continue;
             const double q[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2], tv[0] * e1[1] - tv[1] * e1[0]};
             const double w = dot3(v, q) / det;
-            if (!(w >= 0 && u + w <= 1)) continue;
+            if (!(w >= -1e-5 && u + w <= 1 + 1e-5)) continue;
             t = dot3(e2, q) / det;
         }
         if (t > 0 && t < tmax && t < best) { best = t; *e_out = e; }
@@ -798,6 +825,18 @@ static void run_one(const oracle_scene* s, const Adjacency* adj, const double* x
     /* offset point and nested forward walks */
     double xoff[3] = {0, 0, 0};
     for (int i = 0; i < s->dim; ++i) xoff[i] = main.xbar[i] - s->h * n[i];
+    if (s->neumann) {   /* mirrored across the Neumann part where the offset crosses it */
+        double back[3] = {-n[0], -n[1], -n[2]};
+        int he;
+        const double th = ray_neumann(s, main.xbar, back, s->h, -1, &he);
+        if (he >= 0) {
+            double m[3];
+            element_normal(s, he, m);
+            double c[3], r[3], rm = 0;
+            for (int i = 0; i < 3; ++i) { c[i] = main.xbar[i] + th * back[i]; r[i] = xoff[i] - c[i]; rm += r[i] * m[i]; }
+            for (int i = 0; i < s->dim; ++i) xoff[i] = c[i] + r[i] - 2 * rm * m[i];
+        }
+    }
     double sum = 0, sum_plain = 0, sum_dn = 0, sum_dt = 0, sum_ball = 0;
     const double* q_cv = s->cv_elem ? s->cv_elem + 4 * (size_t)main.e : NULL;
     for (int j = 1; j <= s->K; ++j) {

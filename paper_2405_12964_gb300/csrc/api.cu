@@ -9,6 +9,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "ctx.h"
@@ -94,8 +95,50 @@ dwos_status set_device(dwos_ctx* ctx) {
 }
 
 dwos_status rebuild(dwos_ctx* ctx) {
-    CK(bvh_build(ctx->bvh, ctx->dim, ctx->vert, ctx->elem, ctx->n_elem, ctx->stream), "BVH build");
+    if (ctx->n_neumann == 0) {
+        CK(bvh_build(ctx->bvh, ctx->dim, ctx->vert, ctx->elem, ctx->n_elem, ctx->stream), "BVH build");
+        return DWOS_OK;
+    }
+    // walk on stars: one tree over the Dirichlet part (distance queries), one over the Neumann part
+    CK(bvh_build(ctx->bvh, ctx->dim, ctx->vert, ctx->elem_d, ctx->n_elem - ctx->n_neumann, ctx->stream), "BVH build");
+    CK(bvh_build(ctx->bvh_n, ctx->dim, ctx->vert, ctx->elem_n, ctx->n_neumann, ctx->stream), "Neumann BVH build");
+    DevNeumann N;
+    N.nodes = ctx->bvh_n.nodes;
+    N.prims = ctx->bvh_n.prims;
+    N.prim_elem = ctx->bvh_n.prim_elem;
+    N.n_internal = ctx->bvh_n.n_internal;
+    N.n_tree = ctx->bvh_n.n_tree;
+    N.n_big = ctx->bvh_n.n_big;
+    N.pad = 0;
+    N.elem = ctx->elem_n;
+    N.adj = ctx->nadj;
+    N.vert = ctx->vert;
+    N.dmap = ctx->dmap;
+    CK(cudaMemcpyAsync(ctx->d_neu, &N, sizeof(N), cudaMemcpyHostToDevice, ctx->stream), "copy Neumann part");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     return DWOS_OK;
+}
+
+__global__ void xor_flags_kernel(int n, const int* __restrict__ a, int* __restrict__ b) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] ^= a[i];
+}
+
+__global__ void map_ids_kernel(int n, const int* __restrict__ map, int* __restrict__ ids) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n && ids[i] >= 0) ids[i] = map[ids[i]];
+}
+
+// Inside test by ray parity over the whole boundary: with a Neumann part the
+// crossings of the two trees add up, so the parities combine by XOR.
+cudaError_t inside_all(dwos_ctx* ctx, int n, const float* p, int* inside) {
+    cudaError_t e = launch_inside(ctx->bvh, n, p, inside, ctx->stream);
+    if (e != cudaSuccess || ctx->n_neumann == 0 || n <= 0) return e;
+    e = grow(ctx->inside_tmp, ctx->inside_tmp_cap, (size_t)n);
+    if (e == cudaSuccess) e = launch_inside(ctx->bvh_n, n, p, ctx->inside_tmp, ctx->stream);
+    if (e != cudaSuccess) return e;
+    xor_flags_kernel<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, ctx->inside_tmp, inside);
+    return cudaGetLastError();
 }
 
 // Shared front half of every walk-running call: validate, stage the query
@@ -115,10 +158,16 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     CK(grow(ctx->rec, ctx->rec_cap, (size_t)total), "alloc records");
     CK(to_device(ctx, ctx->xq, xq, (size_t)n_query * ctx->dim, mem), "copy xq");
     const int* valid = nullptr;
+    if (ctx->n_neumann > 0) {
+        if (ctx->opt.dudn_estimator != 0)
+            return fail(ctx, DWOS_ERR_INVALID_ARG, "a Neumann part needs the backward-difference du/dn estimator");
+        if (cv_sample || cv_end || cv_elem)
+            return fail(ctx, DWOS_ERR_NOT_IMPLEMENTED, "control variates with a Neumann part");
+    }
     if (ctx->opt.check_inside && n_query > 0) {
         CK(grow(ctx->valid, ctx->valid_cap, (size_t)n_query), "alloc inside flags");
-        CK(launch_inside(ctx->bvh, n_query, ctx->xq, ctx->valid, ctx->stream), "inside test");
-        ctx->launches += 1;
+        CK(inside_all(ctx, n_query, ctx->xq, ctx->valid), "inside test");
+        ctx->launches += ctx->n_neumann > 0 ? 3 : 1;
         valid = ctx->valid;
     }
     DevProblem P;
@@ -164,6 +213,8 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     P.cv_sample = cv_sample;
     P.cv_end = cv_end;
     P.cv_elem = cv_elem;
+    P.neu = ctx->n_neumann > 0 ? ctx->d_neu : nullptr;
+    if (P.neu && (P.traversal == 2 || P.traversal == 3)) P.traversal = 0;   // per-lane search of the Dirichlet tree
     if (cv_sample) CK(cudaMemsetAsync(cv_sample, 0xff, sizeof(float4) * total, ctx->stream), "init samples");
     CK(cudaMemcpyAsync(ctx->d_prob, &P, sizeof(P), cudaMemcpyHostToDevice, ctx->stream), "copy problem");
     CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->stream), "reset counters");
@@ -173,6 +224,7 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     L.blocks_per_sm = ctx->opt.blocks_per_sm;
     L.n_sm = ctx->n_sm;
     L.traversal = P.traversal;
+    L.star = P.neu != nullptr;
     CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
     int blocks = 0;
     CK(launch_walks(L, ctx->d_prob, 1, total, ctx->d_ctr, ctx->stream, &blocks), "walk kernel");
@@ -293,7 +345,8 @@ void dwos_destroy(dwos_ctx* ctx) {
     void* bufs[] = {ctx->vert_ref, ctx->vert, ctx->elem, ctx->jac, ctx->theta, ctx->g_vert, ctx->dg_vert, ctx->rec,
                     ctx->xq, ctx->valid, ctx->wvec, ctx->out, ctx->acc_vert, ctx->trace, ctx->dbg, ctx->misc_f,
                     ctx->misc_i, ctx->misc_u, ctx->d_prob, ctx->d_ctr, ctx->d_err, ctx->pw, ctx->vert_active,
-                    ctx->misc_d};
+                    ctx->misc_d, ctx->elem_d, ctx->elem_n, ctx->dmap, ctx->nadj, ctx->d_neu, ctx->inside_tmp};
+    bvh_free(ctx->bvh_n);
     for (void* p : bufs) if (p) cudaFree(p);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -370,6 +423,9 @@ dwos_status dwos_set_boundary(dwos_ctx* ctx, int dim, int n_vert, const float* v
     ctx->vert_ref = ctx->vert = ctx->jac = ctx->theta = ctx->g_vert = ctx->dg_vert = nullptr;
     ctx->elem = nullptr;
     ctx->have_boundary = false;
+    for (void* p : {(void*)ctx->elem_d, (void*)ctx->elem_n, (void*)ctx->dmap, (void*)ctx->nadj}) if (p) cudaFree(p);
+    ctx->elem_d = ctx->elem_n = ctx->dmap = ctx->nadj = nullptr;
+    ctx->n_neumann = 0;
     const size_t nv = (size_t)n_vert * dim;
     CK(cudaMalloc(&ctx->vert_ref, nv * sizeof(float)), "alloc vertices");
     CK(cudaMalloc(&ctx->vert, nv * sizeof(float)), "alloc vertices");
@@ -464,6 +520,72 @@ dwos_status dwos_set_pde(dwos_ctx* ctx, float sigma, float f) {
     ctx->sigma = sigma;
     ctx->f = f;
     return DWOS_OK;
+}
+
+dwos_status dwos_set_neumann(dwos_ctx* ctx, const int32_t* flags, int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (!ctx->have_boundary) return fail(ctx, DWOS_ERR_STATE, "no boundary: call dwos_set_boundary first");
+    if (dwos_status s = check_mem(ctx, mem)) return s;
+    if (mem == DWOS_MEM_DEVICE) if (dwos_status s = check_device_ptr(ctx, flags, "flags")) return s;
+    if (dwos_status s = set_device(ctx)) return s;
+    const int n = ctx->n_elem, d = ctx->dim;
+    std::vector<int32_t> f(n, 0);
+    if (flags) CK(cudaMemcpyAsync(f.data(), flags, sizeof(int32_t) * n, mem == DWOS_MEM_DEVICE ? cudaMemcpyDeviceToHost
+                                                                                              : cudaMemcpyHostToHost,
+                                  ctx->stream), "copy flags");
+    std::vector<int32_t> el((size_t)n * d);
+    CK(cudaMemcpyAsync(el.data(), ctx->elem, sizeof(int32_t) * el.size(), cudaMemcpyDeviceToHost, ctx->stream), "copy elements");
+    CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    std::vector<int32_t> ed, en, dmap;
+    for (int e = 0; e < n; ++e) {
+        if (f[e] != 0 && f[e] != 1) return fail(ctx, DWOS_ERR_INVALID_ARG, "flags must be 0 or 1");
+        auto& dst = f[e] ? en : ed;
+        for (int k = 0; k < d; ++k) dst.push_back(el[(size_t)d * e + k]);
+        if (!f[e]) dmap.push_back(e);
+    }
+    const int n_n = (int)(en.size() / d);
+    if (n_n > 0 && n_n == n) return fail(ctx, DWOS_ERR_INVALID_ARG, "the boundary needs a Dirichlet part");
+    for (void* p : {(void*)ctx->elem_d, (void*)ctx->elem_n, (void*)ctx->dmap, (void*)ctx->nadj}) if (p) cudaFree(p);
+    ctx->elem_d = ctx->elem_n = ctx->dmap = ctx->nadj = nullptr;
+    ctx->n_neumann = 0;
+    if (n_n == 0) return rebuild(ctx);            // every element Dirichlet again
+    // neighbours across each endpoint (segments) or edge (triangles) within the Neumann part
+    std::vector<int32_t> adj((size_t)n_n * d, -1);
+    std::unordered_map<unsigned long long, std::vector<int>> at;
+    auto key = [](int a, int b) {
+        const unsigned lo = (unsigned)std::min(a, b), hi = (unsigned)std::max(a, b);
+        return ((unsigned long long)hi << 32) | lo;
+    };
+    for (int c = 0; c < n_n; ++c)
+        for (int j = 0; j < d; ++j) {
+            const int* t = en.data() + (size_t)d * c;
+            at[d == 2 ? (unsigned long long)(unsigned)t[j] : key(t[j], t[(j + 1) % 3])].push_back(c);
+        }
+    for (int c = 0; c < n_n; ++c) {
+        const int* t = en.data() + (size_t)d * c;
+        for (int j = 0; j < d; ++j) {
+            const auto& list = at[d == 2 ? (unsigned long long)(unsigned)t[j] : key(t[j], t[(j + 1) % 3])];
+            for (int o : list) {
+                if (o == c) continue;
+                const int* u = en.data() + (size_t)d * o;
+                if (d == 2) adj[2 * (size_t)c + j] = u[0] == t[j] ? u[1] : u[0];
+                else for (int i = 0; i < 3; ++i)
+                    if (u[i] != t[j] && u[i] != t[(j + 1) % 3]) adj[3 * (size_t)c + j] = u[i];
+                break;
+            }
+        }
+    }
+    CK(cudaMalloc(&ctx->elem_d, sizeof(int32_t) * ed.size()), "alloc Dirichlet elements");
+    CK(cudaMalloc(&ctx->elem_n, sizeof(int32_t) * en.size()), "alloc Neumann elements");
+    CK(cudaMalloc(&ctx->dmap, sizeof(int32_t) * dmap.size()), "alloc element map");
+    CK(cudaMalloc(&ctx->nadj, sizeof(int32_t) * adj.size()), "alloc neighbours");
+    if (!ctx->d_neu) CK(cudaMalloc(&ctx->d_neu, sizeof(DevNeumann)), "alloc Neumann descriptor");
+    CK(cudaMemcpy(ctx->elem_d, ed.data(), sizeof(int32_t) * ed.size(), cudaMemcpyHostToDevice), "copy");
+    CK(cudaMemcpy(ctx->elem_n, en.data(), sizeof(int32_t) * en.size(), cudaMemcpyHostToDevice), "copy");
+    CK(cudaMemcpy(ctx->dmap, dmap.data(), sizeof(int32_t) * dmap.size(), cudaMemcpyHostToDevice), "copy");
+    CK(cudaMemcpy(ctx->nadj, adj.data(), sizeof(int32_t) * adj.size(), cudaMemcpyHostToDevice), "copy");
+    ctx->n_neumann = n_n;
+    return rebuild(ctx);
 }
 
 dwos_status dwos_set_traversal_budget(dwos_ctx* ctx, int max_fetches) {
@@ -924,9 +1046,14 @@ static dwos_status closest_common(dwos_ctx* ctx, int n, const float* p, const in
     if (hint) { dh = ctx->misc_i + std::max(n, 1); CK(to_device(ctx, dh, hint, (size_t)n, mem), "copy hints"); }
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream), "reset");
     CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->stream), "reset counters");
+    if (hint && ctx->n_neumann > 0) return fail(ctx, DWOS_ERR_NOT_IMPLEMENTED, "hinted queries with a Neumann part");
     CK(launch_closest(ctx->bvh, n, dp, dh, dd, ctx->misc_i, db, ctx->d_err, ctx->d_ctr, effective_traversal(ctx),
                       ctx->stream), "closest point");
     ctx->launches += n > 0 ? 1 : 0;
+    if (ctx->n_neumann > 0 && n > 0) {   // the Dirichlet tree numbers its own elements
+        map_ids_kernel<<<(n + 255) / 256, 256, 0, ctx->stream>>>(n, ctx->dmap, ctx->misc_i);
+        CK(cudaGetLastError(), "map element ids");
+    }
     CK(from_device(ctx, dist, dd, n, mem), "copy");
     CK(from_device(ctx, elem_out, ctx->misc_i, n, mem), "copy");
     CK(from_device(ctx, bary, db, 2 * (size_t)n, mem), "copy");
@@ -959,7 +1086,7 @@ dwos_status dwos_inside(dwos_ctx* ctx, int n, const float* p, int32_t* inside, i
     CK(grow(ctx->misc_f, ctx->misc_f_cap, (size_t)n * ctx->dim), "alloc");
     CK(grow(ctx->misc_i, ctx->misc_i_cap, (size_t)std::max(n, 1)), "alloc");
     CK(to_device(ctx, ctx->misc_f, p, (size_t)n * ctx->dim, mem), "copy points");
-    CK(launch_inside(ctx->bvh, n, ctx->misc_f, ctx->misc_i, ctx->stream), "inside test");
+    CK(inside_all(ctx, n, ctx->misc_f, ctx->misc_i), "inside test");
     CK(from_device(ctx, inside, ctx->misc_i, n, mem), "copy");
     if (mem == DWOS_MEM_HOST) CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     return DWOS_OK;
@@ -1009,7 +1136,7 @@ dwos_status dwos_ball_weights(dwos_ctx* ctx, int dim, float sigma, int n, const 
     return DWOS_OK;
 }
 
-dwos_status dwos_bessel_k0(dwos_ctx* ctx, int n, const float* x, float* out, int mem) {
+static dwos_status bessel_k(dwos_ctx* ctx, int order, int n, const float* x, float* out, int mem) {
     if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
     if (dwos_status s = check_mem(ctx, mem)) return s;
     if (n < 0 || (n > 0 && (!x || !out))) return fail(ctx, DWOS_ERR_INVALID_ARG, "bad arguments");
@@ -1017,9 +1144,37 @@ dwos_status dwos_bessel_k0(dwos_ctx* ctx, int n, const float* x, float* out, int
     if (n == 0) return DWOS_OK;
     CK(grow(ctx->misc_f, ctx->misc_f_cap, 2 * (size_t)n), "alloc");
     CK(to_device(ctx, ctx->misc_f, x, (size_t)n, mem), "copy x");
-    CK(launch_bessel_k0(n, ctx->misc_f, ctx->misc_f + n, ctx->stream), "K0");
+    CK(launch_bessel_k(order, n, ctx->misc_f, ctx->misc_f + n, ctx->stream), "K");
     ctx->launches += 1;
-    CK(from_device(ctx, out, ctx->misc_f + n, (size_t)n, mem), "copy K0");
+    CK(from_device(ctx, out, ctx->misc_f + n, (size_t)n, mem), "copy K");
+    if (mem == DWOS_MEM_HOST) CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    return DWOS_OK;
+}
+
+dwos_status dwos_bessel_k0(dwos_ctx* ctx, int n, const float* x, float* out, int mem) {
+    return bessel_k(ctx, 0, n, x, out, mem);
+}
+
+dwos_status dwos_bessel_k1(dwos_ctx* ctx, int n, const float* x, float* out, int mem) {
+    return bessel_k(ctx, 1, n, x, out, mem);
+}
+
+dwos_status dwos_star_weight(dwos_ctx* ctx, int dim, float sigma, int n, const float* t, const float* R, float* out,
+                             int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (dwos_status s = check_mem(ctx, mem)) return s;
+    if (dim != 2 && dim != 3) return fail(ctx, DWOS_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (!(sigma >= 0.0f) || !std::isfinite(sigma)) return fail(ctx, DWOS_ERR_INVALID_ARG, "sigma must be finite and >= 0");
+    if (n < 0 || (n > 0 && (!t || !R || !out))) return fail(ctx, DWOS_ERR_INVALID_ARG, "bad arguments");
+    if (dwos_status s = set_device(ctx)) return s;
+    if (n == 0) return DWOS_OK;
+    CK(grow(ctx->misc_f, ctx->misc_f_cap, 3 * (size_t)n), "alloc");
+    CK(to_device(ctx, ctx->misc_f, t, (size_t)n, mem), "copy t");
+    CK(to_device(ctx, ctx->misc_f + n, R, (size_t)n, mem), "copy R");
+    CK(launch_star_weight(dim, std::sqrt(sigma), n, ctx->misc_f, ctx->misc_f + n, ctx->misc_f + 2 * (size_t)n,
+                          ctx->stream), "star weight");
+    ctx->launches += 1;
+    CK(from_device(ctx, out, ctx->misc_f + 2 * (size_t)n, (size_t)n, mem), "copy weights");
     if (mem == DWOS_MEM_HOST) CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     return DWOS_OK;
 }
@@ -1094,6 +1249,7 @@ extern "C" dwos_status dwos_eval_static(dwos_ctx* ctx, int n_query, const float*
     if (n_query == 0) return DWOS_OK;
     if (!xq || !u_mean) return fail(ctx, DWOS_ERR_INVALID_ARG, "xq and u_mean must be device pointers");
     if (du_mean && ctx->n_param == 0) return fail(ctx, DWOS_ERR_INVALID_ARG, "derivatives requested but n_param = 0");
+    if (ctx->n_neumann > 0) return fail(ctx, DWOS_ERR_NOT_IMPLEMENTED, "dwos_eval_static with a Neumann part");
     for (const void* p : {(const void*)xq, (const void*)u_mean, (const void*)u_se, (const void*)du_mean,
                           (const void*)du_se})
         if (dwos_status s = check_device_ptr(ctx, p, "argument")) return s;

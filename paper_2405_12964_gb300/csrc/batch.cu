@@ -185,6 +185,7 @@ dwos_status dwos_batch_create(dwos_batch** out, const dwos_batch_job* jobs, int 
         if (!j.ctx) return bail(bfail(b, DWOS_ERR_INVALID_ARG, tag + "ctx is NULL"));
         if (j.ctx->device != b->device) return bail(bfail(b, DWOS_ERR_INVALID_ARG, tag + "contexts must share one device"));
         if (!j.ctx->have_boundary) return bail(bfail(b, DWOS_ERR_STATE, tag + "context has no boundary"));
+        if (j.ctx->n_neumann > 0) return bail(bfail(b, DWOS_ERR_NOT_IMPLEMENTED, tag + "batches of problems with a Neumann part"));
         if (j.n_query < 1 || j.walks_per_point < 1) return bail(bfail(b, DWOS_ERR_INVALID_ARG, tag + "empty job"));
         if (j.walks_per_point % j.ctx->opt.B) return bail(bfail(b, DWOS_ERR_INVALID_ARG, tag + "walks_per_point must be a multiple of B"));
         if (!on_device(j.xq, b->device) || !on_device(j.uref, b->device) || !on_device(j.loss, b->device))

@@ -29,8 +29,17 @@ struct dwos_ctx {
     int data_kind = 0;
     double field[10] = {0};
     float sigma = 0.0f, f = 0.0f;
-    dwos::BvhBuffers bvh;
+    dwos::BvhBuffers bvh;        // over every element, or over the Dirichlet part when there is a Neumann part
     bool have_boundary = false;
+    // reflecting Neumann part (walk on stars); n_neumann = 0 when every element is Dirichlet
+    int n_neumann = 0;
+    int* elem_d = nullptr;       // compact Dirichlet elements (the main BVH's numbering)
+    int* elem_n = nullptr;       // compact Neumann elements
+    int* dmap = nullptr;         // compact Dirichlet element -> input element
+    int* nadj = nullptr;         // per Neumann element and endpoint / edge: the neighbour's vertex, -1 open
+    dwos::BvhBuffers bvh_n;      // over the Neumann part
+    dwos::DevNeumann* d_neu = nullptr;
+    int* inside_tmp = nullptr; size_t inside_tmp_cap = 0;
 
     // workspaces (grow-only)
     dwos_record* rec = nullptr; size_t rec_cap = 0;

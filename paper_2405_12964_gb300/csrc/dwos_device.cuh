@@ -76,6 +76,31 @@ __device__ __forceinline__ float bessel_k0(float x) {
     return expf(-x) * rsqrtf(x) * p;
 }
 
+// Modified Bessel K1 for x > 0: Abramowitz & Stegun 9.8.7 (x <= 2, with I1)
+// and 9.8.8 (x > 2) polynomial approximations.
+__device__ __forceinline__ float bessel_k1(float x) {
+    if (x <= 2.0f) {
+        const float t = 0.25f * x * x;   // (x/2)^2
+        float p = -0.00004686f;
+        p = fmaf(p, t, -0.00110404f);
+        p = fmaf(p, t, -0.01919402f);
+        p = fmaf(p, t, -0.18156897f);
+        p = fmaf(p, t, -0.67278579f);
+        p = fmaf(p, t, 0.15443144f);
+        p = fmaf(p, t, 1.0f);             // x K1(x) = x log(x/2) I1(x) + p
+        return logf(0.5f * x) * cyl_bessel_i1f(x) + p / x;
+    }
+    const float t = 2.0f / x;
+    float p = -0.00068245f;
+    p = fmaf(p, t, 0.00325614f);
+    p = fmaf(p, t, -0.00780353f);
+    p = fmaf(p, t, 0.01504268f);
+    p = fmaf(p, t, -0.03655620f);
+    p = fmaf(p, t, 0.23498619f);
+    p = fmaf(p, t, 1.25331414f);
+    return expf(-x) * rsqrtf(x) * p;
+}
+
 // Russian roulette of Algorithm 1: true when the walk stops (alpha < u).
 // alpha >= exp(-(kd)^2/4) >= 1 - (kd)^2/4 in 2D (I0(x) <= exp(x^2/4)) and
 // alpha >= 1 - (kd)^2/6 in 3D (sinh(x)/x <= exp(x^2/6)); when u lies below that

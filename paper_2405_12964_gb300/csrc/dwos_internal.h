@@ -9,6 +9,22 @@
 
 namespace dwos {
 
+// The reflecting Neumann part of a mixed boundary (walk on stars): its own
+// BVH, its elements in compact numbering with their neighbours (for the
+// silhouette test), and the map from the Dirichlet BVH's compact element
+// numbering to the input numbering.
+struct DevNeumann {
+    const float4* nodes;        // binary BVH of the Neumann elements (layout of the main BVH)
+    const float4* prims;
+    const int* prim_elem;       // leaf -> Neumann element (compact)
+    int n_internal, n_tree, n_big, pad;
+    const int* elem;            // compact Neumann elements, dim vertex ids each
+    const int* adj;             // per Neumann element and endpoint (2D) / edge ab, bc, ca (3D): the
+                                // neighbour's vertex across it, -1 where the Neumann part ends
+    const float* vert;          // current vertices
+    const int* dmap;            // Dirichlet element (compact, the main BVH's numbering) -> input element
+};
+
 // Everything a walk needs about one problem.  Copied to the device (and, in
 // the walk kernel, into shared memory) once per launch.
 struct DevProblem {
@@ -57,6 +73,7 @@ struct DevProblem {
     float4* cv_sample;          // per walk: main walk's first-step point x1 and its source S0, or null
     float4* cv_end;             // per walk: main walk's last point (where it stopped), or null
     const float4* cv_elem;      // per element (q, t): surrogate grad u = q n + t for the nested walks' correction, or null
+    const DevNeumann* neu;      // reflecting Neumann part (walk on stars), or null
 };
 
 // Control variate applied by the estimator kernels: u - grad(x0) . (x1 - x0)
@@ -136,16 +153,18 @@ struct WalkLaunch {
     int blocks_per_sm;
     int n_sm;
     int traversal = 0;          // 2, 3: warp-wide search (every problem of the launch has wide_ok)
+    bool star = false;          // walk on stars (one problem with a Neumann part; traversal 0 or 1)
 };
 cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_probs,
                          unsigned long long total_work, DevCounters* d_counters, cudaStream_t stream,
                          int* blocks_used);
-int walk_max_blocks_per_sm(int dim, int block_size, int traversal = 0);
+int walk_max_blocks_per_sm(int dim, int block_size, int traversal = 0, bool star = false);
 // The walk step's ball weights (source factor for uniform u, recursive weight) and the
 // K0 of the 2D source weight, evaluated as the walk kernel evaluates them (walk.cu).
 cudaError_t launch_ball_weights(int dim, float k, int n, const float* d, const float* u, float* src, float* alpha,
                                 cudaStream_t stream);
-cudaError_t launch_bessel_k0(int n, const float* x, float* out, cudaStream_t stream);
+cudaError_t launch_bessel_k(int order, int n, const float* x, float* out, cudaStream_t stream);
+cudaError_t launch_star_weight(int dim, float k, int n, const float* t, const float* R, float* out, cudaStream_t stream);
 
 // Estimator reductions (estimators.cu).
 // mean / SE of the first `used` (0: all W) walks of each point

@@ -250,6 +250,7 @@ dwos_status dwos_sample_domain(dwos_ctx* ctx, int n_try, const float* box_lo, co
                                float* points, int* n_inside, float* weight) {
     if (!ctx) return DWOS_ERR_INVALID_ARG;
     if (!ctx->have_boundary) return ffail(ctx, DWOS_ERR_STATE, "no boundary: call dwos_set_boundary first");
+    if (ctx->n_neumann > 0) return ffail(ctx, DWOS_ERR_NOT_IMPLEMENTED, "shape functionals with a Neumann part");
     if (n_try < 1 || !points || !n_inside || !weight || !box_ok(ctx, box_lo, box_hi))
         return ffail(ctx, DWOS_ERR_INVALID_ARG, "bad arguments (box: hi > lo, finite; n_try >= 1)");
     FK(cudaSetDevice(ctx->device), "cudaSetDevice");
@@ -296,6 +297,7 @@ dwos_status dwos_boundary_term_l2(dwos_ctx* ctx, const float* box_lo, const floa
                                   double* grad_param, int mem) {
     if (!ctx) return DWOS_ERR_INVALID_ARG;
     if (!ctx->have_boundary) return ffail(ctx, DWOS_ERR_STATE, "no boundary: call dwos_set_boundary first");
+    if (ctx->n_neumann > 0) return ffail(ctx, DWOS_ERR_NOT_IMPLEMENTED, "shape functionals with a Neumann part");
     if (!box_ok(ctx, box_lo, box_hi) || (ctx->n_param > 0 && !grad_param) ||
         (mem != DWOS_MEM_HOST && mem != DWOS_MEM_DEVICE))
         return ffail(ctx, DWOS_ERR_INVALID_ARG, "bad arguments");
@@ -352,6 +354,7 @@ dwos_status dwos_boundary_loss_l2(dwos_ctx* ctx, const float* box_lo, const floa
                                   double* loss, double* grad_param, int mem) {
     if (!ctx) return DWOS_ERR_INVALID_ARG;
     if (!ctx->have_boundary) return ffail(ctx, DWOS_ERR_STATE, "no boundary: call dwos_set_boundary first");
+    if (ctx->n_neumann > 0) return ffail(ctx, DWOS_ERR_NOT_IMPLEMENTED, "shape functionals with a Neumann part");
     if (!box_ok(ctx, box_lo, box_hi) || !loss || (ctx->n_param > 0 && !grad_param) ||
         (mem != DWOS_MEM_HOST && mem != DWOS_MEM_DEVICE))
         return ffail(ctx, DWOS_ERR_INVALID_ARG, "bad arguments");

@@ -18,6 +18,7 @@
 // from its id alone.
 #include "dwos_device.cuh"
 #include "dwos_internal.h"
+#include "wost.cuh"
 
 namespace dwos {
 
@@ -91,17 +92,39 @@ struct PhaseState {
 };
 
 // Dynamic shared memory: the problem descriptors, then (warp-wide search only)
-// one traversal stack per warp and the threads' phase states.
-__host__ __device__ inline size_t walk_smem_bytes(int n_probs, int block_size, int traversal, int dim = 3) {
+// one traversal stack per warp and the threads' phase states, or (walk on
+// stars) the Neumann part's descriptor.
+__host__ __device__ inline size_t walk_smem_bytes(int n_probs, int block_size, int traversal, int dim = 3,
+                                                  bool star = false) {
     size_t b = (sizeof(DevProblem) * (size_t)n_probs + 15) & ~(size_t)15;
     if (traversal == 2 || traversal == 3)
         b += sizeof(float2) * kWideStack * (size_t)(block_size / 32) +
              (dim == 2 ? sizeof(PhaseState<2>) : sizeof(PhaseState<3>)) * (size_t)block_size;
+    if (star) b += sizeof(DevNeumann);
     return b;
 }
 
-template <int DIM, bool WIDE>
-__global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
+// Uniform direction on the unit circle / sphere from words 0 (and 1) of a block.
+template <int DIM>
+__device__ __forceinline__ void sphere_dir(const U4& r, float* om) {
+    if (DIM == 2) {
+        float s, c;
+        sincospif(2.0f * u01(r.x), &s, &c);
+        om[0] = c; om[1] = s; om[2] = 0.0f;
+    } else {
+        const float u0 = u01(r.x);
+        const float z = 1.0f - 2.0f * u0;
+        const float sth = 2.0f * sqrtf(u0 * (1.0f - u0));
+        float s, c;
+        sincospif(2.0f * u01(r.y), &s, &c);
+        om[0] = sth * c; om[1] = sth * s; om[2] = z;
+    }
+}
+
+// STAR: walk on stars over a boundary with a reflecting Neumann part (one
+// problem per launch, per-lane binary search of the Dirichlet part's BVH).
+template <int DIM, bool WIDE, bool STAR = false>
+__global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
     walk_kernel(const DevProblem* __restrict__ g_probs, int n_probs, unsigned long long total,
                 DevCounters* __restrict__ ctr) {
     constexpr bool wide = WIDE;
@@ -119,6 +142,18 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
         for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
     }
     __syncthreads();
+    DevNeumann& NS = *reinterpret_cast<DevNeumann*>(smem_raw + walk_smem_bytes(n_probs, 0, 0));
+    if constexpr (STAR) {
+        const int words = (int)(sizeof(DevNeumann) / sizeof(int));
+        const int* src = reinterpret_cast<const int*>(sp[0].neu);
+        int* dst = reinterpret_cast<int*>(&NS);
+        for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+        __syncthreads();
+    }
+    int on_e = -1;                  // STAR: the Neumann element the walk sits on (compact), -1 inside
+    float n_on[DIM];                // STAR: its normal, out of the domain
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) n_on[k] = 0.0f;
 
     const int lane = threadIdx.x & 31;
     bool active = false, exhausted = false;
@@ -167,6 +202,7 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
                         error |= finite ? 2 : 4;
                     } else {
                         phase = 0; step = 0; hint = -1; acc = 0.0f;
+                        on_e = -1;
                         active = true;
                     }
                 } else {
@@ -229,7 +265,8 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
         ++step;
         if (phase == 0) ++st.steps_main; else ++st.steps_nested;
 
-        const bool lost = best < 0;   // only with non-finite geometry or points: end the walk
+        bool lost = best < 0;   // only with non-finite geometry or points: end the walk
+        if constexpr (STAR) lost = lost || !(best2 < kInf);   // a walk that left the domain
         const bool shell = !lost && d < P.eps;
         const bool capped = !lost && !shell && step >= P.max_steps;
         int kind;
@@ -246,6 +283,7 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
             if (capped) ++st.capped;
             leaf_geometry<DIM>(P.prims, best, x, xbar, w1, w2, va, vb, vc);
             e = __ldg(P.prim_elem + best);
+            if constexpr (STAR) e = __ldg(NS.dmap + e);      // the Dirichlet BVH numbers its own elements
             if (P.data_kind == 1) {
                 float gr[DIM];
                 g = field_value<DIM>(P.field, xbar, gr);
@@ -254,6 +292,62 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
                 const float w0 = 1.0f - w1 - w2;
                 g = w0 * __ldg(P.g_vert + ev[0]) + w1 * __ldg(P.g_vert + ev[1]);
                 if (DIM == 3) g += w2 * __ldg(P.g_vert + ev[2]);
+            }
+        } else if constexpr (STAR) {
+            // walk on stars: R from the Dirichlet distance and the Neumann silhouettes
+            const unsigned long long wid = P.walk_id_base + local;
+            bool ok1 = true, ok2 = true, ok3 = true;
+            const float sd2 = silhouette_dist2<DIM>(NS, x, best2, ok1);
+            const float R = fmaxf(sqrtf(sd2), P.eps);
+            if (P.f != 0.0f) {   // source: a point of the ball, counted if x sees it
+                const U4 r1 = draw_block(P.seed_lo, P.seed_hi, wid, k_step, (uint32_t)phase, 1u);
+                float w[3];
+                sphere_dir<DIM>(r1, w);
+                float wn = 0.0f;
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) wn = fmaf(w[k], n_on[k], wn);
+                if (on_e >= 0 && wn > 0.0f) {
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) w[k] = -w[k];
+                }
+                const float ub = u01(r1.z);
+                const float rr = R * (DIM == 2 ? sqrtf(ub) : cbrtf(ub));
+                int h2;
+                ray_neumann<DIM>(NS, x, w, rr, on_e, h2, ok2);
+                if (h2 < 0) acc = fmaf(source_weight<DIM>(P.sqrt_sigma, R, ub), P.f, acc);
+            }
+            const U4 r0 = draw_block(P.seed_lo, P.seed_hi, wid, k_step, (uint32_t)phase, 0u);
+            float om[3];
+            sphere_dir<DIM>(r0, om);
+            float vn = 0.0f;
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) vn = fmaf(om[k], n_on[k], vn);
+            if (on_e >= 0 && vn > 0.0f) {   // on the Neumann part: the inward half-space
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) om[k] = -om[k];
+            }
+            int hit;
+            const float th = ray_neumann<DIM>(NS, x, om, R, on_e, hit, ok3);
+            if (!(ok1 && ok2 && ok3)) error |= 1;
+            const float t = hit >= 0 ? th : R;
+            if (P.sqrt_sigma > 0.0f && star_weight<DIM>(P.sqrt_sigma, t, R) < u01(r0.z)) {
+                kind = DWOS_KIND_ROULETTE;
+            } else {
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) x[k] = fmaf(t, om[k], x[k]);
+                if (hit >= 0) {   // on the Neumann part: its normal, oriented along the ray (out of the domain)
+                    neumann_normal<DIM>(NS, hit, n_on);
+                    float s = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) s = fmaf(n_on[k], om[k], s);
+                    if (s < 0.0f) {
+#pragma unroll
+                        for (int k = 0; k < DIM; ++k) n_on[k] = -n_on[k];
+                    }
+                }
+                on_e = hit;
+                hint = best;
+                continue;
             }
         } else {
             const unsigned long long wid = P.walk_id_base + local;
@@ -379,6 +473,26 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
             }
 #pragma unroll
             for (int k = 0; k < DIM; ++k) S.xoff[k] = fmaf(-P.h, S.nrm[k], xbar[k]);
+            if constexpr (STAR) {   // mirrored across the Neumann part where the offset crosses it
+                float back[3] = {-S.nrm[0], -S.nrm[1], DIM == 3 ? -S.nrm[DIM - 1] : 0.0f};
+                int he;
+                bool okr = true;
+                const float th = ray_neumann<DIM>(NS, xbar, back, P.h, -1, he, okr);
+                if (!okr) error |= 1;
+                if (he >= 0) {
+                    float m[3];
+                    neumann_normal<DIM>(NS, he, m);
+                    float c[DIM], r[DIM], rm = 0.0f;
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) {
+                        c[k] = fmaf(th, back[k], xbar[k]);
+                        r[k] = S.xoff[k] - c[k];
+                        rm = fmaf(r[k], m[k], rm);
+                    }
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) S.xoff[k] = c[k] + fmaf(-2.0f * rm, m[k], r[k]);
+                }
+            }
             S.g_main = g; S.b1 = w1; S.b2 = w2; S.leaf_main = best; S.e_main = e;
             S.sum_plain = 0.0f; S.sum_dn = 0.0f; S.sum_dt = 0.0f; S.sum_ball = 0.0f; S.w_ball = 0.0f;
         } else {
@@ -435,6 +549,7 @@ __global__ void __launch_bounds__(256, (DIM == 2 || WIDE) ? 4 : 3)
         ++phase;
         step = 0;
         acc = 0.0f;
+        on_e = -1;
         hint = S.leaf_main;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) x[k] = S.xoff[k];
@@ -477,9 +592,16 @@ __global__ void ball_weights_kernel(float k, int n, const float* __restrict__ d,
     if (alpha) alpha[i] = recursive_weight<DIM>(k, d[i]);
 }
 
-__global__ void bessel_k0_kernel(int n, const float* __restrict__ x, float* __restrict__ out) {
+__global__ void bessel_k_kernel(int order, int n, const float* __restrict__ x, float* __restrict__ out) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) out[i] = bessel_k0(x[i]);
+    if (i < n) out[i] = order == 0 ? bessel_k0(x[i]) : bessel_k1(x[i]);
+}
+
+template <int DIM>
+__global__ void star_weight_kernel(float k, int n, const float* __restrict__ t, const float* __restrict__ R,
+                                   float* __restrict__ out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = star_weight<DIM>(k, t[i], R[i]);
 }
 
 }  // namespace
@@ -493,16 +615,26 @@ cudaError_t launch_ball_weights(int dim, float k, int n, const float* d, const f
     return cudaGetLastError();
 }
 
-cudaError_t launch_bessel_k0(int n, const float* x, float* out, cudaStream_t stream) {
+cudaError_t launch_bessel_k(int order, int n, const float* x, float* out, cudaStream_t stream) {
     if (n <= 0) return cudaSuccess;
-    bessel_k0_kernel<<<(n + 255) / 256, 256, 0, stream>>>(n, x, out);
+    bessel_k_kernel<<<(n + 255) / 256, 256, 0, stream>>>(order, n, x, out);
     return cudaGetLastError();
 }
 
-int walk_max_blocks_per_sm(int dim, int block_size, int traversal) {
+cudaError_t launch_star_weight(int dim, float k, int n, const float* t, const float* R, float* out, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    if (dim == 2) star_weight_kernel<2><<<(n + 255) / 256, 256, 0, stream>>>(k, n, t, R, out);
+    else star_weight_kernel<3><<<(n + 255) / 256, 256, 0, stream>>>(k, n, t, R, out);
+    return cudaGetLastError();
+}
+
+int walk_max_blocks_per_sm(int dim, int block_size, int traversal, bool star) {
     int n = 0;
-    const size_t smem = walk_smem_bytes(1, block_size, traversal, dim);
-    if (traversal == 2 || traversal == 3) {
+    const size_t smem = walk_smem_bytes(1, block_size, traversal, dim, star);
+    if (star) {
+        if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<2, false, true>, block_size, smem);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<3, false, true>, block_size, smem);
+    } else if (traversal == 2 || traversal == 3) {
         if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<2, true>, block_size, smem);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<3, true>, block_size, smem);
     } else {
@@ -517,7 +649,9 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
     if (n_probs < 1 || n_probs > kMaxProblems) return cudaErrorInvalidValue;
     if (total == 0) { if (blocks_used) *blocks_used = 0; return cudaSuccess; }
     const int bs = L.block_size;
-    int per_sm = L.blocks_per_sm > 0 ? L.blocks_per_sm : walk_max_blocks_per_sm(L.dim, bs, L.traversal);
+    if (L.star && (n_probs != 1 || L.traversal == 2 || L.traversal == 3)) return cudaErrorInvalidValue;
+    int per_sm = L.blocks_per_sm > 0 ? L.blocks_per_sm
+                                     : walk_max_blocks_per_sm(L.dim, bs, L.traversal, L.star);
     if (per_sm < 1) per_sm = 1;
     long long blocks = (long long)per_sm * L.n_sm;
     const long long need = (long long)((total + bs - 1) / bs);
@@ -525,7 +659,7 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
     if (blocks < 1) blocks = 1;
     if (blocks_used) *blocks_used = (int)blocks;
     if (bs % 32 != 0) return cudaErrorInvalidValue;
-    const size_t smem = walk_smem_bytes(n_probs, bs, L.traversal, L.dim);
+    const size_t smem = walk_smem_bytes(n_probs, bs, L.traversal, L.dim, L.star);
     auto go = [&](auto kernel) -> cudaError_t {
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -534,6 +668,7 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
         kernel<<<(int)blocks, bs, smem, stream>>>(d_probs, n_probs, total, d_counters);
         return cudaGetLastError();
     };
+    if (L.star) return L.dim == 2 ? go(walk_kernel<2, false, true>) : go(walk_kernel<3, false, true>);
     if (L.traversal == 2 || L.traversal == 3) return L.dim == 2 ? go(walk_kernel<2, true>) : go(walk_kernel<3, true>);
     return L.dim == 2 ? go(walk_kernel<2, false>) : go(walk_kernel<3, false>);
 }

@@ -1,0 +1,256 @@
+// Device helpers of the walk-on-stars step (Sec. 3.4: mixed Dirichlet /
+// reflecting Neumann boundaries; the walk-on-stars estimator of Sawhney et
+// al. 2023).  From x the walk uses the star-shaped region St(x, R): the points
+// of the ball B(x, R) that x sees without crossing the Neumann part, with
+// R = max(min(distance to the Dirichlet part, distance to the closest
+// silhouette point of the Neumann part), eps).  A step samples a direction
+// (reflected into the inward half-space when x lies on the Neumann part),
+// casts the ray to the first Neumann crossing within R and moves there or to
+// x + R v; its survival weight is |S| t^(d-1) |G_R'(t)| for the step length t.
+#pragma once
+#include "dwos_device.cuh"
+#include "dwos_internal.h"
+
+namespace dwos {
+
+// Leaves of a binary BVH in near-first order with pruning: key(lo, hi) is a
+// lower bound of what any leaf under the box can give and leaf(l) may lower
+// `best`; a box whose key exceeds best is skipped.  The outsized leaves after
+// the tree's are offered first.  Stackless: the walk back up refetches each
+// parent and re-orders its children by the same keys.  Returns false if the
+// node budget ran out.
+template <int DIM, class Key, class Leaf>
+__device__ __forceinline__ bool bvh_best_first(const float4* __restrict__ nodes, int n_internal, int n_tree, int n_big,
+                                               const float& best, Key key, Leaf leaf) {
+    for (int p = n_tree; p < n_tree + n_big; ++p) leaf(p);
+    if (n_tree == 0) return true;
+    if (n_internal == 0) { leaf(0); return true; }
+    int budget = 4 * n_internal + 64;
+    int node = 0, from = kFromParent;
+    for (;;) {
+        if (--budget < 0) return false;
+        float lo0[DIM], hi0[DIM], lo1[DIM], hi1[DIM];
+        int c0, c1, parent;
+        load_node<DIM>(nodes, node, lo0, hi0, lo1, hi1, c0, c1, parent);
+        const float k0 = c0 == kEmptyChild ? kInf : key(lo0, hi0);
+        const float k1 = c1 == kEmptyChild ? kInf : key(lo1, hi1);
+        const bool first0 = k0 <= k1;
+        const int nearc = first0 ? c0 : c1, farc = first0 ? c1 : c0;
+        const float kn = first0 ? k0 : k1, kf = first0 ? k1 : k0;
+        int state = (from == kFromParent) ? 0 : (from == nearc ? 1 : 2);
+        int next = kFromParent;
+        for (;;) {
+            int cand = kFromParent;
+            if (state == 0) { if (kn <= best) cand = nearc; else state = 2; }
+            if (state == 1) { if (kf <= best) cand = farc; }
+            if (cand == kFromParent || cand == kEmptyChild) break;
+            if (cand < 0) {
+                leaf(~cand);
+                state = (state == 0) ? 1 : 2;
+                continue;
+            }
+            next = cand;
+            break;
+        }
+        if (next != kFromParent) { from = kFromParent; node = next; continue; }
+        if (node == 0) return true;
+        from = node;
+        node = parent;
+    }
+}
+
+template <int DIM>
+__device__ __forceinline__ void vload(const float* __restrict__ vert, int v, float* out) {
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) out[k] = __ldg(vert + (size_t)DIM * v + k);
+}
+
+// The silhouette rule from the two side tests s1, s2 and their scales m1, m2
+// (the products of the lengths involved): a side test within a relative 1e-4
+// of zero counts as collinear / coplanar.  Both collinear: the boundary runs
+// straight on through the vertex (flat across the edge) as seen from x, no
+// silhouette; one collinear and the other turning away: a silhouette; else a
+// silhouette when both neighbours lie on the same side.
+__device__ __forceinline__ bool silhouette_rule(float s1, float m1, float s2, float m2) {
+    const bool c1 = fabsf(s1) <= 1e-4f * m1, c2 = fabsf(s2) <= 1e-4f * m2;
+    if (c1 && c2) return false;
+    if (c1 || c2) return true;
+    return s1 * s2 > 0.0f;
+}
+
+// Squared distance from x to the closest silhouette point of the Neumann part
+// below `bound2` (bound2 itself if there is none): vertices (2D) or edges (3D)
+// where the part ends, or whose two elements lie on the same side of the ray
+// (2D) or plane (3D) through x (silhouette_rule).
+template <int DIM>
+__device__ __forceinline__ float silhouette_dist2(const DevNeumann& N, const float* x, float bound2, bool& ok) {
+    float best = bound2;
+    auto key = [&](const float* lo, const float* hi) { return box_dist2<DIM>(x, lo, hi); };
+    auto leaf = [&](int l) {
+        const int e = __ldg(N.prim_elem + l);
+        const int* ev = N.elem + (size_t)DIM * e;
+        if (DIM == 2) {
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                float v[2], w[2];
+                vload<2>(N.vert, __ldg(ev + j), v);
+                const float rv0 = v[0] - x[0], rv1 = v[1] - x[1];
+                const float d2 = rv0 * rv0 + rv1 * rv1;
+                if (d2 >= best) continue;
+                const int nb = __ldg(N.adj + 2 * (size_t)e + j);
+                bool sil = nb < 0;
+                if (!sil) {
+                    float z[2];
+                    vload<2>(N.vert, __ldg(ev + 1 - j), w);
+                    vload<2>(N.vert, nb, z);
+                    const float rw0 = w[0] - x[0], rw1 = w[1] - x[1], rz0 = z[0] - x[0], rz1 = z[1] - x[1];
+                    const float lv = sqrtf(d2);
+                    sil = silhouette_rule(rv0 * rw1 - rv1 * rw0, lv * sqrtf(rw0 * rw0 + rw1 * rw1),
+                                          rv0 * rz1 - rv1 * rz0, lv * sqrtf(rz0 * rz0 + rz1 * rz1));
+                }
+                if (sil) best = d2;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                float a[3], b[3];
+                vload<3>(N.vert, __ldg(ev + j), a);
+                vload<3>(N.vert, __ldg(ev + (j + 1) % 3), b);
+                const float ab[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+                const float ra[3] = {a[0] - x[0], a[1] - x[1], a[2] - x[2]};
+                const float len2 = ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2];
+                float t = len2 > 0.0f ? -(ra[0] * ab[0] + ra[1] * ab[1] + ra[2] * ab[2]) / len2 : 0.0f;
+                t = fminf(fmaxf(t, 0.0f), 1.0f);
+                const float o[3] = {ra[0] + t * ab[0], ra[1] + t * ab[1], ra[2] + t * ab[2]};
+                const float d2 = o[0] * o[0] + o[1] * o[1] + o[2] * o[2];
+                if (d2 >= best) continue;
+                const int nb = __ldg(N.adj + 3 * (size_t)e + j);
+                bool sil = nb < 0;
+                if (!sil) {
+                    float c[3], z[3];
+                    vload<3>(N.vert, __ldg(ev + (j + 2) % 3), c);
+                    vload<3>(N.vert, nb, z);
+                    const float rb[3] = {b[0] - x[0], b[1] - x[1], b[2] - x[2]};
+                    const float n[3] = {ra[1] * rb[2] - ra[2] * rb[1], ra[2] * rb[0] - ra[0] * rb[2],
+                                        ra[0] * rb[1] - ra[1] * rb[0]};
+                    const float rc[3] = {c[0] - x[0], c[1] - x[1], c[2] - x[2]};
+                    const float rz[3] = {z[0] - x[0], z[1] - x[1], z[2] - x[2]};
+                    const float ln = sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+                    sil = silhouette_rule(n[0] * rc[0] + n[1] * rc[1] + n[2] * rc[2],
+                                          ln * sqrtf(rc[0] * rc[0] + rc[1] * rc[1] + rc[2] * rc[2]),
+                                          n[0] * rz[0] + n[1] * rz[1] + n[2] * rz[2],
+                                          ln * sqrtf(rz[0] * rz[0] + rz[1] * rz[1] + rz[2] * rz[2]));
+                }
+                if (sil) best = d2;
+            }
+        }
+    };
+    ok = bvh_best_first<DIM>(N.nodes, N.n_internal, N.n_tree, N.n_big, best, key, leaf);
+    return best;
+}
+
+// Entry distance of the ray x + t v, t >= 0, into a box (kInf if it misses).
+template <int DIM>
+__device__ __forceinline__ float ray_box_entry(const float* x, const float* inv, const float* lo, const float* hi) {
+    float t0 = 0.0f, t1 = kInf;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        const float a = (lo[k] - x[k]) * inv[k], b = (hi[k] - x[k]) * inv[k];
+        t0 = fmaxf(t0, fminf(a, b));
+        t1 = fminf(t1, fmaxf(a, b));
+    }
+    return t0 <= t1 ? t0 : kInf;
+}
+
+// First crossing of the ray x + t v (0 < t < tmax) with a Neumann element
+// other than `skip` (compact numbering): returns t (tmax if none) and the
+// element in hit (-1 if none).
+template <int DIM>
+__device__ __forceinline__ float ray_neumann(const DevNeumann& N, const float* x, const float* v, float tmax, int skip,
+                                             int& hit, bool& ok) {
+    float best = tmax;
+    hit = -1;
+    float inv[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) inv[k] = 1.0f / v[k];
+    auto key = [&](const float* lo, const float* hi) { return ray_box_entry<DIM>(x, inv, lo, hi); };
+    auto leaf = [&](int l) {
+        const int e = __ldg(N.prim_elem + l);
+        if (e == skip) return;
+        float t;
+        if (DIM == 2) {
+            const float4 s = __ldg(N.prims + l);
+            const float ab0 = s.z - s.x, ab1 = s.w - s.y, ax0 = s.x - x[0], ax1 = s.y - x[1];
+            const float den = v[0] * ab1 - v[1] * ab0;
+            if (den == 0.0f) return;
+            t = (ax0 * ab1 - ax1 * ab0) / den;
+            const float u = (ax0 * v[1] - ax1 * v[0]) / den;
+            if (!(u >= -1e-5f && u <= 1.0f + 1e-5f)) return;     // no ray slips between two neighbours
+        } else {
+            const float4 a = __ldg(N.prims + 3 * l), b = __ldg(N.prims + 3 * l + 1), c = __ldg(N.prims + 3 * l + 2);
+            const float e1[3] = {b.x - a.x, b.y - a.y, b.z - a.z}, e2[3] = {c.x - a.x, c.y - a.y, c.z - a.z};
+            const float tv[3] = {x[0] - a.x, x[1] - a.y, x[2] - a.z};
+            const float p[3] = {v[1] * e2[2] - v[2] * e2[1], v[2] * e2[0] - v[0] * e2[2], v[0] * e2[1] - v[1] * e2[0]};
+            const float det = e1[0] * p[0] + e1[1] * p[1] + e1[2] * p[2];
+            if (det == 0.0f) return;
+            const float id = 1.0f / det;
+            const float u = (tv[0] * p[0] + tv[1] * p[1] + tv[2] * p[2]) * id;
+            if (!(u >= -1e-5f && u <= 1.0f + 1e-5f)) return;    // no ray slips between two neighbours
+            const float q[3] = {tv[1] * e1[2] - tv[2] * e1[1], tv[2] * e1[0] - tv[0] * e1[2], tv[0] * e1[1] - tv[1] * e1[0]};
+            const float w = (v[0] * q[0] + v[1] * q[1] + v[2] * q[2]) * id;
+            if (!(w >= -1e-5f && u + w <= 1.0f + 1e-5f)) return;
+            t = (e2[0] * q[0] + e2[1] * q[1] + e2[2] * q[2]) * id;
+        }
+        if (t > 0.0f && t < best) { best = t; hit = e; }
+    };
+    ok = bvh_best_first<DIM>(N.nodes, N.n_internal, N.n_tree, N.n_big, best, key, leaf);
+    return best;
+}
+
+// Unit normal (up to orientation) of Neumann element e.
+template <int DIM>
+__device__ __forceinline__ void neumann_normal(const DevNeumann& N, int e, float* m) {
+    const int* ev = N.elem + (size_t)DIM * e;
+    float a[DIM], b[DIM];
+    vload<DIM>(N.vert, __ldg(ev), a);
+    vload<DIM>(N.vert, __ldg(ev + 1), b);
+    if (DIM == 2) {
+        m[0] = b[1] - a[1];
+        m[1] = a[0] - b[0];
+    } else {
+        float c[DIM];
+        vload<DIM>(N.vert, __ldg(ev + 2), c);
+        const float e1[3] = {b[0] - a[0], b[1] - a[1], b[DIM - 1] - a[DIM - 1]};
+        const float e2[3] = {c[0] - a[0], c[1] - a[1], c[DIM - 1] - a[DIM - 1]};
+        m[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        m[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        m[DIM - 1] = e1[0] * e2[1] - e1[1] * e2[0];
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) s = fmaf(m[k], m[k], s);
+    s = rsqrtf(s);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) m[k] *= s;
+}
+
+// Survival weight of a star step of length t in the ball of radius R:
+// |S^(d-1)| t^(d-1) |G_R'(t)|, which is 1 for sigma = 0 and alpha(R) at t = R.
+//   2D: kt K1(kt) + kt I1(kt) K0(kR) / I0(kR)
+//   3D: (kt cosh(k(R - t)) + sinh(k(R - t))) / sinh(kR)
+//     = e^{-kt} (kt (1 + e^{-2a}) - expm1(-2a)) / -expm1(-2kR),  a = k (R - t)
+template <int DIM>
+__device__ __forceinline__ float star_weight(float k, float t, float R) {
+    if (k == 0.0f) return 1.0f;
+    if (t >= R) return recursive_weight<DIM>(k, R);
+    const float kt = k * t, kR = k * R;
+    if (DIM == 2) {
+        float w = kt * bessel_k1(kt);
+        if (kR < 80.0f) w += kt * cyl_bessel_i1f(kt) * bessel_k0(kR) / cyl_bessel_i0f(kR);
+        return w;
+    }
+    const float a = k * (R - t);
+    return expf(-kt) * (kt * (1.0f + expf(-2.0f * a)) - expm1f(-2.0f * a)) / -expm1f(-2.0f * kR);
+}
+
+}  // namespace dwos

@@ -84,6 +84,9 @@ _SIGS = {
     "dwos_philox4x32_10": [_vp, _i, _vp, _vp, _vp, _i],
     "dwos_ball_weights": [_vp, _i, ctypes.c_float, _i, _vp, _vp, _vp, _vp, _i],
     "dwos_bessel_k0": [_vp, _i, _vp, _vp, _i],
+    "dwos_bessel_k1": [_vp, _i, _vp, _vp, _i],
+    "dwos_star_weight": [_vp, _i, ctypes.c_float, _i, _vp, _vp, _vp, _i],
+    "dwos_set_neumann": [_vp, _vp, _i],
     "dwos_eval_static": [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp],
     "dwos_batch_create": [ctypes.POINTER(_vp), ctypes.POINTER(BatchJob), _i, _vp],
     "dwos_batch_run": [_vp],
@@ -229,6 +232,12 @@ class Solver:
         c = (ctypes.c_double * 10)(*[float(x) for x in np.asarray(coeffs, dtype=np.float64).reshape(-1)[:10]])
         self._check(lib().dwos_set_dirichlet_field(self._h, c))
 
+    def set_neumann(self, flags):
+        """dwos_set_neumann: per-element flags, 1 = reflecting Neumann element (None: all Dirichlet)."""
+        self._stream()
+        ft = None if flags is None else self._dev(np.asarray(flags, dtype=np.int32), torch.int32)
+        self._check(lib().dwos_set_neumann(self._h, _ptr(ft), MEM_DEVICE))
+
     def set_pde(self, sigma: float, f: float = 0.0):
         self._check(lib().dwos_set_pde(self._h, float(sigma), float(f)))
 
@@ -239,6 +248,8 @@ class Solver:
     def load_scene(self, sc, **opt):
         """Set boundary, data, PDE and the scene's eps / h / K / B / seed."""
         self.set_boundary(sc.vert, sc.elem, sc.jac)
+        if getattr(sc, "neumann", None) is not None:
+            self.set_neumann(sc.neumann)
         if sc.data == "field":
             self.set_dirichlet_field(sc.field)
         else:
@@ -522,10 +533,26 @@ class Solver:
 
     def bessel_k0(self, x):
         """K0(x) as the 2D source weight evaluates it (dwos_bessel_k0); numpy float32."""
+        return self._bessel(lib().dwos_bessel_k0, x)
+
+    def bessel_k1(self, x):
+        """K1(x) as the walk-on-stars step weight evaluates it (dwos_bessel_k1); numpy float32."""
+        return self._bessel(lib().dwos_bessel_k1, x)
+
+    def _bessel(self, fn, x):
         self._stream()
         xt = self._dev(x, torch.float32)
         out = torch.empty(xt.numel(), device=self.device, dtype=torch.float32)
-        self._check(lib().dwos_bessel_k0(self._h, xt.numel(), _ptr(xt), _ptr(out), MEM_DEVICE))
+        self._check(fn(self._h, xt.numel(), _ptr(xt), _ptr(out), MEM_DEVICE))
+        return out.cpu().numpy()
+
+    def star_weight(self, dim: int, sigma: float, t, R):
+        """The walk-on-stars step's survival weight (dwos_star_weight); numpy float32."""
+        self._stream()
+        tt, Rt = self._dev(t, torch.float32), self._dev(R, torch.float32)
+        out = torch.empty(tt.numel(), device=self.device, dtype=torch.float32)
+        self._check(lib().dwos_star_weight(self._h, int(dim), float(sigma), tt.numel(), _ptr(tt), _ptr(Rt), _ptr(out),
+                                           MEM_DEVICE))
         return out.cpu().numpy()
 
 
