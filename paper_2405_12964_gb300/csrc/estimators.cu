@@ -40,6 +40,21 @@ __device__ __forceinline__ double walk_u(const dwos_record* __restrict__ rec, lo
     return u;
 }
 
+// The same in FP32, for the scatter's per-walk weights.
+__device__ __forceinline__ float walk_u32(const dwos_record* __restrict__ rec, long long i, int p, const CvView cv) {
+    float u = rec[i].u;
+    if (cv.sample) {
+        const float4 s = cv.end ? cv.end[i] : cv.sample[i];
+        if (s.x == s.x) {
+            float dot = cv.grad[p * cv.dim] * (s.x - cv.xq[p * cv.dim]) +
+                        cv.grad[p * cv.dim + 1] * (s.y - cv.xq[p * cv.dim + 1]);
+            if (cv.dim == 3) dot += cv.grad[p * 3 + 2] * (s.z - cv.xq[p * 3 + 2]);
+            u -= dot;
+        }
+    }
+    return u;
+}
+
 // Mean (and standard error) of the first `used` walks of each point's W.
 __global__ void reduce_u_kernel(const dwos_record* __restrict__ rec, int W, int used, double* mean, double* se,
                                 CvView cv) {
@@ -131,6 +146,10 @@ __global__ void reduce_udot_kernel(const dwos_record* __restrict__ rec, const in
 // to global memory).  The table is then flushed with one FP64 atomic per
 // distinct vertex and value, so vertices that many walks reach (an enclosing
 // box, a coarse mesh) cost one global atomic per block instead of one per walk.
+// A walk's weight and its terms, and their sum over the lanes of a warp that
+// hold the same vertex, are FP32 like the walk values they come from (GB300's
+// FP64 rate is a small fraction of its FP32 rate); the table and the global
+// accumulators that sum them over walks are FP64.
 constexpr int kSlots = 1024;
 
 // Position of the n-th (0-based) set bit of m, or -1.
@@ -176,28 +195,28 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
         if (valid) r = rec[i];
         else { r.u = 0.0f; r.elem = -1; r.b1 = 0.0f; r.b2 = 0.0f; r.c[0] = r.c[1] = r.c[2] = 0.0f; r.meta = 0; }
         const int p = valid ? (int)(i / W) : 0;
-        const double u = valid ? walk_u(rec, i, p, cv) : 0.0;
-        double wt;
+        const float u = valid ? walk_u32(rec, i, p, cv) : 0.0f;
+        float wt;
         if (mode == 0) {
-            wt = valid ? (double)cot_or_uref[p] / W : 0.0;
+            wt = valid ? cot_or_uref[p] / (float)W : 0.0f;
         } else if (mode == 2) {
             // correlated product, Eq. (correlated_product): (mean u - uref) mean udot, all W walks
-            wt = valid ? (umean[p] - (double)cot_or_uref[p]) / W : 0.0;
+            wt = valid ? (float)(umean[p] - (double)cot_or_uref[p]) / (float)W : 0.0f;
         } else if (mode == 3) {
             // uncorrelated product, Eq. (uncorrelated_product): u from the first W/2 walks,
             // udot from the other W/2
             const int M = W / 2;
-            wt = (valid && (int)(i % W) >= M) ? (umean[p] - (double)cot_or_uref[p]) / M : 0.0;
+            wt = (valid && (int)(i % W) >= M) ? (float)(umean[p] - (double)cot_or_uref[p]) / (float)M : 0.0f;
         } else {
             // U-statistic weight, Eq. (ustatistics): u*udot is estimated by
             // sum_m udot_m (S - u_m)/(B(B-1)), uref*udot by uref sum_m udot_m / B;
             // each batch is one of W/B estimates of the point's derivative.
-            double S = u;
+            float S = u;
             for (int o = B >> 1; o > 0; o >>= 1) S += __shfl_xor_sync(kFull, S, o);
-            const double ur = valid ? (double)cot_or_uref[p] : 0.0;
-            wt = ((S - u) / ((double)B * (B - 1)) - ur / B) / (double)(W / B);
+            const float ur = valid ? cot_or_uref[p] : 0.0f;
+            wt = ((S - u) / (float)(B * (B - 1)) - ur / (float)B) / (float)(W / B);
         }
-        if (pweight && valid) wt *= (double)pweight[p];     // quadrature weight of the point
+        if (pweight && valid) wt *= pweight[p];     // quadrature weight of the point
         const bool hit = valid && r.elem >= 0;
         const float wv[3] = {1.0f - r.b1 - r.b2, r.b1, r.b2};
         const int lane = threadIdx.x & 31;
@@ -206,10 +225,10 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
             int vid = hit ? __ldg(elem + DIM * r.elem + sidx) : -1;
             if (active && vid >= 0 && !__ldg(active + vid)) vid = -1;   // cannot reach the gradient
             if (!__any_sync(kFull, vid >= 0)) continue;
-            const double ws = vid >= 0 ? wt * (double)wv[sidx] : 0.0;
-            double val[NV];
+            const float ws = vid >= 0 ? wt * wv[sidx] : 0.0f;
+            float val[NV];
 #pragma unroll
-            for (int k = 0; k < DIM; ++k) val[k] = ws * (double)r.c[k];
+            for (int k = 0; k < DIM; ++k) val[k] = ws * r.c[k];
             if (G) val[NV - 1] = ws;
             // sum over the lanes that hold the same vertex: a log-step tree over
             // each peer group (lane of rank j adds the partial sum of rank j + off)
@@ -221,7 +240,7 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
                     const bool has = src >= 0;
 #pragma unroll
                     for (int k = 0; k < NV; ++k) {
-                        const double t = __shfl_sync(kFull, val[k], has ? src : lane);
+                        const float t = __shfl_sync(kFull, val[k], has ? src : lane);
                         if (has) val[k] += t;
                     }
                 }
@@ -234,14 +253,14 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
                 const int prev = atomicCAS(&keys[slot], -1, vid);
                 if (prev == -1 || prev == vid) {
 #pragma unroll
-                    for (int k = 0; k < NV; ++k) atomicAdd(&vals[slot][k], val[k]);
+                    for (int k = 0; k < NV; ++k) atomicAdd(&vals[slot][k], (double)val[k]);
                     done = true;
                 }
             }
             if (!done) {
 #pragma unroll
-                for (int k = 0; k < DIM; ++k) atomicAdd(acc_vert + (size_t)vid * DIM + k, val[k]);
-                if (G) atomicAdd(acc_g + vid, val[NV - 1]);
+                for (int k = 0; k < DIM; ++k) atomicAdd(acc_vert + (size_t)vid * DIM + k, (double)val[k]);
+                if (G) atomicAdd(acc_g + vid, (double)val[NV - 1]);
             }
         }
     }

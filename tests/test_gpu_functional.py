@@ -100,7 +100,9 @@ def test_weighted_gradient_matches_oracle(Solver):
     g0 = s.grad_l2(pts, ur, W)[1].cpu().numpy()
     g2 = s.grad_l2_weighted(pts, ur, np.full(len(p), 2.5, np.float32), W)[1].cpu().numpy()
     assert np.allclose(g1, g0, rtol=1e-9, atol=1e-12 * np.abs(g0).max())
-    assert np.allclose(g2, 2.5 * g0, rtol=1e-9, atol=1e-12 * np.abs(g0).max())
+    # the per-walk weights are FP32: a factor of 2.5 rounds each walk's term afresh
+    # (relative 2^-24 a term), the FP64 sums over walks then differ in the last FP32 bits
+    assert np.allclose(g2, 2.5 * g0, rtol=1e-6, atol=1e-6 * np.abs(g0).max())
 
 
 def test_functional_gradient_matches_the_closed_form(Solver):
