@@ -552,21 +552,15 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    steps_done = nodes = wnodes = prims = 0
-    kernel_ms = []
-    grads = []
+    # the timed steps are enqueued back to back (no host synchronisation inside the
+    # region), each bracketed by its own events, with the L2 flush between them
+    grads_dev = []
     for i in range(args.steps):
         flush.fill_(float(i))                      # evict L2 between timed steps (outside the events)
         ev[i][0].record(stream)
         loss, g = step(args.warmup + i)
         ev[i][1].record(stream)
-        st = s.stats()                             # synchronises; outside the events
-        steps_done += st["steps_main"] + st["steps_nested"]
-        nodes += st["nodes_visited"]
-        wnodes += st["wide_nodes_visited"]
-        prims += st["prims_tested"]
-        kernel_ms.append(st["kernel_ms"])
-        grads.append(g.cpu().numpy())
+        grads_dev.append(g)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -574,6 +568,20 @@ def main():
     launches = s.stats()["launches"] - launches_warm
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_local = sum(step_ms) / 1e3
+    grads = [g.cpu().numpy() for g in grads_dev]
+    # walk-step counts, search counters and the walk kernel's own launch time: the
+    # same steps replayed one at a time (same walk ids, hence the same walks)
+    steps_done = nodes = wnodes = prims = 0
+    kernel_ms = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        step(args.warmup + i)
+        st = s.stats()                             # synchronises
+        steps_done += st["steps_main"] + st["steps_nested"]
+        nodes += st["nodes_visited"]
+        wnodes += st["wide_nodes_visited"]
+        prims += st["prims_tested"]
+        kernel_ms.append(st["kernel_ms"])
     t, steps_all = aggregate_ranks(t_local, steps_done, dist, dev)
     value = steps_all / t
     ms_per_step = 1e3 * t / args.steps
@@ -643,6 +651,9 @@ def main():
                                                 3: "routed: binary-root test per query, then the 32-wide BVH "
                                                    "warp-wide for the queries that need the tree"}[trav],
                        "l2": "flushed between timed steps (256 MB write outside the events)",
+                       "timing": ("timed steps enqueued back to back, each between its own CUDA events; "
+                                  "walk-step counts and the walk kernel's launch time from a replay of the "
+                                  "same walk ids"),
                        "parallelism": f"replicas x{world} (independent walk ranges, no collective)"},
             "gradient_estimates_per_s": world * total * args.steps / t,
             "grad_rmse": rmse, "grad_rel_rmse": rel, "grad_rmse_x_seconds": rmse * (ms_per_step / 1e3),

@@ -27,8 +27,11 @@
  *    outputs and dwos_last_error() describes the cause.
  *  - Pointers are host or device memory as the call's `mem` flag says
  *    (DWOS_MEM_HOST / DWOS_MEM_DEVICE; device pointers must be on the
- *    context's device).  The library copies every input it keeps; the caller
- *    keeps ownership of all its buffers.
+ *    context's device).  The library copies every input it keeps (geometry,
+ *    data, parameters); the caller keeps ownership of all its buffers.  A
+ *    call's own device inputs (query points, targets, weights) are read in
+ *    place by its work on the context's stream: keep them valid and unchanged
+ *    until that work has run, as for any stream-ordered CUDA call.
  *  - Work is enqueued on the context's stream (dwos_set_stream).  A call whose
  *    outputs are host memory synchronises that stream before it returns; a
  *    call whose outputs are device memory returns as soon as the work is

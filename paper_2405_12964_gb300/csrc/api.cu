@@ -94,7 +94,12 @@ dwos_status set_device(dwos_ctx* ctx) {
     return DWOS_OK;
 }
 
+// The counters of the current launch (of two buffers; the other one is kept
+// zero for the next walk launch, which zeroes this one in turn).
+inline DevCounters* cur_ctr(dwos_ctx* ctx) { return ctx->d_ctr + ctx->ctr_cur; }
+
 dwos_status rebuild(dwos_ctx* ctx) {
+    ctx->inside_cached = -1;   // the inside flags belong to the old geometry
     if (ctx->n_neumann == 0) {
         CK(bvh_build(ctx->bvh, ctx->dim, ctx->vert, ctx->elem, ctx->n_elem, ctx->stream), "BVH build");
         return DWOS_OK;
@@ -154,9 +159,15 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     if (mem == DWOS_MEM_HOST && n_query > 0 && !finite_all(xq, (size_t)n_query * ctx->dim))
         return fail(ctx, DWOS_ERR_INVALID_ARG, "query points must be finite");
     if (mem == DWOS_MEM_DEVICE) { dwos_status s = check_device_ptr(ctx, xq, "xq"); if (s) return s; }
-    CK(grow(ctx->xq, ctx->xq_cap, (size_t)n_query * ctx->dim), "alloc xq");
     CK(grow(ctx->rec, ctx->rec_cap, (size_t)total), "alloc records");
-    CK(to_device(ctx, ctx->xq, xq, (size_t)n_query * ctx->dim, mem), "copy xq");
+    // device query points are read in place (stream order); host ones are staged
+    const float* d_xq = xq;
+    if (mem == DWOS_MEM_HOST) {
+        CK(grow(ctx->xq, ctx->xq_cap, (size_t)n_query * ctx->dim), "alloc xq");
+        CK(to_device(ctx, ctx->xq, xq, (size_t)n_query * ctx->dim, mem), "copy xq");
+        d_xq = ctx->xq;
+    }
+    ctx->xq_in = d_xq;
     const int* valid = nullptr;
     if (ctx->n_neumann > 0) {
         if (ctx->opt.dudn_estimator != 0)
@@ -166,8 +177,19 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     }
     if (ctx->opt.check_inside && n_query > 0) {
         CK(grow(ctx->valid, ctx->valid_cap, (size_t)n_query), "alloc inside flags");
-        CK(inside_all(ctx, n_query, ctx->xq, ctx->valid), "inside test");
-        ctx->launches += ctx->n_neumann > 0 ? 3 : 1;
+        if (ctx->n_neumann == 0) {
+            // the flags of points equal to the previous call's (same geometry) are kept
+            CK(grow(ctx->xq_prev, ctx->xq_prev_cap, (size_t)n_query * ctx->dim), "alloc inside cache");
+            const bool cached = ctx->inside_cached == n_query;
+            ctx->inside_cached = -1;
+            CK(launch_inside(ctx->bvh, n_query, d_xq, ctx->valid, ctx->stream, cached ? ctx->xq_prev : nullptr,
+                             ctx->xq_prev), "inside test");
+            ctx->inside_cached = n_query;
+            ctx->launches += 1;
+        } else {
+            CK(inside_all(ctx, n_query, d_xq, ctx->valid), "inside test");
+            ctx->launches += 3;
+        }
         valid = ctx->valid;
     }
     DevProblem P;
@@ -200,7 +222,7 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     P.dudn_mode = ctx->opt.dudn_estimator;
     P.seed_lo = (uint32_t)ctx->opt.seed;
     P.seed_hi = (uint32_t)(ctx->opt.seed >> 32);
-    P.xq = ctx->xq;
+    P.xq = d_xq;
     P.valid = valid;
     P.walks = W;
     P.node_budget = ctx->node_budget;
@@ -216,8 +238,11 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     P.neu = ctx->n_neumann > 0 ? ctx->d_neu : nullptr;
     if (P.neu && (P.traversal == 2 || P.traversal == 3)) P.traversal = 0;   // per-lane search of the Dirichlet tree
     if (cv_sample) CK(cudaMemsetAsync(cv_sample, 0xff, sizeof(float4) * total, ctx->stream), "init samples");
-    CK(cudaMemcpyAsync(ctx->d_prob, &P, sizeof(P), cudaMemcpyHostToDevice, ctx->stream), "copy problem");
-    CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->stream), "reset counters");
+    // counters: this launch takes the zeroed buffer and zeroes the other for the next one
+    if (!ctx->ctr_next_zero)
+        CK(cudaMemsetAsync(ctx->d_ctr + (ctx->ctr_cur ^ 1), 0, sizeof(DevCounters), ctx->stream), "reset counters");
+    ctx->ctr_cur ^= 1;
+    ctx->ctr_next_zero = false;
     WalkLaunch L;
     L.dim = ctx->dim;
     L.block_size = ctx->opt.block_size > 0 ? ctx->opt.block_size : 256;
@@ -227,7 +252,9 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     L.star = P.neu != nullptr;
     CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
     int blocks = 0;
-    CK(launch_walks(L, ctx->d_prob, 1, total, ctx->d_ctr, ctx->stream, &blocks), "walk kernel");
+    CK(launch_walks(L, nullptr, 1, total, cur_ctr(ctx), ctx->stream, &blocks, &P, ctx->d_ctr + (ctx->ctr_cur ^ 1)),
+       "walk kernel");
+    ctx->ctr_next_zero = true;
     ctx->launches += blocks > 0 ? 1 : 0;
     ctx->last_blocks = blocks;
     CK(cudaEventRecord(ctx->ev1, ctx->stream), "event");
@@ -239,7 +266,7 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
 dwos_status finish_sync(dwos_ctx* ctx) {
     CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     DevCounters c;
-    CK(cudaMemcpy(&c, ctx->d_ctr, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
+    CK(cudaMemcpy(&c, cur_ctr(ctx), sizeof(c), cudaMemcpyDeviceToHost), "read counters");
     if (c.error & 4) return fail(ctx, DWOS_ERR_INVALID_ARG, "a query point is not finite");
     if (c.error & 2) return fail(ctx, DWOS_ERR_OUTSIDE, "a query point lies outside the domain");
     if (c.error & 1) return fail(ctx, DWOS_ERR_STEP_LIMIT, "BVH traversal exceeded its iteration bound");
@@ -321,12 +348,11 @@ dwos_status dwos_create(dwos_ctx** out, int device) {
     dwos_default_options(&ctx->opt);
     cudaError_t ce = cudaSetDevice(device);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
-    if (ce == cudaSuccess) ce = cudaMalloc(&ctx->d_prob, sizeof(DevProblem));
-    if (ce == cudaSuccess) ce = cudaMalloc(&ctx->d_ctr, sizeof(DevCounters));
+    if (ce == cudaSuccess) ce = cudaMalloc(&ctx->d_ctr, 2 * sizeof(DevCounters));
     if (ce == cudaSuccess) ce = cudaMalloc(&ctx->d_err, sizeof(int));
     if (ce == cudaSuccess) ce = cudaEventCreate(&ctx->ev0);
     if (ce == cudaSuccess) ce = cudaEventCreate(&ctx->ev1);
-    if (ce == cudaSuccess) ce = cudaMemset(ctx->d_ctr, 0, sizeof(DevCounters));
+    if (ce == cudaSuccess) ce = cudaMemset(ctx->d_ctr, 0, 2 * sizeof(DevCounters));
     if (ce != cudaSuccess) {
         cudaGetLastError();
         g_create_err = std::string("context setup failed: ") + cudaGetErrorString(ce);
@@ -344,7 +370,7 @@ void dwos_destroy(dwos_ctx* ctx) {
     bvh_free(ctx->bvh);
     void* bufs[] = {ctx->vert_ref, ctx->vert, ctx->elem, ctx->jac, ctx->theta, ctx->g_vert, ctx->dg_vert, ctx->rec,
                     ctx->xq, ctx->valid, ctx->wvec, ctx->out, ctx->acc_vert, ctx->trace, ctx->dbg, ctx->misc_f,
-                    ctx->misc_i, ctx->misc_u, ctx->d_prob, ctx->d_ctr, ctx->d_err, ctx->pw, ctx->vert_active,
+                    ctx->misc_i, ctx->misc_u, ctx->xq_prev, ctx->d_ctr, ctx->d_err, ctx->pw, ctx->vert_active,
                     ctx->misc_d, ctx->elem_d, ctx->elem_n, ctx->dmap, ctx->nadj, ctx->d_neu, ctx->inside_tmp};
     bvh_free(ctx->bvh_n);
     for (void* p : bufs) if (p) cudaFree(p);
@@ -665,18 +691,29 @@ static dwos_status reverse_common(dwos_ctx* ctx, int n_query, const float* xq, c
     if (dwos_status s = set_device(ctx)) return s;
     if (dwos_status s = run_walks(ctx, n_query, xq, W, base, 1, mem, nullptr, nullptr)) return s;
     const int N = ctx->n_param;
-    CK(grow(ctx->wvec, ctx->wvec_cap, (size_t)std::max(n_query, 1)), "alloc weights");
-    CK(to_device(ctx, ctx->wvec, wv, (size_t)n_query, mem), "copy weights");
+    // device weights are read in place (stream order); host ones are staged
+    const float* d_w = wv;
+    if (mem == DWOS_MEM_HOST) {
+        CK(grow(ctx->wvec, ctx->wvec_cap, (size_t)std::max(n_query, 1)), "alloc weights");
+        CK(to_device(ctx, ctx->wvec, wv, (size_t)n_query, mem), "copy weights");
+        d_w = ctx->wvec;
+    }
     const float* d_pw = nullptr;
     if (pweight) {
-        CK(grow(ctx->pw, ctx->pw_cap, (size_t)std::max(n_query, 1)), "alloc point weights");
-        CK(to_device(ctx, ctx->pw, pweight, (size_t)n_query, mem), "copy point weights");
-        d_pw = ctx->pw;
+        d_pw = pweight;
+        if (mem == DWOS_MEM_HOST) {
+            CK(grow(ctx->pw, ctx->pw_cap, (size_t)std::max(n_query, 1)), "alloc point weights");
+            CK(to_device(ctx, ctx->pw, pweight, (size_t)n_query, mem), "copy point weights");
+            d_pw = ctx->pw;
+        }
     }
-    const size_t nacc = (size_t)ctx->n_vert * ctx->dim + (size_t)ctx->n_vert;
+    // accumulators: per-vertex sums (and data sums), then the per-point sums of u (U-statistic mode)
+    const size_t nvacc = (size_t)ctx->n_vert * ctx->dim + (size_t)ctx->n_vert;
+    const size_t nacc = nvacc + (mode == 1 ? (size_t)n_query : 0);
     CK(grow(ctx->acc_vert, ctx->acc_cap, nacc), "alloc accumulators");
     CK(cudaMemsetAsync(ctx->acc_vert, 0, nacc * sizeof(double), ctx->stream), "zero accumulators");
     double* acc_g = ctx->dg_vert ? ctx->acc_vert + (size_t)ctx->n_vert * ctx->dim : nullptr;
+    double* d_usum = mode == 1 ? ctx->acc_vert + nvacc : nullptr;
     const size_t need = 2 * (size_t)n_query + (size_t)std::max(N, 1) + 1;
     CK(grow(ctx->out, ctx->out_cap, need), "alloc outputs");
     double* d_umean = ctx->out + std::max(N, 1) + n_query + 1;   // per-point mean for the product weights
@@ -690,22 +727,27 @@ static dwos_status reverse_common(dwos_ctx* ctx, int n_query, const float* xq, c
         if (dwos_status s = ensure_vert_active(ctx)) return s;
         active = ctx->vert_active;
     }
-    CK(launch_scatter(ctx->rec, ctx->elem, ctx->dim, n_query, W, ctx->opt.B, mode, ctx->wvec, ctx->acc_vert, acc_g,
-                      ctx->stream, nullptr, d_umean, d_pw, active), "scatter");
-    ctx->launches += n_query > 0 ? 1 : 0;
     double* d_grad = mem == DWOS_MEM_DEVICE ? grad_param : ctx->out;
+    // the scatter also zeroes the parameter gradient the adjoint GEMV accumulates into
+    CK(launch_scatter(ctx->rec, ctx->elem, ctx->dim, n_query, W, ctx->opt.B, mode, d_w, ctx->acc_vert, acc_g,
+                      ctx->stream, nullptr, d_umean, d_pw, active, d_usum, N > 0 ? d_grad : nullptr, N), "scatter");
+    ctx->launches += n_query > 0 ? 1 : 0;
     if (N > 0) {
-        CK(cudaMemsetAsync(d_grad, 0, (size_t)N * sizeof(double), ctx->stream), "zero grad");
         CK(launch_gemv(ctx->jac, ctx->dg_vert, ctx->acc_vert, acc_g, ctx->n_vert, ctx->dim, N, d_grad, ctx->stream), "adjoint gemv");
         ctx->launches += 1;
     }
     double* d_loss = nullptr;
     if (mode >= 1) {
-        double* d_mean = ctx->out + std::max(N, 1);
-        CK(launch_reduce_u(ctx->rec, n_query, W, d_mean, nullptr, ctx->stream), "reduce u");
         d_loss = mem == DWOS_MEM_DEVICE ? loss : ctx->out + std::max(N, 1) + n_query;
-        CK(launch_loss(d_mean, ctx->wvec, n_query, d_loss, ctx->stream, d_pw), "loss");
-        ctx->launches += n_query > 0 ? 2 : 1;
+        if (mode == 1) {   // the means from the scatter's per-point sums
+            CK(launch_loss(d_usum, d_w, n_query, d_loss, ctx->stream, d_pw, 1.0 / W), "loss");
+            ctx->launches += 1;
+        } else {
+            double* d_mean = ctx->out + std::max(N, 1);
+            CK(launch_reduce_u(ctx->rec, n_query, W, d_mean, nullptr, ctx->stream), "reduce u");
+            CK(launch_loss(d_mean, d_w, n_query, d_loss, ctx->stream, d_pw), "loss");
+            ctx->launches += n_query > 0 ? 2 : 1;
+        }
     }
     if (grad_vert)
         CK(from_device(ctx, grad_vert, ctx->acc_vert, (size_t)ctx->n_vert * ctx->dim, mem), "copy vertex gradient");
@@ -774,7 +816,7 @@ dwos_status dwos_grad_l2_cv(dwos_ctx* ctx, int n_query, const float* xq, const f
     if (dwos_status s = run_walks(ctx, n_query, xq, W, walk_id_base, 1, DWOS_MEM_DEVICE, nullptr, debug, smp, end,
                                   reinterpret_cast<const float4*>(cv_elem)))
         return s;
-    const CvView cv{smp, cv_grad, ctx->xq, ctx->dim, end};
+    const CvView cv{smp, cv_grad, ctx->xq_in, ctx->dim, end};
     const CvView* cvp = cv_grad ? &cv : nullptr;
     const int N = ctx->n_param;
     CK(grow(ctx->wvec, ctx->wvec_cap, (size_t)n_query), "alloc weights");
@@ -1010,7 +1052,7 @@ dwos_status dwos_last_stats(dwos_ctx* ctx, dwos_run_stats* out) {
     if (dwos_status s = set_device(ctx)) return s;
     CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     DevCounters c;
-    CK(cudaMemcpy(&c, ctx->d_ctr, sizeof(c), cudaMemcpyDeviceToHost), "read counters");
+    CK(cudaMemcpy(&c, cur_ctr(ctx), sizeof(c), cudaMemcpyDeviceToHost), "read counters");
     out->steps_main = c.steps_main;
     out->steps_nested = c.steps_nested;
     out->walks = c.next_work;
@@ -1045,9 +1087,9 @@ static dwos_status closest_common(dwos_ctx* ctx, int n, const float* p, const in
     CK(to_device(ctx, dp, p, (size_t)n * ctx->dim, mem), "copy points");
     if (hint) { dh = ctx->misc_i + std::max(n, 1); CK(to_device(ctx, dh, hint, (size_t)n, mem), "copy hints"); }
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), ctx->stream), "reset");
-    CK(cudaMemsetAsync(ctx->d_ctr, 0, sizeof(DevCounters), ctx->stream), "reset counters");
+    CK(cudaMemsetAsync(cur_ctr(ctx), 0, sizeof(DevCounters), ctx->stream), "reset counters");
     if (hint && ctx->n_neumann > 0) return fail(ctx, DWOS_ERR_NOT_IMPLEMENTED, "hinted queries with a Neumann part");
-    CK(launch_closest(ctx->bvh, n, dp, dh, dd, ctx->misc_i, db, ctx->d_err, ctx->d_ctr, effective_traversal(ctx),
+    CK(launch_closest(ctx->bvh, n, dp, dh, dd, ctx->misc_i, db, ctx->d_err, cur_ctr(ctx), effective_traversal(ctx),
                       ctx->stream), "closest point");
     ctx->launches += n > 0 ? 1 : 0;
     if (ctx->n_neumann > 0 && n > 0) {   // the Dirichlet tree numbers its own elements

@@ -47,8 +47,6 @@ struct dwos_batch {
     std::vector<size_t> trace_off;
     double* acc = nullptr;              // per job: n_vert*dim + n_vert doubles
     std::vector<size_t> acc_off;
-    double* means = nullptr;            // per job: n_query doubles
-    std::vector<size_t> mean_off;
     unsigned char* active = nullptr;    // per job: n_vert vertex flags (nonzero Jacobian / dg row)
     std::vector<size_t> active_off;
     WalkLaunch cfg[4];                  // per dimension (index 2 and 3)
@@ -218,18 +216,15 @@ dwos_status dwos_batch_create(dwos_batch** out, const dwos_batch_job* jobs, int 
         cudaFree(flags);
     }
     // buffers
-    size_t n_rec = 0, n_acc = 0, n_mean = 0;
+    size_t n_rec = 0, n_acc = 0;
     for (auto& j : b->jobs) {
         b->rec_off.push_back(n_rec);
         b->acc_off.push_back(n_acc);
-        b->mean_off.push_back(n_mean);
         n_rec += (size_t)j.n_query * j.walks_per_point;
-        n_acc += (size_t)j.ctx->n_vert * j.ctx->dim + j.ctx->n_vert;
-        n_mean += j.n_query;
+        n_acc += (size_t)j.ctx->n_vert * j.ctx->dim + j.ctx->n_vert + j.n_query;   // + per-point sums of u
     }
     if ((e = cudaMalloc(&b->rec, sizeof(dwos_record) * n_rec)) != cudaSuccess) return bail(bcuda(b, e, "alloc records"));
     if ((e = cudaMalloc(&b->acc, sizeof(double) * n_acc)) != cudaSuccess) return bail(bcuda(b, e, "alloc accumulators"));
-    if ((e = cudaMalloc(&b->means, sizeof(double) * n_mean)) != cudaSuccess) return bail(bcuda(b, e, "alloc means"));
     // vertices with zero Jacobian and dg rows cannot reach a job's parameter gradient: the
     // scatter skips them (the batch returns no vertex gradients)
     {
@@ -278,7 +273,6 @@ void dwos_batch_destroy(dwos_batch* b) {
     cudaFree(b->rec);
     cudaFree(b->trace);
     cudaFree(b->acc);
-    cudaFree(b->means);
     cudaFree(b->active);
     if (b->ev0) cudaEventDestroy(b->ev0);
     if (b->ev1) cudaEventDestroy(b->ev1);
@@ -295,19 +289,19 @@ dwos_status dwos_batch_run(dwos_batch* b) {
         const dwos_batch_job& j = b->jobs[i];
         const dwos_ctx* c = j.ctx;
         double* acc = b->acc + b->acc_off[i];
-        const size_t nacc = (size_t)c->n_vert * c->dim + c->n_vert;
+        const size_t nvacc = (size_t)c->n_vert * c->dim + c->n_vert;
         double* acc_g = c->dg_vert ? acc + (size_t)c->n_vert * c->dim : nullptr;
+        double* usum = acc + nvacc;
         const dwos_record* rec = b->rec + b->rec_off[i];
-        BK(cudaMemsetAsync(acc, 0, nacc * sizeof(double), b->stream), "zero accumulators");
+        BK(cudaMemsetAsync(acc, 0, (nvacc + j.n_query) * sizeof(double), b->stream), "zero accumulators");
+        // the scatter also sums u per point and zeroes the gradient the GEMV accumulates into
         BK(launch_scatter(rec, c->elem, c->dim, j.n_query, j.walks_per_point, c->opt.B, 1, j.uref, acc, acc_g, b->stream,
-                          nullptr, nullptr, nullptr, b->active + b->active_off[i]), "scatter");
-        if (c->n_param > 0) {
-            BK(cudaMemsetAsync(j.grad_param, 0, sizeof(double) * c->n_param, b->stream), "zero grad");
+                          nullptr, nullptr, nullptr, b->active + b->active_off[i], usum,
+                          c->n_param > 0 ? j.grad_param : nullptr, c->n_param), "scatter");
+        if (c->n_param > 0)
             BK(launch_gemv(c->jac, c->dg_vert, acc, acc_g, c->n_vert, c->dim, c->n_param, j.grad_param, b->stream), "gemv");
-        }
-        double* mean = j.u_mean ? j.u_mean : b->means + b->mean_off[i];
-        BK(launch_reduce_u(rec, j.n_query, j.walks_per_point, mean, nullptr, b->stream), "reduce u");
-        BK(launch_loss(mean, j.uref, j.n_query, j.loss, b->stream), "loss");
+        BK(launch_loss(usum, j.uref, j.n_query, j.loss, b->stream, nullptr, 1.0 / j.walks_per_point, j.u_mean),
+           "loss");
     }
     return DWOS_OK;
 }

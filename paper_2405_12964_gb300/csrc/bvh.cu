@@ -652,7 +652,7 @@ __device__ __forceinline__ void prim_box(const float4* prims, int p, float* lo, 
 }
 
 template <int DIM>
-__global__ void inside_kernel(BvhView bvh, int n, const float* p, int* inside) {
+__global__ void inside_kernel(BvhView bvh, int n, const float* p, int* inside, const float* prev, float* prev_out) {
     const int pt = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (pt >= n) return;    // whole warps exit together
@@ -669,6 +669,12 @@ __global__ void inside_kernel(BvhView bvh, int n, const float* p, int* inside) {
     const float* dir = F.dir;
 #pragma unroll
     for (int k = 0; k < DIM; ++k) { o[k] = p[DIM * pt + k]; inv[k] = 1.0f / dir[k]; }
+    if (prev) {   // the same point as last time: its flag stands
+        bool same = true;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) same = same && __float_as_uint(o[k]) == __float_as_uint(prev[DIM * pt + k]);
+        if (same) return;
+    }
     // scene box: the root's two children and the outsized elements
     float slo[DIM], shi[DIM];
 #pragma unroll
@@ -731,7 +737,13 @@ __global__ void inside_kernel(BvhView bvh, int n, const float* p, int* inside) {
         }
     }
     for (int off = 16; off > 0; off >>= 1) count += __shfl_xor_sync(0xffffffffu, count, off);
-    if (lane == 0) inside[pt] = count & 1;
+    if (lane == 0) {
+        inside[pt] = count & 1;
+        if (prev_out) {
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) prev_out[DIM * pt + k] = o[k];
+        }
+    }
 }
 
 __global__ void philox_kernel(int n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out) {
@@ -988,10 +1000,11 @@ cudaError_t launch_closest(const BvhBuffers& b, int n, const float* p, const int
     return cudaGetLastError();
 }
 
-cudaError_t launch_inside(const BvhBuffers& b, int n, const float* p, int* inside, cudaStream_t s) {
+cudaError_t launch_inside(const BvhBuffers& b, int n, const float* p, int* inside, cudaStream_t s,
+                          const float* prev, float* prev_out) {
     if (n <= 0) return cudaSuccess;
-    if (b.dim == 2) inside_kernel<2><<<nblk(32LL * n, 128), 128, 0, s>>>(view_of(b), n, p, inside);
-    else inside_kernel<3><<<nblk(32LL * n, 128), 128, 0, s>>>(view_of(b), n, p, inside);
+    if (b.dim == 2) inside_kernel<2><<<nblk(32LL * n, 128), 128, 0, s>>>(view_of(b), n, p, inside, prev, prev_out);
+    else inside_kernel<3><<<nblk(32LL * n, 128), 128, 0, s>>>(view_of(b), n, p, inside, prev, prev_out);
     return cudaGetLastError();
 }
 

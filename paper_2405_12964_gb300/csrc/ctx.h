@@ -43,7 +43,10 @@ struct dwos_ctx {
 
     // workspaces (grow-only)
     dwos_record* rec = nullptr; size_t rec_cap = 0;
-    float* xq = nullptr; size_t xq_cap = 0;
+    float* xq = nullptr; size_t xq_cap = 0;           // host query points staged on the device
+    const float* xq_in = nullptr;                         // the query points the last walks read
+    float* xq_prev = nullptr; size_t xq_prev_cap = 0;     // the points whose inside flags `valid` holds
+    int inside_cached = -1;                               // their count (-1: none, e.g. after a rebuild)
     int* valid = nullptr; size_t valid_cap = 0;
     float* wvec = nullptr; size_t wvec_cap = 0;           // cotangent / uref
     float* pw = nullptr; size_t pw_cap = 0;               // per-point quadrature weights
@@ -55,8 +58,9 @@ struct dwos_ctx {
     int* misc_i = nullptr; size_t misc_i_cap = 0;
     uint32_t* misc_u = nullptr; size_t misc_u_cap = 0;
     double* misc_d = nullptr; size_t misc_d_cap = 0;
-    dwos::DevProblem* d_prob = nullptr;
-    dwos::DevCounters* d_ctr = nullptr;
+    dwos::DevCounters* d_ctr = nullptr;   // two: the current launch's and the next one's (kept zero)
+    int ctr_cur = 0;
+    bool ctr_next_zero = true;
     int* d_err = nullptr;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     bool timed = false;

@@ -140,7 +140,11 @@ cudaError_t bvh_build(BvhBuffers& b, int dim, const float* vert, const int* elem
 cudaError_t launch_closest(const BvhBuffers& b, int n, const float* p, const int* hint_elem, float* dist,
                            int* elem_out, float* bary, int* err, DevCounters* counters, int traversal,
                            cudaStream_t stream);
-cudaError_t launch_inside(const BvhBuffers& b, int n, const float* p, int* inside, cudaStream_t stream);
+// Inside flags by ray parity.  prev (optional): the points of the call that
+// left `inside` as it is; a point equal to its prev entry bit for bit keeps its
+// flag.  prev_out (optional, may equal prev): receives the points.
+cudaError_t launch_inside(const BvhBuffers& b, int n, const float* p, int* inside, cudaStream_t stream,
+                          const float* prev = nullptr, float* prev_out = nullptr);
 cudaError_t launch_philox(int n, const uint32_t* ctr, uint32_t k0, uint32_t k1, uint32_t* out,
                           cudaStream_t stream);
 cudaError_t launch_apply_params(const float* vert_ref, const float* jac, const float* theta, float* vert,
@@ -155,9 +159,13 @@ struct WalkLaunch {
     int traversal = 0;          // 2, 3: warp-wide search (every problem of the launch has wide_ok)
     bool star = false;          // walk on stars (one problem with a Neumann part; traversal 0 or 1)
 };
+// The problems come from the device table d_probs, or (one problem, d_probs
+// NULL) by value from host_prob.  zero_counters, when given, is zeroed by the
+// launch for the next one (the launch itself uses d_counters).
 cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_probs,
                          unsigned long long total_work, DevCounters* d_counters, cudaStream_t stream,
-                         int* blocks_used);
+                         int* blocks_used, const DevProblem* host_prob = nullptr,
+                         DevCounters* zero_counters = nullptr);
 int walk_max_blocks_per_sm(int dim, int block_size, int traversal = 0, bool star = false);
 // The walk step's ball weights (source factor for uniform u, recursive weight) and the
 // K0 of the 2D source weight, evaluated as the walk kernel evaluates them (walk.cu).
@@ -187,7 +195,11 @@ cudaError_t launch_reduce_udot(const dwos_record* rec, const int* elem, const fl
 cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int n_points, int W, int B,
                            int mode, const float* cot_or_uref, double* acc_vert, double* acc_g,
                            cudaStream_t stream, const CvView* cv = nullptr, const double* umean = nullptr,
-                           const float* pweight = nullptr, const unsigned char* active = nullptr);
+                           const float* pweight = nullptr, const unsigned char* active = nullptr,
+                           double* usum = nullptr, double* zero_out = nullptr, int n_zero = 0);
+// usum (optional, n_points, zeroed by the caller): receives the per-point sums
+// of u (FP64 over walks).  zero_out (optional): n_zero doubles zeroed by the
+// launch, for a later kernel that accumulates into them.
 // out[v] = 1 if vertex v has a nonzero entry in its Jacobian rows (dim x n_param) or its dg row.
 cudaError_t launch_vertex_active(const float* jac, const float* dg, int n_vert, int dim, int n_param,
                                  unsigned char* out, cudaStream_t stream);
@@ -195,6 +207,7 @@ cudaError_t launch_gemv(const float* jac, const float* dg, const double* acc_ver
                         int n_vert, int dim, int n_param, double* grad, cudaStream_t stream);
 // 1/2 sum_p w_p (mean_p - uref_p)^2 with w = pweight (or 1)
 cudaError_t launch_loss(const double* mean, const float* uref, int n_points, double* loss,
-                        cudaStream_t stream, const float* pweight = nullptr);
+                        cudaStream_t stream, const float* pweight = nullptr, double scale = 1.0,
+                        double* mean_out = nullptr);
 
 }  // namespace dwos

@@ -175,8 +175,12 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
                                                       const float* __restrict__ pweight,
                                                       const unsigned char* __restrict__ active,
                                                       long long walks_per_block, double* __restrict__ acc_vert,
-                                                      double* __restrict__ acc_g, CvView cv) {
+                                                      double* __restrict__ acc_g, CvView cv,
+                                                      double* __restrict__ usum, double* __restrict__ zero_out,
+                                                      int n_zero) {
     constexpr int NV = G ? DIM + 1 : DIM;
+    if (zero_out && blockIdx.x == 0)      // an output the next kernel accumulates into
+        for (int i = threadIdx.x; i < n_zero; i += blockDim.x) zero_out[i] = 0.0;
     __shared__ int keys[kSlots];
     __shared__ double vals[kSlots][NV];
     for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
@@ -220,6 +224,17 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
         const bool hit = valid && r.elem >= 0;
         const float wv[3] = {1.0f - r.b1 - r.b2, r.b1, r.b2};
         const int lane = threadIdx.x & 31;
+        if (usum) {   // per-point sum of u: the warp's walks of one point summed in FP32, then in FP64
+            const int p0 = __shfl_sync(kFull, p, 0);
+            if (__all_sync(kFull, !valid || p == p0)) {
+                float su = u;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) su += __shfl_xor_sync(kFull, su, o);
+                if (lane == 0 && valid) atomicAdd(usum + p0, (double)su);
+            } else if (valid) {
+                atomicAdd(usum + p, (double)u);
+            }
+        }
 #pragma unroll
         for (int sidx = 0; sidx < DIM; ++sidx) {
             int vid = hit ? __ldg(elem + DIM * r.elem + sidx) : -1;
@@ -320,10 +335,15 @@ __global__ void gemv_kernel(const float* __restrict__ jac, const float* __restri
     }
 }
 
-__global__ void loss_kernel(const double* mean, const float* uref, const float* pweight, int n, double* loss) {
+// mean[p] * scale is the point's mean (scale 1 / W for per-point sums); it is
+// also written to mean_out when given.
+__global__ void loss_kernel(const double* mean, const float* uref, const float* pweight, int n, double* loss,
+                            double scale, double* mean_out) {
     double s = 0.0;
     for (int p = threadIdx.x; p < n; p += blockDim.x) {
-        const double e = mean[p] - (double)uref[p];
+        const double m = mean[p] * scale;
+        if (mean_out) mean_out[p] = m;
+        const double e = m - (double)uref[p];
         s += 0.5 * e * e * (pweight ? (double)pweight[p] : 1.0);
     }
     __shared__ double sh[32];
@@ -456,11 +476,12 @@ cudaError_t launch_vertex_active(const float* jac, const float* dg, int n_vert, 
 cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int n_points, int W, int B, int mode,
                            const float* cot_or_uref, double* acc_vert, double* acc_g, cudaStream_t s,
                            const CvView* cv, const double* umean, const float* pweight,
-                           const unsigned char* active) {
+                           const unsigned char* active, double* usum, double* zero_out, int n_zero) {
     const CvView none{nullptr, nullptr, nullptr, dim, nullptr};
     const CvView c = cv ? *cv : none;
     const long long total = (long long)n_points * W;
-    if (total <= 0) return cudaSuccess;
+    if (total <= 0)
+        return zero_out && n_zero > 0 ? cudaMemsetAsync(zero_out, 0, sizeof(double) * n_zero, s) : cudaSuccess;
     const int bs = 256;
     // about four blocks per SM; each block a multiple of 256 walks (whole batches)
     long long per = (total + 4 * 152 - 1) / (4 * 152);
@@ -469,7 +490,7 @@ cudaError_t launch_scatter(const dwos_record* rec, const int* elem, int dim, int
     const long long blocks = (total + per - 1) / per;
     auto go = [&](auto kernel) {
         kernel<<<(unsigned)blocks, bs, 0, s>>>(rec, elem, n_points, W, B, mode, cot_or_uref, umean, pweight, active,
-                                              per, acc_vert, acc_g, c);
+                                              per, acc_vert, acc_g, c, usum, zero_out, n_zero);
     };
     if (dim == 2) { if (acc_g) go(scatter_kernel<2, true>); else go(scatter_kernel<2, false>); }
     else { if (acc_g) go(scatter_kernel<3, true>); else go(scatter_kernel<3, false>); }
@@ -489,8 +510,8 @@ cudaError_t launch_gemv(const float* jac, const float* dg, const double* acc_ver
 }
 
 cudaError_t launch_loss(const double* mean, const float* uref, int n_points, double* loss, cudaStream_t s,
-                        const float* pweight) {
-    loss_kernel<<<1, 256, 0, s>>>(mean, uref, pweight, n_points, loss);
+                        const float* pweight, double scale, double* mean_out) {
+    loss_kernel<<<1, 256, 0, s>>>(mean, uref, pweight, n_points, loss, scale, mean_out);
     return cudaGetLastError();
 }
 

@@ -126,7 +126,8 @@ __device__ __forceinline__ void sphere_dir(const U4& r, float* om) {
 template <int DIM, bool WIDE, bool STAR = false>
 __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
     walk_kernel(const DevProblem* __restrict__ g_probs, int n_probs, unsigned long long total,
-                DevCounters* __restrict__ ctr) {
+                DevCounters* __restrict__ ctr, DevCounters* __restrict__ zero_ctr,
+                const __grid_constant__ DevProblem p_arg) {
     constexpr bool wide = WIDE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     DevProblem* sp = reinterpret_cast<DevProblem*>(smem_raw);
@@ -136,10 +137,15 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
     PhaseState<DIM>& S = WIDE ? reinterpret_cast<PhaseState<DIM>*>(stk_base + (size_t)(blockDim.x >> 5) * kWideStack)[threadIdx.x]
                               : ps_reg;
     {
+        // the descriptor table, or the one problem passed by value
         const int words = (int)(sizeof(DevProblem) / sizeof(int)) * n_probs;
-        const int* src = reinterpret_cast<const int*>(g_probs);
+        const int* src = g_probs ? reinterpret_cast<const int*>(g_probs) : reinterpret_cast<const int*>(&p_arg);
         int* dst = reinterpret_cast<int*>(sp);
         for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+        // the counters of the next launch start at zero
+        if (zero_ctr && blockIdx.x == 0)
+            for (int i = threadIdx.x; i < (int)(sizeof(DevCounters) / sizeof(int)); i += blockDim.x)
+                reinterpret_cast<int*>(zero_ctr)[i] = 0;
     }
     __syncthreads();
     DevNeumann& NS = *reinterpret_cast<DevNeumann*>(smem_raw + walk_smem_bytes(n_probs, 0, 0));
@@ -645,9 +651,15 @@ int walk_max_blocks_per_sm(int dim, int block_size, int traversal, bool star) {
 }
 
 cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_probs, unsigned long long total,
-                         DevCounters* d_counters, cudaStream_t stream, int* blocks_used) {
+                         DevCounters* d_counters, cudaStream_t stream, int* blocks_used, const DevProblem* host_prob,
+                         DevCounters* zero_counters) {
     if (n_probs < 1 || n_probs > kMaxProblems) return cudaErrorInvalidValue;
-    if (total == 0) { if (blocks_used) *blocks_used = 0; return cudaSuccess; }
+    if (host_prob ? (n_probs != 1 || d_probs) : !d_probs) return cudaErrorInvalidValue;
+    if (total == 0) {
+        if (blocks_used) *blocks_used = 0;
+        if (zero_counters) return cudaMemsetAsync(zero_counters, 0, sizeof(DevCounters), stream);
+        return cudaSuccess;
+    }
     const int bs = L.block_size;
     if (L.star && (n_probs != 1 || L.traversal == 2 || L.traversal == 3)) return cudaErrorInvalidValue;
     int per_sm = L.blocks_per_sm > 0 ? L.blocks_per_sm
@@ -660,12 +672,15 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
     if (blocks_used) *blocks_used = (int)blocks;
     if (bs % 32 != 0) return cudaErrorInvalidValue;
     const size_t smem = walk_smem_bytes(n_probs, bs, L.traversal, L.dim, L.star);
+    DevProblem P1;
+    if (host_prob) P1 = *host_prob;
+    else memset(&P1, 0, sizeof(P1));
     auto go = [&](auto kernel) -> cudaError_t {
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        kernel<<<(int)blocks, bs, smem, stream>>>(d_probs, n_probs, total, d_counters);
+        kernel<<<(int)blocks, bs, smem, stream>>>(d_probs, n_probs, total, d_counters, zero_counters, P1);
         return cudaGetLastError();
     };
     if (L.star) return L.dim == 2 ? go(walk_kernel<2, false, true>) : go(walk_kernel<3, false, true>);
