@@ -165,6 +165,7 @@ __device__ __forceinline__ int nth_set_bit(unsigned m, int n) {
 }
 
 constexpr int kProbes = 8;
+constexpr int kUSlots = 64;   // per-point u sums a block keeps in shared memory
 
 // G: the data-derivative sums s_v (acc_g) are wanted too (DIM + 1 values per vertex, else DIM).
 template <int DIM, bool G>
@@ -183,15 +184,21 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
         for (int i = threadIdx.x; i < n_zero; i += blockDim.x) zero_out[i] = 0.0;
     __shared__ int keys[kSlots];
     __shared__ double vals[kSlots][NV];
+    __shared__ double usl[kUSlots];
+    const long long total = (long long)n_points * W;
+    const long long begin = (long long)blockIdx.x * walks_per_block;
+    const long long end = min(begin + walks_per_block, total);
+    // the block's walks cover points p_first .. p_first + n_pb - 1
+    const int p_first = (int)(begin / W);
+    const int n_pb = end > begin ? (int)((end - 1) / W) - p_first + 1 : 0;
+    const bool uslots = usum && n_pb <= kUSlots;
     for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
         keys[i] = -1;
 #pragma unroll
         for (int k = 0; k < NV; ++k) vals[i][k] = 0.0;
     }
+    for (int i = threadIdx.x; i < kUSlots; i += blockDim.x) usl[i] = 0.0;
     __syncthreads();
-    const long long total = (long long)n_points * W;
-    const long long begin = (long long)blockIdx.x * walks_per_block;
-    const long long end = min(begin + walks_per_block, total);
     for (long long base = begin; base < end; base += blockDim.x) {
         const long long i = base + threadIdx.x;
         const bool valid = i < end;
@@ -230,9 +237,9 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
                 float su = u;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) su += __shfl_xor_sync(kFull, su, o);
-                if (lane == 0 && valid) atomicAdd(usum + p0, (double)su);
+                if (lane == 0 && valid) atomicAdd(uslots ? usl + (p0 - p_first) : usum + p0, (double)su);
             } else if (valid) {
-                atomicAdd(usum + p, (double)u);
+                atomicAdd(uslots ? usl + (p - p_first) : usum + p, (double)u);
             }
         }
 #pragma unroll
@@ -280,6 +287,8 @@ __global__ void __launch_bounds__(256) scatter_kernel(const dwos_record* __restr
         }
     }
     __syncthreads();
+    if (uslots)
+        for (int i = threadIdx.x; i < n_pb; i += blockDim.x) atomicAdd(usum + p_first + i, usl[i]);
     for (int i = threadIdx.x; i < kSlots; i += blockDim.x) {
         const int vid = keys[i];
         if (vid < 0) continue;
