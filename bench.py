@@ -51,6 +51,10 @@ WORKLOADS = {
            "estimates (4 Adam iterations per step); value = gradient RMSE x seconds of one estimate at "
            "1024 walks/point, the network's inference inside the timed region"),
     "ablation": "estimator ablation (product estimators, du/dn estimators, K, h) on the 2D workload",
+    "sgd": ("noisy-gradient optimisation (Sec. 5.2) on the 2D workload's geometry: the star's position "
+            "(2-vector, Vector Adam, lr 1e-3) from (0.1, -0.06) back to the target's, observations on "
+            "|x|_inf = 0.6, 600 iterations, "
+            "2 / 16 / 128 walks per point and annealed 2 -> 128 (Eq. update_rule), 3 seeds each"),
     "c4": ("batched: 64 independent problems (32 2D star-in-box, 32 3D SH-sphere-in-box), elements "
            "log-uniform 1e3-5e5, 16-4096 points, sigma log-uniform 0.01-100, 256-4096 walks/point, "
            "16 shape params each; L2-loss gradients in one captured CUDA graph, autotuned walk pool"),
@@ -474,6 +478,34 @@ def run_ablation(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sgd(args):
+    """Sec. 5.2's experiment: position error and loss against iterations and
+    against wall time for fixed and annealed walks per point."""
+    import numpy as np
+    from paper_2405_12964_gb300 import build
+    build.build()
+    from paper_2405_12964_gb300 import optimize
+    t0 = time.perf_counter()
+    res = optimize.noisy_gradient_study()
+    table = optimize.study_table(res)
+    curves = {}
+    for name, runs in res.items():    # seed-mean curves, every 10th iteration
+        err = np.mean([r["err"] for r in runs], axis=0)
+        sec = np.mean([r["seconds"] for r in runs], axis=0)
+        curves[name] = {"iter": list(range(10, len(err) + 1, 10)), "err": [float(e) for e in err[9::10]],
+                        "seconds": [float(x) for x in sec[9::10]],
+                        "loss_iter": runs[0]["loss_iter"],
+                        "loss": [float(v) for v in np.mean([r["loss"] for r in runs], axis=0)]}
+    ann = [k for k in table if k.startswith("annealed")][0]
+    last_t = list(table[ann]["err_at_time"])[-1]
+    line = {"metric": "position error at equal wall time (Sec. 5.2)", "value": table[ann]["err_at_time"][last_t],
+            "unit": "|theta - theta*|", "higher_is_better": False, "n_gpus": 1, "steps": 600, "warmup": 0,
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["sgd"], "equal_time_reference": "fractions of the fastest run's time"},
+            "table": table, "curves": curves, "seconds": time.perf_counter() - t0}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -498,6 +530,8 @@ def main():
         return run_control_variate(args)
     if args.workload == "ablation":
         return run_ablation(args)
+    if args.workload == "sgd":
+        return run_sgd(args)
 
     import numpy as np
     import torch

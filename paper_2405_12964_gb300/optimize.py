@@ -56,6 +56,39 @@ class Adam:
         return self.theta
 
 
+class VectorAdam:
+    """Vector Adam (Ling et al. 2022), the optimiser Sec. 5 uses for shape
+    parameters such as vertex positions: Adam on an (n, d) array of d-vectors
+    whose second moment is kept per vector, from the squared norm of its
+    gradient, so that a step is the same whatever the frame the vectors are
+    written in (Adam's per-coordinate second moment is not: it depends on the
+    axes).  For d = 1 it is Adam."""
+
+    def __init__(self, x: np.ndarray, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999,
+                 eps: float = 1e-8):
+        x = np.array(x, dtype=np.float64)
+        self.shape = x.shape
+        self.x = x.reshape(x.shape[0], -1) if x.ndim > 1 else x.reshape(1, -1)
+        self.lr, self.b1, self.b2, self.eps = lr, beta1, beta2, eps
+        self.m = np.zeros_like(self.x)
+        self.v = np.zeros(self.x.shape[0])
+        self.t = 0
+
+    @property
+    def theta(self) -> np.ndarray:
+        return self.x.reshape(self.shape)
+
+    def step(self, g: np.ndarray) -> np.ndarray:
+        g = np.asarray(g, dtype=np.float64).reshape(self.x.shape)
+        self.t += 1
+        self.m = self.b1 * self.m + (1 - self.b1) * g
+        self.v = self.b2 * self.v + (1 - self.b2) * np.sum(g * g, axis=1)
+        mh = self.m / (1 - self.b1 ** self.t)
+        vh = self.v / (1 - self.b2 ** self.t)
+        self.x = self.x - self.lr * mh / (np.sqrt(vh)[:, None] + self.eps)
+        return self.theta
+
+
 @dataclass
 class History:
     loss: List[float] = field(default_factory=list)
@@ -149,6 +182,92 @@ def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 2
         trainer.net.sync()                               # reports a timed-out tensor-core wait, if any
         hist.mlp_loss = [float(l[0]) for l in hist.mlp_loss]
     return opt.theta, hist, trainer
+
+
+def noisy_gradient_study(offset=(0.1, -0.06), iters: int = 600, lr: float = 1e-3, wpps=(2, 16, 128),
+                         anneal=(2, 128), seeds=(1, 2, 3), target_walks: int = 16384, eval_every: int = 20,
+                         eval_walks: int = 4096, device: int = 0, n_seg: int = 4096):
+    """The experiment of Sec. 5.2 (Fig. sgd) on the 2D shape-from-diffusion
+    geometry: the star's position (a 2-vector, Vector Adam, lr 1e-3) is
+    optimised from `offset` back to the origin, where the target profile was
+    taken (target_walks per point), with a fixed number of differential walks
+    per point (each of `wpps`) or the annealing schedule of Eq. (update_rule)
+    from anneal[0] to anneal[1].  Each run records per iteration the position
+    error |theta - theta*| and the seconds spent (the gradient estimate with
+    its BVH rebuild, the read-back and the optimiser step; synchronised), and
+    every eval_every iterations the loss 1/2 sum_p (u_p - uref_p)^2 from
+    eval_walks walks per point (outside the timed region).  Returns a dict
+    config -> list over seeds of {"err", "seconds", "loss_iter", "loss"}."""
+    from . import scenes
+    sc = scenes.translated_star_scene(n_seg=n_seg)
+    s = dwos.Solver(device)
+    s.load_scene(sc)
+    s.set_boundary(sc.reference_vertices(), sc.elem, sc.jac)
+    s.set_dirichlet_mapped(sc.g_vert)
+    xq = torch.tensor(sc.query, dtype=torch.float32, device=s.device)
+    target = np.zeros(2)
+    s.set_params(target)
+    uref = s.eval(xq, target_walks)["u"].to(torch.float32)
+    configs = [("%d WPP" % w, w, w) for w in wpps] + [("annealed %d->%d WPP" % anneal, anneal[0], anneal[1])]
+    out = {}
+    for name, w0, wT in configs:
+        runs = []
+        for seed in seeds:
+            opt = VectorAdam(np.asarray(offset, dtype=np.float64)[None, :], lr=lr)
+            err, secs, loss_it, loss = [], [], [], []
+            total = 0.0
+            for it in range(iters):
+                W = wpp_schedule(it + 1, iters, w0, wT, multiple=sc.B) if w0 != wT else w0
+                if it % eval_every == 0:
+                    s.set_params(opt.theta[0])
+                    u = s.eval(xq, eval_walks)["u"]
+                    loss_it.append(it)
+                    loss.append(float(0.5 * torch.sum((u - uref.double()) ** 2)))
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                s.set_params(opt.theta[0])
+                _, g = s.grad_l2(xq, uref, W, walk_id_base=(seed << 44) + it * (1 << 24))
+                opt.step(g.cpu().numpy()[None, :])
+                total += time.perf_counter() - t0
+                err.append(float(np.linalg.norm(opt.theta[0] - target)))
+                secs.append(total)
+            s.set_params(opt.theta[0])
+            u = s.eval(xq, eval_walks)["u"]
+            loss_it.append(iters)
+            loss.append(float(0.5 * torch.sum((u - uref.double()) ** 2)))
+            runs.append({"err": err, "seconds": secs, "loss_iter": loss_it, "loss": loss,
+                         "err0": float(np.linalg.norm(np.asarray(offset) - target))})
+        out[name] = runs
+    return out
+
+
+def study_table(res: dict, iters=(50, 150, 300, 600), time_fracs=(0.1, 0.25, 0.5, 1.0)) -> dict:
+    """Summary of noisy_gradient_study: per configuration the mean (over
+    seeds) position error and loss at equal iterations, the seconds per
+    iteration, and the position error at equal wall time (fractions of the
+    fastest configuration's run, so that every configuration is still
+    running; before its first iteration ends a run is at its start)."""
+    t_min = min(np.mean([r["seconds"][-1] for r in runs]) for runs in res.values())
+    rows = {}
+    for name, runs in res.items():
+        err = np.array([r["err"] for r in runs])
+        secs = np.array([r["seconds"] for r in runs])
+        li = np.array(runs[0]["loss_iter"])
+        loss = np.array([r["loss"] for r in runs])
+        row = {"seconds_per_iter": float(np.mean(secs[:, -1]) / secs.shape[1])}
+        row["err_at_iter"] = {int(i): float(np.mean(err[:, min(i, err.shape[1]) - 1])) for i in iters}
+        row["loss_at_iter"] = {int(i): float(np.mean(loss[:, int(np.argmin(np.abs(li - i)))])) for i in iters}
+        at_t = {}
+        for f in time_fracs:
+            t = f * t_min
+            vals = []
+            for r, run in enumerate(runs):
+                k = int(np.searchsorted(secs[r], t, side="right"))   # iterations finished by t
+                vals.append(float(err[r, k - 1]) if k > 0 else float(run["err0"]))
+            at_t["%.4f s" % t] = float(np.mean(vals))
+        row["err_at_time"] = at_t
+        rows[name] = row
+    return rows
 
 
 def gradient_rmse_x_time(scene, theta: np.ndarray, uref, walks: int, repeats: int = 16, net=None,

@@ -216,6 +216,29 @@ def star_box_scene(n_seg: int = 4096, n_modes: int = 32, coef_std: float = 0.02,
     return sc
 
 
+def translated_star_scene(offset=(0.0, 0.0), n_seg: int = 4096, n_query: int = 256, B: int = 2,
+                          obs_half: float = 0.6, seed: int = GEOMETRY_SEED) -> Scene:
+    """The shape-from-diffusion geometry (box [-1,1]^2 with g = 0 around the
+    star emitter with g = 1, sigma = 10) with the star's position as the
+    parameter: theta = the star's translation (a 2-vector, so Vector Adam
+    applies), its vertices at v_ref + theta.  `offset` is the translation at
+    which `vert` is given.  Observation points: n_query by arclength on the
+    square |x|_inf = obs_half, near the star (the nearby slice of Sec. 5.2).
+    U-statistic batches of B = 2 allow 2 walks per point."""
+    sc = star_box_scene(n_seg=n_seg, n_query=n_query, seed=seed)
+    sc.query = box_perimeter_points(n_query, obs_half)
+    off = np.asarray(offset, dtype=np.float64)
+    jac = np.zeros((sc.vert.shape[0], 2, 2))
+    jac[4:, 0, 0] = 1.0
+    jac[4:, 1, 1] = 1.0
+    vert = sc.vert.copy()
+    vert[4:] += off
+    out = Scene("translated_star", vert, sc.elem, jac, data="mapped", g_vert=sc.g_vert, sigma=sc.sigma,
+                eps=sc.eps, h=sc.h, K=sc.K, B=B, query=sc.query, walks=sc.walks, u_ref=sc.u_ref)
+    out.meta = {"theta0": off.copy(), "coeffs": sc.meta["coeffs"]}
+    return out
+
+
 # ---------------------------------------------------------------------------- 3D
 def icosahedron():
     p = (1 + 5 ** 0.5) / 2

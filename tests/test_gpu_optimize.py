@@ -20,12 +20,6 @@ def opt():
     return optimize
 
 
-def test_wpp_schedule_follows_update_rule(opt):
-    assert opt.wpp_schedule(0, 100, 16, 256) == 16
-    assert opt.wpp_schedule(100, 100, 16, 256) == 256
-    assert opt.wpp_schedule(50, 100, 16, 256) == 64      # geometric midpoint
-
-
 @pytest.mark.parametrize("use_cv", [False, True])
 def test_optimisation_reduces_the_loss(opt, use_cv):
     sc = scenes.star_box_scene(n_seg=1024, n_modes=4, coef_std=0.1, n_query=64)
@@ -50,3 +44,19 @@ def test_optimisation_reduces_the_loss_in_3d(opt):
     theta, hist, _ = opt.run(sc, target, start, steps=40, lr=2e-2, wpp0=64, wppT=256, use_cv=False, seed=4)
     assert np.mean(hist.loss[-8:]) < 0.5 * np.mean(hist.loss[:4])
     assert np.all(np.isfinite(theta))
+
+
+def test_noisy_gradient_study_runs_and_converges(opt):
+    # Sec. 5.2's loop at a small size: the star's position (Vector Adam) back to the
+    # target's from an offset, fixed 16 walks per point and annealed 2 -> 32
+    res = opt.noisy_gradient_study(offset=(0.05, -0.03), iters=120, lr=4e-3, wpps=(16,), anneal=(2, 32),
+                                   seeds=(1,), target_walks=2048, eval_every=60, eval_walks=512, n_seg=1024)
+    table = opt.study_table(res, iters=(10, 60, 120))
+    assert set(table) == {"16 WPP", "annealed 2->32 WPP"}
+    for name, runs in res.items():
+        err = runs[0]["err"]
+        assert err[-1] < 0.5 * runs[0]["err0"], (name, err[-1])
+        assert runs[0]["loss"][-1] < runs[0]["loss"][0]
+        assert np.all(np.diff(runs[0]["seconds"]) > 0)
+    # the annealed run starts with cheaper iterations
+    assert table["annealed 2->32 WPP"]["seconds_per_iter"] < table["16 WPP"]["seconds_per_iter"] * 1.5
