@@ -184,7 +184,12 @@ dwos_status dwos_set_boundary(dwos_ctx* ctx, int dim, int n_vert, const float* v
                               int n_elem, const int32_t* elem, int n_param,
                               const float* vert_jac, int mem);
 /* Set theta (n_param values): v = vert_ref + vert_jac theta on the device,
- * then rebuild the BVH. */
+ * then update the BVH for the moved vertices.  The update refits the tree's
+ * boxes over its existing topology, on the device, with no host
+ * synchronisation; every 64th update, and every update while search order 1
+ * is selected (its Morton cells need a fresh tree), rebuilds it instead.  The
+ * searches are exact over either tree, so the walks do not depend on which
+ * was done, up to the choice between equally distant elements. */
 dwos_status dwos_set_params(dwos_ctx* ctx, const float* theta, int mem);
 /* Mapped (per-vertex, linearly interpolated) Dirichlet data, Sec. 4.1
  * "Mapped boundary data": g_vert (n_vert) and optionally dg_vert
@@ -222,7 +227,7 @@ dwos_status dwos_set_pde(dwos_ctx* ctx, float sigma, float f);
  * batches, dwos_eval_static and the shape-functional calls
  * (DWOS_ERR_NOT_IMPLEMENTED / DWOS_ERR_INVALID_ARG).  dwos_closest_point
  * then answers for the Dirichlet part, dwos_inside for the whole boundary.
- * Builds a BVH for each part; dwos_set_params rebuilds both.  Synchronises. */
+ * Builds a BVH for each part; dwos_set_params updates both.  Synchronises. */
 dwos_status dwos_set_neumann(dwos_ctx* ctx, const int32_t* flags, int mem);
 
 /* Bound on the BVH node fetches (binary nodes, or 32-wide node visits) that one

@@ -27,9 +27,12 @@ dwos_status fail(dwos_ctx* c, dwos_status s, const std::string& msg) {
 }
 
 // The search order a launch uses: the warp-wide one only where the tree supports it.
+constexpr int kMaxRefits = 64;   // parameter updates between full BVH builds
+
 int effective_traversal(const dwos_ctx* c) {
     int t = c->opt.traversal;
     if (t < 0) t = 3;
+    if (t == 1 && !c->bvh.cells_ok) return 0;   // a refit tree: its Morton cells no longer hold
     return ((t == 2 || t == 3) && !c->bvh.wide_ok) ? 0 : t;
 }
 
@@ -100,6 +103,7 @@ inline DevCounters* cur_ctr(dwos_ctx* ctx) { return ctx->d_ctr + ctx->ctr_cur; }
 
 dwos_status rebuild(dwos_ctx* ctx) {
     ctx->inside_cached = -1;   // the inside flags belong to the old geometry
+    ctx->refits = 0;
     if (ctx->n_neumann == 0) {
         CK(bvh_build(ctx->bvh, ctx->dim, ctx->vert, ctx->elem, ctx->n_elem, ctx->stream), "BVH build");
         return DWOS_OK;
@@ -503,6 +507,17 @@ dwos_status dwos_set_params(dwos_ctx* ctx, const float* theta, int mem) {
     CK(to_device(ctx, ctx->theta, theta, ctx->n_param, mem), "copy theta");
     CK(launch_apply_params(ctx->vert_ref, ctx->jac, ctx->theta, ctx->vert, ctx->n_vert * ctx->dim, ctx->n_param,
                            ctx->stream), "apply theta");
+    // the same elements moved: refit the trees' boxes (no host synchronisation), with a
+    // full rebuild every kMaxRefits updates to restore the tree's quality, and for
+    // search order 1, which needs the Morton cells of a fresh build
+    if (ctx->refits < kMaxRefits && ctx->opt.traversal != 1) {
+        ctx->inside_cached = -1;
+        CK(bvh_refit(ctx->bvh, ctx->vert, ctx->n_neumann > 0 ? ctx->elem_d : ctx->elem, ctx->stream), "BVH refit");
+        if (ctx->n_neumann > 0) CK(bvh_refit(ctx->bvh_n, ctx->vert, ctx->elem_n, ctx->stream), "Neumann BVH refit");
+        ++ctx->refits;
+        ctx->launches += 3;
+        return DWOS_OK;
+    }
     return rebuild(ctx);
 }
 

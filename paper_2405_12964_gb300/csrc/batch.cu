@@ -96,7 +96,7 @@ void fill_problem(const dwos_ctx* c, const dwos_batch_job& j, dwos_record* rec, 
     P.leaf_parent = c->bvh.leaf_parent;
     P.node_cell = c->bvh.node_cell;
     P.r_max = c->bvh.r_max;
-    P.traversal = traversal;
+    P.traversal = (traversal == 1 && !c->bvh.cells_ok) ? 0 : traversal;   // order 1 needs a fresh build
     P.wnodes = c->bvh.wnodes;
     P.n_wide = c->bvh.n_wide;
     P.data_kind = c->data_kind;

@@ -965,7 +965,39 @@ static cudaError_t build_impl(BvhBuffers& b, const float* vert, const int* elem,
 cudaError_t bvh_build(BvhBuffers& b, int dim, const float* vert, const int* elem, int n_elem, cudaStream_t s) {
     cudaError_t e = bvh_reserve(b, dim, n_elem);
     if (e != cudaSuccess) return e;
-    return dim == 2 ? build_impl<2>(b, vert, elem, n_elem, s) : build_impl<3>(b, vert, elem, n_elem, s);
+    b.cells_ok = false;
+    e = dim == 2 ? build_impl<2>(b, vert, elem, n_elem, s) : build_impl<3>(b, vert, elem, n_elem, s);
+    b.cells_ok = e == cudaSuccess;
+    return e;
+}
+
+template <int DIM>
+static cudaError_t refit_impl(BvhBuffers& b, const float* vert, const int* elem, cudaStream_t s) {
+    const int n = b.n_elem, nt = b.n_tree;
+    if (n <= 0) return cudaSuccess;
+    if (nt >= 2) {
+        cudaError_t e = cudaMemsetAsync(b.counters, 0, sizeof(int) * (size_t)(nt - 1), s);
+        if (e != cudaSuccess) return e;
+        refit_kernel<DIM><<<nblk(nt, 256), 256, 0, s>>>(vert, elem, b.vals_sorted, nt, b.node_child,
+                                                        b.node_parent, b.leaf_parent, b.counters, b.nodes);
+        finalize_kernel<DIM><<<nblk(n, 256), 256, 0, s>>>(vert, elem, b.vals_sorted, n, b.node_child,
+                                                          b.node_parent, nt - 1, b.nodes, b.prims, b.prim_elem,
+                                                          b.leaf_of_elem);
+        if (b.n_wide > 0)
+            wide_refit_kernel<DIM><<<nblk((long long)b.n_wide * kWide, 256), 256, 0, s>>>(
+                b.nodes, b.prims, b.wsrc, b.wsrc + kWide * (size_t)b.n_wide, b.n_wide, b.wnodes);
+    } else {
+        if (nt == 1) single_leaf_kernel<DIM><<<1, 1, 0, s>>>(vert, elem, b.vals_sorted, b.nodes, b.leaf_parent,
+                                                             b.node_cell);
+        finalize_kernel<DIM><<<nblk(n, 256), 256, 0, s>>>(vert, elem, b.vals_sorted, n, nullptr, nullptr, 0,
+                                                          b.nodes, b.prims, b.prim_elem, b.leaf_of_elem);
+    }
+    b.cells_ok = false;
+    return cudaGetLastError();
+}
+
+cudaError_t bvh_refit(BvhBuffers& b, const float* vert, const int* elem, cudaStream_t s) {
+    return b.dim == 2 ? refit_impl<2>(b, vert, elem, s) : refit_impl<3>(b, vert, elem, s);
 }
 
 static BvhView view_of(const BvhBuffers& b) {

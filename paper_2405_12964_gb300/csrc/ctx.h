@@ -30,6 +30,7 @@ struct dwos_ctx {
     double field[10] = {0};
     float sigma = 0.0f, f = 0.0f;
     dwos::BvhBuffers bvh;        // over every element, or over the Dirichlet part when there is a Neumann part
+    int refits = 0;              // parameter updates applied by refitting since the last full build
     bool have_boundary = false;
     // reflecting Neumann part (walk on stars); n_neumann = 0 when every element is Dirichlet
     int n_neumann = 0;

@@ -102,6 +102,8 @@ struct DevCounters {
 // BVH build (bvh.cu).  All pointers are device pointers; work on `stream`.
 struct BvhBuffers {
     int dim = 0, n_elem = 0, n_internal = 0;
+    bool cells_ok = false;        // node_cell / r_max describe the elements (false after a refit):
+                                  // search order 1 needs them
     int n_tree = 0, n_big = 0;    // leaves in the LBVH, outsized elements kept out of it
     float4* nodes = nullptr;      // max(1, n_elem-1) nodes
     float4* prims = nullptr;      // n_elem prims
@@ -135,6 +137,11 @@ cudaError_t bvh_reserve(BvhBuffers& b, int dim, int n_elem);
 void bvh_free(BvhBuffers& b);
 cudaError_t bvh_build(BvhBuffers& b, int dim, const float* vert, const int* elem, int n_elem,
                       cudaStream_t stream);
+// New boxes for moved vertices over the same elements and tree topology (binary
+// and 32-wide): every box again bounds its subtree, so the exact searches of
+// orders 0, 2 and 3 stay exact; no host synchronisation and no allocation.
+// The Morton cells go stale (cells_ok = false).
+cudaError_t bvh_refit(BvhBuffers& b, const float* vert, const int* elem, cudaStream_t stream);
 
 // Batched queries through the BVH (bvh.cu).
 cudaError_t launch_closest(const BvhBuffers& b, int n, const float* p, const int* hint_elem, float* dist,

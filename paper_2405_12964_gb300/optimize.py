@@ -186,7 +186,7 @@ def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 2
 
 def noisy_gradient_study(offset=(0.1, -0.06), iters: int = 600, lr: float = 1e-3, wpps=(2, 16, 128),
                          anneal=(2, 128), seeds=(1, 2, 3), target_walks: int = 16384, eval_every: int = 20,
-                         eval_walks: int = 4096, device: int = 0, n_seg: int = 4096):
+                         eval_walks: int = 4096, device: int = 0, n_seg: int = 4096, n_query: int = 256):
     """The experiment of Sec. 5.2 (Fig. sgd) on the 2D shape-from-diffusion
     geometry: the star's position (a 2-vector, Vector Adam, lr 1e-3) is
     optimised from `offset` back to the origin, where the target profile was
@@ -196,10 +196,11 @@ def noisy_gradient_study(offset=(0.1, -0.06), iters: int = 600, lr: float = 1e-3
     error |theta - theta*| and the seconds spent (the gradient estimate with
     its BVH rebuild, the read-back and the optimiser step; synchronised), and
     every eval_every iterations the loss 1/2 sum_p (u_p - uref_p)^2 from
-    eval_walks walks per point (outside the timed region).  Returns a dict
-    config -> list over seeds of {"err", "seconds", "loss_iter", "loss"}."""
+    eval_walks walks per point (outside the timed region).  n_query
+    observation points on the square |x|_inf = 0.6.  Returns a dict config ->
+    list over seeds of {"err", "seconds", "loss_iter", "loss", "err0"}."""
     from . import scenes
-    sc = scenes.translated_star_scene(n_seg=n_seg)
+    sc = scenes.translated_star_scene(n_seg=n_seg, n_query=n_query)
     s = dwos.Solver(device)
     s.load_scene(sc)
     s.set_boundary(sc.reference_vertices(), sc.elem, sc.jac)
