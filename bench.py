@@ -48,7 +48,8 @@ WORKLOADS = {
     "c5": ("learned control variate on the 2D shape-from-diffusion geometry: 200 Adam steps (lr 1e-3) "
            "on 64 Fourier coefficients from a circle toward the star, walks/point annealed 256->1024, MLP "
            "5->64x4->2 (tcgen05 BF16 products, FP32 accumulation in TMEM) trained online on the walks' "
-           "estimates (4 Adam iterations per step); value = gradient RMSE x seconds of one estimate at "
+           "estimates (4 Adam iterations on every second step's walks), 6 seeds; value = gradient RMSE x "
+           "seconds of one estimate at "
            "1024 walks/point, the network's inference inside the timed region"),
     "ablation": "estimator ablation (product estimators, du/dn estimators, K, h) on the 2D workload",
     "sgd": ("noisy-gradient optimisation (Sec. 5.2) on the 2D workload's geometry: the star's position "
@@ -88,11 +89,12 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def measured_traffic(kernel: str, workload: str):
-    """DRAM bytes per walk-step of `kernel` on `workload` from a committed ncu
-    summary (a line 'traffic: kernel=... workload=... dram_bytes=... walk_steps=...
-    source_sha256=...' under profiles/), or None if there is none or the
-    kernel's sources changed since it was captured."""
+def measured_traffic(kernel: str, workload: str, tag: str = "traffic", key: str = "dram_bytes"):
+    """Bytes per walk-step of `kernel` on `workload` from a committed ncu
+    summary (a line '<tag>: kernel=... workload=... <key>=... walk_steps=...
+    source_sha256=...' under profiles/; tag 'traffic' for DRAM bytes, 'l2l1'
+    for L2 -> L1 bytes), or None if there is none or the kernel's sources
+    changed since it was captured."""
     d = os.path.join(ROOT, "profiles")
     if not os.path.isdir(d):
         return None
@@ -103,11 +105,11 @@ def measured_traffic(kernel: str, workload: str):
         with open(os.path.join(d, name)) as fh:
             for line in fh:
                 line = line.strip().strip("`")
-                if not line.startswith("traffic:"):
+                if not line.startswith(tag + ":"):
                     continue
-                kv = dict(t.split("=", 1) for t in line[len("traffic:"):].split() if "=" in t)
+                kv = dict(t.split("=", 1) for t in line[len(tag) + 1:].split() if "=" in t)
                 if kv.get("kernel") == kernel and kv.get("workload") == workload and kv.get("source_sha256") == want:
-                    return float(kv["dram_bytes"]) / float(kv["walk_steps"])
+                    return float(kv[key]) / float(kv["walk_steps"])
     return None
 
 
@@ -309,12 +311,13 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
-def control_variate_summary(seeds=(3, 4, 5), steps: int = 200):
+def control_variate_summary(seeds=(3, 4, 5, 6, 7, 8), steps: int = 200, train_every: int = 2):
     """Config 5: the optimisation of the 2D shape-from-diffusion workload with
     and without the learned control variate, per seed: final losses of the CV
-    run, of a plain run of the same number of steps and of a plain run given
-    the CV run's wall time (training included); and the gradient RMSE x seconds
-    of one estimate (network inference timed) at the start shape and midway."""
+    run (the network trained on every train_every-th step's walks), of a plain
+    run of the same number of steps and of a plain run given the CV run's wall
+    time (training included); and the gradient RMSE x seconds of one estimate
+    (network inference timed) at the start shape and midway."""
     import numpy as np
     import torch
     from paper_2405_12964_gb300 import build, scenes
@@ -346,7 +349,8 @@ def control_variate_summary(seeds=(3, 4, 5), steps: int = 200):
     runs, trainer = [], None
     for seed in seeds:
         th_p, hp, _ = optimize.run(sc, target, start, steps=steps, use_cv=False, seed=seed)
-        th_c, hc, trainer = optimize.run(sc, target, start, steps=steps, use_cv=True, whole_walk=True, seed=seed)
+        th_c, hc, trainer = optimize.run(sc, target, start, steps=steps, use_cv=True, whole_walk=True, seed=seed,
+                                         train_every=train_every)
         # equal wall time: the plain optimiser gets the seconds the CV run took (training included)
         steps_eq = max(steps, int(round(steps * hc.seconds[-1] / max(hp.seconds[-1], 1e-9))))
         th_e, he, _ = optimize.run(sc, target, start, steps=steps_eq, use_cv=False, seed=seed)
@@ -364,7 +368,7 @@ def control_variate_summary(seeds=(3, 4, 5), steps: int = 200):
         plain = optimize.gradient_rmse_x_time(sc, th, s_uref, 1024)
         cv = optimize.gradient_rmse_x_time(sc, th, s_uref, 1024, net=trainer.net, whole_walk=True)
         rows[name] = {"plain": plain, "cv": cv, "rmse_x_seconds_ratio": cv["rmse_x_seconds"] / plain["rmse_x_seconds"]}
-    return {"workload": WORKLOADS["c5"], "steps": steps, "runs": runs,
+    return {"workload": WORKLOADS["c5"], "steps": steps, "train_every": train_every, "runs": runs,
             "equal_time_final_loss_ratio": {"geometric_mean": float(np.exp(np.mean(np.log(ratios)))),
                                             "min": float(ratios.min()), "max": float(ratios.max()),
                                             "seeds": list(seeds)},
@@ -648,6 +652,7 @@ def main():
     l2 = probe_l2_read(local)
     kname = f"walk_kernel<{sc.dim},{'true' if trav in (2, 3) else 'false'}>"
     traffic_per_step = measured_traffic(kname, args.workload)
+    l2l1_per_step = measured_traffic(kname, args.workload, tag="l2l1", key="bytes")
 
     e2e = None
     if rank == 0:
@@ -716,6 +721,11 @@ def main():
                                             else "no ncu capture of the current kernel sources"),
                          "kernel": kname, "peak_source": src,
                          "bytes_per_walk_step": alg_bytes / max(steps_done, 1),
+                         "l2_to_l1_bytes_per_walk_step": l2l1_per_step,
+                         "l2_to_l1_source": ("ncu lts__t_sectors_srcunit_tex_op_read.sum x 32 B of one launch "
+                                             "(full section set on 1024 walks per point)"
+                                             if l2l1_per_step is not None
+                                             else "no ncu capture of the current kernel sources"),
                          "walk_kernel_ms": walk_s * 1e3 / args.steps,
                          "l2": {"peak": l2, "unit": "GB/s", "frac": achieved / l2,
                                 "peak_source": "measured in this run: 32 MB L2-resident buffer read 50 times "
