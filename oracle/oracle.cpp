@@ -697,15 +697,16 @@ double oracle_star_weight(int dim, double sigma, double t, double R) {
 }
 
 static PhaseResult wost_walk(const oracle_scene* s, const Adjacency& adj, const double* x0, uint64_t walk_id,
-                             uint32_t phase) {
+                             uint32_t phase, int on0, const double* n0) {
     PhaseResult res;
     res.x1[0] = res.x1[1] = res.x1[2] = NAN;
     res.ball_w = 0;
     const int d = s->dim;
     double x[3] = {x0[0], x0[1], d == 3 ? x0[2] : 0.0};
     double acc = 0;
-    int on = -1;                       /* the Neumann element the walk sits on, -1 inside */
+    int on = on0;                      /* the Neumann element the walk sits on, -1 inside */
     double n_on[3] = {0, 0, 0};        /* its normal, out of the domain */
+    if (on >= 0) for (int i = 0; i < 3; ++i) n_on[i] = n0[i];
     for (int k = 0;; ++k) {
         double xbar[3] = {0, 0, 0}, bary[2];
         int e;
@@ -759,10 +760,59 @@ static PhaseResult wost_walk(const oracle_scene* s, const Adjacency& adj, const 
     }
 }
 
-/* One phase of a walk: walk on spheres, or walk on stars with a Neumann part. */
+/* A query point on the Neumann part (within 1e-3 eps of it) starts its walk
+ * on the closest Neumann element (ties to the lower index), with that
+ * element's normal oriented out of the domain: the point 1e-3 of the
+ * element's size behind the element's centre is inside.  Returns the
+ * element, or -1 for a point inside the domain. */
+int oracle_inside(const oracle_scene* s, int n, const double* xq, int* inside);
+
+static int neumann_start(const oracle_scene* s, const double* x0, double* n_out) {
+    const int d = s->dim;
+    double best = INFINITY;
+    int best_e = -1;
+    for (int e = 0; e < s->n_elem; ++e) {
+        if (!s->neumann[e]) continue;
+        double xb[3] = {0, 0, 0}, b2[2];
+        const int* el = s->elem + (size_t)d * e;
+        const double d2 = d == 2 ? closest_on_segment(x0, s->vert + 2 * el[0], s->vert + 2 * el[1], xb, b2)
+                                 : closest_on_triangle(x0, s->vert + 3 * el[0], s->vert + 3 * el[1],
+                                                       s->vert + 3 * el[2], xb, b2);
+        if (d2 < best) { best = d2; best_e = e; }
+    }
+    if (best_e < 0 || std::sqrt(best) > 1e-3 * s->eps) return -1;
+    double n[3];
+    element_normal(s, best_e, n);
+    const int* el = s->elem + (size_t)d * best_e;
+    double c[3] = {0, 0, 0}, size;
+    for (int j = 0; j < d; ++j)
+        for (int i = 0; i < d; ++i) c[i] += s->vert[(size_t)d * el[j] + i] / d;
+    if (d == 2) {
+        size = std::hypot(s->vert[2 * el[1]] - s->vert[2 * el[0]], s->vert[2 * el[1] + 1] - s->vert[2 * el[0] + 1]);
+    } else {
+        double u[3], v[3], w[3];
+        for (int i = 0; i < 3; ++i) { u[i] = s->vert[3 * el[1] + i] - s->vert[3 * el[0] + i];
+                                      v[i] = s->vert[3 * el[2] + i] - s->vert[3 * el[0] + i]; }
+        w[0] = u[1] * v[2] - u[2] * v[1]; w[1] = u[2] * v[0] - u[0] * v[2]; w[2] = u[0] * v[1] - u[1] * v[0];
+        size = std::sqrt(std::sqrt(dot3(w, w)));
+    }
+    double behind[3];
+    for (int i = 0; i < d; ++i) behind[i] = c[i] - 1e-3 * size * n[i];
+    int in = 0;
+    oracle_inside(s, 1, behind, &in);
+    for (int i = 0; i < 3; ++i) n_out[i] = in ? n[i] : -n[i];
+    return best_e;
+}
+
+/* One phase of a walk: walk on spheres, or walk on stars with a Neumann part
+ * (the main walk of a query point on the Neumann part starts on it). */
 static PhaseResult phase_walk(const oracle_scene* s, const Adjacency* adj, const double* x0, uint64_t walk_id,
                               uint32_t phase, const double* ball_n) {
-    if (s->neumann) return wost_walk(s, *adj, x0, walk_id, phase);
+    if (s->neumann) {
+        double n0[3] = {0, 0, 0};
+        const int on0 = phase == 0 ? neumann_start(s, x0, n0) : -1;
+        return wost_walk(s, *adj, x0, walk_id, phase, on0, n0);
+    }
     return forward_walk(s, x0, walk_id, phase, ball_n);
 }
 

@@ -112,3 +112,55 @@ def test_cube_with_neumann_faces_closed_form():
     dirichlet = np.nonzero(sc.neumann == 0)[0]
     hit = o["kind"][:, 0] == oracle.KIND_SHELL
     assert np.isin(o["elem"][hit], dirichlet).all()
+
+
+def _on_neumann_points(name):
+    """Query points on the Neumann part (off its vertices), with the scene."""
+    if name == "quarter_disk":
+        sc = scenes.quarter_disk_scene("mapped", n_query=2)
+        s = (np.arange(6) + 0.37) / 16 + 0.1
+        q = np.concatenate([np.stack([s, 0 * s], 1), np.stack([0 * s, s], 1)])
+    elif name == "strip":
+        sc = scenes.strip_scene(sigma=4.0, n_query=2)
+        s = (np.arange(6) + 0.37) / 4 - 0.8
+        q = np.concatenate([np.stack([s, np.full(6, -0.5)], 1), np.stack([s, np.full(6, 0.5)], 1)])
+    else:
+        sc = scenes.cube_neumann_scene(n_query=2)
+        s = np.array([-0.63, -0.21, 0.17, 0.58])
+        q = np.concatenate([np.stack([s, np.full(4, 1.0), 0.31 + 0 * s], 1),
+                            np.stack([s, -0.27 + 0 * s, np.full(4, -1.0)], 1)])
+    sc.query = q
+    return sc
+
+
+@pytest.mark.parametrize("name", ["quarter_disk", "strip", "cube"])
+def test_query_points_on_the_neumann_part(name):
+    # a query point on the Neumann part starts its walk there, with the element's normal
+    # oriented out of the domain: the closed forms hold on that part too (u and du/dtheta;
+    # du is a rare-event estimate near the fixed side, so its SE is floored at the median)
+    sc = _on_neumann_points(name)
+    r = _run(sc, 2048 if name == "cube" else 4096)
+    if name == "quarter_disk":
+        u, du = cf.quarter_disk(sc.query, "mapped")
+        rel, ab, drel, dab = 3e-3, 2e-3, 0.08, 0.02
+    elif name == "strip":
+        u, du = cf.strip(sc.query, 4.0)
+        rel, ab, drel, dab = 3e-3, 1e-3, 0.08, 0.01
+    else:
+        u, du = cf.cube_linear(sc.query)
+        rel, ab, drel, dab = 0.0, 4e-3, 0.08, 0.02
+    _check(r["u"], r["u_se"], u, rel, ab)
+    _check(r["du"], np.maximum(r["du_se"], np.median(r["du_se"], axis=0)), du, drel, dab)
+    # the first move goes into the domain (a normal pointing inwards would send it out)
+    o = r["out"]
+    assert np.all(np.isfinite(o["u_hat"]))
+    x1 = o["x1"].reshape(-1, 3)
+    x1 = x1[np.isfinite(x1[:, 0])]
+    tol = 1e-12
+    if name == "quarter_disk":
+        assert np.all(x1[:, 0] >= -tol) and np.all(x1[:, 1] >= -tol)
+        assert np.all(np.hypot(x1[:, 0], x1[:, 1]) <= 1 + tol)
+    elif name == "strip":
+        assert np.all(np.abs(x1[:, 1]) <= 0.5 + tol)
+    else:
+        assert np.all(np.abs(x1) <= 1 + tol)
