@@ -221,8 +221,13 @@ dwos_status dwos_set_pde(dwos_ctx* ctx, float sigma, float f);
  * only.  The differential walk nests there (Sec. 4.2, Eq. mixed_bvp_deriv):
  * the Neumann part contributes no boundary term, and its vertices' motion
  * (for instance the tangential stretch of a side next to a moving Dirichlet
- * part) enters only through the geometry.  Query points must lie in the
- * interior.  Records number elements as the input does.  Not available with
+ * part) enters only through the geometry.  Query points lie in the interior
+ * or on the Neumann part (the thermal design observes its temperature there):
+ * a point within 1e-3 eps of the Neumann part starts its walk on the closest
+ * Neumann element (at a vertex shared by two, the search's pick), with that
+ * element's normal oriented out of the domain (the point 1e-3 of the
+ * element's size behind its centre is inside); such points count as inside.
+ * Records number elements as the input does.  Not available with
  * a Neumann part: the ball-gradient du/dn estimator, control variates,
  * batches, dwos_eval_static and the shape-functional calls
  * (DWOS_ERR_NOT_IMPLEMENTED / DWOS_ERR_INVALID_ARG).  dwos_closest_point

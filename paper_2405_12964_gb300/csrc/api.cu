@@ -123,7 +123,10 @@ dwos_status rebuild(dwos_ctx* ctx) {
     N.adj = ctx->nadj;
     N.vert = ctx->vert;
     N.dmap = ctx->dmap;
-    CK(cudaMemcpyAsync(ctx->d_neu, &N, sizeof(N), cudaMemcpyHostToDevice, ctx->stream), "copy Neumann part");
+    N.q_start = ctx->q_start;
+    ctx->neu_host = N;
+    CK(cudaMemcpyAsync(ctx->d_neu, &ctx->neu_host, sizeof(N), cudaMemcpyHostToDevice, ctx->stream),
+       "copy Neumann part");
     CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     return DWOS_OK;
 }
@@ -195,6 +198,24 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
             ctx->launches += 3;
         }
         valid = ctx->valid;
+    }
+    if (ctx->n_neumann > 0 && n_query > 0) {
+        // query points on the Neumann part (within 1e-3 eps) start their walks on it, the
+        // element's normal oriented out of the domain by an inside test behind its centre
+        CK(grow(ctx->q_start, ctx->q_start_cap, (size_t)n_query), "alloc start states");
+        CK(grow(ctx->behind, ctx->behind_cap, (size_t)n_query * ctx->dim), "alloc start states");
+        CK(grow(ctx->behind_in, ctx->behind_in_cap, (size_t)n_query), "alloc start states");
+        if (ctx->neu_host.q_start != ctx->q_start) {
+            ctx->neu_host.q_start = ctx->q_start;
+            CK(cudaMemcpyAsync(ctx->d_neu, &ctx->neu_host, sizeof(DevNeumann), cudaMemcpyHostToDevice, ctx->stream),
+               "copy Neumann part");
+        }
+        CK(launch_neumann_start(ctx->dim, n_query, d_xq, ctx->neu_host, 1e-3f * ctx->opt.eps, ctx->q_start,
+                                ctx->behind, ctx->stream), "Neumann start");
+        CK(inside_all(ctx, n_query, ctx->behind, ctx->behind_in), "Neumann start orientation");
+        CK(launch_neumann_orient(n_query, ctx->behind_in, ctx->q_start,
+                                 ctx->opt.check_inside ? ctx->valid : nullptr, ctx->stream), "Neumann start");
+        ctx->launches += 5;
     }
     DevProblem P;
     std::memset(&P, 0, sizeof(P));
@@ -375,7 +396,8 @@ void dwos_destroy(dwos_ctx* ctx) {
     void* bufs[] = {ctx->vert_ref, ctx->vert, ctx->elem, ctx->jac, ctx->theta, ctx->g_vert, ctx->dg_vert, ctx->rec,
                     ctx->xq, ctx->valid, ctx->wvec, ctx->out, ctx->acc_vert, ctx->trace, ctx->dbg, ctx->misc_f,
                     ctx->misc_i, ctx->misc_u, ctx->xq_prev, ctx->d_ctr, ctx->d_err, ctx->pw, ctx->vert_active,
-                    ctx->misc_d, ctx->elem_d, ctx->elem_n, ctx->dmap, ctx->nadj, ctx->d_neu, ctx->inside_tmp};
+                    ctx->misc_d, ctx->elem_d, ctx->elem_n, ctx->dmap, ctx->nadj, ctx->d_neu, ctx->inside_tmp,
+                    ctx->q_start, ctx->behind, ctx->behind_in};
     bvh_free(ctx->bvh_n);
     for (void* p : bufs) if (p) cudaFree(p);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);

@@ -40,6 +40,10 @@ struct dwos_ctx {
     int* nadj = nullptr;         // per Neumann element and endpoint / edge: the neighbour's vertex, -1 open
     dwos::BvhBuffers bvh_n;      // over the Neumann part
     dwos::DevNeumann* d_neu = nullptr;
+    dwos::DevNeumann neu_host{};                          // what d_neu holds
+    float4* q_start = nullptr; size_t q_start_cap = 0;    // per query: start on the Neumann part
+    float* behind = nullptr; size_t behind_cap = 0;       // per query: the orientation test point
+    int* behind_in = nullptr; size_t behind_in_cap = 0;
     int* inside_tmp = nullptr; size_t inside_tmp_cap = 0;
 
     // workspaces (grow-only)

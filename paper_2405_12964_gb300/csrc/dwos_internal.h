@@ -23,6 +23,8 @@ struct DevNeumann {
                                 // neighbour's vertex across it, -1 where the Neumann part ends
     const float* vert;          // current vertices
     const int* dmap;            // Dirichlet element (compact, the main BVH's numbering) -> input element
+    const float4* q_start;      // per query point of the current call: normal out of the domain (xyz) and
+                                // the Neumann element (compact, int bits in w) its walk starts on, -1 inside
 };
 
 // Everything a walk needs about one problem.  Copied to the device (and, in
@@ -174,6 +176,16 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
                          int* blocks_used, const DevProblem* host_prob = nullptr,
                          DevCounters* zero_counters = nullptr);
 int walk_max_blocks_per_sm(int dim, int block_size, int traversal = 0, bool star = false);
+// Query points on the Neumann part: per point the closest Neumann element if it
+// lies within tol of it (q_start w = its compact index, xyz = its unit normal,
+// not yet oriented) and the point 1e-3 of the element's size behind its centre
+// along that normal (behind, dim floats); -1 and the point itself otherwise.
+cudaError_t launch_neumann_start(int dim, int n, const float* xq, const DevNeumann& N, float tol,
+                                 float4* q_start, float* behind, cudaStream_t stream);
+// Orients each start normal out of the domain (flipped where the point behind the
+// centre is outside) and marks the point valid (valid may be null).
+cudaError_t launch_neumann_orient(int n, const int* behind_inside, float4* q_start, int* valid,
+                                  cudaStream_t stream);
 // The walk step's ball weights (source factor for uniform u, recursive weight) and the
 // K0 of the 2D source weight, evaluated as the walk kernel evaluates them (walk.cu).
 cudaError_t launch_ball_weights(int dim, float k, int n, const float* d, const float* u, float* src, float* alpha,

@@ -209,6 +209,14 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
                     } else {
                         phase = 0; step = 0; hint = -1; acc = 0.0f;
                         on_e = -1;
+                        if constexpr (STAR) {   // a query point on the Neumann part starts on it
+                            if (NS.q_start) {
+                                const float4 qs = NS.q_start[point];
+                                on_e = __float_as_int(qs.w);
+                                n_on[0] = qs.x; n_on[1] = qs.y;
+                                if (DIM == 3) n_on[DIM - 1] = qs.z;
+                            }
+                        }
                         active = true;
                     }
                 } else {
@@ -631,6 +639,82 @@ cudaError_t launch_star_weight(int dim, float k, int n, const float* t, const fl
     if (n <= 0) return cudaSuccess;
     if (dim == 2) star_weight_kernel<2><<<(n + 255) / 256, 256, 0, stream>>>(k, n, t, R, out);
     else star_weight_kernel<3><<<(n + 255) / 256, 256, 0, stream>>>(k, n, t, R, out);
+    return cudaGetLastError();
+}
+
+namespace {
+
+template <int DIM>
+__global__ void neumann_start_kernel(int n, const float* __restrict__ xq, DevNeumann N, float tol2,
+                                     float4* __restrict__ q_start, float* __restrict__ behind) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    float x[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) x[k] = xq[DIM * p + k];
+    BvhView bvh{N.nodes, N.prims, 0, N.n_internal, N.n_tree, N.n_big, 0, nullptr, nullptr, 0.0f};
+    float best2 = kInf;
+    int best = -1;
+    unsigned nn = 0, np = 0;
+    closest_leaf<DIM>(bvh, x, best2, best, nn, np);
+    float4 out = make_float4(0.0f, 0.0f, 0.0f, __int_as_float(-1));
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) behind[DIM * p + k] = x[k];
+    if (best >= 0 && best2 <= tol2) {
+        const int e = __ldg(N.prim_elem + best);
+        float m[3] = {0.0f, 0.0f, 0.0f};
+        neumann_normal<DIM>(N, e, m);
+        float a[DIM], b[DIM], c[DIM], size;
+        const int* ev = N.elem + (size_t)DIM * e;
+        vload<DIM>(N.vert, __ldg(ev), a);
+        vload<DIM>(N.vert, __ldg(ev + 1), b);
+        if (DIM == 2) {
+            size = sqrtf((b[0] - a[0]) * (b[0] - a[0]) + (b[1] - a[1]) * (b[1] - a[1]));
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) c[k] = 0.5f * (a[k] + b[k]);
+        } else {
+            float v[DIM];
+            vload<DIM>(N.vert, __ldg(ev + 2), v);
+            const float u1[3] = {b[0] - a[0], b[1] - a[1], b[DIM - 1] - a[DIM - 1]};
+            const float u2[3] = {v[0] - a[0], v[1] - a[1], v[DIM - 1] - a[DIM - 1]};
+            const float w0 = u1[1] * u2[2] - u1[2] * u2[1], w1 = u1[2] * u2[0] - u1[0] * u2[2],
+                        w2 = u1[0] * u2[1] - u1[1] * u2[0];
+            size = sqrtf(sqrtf(w0 * w0 + w1 * w1 + w2 * w2));
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) c[k] = (a[k] + b[k] + v[k]) * (1.0f / 3.0f);
+        }
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) behind[DIM * p + k] = c[k] - 1e-3f * size * m[k];
+        out = make_float4(m[0], m[1], m[2], __int_as_float(e));
+    }
+    q_start[p] = out;
+}
+
+__global__ void neumann_orient_kernel(int n, const int* __restrict__ behind_inside, float4* __restrict__ q_start,
+                                      int* __restrict__ valid) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    float4 q = q_start[p];
+    if (__float_as_int(q.w) < 0) return;
+    if (!behind_inside[p]) { q.x = -q.x; q.y = -q.y; q.z = -q.z; }
+    q_start[p] = q;
+    if (valid) valid[p] = 1;     // on the boundary: ray parity says nothing there
+}
+
+}  // namespace
+
+cudaError_t launch_neumann_start(int dim, int n, const float* xq, const DevNeumann& N, float tol,
+                                 float4* q_start, float* behind, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (n + 127) / 128;
+    if (dim == 2) neumann_start_kernel<2><<<blocks, 128, 0, s>>>(n, xq, N, tol * tol, q_start, behind);
+    else neumann_start_kernel<3><<<blocks, 128, 0, s>>>(n, xq, N, tol * tol, q_start, behind);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_neumann_orient(int n, const int* behind_inside, float4* q_start, int* valid, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    neumann_orient_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, behind_inside, q_start, valid);
     return cudaGetLastError();
 }
 

@@ -178,3 +178,27 @@ def test_queries_and_refusals_with_a_neumann_part(Solver):
     s.set_neumann(None)                                     # all Dirichlet again: plain walk on spheres
     s.eval(sc.query, 16)
     s.sync()
+
+
+@pytest.mark.parametrize("name", ["quarter_disk", "strip", "cube"])
+def test_query_points_on_the_neumann_part(Solver, name):
+    # points on the Neumann part start their walks on it (normal oriented out of the domain):
+    # per-walk replay against the oracle, and the closed forms on that part
+    from tests.test_oracle_wost import _on_neumann_points
+    sc = _on_neumann_points(name)
+    sc.query = sc.query.astype(np.float32).astype(np.float64)     # the same start on both sides
+    s, g, o, same = _replay(Solver, sc, 64, u_scale=1.0)
+    assert np.all(np.isfinite(g["rec"]["u"]))
+    W = 4096 if name == "cube" else 8192
+    out = s.eval(sc.query, W, grad=True)
+    u, use = out["u"].cpu().numpy(), out["u_se"].cpu().numpy()
+    du, dse = out["du"].cpu().numpy(), out["du_se"].cpu().numpy()
+    if name == "quarter_disk":
+        ue, due = cf.quarter_disk(sc.query, "mapped")
+    elif name == "strip":
+        ue, due = cf.strip(sc.query, 4.0)
+    else:
+        ue, due = cf.cube_linear(sc.query)
+    assert np.all(np.abs(u - ue) <= 4.5 * use + 3e-3 * np.abs(ue) + 4e-3)
+    dse_ref = np.maximum(dse, np.median(dse, axis=0, keepdims=True))
+    assert np.all(np.abs(du - due) <= 4.5 * dse_ref + 0.08 * np.abs(due) + 0.02)
