@@ -11,8 +11,10 @@ Scenes (all seeds fixed; geometry seed 0x2405):
   disk_scene       128-gon of radius R with radial Fourier parameters
   star_box_scene   star-shaped emitter inside the box [-1, 1]^2
   sh_sphere_scene  SH-perturbed icosphere inside the box [-2, 2]^3
+  translated_star_scene  the star_box geometry with the star's position as the parameter
   mixed boundaries (a Dirichlet part and a reflecting Neumann part):
-  quarter_disk_scene, strip_scene, slit_disk_scene, cube_neumann_scene
+  quarter_disk_scene, strip_scene, slit_disk_scene, cube_neumann_scene,
+  thermal_scene (a heating wire under an insulating slab, observed on the slab)
 """
 from __future__ import annotations
 
@@ -491,6 +493,42 @@ def slit_disk_scene(n_circle: int = 256, n_slit: int = 32, n_query: int = 12, wa
     q = np.stack([r * np.cos(a), r * np.sin(a)], 1)
     sc = Scene("slit_disk", vert, elem, None, data="mapped", g_vert=g, sigma=0.0)
     sc.eps, sc.query, sc.walks, sc.neumann = eps, q, walks, neumann
+    return sc
+
+
+def thermal_scene(offset=(0.0, 0.0), n_wire: int = 64, n_slab: int = 40, n_query: int = 32, walks: int = 1024,
+                  eps: float = 1e-3, h: float = 1e-2, K: int = 2, seed: int = GEOMETRY_SEED) -> Scene:
+    """A 2D thermal design in the manner of Sec. 6.3: a heating wire (a circle of
+    radius 0.06 around (0, -0.35), n_wire segments, Dirichlet g = 1) warms an
+    insulating slab ([-0.5, 0.5] x [0.2, 0.3], a closed polyline of n_slab
+    segments per long side, reflecting Neumann) inside the box [-1, 1]^2 held
+    at g = 0; sigma = 0, no source.  theta = the wire's translation (a
+    2-vector: Vector Adam applies), at `offset` in `vert`.  Observation points:
+    n_query points on the slab's underside y = 0.2 (on the Neumann part, where
+    the thermal design reads its temperatures)."""
+    bv, be = box2d()
+    t = 2 * np.pi * np.arange(n_wire) / n_wire
+    wire = np.stack([0.06 * np.cos(t), -0.35 + 0.06 * np.sin(t)], 1) + np.asarray(offset, dtype=np.float64)
+    xs = -0.5 + np.arange(n_slab) / n_slab
+    n_end = 4
+    ye = 0.2 + 0.1 * np.arange(n_end) / n_end
+    slab = np.concatenate([np.stack([xs, np.full(n_slab, 0.2)], 1), np.stack([np.full(n_end, 0.5), ye], 1),
+                           np.stack([-xs, np.full(n_slab, 0.3)], 1), np.stack([np.full(n_end, -0.5), 0.5 - ye], 1)])
+    ws = np.stack([np.arange(n_wire), (np.arange(n_wire) + 1) % n_wire], 1) + 4
+    ns = len(slab)
+    ss = np.stack([np.arange(ns), (np.arange(ns) + 1) % ns], 1) + 4 + n_wire
+    vert = np.concatenate([bv, wire, slab], 0)
+    elem = np.concatenate([be, ws, ss], 0).astype(np.int32)
+    neumann = np.concatenate([np.zeros(4 + n_wire), np.ones(ns)]).astype(np.int32)
+    g = np.concatenate([np.zeros(4), np.ones(n_wire), np.zeros(ns)])
+    jac = np.zeros((len(vert), 2, 2))
+    jac[4:4 + n_wire, 0, 0] = 1.0
+    jac[4:4 + n_wire, 1, 1] = 1.0
+    qx = -0.45 + 0.9 * (np.arange(n_query) + 0.5) / n_query
+    q = np.stack([qx, np.full(n_query, 0.2)], 1)
+    sc = Scene("thermal", vert, elem, jac, data="mapped", g_vert=g, sigma=0.0)
+    sc.eps, sc.h, sc.K, sc.query, sc.walks, sc.neumann = eps, h, K, q, walks, neumann
+    sc.meta = {"theta0": np.asarray(offset, dtype=np.float64)}
     return sc
 
 

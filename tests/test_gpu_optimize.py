@@ -60,3 +60,13 @@ def test_noisy_gradient_study_runs_and_converges(opt):
         assert np.all(np.diff(runs[0]["seconds"]) > 0)
     # the annealed run starts with cheaper iterations
     assert table["annealed 2->32 WPP"]["seconds_per_iter"] < table["16 WPP"]["seconds_per_iter"] * 1.5
+
+
+def test_thermal_design_moves_the_heating_wire(opt):
+    # Sec. 6.3 in 2D: differential walks on stars from points on the insulating slab give
+    # the gradient of the temperature loss with respect to the wire's position
+    theta, err, losses = opt.thermal_design(iters=200, lr=5e-3, walks=128, target_walks=4096)
+    # from 0.158 to the noise floor of the target profile and the gradients (about 0.01-0.03)
+    assert np.mean(err[-20:]) < 0.35 * err[0], (err[0], err[-20:])
+    # the loss estimates carry the walks' variance (sum_p Var(u_p) / W, about 0.03 here)
+    assert np.mean(losses[-20:]) < 0.7 * np.mean(losses[:5])

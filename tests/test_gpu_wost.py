@@ -202,3 +202,13 @@ def test_query_points_on_the_neumann_part(Solver, name):
     assert np.all(np.abs(u - ue) <= 4.5 * use + 3e-3 * np.abs(ue) + 4e-3)
     dse_ref = np.maximum(dse, np.median(dse, axis=0, keepdims=True))
     assert np.all(np.abs(du - due) <= 4.5 * dse_ref + 0.08 * np.abs(due) + 0.02)
+
+
+def test_thermal_scene_replay(Solver):
+    # the thermal design's scene: a Dirichlet wire under a Neumann slab in a Dirichlet box,
+    # differential walks (K = 2) from points on the slab, per walk against the oracle
+    sc = scenes.thermal_scene(n_query=8)
+    sc.query = sc.query.astype(np.float32).astype(np.float64)
+    s, g, o, same = _replay(Solver, sc, 64)
+    assert np.all(np.isfinite(g["rec"]["u"]))
+    assert (o["kind"][:, 0] == oracle.KIND_SHELL).mean() > 0.99      # sigma = 0: every walk ends in a shell
