@@ -2,8 +2,10 @@
 // -> 4 x 64 tanh -> 8 linear outputs (0: u, 1: du/dn), trained and evaluated
 // on the 5th-generation tensor cores.
 //
-// One persistent kernel (128 threads, one CTA per SM) walks over tiles of 128
-// samples; thread r owns sample row r, which is also TMEM lane r.  Operands
+// One persistent kernel (256 threads, one CTA per SM) walks over tiles of 128
+// samples; sample row r is TMEM lane r, and threads r and r + 128 share it
+// (warps w and w + 4 reach the same TMEM lane quarter): each takes half of the
+// row's columns in the epilogues between the products.  Operands
 // live in shared memory as BF16 in the canonical no-swizzle core-matrix
 // layout (8 rows x 16 bytes per 128-byte core matrix), the products are
 // tcgen05.mma (kind::f16, BF16 in, FP32 accumulate) issued by one thread and
@@ -36,7 +38,7 @@ constexpr int OUT = 8;           // output width
 constexpr int OUTP = 16;         // output rows padded for the N = 16 product
 constexpr int NP = DWOS_MLP_NPARAM;
 constexpr int TILE = 128;        // samples per tile (the MMA's M)
-constexpr int THREADS = 128;
+constexpr int THREADS = 256;          // two threads per sample row
 // offsets of W_l and b_l (l = 1..5) in the flat parameter vector
 __host__ __device__ constexpr int off_w(int l) { return l == 1 ? 0 : 1088 + (l - 2) * 4160; }
 __host__ __device__ constexpr int off_b(int l) { return l == 1 ? 1024 : (l == 5 ? 14080 : 1088 + (l - 2) * 4160 + 4096); }
@@ -201,10 +203,12 @@ __global__ void __launch_bounds__(THREADS, 1)
                float* __restrict__ g_out, float* __restrict__ q_out, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char raw[];
     Smem& S = *reinterpret_cast<Smem*>(raw);
-    const int r = threadIdx.x;                 // sample row and TMEM lane
-    const int warp = r >> 5;
+    const int tid = threadIdx.x;
+    const int r = tid & (TILE - 1);            // sample row and TMEM lane
+    const int half = tid >> 7;                 // which half of the row's columns this thread takes
+    const int warp = tid >> 5;
     const uint32_t bar_load = smem_u32(&S.bar_load), bar_mma = smem_u32(&S.bar_mma);
-    if (r == 0) {
+    if (tid == 0) {
         bar_init(bar_load, 1);
         bar_init(bar_mma, 1);
         S.fail = 0;
@@ -216,25 +220,27 @@ __global__ void __launch_bounds__(THREADS, 1)
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     // constants: biases; zero the columns of the tiles that no tile overwrites
-    for (int i = r; i < 4 * H + OUT; i += THREADS)
+    for (int i = tid; i < 4 * H + OUT; i += THREADS)
         S.bias[i] = params[i < 4 * H ? off_b(1 + i / H) + i % H : off_b(5) + (i - 4 * H)];
     {
         const float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         const float one[8] = {1, 0, 0, 0, 0, 0, 0, 0};
-        put8(S.a0, C0, r, 2, one);
-        put8(S.a0, C0, r, 3, z);
-        for (int l = 0; l < 4; ++l) {
-            put8(S.a[l], CA, r, 8, one);
-            put8(S.a[l], CA, r, 9, z);
+        if (half == 0) {
+            put8(S.a0, C0, r, 2, one);
+            put8(S.a0, C0, r, 3, z);
+            for (int l = 0; l < 4; ++l) {
+                put8(S.a[l], CA, r, 8, one);
+                put8(S.a[l], CA, r, 9, z);
+            }
         }
-        for (int cc = 0; cc < CD / 8; ++cc) put8(S.d, CD, r, cc, z);
+        for (int cc = half * (CD / 16); cc < (half + 1) * (CD / 16); ++cc) put8(S.d, CD, r, cc, z);
     }
     fence_before();
     __syncthreads();
     fence_after();
     const uint32_t tmem = S.tmem_base;
-    const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-    if (r == 0) {
+    const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);   // this warp's TMEM lane quarter
+    if (tid == 0) {
         bar_expect_tx(bar_load, sizeof(WImage));
         bulk_g2s(smem_u32(&S.w), wimg, sizeof(WImage), bar_load);
     }
@@ -249,7 +255,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     // thread 0 commits the issued products; everyone waits; false if any wait failed
     auto sync_mma = [&]() -> bool {
-        if (r == 0) mma_commit(bar_mma);
+        if (tid == 0) mma_commit(bar_mma);
         const bool got = bar_wait(bar_mma, phase);
         phase ^= 1u;
         fence_after();
@@ -268,7 +274,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const bool valid = s < n;
         float px = 0.0f, py = 0.0f;
         if (valid) { px = x[2 * s]; py = x[2 * s + 1]; }
-        {
+        if (half == 0) {
             float f[8] = {0, 0, 0, 0, 0, 0, 0, 0};
             if (valid) feats(px, py, f);
             const float z[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int l = 1; l <= 4 && ok; ++l) {
             const __nv_bfloat16* A = l == 1 ? S.a0 : S.a[l - 2];
             const int CAin = l == 1 ? C0 : CA;
-            if (r == 0) {
+            if (tid == 0) {
                 fence_after();
                 for (int ks = 0; ks < CW[l] / 16; ++ks)
                     mma(tmem + T_SCR, kmajor(A, CAin, ks), kmajor(W[l], CW[l], ks), idesc_bf16(128, 64, false, false),
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             ok = sync_mma();
             if (!ok) break;
-            for (int c16 = 0; c16 < 4; ++c16) {
+            for (int c16 = 2 * half; c16 < 2 * half + 2; ++c16) {
                 float v[16];
                 tmem_ld16(lane_addr + T_SCR + 16 * c16, v);
 #pragma unroll
@@ -300,7 +306,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         if (!ok) break;
         // ---- output layer
-        if (r == 0) {
+        if (tid == 0) {
             fence_after();
             for (int ks = 0; ks < 4; ++ks)
                 mma(tmem + T_SCR, kmajor(S.a[3], CA, ks), kmajor(S.w.w5, H, ks), idesc_bf16(128, 16, false, false),
@@ -308,7 +314,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         ok = sync_mma();
         if (!ok) break;
-        {
+        if (half == 0) {
             float o[16];
             tmem_ld16(lane_addr + T_SCR, o);
             float d5[16];
@@ -337,7 +343,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const __nv_bfloat16* Ain = l == 1 ? S.a0 : S.a[l - 2];
             const int CAin = l == 1 ? C0 : CA;
             const bool delta_product = l > 1 || MODE == kEval;
-            if (r == 0) {
+            if (tid == 0) {
                 fence_after();
                 if (MODE == kTrain)
                     for (int ks = 0; ks < TILE / 16; ++ks)
@@ -355,7 +361,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!ok) break;
             if (l > 1) {
                 // delta_{l-1} = (delta_l W_l) * (1 - a_{l-1}^2), a as stored (BF16)
-                for (int c16 = 0; c16 < 4; ++c16) {
+                for (int c16 = 2 * half; c16 < 2 * half + 2; ++c16) {
                     float v[16], a[16];
                     tmem_ld16(lane_addr + T_SCR + 16 * c16, v);
                     get8(S.a[l - 2], CA, r, 2 * c16, a);
@@ -368,8 +374,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                 publish();
             } else if (MODE == kEval) {
                 float df[16];
-                tmem_ld16(lane_addr + T_SCR, df);       // d u / d features
-                if (valid && g_out) {
+                if (half == 0) tmem_ld16(lane_addr + T_SCR, df);       // d u / d features
+                if (half == 0 && valid && g_out) {
                     const float c0 = 3.14159265358979f * cospif(px), c1 = 3.14159265358979f * cospif(py);
                     const float c01 = 3.14159265358979f * cospif(px + py);
                     g_out[2 * s] = df[0] + df[2] * c0 + df[4] * c01;
@@ -384,13 +390,13 @@ __global__ void __launch_bounds__(THREADS, 1)
 
     if (MODE == kTrain && ok) {
         for (int off = 16; off > 0; off >>= 1) loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
-        if ((r & 31) == 0 && loss_acc != 0.0f) atomicAdd(loss, (double)loss_acc * (double)inv_n);
+        if ((tid & 31) == 0 && loss_acc != 0.0f) atomicAdd(loss, (double)loss_acc * (double)inv_n);
         // the CTA's weight and bias gradients: rows (outputs) are TMEM lanes 0..63
         float* P = part + (size_t)blockIdx.x * NP;
         for (int l = 1; l <= 5; ++l) {
             const int outs = l == 5 ? OUT : H, ins = l == 1 ? IN : H;
             const int ncol = l == 1 ? C0 : CA;
-            for (int c16 = 0; c16 < ncol / 16; ++c16) {
+            for (int c16 = half; c16 < ncol / 16; c16 += 2) {
                 float v[16];
                 tmem_ld16(lane_addr + t_dw(l) + 16 * c16, v);     // warp-wide: every warp loads
                 if (r < outs)
@@ -408,7 +414,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(TMEM_COLS));
-    if (r == 0 && !ok) atomicOr(err, 1);
+    if (tid == 0 && !ok) atomicOr(err, 1);
 }
 
 // The failure path of the bounded wait, without a fault: thread 0 initialises an
