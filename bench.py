@@ -213,6 +213,118 @@ def cpu_baseline(sc, budget_s: float = 15.0):
                       f"FP64 brute-force closest point, {dt:.1f} s, {steps} walk-steps"}
 
 
+def wost_summary(steps: int = 5, warmup: int = 2, oracle_budget_s: float = 3.0):
+    """Walks on stars (Sec. 3.4, 4.2) on the GPU and in the oracle: walk-steps/s
+    of the differential gradient step (U-statistic L2 gradient, K = 2) on the
+    2D thermal scene (32 points on the insulating slab x 16384 walks) and on
+    the 3D cube with four Neumann faces (64 interior points x 4096 walks),
+    inputs resident, L2 flushed between timed steps; and the FP64 oracle
+    (brute force over every element and silhouette) on a bounded sample of
+    the same walks on the host cores."""
+    import numpy as np
+    import torch
+    from paper_2405_12964_gb300 import build, scenes
+    build.build()
+    import oracle
+    oracle.build()
+    from paper_2405_12964_gb300.dwos import Solver
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    out = {}
+    for name, sc in (("thermal_2d", scenes.thermal_scene(n_query=32, walks=16384)),
+                     ("cube_3d", scenes.cube_neumann_scene(n_query=64, walks=4096, K=2))):
+        s = Solver(0)
+        s.load_scene(sc)
+        xq = torch.tensor(sc.query, dtype=torch.float32, device="cuda")
+        uref = torch.zeros(sc.query.shape[0], dtype=torch.float32, device="cuda")
+        total = sc.query.shape[0] * sc.walks
+        for i in range(warmup):
+            s.grad_l2(xq, uref, sc.walks, walk_id_base=(i + 1) * total)
+        torch.cuda.synchronize()
+        t, walk_steps, capped = [], 0, 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for i in range(steps):
+            flush.fill_(float(i))
+            e0.record()
+            s.grad_l2(xq, uref, sc.walks, walk_id_base=(warmup + i + 1) * total)
+            e1.record()
+            st = s.stats()
+            t.append(e0.elapsed_time(e1))
+            walk_steps += st["steps_main"] + st["steps_nested"]
+            capped += st["capped"]
+        device_error = None
+        try:
+            s.sync()   # raises on a walk that left the domain or a search out of budget
+        except Exception as ex:
+            device_error = str(ex)
+        pr = oracle.Problem(vert=sc.vert, elem=sc.elem, jac=sc.jac, data_kind="mapped", g_vert=sc.g_vert,
+                            sigma=sc.sigma, f=sc.f, eps=sc.eps, h=sc.h, K=sc.K, seed=sc.seed, neumann=sc.neumann)
+        n_pts = min(8, sc.query.shape[0])
+        t0 = time.perf_counter()
+        o = oracle.run_walks(pr, sc.query[:n_pts], 8, differential=True, walk_id_base=1 << 41)
+        per = (time.perf_counter() - t0) / (8 * n_pts)
+        W = int(max(8, min(4096, oracle_budget_s / max(per, 1e-9) / n_pts)))
+        t0 = time.perf_counter()
+        o = oracle.run_walks(pr, sc.query[:n_pts], W, differential=True, walk_id_base=1 << 41)
+        dt = time.perf_counter() - t0
+        o_steps = int(np.clip(o["steps"], 0, None).sum())
+        out[name] = {"points": int(sc.query.shape[0]), "walks_per_point": int(sc.walks), "elements": int(len(sc.elem)),
+                     "neumann_elements": int(sc.neumann.sum()), "value": walk_steps / (sum(t) / 1e3), "unit": UNIT,
+                     "ms_per_step": float(np.mean(t)), "walk_steps_per_step": walk_steps / steps,
+                     "capped_walks": int(capped), "device_error": device_error,
+                     "oracle": {"value": o_steps / dt, "unit": UNIT, "cores": oracle.num_threads(),
+                                "sample": f"{n_pts} points x {W} differential walks, {dt:.1f} s"}}
+    return out
+
+
+def functional_summary(reps: int = 5, n_try: int = 65536, walks: int = 64, oracle_budget_s: float = 3.0):
+    """The volume-integrated functional (Eq. functional, functional_deriv) on
+    the 2D shape-from-diffusion geometry: J = int_M 1/2 (u - uref)^2 over the
+    box M = [-0.9, 0.9]^2 with uref = 0, n_try uniform candidates in M (those in
+    Omega kept), `walks` differential walks per kept point, plus the exact
+    boundary term.  Seconds per gradient (synchronised, the host's uref
+    evaluation included) and walk-steps/s of its walks; the FP64 oracle's walk
+    rate on a bounded sample of the same points on the host cores."""
+    import numpy as np
+    import torch
+    from paper_2405_12964_gb300 import build, scenes
+    build.build()
+    import oracle
+    oracle.build()
+    from paper_2405_12964_gb300.dwos import Solver
+    sc = scenes.star_box_scene()
+    s = Solver(0)
+    s.load_scene(sc)
+    lo, hi = [-0.9, -0.9], [0.9, 0.9]
+    zero = lambda p: np.zeros(len(p))
+    s.functional_gradient(lo, hi, zero, walks, n_try, seed=99)
+    secs, walk_steps = [], 0
+    for r in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.functional_gradient(lo, hi, zero, walks, n_try, seed=r, walk_id_base=(r + 1) << 34)
+        torch.cuda.synchronize()
+        secs.append(time.perf_counter() - t0)
+        st = s.stats()
+        walk_steps += st["steps_main"] + st["steps_nested"]
+    pts, _ = s.sample_domain(n_try, lo, hi, 0)
+    p = pts.cpu().numpy().astype(np.float64)
+    pr = oracle.Problem(vert=sc.vert, elem=sc.elem, jac=sc.jac, data_kind="mapped", g_vert=sc.g_vert,
+                        sigma=sc.sigma, f=sc.f, eps=sc.eps, h=sc.h, K=sc.K, seed=sc.seed)
+    n_pts = 256
+    t0 = time.perf_counter()
+    oracle.run_walks(pr, p[:n_pts], 2, differential=True, walk_id_base=1 << 41)
+    per = (time.perf_counter() - t0) / (2 * n_pts)
+    W = int(max(2, min(walks, oracle_budget_s / max(per, 1e-9) / n_pts)))
+    t0 = time.perf_counter()
+    o = oracle.run_walks(pr, p[:n_pts], W, differential=True, walk_id_base=1 << 41)
+    dt = time.perf_counter() - t0
+    o_steps = int(np.clip(o["steps"], 0, None).sum())
+    return {"kept_points": int(len(p)), "candidates": n_try, "walks_per_point": walks,
+            "seconds_per_gradient": float(np.median(secs)), "value": walk_steps / sum(secs), "unit": UNIT,
+            "oracle": {"value": o_steps / dt, "unit": UNIT, "cores": oracle.num_threads(),
+                       "sample": f"{n_pts} kept points x {W} differential walks, {dt:.1f} s"}}
+
+
 def run_reference(args):
     import torch
     rank = int(os.environ.get("RANK", "0"))
@@ -740,6 +852,8 @@ def main():
             line["c3"] = thermal_summary(steps=5, warmup=2)
             line["c4"] = batched_summary(steps=3, warmup=2)
             line["c5"] = control_variate_summary()
+            line["wost"] = wost_summary()
+            line["functional"] = functional_summary()
             line["extras_seconds"] = time.perf_counter() - t_x
         print(json.dumps(line), flush=True)
     if dist:

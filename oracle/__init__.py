@@ -118,6 +118,8 @@ def lib():
             L.oracle_source_weight.restype = ctypes.c_double
             L.oracle_star_weight.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_double]
             L.oracle_star_weight.restype = ctypes.c_double
+            L.oracle_turn_inward.argtypes = [ctypes.c_int, dp, dp, dp]
+            L.oracle_turn_inward.restype = None
             L.oracle_bessel_k0.argtypes = [ctypes.c_double]
             L.oracle_bessel_k0.restype = ctypes.c_double
             L.oracle_gradient_factor.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
@@ -239,6 +241,17 @@ def alpha(dim: int, sigma: float, d: float) -> float:
 def source_weight(dim: int, sigma: float, d: float, rho: float) -> float:
     """|B(d)| * G_d(rho d): Algorithm 1's source weight per unit source."""
     return lib().oracle_source_weight(dim, sigma, d, rho)
+
+
+def turn_inward(v: np.ndarray, n_on, n2=None) -> np.ndarray:
+    """Directions drawn on the Neumann part turned into the domain: v (n x 3)
+    for a walk on a side with outward normal n_on, or on the edge of two sides
+    (outward normals n_on, n2)."""
+    v = np.array(v, dtype=np.float64, order="C").reshape(-1, 3)
+    a = np.ascontiguousarray(n_on, dtype=np.float64).reshape(3)
+    b = None if n2 is None else np.ascontiguousarray(n2, dtype=np.float64).reshape(3)
+    lib().oracle_turn_inward(v.shape[0], _dp(v), _dp(a), _dp(b))
+    return v
 
 
 def star_weight(dim: int, sigma: float, t: float, R: float) -> float:

@@ -434,7 +434,16 @@ struct PhaseResult {
     double xbar[3];
     double x_last[3];  /* walk point at termination */
     double ball_w;     /* ball-gradient weight F(R) (omega . n) of the first move, 0 if none */
+    int on, on2;       /* walk on stars: the Neumann sides the walk sat on when it ended (-1: none) */
+    double n_on[3], n2[3];   /* their normals, out of the domain */
 };
+
+/* The step's ball keeps a clearance of 1e-3 eps from the Dirichlet part: any
+ * ball inside the domain gives an unbiased step, and the clearance keeps the
+ * walk's landing points, computed in FP32 on the GPU, on the domain's side of
+ * the boundary by more than rounding, which decides the orientation of the
+ * boundary normal where the walk ends (away from its last point). */
+static double step_radius(const oracle_scene* s, double d) { return d - 1e-3 * s->eps; }
 
 /* Algorithm 1 (WalkOnSpheres) with Russian roulette, iterated instead of
  * recursed.  acc collects the source estimates S of every step.  With
@@ -446,6 +455,7 @@ static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_
     PhaseResult res;
     res.x1[0] = res.x1[1] = res.x1[2] = NAN;
     res.ball_w = 0;
+    res.on = res.on2 = -1;
     double x[3] = {x0[0], x0[1], s->dim == 3 ? x0[2] : 0.0};
     double acc = 0;
     for (int k = 0;; ++k) {
@@ -463,13 +473,14 @@ static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_
             return res;
         }
         const bool ball = ball_n && k == 0;
+        const double R = step_radius(s, d);
         if (s->f != 0 && !ball) {
             Draws rb = draw(s->seed_lo, s->seed_hi, walk_id, (uint32_t)k, phase, 1);
             double rho = sample_ball_radius(s->dim, rb);
-            acc += oracle_source_weight(s->dim, s->sigma, d, rho) * s->f;
+            acc += oracle_source_weight(s->dim, s->sigma, R, rho) * s->f;
         }
         Draws r0 = draw(s->seed_lo, s->seed_hi, walk_id, (uint32_t)k, phase, 0);
-        double alpha = oracle_alpha(s->dim, s->sigma, d);
+        double alpha = oracle_alpha(s->dim, s->sigma, R);
         if (!ball && alpha < r0.u[2]) {
             res.u = acc;
             res.kind = KIND_ROULETTE;
@@ -481,11 +492,11 @@ static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_
         }
         double w[3];
         sample_sphere(s->dim, r0, w);
-        for (int i = 0; i < s->dim; ++i) x[i] += d * w[i];
+        for (int i = 0; i < s->dim; ++i) x[i] += R * w[i];
         if (ball) {
             double on = 0;
             for (int i = 0; i < s->dim; ++i) on += w[i] * ball_n[i];
-            res.ball_w = oracle_gradient_factor(s->dim, s->sigma, d) * on;
+            res.ball_w = oracle_gradient_factor(s->dim, s->sigma, R) * on;
         }
         if (k == 0) for (int i = 0; i < 3; ++i) res.x1[i] = i < s->dim ? x[i] : 0.0;
     }
@@ -503,7 +514,8 @@ static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_
  * Neumann part seen from x: a point where a ray from x grazes it (a vertex
  * whose two segments lie on the same side of the ray in 2D; an edge whose two
  * triangles lie on the same side of the plane through x and the edge in 3D)
- * or where it ends.  The radius is R = max(min(d_D, d_sil), eps).  A side
+ * or where it ends.  The radius is R = max(min(d_D - c, d_sil), eps - c)
+ * with the Dirichlet clearance c = 1e-3 eps of step_radius.  A side
  * test whose cross product (triple product in 3D) is within a relative 1e-4
  * of zero counts as collinear (coplanar): where the boundary runs straight on
  * through a vertex (or flat across an edge), seen from a point on its own line
@@ -511,10 +523,30 @@ static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_
  * the other turns away, it is one.  This keeps walks that sit on a flat
  * Neumann side from taking every vertex of that side as a silhouette.
  * A ray meets an element where its barycentric coordinates lie within 1e-5
- * of the element (so that no ray slips between two neighbours).  The offset
+ * of the element (so that no ray slips between two neighbours), except a
+ * neighbour of the side the walk sits on that lies behind that side's plane
+ * (behind_side): a ray from the side into the domain cannot reach it, and
+ * the tolerance would otherwise let a ray that grazes a reflex corner "hit"
+ * the far side at its end, from the wrong side.  A crossing up to a relative 1e-5 beyond the
+ * ray's length counts, at the ray's end: where the sphere of radius R meets
+ * the Neumann part (it passes through the silhouette point that bounds R) a
+ * direction that ends there lands on the boundary, and the walk must know.
+ * Likewise a move from the Neumann part that hits nothing and leaves it by at
+ * most 1e-4 eps along its normal (a direction nearly tangent to it) leaves the
+ * walk on that element.  A walk that hits an element while it is still on
+ * the side it left (within 1e-4 eps of it) sits on the edge (corner in 2D)
+ * of the two: until it leaves either, its rays skip both and its directions
+ * are turned into the wedge they bound (turn_inward).  Without this, a walk
+ * that rounding puts exactly on a convex edge would leave through the side it
+ * no longer tracks, from a start on that side's plane (a crossing at t = 0,
+ * which no ray test counts).  The offset
  * point xbar - h n of the differential walk is mirrored across the Neumann
  * part where the segment from xbar to it crosses that part (next to a
  * Dirichlet-Neumann junction): across a reflecting boundary u extends evenly.
+ * Where the main walk ended on the Neumann part and the offset point lies on
+ * the same side (within 1e-4 eps of its plane, as the move from the end point
+ * to the offset point is along it next to a right-angled junction), the
+ * nested walks start on that side (and edge), as the main walk would.
  * One step: a direction v uniform on the sphere (reflected into the inward
  * half-space when x lies on the Neumann part), the ray x + t v up to the first
  * Neumann hit within R; the walk moves to the hit point (and is then on the
@@ -646,13 +678,47 @@ static double silhouette_distance(const oracle_scene* s, const Adjacency& adj, c
     return best;
 }
 
-/* First crossing of the ray x + t v (0 < t < tmax) with a Neumann element other
- * than `skip`; returns t (INFINITY if none) and the element. */
-static double ray_neumann(const oracle_scene* s, const double* x, const double* v, double tmax, int skip, int* e_out) {
+/* True if elements e and f share a vertex. */
+static bool share_vertex(const oracle_scene* s, int e, int f) {
+    const int* a = s->elem + (size_t)s->dim * e;
+    const int* b = s->elem + (size_t)s->dim * f;
+    for (int i = 0; i < s->dim; ++i)
+        for (int j = 0; j < s->dim; ++j)
+            if (a[i] == b[j]) return true;
+    return false;
+}
+
+/* Element f lies behind side e (unit normal n_e, out of the domain): f
+ * shares a vertex with e and none of its vertices lies in front of e's line
+ * (plane), up to a relative 1e-6: (p - a) . n_e >= -1e-6 |p - a| for every
+ * vertex p of f, a e's first vertex.  Flat continuations of e and the far
+ * side of a reflex corner are behind it; a ray from e into the domain cannot
+ * reach them. */
+static bool behind_side(const oracle_scene* s, int e, const double* n_e, int f) {
+    if (!share_vertex(s, e, f)) return false;
+    const int d = s->dim;
+    const double* a = s->vert + (size_t)d * s->elem[(size_t)d * e];
+    for (int j = 0; j < d; ++j) {
+        const double* p = s->vert + (size_t)d * s->elem[(size_t)d * f + j];
+        double r[3] = {0, 0, 0};
+        for (int i = 0; i < d; ++i) r[i] = p[i] - a[i];
+        if (dot3(r, n_e) < -1e-6 * std::sqrt(dot3(r, r))) return false;
+    }
+    return true;
+}
+
+/* First crossing of the ray x + t v (0 < t < tmax (1 + 1e-5)) with a Neumann
+ * element other than `skip` and `skip2` (the sides the walk sits on, with
+ * their normals n_skip, n_skip2 out of the domain) and the elements behind
+ * them; returns min(t, tmax) (tmax if none) and the element (-1 if none). */
+static double ray_neumann(const oracle_scene* s, const double* x, const double* v, double tmax, int skip,
+                          const double* n_skip, int skip2, const double* n_skip2, int* e_out) {
     double best = INFINITY;
     *e_out = -1;
     for (int e = 0; e < s->n_elem; ++e) {
-        if (!s->neumann[e] || e == skip) continue;
+        if (!s->neumann[e] || e == skip || e == skip2) continue;
+        if ((skip >= 0 && behind_side(s, skip, n_skip, e)) || (skip2 >= 0 && behind_side(s, skip2, n_skip2, e)))
+            continue;
         const int* el = s->elem + (size_t)s->dim * e;
         double t;
         if (s->dim == 2) {
@@ -680,9 +746,9 @@ static double ray_neumann(const oracle_scene* s, const double* x, const double* 
             if (!(w >= -1e-5 && u + w <= 1 + 1e-5)) continue;
             t = dot3(e2, q) / det;
         }
-        if (t > 0 && t < tmax && t < best) { best = t; *e_out = e; }
+        if (t > 0 && t < tmax * (1 + 1e-5) && t < best) { best = t; *e_out = e; }
     }
-    return best;
+    return std::min(best, tmax);
 }
 
 /* Survival weight of a star step of length t inside the ball of radius R:
@@ -696,17 +762,50 @@ double oracle_star_weight(int dim, double sigma, double t, double R) {
     return (k * t * std::cosh(k * (R - t)) + std::sinh(k * (R - t))) / std::sinh(k * R);
 }
 
+/* A direction drawn at a point of the Neumann part is turned into the
+ * domain: into the inner half-space of the side the walk sits on (n_on, out
+ * of the domain) by v -> -v; at an edge, where the walk also lies on a second
+ * side (n2), by mirrors across the plane it still points out of, alternately,
+ * at most 4 (a ray in a wedge of interior angle a turns inward after at most
+ * ceil(pi / a) mirrors: any edge of 45 degrees or more).  At a right-angled
+ * edge this makes the direction uniform over the quarter-space. */
+static void turn_inward(double* v, int on, const double* n_on, int on2, const double* n2) {
+    if (on >= 0 && dot3(v, n_on) > 0) for (int i = 0; i < 3; ++i) v[i] = -v[i];
+    if (on2 < 0) return;
+    for (int m = 0; m < 4; ++m) {
+        const double* n = dot3(v, n2) > 0 ? n2 : dot3(v, n_on) > 0 ? n_on : NULL;
+        if (!n) return;
+        const double c = 2 * dot3(v, n);
+        for (int i = 0; i < 3; ++i) v[i] -= c * n[i];
+    }
+}
+
+/* turn_inward for the tests: n directions v (n x 3, in place) with the sides'
+ * normals n_on and n2 (n2 NULL: on one side only). */
+void oracle_turn_inward(int n, double* v, const double* n_on, const double* n2) {
+    for (int i = 0; i < n; ++i) turn_inward(v + 3 * (size_t)i, 0, n_on, n2 ? 0 : -1, n2 ? n2 : n_on);
+}
+
+/* Where a walk on stars starts: the Neumann side it sits on (-1: inside) and,
+ * on an edge, the second side, with their normals out of the domain. */
+struct StarStart {
+    int on = -1, on2 = -1;
+    double n_on[3] = {0, 0, 0}, n2[3] = {0, 0, 0};
+};
+
 static PhaseResult wost_walk(const oracle_scene* s, const Adjacency& adj, const double* x0, uint64_t walk_id,
-                             uint32_t phase, int on0, const double* n0) {
+                             uint32_t phase, const StarStart& st) {
     PhaseResult res;
     res.x1[0] = res.x1[1] = res.x1[2] = NAN;
     res.ball_w = 0;
     const int d = s->dim;
     double x[3] = {x0[0], x0[1], d == 3 ? x0[2] : 0.0};
     double acc = 0;
-    int on = on0;                      /* the Neumann element the walk sits on, -1 inside */
-    double n_on[3] = {0, 0, 0};        /* its normal, out of the domain */
-    if (on >= 0) for (int i = 0; i < 3; ++i) n_on[i] = n0[i];
+    int on = st.on;                    /* the Neumann element the walk sits on, -1 inside */
+    int on2 = st.on2;                  /* at an edge: the side it came from, still under it */
+    double n_on[3], n2[3];             /* their normals, out of the domain */
+    for (int i = 0; i < 3; ++i) { n_on[i] = st.n_on[i]; n2[i] = st.n2[i]; }
+    const double on_line = 1e-4 * s->eps;
     for (int k = 0;; ++k) {
         double xbar[3] = {0, 0, 0}, bary[2];
         int e;
@@ -719,26 +818,27 @@ static PhaseResult wost_walk(const oracle_scene* s, const Adjacency& adj, const 
             res.e = e;
             res.bary[0] = bary[0]; res.bary[1] = bary[1];
             for (int i = 0; i < 3; ++i) { res.xbar[i] = xbar[i]; res.x_last[i] = x[i]; }
+            res.on = on; res.on2 = on2;
+            for (int i = 0; i < 3; ++i) { res.n_on[i] = n_on[i]; res.n2[i] = n2[i]; }
             return res;
         }
-        const double R = std::max(std::min(dD, silhouette_distance(s, adj, x)), s->eps);
+        const double R = std::max(std::min(step_radius(s, dD), silhouette_distance(s, adj, x)), step_radius(s, s->eps));
         if (s->f != 0) {   /* source: a point of the ball, counted if x sees it */
             Draws rb = draw(s->seed_lo, s->seed_hi, walk_id, (uint32_t)k, phase, 1);
             double w[3];
             sample_sphere(d, rb, w);
-            if (on >= 0 && dot3(w, n_on) > 0) for (int i = 0; i < 3; ++i) w[i] = -w[i];
+            turn_inward(w, on, n_on, on2, n2);
             const double rho = sample_ball_radius(d, rb);
             int e2;
-            if (ray_neumann(s, x, w, rho * R, on, &e2) >= rho * R)
-                acc += oracle_source_weight(d, s->sigma, R, rho) * s->f;
+            ray_neumann(s, x, w, rho * R, on, n_on, on2, n2, &e2);
+            if (e2 < 0) acc += oracle_source_weight(d, s->sigma, R, rho) * s->f;
         }
         Draws r0 = draw(s->seed_lo, s->seed_hi, walk_id, (uint32_t)k, phase, 0);
         double v[3];
         sample_sphere(d, r0, v);
-        if (on >= 0 && dot3(v, n_on) > 0) for (int i = 0; i < 3; ++i) v[i] = -v[i];
+        turn_inward(v, on, n_on, on2, n2);
         int he;
-        const double th = ray_neumann(s, x, v, R, on, &he);
-        const double t = th < R ? th : R;
+        const double t = ray_neumann(s, x, v, R, on, n_on, on2, n2, &he);
         if (oracle_star_weight(d, s->sigma, t, R) < r0.u[2]) {
             res.u = acc;
             res.kind = KIND_ROULETTE;
@@ -746,15 +846,27 @@ static PhaseResult wost_walk(const oracle_scene* s, const Adjacency& adj, const 
             res.e = -1;
             res.bary[0] = res.bary[1] = 0;
             for (int i = 0; i < 3; ++i) { res.xbar[i] = 0; res.x_last[i] = x[i]; }
+            res.on = res.on2 = -1;
             return res;
         }
         for (int i = 0; i < d; ++i) x[i] += t * v[i];
-        if (th < R) {
+        /* a move that leaves a side by at most 1e-4 eps along its normal (a
+         * direction nearly tangent to it) leaves the walk on that side */
+        const bool keep = on >= 0 && std::fabs(t * dot3(v, n_on)) <= on_line;
+        const bool keep2 = on2 >= 0 && std::fabs(t * dot3(v, n2)) <= on_line;
+        if (he >= 0) {   /* on the element hit; on an edge if still on the side it left */
+            if (keep) { on2 = on; for (int i = 0; i < 3; ++i) n2[i] = n_on[i]; } else on2 = -1;
             on = he;
             element_normal(s, he, n_on);
             if (dot3(n_on, v) < 0) for (int i = 0; i < 3; ++i) n_on[i] = -n_on[i];
+        } else if (keep) {
+            if (!keep2) on2 = -1;
+        } else if (keep2) {
+            on = on2;
+            for (int i = 0; i < 3; ++i) n_on[i] = n2[i];
+            on2 = -1;
         } else {
-            on = -1;
+            on = on2 = -1;
         }
         if (k == 0) for (int i = 0; i < 3; ++i) res.x1[i] = i < d ? x[i] : 0.0;
     }
@@ -805,13 +917,15 @@ static int neumann_start(const oracle_scene* s, const double* x0, double* n_out)
 }
 
 /* One phase of a walk: walk on spheres, or walk on stars with a Neumann part
- * (the main walk of a query point on the Neumann part starts on it). */
+ * (the main walk of a query point on the Neumann part starts on it; a nested
+ * walk starts where `nested` says). */
 static PhaseResult phase_walk(const oracle_scene* s, const Adjacency* adj, const double* x0, uint64_t walk_id,
-                              uint32_t phase, const double* ball_n) {
+                              uint32_t phase, const double* ball_n, const StarStart* nested = NULL) {
     if (s->neumann) {
-        double n0[3] = {0, 0, 0};
-        const int on0 = phase == 0 ? neumann_start(s, x0, n0) : -1;
-        return wost_walk(s, *adj, x0, walk_id, phase, on0, n0);
+        StarStart st;
+        if (phase == 0) st.on = neumann_start(s, x0, st.n_on);
+        else if (nested) st = *nested;
+        return wost_walk(s, *adj, x0, walk_id, phase, st);
     }
     return forward_walk(s, x0, walk_id, phase, ball_n);
 }
@@ -878,7 +992,7 @@ static void run_one(const oracle_scene* s, const Adjacency* adj, const double* x
     if (s->neumann) {   /* mirrored across the Neumann part where the offset crosses it */
         double back[3] = {-n[0], -n[1], -n[2]};
         int he;
-        const double th = ray_neumann(s, main.xbar, back, s->h, -1, &he);
+        const double th = ray_neumann(s, main.xbar, back, s->h, -1, NULL, -1, NULL, &he);
         if (he >= 0) {
             double m[3];
             element_normal(s, he, m);
@@ -887,10 +1001,28 @@ static void run_one(const oracle_scene* s, const Adjacency* adj, const double* x
             for (int i = 0; i < s->dim; ++i) xoff[i] = c[i] + r[i] - 2 * rm * m[i];
         }
     }
+    /* the nested walks start on the Neumann side(s) the main walk ended on where
+     * the offset point lies on it (within 1e-4 eps of its plane) */
+    StarStart nst;
+    if (s->neumann) {
+        double r[3] = {0, 0, 0};
+        for (int i = 0; i < s->dim; ++i) r[i] = xoff[i] - main.x_last[i];
+        const double on_line = 1e-4 * s->eps;
+        const bool k1 = main.on >= 0 && std::fabs(dot3(r, main.n_on)) <= on_line;
+        const bool k2 = main.on2 >= 0 && std::fabs(dot3(r, main.n2)) <= on_line;
+        if (k1) {
+            nst.on = main.on;
+            for (int i = 0; i < 3; ++i) nst.n_on[i] = main.n_on[i];
+            if (k2) { nst.on2 = main.on2; for (int i = 0; i < 3; ++i) nst.n2[i] = main.n2[i]; }
+        } else if (k2) {
+            nst.on = main.on2;
+            for (int i = 0; i < 3; ++i) nst.n_on[i] = main.n2[i];
+        }
+    }
     double sum = 0, sum_plain = 0, sum_dn = 0, sum_dt = 0, sum_ball = 0;
     const double* q_cv = s->cv_elem ? s->cv_elem + 4 * (size_t)main.e : NULL;
     for (int j = 1; j <= s->K; ++j) {
-        PhaseResult nr = phase_walk(s, adj, xoff, walk_id, (uint32_t)j, s->dudn_mode == 1 ? n : NULL);
+        PhaseResult nr = phase_walk(s, adj, xoff, walk_id, (uint32_t)j, s->dudn_mode == 1 ? n : NULL, &nst);
         /* control variate: (q n + t) . (x_end - x_off) has mean zero */
         double disp = 0, dn = 0, dt = 0;
         for (int i = 0; i < s->dim; ++i) dn += n[i] * (nr.x_last[i] - xoff[i]);

@@ -158,8 +158,11 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
     }
     int on_e = -1;                  // STAR: the Neumann element the walk sits on (compact), -1 inside
     float n_on[DIM];                // STAR: its normal, out of the domain
+    int on2 = -1;                   // STAR: at an edge, the side it came from and still lies on
+    float n2[DIM];                  // STAR: that side's normal, out of the domain
+    int nst1 = -1, nst2 = -1;       // STAR: the sides the nested walks start on, 2 e + (normal flipped)
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) n_on[k] = 0.0f;
+    for (int k = 0; k < DIM; ++k) { n_on[k] = 0.0f; n2[k] = 0.0f; }
 
     const int lane = threadIdx.x & 31;
     bool active = false, exhausted = false;
@@ -209,6 +212,7 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
                     } else {
                         phase = 0; step = 0; hint = -1; acc = 0.0f;
                         on_e = -1;
+                        on2 = -1;
                         if constexpr (STAR) {   // a query point on the Neumann part starts on it
                             if (NS.q_start) {
                                 const float4 qs = NS.q_start[point];
@@ -312,36 +316,25 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
             const unsigned long long wid = P.walk_id_base + local;
             bool ok1 = true, ok2 = true, ok3 = true;
             const float sd2 = silhouette_dist2<DIM>(NS, x, best2, ok1);
-            const float R = fmaxf(sqrtf(sd2), P.eps);
+            // R = max(min(d_D - c, d_sil), eps - c), c = 1e-3 eps the Dirichlet clearance
+            const float R = fmaxf(fminf(sqrtf(sd2), fmaf(-1e-3f, P.eps, d)), fmaf(-1e-3f, P.eps, P.eps));
             if (P.f != 0.0f) {   // source: a point of the ball, counted if x sees it
                 const U4 r1 = draw_block(P.seed_lo, P.seed_hi, wid, k_step, (uint32_t)phase, 1u);
                 float w[3];
                 sphere_dir<DIM>(r1, w);
-                float wn = 0.0f;
-#pragma unroll
-                for (int k = 0; k < DIM; ++k) wn = fmaf(w[k], n_on[k], wn);
-                if (on_e >= 0 && wn > 0.0f) {
-#pragma unroll
-                    for (int k = 0; k < DIM; ++k) w[k] = -w[k];
-                }
+                turn_inward<DIM>(w, on_e, n_on, on2, n2);
                 const float ub = u01(r1.z);
                 const float rr = R * (DIM == 2 ? sqrtf(ub) : cbrtf(ub));
                 int h2;
-                ray_neumann<DIM>(NS, x, w, rr, on_e, h2, ok2);
+                ray_neumann<DIM>(NS, x, w, rr, on_e, n_on, on2, n2, h2, ok2);
                 if (h2 < 0) acc = fmaf(source_weight<DIM>(P.sqrt_sigma, R, ub), P.f, acc);
             }
             const U4 r0 = draw_block(P.seed_lo, P.seed_hi, wid, k_step, (uint32_t)phase, 0u);
             float om[3];
             sphere_dir<DIM>(r0, om);
-            float vn = 0.0f;
-#pragma unroll
-            for (int k = 0; k < DIM; ++k) vn = fmaf(om[k], n_on[k], vn);
-            if (on_e >= 0 && vn > 0.0f) {   // on the Neumann part: the inward half-space
-#pragma unroll
-                for (int k = 0; k < DIM; ++k) om[k] = -om[k];
-            }
+            turn_inward<DIM>(om, on_e, n_on, on2, n2);   // on the Neumann part: into the domain
             int hit;
-            const float th = ray_neumann<DIM>(NS, x, om, R, on_e, hit, ok3);
+            const float th = ray_neumann<DIM>(NS, x, om, R, on_e, n_on, on2, n2, hit, ok3);
             if (!(ok1 && ok2 && ok3)) error |= 1;
             const float t = hit >= 0 ? th : R;
             if (P.sqrt_sigma > 0.0f && star_weight<DIM>(P.sqrt_sigma, t, R) < u01(r0.z)) {
@@ -349,7 +342,19 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
             } else {
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) x[k] = fmaf(t, om[k], x[k]);
-                if (hit >= 0) {   // on the Neumann part: its normal, oriented along the ray (out of the domain)
+                // a move that leaves a side by at most 1e-4 eps along its normal (a direction
+                // nearly tangent to it) leaves the walk on that side
+                float s1 = 0.0f, s2 = 0.0f;
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) { s1 = fmaf(om[k], n_on[k], s1); s2 = fmaf(om[k], n2[k], s2); }
+                const bool keep = on_e >= 0 && fabsf(t * s1) <= 1e-4f * P.eps;
+                const bool keep2 = on2 >= 0 && fabsf(t * s2) <= 1e-4f * P.eps;
+                if (hit >= 0) {
+                    // on the element hit, and on an edge if still on the side it left; the hit
+                    // element's normal, oriented along the ray (out of the domain)
+                    on2 = keep ? on_e : -1;
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) n2[k] = n_on[k];
                     neumann_normal<DIM>(NS, hit, n_on);
                     float s = 0.0f;
 #pragma unroll
@@ -358,8 +363,18 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
 #pragma unroll
                         for (int k = 0; k < DIM; ++k) n_on[k] = -n_on[k];
                     }
+                    on_e = hit;
+                } else if (keep) {
+                    if (!keep2) on2 = -1;
+                } else if (keep2) {
+                    on_e = on2;
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) n_on[k] = n2[k];
+                    on2 = -1;
+                } else {
+                    on_e = -1;
+                    on2 = -1;
                 }
-                on_e = hit;
                 hint = best;
                 continue;
             }
@@ -368,14 +383,17 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
             // ball-gradient estimator: a nested walk's first move samples y on the sphere
             // about the offset point (no source, no roulette) and weighs the estimate at y
             const bool ball = P.dudn_mode == 1 && phase > 0 && k_step == 0;
+            // the ball keeps a clearance of 1e-3 eps from the boundary: the landing point stays on
+            // the domain's side by more than FP32 rounding (any ball inside the domain is a valid step)
+            const float rs = fmaf(-1e-3f, P.eps, d);
             if (P.f != 0.0f && !ball) {   // source estimate of this ball (Algorithm 1, S-hat)
                 const U4 r1 = draw_block(P.seed_lo, P.seed_hi, wid, k_step, (uint32_t)phase, 1u);
-                acc = fmaf(source_weight<DIM>(P.sqrt_sigma, d, u01(r1.z)), P.f, acc);
+                acc = fmaf(source_weight<DIM>(P.sqrt_sigma, rs, u01(r1.z)), P.f, acc);
             }
             const U4 r0 = draw_block(P.seed_lo, P.seed_hi, wid, k_step, (uint32_t)phase, 0u);
-            if (!ball && roulette_stops<DIM>(P.sqrt_sigma, d, u01(r0.z))) {
+            if (!ball && roulette_stops<DIM>(P.sqrt_sigma, rs, u01(r0.z))) {
                 kind = DWOS_KIND_ROULETTE;
-            } else {   // next point on the sphere of radius d
+            } else {   // next point on the sphere of radius rs
                 float om[3];
                 if (DIM == 2) {
                     float s, c;
@@ -390,12 +408,12 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
                     om[0] = sth * c; om[1] = sth * s; om[2] = z;
                 }
 #pragma unroll
-                for (int k = 0; k < DIM; ++k) x[k] = fmaf(d, om[k], x[k]);
+                for (int k = 0; k < DIM; ++k) x[k] = fmaf(rs, om[k], x[k]);
                 if (ball) {
                     float on = 0.0f;
 #pragma unroll
                     for (int k = 0; k < DIM; ++k) on = fmaf(om[k], S.nrm[k], on);
-                    S.w_ball = gradient_factor<DIM>(P.sqrt_sigma, d) * on;
+                    S.w_ball = gradient_factor<DIM>(P.sqrt_sigma, rs) * on;
                 }
                 hint = best;
                 if (phase == 0 && k_step == 0 && P.cv_sample)   // first step of the main walk
@@ -491,7 +509,7 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
                 float back[3] = {-S.nrm[0], -S.nrm[1], DIM == 3 ? -S.nrm[DIM - 1] : 0.0f};
                 int he;
                 bool okr = true;
-                const float th = ray_neumann<DIM>(NS, xbar, back, P.h, -1, he, okr);
+                const float th = ray_neumann<DIM>(NS, xbar, back, P.h, -1, back, -1, back, he, okr);
                 if (!okr) error |= 1;
                 if (he >= 0) {
                     float m[3];
@@ -506,6 +524,25 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
 #pragma unroll
                     for (int k = 0; k < DIM; ++k) S.xoff[k] = c[k] + fmaf(-2.0f * rm, m[k], r[k]);
                 }
+                // the nested walks start on the Neumann side(s) the main walk ended on where the
+                // offset point lies on it (within 1e-4 eps of its plane)
+                float r1 = 0.0f, r2 = 0.0f;
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) {
+                    r1 = fmaf(S.xoff[k] - x[k], n_on[k], r1);
+                    r2 = fmaf(S.xoff[k] - x[k], n2[k], r2);
+                }
+                const bool k1 = on_e >= 0 && fabsf(r1) <= 1e-4f * P.eps;
+                const bool k2 = on2 >= 0 && fabsf(r2) <= 1e-4f * P.eps;
+                auto code = [&](int e2, const float* n) {
+                    float m[3] = {0.0f, 0.0f, 0.0f}, sg = 0.0f;
+                    neumann_normal<DIM>(NS, e2, m);
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) sg = fmaf(m[k], n[k], sg);
+                    return 2 * e2 + (sg < 0.0f ? 1 : 0);
+                };
+                nst1 = k1 ? code(on_e, n_on) : (k2 ? code(on2, n2) : -1);
+                nst2 = k1 && k2 ? code(on2, n2) : -1;
             }
             S.g_main = g; S.b1 = w1; S.b2 = w2; S.leaf_main = best; S.e_main = e;
             S.sum_plain = 0.0f; S.sum_dn = 0.0f; S.sum_dt = 0.0f; S.sum_ball = 0.0f; S.w_ball = 0.0f;
@@ -564,6 +601,25 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
         step = 0;
         acc = 0.0f;
         on_e = -1;
+        on2 = -1;
+        if constexpr (STAR) {   // on the side(s) the main walk ended on, where the offset point lies on them
+            if (nst1 >= 0) {
+                on_e = nst1 >> 1;
+                neumann_normal<DIM>(NS, on_e, n_on);
+                if (nst1 & 1) {
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) n_on[k] = -n_on[k];
+                }
+            }
+            if (nst2 >= 0) {
+                on2 = nst2 >> 1;
+                neumann_normal<DIM>(NS, on2, n2);
+                if (nst2 & 1) {
+#pragma unroll
+                    for (int k = 0; k < DIM; ++k) n2[k] = -n2[k];
+                }
+            }
+        }
         hint = S.leaf_main;
 #pragma unroll
         for (int k = 0; k < DIM; ++k) x[k] = S.xoff[k];

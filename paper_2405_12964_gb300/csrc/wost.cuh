@@ -162,13 +162,82 @@ __device__ __forceinline__ float ray_box_entry(const float* x, const float* inv,
     return t0 <= t1 ? t0 : kInf;
 }
 
+// Unit normal (up to orientation) of Neumann element e.
+template <int DIM>
+__device__ __forceinline__ void neumann_normal(const DevNeumann& N, int e, float* m) {
+    const int* ev = N.elem + (size_t)DIM * e;
+    float a[DIM], b[DIM];
+    vload<DIM>(N.vert, __ldg(ev), a);
+    vload<DIM>(N.vert, __ldg(ev + 1), b);
+    if (DIM == 2) {
+        m[0] = b[1] - a[1];
+        m[1] = a[0] - b[0];
+    } else {
+        float c[DIM];
+        vload<DIM>(N.vert, __ldg(ev + 2), c);
+        const float e1[3] = {b[0] - a[0], b[1] - a[1], b[DIM - 1] - a[DIM - 1]};
+        const float e2[3] = {c[0] - a[0], c[1] - a[1], c[DIM - 1] - a[DIM - 1]};
+        m[0] = e1[1] * e2[2] - e1[2] * e2[1];
+        m[1] = e1[2] * e2[0] - e1[0] * e2[2];
+        m[DIM - 1] = e1[0] * e2[1] - e1[1] * e2[0];
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) s = fmaf(m[k], m[k], s);
+    s = rsqrtf(s);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) m[k] *= s;
+}
+
+// True if Neumann element f (compact numbering) lies behind side e (ne: e's
+// unit normal, out of the domain): f shares a vertex with e and none of its
+// vertices p lies in front of e's line (plane) by more than a relative 1e-6,
+// (p - a) . ne >= -1e-6 |p - a| with a e's first vertex.  Flat continuations
+// of e and the far side of a reflex corner are behind e: a ray from e into
+// the domain cannot reach them.
+template <int DIM>
+__device__ __forceinline__ bool behind_side(const DevNeumann& N, int e, const float* ne, int f) {
+    int ev[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) ev[j] = __ldg(N.elem + (size_t)DIM * e + j);
+    bool shared = false;
+    int fv[DIM];
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        fv[k] = __ldg(N.elem + (size_t)DIM * f + k);
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) shared = shared || fv[k] == ev[j];
+    }
+    if (!shared) return false;
+    float a[DIM];
+    vload<DIM>(N.vert, ev[0], a);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) {
+        float p[DIM], dn = 0.0f, r2 = 0.0f;
+        vload<DIM>(N.vert, fv[k], p);
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) {
+            const float r = p[i] - a[i];
+            dn = fmaf(r, ne[i], dn);
+            r2 = fmaf(r, r, r2);
+        }
+        if (dn < -1e-6f * sqrtf(r2)) return false;
+    }
+    return true;
+}
+
 // First crossing of the ray x + t v (0 < t < tmax) with a Neumann element
-// other than `skip` (compact numbering): returns t (tmax if none) and the
-// element in hit (-1 if none).
+// other than `skip` and `skip2` (compact numbering; the sides the walk sits
+// on, -1 for none, with their unit normals n_skip, n_skip2 out of the domain)
+// and the elements behind them (behind_side): returns t (tmax if none) and
+// the element in hit (-1 if none).  A crossing up to a relative 1e-5 beyond
+// tmax counts, at tmax: where the sphere of radius tmax meets the Neumann
+// part, a direction that ends there lands on the boundary, and rounding must
+// not leave the walk unaware of it.
 template <int DIM>
 __device__ __forceinline__ float ray_neumann(const DevNeumann& N, const float* x, const float* v, float tmax, int skip,
-                                             int& hit, bool& ok) {
-    float best = tmax;
+                                             const float* n_skip, int skip2, const float* n_skip2, int& hit, bool& ok) {
+    float best = tmax * (1.0f + 1e-5f);
     hit = -1;
     float inv[DIM];
 #pragma unroll
@@ -176,7 +245,9 @@ __device__ __forceinline__ float ray_neumann(const DevNeumann& N, const float* x
     auto key = [&](const float* lo, const float* hi) { return ray_box_entry<DIM>(x, inv, lo, hi); };
     auto leaf = [&](int l) {
         const int e = __ldg(N.prim_elem + l);
-        if (e == skip) return;
+        if (e == skip || e == skip2) return;
+        if ((skip >= 0 && behind_side<DIM>(N, skip, n_skip, e)) || (skip2 >= 0 && behind_side<DIM>(N, skip2, n_skip2, e)))
+            return;
         float t;
         if (DIM == 2) {
             const float4 s = __ldg(N.prims + l);
@@ -204,34 +275,37 @@ __device__ __forceinline__ float ray_neumann(const DevNeumann& N, const float* x
         if (t > 0.0f && t < best) { best = t; hit = e; }
     };
     ok = bvh_best_first<DIM>(N.nodes, N.n_internal, N.n_tree, N.n_big, best, key, leaf);
-    return best;
+    return fminf(best, tmax);
 }
 
-// Unit normal (up to orientation) of Neumann element e.
+
+// A direction drawn at a point of the Neumann part, turned into the domain:
+// into the inner half-space of the side the walk sits on (n_on, out of the
+// domain) by v -> -v; at an edge (corner in 2D), where the walk also lies on
+// a second side (n2), by mirrors across the plane it still points out of,
+// alternately, at most 4 (a ray in a wedge of interior angle a turns inward
+// after at most ceil(pi / a) mirrors: any edge of 45 degrees or more).  At a
+// right-angled edge the direction is then uniform over the quarter-space.
 template <int DIM>
-__device__ __forceinline__ void neumann_normal(const DevNeumann& N, int e, float* m) {
-    const int* ev = N.elem + (size_t)DIM * e;
-    float a[DIM], b[DIM];
-    vload<DIM>(N.vert, __ldg(ev), a);
-    vload<DIM>(N.vert, __ldg(ev + 1), b);
-    if (DIM == 2) {
-        m[0] = b[1] - a[1];
-        m[1] = a[0] - b[0];
-    } else {
-        float c[DIM];
-        vload<DIM>(N.vert, __ldg(ev + 2), c);
-        const float e1[3] = {b[0] - a[0], b[1] - a[1], b[DIM - 1] - a[DIM - 1]};
-        const float e2[3] = {c[0] - a[0], c[1] - a[1], c[DIM - 1] - a[DIM - 1]};
-        m[0] = e1[1] * e2[2] - e1[2] * e2[1];
-        m[1] = e1[2] * e2[0] - e1[0] * e2[2];
-        m[DIM - 1] = e1[0] * e2[1] - e1[1] * e2[0];
-    }
+__device__ __forceinline__ void turn_inward(float* v, int on, const float* n_on, int on2, const float* n2) {
     float s = 0.0f;
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) s = fmaf(m[k], m[k], s);
-    s = rsqrtf(s);
+    for (int k = 0; k < DIM; ++k) s = fmaf(v[k], n_on[k], s);
+    if (on >= 0 && s > 0.0f) {
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) m[k] *= s;
+        for (int k = 0; k < DIM; ++k) v[k] = -v[k];
+    }
+    if (on2 < 0) return;
+    for (int m = 0; m < 4; ++m) {
+        float a = 0.0f, b = 0.0f;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) { a = fmaf(v[k], n2[k], a); b = fmaf(v[k], n_on[k], b); }
+        const bool out2 = a > 0.0f;
+        if (!out2 && !(b > 0.0f)) return;
+        const float c = 2.0f * (out2 ? a : b);
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) v[k] = fmaf(-c, out2 ? n2[k] : n_on[k], v[k]);
+    }
 }
 
 // Survival weight of a star step of length t in the ball of radius R:

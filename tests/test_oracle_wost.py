@@ -164,3 +164,43 @@ def test_query_points_on_the_neumann_part(name):
         assert np.all(np.abs(x1[:, 1]) <= 0.5 + tol)
     else:
         assert np.all(np.abs(x1) <= 1 + tol)
+
+
+def test_directions_at_an_edge_of_the_neumann_part():
+    # A direction drawn on the Neumann part is turned into the domain.  On one side:
+    # v -> -v where it points out (the inner half-sphere, uniform).  On an edge of two
+    # sides: also mirrored into the wedge they bound; at a right angle that folds the
+    # uniform sphere onto the uniform quarter-sphere (each fold is a symmetry of the
+    # uniform distribution), so the moments are those of |v_i| with E|v_i| = 1/2 in 3D
+    # (2/pi on the circle) and E v_i^2 = 1/d.
+    rng = np.random.default_rng(7)
+    n = 200_000
+    v = rng.normal(size=(n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    se = 4.0 / np.sqrt(n)
+    one = oracle.turn_inward(v, [0.0, 0.0, 1.0])
+    assert np.all(one[:, 2] <= 0)
+    flip = v[:, 2] > 0
+    assert np.array_equal(one[flip], -v[flip]) and np.array_equal(one[~flip], v[~flip])
+    # the edge of the cube's faces y = -1 and z = 1 (outward normals -e_y, +e_z)
+    q = oracle.turn_inward(v, [0.0, -1.0, 0.0], [0.0, 0.0, 1.0])
+    assert np.all(q[:, 1] >= 0) and np.all(q[:, 2] <= 0)
+    assert np.allclose(np.linalg.norm(q, axis=1), 1.0, atol=1e-14)
+    np.testing.assert_allclose(q.mean(0), [0.0, 0.5, -0.5], atol=se)
+    np.testing.assert_allclose((q * q).mean(0), [1 / 3] * 3, atol=se)
+    np.testing.assert_allclose((q[:, 0] * q[:, 1]).mean(), 0.0, atol=se)
+    # the same edge with the sides the other way round: the same quarter-sphere
+    q2 = oracle.turn_inward(v, [0.0, 0.0, 1.0], [0.0, -1.0, 0.0])
+    assert np.all(q2[:, 1] >= 0) and np.all(q2[:, 2] <= 0)
+    np.testing.assert_allclose(q2.mean(0), [0.0, 0.5, -0.5], atol=se)
+    # a right-angled corner in 2D (the slab's corners): the uniform quarter-circle
+    phi = rng.uniform(0, 2 * np.pi, n)
+    c = np.stack([np.cos(phi), np.sin(phi), 0 * phi], 1)
+    c2 = oracle.turn_inward(c, [1.0, 0.0, 0.0], [0.0, 1.0, 0.0])
+    assert np.all(c2[:, :2] <= 0) and np.all(c2[:, 2] == 0)
+    np.testing.assert_allclose(c2[:, :2].mean(0), [-2 / np.pi] * 2, atol=se)
+    # a wedge of 60 degrees (y >= 0 and polar angle <= 60 deg): every direction ends inside
+    a = np.pi / 3
+    n_a = np.array([-np.sin(a), np.cos(a), 0.0])
+    w = oracle.turn_inward(v, [0.0, -1.0, 0.0], n_a)
+    assert np.all(w[:, 1] >= -1e-12) and np.all(w @ n_a <= 1e-12)
