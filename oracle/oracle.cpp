@@ -527,8 +527,12 @@ static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_
  * neighbour of the side the walk sits on that lies behind that side's plane
  * (behind_side): a ray from the side into the domain cannot reach it, and
  * the tolerance would otherwise let a ray that grazes a reflex corner "hit"
- * the far side at its end, from the wrong side.  A crossing up to a relative 1e-5 beyond the
- * ray's length counts, at the ray's end: where the sphere of radius R meets
+ * the far side at its end, from the wrong side.  Nor does a ray from the side
+ * cross an element on the side's own line (plane) through the walk's point
+ * (coplanar_side): a direction nearly along the line would meet it at an
+ * arbitrary t and take its normal's orientation from rounding.  A crossing up
+ * to a relative 1e-5 plus 1e-4 eps beyond the ray's length counts, at the
+ * ray's end: where the sphere of radius R meets
  * the Neumann part (it passes through the silhouette point that bounds R) a
  * direction that ends there lands on the boundary, and the walk must know.
  * Likewise a move from the Neumann part that hits nothing and leaves it by at
@@ -707,18 +711,37 @@ static bool behind_side(const oracle_scene* s, int e, const double* n_e, int f) 
     return true;
 }
 
-/* First crossing of the ray x + t v (0 < t < tmax (1 + 1e-5)) with a Neumann
- * element other than `skip` and `skip2` (the sides the walk sits on, with
- * their normals n_skip, n_skip2 out of the domain) and the elements behind
- * them; returns min(t, tmax) (tmax if none) and the element (-1 if none). */
+/* Element f lies on the line (plane) of side e (unit normal n_e) through x:
+ * their normals are parallel within a relative 1e-6 and f's line (plane)
+ * passes within 1e-4 eps of x.  A ray from x does not cross it, whatever
+ * rounding makes of t (a direction nearly along the line meets f's line at
+ * an arbitrary t). */
+static bool coplanar_side(const oracle_scene* s, const double* x, const double* n_e, int f) {
+    double m[3];
+    element_normal(s, f, m);
+    if (std::fabs(dot3(m, n_e)) < 1 - 1e-6) return false;
+    const double* a = s->vert + (size_t)s->dim * s->elem[(size_t)s->dim * f];
+    double r[3] = {0, 0, 0};
+    for (int i = 0; i < s->dim; ++i) r[i] = x[i] - a[i];
+    return std::fabs(dot3(r, m)) <= 1e-4 * s->eps;
+}
+
+/* A ray from the side e (the walk sits on it) does not hit f. */
+static bool skipped_from(const oracle_scene* s, const double* x, int e, const double* n_e, int f) {
+    return e >= 0 && (behind_side(s, e, n_e, f) || coplanar_side(s, x, n_e, f));
+}
+
+/* First crossing of the ray x + t v (0 < t < tmax (1 + 1e-5) + slack) with a
+ * Neumann element other than `skip` and `skip2` (the sides the walk sits on,
+ * with their normals n_skip, n_skip2 out of the domain), the elements behind
+ * them and those on their lines (planes) through x; returns min(t, tmax)
+ * (tmax if none) and the element (-1 if none). */
 static double ray_neumann(const oracle_scene* s, const double* x, const double* v, double tmax, int skip,
-                          const double* n_skip, int skip2, const double* n_skip2, int* e_out) {
+                          const double* n_skip, int skip2, const double* n_skip2, double slack, int* e_out) {
     double best = INFINITY;
     *e_out = -1;
     for (int e = 0; e < s->n_elem; ++e) {
         if (!s->neumann[e] || e == skip || e == skip2) continue;
-        if ((skip >= 0 && behind_side(s, skip, n_skip, e)) || (skip2 >= 0 && behind_side(s, skip2, n_skip2, e)))
-            continue;
         const int* el = s->elem + (size_t)s->dim * e;
         double t;
         if (s->dim == 2) {
@@ -746,7 +769,10 @@ static double ray_neumann(const oracle_scene* s, const double* x, const double* 
             if (!(w >= -1e-5 && u + w <= 1 + 1e-5)) continue;
             t = dot3(e2, q) / det;
         }
-        if (t > 0 && t < tmax * (1 + 1e-5) && t < best) { best = t; *e_out = e; }
+        if (!(t > 0 && t < tmax * (1 + 1e-5) + slack && t < best)) continue;
+        if (skipped_from(s, x, skip, n_skip, e) || skipped_from(s, x, skip2, n_skip2, e)) continue;
+        best = t;
+        *e_out = e;
     }
     return std::min(best, tmax);
 }
@@ -830,7 +856,7 @@ static PhaseResult wost_walk(const oracle_scene* s, const Adjacency& adj, const 
             turn_inward(w, on, n_on, on2, n2);
             const double rho = sample_ball_radius(d, rb);
             int e2;
-            ray_neumann(s, x, w, rho * R, on, n_on, on2, n2, &e2);
+            ray_neumann(s, x, w, rho * R, on, n_on, on2, n2, on_line, &e2);
             if (e2 < 0) acc += oracle_source_weight(d, s->sigma, R, rho) * s->f;
         }
         Draws r0 = draw(s->seed_lo, s->seed_hi, walk_id, (uint32_t)k, phase, 0);
@@ -838,7 +864,7 @@ static PhaseResult wost_walk(const oracle_scene* s, const Adjacency& adj, const 
         sample_sphere(d, r0, v);
         turn_inward(v, on, n_on, on2, n2);
         int he;
-        const double t = ray_neumann(s, x, v, R, on, n_on, on2, n2, &he);
+        const double t = ray_neumann(s, x, v, R, on, n_on, on2, n2, on_line, &he);
         if (oracle_star_weight(d, s->sigma, t, R) < r0.u[2]) {
             res.u = acc;
             res.kind = KIND_ROULETTE;
@@ -992,7 +1018,7 @@ static void run_one(const oracle_scene* s, const Adjacency* adj, const double* x
     if (s->neumann) {   /* mirrored across the Neumann part where the offset crosses it */
         double back[3] = {-n[0], -n[1], -n[2]};
         int he;
-        const double th = ray_neumann(s, main.xbar, back, s->h, -1, NULL, -1, NULL, &he);
+        const double th = ray_neumann(s, main.xbar, back, s->h, -1, NULL, -1, NULL, 0.0, &he);
         if (he >= 0) {
             double m[3];
             element_normal(s, he, m);

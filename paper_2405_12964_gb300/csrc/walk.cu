@@ -326,7 +326,7 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
                 const float ub = u01(r1.z);
                 const float rr = R * (DIM == 2 ? sqrtf(ub) : cbrtf(ub));
                 int h2;
-                ray_neumann<DIM>(NS, x, w, rr, on_e, n_on, on2, n2, h2, ok2);
+                ray_neumann<DIM>(NS, x, w, rr, on_e, n_on, on2, n2, 1e-4f * P.eps, h2, ok2);
                 if (h2 < 0) acc = fmaf(source_weight<DIM>(P.sqrt_sigma, R, ub), P.f, acc);
             }
             const U4 r0 = draw_block(P.seed_lo, P.seed_hi, wid, k_step, (uint32_t)phase, 0u);
@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
             sphere_dir<DIM>(r0, om);
             turn_inward<DIM>(om, on_e, n_on, on2, n2);   // on the Neumann part: into the domain
             int hit;
-            const float th = ray_neumann<DIM>(NS, x, om, R, on_e, n_on, on2, n2, hit, ok3);
+            const float th = ray_neumann<DIM>(NS, x, om, R, on_e, n_on, on2, n2, 1e-4f * P.eps, hit, ok3);
             if (!(ok1 && ok2 && ok3)) error |= 1;
             const float t = hit >= 0 ? th : R;
             if (P.sqrt_sigma > 0.0f && star_weight<DIM>(P.sqrt_sigma, t, R) < u01(r0.z)) {
@@ -509,7 +509,7 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
                 float back[3] = {-S.nrm[0], -S.nrm[1], DIM == 3 ? -S.nrm[DIM - 1] : 0.0f};
                 int he;
                 bool okr = true;
-                const float th = ray_neumann<DIM>(NS, xbar, back, P.h, -1, back, -1, back, he, okr);
+                const float th = ray_neumann<DIM>(NS, xbar, back, P.h, -1, back, -1, back, 0.0f, he, okr);
                 if (!okr) error |= 1;
                 if (he >= 0) {
                     float m[3];

@@ -226,18 +226,42 @@ __device__ __forceinline__ bool behind_side(const DevNeumann& N, int e, const fl
     return true;
 }
 
+// True if Neumann element f lies on the line (plane) of side e through x
+// (ne: e's unit normal): their normals are parallel within a relative 1e-6
+// and f's line (plane) passes within on_line of x.  A ray from x does not
+// cross it, whatever rounding makes of t (a direction nearly along the line
+// meets f's line at an arbitrary t).
+template <int DIM>
+__device__ __forceinline__ bool coplanar_side(const DevNeumann& N, const float* x, const float* ne, int f,
+                                              float on_line) {
+    float m[3] = {0.0f, 0.0f, 0.0f};
+    neumann_normal<DIM>(N, f, m);
+    float c = 0.0f;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) c = fmaf(m[k], ne[k], c);
+    if (fabsf(c) < 1.0f - 1e-6f) return false;
+    float a[DIM], r = 0.0f;
+    vload<DIM>(N.vert, __ldg(N.elem + (size_t)DIM * f), a);
+#pragma unroll
+    for (int k = 0; k < DIM; ++k) r = fmaf(x[k] - a[k], m[k], r);
+    return fabsf(r) <= on_line;
+}
+
 // First crossing of the ray x + t v (0 < t < tmax) with a Neumann element
 // other than `skip` and `skip2` (compact numbering; the sides the walk sits
-// on, -1 for none, with their unit normals n_skip, n_skip2 out of the domain)
-// and the elements behind them (behind_side): returns t (tmax if none) and
-// the element in hit (-1 if none).  A crossing up to a relative 1e-5 beyond
-// tmax counts, at tmax: where the sphere of radius tmax meets the Neumann
-// part, a direction that ends there lands on the boundary, and rounding must
-// not leave the walk unaware of it.
+// on, -1 for none, with their unit normals n_skip, n_skip2 out of the domain),
+// the elements behind them (behind_side) and those on their lines (planes)
+// through x (coplanar_side): returns t (tmax if none) and the element in hit
+// (-1 if none).  A crossing up to a relative 1e-5 plus
+// on_line beyond tmax counts, at tmax: where the sphere of radius tmax meets
+// the Neumann part, a direction that ends there lands on the boundary, and
+// rounding (of the landing point too: a relative tolerance alone is below it
+// for short rays) must not leave the walk unaware of it.
 template <int DIM>
 __device__ __forceinline__ float ray_neumann(const DevNeumann& N, const float* x, const float* v, float tmax, int skip,
-                                             const float* n_skip, int skip2, const float* n_skip2, int& hit, bool& ok) {
-    float best = tmax * (1.0f + 1e-5f);
+                                             const float* n_skip, int skip2, const float* n_skip2, float on_line,
+                                             int& hit, bool& ok) {
+    float best = fmaf(tmax, 1e-5f, tmax) + on_line;
     hit = -1;
     float inv[DIM];
 #pragma unroll
@@ -246,8 +270,6 @@ __device__ __forceinline__ float ray_neumann(const DevNeumann& N, const float* x
     auto leaf = [&](int l) {
         const int e = __ldg(N.prim_elem + l);
         if (e == skip || e == skip2) return;
-        if ((skip >= 0 && behind_side<DIM>(N, skip, n_skip, e)) || (skip2 >= 0 && behind_side<DIM>(N, skip2, n_skip2, e)))
-            return;
         float t;
         if (DIM == 2) {
             const float4 s = __ldg(N.prims + l);
@@ -272,7 +294,12 @@ __device__ __forceinline__ float ray_neumann(const DevNeumann& N, const float* x
             if (!(w >= -1e-5f && u + w <= 1.0f + 1e-5f)) return;
             t = (e2[0] * q[0] + e2[1] * q[1] + e2[2] * q[2]) * id;
         }
-        if (t > 0.0f && t < best) { best = t; hit = e; }
+        if (!(t > 0.0f && t < best)) return;
+        if (skip >= 0 && (behind_side<DIM>(N, skip, n_skip, e) || coplanar_side<DIM>(N, x, n_skip, e, on_line))) return;
+        if (skip2 >= 0 && (behind_side<DIM>(N, skip2, n_skip2, e) || coplanar_side<DIM>(N, x, n_skip2, e, on_line)))
+            return;
+        best = t;
+        hit = e;
     };
     ok = bvh_best_first<DIM>(N.nodes, N.n_internal, N.n_tree, N.n_big, best, key, leaf);
     return fminf(best, tmax);
