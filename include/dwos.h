@@ -232,7 +232,12 @@ dwos_status dwos_set_pde(dwos_ctx* ctx, float sigma, float f);
  * batches, dwos_eval_static and the shape-functional calls
  * (DWOS_ERR_NOT_IMPLEMENTED / DWOS_ERR_INVALID_ARG).  dwos_closest_point
  * then answers for the Dirichlet part, dwos_inside for the whole boundary.
- * Builds a BVH for each part; dwos_set_params updates both.  Synchronises. */
+ * A silhouette point lies where the Neumann part ends or turns: where it runs
+ * straight on through a vertex (flat across an edge: unit directions or
+ * normals within a relative 1e-6) it has none.  Builds a BVH for each part
+ * and one over the silhouette candidates (every vertex / edge where the part
+ * ends or turns; every one if a Neumann vertex has a nonzero Jacobian row);
+ * dwos_set_params updates all three.  Synchronises. */
 dwos_status dwos_set_neumann(dwos_ctx* ctx, const int32_t* flags, int mem);
 
 /* Bound on the BVH node fetches (binary nodes, or 32-wide node visits) that one

@@ -185,3 +185,16 @@ def cube_linear(x):
     u = x and du/dX = -(x + 1) / 2."""
     x = np.atleast_2d(np.asarray(x, dtype=np.float64))
     return x[:, 0].copy(), (-(x[:, 0] + 1) / 2)[:, None]
+
+
+def cylinder_flow(x, a: float):
+    """Potential flow past a cylinder: u = x (1 + a^2 / r^2) = (r + a^2 / r) cos phi
+    is harmonic where r > 0 (the radial part f = r + a^2/r has
+    f'' + f'/r - f/r^2 = 0) and du/dr = f'(a) cos phi = 0 on the circle r = a:
+    with a reflecting Neumann circle of radius a and Dirichlet data u on an
+    outer boundary, the solution is u itself.  With the data scaled by a
+    parameter c (at c = 1), du/dc = u."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    r2 = x[:, 0] ** 2 + x[:, 1] ** 2
+    u = x[:, 0] * (1.0 + a * a / r2)
+    return u, u[:, None].copy()

@@ -514,14 +514,16 @@ static PhaseResult forward_walk(const oracle_scene* s, const double* x0, uint64_
  * Neumann part seen from x: a point where a ray from x grazes it (a vertex
  * whose two segments lie on the same side of the ray in 2D; an edge whose two
  * triangles lie on the same side of the plane through x and the edge in 3D)
- * or where it ends.  The radius is R = max(min(d_D - c, d_sil), eps - c)
- * with the Dirichlet clearance c = 1e-3 eps of step_radius.  A side
- * test whose cross product (triple product in 3D) is within a relative 1e-4
- * of zero counts as collinear (coplanar): where the boundary runs straight on
- * through a vertex (or flat across an edge), seen from a point on its own line
- * (plane), the vertex (edge) is no silhouette; where one side is collinear and
- * the other turns away, it is one.  This keeps walks that sit on a flat
- * Neumann side from taking every vertex of that side as a silhouette.
+ * or where it ends; where the part runs straight on through a vertex (flat
+ * across an edge) it has none (runs_straight_on).  The radius is
+ * R = max(min(d_D - c, d_sil), eps - c)
+ * with the Dirichlet clearance c = 1e-3 eps of step_radius.  At the other
+ * vertices (edges) a side test whose cross product (triple product in 3D) is
+ * within a relative 1e-4 of zero counts as collinear (coplanar): both sides
+ * collinear, no silhouette; one collinear and the other turning away, a
+ * silhouette (seen from a point on the line of one side of a corner).  Seen
+ * from a walk sitting on an element, that element's own vertices are
+ * collinear (coplanar) with the walk's point by definition.
  * A ray meets an element where its barycentric coordinates lie within 1e-5
  * of the element (so that no ray slips between two neighbours), except a
  * neighbour of the side the walk sits on that lies behind that side's plane
@@ -626,7 +628,42 @@ static double det3(const double* a, const double* b, const double* c) {
 }
 
 /* Distance from x to the closest silhouette point of the Neumann part. */
-static double silhouette_distance(const oracle_scene* s, const Adjacency& adj, const double* x) {
+/* Where the Neumann part runs straight on, it has no silhouette point from any
+ * x: a vertex v between segments vw and vz whose unit directions w -> v and
+ * v -> z agree within a relative 1e-6 (2D), or an edge ab between triangles
+ * abc and abz whose unit normals (b - a) x (c - a) and (z - a) x (b - a)
+ * agree within a relative 1e-6 (3D; c and z on opposite sides of ab). */
+static bool runs_straight_on(int d, const double* a, const double* b, const double* c, const double* z) {
+    if (d == 2) {   /* v = a, w = b, z: directions w -> v and v -> z */
+        const double u1[3] = {a[0] - b[0], a[1] - b[1], 0}, u2[3] = {z[0] - a[0], z[1] - a[1], 0};
+        return dot3(u1, u2) >= (1 - 1e-6) * std::sqrt(dot3(u1, u1) * dot3(u2, u2));
+    }
+    const double ab[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    const double ac[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    const double az[3] = {z[0] - a[0], z[1] - a[1], z[2] - a[2]};
+    const double n1[3] = {ab[1] * ac[2] - ab[2] * ac[1], ab[2] * ac[0] - ab[0] * ac[2], ab[0] * ac[1] - ab[1] * ac[0]};
+    const double n2[3] = {az[1] * ab[2] - az[2] * ab[1], az[2] * ab[0] - az[0] * ab[2], az[0] * ab[1] - az[1] * ab[0]};
+    return dot3(n1, n2) >= (1 - 1e-6) * std::sqrt(dot3(n1, n1) * dot3(n2, n2));
+}
+
+/* True if element f (-1: none) has exactly the vertices p, q (and r in 3D). */
+static bool element_is(const oracle_scene* s, int f, int p, int q, int r) {
+    if (f < 0) return false;
+    const int* el = s->elem + (size_t)s->dim * f;
+    const int want[3] = {p, q, r};
+    for (int i = 0; i < s->dim; ++i) {
+        bool found = false;
+        for (int j = 0; j < s->dim; ++j) found = found || el[j] == want[i];
+        if (!found) return false;
+    }
+    return true;
+}
+
+/* The walk sits on element `on` (and `on2` at an edge; -1: none): x lies on
+ * them, so a side test of the silhouette rule whose three points (x, the
+ * site's vertex / edge and the other vertex) span one of them is zero by
+ * definition, whatever the arithmetic gives. */
+static double silhouette_distance(const oracle_scene* s, const Adjacency& adj, const double* x, int on, int on2) {
     double best = INFINITY;
     const int d = s->dim;
     for (int e = 0; e < s->n_elem; ++e) {
@@ -637,14 +674,17 @@ static double silhouette_distance(const oracle_scene* s, const Adjacency& adj, c
                 const double* v = s->vert + 2 * el[j];
                 const double* w = s->vert + 2 * el[1 - j];
                 const int nb = adj.other[2 * (size_t)e + j];
+                if (nb >= 0 && runs_straight_on(2, v, w, NULL, s->vert + 2 * nb)) continue;
                 const double rv[2] = {v[0] - x[0], v[1] - x[1]};
                 bool sil = nb < 0;
                 if (!sil) {
                     const double* z = s->vert + 2 * nb;
                     const double rw[2] = {w[0] - x[0], w[1] - x[1]}, rz[2] = {z[0] - x[0], z[1] - x[1]};
                     const double lv = std::hypot(rv[0], rv[1]);
-                    sil = silhouette_rule(cross2(rv, rw), lv * std::hypot(rw[0], rw[1]),
-                                          cross2(rv, rz), lv * std::hypot(rz[0], rz[1]));
+                    const bool own1 = e == on || e == on2;
+                    const bool own2 = element_is(s, on, el[j], nb, -1) || element_is(s, on2, el[j], nb, -1);
+                    sil = silhouette_rule(own1 ? 0.0 : cross2(rv, rw), lv * std::hypot(rw[0], rw[1]),
+                                          own2 ? 0.0 : cross2(rv, rz), lv * std::hypot(rz[0], rz[1]));
                 }
                 if (sil) best = std::min(best, std::sqrt(rv[0] * rv[0] + rv[1] * rv[1]));
             }
@@ -654,6 +694,7 @@ static double silhouette_distance(const oracle_scene* s, const Adjacency& adj, c
                 const double* b = s->vert + 3 * el[(j + 1) % 3];
                 const double* c = s->vert + 3 * el[(j + 2) % 3];
                 const int nb = adj.other[3 * (size_t)e + j];
+                if (nb >= 0 && runs_straight_on(3, a, b, c, s->vert + 3 * nb)) continue;
                 const double ra[3] = {a[0] - x[0], a[1] - x[1], a[2] - x[2]};
                 const double rb[3] = {b[0] - x[0], b[1] - x[1], b[2] - x[2]};
                 bool sil = nb < 0;
@@ -664,8 +705,11 @@ static double silhouette_distance(const oracle_scene* s, const Adjacency& adj, c
                     const double n[3] = {ra[1] * rb[2] - ra[2] * rb[1], ra[2] * rb[0] - ra[0] * rb[2],
                                          ra[0] * rb[1] - ra[1] * rb[0]};
                     const double ln = std::sqrt(dot3(n, n));
-                    sil = silhouette_rule(det3(ra, rb, rc), ln * std::sqrt(dot3(rc, rc)),
-                                          det3(ra, rb, rz), ln * std::sqrt(dot3(rz, rz)));
+                    const bool own1 = e == on || e == on2;
+                    const int ia = el[j], ib = el[(j + 1) % 3];
+                    const bool own2 = element_is(s, on, ia, ib, nb) || element_is(s, on2, ia, ib, nb);
+                    sil = silhouette_rule(own1 ? 0.0 : det3(ra, rb, rc), ln * std::sqrt(dot3(rc, rc)),
+                                          own2 ? 0.0 : det3(ra, rb, rz), ln * std::sqrt(dot3(rz, rz)));
                 }
                 if (!sil) continue;
                 /* distance from x to the segment ab */
@@ -848,7 +892,7 @@ static PhaseResult wost_walk(const oracle_scene* s, const Adjacency& adj, const 
             for (int i = 0; i < 3; ++i) { res.n_on[i] = n_on[i]; res.n2[i] = n2[i]; }
             return res;
         }
-        const double R = std::max(std::min(step_radius(s, dD), silhouette_distance(s, adj, x)), step_radius(s, s->eps));
+        const double R = std::max(std::min(step_radius(s, dD), silhouette_distance(s, adj, x, on, on2)), step_radius(s, s->eps));
         if (s->f != 0) {   /* source: a point of the ball, counted if x sees it */
             Draws rb = draw(s->seed_lo, s->seed_hi, walk_id, (uint32_t)k, phase, 1);
             double w[3];

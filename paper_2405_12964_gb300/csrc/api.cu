@@ -111,6 +111,8 @@ dwos_status rebuild(dwos_ctx* ctx) {
     // walk on stars: one tree over the Dirichlet part (distance queries), one over the Neumann part
     CK(bvh_build(ctx->bvh, ctx->dim, ctx->vert, ctx->elem_d, ctx->n_elem - ctx->n_neumann, ctx->stream), "BVH build");
     CK(bvh_build(ctx->bvh_n, ctx->dim, ctx->vert, ctx->elem_n, ctx->n_neumann, ctx->stream), "Neumann BVH build");
+    if (ctx->n_sites > 0)
+        CK(bvh_build(ctx->bvh_s, ctx->dim, ctx->vert, ctx->elem_s, ctx->n_sites, ctx->stream), "silhouette BVH build");
     DevNeumann N;
     N.nodes = ctx->bvh_n.nodes;
     N.prims = ctx->bvh_n.prims;
@@ -124,6 +126,15 @@ dwos_status rebuild(dwos_ctx* ctx) {
     N.vert = ctx->vert;
     N.dmap = ctx->dmap;
     N.q_start = ctx->q_start;
+    const bool sil = ctx->n_sites > 0;
+    N.sil_nodes = sil ? ctx->bvh_s.nodes : nullptr;
+    N.sil_prims = sil ? ctx->bvh_s.prims : nullptr;
+    N.sil_prim = sil ? ctx->bvh_s.prim_elem : nullptr;
+    N.sites = ctx->sites;
+    N.sil_n_internal = sil ? ctx->bvh_s.n_internal : 0;
+    N.sil_n_tree = sil ? ctx->bvh_s.n_tree : 0;
+    N.sil_n_big = sil ? ctx->bvh_s.n_big : 0;
+    N.n_sites = ctx->n_sites;
     ctx->neu_host = N;
     CK(cudaMemcpyAsync(ctx->d_neu, &ctx->neu_host, sizeof(N), cudaMemcpyHostToDevice, ctx->stream),
        "copy Neumann part");
@@ -397,8 +408,9 @@ void dwos_destroy(dwos_ctx* ctx) {
                     ctx->xq, ctx->valid, ctx->wvec, ctx->out, ctx->acc_vert, ctx->trace, ctx->dbg, ctx->misc_f,
                     ctx->misc_i, ctx->misc_u, ctx->xq_prev, ctx->d_ctr, ctx->d_err, ctx->pw, ctx->vert_active,
                     ctx->misc_d, ctx->elem_d, ctx->elem_n, ctx->dmap, ctx->nadj, ctx->d_neu, ctx->inside_tmp,
-                    ctx->q_start, ctx->behind, ctx->behind_in};
+                    ctx->q_start, ctx->behind, ctx->behind_in, ctx->sites, ctx->elem_s};
     bvh_free(ctx->bvh_n);
+    bvh_free(ctx->bvh_s);
     for (void* p : bufs) if (p) cudaFree(p);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -475,9 +487,11 @@ dwos_status dwos_set_boundary(dwos_ctx* ctx, int dim, int n_vert, const float* v
     ctx->vert_ref = ctx->vert = ctx->jac = ctx->theta = ctx->g_vert = ctx->dg_vert = nullptr;
     ctx->elem = nullptr;
     ctx->have_boundary = false;
-    for (void* p : {(void*)ctx->elem_d, (void*)ctx->elem_n, (void*)ctx->dmap, (void*)ctx->nadj}) if (p) cudaFree(p);
-    ctx->elem_d = ctx->elem_n = ctx->dmap = ctx->nadj = nullptr;
+    for (void* p : {(void*)ctx->elem_d, (void*)ctx->elem_n, (void*)ctx->dmap, (void*)ctx->nadj, (void*)ctx->sites,
+                    (void*)ctx->elem_s}) if (p) cudaFree(p);
+    ctx->elem_d = ctx->elem_n = ctx->dmap = ctx->nadj = ctx->sites = ctx->elem_s = nullptr;
     ctx->n_neumann = 0;
+    ctx->n_sites = 0;
     const size_t nv = (size_t)n_vert * dim;
     CK(cudaMalloc(&ctx->vert_ref, nv * sizeof(float)), "alloc vertices");
     CK(cudaMalloc(&ctx->vert, nv * sizeof(float)), "alloc vertices");
@@ -536,6 +550,7 @@ dwos_status dwos_set_params(dwos_ctx* ctx, const float* theta, int mem) {
         ctx->inside_cached = -1;
         CK(bvh_refit(ctx->bvh, ctx->vert, ctx->n_neumann > 0 ? ctx->elem_d : ctx->elem, ctx->stream), "BVH refit");
         if (ctx->n_neumann > 0) CK(bvh_refit(ctx->bvh_n, ctx->vert, ctx->elem_n, ctx->stream), "Neumann BVH refit");
+        if (ctx->n_sites > 0) CK(bvh_refit(ctx->bvh_s, ctx->vert, ctx->elem_s, ctx->stream), "silhouette BVH refit");
         ++ctx->refits;
         ctx->launches += 3;
         return DWOS_OK;
@@ -608,9 +623,11 @@ dwos_status dwos_set_neumann(dwos_ctx* ctx, const int32_t* flags, int mem) {
     }
     const int n_n = (int)(en.size() / d);
     if (n_n > 0 && n_n == n) return fail(ctx, DWOS_ERR_INVALID_ARG, "the boundary needs a Dirichlet part");
-    for (void* p : {(void*)ctx->elem_d, (void*)ctx->elem_n, (void*)ctx->dmap, (void*)ctx->nadj}) if (p) cudaFree(p);
-    ctx->elem_d = ctx->elem_n = ctx->dmap = ctx->nadj = nullptr;
+    for (void* p : {(void*)ctx->elem_d, (void*)ctx->elem_n, (void*)ctx->dmap, (void*)ctx->nadj, (void*)ctx->sites,
+                    (void*)ctx->elem_s}) if (p) cudaFree(p);
+    ctx->elem_d = ctx->elem_n = ctx->dmap = ctx->nadj = ctx->sites = ctx->elem_s = nullptr;
     ctx->n_neumann = 0;
+    ctx->n_sites = 0;
     if (n_n == 0) return rebuild(ctx);            // every element Dirichlet again
     // neighbours across each endpoint (segments) or edge (triangles) within the Neumann part
     std::vector<int32_t> adj((size_t)n_n * d, -1);
@@ -638,6 +655,58 @@ dwos_status dwos_set_neumann(dwos_ctx* ctx, const int32_t* flags, int mem) {
             }
         }
     }
+    // silhouette candidates: the sites where the Neumann part ends or does not run straight on
+    // (a vertex between two segments whose directions agree, an edge between two coplanar
+    // triangles is a silhouette from no point); every site if the part moves with theta.  The
+    // walk kernel applies the same test with a relative 1e-6; a site is left out here only if
+    // it is straight within 1e-7, so that rounding cannot leave out one the kernel would keep.
+    std::vector<float> vh((size_t)ctx->n_vert * d);
+    CK(cudaMemcpy(vh.data(), ctx->vert, sizeof(float) * vh.size(), cudaMemcpyDeviceToHost), "copy vertices");
+    bool moving = false;
+    if (ctx->n_param > 0 && ctx->jac) {
+        std::vector<float> jh((size_t)ctx->n_vert * d * ctx->n_param);
+        CK(cudaMemcpy(jh.data(), ctx->jac, sizeof(float) * jh.size(), cudaMemcpyDeviceToHost), "copy Jacobian");
+        for (size_t i = 0; i < en.size() && !moving; ++i)
+            for (size_t q = 0; q < (size_t)d * ctx->n_param && !moving; ++q)
+                moving = jh[(size_t)en[i] * d * ctx->n_param + q] != 0.0f;
+    }
+    auto vx = [&](int v, int k) { return (double)vh[(size_t)d * v + k]; };
+    std::vector<int32_t> sites, elem_s;
+    for (int c = 0; c < n_n; ++c) {
+        const int* t = en.data() + (size_t)d * c;
+        int mask = 0;
+        for (int j = 0; j < d; ++j) {
+            const int nb = adj[(size_t)d * c + j];
+            bool straight = false;
+            if (nb >= 0 && !moving) {
+                double u1[3] = {0, 0, 0}, u2[3] = {0, 0, 0};
+                if (d == 2) {   // directions w -> v and v -> z at v = t[j]
+                    for (int k = 0; k < 2; ++k) { u1[k] = vx(t[j], k) - vx(t[1 - j], k); u2[k] = vx(nb, k) - vx(t[j], k); }
+                } else {        // normals (b - a) x (c - a) and (z - a) x (b - a) of the edge ab
+                    const int a = t[j], b = t[(j + 1) % 3], cc = t[(j + 2) % 3];
+                    double ab[3], ac[3], az[3];
+                    for (int k = 0; k < 3; ++k) { ab[k] = vx(b, k) - vx(a, k); ac[k] = vx(cc, k) - vx(a, k); az[k] = vx(nb, k) - vx(a, k); }
+                    u1[0] = ab[1] * ac[2] - ab[2] * ac[1]; u1[1] = ab[2] * ac[0] - ab[0] * ac[2]; u1[2] = ab[0] * ac[1] - ab[1] * ac[0];
+                    u2[0] = az[1] * ab[2] - az[2] * ab[1]; u2[1] = az[2] * ab[0] - az[0] * ab[2]; u2[2] = az[0] * ab[1] - az[1] * ab[0];
+                }
+                const double dot = u1[0] * u2[0] + u1[1] * u2[1] + u1[2] * u2[2];
+                const double n1 = u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2];
+                const double n2 = u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2];
+                straight = dot >= (1.0 - 1e-7) * std::sqrt(n1 * n2);
+            }
+            if (!straight) mask |= 1 << j;
+        }
+        if (!mask) continue;
+        sites.push_back(8 * c + mask);
+        for (int j = 0; j < d; ++j) elem_s.push_back(t[j]);
+    }
+    if (!sites.empty()) {
+        CK(cudaMalloc(&ctx->sites, sizeof(int32_t) * sites.size()), "alloc silhouette sites");
+        CK(cudaMalloc(&ctx->elem_s, sizeof(int32_t) * elem_s.size()), "alloc silhouette sites");
+        CK(cudaMemcpy(ctx->sites, sites.data(), sizeof(int32_t) * sites.size(), cudaMemcpyHostToDevice), "copy");
+        CK(cudaMemcpy(ctx->elem_s, elem_s.data(), sizeof(int32_t) * elem_s.size(), cudaMemcpyHostToDevice), "copy");
+    }
+    ctx->n_sites = (int)sites.size();
     CK(cudaMalloc(&ctx->elem_d, sizeof(int32_t) * ed.size()), "alloc Dirichlet elements");
     CK(cudaMalloc(&ctx->elem_n, sizeof(int32_t) * en.size()), "alloc Neumann elements");
     CK(cudaMalloc(&ctx->dmap, sizeof(int32_t) * dmap.size()), "alloc element map");

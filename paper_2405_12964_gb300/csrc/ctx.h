@@ -39,6 +39,10 @@ struct dwos_ctx {
     int* dmap = nullptr;         // compact Dirichlet element -> input element
     int* nadj = nullptr;         // per Neumann element and endpoint / edge: the neighbour's vertex, -1 open
     dwos::BvhBuffers bvh_n;      // over the Neumann part
+    int n_sites = 0;             // elements with silhouette candidates (DevNeumann::sites)
+    int* sites = nullptr;
+    int* elem_s = nullptr;       // per entry of sites its element's vertices (what their BVH bounds)
+    dwos::BvhBuffers bvh_s;      // over the silhouette candidates
     dwos::DevNeumann* d_neu = nullptr;
     dwos::DevNeumann neu_host{};                          // what d_neu holds
     float4* q_start = nullptr; size_t q_start_cap = 0;    // per query: start on the Neumann part

@@ -25,6 +25,14 @@ struct DevNeumann {
     const int* dmap;            // Dirichlet element (compact, the main BVH's numbering) -> input element
     const float4* q_start;      // per query point of the current call: normal out of the domain (xyz) and
                                 // the Neumann element (compact, int bits in w) its walk starts on, -1 inside
+    // silhouette candidates: the sites (element endpoint in 2D, edge in 3D) where the Neumann part
+    // ends or does not run straight on (every site when its vertices move with the parameters),
+    // grouped by element, with a binary BVH over the elements that have one
+    const float4* sil_nodes;
+    const float4* sil_prims;
+    const int* sil_prim;        // leaf -> entry of sites
+    const int* sites;           // 8 e + mask: compact Neumann element e, bit j for its endpoint / edge j
+    int sil_n_internal, sil_n_tree, sil_n_big, n_sites;   // n_sites: entries of sites
 };
 
 // Everything a walk needs about one problem.  Copied to the device (and, in

@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
             // walk on stars: R from the Dirichlet distance and the Neumann silhouettes
             const unsigned long long wid = P.walk_id_base + local;
             bool ok1 = true, ok2 = true, ok3 = true;
-            const float sd2 = silhouette_dist2<DIM>(NS, x, best2, ok1);
+            const float sd2 = silhouette_dist2<DIM>(NS, x, best2, on_e, on2, ok1);
             // R = max(min(d_D - c, d_sil), eps - c), c = 1e-3 eps the Dirichlet clearance
             const float R = fmaxf(fminf(sqrtf(sd2), fmaf(-1e-3f, P.eps, d)), fmaf(-1e-3f, P.eps, P.eps));
             if (P.f != 0.0f) {   // source: a point of the ball, counted if x sees it

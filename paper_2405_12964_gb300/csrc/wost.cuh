@@ -78,74 +78,122 @@ __device__ __forceinline__ bool silhouette_rule(float s1, float m1, float s2, fl
     return s1 * s2 > 0.0f;
 }
 
-// Squared distance from x to the closest silhouette point of the Neumann part
-// below `bound2` (bound2 itself if there is none): vertices (2D) or edges (3D)
-// where the part ends, or whose two elements lie on the same side of the ray
-// (2D) or plane (3D) through x (silhouette_rule).
+// True where the Neumann part runs straight on through a site, which is then
+// a silhouette from no x: at a vertex v between segments vw and vz the unit
+// directions w -> v and v -> z agree within a relative 1e-6 (2D, u1 = v - w,
+// u2 = z - v); across an edge ab between triangles abc and abz the unit
+// normals (b - a) x (c - a) and (z - a) x (b - a) agree within 1e-6 (3D).
+__device__ __forceinline__ bool runs_straight_on(const float* u1, const float* u2) {
+    const float dot = u1[0] * u2[0] + u1[1] * u2[1] + u1[2] * u2[2];
+    const float n1 = u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2];
+    const float n2 = u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2];
+    return dot >= (1.0f - 1e-6f) * sqrtf(n1 * n2);
+}
+
+// True if Neumann element f (-1: none) has exactly the vertices p, q (and r
+// in 3D).
 template <int DIM>
-__device__ __forceinline__ float silhouette_dist2(const DevNeumann& N, const float* x, float bound2, bool& ok) {
+__device__ __forceinline__ bool element_is(const DevNeumann& N, int f, int p, int q, int r) {
+    if (f < 0) return false;
+    bool all = true;
+    const int want[3] = {p, q, r};
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        bool found = false;
+#pragma unroll
+        for (int k = 0; k < DIM; ++k) found = found || __ldg(N.elem + (size_t)DIM * f + k) == want[i];
+        all = all && found;
+    }
+    return all;
+}
+
+// Squared distance from x to the closest silhouette point of the Neumann part
+// below `bound2` (bound2 itself if there is none), over the candidate sites
+// (DevNeumann::sites): vertices (2D) or edges (3D) where the part ends, or
+// whose two elements lie on the same side of the ray (2D) or plane (3D)
+// through x (silhouette_rule) without the part running straight on there.
+// The walk sits on elements on and on2 (-1: none): a side test whose points
+// span one of them is zero by definition (x lies on it).
+template <int DIM>
+__device__ __forceinline__ float silhouette_dist2(const DevNeumann& N, const float* x, float bound2, int on, int on2,
+                                                  bool& ok) {
     float best = bound2;
     auto key = [&](const float* lo, const float* hi) { return box_dist2<DIM>(x, lo, hi); };
-    auto leaf = [&](int l) {
-        const int e = __ldg(N.prim_elem + l);
+    auto test = [&](int e, int j) {
         const int* ev = N.elem + (size_t)DIM * e;
         if (DIM == 2) {
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                float v[2], w[2];
-                vload<2>(N.vert, __ldg(ev + j), v);
-                const float rv0 = v[0] - x[0], rv1 = v[1] - x[1];
-                const float d2 = rv0 * rv0 + rv1 * rv1;
-                if (d2 >= best) continue;
-                const int nb = __ldg(N.adj + 2 * (size_t)e + j);
-                bool sil = nb < 0;
-                if (!sil) {
-                    float z[2];
-                    vload<2>(N.vert, __ldg(ev + 1 - j), w);
-                    vload<2>(N.vert, nb, z);
-                    const float rw0 = w[0] - x[0], rw1 = w[1] - x[1], rz0 = z[0] - x[0], rz1 = z[1] - x[1];
-                    const float lv = sqrtf(d2);
-                    sil = silhouette_rule(rv0 * rw1 - rv1 * rw0, lv * sqrtf(rw0 * rw0 + rw1 * rw1),
-                                          rv0 * rz1 - rv1 * rz0, lv * sqrtf(rz0 * rz0 + rz1 * rz1));
-                }
-                if (sil) best = d2;
+            float v[2], w[2];
+            const int iv = __ldg(ev + j);
+            vload<2>(N.vert, iv, v);
+            const float rv0 = v[0] - x[0], rv1 = v[1] - x[1];
+            const float d2 = rv0 * rv0 + rv1 * rv1;
+            if (d2 >= best) return;
+            const int nb = __ldg(N.adj + 2 * (size_t)e + j);
+            bool sil = nb < 0;
+            if (!sil) {
+                float z[2];
+                vload<2>(N.vert, __ldg(ev + 1 - j), w);
+                vload<2>(N.vert, nb, z);
+                const float u1[3] = {v[0] - w[0], v[1] - w[1], 0.0f}, u2[3] = {z[0] - v[0], z[1] - v[1], 0.0f};
+                if (runs_straight_on(u1, u2)) return;
+                const float rw0 = w[0] - x[0], rw1 = w[1] - x[1], rz0 = z[0] - x[0], rz1 = z[1] - x[1];
+                const float lv = sqrtf(d2);
+                const bool own1 = e == on || e == on2;
+                const bool own2 = element_is<2>(N, on, iv, nb, -1) || element_is<2>(N, on2, iv, nb, -1);
+                sil = silhouette_rule(own1 ? 0.0f : rv0 * rw1 - rv1 * rw0, lv * sqrtf(rw0 * rw0 + rw1 * rw1),
+                                      own2 ? 0.0f : rv0 * rz1 - rv1 * rz0, lv * sqrtf(rz0 * rz0 + rz1 * rz1));
             }
+            if (sil) best = d2;
         } else {
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                float a[3], b[3];
-                vload<3>(N.vert, __ldg(ev + j), a);
-                vload<3>(N.vert, __ldg(ev + (j + 1) % 3), b);
-                const float ab[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
-                const float ra[3] = {a[0] - x[0], a[1] - x[1], a[2] - x[2]};
-                const float len2 = ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2];
-                float t = len2 > 0.0f ? -(ra[0] * ab[0] + ra[1] * ab[1] + ra[2] * ab[2]) / len2 : 0.0f;
-                t = fminf(fmaxf(t, 0.0f), 1.0f);
-                const float o[3] = {ra[0] + t * ab[0], ra[1] + t * ab[1], ra[2] + t * ab[2]};
-                const float d2 = o[0] * o[0] + o[1] * o[1] + o[2] * o[2];
-                if (d2 >= best) continue;
-                const int nb = __ldg(N.adj + 3 * (size_t)e + j);
-                bool sil = nb < 0;
-                if (!sil) {
-                    float c[3], z[3];
-                    vload<3>(N.vert, __ldg(ev + (j + 2) % 3), c);
-                    vload<3>(N.vert, nb, z);
-                    const float rb[3] = {b[0] - x[0], b[1] - x[1], b[2] - x[2]};
-                    const float n[3] = {ra[1] * rb[2] - ra[2] * rb[1], ra[2] * rb[0] - ra[0] * rb[2],
-                                        ra[0] * rb[1] - ra[1] * rb[0]};
-                    const float rc[3] = {c[0] - x[0], c[1] - x[1], c[2] - x[2]};
-                    const float rz[3] = {z[0] - x[0], z[1] - x[1], z[2] - x[2]};
-                    const float ln = sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-                    sil = silhouette_rule(n[0] * rc[0] + n[1] * rc[1] + n[2] * rc[2],
-                                          ln * sqrtf(rc[0] * rc[0] + rc[1] * rc[1] + rc[2] * rc[2]),
-                                          n[0] * rz[0] + n[1] * rz[1] + n[2] * rz[2],
-                                          ln * sqrtf(rz[0] * rz[0] + rz[1] * rz[1] + rz[2] * rz[2]));
-                }
-                if (sil) best = d2;
+            float a[3], b[3];
+            const int ia = __ldg(ev + j), ib = __ldg(ev + (j + 1) % 3);
+            vload<3>(N.vert, ia, a);
+            vload<3>(N.vert, ib, b);
+            const float ab[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+            const float ra[3] = {a[0] - x[0], a[1] - x[1], a[2] - x[2]};
+            const float len2 = ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2];
+            float t = len2 > 0.0f ? -(ra[0] * ab[0] + ra[1] * ab[1] + ra[2] * ab[2]) / len2 : 0.0f;
+            t = fminf(fmaxf(t, 0.0f), 1.0f);
+            const float o[3] = {ra[0] + t * ab[0], ra[1] + t * ab[1], ra[2] + t * ab[2]};
+            const float d2 = o[0] * o[0] + o[1] * o[1] + o[2] * o[2];
+            if (d2 >= best) return;
+            const int nb = __ldg(N.adj + 3 * (size_t)e + j);
+            bool sil = nb < 0;
+            if (!sil) {
+                float c[3], z[3];
+                vload<3>(N.vert, __ldg(ev + (j + 2) % 3), c);
+                vload<3>(N.vert, nb, z);
+                const float ac[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+                const float az[3] = {z[0] - a[0], z[1] - a[1], z[2] - a[2]};
+                const float u1[3] = {ab[1] * ac[2] - ab[2] * ac[1], ab[2] * ac[0] - ab[0] * ac[2],
+                                     ab[0] * ac[1] - ab[1] * ac[0]};
+                const float u2[3] = {az[1] * ab[2] - az[2] * ab[1], az[2] * ab[0] - az[0] * ab[2],
+                                     az[0] * ab[1] - az[1] * ab[0]};
+                if (runs_straight_on(u1, u2)) return;
+                const float rb[3] = {b[0] - x[0], b[1] - x[1], b[2] - x[2]};
+                const float n[3] = {ra[1] * rb[2] - ra[2] * rb[1], ra[2] * rb[0] - ra[0] * rb[2],
+                                    ra[0] * rb[1] - ra[1] * rb[0]};
+                const float rc[3] = {c[0] - x[0], c[1] - x[1], c[2] - x[2]};
+                const float rz[3] = {z[0] - x[0], z[1] - x[1], z[2] - x[2]};
+                const float ln = sqrtf(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+                const bool own1 = e == on || e == on2;
+                const bool own2 = element_is<3>(N, on, ia, ib, nb) || element_is<3>(N, on2, ia, ib, nb);
+                sil = silhouette_rule(own1 ? 0.0f : n[0] * rc[0] + n[1] * rc[1] + n[2] * rc[2],
+                                      ln * sqrtf(rc[0] * rc[0] + rc[1] * rc[1] + rc[2] * rc[2]),
+                                      own2 ? 0.0f : n[0] * rz[0] + n[1] * rz[1] + n[2] * rz[2],
+                                      ln * sqrtf(rz[0] * rz[0] + rz[1] * rz[1] + rz[2] * rz[2]));
             }
+            if (sil) best = d2;
         }
     };
-    ok = bvh_best_first<DIM>(N.nodes, N.n_internal, N.n_tree, N.n_big, best, key, leaf);
+    // a leaf is a Neumann element with a mask of its candidate endpoints / edges
+    auto leaf = [&](int l) {
+        const int site = __ldg(N.sites + __ldg(N.sil_prim + l));
+#pragma unroll
+        for (int j = 0; j < DIM; ++j)
+            if ((site >> j) & 1) test(site >> 3, j);
+    };
+    ok = bvh_best_first<DIM>(N.sil_nodes, N.sil_n_internal, N.sil_n_tree, N.sil_n_big, best, key, leaf);
     return best;
 }
 

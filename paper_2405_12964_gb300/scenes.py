@@ -532,6 +532,38 @@ def thermal_scene(offset=(0.0, 0.0), n_wire: int = 64, n_slab: int = 40, n_query
     return sc
 
 
+def cylinder_flow_scene(a: float = 0.4, n_circle: int = 300, n_side: int = 64, n_query: int = 8,
+                        walks: int = 1024, eps: float = 1e-3, h: float = 1e-2, K: int = 1,
+                        seed: int = GEOMETRY_SEED) -> Scene:
+    """Potential flow past a cylinder: the box [-1, 1]^2 (n_side segments per
+    side, Dirichlet, mapped data g = x (1 + a^2 / r^2) at the vertices, scaled
+    by one data parameter c at c = 1) around an insulating circle of radius a
+    (n_circle segments, reflecting Neumann; every vertex a silhouette
+    candidate).  u = x (1 + a^2 / r^2) in the domain, du/dc = u.  Query points
+    uniform in |x|_inf < 0.9 with r > a + 0.05."""
+    t = np.linspace(-1.0, 1.0, n_side + 1)[:-1]
+    box = np.concatenate([np.stack([t, np.full(n_side, -1.0)], 1), np.stack([np.full(n_side, 1.0), t], 1),
+                          np.stack([-t, np.full(n_side, 1.0)], 1), np.stack([np.full(n_side, -1.0), -t], 1)])
+    nb = len(box)
+    ph = 2 * np.pi * np.arange(n_circle) / n_circle
+    circ = a * np.stack([np.cos(ph), np.sin(ph)], 1)
+    vert = np.concatenate([box, circ], 0)
+    elem = np.concatenate([np.stack([np.arange(nb), (np.arange(nb) + 1) % nb], 1),
+                           np.stack([np.arange(n_circle), (np.arange(n_circle) + 1) % n_circle], 1) + nb]).astype(np.int32)
+    neumann = np.concatenate([np.zeros(nb), np.ones(n_circle)]).astype(np.int32)
+    g = vert[:, 0] * (1.0 + a * a / (vert[:, 0] ** 2 + vert[:, 1] ** 2))
+    rng = np.random.default_rng(seed)
+    q = np.zeros((0, 2))
+    while len(q) < n_query:
+        p = rng.uniform(-0.9, 0.9, size=(4 * n_query, 2))
+        q = np.concatenate([q, p[np.hypot(p[:, 0], p[:, 1]) > a + 0.05]])[:n_query]
+    sc = Scene("cylinder_flow", vert, elem, np.zeros((len(vert), 2, 1)), data="mapped", g_vert=g,
+               dg_vert=g[:, None].copy(), sigma=0.0)
+    sc.eps, sc.h, sc.K, sc.query, sc.walks, sc.neumann = eps, h, K, q, walks, neumann
+    sc.meta = {"a": a}
+    return sc
+
+
 def cube_neumann_scene(m: int = 4, n_query: int = 8, walks: int = 1024, eps: float = 1e-3, h: float = 1e-2,
                        K: int = 1, sigma: float = 0.0, seed: int = GEOMETRY_SEED) -> Scene:
     """Cube [-1, 1]^3, each face split into 2 m^2 triangles: the faces x = -1 and

@@ -4,8 +4,8 @@ Sec. 3.4 and 4.2) against the FP64 oracle, through the C ABI.
 * The K1 of the 2D star weight and the star weight itself against the
   oracle's FP64 definitions (std::cyl_bessel_k and the Green's function flux).
 * Per-walk replays of the same Philox walks on the quarter disk (field and
-  mapped data), the screened strip, the strip with a source, the slit disk and
-  the cube with four Neumann faces: on walks whose branch (steps and
+  mapped data), the screened strip, the strip with a source, the slit disk,
+  the cube with four Neumann faces and the potential flow past a cylinder: on walks whose branch (steps and
   termination per phase, terminal element) matches, u and udot agree as in the
   Dirichlet parity tests.  Walks end only on Dirichlet elements, numbered as
   the input numbers them.
@@ -146,6 +146,18 @@ def test_cube_with_neumann_faces_replay_and_closed_form(Solver):
     assert np.all(np.abs(u - ue) <= 4.5 * use + 4e-3)
     dse_ref = np.maximum(dse, np.median(dse, axis=0, keepdims=True))
     assert np.all(np.abs(du - due) <= 4.5 * dse_ref + 0.08 * np.abs(due) + 0.02)
+
+
+def test_cylinder_flow_replay_and_closed_form(Solver):
+    # a curved Neumann part: 600 silhouette candidates, searched through their own tree
+    sc = scenes.cylinder_flow_scene(n_query=12)
+    s, g, o, same = _replay(Solver, sc, 64, u_scale=1.0)
+    out = s.eval(sc.query, 8192, grad=True)
+    ue, due = cf.cylinder_flow(sc.query, sc.meta["a"])
+    u, use = out["u"].cpu().numpy(), out["u_se"].cpu().numpy()
+    du, dse = out["du"].cpu().numpy(), out["du_se"].cpu().numpy()
+    assert np.all(np.abs(u - ue) <= 4.5 * use + 2e-3)
+    assert np.all(np.abs(du - due) <= 4.5 * dse + 2e-3)
 
 
 def test_queries_and_refusals_with_a_neumann_part(Solver):

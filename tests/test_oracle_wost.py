@@ -11,8 +11,10 @@ data) and its differential walk, which nests at the Dirichlet shell only
   bottom; du/dL of the moving side), a strip with a source, a slit disk
   (u = sqrt(r) cos(phi/2), discontinuous across a two-sided Neumann slit with
   an open end: a walk that stepped across the slit, as it would with a radius
-  not bounded by the slit's silhouette, lands on the other side's data), and a
-  cube with four Neumann faces (u = x, du/dX of the moving face).
+  not bounded by the slit's silhouette, lands on the other side's data), a
+  cube with four Neumann faces (u = x, du/dX of the moving face), and the
+  potential flow past an insulating cylinder (u = x (1 + a^2/r^2), a curved
+  Neumann part whose silhouettes are the points where rays graze it).
 * Walks never end on the Neumann part.
 Tolerances: 3.5 SE + a bias budget (polygon / mesh, eps-shell and the O(h)
 backward difference of Sec. 5.3).
@@ -112,6 +114,22 @@ def test_cube_with_neumann_faces_closed_form():
     dirichlet = np.nonzero(sc.neumann == 0)[0]
     hit = o["kind"][:, 0] == oracle.KIND_SHELL
     assert np.isin(o["elem"][hit], dirichlet).all()
+
+
+def test_cylinder_flow_closed_form():
+    # a curved Neumann part: an insulating circle in a box held at the potential flow past it,
+    # u = x (1 + a^2/r^2); its silhouette points (where rays from x graze the circle) bound the
+    # stars, and du/dc = u tests the data derivative through walks on stars
+    sc = scenes.cylinder_flow_scene(n_query=6)
+    r = _run(sc, 2048)
+    u, du = cf.cylinder_flow(sc.query, sc.meta["a"])
+    _check(r["u"], r["u_se"], u, 0.0, 2e-3)
+    _check(r["du"], r["du_se"], du, 0.0, 2e-3)
+    o = r["out"]
+    dirichlet = np.nonzero(sc.neumann == 0)[0]
+    hit = o["kind"][:, 0] == oracle.KIND_SHELL
+    assert np.isin(o["elem"][hit], dirichlet).all()
+    assert np.all(np.hypot(o["x_end"][:, 0], o["x_end"][:, 1]) >= sc.meta["a"] * np.cos(np.pi / 300) - 1e-9)
 
 
 def _on_neumann_points(name):
