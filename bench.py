@@ -12,13 +12,17 @@ gradient RMSE x seconds, the walk kernel's roofline entry, the oracle's CPU
 baseline on a bounded sample, the end-to-end figure through the C ABI with
 host buffers, launch count and SM clocks sampled during the timed region.
 After the C2 figures, and outside their timed region, the same line carries
-the other configurations' headline figures (about a minute in all; skip with
---no-extras): "c3" walk-steps/s of the 200k-triangle 3D workload, "c4" the
-64-problem batch against the same problems as separate calls, "c5" the
-learned control variate against the plain estimator (equal-time final
-losses over three seeds, gradient RMSE x seconds per estimate).
+the other configurations' headline figures (about a minute and a half in
+all; skip with --no-extras): "c3" walk-steps/s of the 200k-triangle 3D
+workload, "c4" the 64-problem batch against the same problems as separate
+calls, "c5" the learned control variate against the plain estimator
+(equal-time final losses over six seeds, gradient RMSE x seconds per
+estimate), "wost" walks on stars on the 2D thermal design and a 3D cube, and
+"functional" the volume-integrated shape functional, each with the oracle's
+rate on a bounded sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py --workload {c3,c4,c5,ablation,sgd,wost} ...
 """
 from __future__ import annotations
 
@@ -52,6 +56,9 @@ WORKLOADS = {
            "seconds of one estimate at "
            "1024 walks/point, the network's inference inside the timed region"),
     "ablation": "estimator ablation (product estimators, du/dn estimators, K, h) on the 2D workload",
+    "wost": ("walks on stars (Sec. 3.4, 4.2): differential gradient step (U-statistic L2 gradient, K = 2) on the "
+             "2D thermal design (32 points on the insulating slab x 16384 walks) and on the 3D cube with four "
+             "Neumann faces (64 points x 4096 walks)"),
     "sgd": ("noisy-gradient optimisation (Sec. 5.2) on the 2D workload's geometry: the star's position "
             "(2-vector, Vector Adam, lr 1e-3) from (0.1, -0.06) back to the target's, 256 and 16384 "
             "observation points on |x|_inf = 0.6, 600 iterations, "
@@ -225,8 +232,9 @@ def wost_summary(steps: int = 5, warmup: int = 2, oracle_budget_s: float = 3.0):
     import torch
     from paper_2405_12964_gb300 import build, scenes
     build.build()
-    import oracle
-    oracle.build()
+    if oracle_budget_s > 0:
+        import oracle
+        oracle.build()
     from paper_2405_12964_gb300.dwos import Solver
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     out = {}
@@ -256,6 +264,12 @@ def wost_summary(steps: int = 5, warmup: int = 2, oracle_budget_s: float = 3.0):
             s.sync()   # raises on a walk that left the domain or a search out of budget
         except Exception as ex:
             device_error = str(ex)
+        out[name] = {"points": int(sc.query.shape[0]), "walks_per_point": int(sc.walks), "elements": int(len(sc.elem)),
+                     "neumann_elements": int(sc.neumann.sum()), "value": walk_steps / (sum(t) / 1e3), "unit": UNIT,
+                     "ms_per_step": float(np.mean(t)), "walk_steps_per_step": walk_steps / steps,
+                     "capped_walks": int(capped), "device_error": device_error}
+        if oracle_budget_s <= 0:
+            continue
         pr = oracle.Problem(vert=sc.vert, elem=sc.elem, jac=sc.jac, data_kind="mapped", g_vert=sc.g_vert,
                             sigma=sc.sigma, f=sc.f, eps=sc.eps, h=sc.h, K=sc.K, seed=sc.seed, neumann=sc.neumann)
         n_pts = min(8, sc.query.shape[0])
@@ -267,12 +281,8 @@ def wost_summary(steps: int = 5, warmup: int = 2, oracle_budget_s: float = 3.0):
         o = oracle.run_walks(pr, sc.query[:n_pts], W, differential=True, walk_id_base=1 << 41)
         dt = time.perf_counter() - t0
         o_steps = int(np.clip(o["steps"], 0, None).sum())
-        out[name] = {"points": int(sc.query.shape[0]), "walks_per_point": int(sc.walks), "elements": int(len(sc.elem)),
-                     "neumann_elements": int(sc.neumann.sum()), "value": walk_steps / (sum(t) / 1e3), "unit": UNIT,
-                     "ms_per_step": float(np.mean(t)), "walk_steps_per_step": walk_steps / steps,
-                     "capped_walks": int(capped), "device_error": device_error,
-                     "oracle": {"value": o_steps / dt, "unit": UNIT, "cores": oracle.num_threads(),
-                                "sample": f"{n_pts} points x {W} differential walks, {dt:.1f} s"}}
+        out[name]["oracle"] = {"value": o_steps / dt, "unit": UNIT, "cores": oracle.num_threads(),
+                                "sample": f"{n_pts} points x {W} differential walks, {dt:.1f} s"}
     return out
 
 
@@ -488,6 +498,16 @@ def control_variate_summary(seeds=(3, 4, 5, 6, 7, 8), steps: int = 200, train_ev
             "gradient_rmse_x_seconds": rows, "clocks": clk}
 
 
+def run_wost(args):
+    """--workload wost: the walk-on-stars summary alone (the oracle leg unless --no-cpu)."""
+    r = wost_summary(steps=args.steps, warmup=args.warmup, oracle_budget_s=0.0 if args.no_cpu else 3.0)
+    line = {"metric": METRIC, "value": r["thermal_2d"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOADS["wost"], "l2": "flushed between timed steps (256 MB write)"}}
+    line.update(r)
+    print(json.dumps(line), flush=True)
+
+
 def run_control_variate(args):
     r = control_variate_summary()
     line = {"metric": METRIC, "value": r["gradient_rmse_x_seconds"]["start"]["cv"]["rmse_x_seconds"],
@@ -655,6 +675,8 @@ def main():
         return run_ablation(args)
     if args.workload == "sgd":
         return run_sgd(args)
+    if args.workload == "wost":
+        return run_wost(args)
 
     import numpy as np
     import torch

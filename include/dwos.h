@@ -91,8 +91,9 @@ typedef struct {
                            binary root needs no tree search; the others are
                            searched as in order 2 (for segments, as in order 0
                            when more than 16 lanes of a warp need one at once);
-                           -1 = automatic (3; orders 2 and 3 fall back to 0
-                           without a 32-wide tree) */
+                           -1 = automatic (3; with a Neumann part, 0 while the
+                           Dirichlet part has fewer than 128 elements; orders 2
+                           and 3 fall back to 0 without a 32-wide tree) */
     int dudn_estimator; /* du/dn at a shell hit from the K nested walks: 0 = backward
                            difference (g(xbar) - mean u(xbar - h n)) / h, Eq.
                            (dudn_fd_estimate); 1 = ball gradient at x_off = xbar - h n:

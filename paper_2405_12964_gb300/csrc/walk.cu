@@ -122,7 +122,8 @@ __device__ __forceinline__ void sphere_dir(const U4& r, float* om) {
 }
 
 // STAR: walk on stars over a boundary with a reflecting Neumann part (one
-// problem per launch, per-lane binary search of the Dirichlet part's BVH).
+// problem per launch; the Dirichlet part's distance queries take the launch's
+// search order, the Neumann queries per lane).
 template <int DIM, bool WIDE, bool STAR = false>
 __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
     walk_kernel(const DevProblem* __restrict__ g_probs, int n_probs, unsigned long long total,
@@ -148,7 +149,9 @@ __global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
                 reinterpret_cast<int*>(zero_ctr)[i] = 0;
     }
     __syncthreads();
-    DevNeumann& NS = *reinterpret_cast<DevNeumann*>(smem_raw + walk_smem_bytes(n_probs, 0, 0));
+    // the Neumann descriptor follows the problems (and, warp-wide, the stacks and phase states)
+    DevNeumann& NS = *reinterpret_cast<DevNeumann*>(smem_raw + walk_smem_bytes(n_probs, WIDE ? (int)blockDim.x : 0,
+                                                                               WIDE ? 3 : 0, DIM, false));
     if constexpr (STAR) {
         const int words = (int)(sizeof(DevNeumann) / sizeof(int));
         const int* src = reinterpret_cast<const int*>(sp[0].neu);
@@ -777,7 +780,10 @@ cudaError_t launch_neumann_orient(int n, const int* behind_inside, float4* q_sta
 int walk_max_blocks_per_sm(int dim, int block_size, int traversal, bool star) {
     int n = 0;
     const size_t smem = walk_smem_bytes(1, block_size, traversal, dim, star);
-    if (star) {
+    if (star && (traversal == 2 || traversal == 3)) {
+        if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<2, true, true>, block_size, smem);
+        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<3, true, true>, block_size, smem);
+    } else if (star) {
         if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<2, false, true>, block_size, smem);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<3, false, true>, block_size, smem);
     } else if (traversal == 2 || traversal == 3) {
@@ -801,7 +807,7 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
         return cudaSuccess;
     }
     const int bs = L.block_size;
-    if (L.star && (n_probs != 1 || L.traversal == 2 || L.traversal == 3)) return cudaErrorInvalidValue;
+    if (L.star && n_probs != 1) return cudaErrorInvalidValue;
     int per_sm = L.blocks_per_sm > 0 ? L.blocks_per_sm
                                      : walk_max_blocks_per_sm(L.dim, bs, L.traversal, L.star);
     if (per_sm < 1) per_sm = 1;
@@ -823,6 +829,8 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
         kernel<<<(int)blocks, bs, smem, stream>>>(d_probs, n_probs, total, d_counters, zero_counters, P1);
         return cudaGetLastError();
     };
+    if (L.star && (L.traversal == 2 || L.traversal == 3))
+        return L.dim == 2 ? go(walk_kernel<2, true, true>) : go(walk_kernel<3, true, true>);
     if (L.star) return L.dim == 2 ? go(walk_kernel<2, false, true>) : go(walk_kernel<3, false, true>);
     if (L.traversal == 2 || L.traversal == 3) return L.dim == 2 ? go(walk_kernel<2, true>) : go(walk_kernel<3, true>);
     return L.dim == 2 ? go(walk_kernel<2, false>) : go(walk_kernel<3, false>);

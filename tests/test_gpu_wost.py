@@ -160,6 +160,24 @@ def test_cylinder_flow_replay_and_closed_form(Solver):
     assert np.all(np.abs(du - due) <= 4.5 * dse + 2e-3)
 
 
+@pytest.mark.parametrize("name", ["slit", "thermal"])
+def test_walks_on_stars_do_not_depend_on_the_search_order(Solver, name):
+    # the Dirichlet tree's search order (per lane: 0; warp-wide: 2; routed: 3, the automatic
+    # choice from 128 Dirichlet elements up) changes no walk: records equal bit for bit
+    if name == "slit":
+        sc, opt, diff = scenes.slit_disk_scene(n_query=8), {"check_inside": 0}, False
+    else:
+        sc, opt, diff = scenes.thermal_scene(n_query=8), {}, True
+    recs = []
+    for t in (0, 2, 3, -1):
+        s = Solver(0)
+        s.load_scene(sc, traversal=t, **opt)
+        recs.append(s.walk_records(sc.query, 128, walk_id_base=7, differential=diff)["rec"].view(np.uint32))
+        s.sync()
+    for r in recs[1:]:
+        assert np.array_equal(recs[0], r)
+
+
 def test_queries_and_refusals_with_a_neumann_part(Solver):
     from paper_2405_12964_gb300.dwos import DwosError
     sc = scenes.quarter_disk_scene("field", n_query=8)
