@@ -125,7 +125,7 @@ __device__ __forceinline__ void sphere_dir(const U4& r, float* om) {
 // problem per launch; the Dirichlet part's distance queries take the launch's
 // search order, the Neumann queries per lane).
 template <int DIM, bool WIDE, bool STAR = false>
-__global__ void __launch_bounds__(256, STAR ? 2 : ((DIM == 2 || WIDE) ? 4 : 3))
+__global__ void __launch_bounds__(256, STAR ? 3 : ((DIM == 2 || WIDE) ? 4 : 3))
     walk_kernel(const DevProblem* __restrict__ g_probs, int n_probs, unsigned long long total,
                 DevCounters* __restrict__ ctr, DevCounters* __restrict__ zero_ctr,
                 const __grid_constant__ DevProblem p_arg) {
