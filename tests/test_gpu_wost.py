@@ -178,6 +178,29 @@ def test_walks_on_stars_do_not_depend_on_the_search_order(Solver, name):
         assert np.array_equal(recs[0], r)
 
 
+@pytest.mark.parametrize("name", ["thermal", "cube"])
+def test_walks_on_stars_at_scale_stay_in_the_domain(Solver, name):
+    # FP32 walks at scale meet what a few thousand oracle walks do not (rays ending where the
+    # sphere touches the Neumann part, tangent moves, convex edges, reflex corners, nested walks
+    # starting on a Neumann side, landing points within rounding of the Dirichlet part): over
+    # 4 launches of the thermal design (32 x 16384 walks) or the Neumann cube (64 x 4096, K = 2)
+    # no walk leaves the domain (a device error) and none reaches the step cap
+    if name == "thermal":
+        sc = scenes.thermal_scene(n_query=32, walks=16384)
+    else:
+        sc = scenes.cube_neumann_scene(n_query=64, walks=4096, K=2)
+    s = Solver(0)
+    s.load_scene(sc)
+    total = sc.query.shape[0] * sc.walks
+    for i in range(1, 5):
+        r = s.walk_records(sc.query, sc.walks, walk_id_base=i * total, differential=True, trace=True)
+        s.sync()
+        assert s.stats()["capped"] == 0
+        tr = r["trace"]
+        steps = np.where(tr != 0xFFFFFFFF, tr & 0x3FFFFFFF, 0)
+        assert steps.max() < 2000
+
+
 def test_queries_and_refusals_with_a_neumann_part(Solver):
     from paper_2405_12964_gb300.dwos import DwosError
     sc = scenes.quarter_disk_scene("field", n_query=8)
