@@ -7,7 +7,10 @@
  *         -Lap u + sigma u = f  in Omega,   u = g  on Gamma
  *     by walk on spheres (Miller et al., "Differential Walk on Spheres",
  *     TOG 2024: Eq. (bvp) of Sec. 3.2, the estimator Eq. (wos) and Algorithm 1
- *     of Sec. 3.3, Russian roulette as in Sec. 3.3);
+ *     of Sec. 3.3, Russian roulette as in Sec. 3.3; each step's ball has
+ *     radius d(x) - 1e-3 eps, a clearance that keeps FP32 landing points on
+ *     the domain's side of the boundary; any ball inside the domain gives an
+ *     unbiased step);
  *   - its derivative udot = du/dtheta with respect to every shape and
  *     boundary-data parameter theta in R^N, by differential walk on spheres
  *     (Eq. (bvp_deriv) of Sec. 4.1, the estimator Eq. (wos_deriv) and
@@ -212,10 +215,12 @@ dwos_status dwos_set_pde(dwos_ctx* ctx, float sigma, float f);
  * not be empty.  With a Neumann part every walk-running call (dwos_eval,
  * dwos_vjp, dwos_grad_l2, dwos_grad_l2_product, dwos_walk_records) runs walks
  * on stars (Sawhney et al. 2023): from x the walk takes the star-shaped
- * region of the ball of radius R = max(min(distance to the Dirichlet part,
- * distance to the closest Neumann silhouette point), eps) that x sees without
- * crossing the Neumann part, moves along a uniform direction (into the
- * domain's half-space when x lies on the Neumann part) to the first Neumann
+ * region of the ball of radius R = max(min(distance to the Dirichlet part
+ * - c, distance to the closest Neumann silhouette point), eps - c), with the
+ * clearance c = 1e-3 eps, that x sees without crossing the Neumann part,
+ * moves along a uniform direction (into the domain's half-space when x lies
+ * on the Neumann part, into the wedge of the two sides at an edge) to the
+ * first Neumann
  * crossing or the sphere, survives Russian roulette with probability
  * |S| t^(d-1) |G_R'(t)| for the step length t, and counts a source sample of
  * the ball where x sees it; walks end in the eps-shell of the Dirichlet part

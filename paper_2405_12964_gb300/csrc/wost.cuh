@@ -2,9 +2,10 @@
 // reflecting Neumann boundaries; the walk-on-stars estimator of Sawhney et
 // al. 2023).  From x the walk uses the star-shaped region St(x, R): the points
 // of the ball B(x, R) that x sees without crossing the Neumann part, with
-// R = max(min(distance to the Dirichlet part, distance to the closest
-// silhouette point of the Neumann part), eps).  A step samples a direction
-// (reflected into the inward half-space when x lies on the Neumann part),
+// R = max(min(distance to the Dirichlet part - c, distance to the closest
+// silhouette point of the Neumann part), eps - c), c = 1e-3 eps the Dirichlet
+// clearance.  A step samples a direction (turned into the domain when x lies
+// on the Neumann part: turn_inward),
 // casts the ray to the first Neumann crossing within R and moves there or to
 // x + R v; its survival weight is |S| t^(d-1) |G_R'(t)| for the step length t.
 #pragma once
