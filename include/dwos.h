@@ -242,7 +242,7 @@ dwos_status dwos_set_pde(dwos_ctx* ctx, float sigma, float f);
  * straight on through a vertex (flat across an edge: unit directions or
  * normals within a relative 1e-6) it has none.  Builds a BVH for each part
  * and one over the silhouette candidates (every vertex / edge where the part
- * ends or turns; every one if a Neumann vertex has a nonzero Jacobian row);
+ * ends or turns, and every one with a vertex whose Jacobian row is nonzero);
  * dwos_set_params updates all three.  Synchronises. */
 dwos_status dwos_set_neumann(dwos_ctx* ctx, const int32_t* flags, int mem);
 

@@ -662,18 +662,19 @@ dwos_status dwos_set_neumann(dwos_ctx* ctx, const int32_t* flags, int mem) {
     }
     // silhouette candidates: the sites where the Neumann part ends or does not run straight on
     // (a vertex between two segments whose directions agree, an edge between two coplanar
-    // triangles is a silhouette from no point); every site if the part moves with theta.  The
-    // walk kernel applies the same test with a relative 1e-6; a site is left out here only if
-    // it is straight within 1e-7, so that rounding cannot leave out one the kernel would keep.
+    // triangles is a silhouette from no point); every site one of whose vertices moves with
+    // theta.  The walk kernel applies the same test with a relative 1e-6; a site is left out
+    // here only if it is straight within 1e-7, so that rounding cannot leave out one the
+    // kernel would keep.
     std::vector<float> vh((size_t)ctx->n_vert * d);
     CK(cudaMemcpy(vh.data(), ctx->vert, sizeof(float) * vh.size(), cudaMemcpyDeviceToHost), "copy vertices");
-    bool moving = false;
+    std::vector<char> moves(ctx->n_vert, 0);
     if (ctx->n_param > 0 && ctx->jac) {
         std::vector<float> jh((size_t)ctx->n_vert * d * ctx->n_param);
         CK(cudaMemcpy(jh.data(), ctx->jac, sizeof(float) * jh.size(), cudaMemcpyDeviceToHost), "copy Jacobian");
-        for (size_t i = 0; i < en.size() && !moving; ++i)
-            for (size_t q = 0; q < (size_t)d * ctx->n_param && !moving; ++q)
-                moving = jh[(size_t)en[i] * d * ctx->n_param + q] != 0.0f;
+        for (size_t v = 0; v < (size_t)ctx->n_vert; ++v)
+            for (size_t q = 0; q < (size_t)d * ctx->n_param && !moves[v]; ++q)
+                moves[v] = jh[v * d * ctx->n_param + q] != 0.0f;
     }
     auto vx = [&](int v, int k) { return (double)vh[(size_t)d * v + k]; };
     std::vector<int32_t> sites, elem_s;
@@ -683,6 +684,7 @@ dwos_status dwos_set_neumann(dwos_ctx* ctx, const int32_t* flags, int mem) {
         for (int j = 0; j < d; ++j) {
             const int nb = adj[(size_t)d * c + j];
             bool straight = false;
+            const bool moving = nb >= 0 && (moves[t[0]] || moves[t[1]] || (d == 3 && moves[t[2]]) || moves[nb]);
             if (nb >= 0 && !moving) {
                 double u1[3] = {0, 0, 0}, u2[3] = {0, 0, 0};
                 if (d == 2) {   // directions w -> v and v -> z at v = t[j]
