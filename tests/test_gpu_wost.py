@@ -160,14 +160,16 @@ def test_cylinder_flow_replay_and_closed_form(Solver):
     assert np.all(np.abs(du - due) <= 4.5 * dse + 2e-3)
 
 
-@pytest.mark.parametrize("name", ["slit", "thermal"])
+@pytest.mark.parametrize("name", ["slit", "thermal", "cube8"])
 def test_walks_on_stars_do_not_depend_on_the_search_order(Solver, name):
     # the Dirichlet tree's search order (per lane: 0; warp-wide: 2; routed: 3, the automatic
     # choice from 128 Dirichlet elements up) changes no walk: records equal bit for bit
     if name == "slit":
         sc, opt, diff = scenes.slit_disk_scene(n_query=8), {"check_inside": 0}, False
-    else:
+    elif name == "thermal":
         sc, opt, diff = scenes.thermal_scene(n_query=8), {}, True
+    else:   # 3D, 256 Dirichlet triangles: the automatic order is the warp-wide one
+        sc, opt, diff = scenes.cube_neumann_scene(m=8, n_query=8, K=2), {}, True
     recs = []
     for t in (0, 2, 3, -1):
         s = Solver(0)
@@ -199,6 +201,19 @@ def test_walks_on_stars_at_scale_stay_in_the_domain(Solver, name):
         tr = r["trace"]
         steps = np.where(tr != 0xFFFFFFFF, tr & 0x3FFFFFFF, 0)
         assert steps.max() < 2000
+
+
+def test_fine_cube_replay_warp_wide(Solver):
+    # the 3D walk-on-stars kernel with the warp-wide search of the Dirichlet tree (256 triangles)
+    sc = scenes.cube_neumann_scene(m=8, n_query=8)
+    s, g, o, same = _replay(Solver, sc, 64, u_scale=1.0)
+    out = s.eval(sc.query, 4096, grad=True)
+    ue, due = cf.cube_linear(sc.query)
+    u, use = out["u"].cpu().numpy(), out["u_se"].cpu().numpy()
+    du, dse = out["du"].cpu().numpy(), out["du_se"].cpu().numpy()
+    assert np.all(np.abs(u - ue) <= 4.5 * use + 4e-3)
+    dse_ref = np.maximum(dse, np.median(dse, axis=0, keepdims=True))
+    assert np.all(np.abs(du - due) <= 4.5 * dse_ref + 0.08 * np.abs(due) + 0.02)
 
 
 def test_queries_and_refusals_with_a_neumann_part(Solver):
