@@ -16,7 +16,7 @@ the other configurations' headline figures (about a minute and a half in
 all; skip with --no-extras): "c3" walk-steps/s of the 200k-triangle 3D
 workload, "c4" the 64-problem batch against the same problems as separate
 calls, "c5" the learned control variate against the plain estimator
-(equal-time final losses over six seeds, gradient RMSE x seconds per
+(equal-time final losses over ten seeds, gradient RMSE x seconds per
 estimate), "wost" walks on stars on the 2D thermal design and a 3D cube, and
 "functional" the volume-integrated shape functional, each with the oracle's
 rate on a bounded sample.
@@ -52,7 +52,7 @@ WORKLOADS = {
     "c5": ("learned control variate on the 2D shape-from-diffusion geometry: 200 Adam steps (lr 1e-3) "
            "on 64 Fourier coefficients from a circle toward the star, walks/point annealed 256->1024, MLP "
            "5->64x4->2 (tcgen05 BF16 products, FP32 accumulation in TMEM) trained online on the walks' "
-           "estimates (4 Adam iterations on every second step's walks), 6 seeds; value = gradient RMSE x "
+           "estimates (4 Adam iterations on every second step's walks), 10 seeds; value = gradient RMSE x "
            "seconds of one estimate at "
            "1024 walks/point, the network's inference inside the timed region"),
     "ablation": "estimator ablation (product estimators, du/dn estimators, K, h) on the 2D workload",
@@ -433,13 +433,18 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
-def control_variate_summary(seeds=(3, 4, 5, 6, 7, 8), steps: int = 200, train_every: int = 2):
+def control_variate_summary(seeds=tuple(range(3, 13)), steps: int = 200, train_every: int = 2, tail: int = 10):
     """Config 5: the optimisation of the 2D shape-from-diffusion workload with
     and without the learned control variate, per seed: final losses of the CV
     run (the network trained on every train_every-th step's walks), of a plain
     run of the same number of steps and of a plain run given the CV run's wall
-    time (training included); and the gradient RMSE x seconds of one estimate
-    (network inference timed) at the start shape and midway."""
+    time (training included), each as the loss of the final iterate and as
+    the mean loss of the last `tail` iterates (the noisy optimiser's iterate
+    wanders about the optimum: the plain equal-time run's final loss moved 2x
+    with a change of its step count by 4); and the gradient RMSE x seconds of
+    one estimate (network inference timed) at the start shape and midway.
+    The plain equal-time run's step count is the CV run's time over the plain
+    run's per-step time, rounded up to a multiple of 10."""
     import numpy as np
     import torch
     from paper_2405_12964_gb300 import build, scenes
@@ -473,17 +478,25 @@ def control_variate_summary(seeds=(3, 4, 5, 6, 7, 8), steps: int = 200, train_ev
         th_p, hp, _ = optimize.run(sc, target, start, steps=steps, use_cv=False, seed=seed)
         th_c, hc, trainer = optimize.run(sc, target, start, steps=steps, use_cv=True, whole_walk=True, seed=seed,
                                          train_every=train_every)
-        # equal wall time: the plain optimiser gets the seconds the CV run took (training included)
-        steps_eq = max(steps, int(round(steps * hc.seconds[-1] / max(hp.seconds[-1], 1e-9))))
+        # equal wall time: the plain optimiser gets the seconds the CV run took (training included),
+        # rounded up to a multiple of 10 steps (at least equal time; the walks-per-point schedule
+        # anneals over the run, so the step count fixes the trajectory, and rounding keeps it the
+        # same from one measurement to the next)
+        steps_eq = max(steps, 10 * int(np.ceil(steps * hc.seconds[-1] / max(hp.seconds[-1], 1e-9) / 10)))
         th_e, he, _ = optimize.run(sc, target, start, steps=steps_eq, use_cv=False, seed=seed)
         lc, lp, le = true_loss(th_c), true_loss(th_p), true_loss(th_e)
-        runs.append({"seed": seed, "cv": {"final_loss": lc, "seconds": hc.seconds[-1],
+        tail_loss = lambda h: float(np.mean([true_loss(t) for t in h.thetas[-tail:]]))
+        mc, mp, me = tail_loss(hc), tail_loss(hp), tail_loss(he)
+        runs.append({"seed": seed, "cv": {"final_loss": lc, "tail_mean_loss": mc, "seconds": hc.seconds[-1],
                                           "median_var_ratio_last20": float(np.median(hc.var_ratio[-20:]))},
-                     "plain": {"final_loss": lp, "seconds": hp.seconds[-1]},
-                     "plain_equal_time": {"final_loss": le, "seconds": he.seconds[-1], "steps": steps_eq},
-                     "ratio_cv_over_plain_equal_time": lc / le})
+                     "plain": {"final_loss": lp, "tail_mean_loss": mp, "seconds": hp.seconds[-1]},
+                     "plain_equal_time": {"final_loss": le, "tail_mean_loss": me, "seconds": he.seconds[-1],
+                                          "steps": steps_eq},
+                     "ratio_cv_over_plain_equal_time": mc / me,
+                     "ratio_cv_over_plain_equal_time_final_iterate": lc / le})
     clk = clocks.stop()
     ratios = np.array([r["ratio_cv_over_plain_equal_time"] for r in runs])
+    ratios_f = np.array([r["ratio_cv_over_plain_equal_time_final_iterate"] for r in runs])
     mid = 0.5 * (start + target)
     rows = {}
     for name, th in [("start", start), ("midway", mid)]:
@@ -493,8 +506,10 @@ def control_variate_summary(seeds=(3, 4, 5, 6, 7, 8), steps: int = 200, train_ev
     return {"workload": WORKLOADS["c5"], "steps": steps, "train_every": train_every, "runs": runs,
             "equal_time_final_loss_ratio": {"geometric_mean": float(np.exp(np.mean(np.log(ratios)))),
                                             "min": float(ratios.min()), "max": float(ratios.max()),
-                                            "seeds": list(seeds)},
-            "final_loss_note": "1/2 sum (u - u_target)^2 of the final shape, u from 16384 walks per point",
+                                            "seeds": list(seeds), "loss": f"mean over the last {tail} iterates"},
+            "equal_time_final_iterate_loss_ratio": {"geometric_mean": float(np.exp(np.mean(np.log(ratios_f)))),
+                                                    "min": float(ratios_f.min()), "max": float(ratios_f.max())},
+            "final_loss_note": "1/2 sum (u - u_target)^2 of a shape, u from 16384 walks per point",
             "gradient_rmse_x_seconds": rows, "clocks": clk}
 
 

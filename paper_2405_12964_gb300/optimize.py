@@ -97,6 +97,7 @@ class History:
     seconds: List[float] = field(default_factory=list)
     var_ratio: List[float] = field(default_factory=list)     # median per-point Var(u with CV) / Var(u)
     mlp_loss: List[float] = field(default_factory=list)
+    thetas: List[np.ndarray] = field(default_factory=list)   # the iterate after each step
 
 
 class ControlVariateTrainer:
@@ -173,6 +174,7 @@ def run(scene, theta_target: np.ndarray, theta_start: np.ndarray, steps: int = 2
         opt.step(g)
         hist.loss.append(float(out["loss"][0]))
         hist.theta_err.append(float(np.linalg.norm(opt.theta - theta_target)))
+        hist.thetas.append(opt.theta.copy())
         hist.wpp.append(W)
         hist.seconds.append(total)
         if use_cv:
