@@ -198,3 +198,16 @@ def cylinder_flow(x, a: float):
     r2 = x[:, 0] ** 2 + x[:, 1] ** 2
     u = x[:, 0] * (1.0 + a * a / r2)
     return u, u[:, None].copy()
+
+
+def sphere_flow(x, a: float):
+    """Potential flow past a sphere: u = x (1 + a^3 / (2 r^3)) = f(r) cos(theta)
+    with f = r + a^3 / (2 r^2), harmonic where r > 0 (f'' + 2 f'/r - 2 f/r^2 = 0)
+    and du/dr = f'(a) cos(theta) = 0 on the sphere r = a: with a reflecting
+    Neumann sphere of radius a and Dirichlet data u on an outer boundary, the
+    solution is u itself.  With the data scaled by a parameter c (at c = 1),
+    du/dc = u."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    r3 = np.sum(x * x, axis=1) ** 1.5
+    u = x[:, 0] * (1.0 + a ** 3 / (2.0 * r3))
+    return u, u[:, None].copy()

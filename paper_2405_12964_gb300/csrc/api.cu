@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "ctx.h"
+#include "dwos_device.cuh"
 #include "dwos_internal.h"
 
 using namespace dwos;
@@ -103,6 +104,167 @@ dwos_status set_device(dwos_ctx* ctx) {
 // zero for the next walk launch, which zeroes this one in turn).
 inline DevCounters* cur_ctr(dwos_ctx* ctx) { return ctx->d_ctr + ctx->ctr_cur; }
 
+// Normal cones of the silhouette candidates' tree.  A site (an endpoint in 2D,
+// an edge in 3D) with its two normals n1, n2 oriented consistently across it
+// is a silhouette from x only where n1 . (x - p) and n2 . (x - p) have
+// opposite signs (the silhouette rule restated: 2D n = perp of the segment
+// directions w -> v and v -> z, 3D n1 = (b - a) x (c - a), n2 = (z - a) x (b - a));
+// a whole pair may be negated.  Each leaf's cone covers its sites' pairs,
+// oriented so that the element's own normal is the same for all its sites;
+// each node's cone covers its children's.  A site that ends the Neumann part,
+// or any site when the part moves with theta, gets the whole sphere.
+// The cones are built and tested from this many candidate elements up, for a
+// Neumann part that does not move (walk kernel ms with / without them:
+// icosphere of 200k triangles 0.97 s / 6.8 s, 20k 0.31 / 0.79 s; but 720
+// triangles 41 / 35 ms, thermal slab 7.5 / 5.6 ms: the test costs more than
+// it prunes on small trees).
+constexpr int kConeMinSites = 1024;
+
+struct Cone {
+    double a[3] = {0, 0, 0};
+    double t = 0;
+    bool full = false, empty = true;
+};
+
+static void cone_add(Cone& c, const Cone& d) {
+    if (d.empty || c.full) return;
+    if (d.full) { c.full = true; c.empty = false; return; }
+    if (c.empty) { c = d; return; }
+    const double dot = c.a[0] * d.a[0] + c.a[1] * d.a[1] + c.a[2] * d.a[2];
+    const double phi = std::acos(std::max(-1.0, std::min(1.0, dot)));
+    if (phi + d.t <= c.t) return;
+    if (phi + c.t <= d.t) { c = d; return; }
+    const double t = 0.5 * (phi + c.t + d.t);
+    if (t >= M_PI || phi >= M_PI - 1e-9) { c.full = true; return; }
+    const double r = t - c.t;          // turn c's axis toward d's by r
+    if (phi > 1e-12) {
+        const double s0 = std::sin(phi - r) / std::sin(phi), s1 = std::sin(r) / std::sin(phi);
+        double n = 0;
+        for (int i = 0; i < 3; ++i) { c.a[i] = s0 * c.a[i] + s1 * d.a[i]; n += c.a[i] * c.a[i]; }
+        n = std::sqrt(n);
+        for (int i = 0; i < 3; ++i) c.a[i] /= n;
+    }
+    c.t = t;
+}
+
+static Cone cone_of(const double* n) {
+    Cone c;
+    const double l = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    if (!(l > 0)) { c.full = true; c.empty = false; return c; }
+    for (int i = 0; i < 3; ++i) c.a[i] = n[i] / l;
+    c.empty = false;
+    return c;
+}
+
+static dwos_status build_silhouette_cones(dwos_ctx* ctx) {
+    const int d = ctx->dim;
+    const BvhBuffers& b = ctx->bvh_s;
+    const int n_int = b.n_internal, n_leaf = b.n_tree + b.n_big;
+    std::vector<Cone> leaf(n_leaf), node(std::max(n_int, 0));
+    std::vector<int32_t> prim(n_leaf);
+    CK(cudaMemcpy(prim.data(), b.prim_elem, sizeof(int32_t) * n_leaf, cudaMemcpyDeviceToHost), "copy leaves");
+    const std::vector<float>& V = ctx->vert_neu_h;
+    auto vx = [&](int v, int k) { return (double)V[(size_t)d * v + k]; };
+    // the silhouette rule's collinear tolerance is relative to the distance from x to the
+    // site's other vertices: as an angle about the perpendicular it reaches 1e-4 (distance) /
+    // (segment length, 3D: triangle height over the edge); the smallest such length over the
+    // candidates and the largest element size bound it in the walk kernel
+    double h_min = INFINITY, l_max = 0;
+    auto dist = [&](int p, int q) {
+        double r = 0;
+        for (int k = 0; k < d; ++k) r += (vx(p, k) - vx(q, k)) * (vx(p, k) - vx(q, k));
+        return std::sqrt(r);
+    };
+    for (int l = 0; l < n_leaf; ++l) {
+        Cone& c = leaf[l];
+        if (ctx->neu_moving) { c.full = true; c.empty = false; continue; }
+        const int site = ctx->sites_h[prim[l]];
+        const int e = site >> 3, mask = site & 7;
+        const int* t = ctx->elem_n_h.data() + (size_t)d * e;
+        double ne[3] = {0, 0, 0};
+        if (d == 2) {
+            ne[0] = vx(t[1], 1) - vx(t[0], 1);
+            ne[1] = -(vx(t[1], 0) - vx(t[0], 0));
+        } else {
+            double u[3], w[3];
+            for (int k = 0; k < 3; ++k) { u[k] = vx(t[1], k) - vx(t[0], k); w[k] = vx(t[2], k) - vx(t[0], k); }
+            ne[0] = u[1] * w[2] - u[2] * w[1]; ne[1] = u[2] * w[0] - u[0] * w[2]; ne[2] = u[0] * w[1] - u[1] * w[0];
+        }
+        cone_add(c, cone_of(ne));
+        const double len_e = std::sqrt(ne[0] * ne[0] + ne[1] * ne[1] + ne[2] * ne[2]);
+        for (int j = 0; j < d; ++j) l_max = std::max(l_max, dist(t[j], t[(j + 1) % d]));
+        for (int j = 0; j < d; ++j) {
+            if (!((mask >> j) & 1)) continue;
+            const int nb = ctx->nadj_h[(size_t)d * e + j];
+            if (nb < 0) { c.full = true; break; }
+            if (d == 2) {
+                h_min = std::min(h_min, std::min(len_e, dist(nb, t[j])));
+                l_max = std::max(l_max, dist(nb, t[j]));
+            } else {
+                const double lab = dist(t[j], t[(j + 1) % 3]);
+                double ab[3], az[3], cr[3];
+                for (int k = 0; k < 3; ++k) { ab[k] = vx(t[(j + 1) % 3], k) - vx(t[j], k); az[k] = vx(nb, k) - vx(t[j], k); }
+                cr[0] = az[1] * ab[2] - az[2] * ab[1]; cr[1] = az[2] * ab[0] - az[0] * ab[2]; cr[2] = az[0] * ab[1] - az[1] * ab[0];
+                const double h2 = std::sqrt(cr[0] * cr[0] + cr[1] * cr[1] + cr[2] * cr[2]) / lab;
+                h_min = std::min(h_min, std::min(len_e / lab, h2));
+                l_max = std::max(l_max, std::max(dist(nb, t[j]), dist(nb, t[(j + 1) % 3])));
+            }
+            double n2[3] = {0, 0, 0};
+            if (d == 2) {   // v -> z; the pair (perp(v - w), perp(z - v)) negated where perp(v - w) = -ne
+                const int v = t[j];
+                const double sgn = j == 1 ? 1.0 : -1.0;
+                n2[0] = sgn * (vx(nb, 1) - vx(v, 1));
+                n2[1] = -sgn * (vx(nb, 0) - vx(v, 0));
+            } else {        // (z - a) x (b - a) for the edge a = t[j], b = t[j + 1]
+                const int a = t[j], bb = t[(j + 1) % 3];
+                double ab[3], az[3];
+                for (int k = 0; k < 3; ++k) { ab[k] = vx(bb, k) - vx(a, k); az[k] = vx(nb, k) - vx(a, k); }
+                n2[0] = az[1] * ab[2] - az[2] * ab[1]; n2[1] = az[2] * ab[0] - az[0] * ab[2]; n2[2] = az[0] * ab[1] - az[1] * ab[0];
+            }
+            cone_add(c, cone_of(n2));
+        }
+    }
+    if (n_int > 0) {
+        const int f4 = d == 2 ? BvhLayout<2>::kNodeF4 : BvhLayout<3>::kNodeF4;
+        std::vector<float4> nodes((size_t)n_int * f4);
+        CK(cudaMemcpy(nodes.data(), b.nodes, sizeof(float4) * nodes.size(), cudaMemcpyDeviceToHost), "copy nodes");
+        // post-order over the tree from the root (node 0)
+        std::vector<std::pair<int, int>> stack{{0, 0}};
+        while (!stack.empty()) {
+            auto& top = stack.back();
+            const float4 m = nodes[(size_t)f4 * top.first + f4 - 1];
+            int ch[2];
+            std::memcpy(&ch[0], &m.x, sizeof(int));
+            std::memcpy(&ch[1], &m.y, sizeof(int));
+            if (top.second < 2) {
+                const int c = ch[top.second++];
+                if (c >= 0 && c != kEmptyChild) stack.push_back({c, 0});
+                continue;
+            }
+            Cone& c = node[top.first];
+            for (int k = 0; k < 2; ++k) {
+                if (ch[k] == kEmptyChild) continue;
+                cone_add(c, ch[k] >= 0 ? node[ch[k]] : leaf[~ch[k]]);
+            }
+            stack.pop_back();
+        }
+    }
+    std::vector<float4> out((size_t)std::max(n_int, 0) + n_leaf);
+    auto pack = [](const Cone& c) {
+        if (c.full || c.empty) return make_float4(0.0f, 0.0f, 0.0f, 4.0f);
+        return make_float4((float)c.a[0], (float)c.a[1], (float)c.a[2], (float)c.t + 1e-6f);
+    };
+    for (int i = 0; i < n_int; ++i) out[i] = pack(node[i]);
+    for (int l = 0; l < n_leaf; ++l) out[(size_t)std::max(n_int, 0) + l] = pack(leaf[l]);
+    ctx->cone_tol = h_min > 0 && std::isfinite(h_min) ? (float)(1e-4 / h_min) : 1e30f;
+    ctx->cone_lmax = (float)l_max;
+    if (ctx->sil_cones) cudaFree(ctx->sil_cones);
+    ctx->sil_cones = nullptr;
+    CK(cudaMalloc(&ctx->sil_cones, sizeof(float4) * out.size()), "alloc cones");
+    CK(cudaMemcpy(ctx->sil_cones, out.data(), sizeof(float4) * out.size(), cudaMemcpyHostToDevice), "copy cones");
+    return DWOS_OK;
+}
+
 dwos_status rebuild(dwos_ctx* ctx) {
     ctx->inside_cached = -1;   // the inside flags belong to the old geometry
     ctx->refits = 0;
@@ -113,8 +275,12 @@ dwos_status rebuild(dwos_ctx* ctx) {
     // walk on stars: one tree over the Dirichlet part (distance queries), one over the Neumann part
     CK(bvh_build(ctx->bvh, ctx->dim, ctx->vert, ctx->elem_d, ctx->n_elem - ctx->n_neumann, ctx->stream), "BVH build");
     CK(bvh_build(ctx->bvh_n, ctx->dim, ctx->vert, ctx->elem_n, ctx->n_neumann, ctx->stream), "Neumann BVH build");
-    if (ctx->n_sites > 0)
+    if (ctx->n_sites > 0) {
         CK(bvh_build(ctx->bvh_s, ctx->dim, ctx->vert, ctx->elem_s, ctx->n_sites, ctx->stream), "silhouette BVH build");
+        CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+        if (ctx->n_sites >= kConeMinSites && !ctx->neu_moving)
+            if (dwos_status st = build_silhouette_cones(ctx)) return st;
+    }
     DevNeumann N;
     N.nodes = ctx->bvh_n.nodes;
     N.prims = ctx->bvh_n.prims;
@@ -137,6 +303,11 @@ dwos_status rebuild(dwos_ctx* ctx) {
     N.sil_n_tree = sil ? ctx->bvh_s.n_tree : 0;
     N.sil_n_big = sil ? ctx->bvh_s.n_big : 0;
     N.n_sites = ctx->n_sites;
+    const bool cones = sil && ctx->n_sites >= kConeMinSites && !ctx->neu_moving && ctx->sil_cones;
+    N.sil_cone_node = cones ? ctx->sil_cones : nullptr;
+    N.sil_cone_leaf = cones ? ctx->sil_cones + std::max(ctx->bvh_s.n_internal, 0) : nullptr;
+    N.cone_tol = ctx->cone_tol;
+    N.cone_lmax = ctx->cone_lmax;
     ctx->neu_host = N;
     CK(cudaMemcpyAsync(ctx->d_neu, &ctx->neu_host, sizeof(N), cudaMemcpyHostToDevice, ctx->stream),
        "copy Neumann part");
@@ -291,6 +462,7 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     L.n_sm = ctx->n_sm;
     L.traversal = P.traversal;
     L.star = P.neu != nullptr;
+    L.cones = L.star && ctx->neu_host.sil_cone_node != nullptr;
     CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
     int blocks = 0;
     CK(launch_walks(L, nullptr, 1, total, cur_ctr(ctx), ctx->stream, &blocks, &P, ctx->d_ctr + (ctx->ctr_cur ^ 1)),
@@ -413,7 +585,7 @@ void dwos_destroy(dwos_ctx* ctx) {
                     ctx->xq, ctx->valid, ctx->wvec, ctx->out, ctx->acc_vert, ctx->trace, ctx->dbg, ctx->misc_f,
                     ctx->misc_i, ctx->misc_u, ctx->xq_prev, ctx->d_ctr, ctx->d_err, ctx->pw, ctx->vert_active,
                     ctx->misc_d, ctx->elem_d, ctx->elem_n, ctx->dmap, ctx->nadj, ctx->d_neu, ctx->inside_tmp,
-                    ctx->q_start, ctx->behind, ctx->behind_in, ctx->sites, ctx->elem_s};
+                    ctx->q_start, ctx->behind, ctx->behind_in, ctx->sites, ctx->elem_s, ctx->sil_cones};
     bvh_free(ctx->bvh_n);
     bvh_free(ctx->bvh_s);
     for (void* p : bufs) if (p) cudaFree(p);
@@ -493,8 +665,9 @@ dwos_status dwos_set_boundary(dwos_ctx* ctx, int dim, int n_vert, const float* v
     ctx->elem = nullptr;
     ctx->have_boundary = false;
     for (void* p : {(void*)ctx->elem_d, (void*)ctx->elem_n, (void*)ctx->dmap, (void*)ctx->nadj, (void*)ctx->sites,
-                    (void*)ctx->elem_s}) if (p) cudaFree(p);
+                    (void*)ctx->elem_s, (void*)ctx->sil_cones}) if (p) cudaFree(p);
     ctx->elem_d = ctx->elem_n = ctx->dmap = ctx->nadj = ctx->sites = ctx->elem_s = nullptr;
+    ctx->sil_cones = nullptr;
     ctx->n_neumann = 0;
     ctx->n_sites = 0;
     const size_t nv = (size_t)n_vert * dim;
@@ -629,8 +802,9 @@ dwos_status dwos_set_neumann(dwos_ctx* ctx, const int32_t* flags, int mem) {
     const int n_n = (int)(en.size() / d);
     if (n_n > 0 && n_n == n) return fail(ctx, DWOS_ERR_INVALID_ARG, "the boundary needs a Dirichlet part");
     for (void* p : {(void*)ctx->elem_d, (void*)ctx->elem_n, (void*)ctx->dmap, (void*)ctx->nadj, (void*)ctx->sites,
-                    (void*)ctx->elem_s}) if (p) cudaFree(p);
+                    (void*)ctx->elem_s, (void*)ctx->sil_cones}) if (p) cudaFree(p);
     ctx->elem_d = ctx->elem_n = ctx->dmap = ctx->nadj = ctx->sites = ctx->elem_s = nullptr;
+    ctx->sil_cones = nullptr;
     ctx->n_neumann = 0;
     ctx->n_sites = 0;
     if (n_n == 0) return rebuild(ctx);            // every element Dirichlet again
@@ -714,6 +888,12 @@ dwos_status dwos_set_neumann(dwos_ctx* ctx, const int32_t* flags, int mem) {
         CK(cudaMemcpy(ctx->elem_s, elem_s.data(), sizeof(int32_t) * elem_s.size(), cudaMemcpyHostToDevice), "copy");
     }
     ctx->n_sites = (int)sites.size();
+    ctx->elem_n_h = en;
+    ctx->nadj_h = adj;
+    ctx->sites_h = sites;
+    ctx->vert_neu_h = vh;
+    ctx->neu_moving = false;
+    for (size_t i = 0; i < en.size() && !ctx->neu_moving; ++i) ctx->neu_moving = moves[en[i]] != 0;
     CK(cudaMalloc(&ctx->elem_d, sizeof(int32_t) * ed.size()), "alloc Dirichlet elements");
     CK(cudaMalloc(&ctx->elem_n, sizeof(int32_t) * en.size()), "alloc Neumann elements");
     CK(cudaMalloc(&ctx->dmap, sizeof(int32_t) * dmap.size()), "alloc element map");

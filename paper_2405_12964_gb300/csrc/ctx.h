@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <string>
+#include <vector>
 
 #include "dwos_internal.h"
 
@@ -43,6 +44,13 @@ struct dwos_ctx {
     int* sites = nullptr;
     int* elem_s = nullptr;       // per entry of sites its element's vertices (what their BVH bounds)
     dwos::BvhBuffers bvh_s;      // over the silhouette candidates
+    float4* sil_cones = nullptr; // their tree's normal cones: internal nodes, then leaves
+    // host copies for the cones: compact Neumann elements, neighbours, site entries, vertices at
+    // dwos_set_neumann, and whether a Neumann vertex moves with theta (then no cones)
+    std::vector<int32_t> elem_n_h, nadj_h, sites_h;
+    std::vector<float> vert_neu_h;
+    bool neu_moving = false;
+    float cone_tol = 1e30f, cone_lmax = 0.0f;               // DevNeumann::cone_tol, cone_lmax
     dwos::DevNeumann* d_neu = nullptr;
     dwos::DevNeumann neu_host{};                          // what d_neu holds
     float4* q_start = nullptr; size_t q_start_cap = 0;    // per query: start on the Neumann part

@@ -33,6 +33,16 @@ struct DevNeumann {
     const int* sil_prim;        // leaf -> entry of sites
     const int* sites;           // 8 e + mask: compact Neumann element e, bit j for its endpoint / edge j
     int sil_n_internal, sil_n_tree, sil_n_big, n_sites;   // n_sites: entries of sites
+    // normal cones of that tree (NULL: none): per internal node and per leaf an axis (xyz) and a
+    // half-angle (w, radians; >= 3 for the whole sphere) covering the sites' normal pairs,
+    // oriented consistently across each site (a site is a silhouette from x only where its two
+    // normals n satisfy n . (x - p) with opposite signs)
+    const float4* sil_cone_node;
+    const float4* sil_cone_leaf;
+    // the silhouette rule's collinear tolerance seen as an angle about the perpendicular: at most
+    // cone_tol (distance + cone_lmax), cone_tol = 1e-4 / (the smallest segment length, 3D: triangle
+    // height over a candidate edge), cone_lmax the largest element size
+    float cone_tol, cone_lmax;
 };
 
 // Everything a walk needs about one problem.  Copied to the device (and, in
@@ -174,7 +184,8 @@ struct WalkLaunch {
     int blocks_per_sm;
     int n_sm;
     int traversal = 0;          // 2, 3: warp-wide search (every problem of the launch has wide_ok)
-    bool star = false;          // walk on stars (one problem with a Neumann part; traversal 0 or 1)
+    bool star = false;          // walk on stars (one problem with a Neumann part)
+    bool cones = false;         // walk on stars whose silhouette tree has normal cones
 };
 // The problems come from the device table d_probs, or (one problem, d_probs
 // NULL) by value from host_prob.  zero_counters, when given, is zeroed by the
@@ -183,7 +194,7 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
                          unsigned long long total_work, DevCounters* d_counters, cudaStream_t stream,
                          int* blocks_used, const DevProblem* host_prob = nullptr,
                          DevCounters* zero_counters = nullptr);
-int walk_max_blocks_per_sm(int dim, int block_size, int traversal = 0, bool star = false);
+int walk_max_blocks_per_sm(int dim, int block_size, int traversal = 0, bool star = false, bool cones = false);
 // Query points on the Neumann part: per point the closest Neumann element if it
 // lies within tol of it (q_start w = its compact index, xyz = its unit normal,
 // not yet oriented) and the point 1e-3 of the element's size behind its centre

@@ -124,7 +124,7 @@ __device__ __forceinline__ void sphere_dir(const U4& r, float* om) {
 // STAR: walk on stars over a boundary with a reflecting Neumann part (one
 // problem per launch; the Dirichlet part's distance queries take the launch's
 // search order, the Neumann queries per lane).
-template <int DIM, bool WIDE, bool STAR = false>
+template <int DIM, bool WIDE, bool STAR = false, bool CONES = false>
 __global__ void __launch_bounds__(256, STAR ? 3 : ((DIM == 2 || WIDE) ? 4 : 3))
     walk_kernel(const DevProblem* __restrict__ g_probs, int n_probs, unsigned long long total,
                 DevCounters* __restrict__ ctr, DevCounters* __restrict__ zero_ctr,
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(256, STAR ? 3 : ((DIM == 2 || WIDE) ? 4 : 3))
             // walk on stars: R from the Dirichlet distance and the Neumann silhouettes
             const unsigned long long wid = P.walk_id_base + local;
             bool ok1 = true, ok2 = true, ok3 = true;
-            const float sd2 = silhouette_dist2<DIM>(NS, x, best2, on_e, on2, ok1);
+            const float sd2 = silhouette_dist2<DIM, CONES>(NS, x, best2, on_e, on2, ok1);
             // R = max(min(d_D - c, d_sil), eps - c), c = 1e-3 eps the Dirichlet clearance
             const float R = fmaxf(fminf(sqrtf(sd2), fmaf(-1e-3f, P.eps, d)), fmaf(-1e-3f, P.eps, P.eps));
             if (P.f != 0.0f) {   // source: a point of the ball, counted if x sees it
@@ -777,15 +777,19 @@ cudaError_t launch_neumann_orient(int n, const int* behind_inside, float4* q_sta
     return cudaGetLastError();
 }
 
-int walk_max_blocks_per_sm(int dim, int block_size, int traversal, bool star) {
+int walk_max_blocks_per_sm(int dim, int block_size, int traversal, bool star, bool cones) {
     int n = 0;
     const size_t smem = walk_smem_bytes(1, block_size, traversal, dim, star);
-    if (star && (traversal == 2 || traversal == 3)) {
-        if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<2, true, true>, block_size, smem);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<3, true, true>, block_size, smem);
-    } else if (star) {
-        if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<2, false, true>, block_size, smem);
-        else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<3, false, true>, block_size, smem);
+    const bool wide = traversal == 2 || traversal == 3;
+    auto occ = [&](auto kernel) { cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block_size, smem); };
+    if (star) {
+        if (dim == 2) {
+            if (wide) cones ? occ(walk_kernel<2, true, true, true>) : occ(walk_kernel<2, true, true>);
+            else cones ? occ(walk_kernel<2, false, true, true>) : occ(walk_kernel<2, false, true>);
+        } else {
+            if (wide) cones ? occ(walk_kernel<3, true, true, true>) : occ(walk_kernel<3, true, true>);
+            else cones ? occ(walk_kernel<3, false, true, true>) : occ(walk_kernel<3, false, true>);
+        }
     } else if (traversal == 2 || traversal == 3) {
         if (dim == 2) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<2, true>, block_size, smem);
         else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, walk_kernel<3, true>, block_size, smem);
@@ -809,7 +813,7 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
     const int bs = L.block_size;
     if (L.star && n_probs != 1) return cudaErrorInvalidValue;
     int per_sm = L.blocks_per_sm > 0 ? L.blocks_per_sm
-                                     : walk_max_blocks_per_sm(L.dim, bs, L.traversal, L.star);
+                                     : walk_max_blocks_per_sm(L.dim, bs, L.traversal, L.star, L.cones);
     if (per_sm < 1) per_sm = 1;
     long long blocks = (long long)per_sm * L.n_sm;
     const long long need = (long long)((total + bs - 1) / bs);
@@ -829,9 +833,15 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
         kernel<<<(int)blocks, bs, smem, stream>>>(d_probs, n_probs, total, d_counters, zero_counters, P1);
         return cudaGetLastError();
     };
-    if (L.star && (L.traversal == 2 || L.traversal == 3))
-        return L.dim == 2 ? go(walk_kernel<2, true, true>) : go(walk_kernel<3, true, true>);
-    if (L.star) return L.dim == 2 ? go(walk_kernel<2, false, true>) : go(walk_kernel<3, false, true>);
+    if (L.star) {
+        const bool wide = L.traversal == 2 || L.traversal == 3;
+        if (L.cones) {
+            if (wide) return L.dim == 2 ? go(walk_kernel<2, true, true, true>) : go(walk_kernel<3, true, true, true>);
+            return L.dim == 2 ? go(walk_kernel<2, false, true, true>) : go(walk_kernel<3, false, true, true>);
+        }
+        if (wide) return L.dim == 2 ? go(walk_kernel<2, true, true>) : go(walk_kernel<3, true, true>);
+        return L.dim == 2 ? go(walk_kernel<2, false, true>) : go(walk_kernel<3, false, true>);
+    }
     if (L.traversal == 2 || L.traversal == 3) return L.dim == 2 ? go(walk_kernel<2, true>) : go(walk_kernel<3, true>);
     return L.dim == 2 ? go(walk_kernel<2, false>) : go(walk_kernel<3, false>);
 }

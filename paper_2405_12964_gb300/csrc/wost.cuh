@@ -14,9 +14,10 @@
 
 namespace dwos {
 
-// Leaves of a binary BVH in near-first order with pruning: key(lo, hi) is a
-// lower bound of what any leaf under the box can give and leaf(l) may lower
-// `best`; a box whose key exceeds best is skipped.  The outsized leaves after
+// Leaves of a binary BVH in near-first order with pruning: key(lo, hi, child)
+// is a lower bound of what any leaf under the child (>= 0 an internal node,
+// < 0 ~leaf) with that box can give and leaf(l) may lower `best`; a box whose
+// key exceeds best is skipped.  The outsized leaves after
 // the tree's are offered first.  Stackless: the walk back up refetches each
 // parent and re-orders its children by the same keys.  Returns false if the
 // node budget ran out.
@@ -33,8 +34,8 @@ __device__ __forceinline__ bool bvh_best_first(const float4* __restrict__ nodes,
         float lo0[DIM], hi0[DIM], lo1[DIM], hi1[DIM];
         int c0, c1, parent;
         load_node<DIM>(nodes, node, lo0, hi0, lo1, hi1, c0, c1, parent);
-        const float k0 = c0 == kEmptyChild ? kInf : key(lo0, hi0);
-        const float k1 = c1 == kEmptyChild ? kInf : key(lo1, hi1);
+        const float k0 = c0 == kEmptyChild ? kInf : key(lo0, hi0, c0);
+        const float k1 = c1 == kEmptyChild ? kInf : key(lo1, hi1, c1);
         const bool first0 = k0 <= k1;
         const int nearc = first0 ? c0 : c1, farc = first0 ? c1 : c0;
         const float kn = first0 ? k0 : k1, kf = first0 ? k1 : k0;
@@ -108,6 +109,37 @@ __device__ __forceinline__ bool element_is(const DevNeumann& N, int f, int p, in
     return all;
 }
 
+// True if the box (lo, hi) of the silhouette tree's child (>= 0 an internal
+// node, < 0 ~leaf) holds no silhouette point seen from x: its normal cone
+// shows that every normal of its sites has one sign against every direction
+// from the box to x, with room to spare for the silhouette rule's collinear
+// tolerance: |phi - pi/2| > theta + beta + m (phi: cone axis to the box
+// centre's direction, beta: the box's angular radius seen from x; m = 1.1 tau
+// + 2e-3 rad for FP32 rounding, tau the tolerance's angle, cone_tol (d + rho +
+// cone_lmax), bounded by 0.5, above which nothing is skipped).
+template <int DIM>
+__device__ __forceinline__ bool cone_prunes(const DevNeumann& N, const float* x, const float* lo, const float* hi,
+                                         int child) {
+    const float4 cn = child >= 0 ? __ldg(N.sil_cone_node + child) : __ldg(N.sil_cone_leaf + ~child);
+    if (cn.w >= 3.0f) return false;
+    const float ax[3] = {cn.x, cn.y, cn.z};
+    float r2 = 0.0f, d2 = 0.0f, dot = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+        const float hh = 0.5f * (hi[i] - lo[i]), w = x[i] - 0.5f * (lo[i] + hi[i]);
+        r2 = fmaf(hh, hh, r2);
+        d2 = fmaf(w, w, d2);
+        dot = fmaf(ax[i], w, dot);
+    }
+    if (d2 <= r2) return false;
+    const float d = sqrtf(d2), rho = sqrtf(r2);
+    const float tau = N.cone_tol * (d + rho + N.cone_lmax);
+    if (tau >= 0.5f) return false;
+    const float beta = asinf(fminf(rho / d, 1.0f));
+    const float phi = acosf(fminf(fmaxf(dot / d, -1.0f), 1.0f));
+    return fabsf(phi - 1.57079633f) > cn.w + beta + fmaf(1.1f, tau, 2e-3f);
+}
+
 // Squared distance from x to the closest silhouette point of the Neumann part
 // below `bound2` (bound2 itself if there is none), over the candidate sites
 // (DevNeumann::sites): vertices (2D) or edges (3D) where the part ends, or
@@ -115,11 +147,19 @@ __device__ __forceinline__ bool element_is(const DevNeumann& N, int f, int p, in
 // through x (silhouette_rule) without the part running straight on there.
 // The walk sits on elements on and on2 (-1: none): a side test whose points
 // span one of them is zero by definition (x lies on it).
-template <int DIM>
+// CONES: the tree has normal cones (a separate kernel instantiation: the cone
+// test's code costs the kernels without cones 4-9 % even where it never runs).
+template <int DIM, bool CONES>
 __device__ __forceinline__ float silhouette_dist2(const DevNeumann& N, const float* x, float bound2, int on, int on2,
                                                   bool& ok) {
     float best = bound2;
-    auto key = [&](const float* lo, const float* hi) { return box_dist2<DIM>(x, lo, hi); };
+    auto key = [&](const float* lo, const float* hi, int child) {
+        const float k = box_dist2<DIM>(x, lo, hi);
+        if constexpr (CONES) {
+            if (k < best && cone_prunes<DIM>(N, x, lo, hi, child)) return kInf;
+        }
+        return k;
+    };
     auto test = [&](int e, int j) {
         const int* ev = N.elem + (size_t)DIM * e;
         if (DIM == 2) {
@@ -315,7 +355,7 @@ __device__ __forceinline__ float ray_neumann(const DevNeumann& N, const float* x
     float inv[DIM];
 #pragma unroll
     for (int k = 0; k < DIM; ++k) inv[k] = 1.0f / v[k];
-    auto key = [&](const float* lo, const float* hi) { return ray_box_entry<DIM>(x, inv, lo, hi); };
+    auto key = [&](const float* lo, const float* hi, int) { return ray_box_entry<DIM>(x, inv, lo, hi); };
     auto leaf = [&](int l) {
         const int e = __ldg(N.prim_elem + l);
         if (e == skip || e == skip2) return;

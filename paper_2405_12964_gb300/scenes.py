@@ -564,6 +564,58 @@ def cylinder_flow_scene(a: float = 0.4, n_circle: int = 300, n_side: int = 64, n
     return sc
 
 
+def box3d_grid(m: int, half: float = 1.0):
+    """The cube [-half, half]^3 with each face split into 2 m^2 triangles
+    (shared vertices merged)."""
+    pts, tris = [], []
+    u = np.linspace(-half, half, m + 1)
+    for axis in range(3):
+        for sgn in (-half, half):
+            a, b = [k for k in range(3) if k != axis]
+            base = sum(len(p) for p in pts)
+            P = np.zeros(((m + 1) ** 2, 3))
+            P[:, axis] = sgn
+            P[:, a] = np.repeat(u, m + 1)
+            P[:, b] = np.tile(u, m + 1)
+            pts.append(P)
+            for i in range(m):
+                for j in range(m):
+                    p0 = base + i * (m + 1) + j
+                    tris += [(p0, p0 + m + 1, p0 + 1), (p0 + 1, p0 + m + 1, p0 + m + 2)]
+    flat = np.concatenate(pts, 0)
+    key = np.round(flat * 1e6).astype(np.int64)
+    _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    return flat[first], inv.reshape(-1)[np.array(tris)].astype(np.int32)
+
+
+def sphere_flow_scene(a: float = 0.4, freq: int = 6, m: int = 8, n_query: int = 8, walks: int = 1024,
+                      eps: float = 1e-3, h: float = 1e-2, K: int = 1, r_min: float = 0.6,
+                      seed: int = GEOMETRY_SEED) -> Scene:
+    """Potential flow past a sphere in 3D: the box [-1, 1]^3 (2 m^2 triangles
+    per face, Dirichlet, mapped data g = x (1 + a^3 / (2 r^3)) at the vertices,
+    scaled by one data parameter c at c = 1) around an insulating geodesic
+    icosphere of radius a (20 freq^2 triangles, reflecting Neumann; every edge
+    a silhouette candidate).  u = x (1 + a^3 / (2 r^3)) in the domain,
+    du/dc = u.  Query points uniform in |x|_inf < 0.9 with r > r_min."""
+    bv, be = box3d_grid(m)
+    sv, se = icosphere(freq)
+    vert = np.concatenate([bv, a * sv], 0)
+    elem = np.concatenate([be, se + len(bv)]).astype(np.int32)
+    neumann = np.concatenate([np.zeros(len(be)), np.ones(len(se))]).astype(np.int32)
+    r3 = np.sum(vert * vert, axis=1) ** 1.5
+    g = vert[:, 0] * (1.0 + a ** 3 / (2.0 * r3))
+    rng = np.random.default_rng(seed)
+    q = np.zeros((0, 3))
+    while len(q) < n_query:
+        p = rng.uniform(-0.9, 0.9, size=(4 * n_query, 3))
+        q = np.concatenate([q, p[np.linalg.norm(p, axis=1) > r_min]])[:n_query]
+    sc = Scene("sphere_flow", vert, elem, np.zeros((len(vert), 3, 1)), data="mapped", g_vert=g,
+               dg_vert=g[:, None].copy(), sigma=0.0)
+    sc.eps, sc.h, sc.K, sc.query, sc.walks, sc.neumann = eps, h, K, q, walks, neumann
+    sc.meta = {"a": a}
+    return sc
+
+
 def cube_neumann_scene(m: int = 4, n_query: int = 8, walks: int = 1024, eps: float = 1e-3, h: float = 1e-2,
                        K: int = 1, sigma: float = 0.0, seed: int = GEOMETRY_SEED) -> Scene:
     """Cube [-1, 1]^3, each face split into 2 m^2 triangles: the faces x = -1 and

@@ -216,6 +216,48 @@ def test_fine_cube_replay_warp_wide(Solver):
     assert np.all(np.abs(du - due) <= 4.5 * dse_ref + 0.08 * np.abs(due) + 0.02)
 
 
+def test_sphere_flow_replay_and_closed_form(Solver):
+    # a curved Neumann part in 3D (720-triangle icosphere; 768 Dirichlet box triangles: the
+    # warp-wide search)
+    sc = scenes.sphere_flow_scene(n_query=8)
+    s, g, o, same = _replay(Solver, sc, 64, u_scale=1.0)
+    out = s.eval(sc.query, 8192, grad=True)
+    ue, due = cf.sphere_flow(sc.query, sc.meta["a"])
+    u, use = out["u"].cpu().numpy(), out["u_se"].cpu().numpy()
+    du, dse = out["du"].cpu().numpy(), out["du_se"].cpu().numpy()
+    assert np.all(np.abs(u - ue) <= 4.5 * use + 3e-3)
+    assert np.all(np.abs(du - due) <= 4.5 * dse + 3e-3)
+
+
+@pytest.mark.parametrize("name", ["sphere", "cylinder"])
+def test_normal_cones_change_no_walk(Solver, name):
+    # the silhouette query skips tree nodes whose normal cone shows they hold no silhouette (from
+    # 1024 candidate elements up, for a fixed Neumann part): the same walks with the cones and
+    # without them (a Neumann vertex given a Jacobian column: no cones) are bit-identical
+    if name == "sphere":
+        sc = scenes.sphere_flow_scene(freq=12, n_query=8)          # 2880 triangles
+    else:
+        sc = scenes.cylinder_flow_scene(n_circle=2048, n_query=8)
+    recs = []
+    for moving in (False, True):
+        jac = sc.jac
+        if moving:
+            extra = np.zeros((len(sc.vert), sc.dim, 1))
+            extra[sc.elem[np.nonzero(sc.neumann)[0][0], 0], 0, 0] = 1.0
+            jac = np.concatenate([sc.jac, extra], axis=2)
+        s = Solver(0)
+        s.load_scene(sc)
+        s.set_boundary(sc.reference_vertices(), sc.elem, jac)
+        s.set_neumann(sc.neumann)
+        if sc.data == "mapped":
+            dg = None if sc.dg_vert is None else np.concatenate([sc.dg_vert, np.zeros((len(sc.vert), 1))], 1) \
+                if moving else sc.dg_vert
+            s.set_dirichlet_mapped(sc.g_vert, dg)
+        recs.append(s.walk_records(sc.query, 256, walk_id_base=11, differential=False)["rec"].view(np.uint32))
+        s.sync()
+    assert np.array_equal(recs[0], recs[1])
+
+
 def test_queries_and_refusals_with_a_neumann_part(Solver):
     from paper_2405_12964_gb300.dwos import DwosError
     sc = scenes.quarter_disk_scene("field", n_query=8)

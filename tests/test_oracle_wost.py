@@ -14,7 +14,8 @@ data) and its differential walk, which nests at the Dirichlet shell only
   not bounded by the slit's silhouette, lands on the other side's data), a
   cube with four Neumann faces (u = x, du/dX of the moving face), and the
   potential flow past an insulating cylinder (u = x (1 + a^2/r^2), a curved
-  Neumann part whose silhouettes are the points where rays graze it).
+  Neumann part whose silhouettes are the points where rays graze it) and
+  past an insulating sphere in 3D (u = x (1 + a^3 / (2 r^3))).
 * Walks never end on the Neumann part.
 Tolerances: 3.5 SE + a bias budget (polygon / mesh, eps-shell and the O(h)
 backward difference of Sec. 5.3).
@@ -130,6 +131,22 @@ def test_cylinder_flow_closed_form():
     hit = o["kind"][:, 0] == oracle.KIND_SHELL
     assert np.isin(o["elem"][hit], dirichlet).all()
     assert np.all(np.hypot(o["x_end"][:, 0], o["x_end"][:, 1]) >= sc.meta["a"] * np.cos(np.pi / 300) - 1e-9)
+
+
+def test_sphere_flow_closed_form():
+    # a curved Neumann part in 3D: an insulating icosphere (720 triangles) in a box held at the
+    # potential flow past it, u = x (1 + a^3 / (2 r^3)); du/dc = u through the mapped data
+    sc = scenes.sphere_flow_scene(n_query=6)
+    r = _run(sc, 2048)
+    u, du = cf.sphere_flow(sc.query, sc.meta["a"])
+    _check(r["u"], r["u_se"], u, 0.0, 3e-3)
+    _check(r["du"], r["du_se"], du, 0.0, 3e-3)
+    o = r["out"]
+    dirichlet = np.nonzero(sc.neumann == 0)[0]
+    hit = o["kind"][:, 0] == oracle.KIND_SHELL
+    assert np.isin(o["elem"][hit], dirichlet).all()
+    # no walk ends inside the sphere (the icosphere's inscribed radius bounds it)
+    assert np.all(np.linalg.norm(o["x_end"], axis=1) >= 0.9 * sc.meta["a"])
 
 
 def _on_neumann_points(name):
