@@ -272,6 +272,35 @@ def thermal_design(target=(0.15, 0.05), start=(0.0, 0.0), iters: int = 200, lr: 
     return opt.theta[0], err, losses
 
 
+def thermal_design_3d(target=(0.12, -0.08, 0.05), start=(0.0, 0.0, 0.0), iters: int = 200, lr: float = 5e-3,
+                      walks: int = 128, target_walks: int = 8192, n_side: int = 6, seed: int = 1, device: int = 0):
+    """The thermal design of Sec. 6.3 in 3D: move the heating element of
+    scenes.thermal_scene_3d (a Dirichlet sphere, g = 1) so that the temperature
+    on the insulating slab's underside (the Neumann part; an n_side x n_side
+    grid of query points on it) matches the profile the element makes at
+    `target`.  Differential walks on stars give dL/dtheta of
+    L = 1/2 sum_p (u_p - uref_p)^2 (U-statistic estimator); the element's
+    position is one 3-vector, updated by Vector Adam.  Returns (theta, position
+    errors, losses of the estimates)."""
+    from . import scenes
+    sc = scenes.thermal_scene_3d(n_side=n_side)
+    s = dwos.Solver(device)
+    s.load_scene(sc)
+    xq = torch.tensor(sc.query, dtype=torch.float32, device=s.device)
+    tgt = np.asarray(target, dtype=np.float64)
+    s.set_params(tgt)
+    uref = s.eval(xq, target_walks)["u"].to(torch.float32)
+    opt = VectorAdam(np.asarray(start, dtype=np.float64)[None, :], lr=lr)
+    err, losses = [float(np.linalg.norm(opt.theta[0] - tgt))], []
+    for it in range(iters):
+        s.set_params(opt.theta[0])
+        loss, g = s.grad_l2(xq, uref, walks, walk_id_base=(seed << 40) + it * (1 << 24))
+        opt.step(g.cpu().numpy()[None, :])
+        err.append(float(np.linalg.norm(opt.theta[0] - tgt)))
+        losses.append(float(loss[0]))
+    return opt.theta[0], err, losses
+
+
 def study_table(res: dict, iters=(50, 150, 300, 600), time_fracs=(0.1, 0.25, 0.5, 1.0)) -> dict:
     """Summary of noisy_gradient_study: per configuration the mean (over
     seeds) position error and loss at equal iterations, the seconds per

@@ -588,6 +588,53 @@ def box3d_grid(m: int, half: float = 1.0):
     return flat[first], inv.reshape(-1)[np.array(tris)].astype(np.int32)
 
 
+def box_grid(lo, hi, m: int):
+    """The box [lo, hi] (3-vectors) with each face split into 2 m^2 triangles,
+    wound consistently (normals out of the box; shared vertices merged)."""
+    lo, hi = np.asarray(lo, dtype=np.float64), np.asarray(hi, dtype=np.float64)
+    v, e = box3d_grid(m, 1.0)
+    vert = lo + 0.5 * (v + 1.0) * (hi - lo)
+    # orient every triangle's normal away from the box centre
+    c = 0.5 * (lo + hi)
+    a, b, cc = vert[e[:, 0]], vert[e[:, 1]], vert[e[:, 2]]
+    n = np.cross(b - a, cc - a)
+    flip = np.sum(n * ((a + b + cc) / 3.0 - c), axis=1) < 0
+    e = e.copy()
+    e[flip] = e[flip][:, [0, 2, 1]]
+    return vert, e
+
+
+def thermal_scene_3d(offset=(0.0, 0.0, 0.0), freq: int = 4, slab_m: int = 4, box_m: int = 2, n_side: int = 6,
+                     walks: int = 1024, eps: float = 1e-3, h: float = 1e-2, K: int = 2,
+                     seed: int = GEOMETRY_SEED) -> Scene:
+    """The thermal design of Sec. 6.3 in 3D: a heating element (a sphere of
+    radius 0.1 around (0, 0, -0.35), an icosphere of 20 freq^2 triangles,
+    Dirichlet g = 1) warms an insulating slab ([-0.5, 0.5]^2 x [0.2, 0.3], its
+    faces split into 2 slab_m^2 triangles each, reflecting Neumann) inside the
+    box [-1, 1]^3 held at g = 0; sigma = 0, no source.  theta = the heater's
+    translation (a 3-vector: Vector Adam applies), at `offset` in `vert`.
+    Observation points: an n_side x n_side grid on the slab's underside z = 0.2
+    (on the Neumann part)."""
+    bv, be = box3d_grid(box_m)
+    hv, he = icosphere(freq)
+    hv = 0.1 * hv + np.array([0.0, 0.0, -0.35]) + np.asarray(offset, dtype=np.float64)
+    sv, se = box_grid((-0.5, -0.5, 0.2), (0.5, 0.5, 0.3), slab_m)
+    vert = np.concatenate([bv, hv, sv], 0)
+    nb, nh = len(bv), len(hv)
+    elem = np.concatenate([be, he + nb, se + nb + nh]).astype(np.int32)
+    neumann = np.concatenate([np.zeros(len(be) + len(he)), np.ones(len(se))]).astype(np.int32)
+    g = np.concatenate([np.zeros(nb), np.ones(nh), np.zeros(len(sv))])
+    jac = np.zeros((len(vert), 3, 3))
+    for k in range(3):
+        jac[nb:nb + nh, k, k] = 1.0
+    t = -0.4 + 0.8 * (np.arange(n_side) + 0.5) / n_side
+    q = np.stack([np.repeat(t, n_side), np.tile(t, n_side), np.full(n_side * n_side, 0.2)], 1)
+    sc = Scene("thermal_3d", vert, elem, jac, data="mapped", g_vert=g, sigma=0.0)
+    sc.eps, sc.h, sc.K, sc.query, sc.walks, sc.neumann = eps, h, K, q, walks, neumann
+    sc.meta = {"theta0": np.asarray(offset, dtype=np.float64)}
+    return sc
+
+
 def sphere_flow_scene(a: float = 0.4, freq: int = 6, m: int = 8, n_query: int = 8, walks: int = 1024,
                       eps: float = 1e-3, h: float = 1e-2, K: int = 1, r_min: float = 0.6,
                       seed: int = GEOMETRY_SEED) -> Scene:

@@ -70,3 +70,24 @@ def test_thermal_design_moves_the_heating_wire(opt):
     assert np.mean(err[-20:]) < 0.35 * err[0], (err[0], err[-20:])
     # the loss estimates carry the walks' variance (sum_p Var(u_p) / W, about 0.03 here)
     assert np.mean(losses[-20:]) < 0.7 * np.mean(losses[:5])
+
+
+def test_thermal_design_3d_moves_the_heater(opt):
+    # Sec. 6.3 in 3D: an insulating slab (Neumann) over a heating sphere (Dirichlet) in a cold
+    # box; differential walks on stars from points on the slab's underside move the heater
+    target, start = np.array([0.12, -0.08, 0.05]), np.zeros(3)
+    theta, err, losses = opt.thermal_design_3d(target=target, start=start, iters=200, lr=5e-3, walks=128,
+                                               target_walks=4096)
+    assert np.mean(err[-20:]) < 0.35 * err[0], (err[0], err[-20:])
+    # the loss estimates sit on the walks' variance floor: judge the temperature profile itself
+    # (8192 walks per point at the start, the final and the target positions)
+    sc = scenes.thermal_scene_3d()
+    s = opt.dwos.Solver(0)
+    s.load_scene(sc)
+    u = {}
+    for name, th in (("target", target), ("start", start), ("final", theta)):
+        s.set_params(th)
+        u[name] = s.eval(sc.query, 8192)["u"].cpu().numpy()
+    l0 = 0.5 * np.sum((u["start"] - u["target"]) ** 2)
+    l1 = 0.5 * np.sum((u["final"] - u["target"]) ** 2)
+    assert l1 < 0.25 * l0, (l0, l1)

@@ -258,6 +258,15 @@ def test_normal_cones_change_no_walk(Solver, name):
     assert np.array_equal(recs[0], recs[1])
 
 
+def test_thermal_3d_replay(Solver):
+    # the 3D thermal design: query points on the slab's underside (they start on the Neumann
+    # part), a Dirichlet sphere and box (368 triangles: the warp-wide search), K = 2
+    sc = scenes.thermal_scene_3d(n_side=4)
+    sc.query = sc.query.astype(np.float32).astype(np.float64)
+    s, g, o, same = _replay(Solver, sc, 64, u_scale=1.0)
+    assert np.all(np.isfinite(g["rec"]["u"]))
+
+
 def test_queries_and_refusals_with_a_neumann_part(Solver):
     from paper_2405_12964_gb300.dwos import DwosError
     sc = scenes.quarter_disk_scene("field", n_query=8)
