@@ -267,6 +267,20 @@ def test_thermal_3d_replay(Solver):
     assert np.all(np.isfinite(g["rec"]["u"]))
 
 
+def test_cones_survive_parameter_updates(Solver):
+    # parameter updates refit the trees and rebuild them every 64th time, the candidate tree's
+    # normal cones with them: at the same geometry the walks after 65 updates equal the first
+    sc = scenes.cylinder_flow_scene(n_circle=2048, n_query=8)
+    s = Solver(0)
+    s.load_scene(sc)
+    first = s.walk_records(sc.query, 128, walk_id_base=3, differential=True)["rec"].view(np.uint32)
+    for _ in range(65):
+        s.set_params(np.zeros(1))
+    again = s.walk_records(sc.query, 128, walk_id_base=3, differential=True)["rec"].view(np.uint32)
+    s.sync()
+    assert np.array_equal(first, again)
+
+
 def test_queries_and_refusals_with_a_neumann_part(Solver):
     from paper_2405_12964_gb300.dwos import DwosError
     sc = scenes.quarter_disk_scene("field", n_query=8)
