@@ -179,12 +179,14 @@ def slit_sqrt(x):
     return np.sqrt(r) * np.cos(phi / 2)
 
 
-def cube_linear(x):
+def cube_linear(x, f: float = 0.0):
     """Cube with Dirichlet faces x = -1 (g = -1) and x = X (g = 1), reflecting
-    Neumann elsewhere, sigma = 0: u = 2 (x + 1) / (X + 1) - 1, so at X = 1
-    u = x and du/dX = -(x + 1) / 2."""
+    Neumann elsewhere, sigma = 0, constant source f of -u'' = f: u depends on
+    x alone, u = 2 (x + 1) / (X + 1) - 1 + f (x + 1) (X - x) / 2, so at X = 1
+    u = x + f (1 - x^2) / 2 and du/dX = -(x + 1) / 2 + f (x + 1) / 2."""
     x = np.atleast_2d(np.asarray(x, dtype=np.float64))
-    return x[:, 0].copy(), (-(x[:, 0] + 1) / 2)[:, None]
+    xx = x[:, 0]
+    return xx + f * (1 - xx * xx) / 2, ((xx + 1) * (f - 1) / 2)[:, None]
 
 
 def cylinder_flow(x, a: float):

@@ -664,11 +664,12 @@ def sphere_flow_scene(a: float = 0.4, freq: int = 6, m: int = 8, n_query: int = 
 
 
 def cube_neumann_scene(m: int = 4, n_query: int = 8, walks: int = 1024, eps: float = 1e-3, h: float = 1e-2,
-                       K: int = 1, sigma: float = 0.0, seed: int = GEOMETRY_SEED) -> Scene:
+                       K: int = 1, sigma: float = 0.0, f: float = 0.0, seed: int = GEOMETRY_SEED) -> Scene:
     """Cube [-1, 1]^3, each face split into 2 m^2 triangles: the faces x = -1 and
     x = X (X = 1) are Dirichlet with mapped data g = x (-1 and 1), the other
-    four reflecting Neumann.  theta = [X] moves the face x = X (its vertices
-    move in x; the side faces stretch along themselves)."""
+    four reflecting Neumann; constant source f of -Lap u + sigma u = f.
+    theta = [X] moves the face x = X (its vertices move in x; the side faces
+    stretch along themselves)."""
     pts, tris, flags = [], [], []
     u = np.linspace(-1.0, 1.0, m + 1)
     for axis in range(3):
@@ -694,7 +695,7 @@ def cube_neumann_scene(m: int = 4, n_query: int = 8, walks: int = 1024, eps: flo
     jac[np.isclose(vert[:, 0], 1.0), 0, 0] = 1.0
     rng = np.random.default_rng(seed)
     q = rng.uniform(-0.8, 0.8, size=(n_query, 3))
-    sc = Scene("cube_neumann", vert, elem, jac, data="mapped", g_vert=vert[:, 0].copy(), sigma=sigma)
+    sc = Scene("cube_neumann", vert, elem, jac, data="mapped", g_vert=vert[:, 0].copy(), sigma=sigma, f=f)
     sc.eps, sc.h, sc.K, sc.query, sc.walks, sc.neumann = eps, h, K, q, walks, np.array(flags, np.int32)
     sc.meta = {"theta0": np.array([1.0])}
     return sc

@@ -117,6 +117,16 @@ def test_cube_with_neumann_faces_closed_form():
     assert np.isin(o["elem"][hit], dirichlet).all()
 
 
+def test_cube_with_neumann_faces_and_a_source():
+    # the source's samples count only where x sees them through the star: in 3D, with a source
+    # f = 1.5, u = x + f (1 - x^2) / 2 and du/dX = (x + 1) (f - 1) / 2
+    sc = scenes.cube_neumann_scene(n_query=6, f=1.5)
+    r = _run(sc, 2048)
+    u, du = cf.cube_linear(sc.query, 1.5)
+    _check(r["u"], r["u_se"], u, 0.0, 5e-3)
+    _check(r["du"], r["du_se"], du, 0.08, 0.02)
+
+
 def test_cylinder_flow_closed_form():
     # a curved Neumann part: an insulating circle in a box held at the potential flow past it,
     # u = x (1 + a^2/r^2); its silhouette points (where rays from x graze the circle) bound the
