@@ -189,6 +189,20 @@ def cube_linear(x, f: float = 0.0):
     return xx + f * (1 - xx * xx) / 2, ((xx + 1) * (f - 1) / 2)[:, None]
 
 
+def cube_screened(x, sigma: float):
+    """Cube with Dirichlet faces x = -1 (g = -1) and x = X (g = 1), reflecting
+    Neumann elsewhere, -u'' + sigma u = 0 (k = sqrt(sigma)): u depends on x
+    alone, u = (sinh(k (x + 1)) - sinh(k (X - x))) / sinh(k (X + 1)), at X = 1
+    sinh(k x) / sinh(k); du/dX is its central difference in X (step 1e-6, an
+    error of order 1e-12 against the exact derivative)."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    k = np.sqrt(sigma)
+    xx = x[:, 0]
+    u = lambda X: (np.sinh(k * (xx + 1)) - np.sinh(k * (X - xx))) / np.sinh(k * (X + 1))
+    d = 1e-6
+    return u(1.0), ((u(1.0 + d) - u(1.0 - d)) / (2 * d))[:, None]
+
+
 def cylinder_flow(x, a: float):
     """Potential flow past a cylinder: u = x (1 + a^2 / r^2) = (r + a^2 / r) cos phi
     is harmonic where r > 0 (the radial part f = r + a^2/r has

@@ -294,6 +294,20 @@ def test_cube_with_a_source_replay_and_closed_form(Solver):
     assert np.all(np.abs(du - due) <= 4.5 * dse_ref + 0.08 * np.abs(due) + 0.02)
 
 
+def test_screened_cube_replay_and_closed_form(Solver):
+    # the 3D star weight's roulette on the GPU: -u'' + 4 u = 0 on the Neumann cube
+    sc = scenes.cube_neumann_scene(n_query=8, sigma=4.0)
+    s, g, o, same = _replay(Solver, sc, 64, u_scale=1.0)
+    assert (o["kind"][:, 0] == oracle.KIND_ROULETTE).any()
+    out = s.eval(sc.query, 4096, grad=True)
+    ue, due = cf.cube_screened(sc.query, 4.0)
+    u, use = out["u"].cpu().numpy(), out["u_se"].cpu().numpy()
+    du, dse = out["du"].cpu().numpy(), out["du_se"].cpu().numpy()
+    assert np.all(np.abs(u - ue) <= 4.5 * use + 4e-3)
+    dse_ref = np.maximum(dse, np.median(dse, axis=0, keepdims=True))
+    assert np.all(np.abs(du - due) <= 4.5 * dse_ref + 0.08 * np.abs(due) + 0.02)
+
+
 def test_queries_and_refusals_with_a_neumann_part(Solver):
     from paper_2405_12964_gb300.dwos import DwosError
     sc = scenes.quarter_disk_scene("field", n_query=8)

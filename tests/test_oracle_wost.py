@@ -127,6 +127,19 @@ def test_cube_with_neumann_faces_and_a_source():
     _check(r["du"], r["du_se"], du, 0.08, 0.02)
 
 
+def test_screened_cube_closed_form():
+    # screened walks on stars in 3D (Russian roulette by the 3D star weight): -u'' + 4 u = 0
+    # between the Dirichlet faces, u = sinh(2 x) / sinh(2)
+    sc = scenes.cube_neumann_scene(n_query=6, sigma=4.0)
+    r = _run(sc, 2048)
+    u, du = cf.cube_screened(sc.query, 4.0)
+    _check(r["u"], r["u_se"], u, 0.0, 4e-3)
+    # du/dX is a rare-event estimate far from the moving face (roulette ends most walks first):
+    # its SE is floored at the median over the points
+    _check(r["du"], np.maximum(r["du_se"], np.median(r["du_se"], axis=0)), du, 0.08, 0.02)
+    assert (r["out"]["kind"][:, 0] == oracle.KIND_ROULETTE).any()
+
+
 def test_cylinder_flow_closed_form():
     # a curved Neumann part: an insulating circle in a box held at the potential flow past it,
     # u = x (1 + a^2/r^2); its silhouette points (where rays from x graze the circle) bound the
