@@ -120,6 +120,9 @@ def lib():
             L.oracle_star_weight.restype = ctypes.c_double
             L.oracle_turn_inward.argtypes = [ctypes.c_int, dp, dp, dp]
             L.oracle_turn_inward.restype = None
+            L.oracle_ray_neumann.argtypes = [ctypes.POINTER(_Scene), dp, dp, ctypes.c_double, ctypes.c_int, dp,
+                                             ctypes.c_int, dp, ip]
+            L.oracle_ray_neumann.restype = ctypes.c_double
             L.oracle_bessel_k0.argtypes = [ctypes.c_double]
             L.oracle_bessel_k0.restype = ctypes.c_double
             L.oracle_gradient_factor.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
@@ -241,6 +244,24 @@ def alpha(dim: int, sigma: float, d: float) -> float:
 def source_weight(dim: int, sigma: float, d: float, rho: float) -> float:
     """|B(d)| * G_d(rho d): Algorithm 1's source weight per unit source."""
     return lib().oracle_source_weight(dim, sigma, d, rho)
+
+
+def ray_neumann(prob: "Problem", x, v, tmax: float, skip: int = -1, n_skip=None, skip2: int = -1, n_skip2=None):
+    """First crossing of the ray x + t v (t <= tmax, plus the walk's slack) with
+    the Neumann part, for a walk sitting on element `skip` (and `skip2` at an
+    edge) with outward normals n_skip (n_skip2).  Returns (t, element or -1)."""
+    s = prob._struct()
+    d = prob.dim
+    xx = np.zeros(3); xx[:d] = np.asarray(x, dtype=np.float64)[:d]
+    vv = np.zeros(3); vv[:d] = np.asarray(v, dtype=np.float64)[:d]
+    a = None if n_skip is None else np.ascontiguousarray(np.resize(np.asarray(n_skip, dtype=np.float64), 3))
+    b = None if n_skip2 is None else np.ascontiguousarray(np.resize(np.asarray(n_skip2, dtype=np.float64), 3))
+    if a is not None and d == 2: a[2] = 0.0
+    if b is not None and d == 2: b[2] = 0.0
+    e = ctypes.c_int(-1)
+    t = lib().oracle_ray_neumann(ctypes.byref(s), _dp(xx), _dp(vv), float(tmax), int(skip), _dp(a), int(skip2),
+                                 _dp(b), ctypes.byref(e))
+    return float(t), int(e.value)
 
 
 def turn_inward(v: np.ndarray, n_on, n2=None) -> np.ndarray:

@@ -856,6 +856,15 @@ void oracle_turn_inward(int n, double* v, const double* n_on, const double* n2) 
     for (int i = 0; i < n; ++i) turn_inward(v + 3 * (size_t)i, 0, n_on, n2 ? 0 : -1, n2 ? n2 : n_on);
 }
 
+/* ray_neumann for the tests: the first Neumann crossing of x + t v within
+ * tmax for a walk on sides `skip` (normal n_skip) and `skip2` (n_skip2; -1 /
+ * NULL: none), with the walk's slack of 1e-4 eps.  Returns t, the element in
+ * *e_out. */
+double oracle_ray_neumann(const oracle_scene* s, const double* x, const double* v, double tmax, int skip,
+                          const double* n_skip, int skip2, const double* n_skip2, int* e_out) {
+    return ray_neumann(s, x, v, tmax, skip, n_skip, skip2, n_skip2, 1e-4 * s->eps, e_out);
+}
+
 /* Where a walk on stars starts: the Neumann side it sits on (-1: inside) and,
  * on an edge, the second side, with their normals out of the domain. */
 struct StarStart {

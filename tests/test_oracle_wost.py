@@ -262,3 +262,35 @@ def test_directions_at_an_edge_of_the_neumann_part():
     n_a = np.array([-np.sin(a), np.cos(a), 0.0])
     w = oracle.turn_inward(v, [0.0, -1.0, 0.0], n_a)
     assert np.all(w[:, 1] >= -1e-12) and np.all(w @ n_a <= 1e-12)
+
+
+def test_ray_rules_on_the_slab():
+    # The ray test against the Neumann part, on the thermal scene's slab (the box: elements 0-3,
+    # the wire: 4-67, the slab polyline: 68-155; its underside y = 0.2 runs from x = -0.5 (68)
+    # to 0.5 (107), then the right end x = 0.5 (108-111)).
+    sc = scenes.thermal_scene(n_query=2)
+    pr = to_oracle(sc)
+    up = [0.0, 1.0]                       # the underside's normal out of the domain (into the slab)
+    # a plain crossing from the domain below: the underside at t = 0.1
+    t, e = oracle.ray_neumann(pr, [0.11, 0.1], [0.0, 1.0], 0.5)
+    assert e == 92 and abs(t - 0.1) < 1e-12
+    # a crossing up to 1e-5 tmax + 1e-4 eps past the ray's end counts, at the end
+    t, e = oracle.ray_neumann(pr, [0.11, 0.1], [0.0, 1.0], 0.1 - 5e-7)
+    assert e == 92 and t == 0.1 - 5e-7
+    t, e = oracle.ray_neumann(pr, [0.11, 0.1], [0.0, 1.0], 0.1 - 1e-5)
+    assert e == -1
+    # a ray grazing the reflex corner (0.5, 0.2) from a walk on the last underside segment: the
+    # end side lies behind the underside and is not hit, though the ray passes within the 1e-5
+    # barycentric tolerance of its end (from a point not on the underside it is)
+    v = [np.cos(1e-4), -np.sin(1e-4)]
+    t, e = oracle.ray_neumann(pr, [0.4993, 0.2], v, 1e-3, skip=107, n_skip=up)
+    assert e == -1 and t == 1e-3
+    t, e = oracle.ray_neumann(pr, [0.4993, 0.2], v, 1e-3)
+    assert e == 108
+    # a ray nearly along the underside from a walk on it, rounding having put the walk 1e-8
+    # inside the slab: the segments on its line are not hit (from the wrong side), adjacent or not
+    x, v = [0.0125, 0.2 + 1e-8], [-1.0, -1e-7]
+    t, e = oracle.ray_neumann(pr, x, v, 0.5, skip=88, n_skip=up)
+    assert e == -1
+    t, e = oracle.ray_neumann(pr, x, v, 0.5)
+    assert e == 84
