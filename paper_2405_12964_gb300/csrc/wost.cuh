@@ -336,6 +336,28 @@ __device__ __forceinline__ bool coplanar_side(const DevNeumann& N, const float* 
     return fabsf(r) <= on_line;
 }
 
+// The side tests out of line: in 3D the walk-on-stars kernel's code outgrows
+// the instruction cache, and these run only for a candidate hit while the
+// walk sits on a side (3D walk kernel 6 % faster; in 2D inline is 5-7 %
+// faster).
+template <int DIM>
+__device__ __noinline__ bool behind_side_ool(const DevNeumann& N, int e, const float* ne, int f) {
+    return behind_side<DIM>(N, e, ne, f);
+}
+template <int DIM>
+__device__ __noinline__ bool coplanar_side_ool(const DevNeumann& N, const float* x, const float* ne, int f,
+                                               float on_line) {
+    return coplanar_side<DIM>(N, x, ne, f, on_line);
+}
+template <int DIM>
+__device__ __forceinline__ bool skipped_from_side(const DevNeumann& N, const float* x, int e, const float* ne, int f,
+                                                  float on_line) {
+    if constexpr (DIM == 3)
+        return behind_side_ool<3>(N, e, ne, f) || coplanar_side_ool<3>(N, x, ne, f, on_line);
+    else
+        return behind_side<DIM>(N, e, ne, f) || coplanar_side<DIM>(N, x, ne, f, on_line);
+}
+
 // First crossing of the ray x + t v (0 < t < tmax) with a Neumann element
 // other than `skip` and `skip2` (compact numbering; the sides the walk sits
 // on, -1 for none, with their unit normals n_skip, n_skip2 out of the domain),
@@ -384,9 +406,8 @@ __device__ __forceinline__ float ray_neumann(const DevNeumann& N, const float* x
             t = (e2[0] * q[0] + e2[1] * q[1] + e2[2] * q[2]) * id;
         }
         if (!(t > 0.0f && t < best)) return;
-        if (skip >= 0 && (behind_side<DIM>(N, skip, n_skip, e) || coplanar_side<DIM>(N, x, n_skip, e, on_line))) return;
-        if (skip2 >= 0 && (behind_side<DIM>(N, skip2, n_skip2, e) || coplanar_side<DIM>(N, x, n_skip2, e, on_line)))
-            return;
+        if (skip >= 0 && skipped_from_side<DIM>(N, x, skip, n_skip, e, on_line)) return;
+        if (skip2 >= 0 && skipped_from_side<DIM>(N, x, skip2, n_skip2, e, on_line)) return;
         best = t;
         hit = e;
     };
