@@ -72,6 +72,7 @@ class _Scene(ctypes.Structure):
         ("cv_elem", ctypes.POINTER(ctypes.c_double)),
         ("dudn_mode", ctypes.c_int),
         ("neumann", ctypes.POINTER(ctypes.c_int)),
+        ("neumann_h", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -123,6 +124,10 @@ def lib():
             L.oracle_ray_neumann.argtypes = [ctypes.POINTER(_Scene), dp, dp, ctypes.c_double, ctypes.c_int, dp,
                                              ctypes.c_int, dp, ip]
             L.oracle_ray_neumann.restype = ctypes.c_double
+            L.oracle_neumann_data_sample.argtypes = [ctypes.POINTER(_Scene), dp, ctypes.c_double, ctypes.c_int,
+                                                     dp, ctypes.c_int, dp, ctypes.c_uint64, ctypes.c_uint32,
+                                                     ctypes.c_uint32]
+            L.oracle_neumann_data_sample.restype = ctypes.c_double
             L.oracle_bessel_k0.argtypes = [ctypes.c_double]
             L.oracle_bessel_k0.restype = ctypes.c_double
             L.oracle_gradient_factor.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
@@ -175,6 +180,7 @@ class Problem:
     cv_elem: Optional[np.ndarray] = None      # (n_elem, 4): q, t of the nested walks' surrogate grad u = q n + t
     dudn_mode: int = 0                        # 0: backward difference (Eq. dudn_fd_estimate), 1: ball gradient
     neumann: Optional[np.ndarray] = None      # (n_elem,) flags: 1 for elements of the reflecting Neumann part
+    neumann_h: Optional[np.ndarray] = None    # (n_elem,) Neumann data du/dn (out of the domain); None: zero
     _keep: list = dc_field(default_factory=list, repr=False)
 
     @property
@@ -193,7 +199,8 @@ class Problem:
         dg = None if self.dg_vert is None else np.ascontiguousarray(self.dg_vert, dtype=np.float64)
         cq = None if self.cv_elem is None else np.ascontiguousarray(self.cv_elem, dtype=np.float64).reshape(-1, 4)
         nm = None if self.neumann is None else np.ascontiguousarray(self.neumann, dtype=np.int32)
-        self._keep = [v, e, jac, g, dg, cq, nm]
+        nh = None if self.neumann_h is None else np.ascontiguousarray(self.neumann_h, dtype=np.float64)
+        self._keep = [v, e, jac, g, dg, cq, nm, nh]
         s = _Scene()
         s.dim = v.shape[1]
         s.n_vert = v.shape[0]
@@ -222,6 +229,7 @@ class Problem:
         s.cv_elem = _dp(cq)
         s.dudn_mode = int(self.dudn_mode)
         s.neumann = _ip(nm)
+        s.neumann_h = _dp(nh)
         return s
 
 
@@ -262,6 +270,22 @@ def ray_neumann(prob: "Problem", x, v, tmax: float, skip: int = -1, n_skip=None,
     t = lib().oracle_ray_neumann(ctypes.byref(s), _dp(xx), _dp(vv), float(tmax), int(skip), _dp(a), int(skip2),
                                  _dp(b), ctypes.byref(e))
     return float(t), int(e.value)
+
+
+def neumann_data_sample(prob: "Problem", x, R: float, on: int = -1, n_on=None, on2: int = -1, n2=None,
+                        walk_id: int = 0, step: int = 0, phase: int = 0) -> float:
+    """The Neumann-data term of one walk-on-stars step from x with star radius
+    R, for a walk on element `on` (and `on2` at an edge; -1: none) with outward
+    normals n_on (n2), drawn at step `step` of phase `phase` of walk walk_id."""
+    s = prob._struct()
+    d = prob.dim
+    xx = np.zeros(3); xx[:d] = np.asarray(x, dtype=np.float64)[:d]
+    a = None if n_on is None else np.ascontiguousarray(np.resize(np.asarray(n_on, dtype=np.float64), 3))
+    b = None if n2 is None else np.ascontiguousarray(np.resize(np.asarray(n2, dtype=np.float64), 3))
+    if a is not None and d == 2: a[2] = 0.0
+    if b is not None and d == 2: b[2] = 0.0
+    return float(lib().oracle_neumann_data_sample(ctypes.byref(s), _dp(xx), float(R), int(on), _dp(a), int(on2),
+                                                  _dp(b), int(walk_id), int(step), int(phase)))
 
 
 def turn_inward(v: np.ndarray, n_on, n2=None) -> np.ndarray:

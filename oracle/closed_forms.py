@@ -227,3 +227,41 @@ def sphere_flow(x, a: float):
     r3 = np.sum(x * x, axis=1) ** 1.5
     u = x[:, 0] * (1.0 + a ** 3 / (2.0 * r3))
     return u, u[:, None].copy()
+
+
+def neumann_data_box(x, c: float, b: float):
+    """Neumann data on the box [-1, 1]^d: the faces x = -1 and x = X (X = 1)
+    Dirichlet, the others Neumann with data du/dn = 2c (n out of the box), and
+    restricted Dirichlet data g = b x + c (y^2 - x^2) (2D), b x + c (y^2 + z^2 -
+    2 x^2) (3D).  g is harmonic and its normal derivative on the Neumann faces
+    is 2c, so u = g in the whole box whatever X is: du/dX = 0."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    if x.shape[1] == 2:
+        u = b * x[:, 0] + c * (x[:, 1] ** 2 - x[:, 0] ** 2)
+    else:
+        u = b * x[:, 0] + c * (x[:, 1] ** 2 + x[:, 2] ** 2 - 2 * x[:, 0] ** 2)
+    return u, np.zeros((len(u), 1))
+
+
+def screened_neumann_data_box(x, k: float, s: float):
+    """-Lap u + k^2 u = 0 on [-1, X] x [-1, 1] with Neumann data du/dn =
+    k sinh(k) on y = -1, 1 and Dirichlet data g = cosh(k y) - s sinh(k) on
+    x = -1 and cosh(k y) + s sinh(k) on x = X, each carried by its side's
+    vertices as X moves: u = cosh(k y) + w(x) with w'' = k^2 w, w(-1) = -S,
+    w(X) = S (S = s sinh k), i.e. w = S (sinh(k (x + 1)) - sinh(k (X - x))) /
+    sinh(k (X + 1)), at X = 1 s sinh(k x).  du/dX is the central difference of
+    w in X (step 1e-6)."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    S = s * np.sinh(k)
+    xx = x[:, 0]
+    w = lambda X: S * (np.sinh(k * (xx + 1)) - np.sinh(k * (X - xx))) / np.sinh(k * (X + 1))
+    d = 1e-6
+    return np.cosh(k * x[:, 1]) + w(1.0), ((w(1.0 + d) - w(1.0 - d)) / (2 * d))[:, None]
+
+
+def annulus_log(x, a: float, b: float):
+    """u = a + b log r on r_in < r < 1: the outer circle carries Dirichlet
+    data a, the inner circle Neumann data du/dn = -b / r_in (n out of the
+    domain points to the centre)."""
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    return a + b * np.log(np.hypot(x[:, 0], x[:, 1]))

@@ -138,6 +138,8 @@ typedef struct {
                                 offset point, Eq. (dudn_mc_estimate) */
     const int* neumann;      /* n_elem flags, 1: element of the (reflecting) Neumann boundary; NULL: all
                                 elements are Dirichlet */
+    const double* neumann_h; /* n_elem Neumann data h = du/dn (n out of the domain), read on the Neumann
+                                elements only; NULL: zero (a reflecting boundary) */
 } oracle_scene;
 
 enum { KIND_SHELL = 0, KIND_ROULETTE = 1, KIND_CAPPED = 2 };
@@ -865,6 +867,123 @@ double oracle_ray_neumann(const oracle_scene* s, const double* x, const double* 
     return ray_neumann(s, x, v, tmax, skip, n_skip, skip2, n_skip2, 1e-4 * s->eps, e_out);
 }
 
+/* Length (2D) or area (3D) of element e. */
+static double element_measure(const oracle_scene* s, int e) {
+    const int d = s->dim;
+    const int* el = s->elem + (size_t)d * e;
+    const double* a = s->vert + (size_t)d * el[0];
+    const double* b = s->vert + (size_t)d * el[1];
+    if (d == 2) return std::hypot(b[0] - a[0], b[1] - a[1]);
+    const double* c = s->vert + (size_t)d * el[2];
+    double u[3], v[3];
+    for (int i = 0; i < 3; ++i) { u[i] = b[i] - a[i]; v[i] = c[i] - a[i]; }
+    const double w[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+    return 0.5 * std::sqrt(dot3(w, w));
+}
+
+/* The ball's Green's function G_R(t) at distance t from the centre (the source
+ * weight above divided by the ball's volume). */
+static double ball_green(int dim, double sigma, double t, double R) {
+    const double vol = dim == 2 ? kPi * R * R : 4.0 / 3.0 * kPi * R * R * R;
+    return oracle_source_weight(dim, sigma, R, t / R) / vol;
+}
+
+/* Uniform in (0, 1) for the Neumann element of index c (counted among the
+ * Neumann elements in input order) at step k of a walk phase: Philox with the
+ * counter (walk id, k, (phase << 8) | 3) and the key (seed_lo, seed_hi ^ (c + 1)),
+ * word 0. */
+static double element_uniform(const oracle_scene* s, uint64_t walk_id, uint32_t k, uint32_t phase, int c) {
+    const uint32_t ctr[4] = {(uint32_t)walk_id, (uint32_t)(walk_id >> 32), k, (phase << 8) | 3u};
+    const uint32_t key[2] = {s->seed_lo, s->seed_hi ^ (uint32_t)(c + 1)};
+    uint32_t out[4];
+    philox4x32_10(ctr, key, out);
+    return to_uniform(out[0]);
+}
+
+/* The Neumann-data term of a walk-on-stars step (Sec. 3.4, Eq. mixed_bvp with
+ * Robin coefficient 0 and data h = du/dn; Green's second identity on the star
+ * St(x, R)): the walk adds (1 / a(x)) times the integral of G_R(x, z) h(z) over
+ * the part of the Neumann boundary in the ball that x sees, a(x) the share of
+ * the directions around x that point into the domain (1 inside, 1/2 on a
+ * side, (pi - angle between the two normals) / 2 pi at an edge).  One sample:
+ * every Neumann element closer to x than R is a candidate, of total measure A;
+ * the element is drawn with probability proportional to its measure (the
+ * candidate with the least -log(U_c) / |e_c|, so that the draw does not depend
+ * on the order of the candidates), z uniformly on it (block 2 of the step:
+ * words 0 and 1); the estimate is A G_R(|z - x|) h(e) / a(x) if |z - x| < R
+ * and x sees z, else 0.  x sees z if z lies on a side the walk sits on, or
+ * else, z not behind those sides (a point (z - x) . n > 1e-4 eps out of a
+ * side's plane, or an element behind it by the ray rule, unless it is on the
+ * side's plane), no Neumann element crosses the segment before 1 - 1e-4 of
+ * its length (the ray rules of the step). */
+static double neumann_data_sample(const oracle_scene* s, const double* x, double R, int on, const double* n_on,
+                                  int on2, const double* n2, uint64_t walk_id, uint32_t k, uint32_t phase) {
+    const int d = s->dim;
+    double A = 0, best = INFINITY;
+    int pick = -1;
+    for (int e = 0, c = 0; e < s->n_elem; ++e) {
+        if (!s->neumann[e]) continue;
+        const int ci = c++;
+        const int* el = s->elem + (size_t)d * e;
+        double xb[3] = {0, 0, 0}, b2[2];
+        const double d2 = d == 2 ? closest_on_segment(x, s->vert + 2 * el[0], s->vert + 2 * el[1], xb, b2)
+                                 : closest_on_triangle(x, s->vert + 3 * el[0], s->vert + 3 * el[1],
+                                                       s->vert + 3 * el[2], xb, b2);
+        if (!(d2 < R * R)) continue;
+        const double m = element_measure(s, e);
+        if (!(m > 0)) continue;
+        A += m;
+        const double key = -std::log(element_uniform(s, walk_id, k, phase, ci)) / m;
+        if (key < best) { best = key; pick = e; }
+    }
+    if (pick < 0) return 0;
+    const Draws r = draw(s->seed_lo, s->seed_hi, walk_id, k, phase, 2);
+    const int* el = s->elem + (size_t)d * pick;
+    double z[3] = {0, 0, 0};
+    if (d == 2) {
+        const double* a = s->vert + 2 * el[0];
+        const double* b = s->vert + 2 * el[1];
+        for (int i = 0; i < 2; ++i) z[i] = a[i] + r.u[0] * (b[i] - a[i]);
+    } else {
+        const double* a = s->vert + 3 * el[0];
+        const double* b = s->vert + 3 * el[1];
+        const double* c = s->vert + 3 * el[2];
+        const double q = std::sqrt(r.u[0]);
+        for (int i = 0; i < 3; ++i) z[i] = (1 - q) * a[i] + q * (1 - r.u[1]) * b[i] + q * r.u[1] * c[i];
+    }
+    double v[3] = {0, 0, 0};
+    for (int i = 0; i < d; ++i) v[i] = z[i] - x[i];
+    const double t = std::sqrt(dot3(v, v));
+    if (!(t < R) || !(t > 0)) return 0;
+    if (pick != on && pick != on2) {
+        const double on_line = 1e-4 * s->eps;
+        const int side[2] = {on, on2};
+        const double* nrm[2] = {n_on, n2};
+        for (int j = 0; j < 2; ++j) {
+            if (side[j] < 0) continue;
+            if (coplanar_side(s, x, nrm[j], pick)) continue;
+            if (behind_side(s, side[j], nrm[j], pick) || dot3(v, nrm[j]) > on_line) return 0;
+        }
+        for (int i = 0; i < 3; ++i) v[i] /= t;
+        int he;
+        ray_neumann(s, x, v, t * (1 - 1e-4), on, n_on, on2, n2, 0.0, &he);
+        if (he >= 0) return 0;
+    }
+    double share = 1;
+    if (on2 >= 0) share = (kPi - std::acos(std::max(-1.0, std::min(1.0, dot3(n_on, n2))))) / (2 * kPi);
+    else if (on >= 0) share = 0.5;
+    return A * ball_green(d, s->sigma, t, R) * s->neumann_h[pick] / share;
+}
+
+/* neumann_data_sample for the tests: the Neumann-data term of one step from x
+ * with radius R, for a walk on sides on / on2 (normals n_on / n2, -1 / NULL:
+ * none), at step k of phase `phase` of walk walk_id. */
+double oracle_neumann_data_sample(const oracle_scene* s, const double* x, double R, int on, const double* n_on,
+                                  int on2, const double* n2, uint64_t walk_id, uint32_t k, uint32_t phase) {
+    const double zero[3] = {0, 0, 0};
+    return neumann_data_sample(s, x, R, on, n_on ? n_on : zero, on2, n2 ? n2 : zero, walk_id, k, phase);
+}
+
 /* Where a walk on stars starts: the Neumann side it sits on (-1: inside) and,
  * on an edge, the second side, with their normals out of the domain. */
 struct StarStart {
@@ -912,6 +1031,8 @@ static PhaseResult wost_walk(const oracle_scene* s, const Adjacency& adj, const 
             ray_neumann(s, x, w, rho * R, on, n_on, on2, n2, on_line, &e2);
             if (e2 < 0) acc += oracle_source_weight(d, s->sigma, R, rho) * s->f;
         }
+        if (s->neumann_h)   /* Neumann data: a point of the Neumann part in the ball, counted if x sees it */
+            acc += neumann_data_sample(s, x, R, on, n_on, on2, n2, walk_id, (uint32_t)k, phase);
         Draws r0 = draw(s->seed_lo, s->seed_hi, walk_id, (uint32_t)k, phase, 0);
         double v[3];
         sample_sphere(d, r0, v);

@@ -15,6 +15,8 @@ Scenes (all seeds fixed; geometry seed 0x2405):
   mixed boundaries (a Dirichlet part and a reflecting Neumann part):
   quarter_disk_scene, strip_scene, slit_disk_scene, cube_neumann_scene,
   thermal_scene (a heating wire under an insulating slab, observed on the slab)
+  Neumann data (du/dn given on the Neumann part): neumann_data_box_scene,
+  screened_neumann_data_box_scene, annulus_neumann_data_scene
 """
 from __future__ import annotations
 
@@ -60,6 +62,7 @@ class Scene:
     seed: int = PHILOX_SEED
     meta: dict = dc_field(default_factory=dict)
     neumann: Optional[np.ndarray] = None     # (n_elem,) int32 flags: 1 = reflecting Neumann element
+    neumann_h: Optional[np.ndarray] = None   # (n_elem,) Neumann data du/dn (n out of the domain), or None
 
     @property
     def dim(self) -> int:
@@ -561,6 +564,68 @@ def cylinder_flow_scene(a: float = 0.4, n_circle: int = 300, n_side: int = 64, n
                dg_vert=g[:, None].copy(), sigma=0.0)
     sc.eps, sc.h, sc.K, sc.query, sc.walks, sc.neumann = eps, h, K, q, walks, neumann
     sc.meta = {"a": a}
+    return sc
+
+
+def neumann_data_box_scene(dim: int = 2, c: float = 0.5, b: float = 0.3, n_side: int = 16, m: int = 4,
+                           n_query: int = 8, walks: int = 1024, eps: float = 1e-3, h: float = 1e-2, K: int = 1,
+                           seed: int = GEOMETRY_SEED) -> Scene:
+    """Neumann data on the box [-1, 1]^dim: the faces x = -1 and x = X (X = 1)
+    Dirichlet with the restricted data g = b x + c (y^2 - x^2) (2D) or
+    b x + c (y^2 + z^2 - 2 x^2) (3D), the other faces Neumann with data
+    du/dn = 2c (n out of the box); u = g.  2D: n_side segments per side; 3D:
+    2 m^2 triangles per face.  theta = [X] moves the face x = X."""
+    if dim == 2:
+        sc = strip_scene(sigma=0.0, half=1.0, n_side=n_side, n_tb=n_side, n_query=n_query, walks=walks, eps=eps,
+                         h=h, K=K, seed=seed)
+        sc.field = _field(c=(b, 0.0, 0.0), A=(-c, c, 0.0, 0.0, 0.0, 0.0))
+    else:
+        sc = cube_neumann_scene(m=m, n_query=n_query, walks=walks, eps=eps, h=h, K=K, seed=seed)
+        sc.field = _field(c=(b, 0.0, 0.0), A=(-2 * c, c, c, 0.0, 0.0, 0.0))
+    sc.name = "neumann_data_box_%dd" % dim
+    sc.data, sc.g_vert = "field", None
+    sc.neumann_h = np.where(sc.neumann == 1, 2.0 * c, 0.0)
+    sc.meta.update(c=c, b=b)
+    return sc
+
+
+def screened_neumann_data_box_scene(k: float = 1.5, s: float = 0.5, n_side: int = 32, n_query: int = 8,
+                                    walks: int = 1024, eps: float = 1e-3, h: float = 1e-2, K: int = 1,
+                                    seed: int = GEOMETRY_SEED) -> Scene:
+    """The square [-1, 1]^2 with -Lap u + k^2 u = 0: the sides x = -1 and
+    x = X (X = 1) Dirichlet with mapped data cosh(k y) -/+ s sinh(k) at their
+    vertices, the sides y = -1, 1 Neumann with data du/dn = k sinh(k);
+    u = cosh(k y) + s sinh(k x).  theta = [X] moves the side x = X."""
+    sc = strip_scene(sigma=k * k, half=1.0, n_side=n_side, n_tb=n_side, n_query=n_query, walks=walks, eps=eps,
+                     h=h, K=K, seed=seed)
+    sc.name = "screened_neumann_data_box"
+    v = sc.vert
+    sc.g_vert = np.cosh(k * v[:, 1]) + s * np.sinh(k) * np.sign(v[:, 0])
+    sc.neumann_h = np.where(sc.neumann == 1, k * np.sinh(k), 0.0)
+    sc.meta.update(k=k, s=s)
+    return sc
+
+
+def annulus_neumann_data_scene(r_in: float = 0.4, n_in: int = 128, n_out: int = 128, a: float = 1.0,
+                               b: float = 0.5, n_query: int = 8, walks: int = 1024, eps: float = 1e-3,
+                               seed: int = GEOMETRY_SEED) -> Scene:
+    """The annulus r_in < r < 1: the outer circle (n_out segments) Dirichlet
+    with mapped data a, the inner circle (n_in segments) Neumann with data
+    du/dn = -b / r_in (n out of the domain, towards the centre); u = a + b log r.
+    No shape parameters.  Query points with r in (r_in + 0.05, 0.9)."""
+    t1 = 2 * np.pi * np.arange(n_out) / n_out
+    t2 = 2 * np.pi * np.arange(n_in) / n_in
+    vert = np.concatenate([np.stack([np.cos(t1), np.sin(t1)], 1), r_in * np.stack([np.cos(t2), np.sin(t2)], 1)])
+    elem = np.concatenate([np.stack([np.arange(n_out), (np.arange(n_out) + 1) % n_out], 1),
+                           n_out + np.stack([np.arange(n_in), (np.arange(n_in) + 1) % n_in], 1)]).astype(np.int32)
+    neumann = np.concatenate([np.zeros(n_out), np.ones(n_in)]).astype(np.int32)
+    rng = np.random.default_rng(seed)
+    r = rng.uniform(r_in + 0.05, 0.9, n_query)
+    ph = rng.uniform(0.0, 2 * np.pi, n_query)
+    sc = Scene("annulus_neumann_data", vert, elem, None, data="mapped", g_vert=np.full(len(vert), a), sigma=0.0)
+    sc.eps, sc.query, sc.walks, sc.neumann = eps, np.stack([r * np.cos(ph), r * np.sin(ph)], 1), walks, neumann
+    sc.neumann_h = np.where(neumann == 1, -b / r_in, 0.0)
+    sc.meta = {"a": a, "b": b, "r_in": r_in}
     return sc
 
 

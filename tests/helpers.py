@@ -9,7 +9,7 @@ import oracle
 def to_oracle(sc, **over) -> "oracle.Problem":
     kw = dict(vert=sc.vert, elem=sc.elem, jac=sc.jac, data_kind=sc.data, g_vert=sc.g_vert,
               dg_vert=sc.dg_vert, field=sc.field, sigma=sc.sigma, f=sc.f, eps=sc.eps, h=sc.h,
-              K=sc.K, seed=sc.seed, neumann=sc.neumann)
+              K=sc.K, seed=sc.seed, neumann=sc.neumann, neumann_h=sc.neumann_h)
     kw.update(over)
     return oracle.Problem(**kw)
 

@@ -1,0 +1,137 @@
+"""Pins for the oracle's Neumann-data term of the walk on stars (Sec. 3.4,
+Eq. mixed_bvp with Robin coefficient 0 and data h = du/dn on the Neumann part;
+the derivative problem of Sec. 4.2, Eq. mixed_bvp_deriv, has zero Neumann data,
+so the data reaches du/dtheta only through the nested walks).
+
+* One step: the mean of the sample over many walk ids is the integral of
+  G_R(x, z) h over the Neumann boundary in the ball that x sees, divided by the
+  share of directions into the domain (1/2 on a side), computed by quadrature
+  from the oracle's own ball Green's function (whose step weight is pinned to
+  its flux elsewhere): a flat side below a point, the point on the side, and
+  the thermal slab, where the far face must not count (hidden behind the near
+  face from below, behind the side from a point on it).
+* Whole walks against closed forms: u = b x + c (y^2 - x^2) on a square and
+  b x + c (y^2 + z^2 - 2 x^2) on a cube with Neumann data 2c (u and du/dX = 0,
+  at interior points and on the Neumann faces), a screened square (u = cosh(k y)
+  + s sinh(k x), du/dX of the moving side) and an annulus with data on the
+  inner circle (u = a + b log r).
+Tolerances: 3.5 SE + a bias budget (eps-shell, polygon, mapped data).
+"""
+import numpy as np
+import pytest
+from scipy.integrate import quad
+
+import oracle
+from oracle import closed_forms as cf
+from oracle import estimators as est
+from paper_2405_12964_gb300 import scenes
+from tests.helpers import to_oracle
+
+Z = 3.5
+
+
+def _green(dim, t, R):
+    vol = np.pi * R * R if dim == 2 else 4.0 / 3.0 * np.pi * R ** 3
+    return oracle.source_weight(dim, 0.0, R, t / R) / vol
+
+
+def _step_mean(prob, x, R, n, **kw):
+    v = np.array([oracle.neumann_data_sample(prob, x, R, walk_id=i, step=1, **kw) for i in range(n)])
+    return v.mean(), v.std() / np.sqrt(n)
+
+
+def _check(mean, se, exact, rel_bias, abs_bias=0.0):
+    ok = np.abs(mean - exact) <= Z * se + rel_bias * np.abs(exact) + abs_bias
+    assert ok.all(), (np.round(np.abs(mean - exact) / (se + 1e-300), 2), mean, exact)
+
+
+def _run(sc, W, differential=True):
+    out = oracle.run_walks(to_oracle(sc), sc.query, W, differential=differential)
+    n = sc.query.shape[0]
+    m, se = est.point_mean_se(out["u_hat"], n, W)
+    res = {"u": m, "u_se": se, "out": out}
+    if differential:
+        res["du"], res["du_se"] = est.point_mean_se(out["udot"], n, W)
+    return res
+
+
+def test_one_step_is_the_integral_over_a_flat_side():
+    # h = 2c = 1 on the Neumann sides y = -1, 1; x at height s above y = -1, ball radius R
+    R, s, n = 0.5, 0.3, 20000
+    L = np.sqrt(R * R - s * s)
+    sc = scenes.neumann_data_box_scene(2, c=0.5)
+    pr = to_oracle(sc)
+    m, se = _step_mean(pr, [0.1, -1 + s], R, n)
+    want = quad(lambda q: _green(2, np.hypot(s, q), R), -L, L)[0]
+    assert abs(m - want) <= Z * se, (m, se, want)
+    # on the side (the bottom element under x = 0.1): the whole chord of the ball, over the share 1/2
+    e = int(np.nonzero((sc.neumann == 1) & (sc.vert[sc.elem[:, 0], 0] <= 0.1) & (sc.vert[sc.elem[:, 1], 0] > 0.1)
+                       & (sc.vert[sc.elem[:, 0], 1] == -1.0))[0][0])
+    m, se = _step_mean(pr, [0.1, -1.0], R, n, on=e, n_on=[0.0, -1.0])
+    want_on = 2 * 2 * quad(lambda q: _green(2, q, R), 0, R)[0]
+    assert abs(want_on - 2 * R / np.pi) < 1e-9          # 2 int_0^R log(R/t) / pi dt = 2 R / pi
+    assert abs(m - want_on) <= Z * se, (m, se, want_on)
+    # 3D, inside: the disk of the face y = -1 in the ball
+    sc3 = scenes.neumann_data_box_scene(3, c=0.5)
+    m, se = _step_mean(to_oracle(sc3), [0.1, -1 + s, 0.05], R, 100000)
+    want = quad(lambda r: _green(3, np.hypot(s, r), R) * 2 * np.pi * r, 0, L)[0]
+    assert abs(want - 0.02) < 1e-12                      # (R - s)^2 / (2 R) for G = (1/t - 1/R) / 4 pi
+    assert abs(m - want) <= Z * se, (m, se, want)
+
+
+def test_one_step_sees_only_the_star():
+    # the thermal slab [-0.5, 0.5] x [0.2, 0.3] with h = 1 on every slab element
+    sc = scenes.thermal_scene(n_query=2)
+    sc.neumann_h = sc.neumann.astype(np.float64)
+    pr = to_oracle(sc)
+    n = 20000
+    # from below, R = 0.25 reaches the top face (at 0.2) too, hidden behind the underside
+    R, s = 0.25, 0.1
+    m, se = _step_mean(pr, [0.0, 0.1], R, n)
+    L = np.sqrt(R * R - s * s)
+    want = quad(lambda q: _green(2, np.hypot(s, q), R), -L, L)[0]
+    hidden = quad(lambda q: _green(2, np.hypot(2 * s, q), R), -np.sqrt(R * R - 4 * s * s), np.sqrt(R * R - 4 * s * s))[0]
+    assert hidden > 4 * Z * se
+    assert abs(m - want) <= Z * se, (m, se, want, hidden)
+    # on the underside (element 88, normal out of the domain (0, 1)), R = 0.15: the top face lies
+    # behind the side; the underside's chord counts, over the share 1/2
+    R = 0.15
+    m, se = _step_mean(pr, [0.0155, 0.2], R, n, on=88, n_on=[0.0, 1.0])
+    want = 2 * R / np.pi
+    Lb = np.sqrt(R * R - 0.01)
+    behind = 2 * quad(lambda q: _green(2, np.hypot(0.1, q), R), -Lb, Lb)[0]
+    assert behind > 4 * Z * se
+    assert abs(m - want) <= Z * se, (m, se, want, behind)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_box_with_neumann_data_closed_form(dim):
+    sc = scenes.neumann_data_box_scene(dim, c=0.5, b=0.3, n_query=6)
+    q = sc.query.copy()
+    face = q[:2].copy()
+    face[:, 1] = [-1.0, 1.0]                              # on the Neumann faces y = -1, 1
+    sc.query = np.concatenate([q, face])
+    r = _run(sc, 2048)
+    u, du = cf.neumann_data_box(sc.query, 0.5, 0.3)
+    _check(r["u"], r["u_se"], u, 0.0, 4e-3)
+    _check(r["du"], np.maximum(r["du_se"], np.median(r["du_se"], axis=0)), du, 0.0, 0.02)
+    # without the data the walks estimate another function, far outside the error bars
+    sc.neumann_h = None
+    r0 = _run(sc, 2048, differential=False)
+    assert np.max(np.abs(r0["u"] - u) / r["u_se"]) > 20
+
+
+def test_screened_square_with_neumann_data_closed_form():
+    sc = scenes.screened_neumann_data_box_scene(k=1.5, s=0.5, n_query=6)
+    r = _run(sc, 2048)
+    u, du = cf.screened_neumann_data_box(sc.query, 1.5, 0.5)
+    _check(r["u"], r["u_se"], u, 3e-3, 2e-3)
+    _check(r["du"], np.maximum(r["du_se"], np.median(r["du_se"], axis=0)), du, 0.08, 0.02)
+    assert (r["out"]["kind"][:, 0] == oracle.KIND_ROULETTE).any()
+
+
+def test_annulus_with_neumann_data_closed_form():
+    sc = scenes.annulus_neumann_data_scene(n_query=6)
+    r = _run(sc, 2048, differential=False)
+    u = cf.annulus_log(sc.query, 1.0, 0.5)
+    _check(r["u"], r["u_se"], u, 0.0, 3e-3)
