@@ -223,9 +223,11 @@ def cpu_baseline(sc, budget_s: float = 15.0):
 def wost_summary(steps: int = 5, warmup: int = 2, oracle_budget_s: float = 3.0):
     """Walks on stars (Sec. 3.4, 4.2) on the GPU and in the oracle: walk-steps/s
     of the differential gradient step (U-statistic L2 gradient, K = 2) on the
-    2D thermal scene (32 points on the insulating slab x 16384 walks) and on
-    the 3D cube with four Neumann faces (64 interior points x 4096 walks),
-    inputs resident, L2 flushed between timed steps; and the FP64 oracle
+    2D thermal scene (32 points on the insulating slab x 16384 walks), on the
+    same scene with Neumann data du/dn = 0.5 on the slab (a heat flux through
+    its surface) and on the 3D cube with four Neumann faces (64 interior
+    points x 4096 walks), inputs resident, L2 flushed between timed steps; and
+    the FP64 oracle
     (brute force over every element and silhouette) on a bounded sample of
     the same walks on the host cores."""
     import numpy as np
@@ -238,7 +240,10 @@ def wost_summary(steps: int = 5, warmup: int = 2, oracle_budget_s: float = 3.0):
     from paper_2405_12964_gb300.dwos import Solver
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     out = {}
+    data = scenes.thermal_scene(n_query=32, walks=16384)
+    data.neumann_h = np.where(data.neumann == 1, 0.5, 0.0)
     for name, sc in (("thermal_2d", scenes.thermal_scene(n_query=32, walks=16384)),
+                     ("thermal_2d_neumann_data", data),
                      ("cube_3d", scenes.cube_neumann_scene(n_query=64, walks=4096, K=2))):
         s = Solver(0)
         s.load_scene(sc)
@@ -271,7 +276,8 @@ def wost_summary(steps: int = 5, warmup: int = 2, oracle_budget_s: float = 3.0):
         if oracle_budget_s <= 0:
             continue
         pr = oracle.Problem(vert=sc.vert, elem=sc.elem, jac=sc.jac, data_kind="mapped", g_vert=sc.g_vert,
-                            sigma=sc.sigma, f=sc.f, eps=sc.eps, h=sc.h, K=sc.K, seed=sc.seed, neumann=sc.neumann)
+                            sigma=sc.sigma, f=sc.f, eps=sc.eps, h=sc.h, K=sc.K, seed=sc.seed, neumann=sc.neumann,
+                            neumann_h=sc.neumann_h)
         n_pts = min(8, sc.query.shape[0])
         t0 = time.perf_counter()
         o = oracle.run_walks(pr, sc.query[:n_pts], 8, differential=True, walk_id_base=1 << 41)

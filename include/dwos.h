@@ -245,6 +245,24 @@ dwos_status dwos_set_pde(dwos_ctx* ctx, float sigma, float f);
  * ends or turns, and every one with a vertex whose Jacobian row is nonzero);
  * dwos_set_params updates all three.  Synchronises. */
 dwos_status dwos_set_neumann(dwos_ctx* ctx, const int32_t* flags, int mem);
+/* Neumann data on the Neumann part (Sec. 3.4, Eq. mixed_bvp with Robin
+ * coefficient 0 and data h = du/dn, n the normal out of the domain):
+ * h (n_elem floats, host or device by mem, constant on each element, read on
+ * the Neumann elements only; NULL or all zeros: a reflecting boundary again).
+ * Each walk-on-stars step then adds one sample of (1 / a(x)) times the
+ * integral of G_R(x, z) h(z) over the Neumann boundary in its ball that x
+ * sees (Green's second identity on the star), a(x) the share of directions
+ * into the domain at x (1 inside, 1/2 on a side, (pi - the angle between the
+ * two normals) / 2 pi at an edge): a Neumann element within R (1 - 1e-4) of x
+ * (an element that only touches the ball at a silhouette point is left out),
+ * drawn with probability proportional to its length (area) among them, and a uniform
+ * point z on it; the sample is A G_R(|z - x|) h / a(x) when |z - x| < R and x
+ * sees z (A the total measure of those elements), else 0.  The data does not
+ * depend on theta, so it enters du/dtheta only through the nested walks at
+ * the Dirichlet shell (Sec. 4.2, Eq. mixed_bvp_deriv).  Kept across
+ * dwos_set_neumann and dwos_set_params; dwos_set_boundary clears it.  Values
+ * must be finite (DWOS_ERR_INVALID_ARG).  Synchronises. */
+dwos_status dwos_set_neumann_data(dwos_ctx* ctx, const float* h, int mem);
 
 /* Bound on the BVH node fetches (binary nodes, or 32-wide node visits) that one
  * distance query of a walk may make; 0 (the default) keeps the trees' own

@@ -906,7 +906,10 @@ static double element_uniform(const oracle_scene* s, uint64_t walk_id, uint32_t 
  * the part of the Neumann boundary in the ball that x sees, a(x) the share of
  * the directions around x that point into the domain (1 inside, 1/2 on a
  * side, (pi - angle between the two normals) / 2 pi at an edge).  One sample:
- * every Neumann element closer to x than R is a candidate, of total measure A;
+ * every Neumann element closer to x than R (1 - 1e-4) is a candidate, of
+ * total measure A (the margin leaves out the elements that only touch the ball
+ * at a silhouette point, whose distance to x is R itself, and parts of others
+ * within 1e-4 R of the sphere, where G_R is below 1e-4 of its size);
  * the element is drawn with probability proportional to its measure (the
  * candidate with the least -log(U_c) / |e_c|, so that the draw does not depend
  * on the order of the candidates), z uniformly on it (block 2 of the step:
@@ -929,7 +932,7 @@ static double neumann_data_sample(const oracle_scene* s, const double* x, double
         const double d2 = d == 2 ? closest_on_segment(x, s->vert + 2 * el[0], s->vert + 2 * el[1], xb, b2)
                                  : closest_on_triangle(x, s->vert + 3 * el[0], s->vert + 3 * el[1],
                                                        s->vert + 3 * el[2], xb, b2);
-        if (!(d2 < R * R)) continue;
+        if (!(d2 < (1 - 2e-4) * R * R)) continue;
         const double m = element_measure(s, e);
         if (!(m > 0)) continue;
         A += m;

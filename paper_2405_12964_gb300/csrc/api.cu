@@ -265,6 +265,24 @@ static dwos_status build_silhouette_cones(dwos_ctx* ctx) {
     return DWOS_OK;
 }
 
+// The Neumann data per compact Neumann element, on the device; none (NULL) when no data was
+// given or it is zero on the whole Neumann part.
+static dwos_status upload_neumann_data(dwos_ctx* ctx) {
+    if (ctx->neu_data) cudaFree(ctx->neu_data);
+    ctx->neu_data = nullptr;
+    if (ctx->n_neumann == 0 || ctx->neu_data_h.size() != (size_t)ctx->n_elem) return DWOS_OK;
+    std::vector<float> c(ctx->nmap_h.size());
+    bool any = false;
+    for (size_t i = 0; i < c.size(); ++i) {
+        c[i] = ctx->neu_data_h[ctx->nmap_h[i]];
+        any = any || c[i] != 0.0f;
+    }
+    if (!any) return DWOS_OK;
+    CK(cudaMalloc(&ctx->neu_data, sizeof(float) * c.size()), "alloc Neumann data");
+    CK(cudaMemcpy(ctx->neu_data, c.data(), sizeof(float) * c.size(), cudaMemcpyHostToDevice), "copy Neumann data");
+    return DWOS_OK;
+}
+
 dwos_status rebuild(dwos_ctx* ctx) {
     ctx->inside_cached = -1;   // the inside flags belong to the old geometry
     ctx->refits = 0;
@@ -308,6 +326,7 @@ dwos_status rebuild(dwos_ctx* ctx) {
     N.sil_cone_leaf = cones ? ctx->sil_cones + std::max(ctx->bvh_s.n_internal, 0) : nullptr;
     N.cone_tol = ctx->cone_tol;
     N.cone_lmax = ctx->cone_lmax;
+    N.flux = ctx->neu_data;
     ctx->neu_host = N;
     CK(cudaMemcpyAsync(ctx->d_neu, &ctx->neu_host, sizeof(N), cudaMemcpyHostToDevice, ctx->stream),
        "copy Neumann part");
@@ -463,6 +482,7 @@ dwos_status run_walks(dwos_ctx* ctx, int n_query, const float* xq, int W, unsign
     L.traversal = P.traversal;
     L.star = P.neu != nullptr;
     L.cones = L.star && ctx->neu_host.sil_cone_node != nullptr;
+    L.data = L.star && ctx->neu_host.flux != nullptr;
     CK(cudaEventRecord(ctx->ev0, ctx->stream), "event");
     int blocks = 0;
     CK(launch_walks(L, nullptr, 1, total, cur_ctr(ctx), ctx->stream, &blocks, &P, ctx->d_ctr + (ctx->ctr_cur ^ 1)),
@@ -585,7 +605,8 @@ void dwos_destroy(dwos_ctx* ctx) {
                     ctx->xq, ctx->valid, ctx->wvec, ctx->out, ctx->acc_vert, ctx->trace, ctx->dbg, ctx->misc_f,
                     ctx->misc_i, ctx->misc_u, ctx->xq_prev, ctx->d_ctr, ctx->d_err, ctx->pw, ctx->vert_active,
                     ctx->misc_d, ctx->elem_d, ctx->elem_n, ctx->dmap, ctx->nadj, ctx->d_neu, ctx->inside_tmp,
-                    ctx->q_start, ctx->behind, ctx->behind_in, ctx->sites, ctx->elem_s, ctx->sil_cones};
+                    ctx->q_start, ctx->behind, ctx->behind_in, ctx->sites, ctx->elem_s, ctx->sil_cones,
+                    ctx->neu_data};
     bvh_free(ctx->bvh_n);
     bvh_free(ctx->bvh_s);
     for (void* p : bufs) if (p) cudaFree(p);
@@ -670,6 +691,10 @@ dwos_status dwos_set_boundary(dwos_ctx* ctx, int dim, int n_vert, const float* v
     ctx->sil_cones = nullptr;
     ctx->n_neumann = 0;
     ctx->n_sites = 0;
+    if (ctx->neu_data) cudaFree(ctx->neu_data);
+    ctx->neu_data = nullptr;
+    ctx->neu_data_h.clear();
+    ctx->nmap_h.clear();
     const size_t nv = (size_t)n_vert * dim;
     CK(cudaMalloc(&ctx->vert_ref, nv * sizeof(float)), "alloc vertices");
     CK(cudaMalloc(&ctx->vert, nv * sizeof(float)), "alloc vertices");
@@ -793,11 +818,12 @@ dwos_status dwos_set_neumann(dwos_ctx* ctx, const int32_t* flags, int mem) {
     CK(cudaMemcpyAsync(el.data(), ctx->elem, sizeof(int32_t) * el.size(), cudaMemcpyDeviceToHost, ctx->stream), "copy elements");
     CK(cudaStreamSynchronize(ctx->stream), "synchronize");
     std::vector<int32_t> ed, en, dmap;
+    std::vector<int32_t> nmap;
     for (int e = 0; e < n; ++e) {
         if (f[e] != 0 && f[e] != 1) return fail(ctx, DWOS_ERR_INVALID_ARG, "flags must be 0 or 1");
         auto& dst = f[e] ? en : ed;
         for (int k = 0; k < d; ++k) dst.push_back(el[(size_t)d * e + k]);
-        if (!f[e]) dmap.push_back(e);
+        (f[e] ? nmap : dmap).push_back(e);
     }
     const int n_n = (int)(en.size() / d);
     if (n_n > 0 && n_n == n) return fail(ctx, DWOS_ERR_INVALID_ARG, "the boundary needs a Dirichlet part");
@@ -807,7 +833,11 @@ dwos_status dwos_set_neumann(dwos_ctx* ctx, const int32_t* flags, int mem) {
     ctx->sil_cones = nullptr;
     ctx->n_neumann = 0;
     ctx->n_sites = 0;
-    if (n_n == 0) return rebuild(ctx);            // every element Dirichlet again
+    ctx->nmap_h = nmap;
+    if (n_n == 0) {                               // every element Dirichlet again
+        if (dwos_status st = upload_neumann_data(ctx)) return st;
+        return rebuild(ctx);
+    }
     // neighbours across each endpoint (segments) or edge (triangles) within the Neumann part
     std::vector<int32_t> adj((size_t)n_n * d, -1);
     std::unordered_map<unsigned long long, std::vector<int>> at;
@@ -904,7 +934,34 @@ dwos_status dwos_set_neumann(dwos_ctx* ctx, const int32_t* flags, int mem) {
     CK(cudaMemcpy(ctx->dmap, dmap.data(), sizeof(int32_t) * dmap.size(), cudaMemcpyHostToDevice), "copy");
     CK(cudaMemcpy(ctx->nadj, adj.data(), sizeof(int32_t) * adj.size(), cudaMemcpyHostToDevice), "copy");
     ctx->n_neumann = n_n;
+    if (dwos_status st = upload_neumann_data(ctx)) return st;
     return rebuild(ctx);
+}
+
+dwos_status dwos_set_neumann_data(dwos_ctx* ctx, const float* h, int mem) {
+    if (!ctx) return fail(nullptr, DWOS_ERR_INVALID_ARG, "ctx is NULL");
+    if (!ctx->have_boundary) return fail(ctx, DWOS_ERR_STATE, "no boundary: call dwos_set_boundary first");
+    if (dwos_status s = check_mem(ctx, mem)) return s;
+    if (mem == DWOS_MEM_DEVICE) if (dwos_status s = check_device_ptr(ctx, h, "h")) return s;
+    if (dwos_status s = set_device(ctx)) return s;
+    std::vector<float> hv;
+    if (h) {
+        hv.resize(ctx->n_elem);
+        CK(cudaMemcpyAsync(hv.data(), h, sizeof(float) * hv.size(), mem == DWOS_MEM_DEVICE ? cudaMemcpyDeviceToHost
+                                                                                           : cudaMemcpyHostToHost,
+                           ctx->stream), "copy Neumann data");
+        CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+        if (!finite_all(hv.data(), hv.size())) return fail(ctx, DWOS_ERR_INVALID_ARG, "Neumann data must be finite");
+    }
+    ctx->neu_data_h = hv;
+    if (dwos_status st = upload_neumann_data(ctx)) return st;
+    if (ctx->n_neumann > 0) {
+        ctx->neu_host.flux = ctx->neu_data;
+        CK(cudaMemcpyAsync(ctx->d_neu, &ctx->neu_host, sizeof(DevNeumann), cudaMemcpyHostToDevice, ctx->stream),
+           "copy Neumann part");
+        CK(cudaStreamSynchronize(ctx->stream), "synchronize");
+    }
+    return DWOS_OK;
 }
 
 dwos_status dwos_set_traversal_budget(dwos_ctx* ctx, int max_fetches) {

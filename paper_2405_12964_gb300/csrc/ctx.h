@@ -51,6 +51,11 @@ struct dwos_ctx {
     std::vector<float> vert_neu_h;
     bool neu_moving = false;
     float cone_tol = 1e30f, cone_lmax = 0.0f;               // DevNeumann::cone_tol, cone_lmax
+    // Neumann data du/dn: per input element as given (empty: none), and per compact Neumann
+    // element on the device (NULL when zero on the whole Neumann part); compact -> input element
+    std::vector<float> neu_data_h;
+    float* neu_data = nullptr;
+    std::vector<int32_t> nmap_h;
     dwos::DevNeumann* d_neu = nullptr;
     dwos::DevNeumann neu_host{};                          // what d_neu holds
     float4* q_start = nullptr; size_t q_start_cap = 0;    // per query: start on the Neumann part

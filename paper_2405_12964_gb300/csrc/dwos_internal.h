@@ -43,6 +43,9 @@ struct DevNeumann {
     // cone_tol (distance + cone_lmax), cone_tol = 1e-4 / (the smallest segment length, 3D: triangle
     // height over a candidate edge), cone_lmax the largest element size
     float cone_tol, cone_lmax;
+    // Neumann data du/dn (n out of the domain) per compact Neumann element; NULL: zero everywhere
+    // (a reflecting boundary)
+    const float* flux;
 };
 
 // Everything a walk needs about one problem.  Copied to the device (and, in
@@ -186,6 +189,7 @@ struct WalkLaunch {
     int traversal = 0;          // 2, 3: warp-wide search (every problem of the launch has wide_ok)
     bool star = false;          // walk on stars (one problem with a Neumann part)
     bool cones = false;         // walk on stars whose silhouette tree has normal cones
+    bool data = false;          // walk on stars with Neumann data (runs without the cones)
 };
 // The problems come from the device table d_probs, or (one problem, d_probs
 // NULL) by value from host_prob.  zero_counters, when given, is zeroed by the
@@ -194,7 +198,8 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
                          unsigned long long total_work, DevCounters* d_counters, cudaStream_t stream,
                          int* blocks_used, const DevProblem* host_prob = nullptr,
                          DevCounters* zero_counters = nullptr);
-int walk_max_blocks_per_sm(int dim, int block_size, int traversal = 0, bool star = false, bool cones = false);
+int walk_max_blocks_per_sm(int dim, int block_size, int traversal = 0, bool star = false, bool cones = false,
+                           bool data = false);
 // Query points on the Neumann part: per point the closest Neumann element if it
 // lies within tol of it (q_start w = its compact index, xyz = its unit normal,
 // not yet oriented) and the point 1e-3 of the element's size behind its centre

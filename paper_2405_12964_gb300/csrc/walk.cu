@@ -121,10 +121,11 @@ __device__ __forceinline__ void sphere_dir(const U4& r, float* om) {
     }
 }
 
-// STAR: walk on stars over a boundary with a reflecting Neumann part (one
-// problem per launch; the Dirichlet part's distance queries take the launch's
-// search order, the Neumann queries per lane).
-template <int DIM, bool WIDE, bool STAR = false, bool CONES = false>
+// STAR: walk on stars over a boundary with a Neumann part (one problem per
+// launch; the Dirichlet part's distance queries take the launch's search
+// order, the Neumann queries per lane).  DATA: the Neumann part carries data
+// du/dn (a separate instantiation, so that reflecting walks keep their code).
+template <int DIM, bool WIDE, bool STAR = false, bool CONES = false, bool DATA = false>
 __global__ void __launch_bounds__(256, STAR ? 3 : ((DIM == 2 || WIDE) ? 4 : 3))
     walk_kernel(const DevProblem* __restrict__ g_probs, int n_probs, unsigned long long total,
                 DevCounters* __restrict__ ctr, DevCounters* __restrict__ zero_ctr,
@@ -331,6 +332,16 @@ __global__ void __launch_bounds__(256, STAR ? 3 : ((DIM == 2 || WIDE) ? 4 : 3))
                 int h2;
                 ray_neumann<DIM>(NS, x, w, rr, on_e, n_on, on2, n2, 1e-4f * P.eps, h2, ok2);
                 if (h2 < 0) acc = fmaf(source_weight<DIM>(P.sqrt_sigma, R, ub), P.f, acc);
+            }
+            if constexpr (DATA) {   // Neumann data: a point of the Neumann part in the ball, counted if x sees it
+                Vec3 xv{{0.0f, 0.0f, 0.0f}}, nv{{0.0f, 0.0f, 0.0f}}, mv{{0.0f, 0.0f, 0.0f}};
+#pragma unroll
+                for (int i = 0; i < DIM; ++i) { xv.v[i] = x[i]; nv.v[i] = n_on[i]; mv.v[i] = n2[i]; }
+                const DataSample ds = neumann_data_sample<DIM>(NS, xv, R, on_e, nv, on2, mv, 1e-4f * P.eps,
+                                                               P.sqrt_sigma, P.seed_lo, P.seed_hi, wid, k_step,
+                                                               (uint32_t)phase);
+                acc += ds.w;
+                if (!ds.ok) ok2 = false;
             }
             const U4 r0 = draw_block(P.seed_lo, P.seed_hi, wid, k_step, (uint32_t)phase, 0u);
             float om[3];
@@ -777,12 +788,15 @@ cudaError_t launch_neumann_orient(int n, const int* behind_inside, float4* q_sta
     return cudaGetLastError();
 }
 
-int walk_max_blocks_per_sm(int dim, int block_size, int traversal, bool star, bool cones) {
+int walk_max_blocks_per_sm(int dim, int block_size, int traversal, bool star, bool cones, bool data) {
     int n = 0;
     const size_t smem = walk_smem_bytes(1, block_size, traversal, dim, star);
     const bool wide = traversal == 2 || traversal == 3;
     auto occ = [&](auto kernel) { cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, block_size, smem); };
-    if (star) {
+    if (star && data) {
+        if (dim == 2) wide ? occ(walk_kernel<2, true, true, false, true>) : occ(walk_kernel<2, false, true, false, true>);
+        else wide ? occ(walk_kernel<3, true, true, false, true>) : occ(walk_kernel<3, false, true, false, true>);
+    } else if (star) {
         if (dim == 2) {
             if (wide) cones ? occ(walk_kernel<2, true, true, true>) : occ(walk_kernel<2, true, true>);
             else cones ? occ(walk_kernel<2, false, true, true>) : occ(walk_kernel<2, false, true>);
@@ -813,7 +827,7 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
     const int bs = L.block_size;
     if (L.star && n_probs != 1) return cudaErrorInvalidValue;
     int per_sm = L.blocks_per_sm > 0 ? L.blocks_per_sm
-                                     : walk_max_blocks_per_sm(L.dim, bs, L.traversal, L.star, L.cones);
+                                     : walk_max_blocks_per_sm(L.dim, bs, L.traversal, L.star, L.cones, L.data);
     if (per_sm < 1) per_sm = 1;
     long long blocks = (long long)per_sm * L.n_sm;
     const long long need = (long long)((total + bs - 1) / bs);
@@ -835,6 +849,11 @@ cudaError_t launch_walks(const WalkLaunch& L, const DevProblem* d_probs, int n_p
     };
     if (L.star) {
         const bool wide = L.traversal == 2 || L.traversal == 3;
+        if (L.data) {   // normal cones only prune; the data instantiation runs without them
+            if (wide) return L.dim == 2 ? go(walk_kernel<2, true, true, false, true>)
+                                        : go(walk_kernel<3, true, true, false, true>);
+            return L.dim == 2 ? go(walk_kernel<2, false, true, false, true>) : go(walk_kernel<3, false, true, false, true>);
+        }
         if (L.cones) {
             if (wide) return L.dim == 2 ? go(walk_kernel<2, true, true, true>) : go(walk_kernel<3, true, true, true>);
             return L.dim == 2 ? go(walk_kernel<2, false, true, true>) : go(walk_kernel<3, false, true, true>);

@@ -464,4 +464,119 @@ __device__ __forceinline__ float star_weight(float k, float t, float R) {
     return expf(-kt) * (kt * (1.0f + expf(-2.0f * a)) - expm1f(-2.0f * a)) / -expm1f(-2.0f * kR);
 }
 
+// The Neumann-data term of a walk-on-stars step (Sec. 3.4, Eq. mixed_bvp with
+// Robin coefficient 0 and data h = du/dn, n out of the domain).  Green's second
+// identity on the star St(x, R) adds (1 / a(x)) times the integral of
+// G_R(x, z) h(z) over the part of the Neumann boundary in the ball that x sees,
+// a(x) the share of the directions around x that point into the domain (1
+// inside, 1/2 on a side, (pi - the angle between the two normals) / 2 pi at an
+// edge).  One sample: the Neumann elements closer to x than R (1 - 1e-4) are
+// the candidates, of total measure A (length in 2D, area in 3D; the margin
+// leaves out the elements that only touch the ball at a silhouette point,
+// whose distance is R itself, and parts within 1e-4 R of the sphere, where G_R
+// is below 1e-4 of its size); one is drawn with
+// probability proportional to its measure as the candidate with the least
+// -log(U_c) / |e_c| (the draw does not depend on the order in which the tree
+// offers them), U_c word 0 of Philox at the counter (walk id, step,
+// phase << 8 | 3) with the key (seed_lo, seed_hi ^ (c + 1)), c the compact
+// element; z uniform on it (block 2 of the step, words 0 and 1).  The sample
+// is A G_R(|z - x|) h / a(x) if |z - x| < R and x sees z, else 0.  x sees z if z
+// lies on a side the walk sits on; else if z is not behind those sides (an
+// element behind a side by the ray rule, or a point (z - x) . n > on_line out
+// of its plane, unless the element lies on the side's plane) and no Neumann
+// element crosses the segment before 1 - 1e-4 of its length.  Out of line:
+// only a walk over a boundary with Neumann data runs it.
+struct Vec3 { float v[3]; };
+struct DataSample { float w; int ok; };
+
+template <int DIM>
+__device__ __noinline__ DataSample neumann_data_sample(const DevNeumann& N, Vec3 xp, float R, int on, Vec3 non,
+                                                       int on2, Vec3 nn2, float on_line, float k, uint32_t seed_lo,
+                                                       uint32_t seed_hi, unsigned long long wid, uint32_t step,
+                                                       uint32_t phase) {
+    const float* x = xp.v;
+    const float R2 = R * R, C2 = R2 * (1.0f - 2e-4f);
+    float A = 0.0f, best_key = kInf;
+    int pick = -1;
+    const U4 c0{(uint32_t)wid, (uint32_t)(wid >> 32), step, (phase << 8) | 3u};
+    auto key = [&](const float* lo, const float* hi, int) { return box_dist2<DIM>(x, lo, hi); };
+    auto leaf = [&](int l) {
+        if (!(prim_dist2<DIM>(N.prims, l, x) < C2)) return;
+        float m;
+        if (DIM == 2) {
+            const float4 s = __ldg(N.prims + l);
+            m = sqrtf((s.z - s.x) * (s.z - s.x) + (s.w - s.y) * (s.w - s.y));
+        } else {
+            const float4 a = __ldg(N.prims + 3 * l), b = __ldg(N.prims + 3 * l + 1), c = __ldg(N.prims + 3 * l + 2);
+            const float e1[3] = {b.x - a.x, b.y - a.y, b.z - a.z}, e2[3] = {c.x - a.x, c.y - a.y, c.z - a.z};
+            const float w0 = e1[1] * e2[2] - e1[2] * e2[1], w1 = e1[2] * e2[0] - e1[0] * e2[2];
+            const float w2 = e1[0] * e2[1] - e1[1] * e2[0];
+            m = 0.5f * sqrtf(w0 * w0 + w1 * w1 + w2 * w2);
+        }
+        if (!(m > 0.0f)) return;
+        A += m;
+        const int e = __ldg(N.prim_elem + l);
+        const float kc = -logf(u01(philox(c0, seed_lo, seed_hi ^ (uint32_t)(e + 1)).x)) / m;
+        if (kc < best_key) { best_key = kc; pick = l; }
+    };
+    DataSample out{0.0f, 1};
+    out.ok = bvh_best_first<DIM>(N.nodes, N.n_internal, N.n_tree, N.n_big, C2, key, leaf) ? 1 : 0;
+    if (pick < 0) return out;
+    const U4 r = draw_block(seed_lo, seed_hi, wid, step, phase, 2u);
+    const float u0 = u01(r.x), u1 = u01(r.y);
+    float z[DIM];
+    if (DIM == 2) {
+        const float4 s = __ldg(N.prims + pick);
+        z[0] = fmaf(u0, s.z - s.x, s.x);
+        z[1] = fmaf(u0, s.w - s.y, s.y);
+    } else {
+        const float4 a = __ldg(N.prims + 3 * pick), b = __ldg(N.prims + 3 * pick + 1), c = __ldg(N.prims + 3 * pick + 2);
+        const float q = sqrtf(u0), wb = q * (1.0f - u1), wc = q * u1, wa = 1.0f - q;
+        z[0] = wa * a.x + wb * b.x + wc * c.x;
+        z[1] = wa * a.y + wb * b.y + wc * c.y;
+        z[DIM - 1] = wa * a.z + wb * b.z + wc * c.z;
+    }
+    float v[3] = {0.0f, 0.0f, 0.0f}, t2 = 0.0f;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) { v[i] = z[i] - x[i]; t2 = fmaf(v[i], v[i], t2); }
+    const float t = sqrtf(t2);
+    if (!(t < R) || !(t > 0.0f)) return out;
+    const int pe = __ldg(N.prim_elem + pick);
+    if (pe != on && pe != on2) {
+        const int side[2] = {on, on2};
+        const float* nrm[2] = {non.v, nn2.v};
+        for (int j = 0; j < 2; ++j) {
+            if (side[j] < 0) continue;
+            if (coplanar_side<DIM>(N, x, nrm[j], pe, on_line)) continue;
+            float dn = 0.0f;
+#pragma unroll
+            for (int i = 0; i < DIM; ++i) dn = fmaf(v[i], nrm[j][i], dn);
+            if (dn > on_line || behind_side<DIM>(N, side[j], nrm[j], pe)) return out;
+        }
+        const float it = 1.0f / t;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) v[i] *= it;
+        int hit;
+        bool ok = true;
+        ray_neumann<DIM>(N, x, v, t * (1.0f - 1e-4f), on, non.v, on2, nn2.v, 0.0f, hit, ok);
+        if (!ok) out.ok = 0;
+        if (hit >= 0) return out;
+    }
+    float share = 1.0f;
+    if (on2 >= 0) {
+        float c = 0.0f;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i) c = fmaf(non.v[i], nn2.v[i], c);
+        share = (3.14159265358979f - acosf(fminf(1.0f, fmaxf(-1.0f, c)))) * 0.159154943091895f;
+    } else if (on >= 0) {
+        share = 0.5f;
+    }
+    // G_R(t): the source weight of the ball at radius t over the ball's volume
+    const float rho = t / R;
+    const float uu = DIM == 2 ? rho * rho : rho * rho * rho;
+    const float vol = DIM == 2 ? 3.14159265358979f * R2 : 4.18879020478639f * R2 * R;
+    out.w = A * (source_weight<DIM>(k, R, uu) / vol) * __ldg(N.flux + pe) / share;
+    return out;
+}
+
 }  // namespace dwos

@@ -87,6 +87,7 @@ _SIGS = {
     "dwos_bessel_k1": [_vp, _i, _vp, _vp, _i],
     "dwos_star_weight": [_vp, _i, ctypes.c_float, _i, _vp, _vp, _vp, _i],
     "dwos_set_neumann": [_vp, _vp, _i],
+    "dwos_set_neumann_data": [_vp, _vp, _i],
     "dwos_eval_static": [_vp, _i, _vp, _i, _vp, _vp, _vp, _vp],
     "dwos_batch_create": [ctypes.POINTER(_vp), ctypes.POINTER(BatchJob), _i, _vp],
     "dwos_batch_run": [_vp],
@@ -238,6 +239,12 @@ class Solver:
         ft = None if flags is None else self._dev(np.asarray(flags, dtype=np.int32), torch.int32)
         self._check(lib().dwos_set_neumann(self._h, _ptr(ft), MEM_DEVICE))
 
+    def set_neumann_data(self, h):
+        """dwos_set_neumann_data: per-element Neumann data du/dn, n out of the domain (None: zero)."""
+        self._stream()
+        ht = None if h is None else self._dev(np.asarray(h, dtype=np.float32), torch.float32)
+        self._check(lib().dwos_set_neumann_data(self._h, _ptr(ht), MEM_DEVICE))
+
     def set_pde(self, sigma: float, f: float = 0.0):
         self._check(lib().dwos_set_pde(self._h, float(sigma), float(f)))
 
@@ -250,6 +257,8 @@ class Solver:
         self.set_boundary(sc.vert, sc.elem, sc.jac)
         if getattr(sc, "neumann", None) is not None:
             self.set_neumann(sc.neumann)
+        if getattr(sc, "neumann_h", None) is not None:
+            self.set_neumann_data(sc.neumann_h)
         if sc.data == "field":
             self.set_dirichlet_field(sc.field)
         else:
