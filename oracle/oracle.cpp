@@ -888,16 +888,23 @@ static double ball_green(int dim, double sigma, double t, double R) {
     return oracle_source_weight(dim, sigma, R, t / R) / vol;
 }
 
+/* The 32-bit finaliser of Appleby's MurmurHash3: a bijection of 32-bit words
+ * in which every input bit reaches every output bit. */
+static uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
 /* Uniform in (0, 1) for the Neumann element of index c (counted among the
- * Neumann elements in input order) at step k of a walk phase: Philox with the
- * counter (walk id, k, (phase << 8) | 3) and the key (seed_lo, seed_hi ^ (c + 1)),
- * word 0. */
-static double element_uniform(const oracle_scene* s, uint64_t walk_id, uint32_t k, uint32_t phase, int c) {
-    const uint32_t ctr[4] = {(uint32_t)walk_id, (uint32_t)(walk_id >> 32), k, (phase << 8) | 3u};
-    const uint32_t key[2] = {s->seed_lo, s->seed_hi ^ (uint32_t)(c + 1)};
-    uint32_t out[4];
-    philox4x32_10(ctr, key, out);
-    return to_uniform(out[0]);
+ * Neumann elements in input order), from the step's word w (word 2 of block 2):
+ * fmix32(w + (c + 1) * 0x9E3779B9).  For each c it is uniform over w (fmix32 is a
+ * bijection); the mix spreads neighbouring indices apart. */
+static double element_uniform(uint32_t w, int c) {
+    return to_uniform(fmix32(w + (uint32_t)(c + 1) * 0x9E3779B9u));
 }
 
 /* The Neumann-data term of a walk-on-stars step (Sec. 3.4, Eq. mixed_bvp with
@@ -911,9 +918,9 @@ static double element_uniform(const oracle_scene* s, uint64_t walk_id, uint32_t 
  * at a silhouette point, whose distance to x is R itself, and parts of others
  * within 1e-4 R of the sphere, where G_R is below 1e-4 of its size);
  * the element is drawn with probability proportional to its measure (the
- * candidate with the least -log(U_c) / |e_c|, so that the draw does not depend
- * on the order of the candidates), z uniformly on it (block 2 of the step:
- * words 0 and 1); the estimate is A G_R(|z - x|) h(e) / a(x) if |z - x| < R
+ * candidate with the least -log(U_c) / |e_c|, U_c from element_uniform, so that
+ * the draw does not depend on the order of the candidates), z uniformly on it
+ * (block 2 of the step: words 0 and 1); the estimate is A G_R(|z - x|) h(e) / a(x) if |z - x| < R
  * and x sees z, else 0.  x sees z if z lies on a side the walk sits on, or
  * else, z not behind those sides (a point (z - x) . n > 1e-4 eps out of a
  * side's plane, or an element behind it by the ray rule, unless it is on the
@@ -922,6 +929,10 @@ static double element_uniform(const oracle_scene* s, uint64_t walk_id, uint32_t 
 static double neumann_data_sample(const oracle_scene* s, const double* x, double R, int on, const double* n_on,
                                   int on2, const double* n2, uint64_t walk_id, uint32_t k, uint32_t phase) {
     const int d = s->dim;
+    const uint32_t ctr[4] = {(uint32_t)walk_id, (uint32_t)(walk_id >> 32), k, (phase << 8) | 2u};
+    const uint32_t key2[2] = {s->seed_lo, s->seed_hi};
+    uint32_t blk[4];
+    philox4x32_10(ctr, key2, blk);
     double A = 0, best = INFINITY;
     int pick = -1;
     for (int e = 0, c = 0; e < s->n_elem; ++e) {
@@ -936,11 +947,11 @@ static double neumann_data_sample(const oracle_scene* s, const double* x, double
         const double m = element_measure(s, e);
         if (!(m > 0)) continue;
         A += m;
-        const double key = -std::log(element_uniform(s, walk_id, k, phase, ci)) / m;
+        const double key = -std::log(element_uniform(blk[2], ci)) / m;
         if (key < best) { best = key; pick = e; }
     }
     if (pick < 0) return 0;
-    const Draws r = draw(s->seed_lo, s->seed_hi, walk_id, k, phase, 2);
+    const Draws r = {{to_uniform(blk[0]), to_uniform(blk[1]), to_uniform(blk[2])}};
     const int* el = s->elem + (size_t)d * pick;
     double z[3] = {0, 0, 0};
     if (d == 2) {

@@ -477,15 +477,25 @@ __device__ __forceinline__ float star_weight(float k, float t, float R) {
 // is below 1e-4 of its size); one is drawn with
 // probability proportional to its measure as the candidate with the least
 // -log(U_c) / |e_c| (the draw does not depend on the order in which the tree
-// offers them), U_c word 0 of Philox at the counter (walk id, step,
-// phase << 8 | 3) with the key (seed_lo, seed_hi ^ (c + 1)), c the compact
-// element; z uniform on it (block 2 of the step, words 0 and 1).  The sample
+// offers them), U_c = fmix32(w + (c + 1) 0x9E3779B9) as a uniform, w word 2 of
+// block 2 of the step, c the compact element, fmix32 the 32-bit finaliser of
+// Appleby's MurmurHash3 (a bijection: each U_c is uniform over w); z uniform on
+// it (block 2, words 0 and 1).  The sample
 // is A G_R(|z - x|) h / a(x) if |z - x| < R and x sees z, else 0.  x sees z if z
 // lies on a side the walk sits on; else if z is not behind those sides (an
 // element behind a side by the ray rule, or a point (z - x) . n > on_line out
 // of its plane, unless the element lies on the side's plane) and no Neumann
 // element crosses the segment before 1 - 1e-4 of its length.  Out of line:
 // only a walk over a boundary with Neumann data runs it.
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
 struct Vec3 { float v[3]; };
 struct DataSample { float w; int ok; };
 
@@ -498,7 +508,7 @@ __device__ __noinline__ DataSample neumann_data_sample(const DevNeumann& N, Vec3
     const float R2 = R * R, C2 = R2 * (1.0f - 2e-4f);
     float A = 0.0f, best_key = kInf;
     int pick = -1;
-    const U4 c0{(uint32_t)wid, (uint32_t)(wid >> 32), step, (phase << 8) | 3u};
+    const U4 r = draw_block(seed_lo, seed_hi, wid, step, phase, 2u);
     auto key = [&](const float* lo, const float* hi, int) { return box_dist2<DIM>(x, lo, hi); };
     auto leaf = [&](int l) {
         if (!(prim_dist2<DIM>(N.prims, l, x) < C2)) return;
@@ -516,13 +526,12 @@ __device__ __noinline__ DataSample neumann_data_sample(const DevNeumann& N, Vec3
         if (!(m > 0.0f)) return;
         A += m;
         const int e = __ldg(N.prim_elem + l);
-        const float kc = -logf(u01(philox(c0, seed_lo, seed_hi ^ (uint32_t)(e + 1)).x)) / m;
+        const float kc = -logf(u01(fmix32(r.z + (uint32_t)(e + 1) * 0x9E3779B9u))) / m;
         if (kc < best_key) { best_key = kc; pick = l; }
     };
     DataSample out{0.0f, 1};
     out.ok = bvh_best_first<DIM>(N.nodes, N.n_internal, N.n_tree, N.n_big, C2, key, leaf) ? 1 : 0;
     if (pick < 0) return out;
-    const U4 r = draw_block(seed_lo, seed_hi, wid, step, phase, 2u);
     const float u0 = u01(r.x), u1 = u01(r.y);
     float z[DIM];
     if (DIM == 2) {
