@@ -7,7 +7,8 @@ so the data reaches du/dtheta only through the nested walks).
   G_R(x, z) h over the Neumann boundary in the ball that x sees, divided by the
   share of directions into the domain (1/2 on a side), computed by quadrature
   from the oracle's own ball Green's function (whose step weight is pinned to
-  its flux elsewhere): a flat side below a point, the point on the side, and
+  its flux elsewhere): a flat side below a point, the point on the side, the
+  quarter disk's right-angled corner of two Neumann radii (share 1/4), and
   the thermal slab, where the far face must not count (hidden behind the near
   face from below, behind the side from a point on it).
 * Whole walks against closed forms: u = b x + c (y^2 - x^2) on a square and
@@ -135,3 +136,22 @@ def test_annulus_with_neumann_data_closed_form():
     r = _run(sc, 2048, differential=False)
     u = cf.annulus_log(sc.query, 1.0, 0.5)
     _check(r["u"], r["u_se"], u, 0.0, 3e-3)
+
+
+def test_one_step_at_an_edge_takes_the_wedge_share():
+    # the quarter disk's corner at the origin, where its two Neumann radii meet at a right angle:
+    # a walk there sits on the x-axis element 144 (normal out of the domain (0, -1)) and the y-axis
+    # element 143 ((-1, 0)); the share of directions into the domain is 1/4, and both radii's
+    # chords of the ball count: 2 int_0^R G / (1/4) = 4 R / pi
+    sc = scenes.quarter_disk_scene("field", n_query=2)
+    sc.neumann_h = sc.neumann.astype(np.float64)
+    pr = to_oracle(sc)
+    assert np.allclose(sc.vert[sc.elem[144]], [[0, 0], [1 / 16, 0]])
+    assert np.allclose(sc.vert[sc.elem[143]], [[0, 1 / 16], [0, 0]])
+    R = 0.3
+    m, se = _step_mean(pr, [0.0, 0.0], R, 20000, on=144, n_on=[0.0, -1.0], on2=143, n2=[-1.0, 0.0])
+    want = 4 * R / np.pi
+    assert abs(m - want) <= Z * se, (m, se, want)
+    # as if the walk were on one side only: the share 1/2 halves it
+    m1, se1 = _step_mean(pr, [0.0, 0.0], R, 20000, on=144, n_on=[0.0, -1.0])
+    assert abs(m1 - want / 2) <= Z * se1, (m1, se1, want / 2)
