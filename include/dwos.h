@@ -208,8 +208,8 @@ dwos_status dwos_set_dirichlet_field(dwos_ctx* ctx, const double* coeffs);
 /* Screening sigma >= 0 and constant source f (of -Lap u + sigma u = f). */
 dwos_status dwos_set_pde(dwos_ctx* ctx, float sigma, float f);
 /* Mixed Dirichlet / Neumann boundary (Sec. 3.4, Eq. mixed_bvp with Robin
- * coefficient 0 and zero Neumann data: a reflecting boundary, as in the
- * paper's thermal design, Sec. 6.3).  flags (n_elem int32, host or device by
+ * coefficient 0: a reflecting boundary, as in the paper's thermal design,
+ * Sec. 6.3, until dwos_set_neumann_data gives it data du/dn).  flags (n_elem int32, host or device by
  * mem): 1 marks an element of the Neumann part, 0 of the Dirichlet part; NULL
  * or all zeros makes every element Dirichlet again.  The Dirichlet part must
  * not be empty.  With a Neumann part every walk-running call (dwos_eval,

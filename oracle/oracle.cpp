@@ -36,10 +36,11 @@
  *    query treats the walk as if it had reached the shell at its current
  *    closest point (kind CAPPED).  The paper sets no cap.
  *  - Mixed Dirichlet-Neumann boundaries (Sec. 3.4, Eq. mixed_bvp, with Robin
- *    coefficient 0 and zero Neumann data, as in the thermal design of
- *    Sec. 6.3): the walks are walks on stars (see wost_walk below), and the
- *    differential walk nests at the Dirichlet shell only (Sec. 4.2, Eq.
- *    mixed_bvp_deriv).  The star radius is at least eps.
+ *    coefficient 0; zero Neumann data as in the thermal design of Sec. 6.3,
+ *    or data du/dn per element, see neumann_data_sample below): the walks are
+ *    walks on stars (see wost_walk below), and the differential walk nests at
+ *    the Dirichlet shell only (Sec. 4.2, Eq. mixed_bvp_deriv).  The star
+ *    radius is at least eps.
  *
  * Random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11), keyed by
  * the seed; counter = (walk id lo, walk id hi, step, (phase << 8) | block).

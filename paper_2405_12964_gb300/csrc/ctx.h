@@ -33,7 +33,7 @@ struct dwos_ctx {
     dwos::BvhBuffers bvh;        // over every element, or over the Dirichlet part when there is a Neumann part
     int refits = 0;              // parameter updates applied by refitting since the last full build
     bool have_boundary = false;
-    // reflecting Neumann part (walk on stars); n_neumann = 0 when every element is Dirichlet
+    // Neumann part (walk on stars); n_neumann = 0 when every element is Dirichlet
     int n_neumann = 0;
     int* elem_d = nullptr;       // compact Dirichlet elements (the main BVH's numbering)
     int* elem_n = nullptr;       // compact Neumann elements

@@ -12,7 +12,8 @@ Scenes (all seeds fixed; geometry seed 0x2405):
   star_box_scene   star-shaped emitter inside the box [-1, 1]^2
   sh_sphere_scene  SH-perturbed icosphere inside the box [-2, 2]^3
   translated_star_scene  the star_box geometry with the star's position as the parameter
-  mixed boundaries (a Dirichlet part and a reflecting Neumann part):
+  mixed boundaries (a Dirichlet part and a Neumann part, reflecting unless
+  the scene sets neumann_h):
   quarter_disk_scene, strip_scene, slit_disk_scene, cube_neumann_scene,
   thermal_scene (a heating wire under an insulating slab, observed on the slab)
   Neumann data (du/dn given on the Neumann part): neumann_data_box_scene,
