@@ -3,8 +3,9 @@
 Walks are independent and keyed by their global walk id, so sharding the
 query points across ranks (each rank running its points with the matching
 walk-id base) and summing per-point partial sums reproduces the unsharded
-result bit for bit.  Also checks the bench's rank aggregation (max time, sum
-of walk-steps).
+result bit for bit, for walks on spheres and for walks on stars with
+Neumann data (whose per-step element draw is keyed by the walk id too).
+Also checks the bench's rank aggregation (max time, sum of walk-steps).
 """
 import os
 import socket
@@ -22,7 +23,14 @@ def _free_port():
     return port
 
 
-def _worker(rank, world, port, q):
+def _scene(name):
+    from paper_2405_12964_gb300 import scenes
+    if name == "disk":
+        return scenes.disk_scene("screened_1", n_query=10)
+    return scenes.neumann_data_box_scene(2, n_query=10)
+
+
+def _worker(rank, world, port, q, name):
     import torch
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
@@ -33,7 +41,7 @@ def _worker(rank, world, port, q):
         from paper_2405_12964_gb300 import scenes
         from tests.helpers import to_oracle
         import bench
-        sc = scenes.disk_scene("screened_1", n_query=10)
+        sc = _scene(name)
         W = 48
         n = sc.query.shape[0]
         bounds = np.linspace(0, n, world + 1).astype(int)
@@ -51,7 +59,8 @@ def _worker(rank, world, port, q):
         dist.destroy_process_group()
 
 
-def test_sharded_walks_reduce_to_the_unsharded_result():
+@pytest.mark.parametrize("name", ["disk", "neumann_data_box"])
+def test_sharded_walks_reduce_to_the_unsharded_result(name):
     import oracle
     from paper_2405_12964_gb300 import scenes
     from tests.helpers import to_oracle
@@ -59,7 +68,7 @@ def test_sharded_walks_reduce_to_the_unsharded_result():
     q = ctx.Queue()
     port = _free_port()
     world = 2
-    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q, name)) for r in range(world)]
     for p in procs:
         p.start()
     res = [q.get(timeout=240) for _ in range(world)]
@@ -67,7 +76,7 @@ def test_sharded_walks_reduce_to_the_unsharded_result():
         p.join(timeout=60)
         assert p.exitcode == 0
     res.sort(key=lambda r: r[0])
-    sc = scenes.disk_scene("screened_1", n_query=10)
+    sc = _scene(name)
     W = 48
     o = oracle.run_walks(to_oracle(sc), sc.query, W, differential=True)
     want = np.zeros((10, 1 + sc.n_param))
