@@ -908,14 +908,29 @@ static double element_uniform(uint32_t w, int c) {
     return to_uniform(fmix32(w + (uint32_t)(c + 1) * 0x9E3779B9u));
 }
 
+/* Element e lies wholly behind side `side` (unit normal n out of the domain)
+ * of a walk at x: every vertex more than 2e-4 eps behind the side's plane
+ * through x.  x sees no point of it. */
+static bool wholly_behind(const oracle_scene* s, int e, const double* x, int side, const double* n) {
+    if (side < 0) return false;
+    const int d = s->dim;
+    for (int j = 0; j < d; ++j) {
+        const double* p = s->vert + (size_t)d * s->elem[(size_t)d * e + j];
+        double r[3] = {0, 0, 0};
+        for (int i = 0; i < d; ++i) r[i] = p[i] - x[i];
+        if (!(dot3(r, n) > 2e-4 * s->eps)) return false;
+    }
+    return true;
+}
+
 /* The Neumann-data term of a walk-on-stars step (Sec. 3.4, Eq. mixed_bvp with
  * Robin coefficient 0 and data h = du/dn; Green's second identity on the star
  * St(x, R)): the walk adds (1 / a(x)) times the integral of G_R(x, z) h(z) over
  * the part of the Neumann boundary in the ball that x sees, a(x) the share of
  * the directions around x that point into the domain (1 inside, 1/2 on a
  * side, (pi - angle between the two normals) / 2 pi at an edge).  One sample:
- * every Neumann element closer to x than R (1 - 1e-4) is a candidate, of
- * total measure A (the margin leaves out the elements that only touch the ball
+ * every Neumann element closer to x than R (1 - 1e-4) and not wholly behind a
+ * side the walk sits on (it would give 0) is a candidate, of total measure A (the margin leaves out the elements that only touch the ball
  * at a silhouette point, whose distance to x is R itself, and parts of others
  * within 1e-4 R of the sphere, where G_R is below 1e-4 of its size);
  * the element is drawn with probability proportional to its measure (the
@@ -945,6 +960,7 @@ static double neumann_data_sample(const oracle_scene* s, const double* x, double
                                  : closest_on_triangle(x, s->vert + 3 * el[0], s->vert + 3 * el[1],
                                                        s->vert + 3 * el[2], xb, b2);
         if (!(d2 < (1 - 2e-4) * R * R)) continue;
+        if (wholly_behind(s, e, x, on, n_on) || wholly_behind(s, e, x, on2, n2)) continue;
         const double m = element_measure(s, e);
         if (!(m > 0)) continue;
         A += m;

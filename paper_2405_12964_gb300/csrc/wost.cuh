@@ -470,8 +470,9 @@ __device__ __forceinline__ float star_weight(float k, float t, float R) {
 // G_R(x, z) h(z) over the part of the Neumann boundary in the ball that x sees,
 // a(x) the share of the directions around x that point into the domain (1
 // inside, 1/2 on a side, (pi - the angle between the two normals) / 2 pi at an
-// edge).  One sample: the Neumann elements closer to x than R (1 - 1e-4) are
-// the candidates, of total measure A (length in 2D, area in 3D; the margin
+// edge).  One sample: the Neumann elements closer to x than R (1 - 1e-4) and
+// not wholly behind a side the walk sits on (every vertex more than 2e-4 eps
+// behind its plane through x: no point of them is seen) are the candidates, of total measure A (length in 2D, area in 3D; the margin
 // leaves out the elements that only touch the ball at a silhouette point,
 // whose distance is R itself, and parts within 1e-4 R of the sphere, where G_R
 // is below 1e-4 of its size); one is drawn with
@@ -505,7 +506,7 @@ __device__ __noinline__ DataSample neumann_data_sample(const DevNeumann& N, Vec3
                                                        uint32_t seed_hi, unsigned long long wid, uint32_t step,
                                                        uint32_t phase) {
     const float* x = xp.v;
-    const float R2 = R * R, C2 = R2 * (1.0f - 2e-4f);
+    const float R2 = R * R, C2 = R2 * (1.0f - 2e-4f), behind_tol = 2.0f * on_line;
     float A = 0.0f, best_key = kInf;
     int pick = -1;
     const U4 r = draw_block(seed_lo, seed_hi, wid, step, phase, 2u);
@@ -515,9 +516,23 @@ __device__ __noinline__ DataSample neumann_data_sample(const DevNeumann& N, Vec3
         float m;
         if (DIM == 2) {
             const float4 s = __ldg(N.prims + l);
+            for (int j = 0; j < 2; ++j) {
+                if ((j ? on2 : on) < 0) continue;
+                const float* n = j ? nn2.v : non.v;
+                if (fmaf(s.x - x[0], n[0], (s.y - x[1]) * n[1]) > behind_tol &&
+                    fmaf(s.z - x[0], n[0], (s.w - x[1]) * n[1]) > behind_tol) return;
+            }
             m = sqrtf((s.z - s.x) * (s.z - s.x) + (s.w - s.y) * (s.w - s.y));
         } else {
             const float4 a = __ldg(N.prims + 3 * l), b = __ldg(N.prims + 3 * l + 1), c = __ldg(N.prims + 3 * l + 2);
+            for (int j = 0; j < 2; ++j) {
+                if ((j ? on2 : on) < 0) continue;
+                const float* n = j ? nn2.v : non.v;
+                auto ahead = [&](float4 p) {
+                    return fmaf(p.x - x[0], n[0], fmaf(p.y - x[1], n[1], (p.z - x[DIM - 1]) * n[DIM - 1]));
+                };
+                if (ahead(a) > behind_tol && ahead(b) > behind_tol && ahead(c) > behind_tol) return;
+            }
             const float e1[3] = {b.x - a.x, b.y - a.y, b.z - a.z}, e2[3] = {c.x - a.x, c.y - a.y, c.z - a.z};
             const float w0 = e1[1] * e2[2] - e1[2] * e2[1], w1 = e1[2] * e2[0] - e1[0] * e2[2];
             const float w2 = e1[0] * e2[1] - e1[1] * e2[0];
