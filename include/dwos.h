@@ -254,8 +254,10 @@ dwos_status dwos_set_neumann(dwos_ctx* ctx, const int32_t* flags, int mem);
  * sees (Green's second identity on the star), a(x) the share of directions
  * into the domain at x (1 inside, 1/2 on a side, (pi - the angle between the
  * two normals) / 2 pi at an edge): a Neumann element within R (1 - 1e-4) of x
- * (an element that only touches the ball at a silhouette point is left out),
- * drawn with probability proportional to its length (area) among them, and a uniform
+ * (an element that only touches the ball at a silhouette point is left out,
+ * and so is one wholly behind a side the walk sits on: every vertex more than
+ * 2e-4 eps behind the side's plane), drawn with probability proportional to its
+ * length (area) among them by per-element keys, and a uniform
  * point z on it; the sample is A G_R(|z - x|) h / a(x) when |z - x| < R and x
  * sees z (A the total measure of those elements), else 0.  The data does not
  * depend on theta, so it enters du/dtheta only through the nested walks at
