@@ -8,9 +8,13 @@ arithmetic.
 
 Contents
   oracle.cpp       Algorithms 1 and 2 in FP64 with brute-force closest point and
-                   an independent Philox4x32-10 (ctypes-loaded from liboracle.so)
+                   an independent Philox4x32-10 (ctypes-loaded from liboracle.so);
+                   walks on stars for mixed Dirichlet / Neumann boundaries (Sec.
+                   3.4, 4.2), reflecting or with Neumann data du/dn
   estimators.py    per-point means, the product estimators of Sec. 4.3, VJPs
-  closed_forms.py  exact disk / ball solutions used to pin the oracle
+  closed_forms.py  exact solutions used to pin the oracle (disk, ball, and the
+                   mixed-boundary scenes: quarter disk, strips, cube, cylinder
+                   and sphere flow, boxes and an annulus with Neumann data)
   cv.py            the nested walks' control-variate table (tangential data gradient)
   mlp.py           the control-variate network with BF16 product operands, and
                    error bounds for an FP32-accumulating implementation
