@@ -11,6 +11,8 @@ so the data reaches du/dtheta only through the nested walks).
   quarter disk's right-angled corner of two Neumann radii (share 1/4), and
   the thermal slab, where the far face must not count (hidden behind the near
   face from below, behind the side from a point on it).
+* The data only adds to the estimate: the walks' paths do not depend on it,
+  and each walk's u and udot are affine in it (superposition of two data sets).
 * Whole walks against closed forms: u = b x + c (y^2 - x^2) on a square and
   b x + c (y^2 + z^2 - 2 x^2) on a cube with Neumann data 2c (u and du/dX = 0,
   at interior points and on the Neumann faces), a screened square (u = cosh(k y)
@@ -155,3 +157,24 @@ def test_one_step_at_an_edge_takes_the_wedge_share():
     # as if the walk were on one side only: the share 1/2 halves it
     m1, se1 = _step_mean(pr, [0.0, 0.0], R, 20000, on=144, n_on=[0.0, -1.0])
     assert abs(m1 - want / 2) <= Z * se1, (m1, se1, want / 2)
+
+
+def test_the_data_enters_linearly_and_leaves_the_walks_unchanged():
+    # the data sample adds to the estimate and draws from its own block: the walks' paths, steps
+    # and terminal elements do not depend on h, and each walk's estimate is affine in h
+    sc = scenes.thermal_scene(n_query=4)
+    rng = np.random.default_rng(7)
+    h1 = np.where(sc.neumann == 1, rng.normal(size=len(sc.elem)), 0.0)
+    h2 = np.where(sc.neumann == 1, rng.normal(size=len(sc.elem)), 0.0)
+    runs = {}
+    for name, hv in (("0", None), ("1", h1), ("2", h2), ("12", h1 + 2.0 * h2)):
+        sc.neumann_h = hv
+        runs[name] = oracle.run_walks(to_oracle(sc), sc.query, 32, differential=True)
+    for k in ("kind", "steps", "elem"):
+        for name in ("1", "2", "12"):
+            assert np.array_equal(runs[name][k], runs["0"][k])
+    u0, u1, u2, u12 = (runs[n]["u_hat"] for n in ("0", "1", "2", "12"))
+    assert np.abs(u1 - u0).max() > 1e-3 and np.abs(u2 - u0).max() > 1e-3
+    assert np.allclose(u12 - u0, (u1 - u0) + 2.0 * (u2 - u0), rtol=1e-9, atol=1e-12)
+    d0, d1, d2, d12 = (runs[n]["udot"] for n in ("0", "1", "2", "12"))
+    assert np.allclose(d12 - d0, (d1 - d0) + 2.0 * (d2 - d0), rtol=1e-9, atol=1e-9)
