@@ -216,17 +216,19 @@ def cylinder_flow(x, a: float):
     return u, u[:, None].copy()
 
 
-def sphere_flow(x, a: float):
+def sphere_flow(x, a: float, q: float = 0.0):
     """Potential flow past a sphere: u = x (1 + a^3 / (2 r^3)) = f(r) cos(theta)
     with f = r + a^3 / (2 r^2), harmonic where r > 0 (f'' + 2 f'/r - 2 f/r^2 = 0)
     and du/dr = f'(a) cos(theta) = 0 on the sphere r = a: with a reflecting
     Neumann sphere of radius a and Dirichlet data u on an outer boundary, the
     solution is u itself.  With the data scaled by a parameter c (at c = 1),
-    du/dc = u."""
+    du/dc = u.  A source q / r (harmonic, du/dn = q / a^2 on the sphere with n
+    towards the centre) adds to u with data q / a^2 on the sphere and q / r on
+    the outer boundary; unscaled by c, it leaves du/dc as it was."""
     x = np.atleast_2d(np.asarray(x, dtype=np.float64))
     r3 = np.sum(x * x, axis=1) ** 1.5
     u = x[:, 0] * (1.0 + a ** 3 / (2.0 * r3))
-    return u, u[:, None].copy()
+    return u + q / np.cbrt(r3), u[:, None].copy()
 
 
 def neumann_data_box(x, c: float, b: float):

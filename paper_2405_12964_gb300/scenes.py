@@ -702,14 +702,17 @@ def thermal_scene_3d(offset=(0.0, 0.0, 0.0), freq: int = 4, slab_m: int = 4, box
 
 
 def sphere_flow_scene(a: float = 0.4, freq: int = 6, m: int = 8, n_query: int = 8, walks: int = 1024,
-                      eps: float = 1e-3, h: float = 1e-2, K: int = 1, r_min: float = 0.6,
+                      eps: float = 1e-3, h: float = 1e-2, K: int = 1, r_min: float = 0.6, q: float = 0.0,
                       seed: int = GEOMETRY_SEED) -> Scene:
     """Potential flow past a sphere in 3D: the box [-1, 1]^3 (2 m^2 triangles
     per face, Dirichlet, mapped data g = x (1 + a^3 / (2 r^3)) at the vertices,
     scaled by one data parameter c at c = 1) around an insulating geodesic
     icosphere of radius a (20 freq^2 triangles, reflecting Neumann; every edge
     a silhouette candidate).  u = x (1 + a^3 / (2 r^3)) in the domain,
-    du/dc = u.  Query points uniform in |x|_inf < 0.9 with r > r_min."""
+    du/dc = u.  With q != 0 the sphere also emits a point-source flow: Neumann
+    data du/dn = q / a^2 on it (n out of the domain, towards the centre) and
+    q / r added to the box's data, not scaled by c; u gains q / r, du/dc stays
+    the flow.  Query points uniform in |x|_inf < 0.9 with r > r_min."""
     bv, be = box3d_grid(m)
     sv, se = icosphere(freq)
     vert = np.concatenate([bv, a * sv], 0)
@@ -718,14 +721,17 @@ def sphere_flow_scene(a: float = 0.4, freq: int = 6, m: int = 8, n_query: int = 
     r3 = np.sum(vert * vert, axis=1) ** 1.5
     g = vert[:, 0] * (1.0 + a ** 3 / (2.0 * r3))
     rng = np.random.default_rng(seed)
-    q = np.zeros((0, 3))
-    while len(q) < n_query:
+    pts = np.zeros((0, 3))
+    while len(pts) < n_query:
         p = rng.uniform(-0.9, 0.9, size=(4 * n_query, 3))
-        q = np.concatenate([q, p[np.linalg.norm(p, axis=1) > r_min]])[:n_query]
-    sc = Scene("sphere_flow", vert, elem, np.zeros((len(vert), 3, 1)), data="mapped", g_vert=g,
+        pts = np.concatenate([pts, p[np.linalg.norm(p, axis=1) > r_min]])[:n_query]
+    g_all = g + (q / np.cbrt(r3) if q else 0.0)
+    sc = Scene("sphere_flow", vert, elem, np.zeros((len(vert), 3, 1)), data="mapped", g_vert=g_all,
                dg_vert=g[:, None].copy(), sigma=0.0)
-    sc.eps, sc.h, sc.K, sc.query, sc.walks, sc.neumann = eps, h, K, q, walks, neumann
-    sc.meta = {"a": a}
+    sc.eps, sc.h, sc.K, sc.query, sc.walks, sc.neumann = eps, h, K, pts, walks, neumann
+    if q:
+        sc.neumann_h = np.where(neumann == 1, q / (a * a), 0.0)
+    sc.meta = {"a": a, "q": q}
     return sc
 
 
