@@ -10,7 +10,10 @@ so the data reaches du/dtheta only through the nested walks).
   its flux elsewhere): a flat side below a point, the point on the side, the
   quarter disk's right-angled corner of two Neumann radii (share 1/4), and
   the thermal slab, where the far face must not count (hidden behind the near
-  face from below, behind the side from a point on it).
+  face from below, behind the side from a point on it); and, on a side cut into
+  segments of very different lengths with data on one segment only, the
+  draw's probability proportional to each candidate's length (a uniform mesh
+  would pass any draw).
 * The data only adds to the estimate: the walks' paths do not depend on it,
   and each walk's u and udot are affine in it (superposition of two data sets).
 * Whole walks against closed forms: u = b x + c (y^2 - x^2) on a square and
@@ -197,3 +200,34 @@ def test_sphere_with_neumann_data_closed_form():
     sc.neumann_h = None
     r0 = _run(sc, 2048, differential=False)
     assert np.max(np.abs(r0["u"] - u) / r0["u_se"]) > 8
+
+
+def test_one_step_draws_elements_in_proportion_to_their_length():
+    # a box whose bottom (the Neumann part) is cut into segments of very different lengths
+    # (nodes at -1 + 2 (i / 12)^2); data 1 on one segment and 0 elsewhere: the mean of the step's
+    # sample is the quadrature over that segment's chord alone only if every candidate is drawn
+    # with probability proportional to its length (on a uniform mesh any draw would pass)
+    n = 12
+    xs = -1.0 + 2.0 * (np.arange(n + 1) / n) ** 2
+    bottom = np.stack([xs[:-1], np.full(n, -1.0)], 1)
+    sides = [np.array([[1.0, -1.0]]), np.array([[1.0, 1.0]]), np.array([[-1.0, 1.0]])]
+    vert = np.concatenate([bottom] + sides, 0)
+    nv = len(vert)
+    elem = np.stack([np.arange(nv), (np.arange(nv) + 1) % nv], 1).astype(np.int32)
+    neumann = np.zeros(nv, np.int32)
+    neumann[:n] = 1
+    x, R = np.array([-0.5, -0.75]), 0.6
+    s = x[1] + 1.0
+    L = np.sqrt(R * R - s * s)
+    lengths = np.diff(xs)
+    cand = np.nonzero((xs[1:] > x[0] - L) & (xs[:-1] < x[0] + L))[0]
+    assert lengths[cand].max() > 5 * lengths[cand].min()
+    for e in (cand[0], cand[len(cand) // 2], cand[-1]):
+        h = np.zeros(nv)
+        h[e] = 1.0
+        pr = oracle.Problem(vert=vert, elem=elem, data_kind="field", field=np.zeros(10), eps=1e-3,
+                            neumann=neumann, neumann_h=h)
+        m, se = _step_mean(pr, x, R, 20000)
+        lo, hi = max(xs[e], x[0] - L), min(xs[e + 1], x[0] + L)
+        want = quad(lambda q: _green(2, np.hypot(s, q - x[0]), R), lo, hi)[0]
+        assert abs(m - want) <= Z * se, (e, lengths[e], m, se, want)
