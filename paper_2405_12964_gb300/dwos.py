@@ -233,16 +233,24 @@ class Solver:
         c = (ctypes.c_double * 10)(*[float(x) for x in np.asarray(coeffs, dtype=np.float64).reshape(-1)[:10]])
         self._check(lib().dwos_set_dirichlet_field(self._h, c))
 
+    def _per_element(self, a, dtype, tdtype):
+        """One value per element of the current boundary, on the device (the C
+        side reads n_elem of them)."""
+        arr = a.reshape(-1) if torch.is_tensor(a) else np.asarray(a, dtype=dtype).reshape(-1)
+        if arr.shape[0] != getattr(self, "n_elem", 0):
+            raise ValueError(f"expected {getattr(self, 'n_elem', 0)} per-element values, got {arr.shape[0]}")
+        return self._dev(arr, tdtype)
+
     def set_neumann(self, flags):
-        """dwos_set_neumann: per-element flags, 1 = reflecting Neumann element (None: all Dirichlet)."""
+        """dwos_set_neumann: per-element flags, 1 = Neumann element (None: all Dirichlet)."""
         self._stream()
-        ft = None if flags is None else self._dev(np.asarray(flags, dtype=np.int32), torch.int32)
+        ft = None if flags is None else self._per_element(flags, np.int32, torch.int32)
         self._check(lib().dwos_set_neumann(self._h, _ptr(ft), MEM_DEVICE))
 
     def set_neumann_data(self, h):
         """dwos_set_neumann_data: per-element Neumann data du/dn, n out of the domain (None: zero)."""
         self._stream()
-        ht = None if h is None else self._dev(np.asarray(h, dtype=np.float32), torch.float32)
+        ht = None if h is None else self._per_element(h, np.float32, torch.float32)
         self._check(lib().dwos_set_neumann_data(self._h, _ptr(ht), MEM_DEVICE))
 
     def set_pde(self, sigma: float, f: float = 0.0):
