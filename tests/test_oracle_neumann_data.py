@@ -13,7 +13,9 @@ so the data reaches du/dtheta only through the nested walks).
   face from below, behind the side from a point on it); and, on a side cut into
   segments of very different lengths with data on one segment only, the
   draw's probability proportional to each candidate's length (a uniform mesh
-  would pass any draw).
+  would pass any draw); in 3D the same with data on the icosphere's largest
+  and smallest triangle (areas 1.6x apart; a uniform draw misses the smaller
+  by 4.7 SE).
 * The data only adds to the estimate: the walks' paths do not depend on it,
   and each walk's u and udot are affine in it (superposition of two data sets).
 * Whole walks against closed forms: u = b x + c (y^2 - x^2) on a square and
@@ -231,3 +233,34 @@ def test_one_step_draws_elements_in_proportion_to_their_length():
         lo, hi = max(xs[e], x[0] - L), min(xs[e + 1], x[0] + L)
         want = quad(lambda q: _green(2, np.hypot(s, q - x[0]), R), lo, hi)[0]
         assert abs(m - want) <= Z * se, (e, lengths[e], m, se, want)
+
+
+def test_one_step_draws_triangles_in_proportion_to_their_area():
+    # 3D: the icosphere's triangles differ in area; data 1 on one triangle, x at 0.1 above its
+    # centroid along its normal (it sees the whole triangle): the mean of the step's sample is
+    # the integral of G_R over that triangle, which needs the draw proportional to area and
+    # uniform points on the triangle
+    from scipy.integrate import dblquad
+    sc = scenes.sphere_flow_scene(n_query=2)
+    v, el = sc.vert, sc.elem
+    sph = np.nonzero(sc.neumann == 1)[0]
+    a, b, c = v[el[sph, 0]], v[el[sph, 1]], v[el[sph, 2]]
+    area = 0.5 * np.linalg.norm(np.cross(b - a, c - a), axis=1)
+    assert area.max() > 1.5 * area.min()
+    R = 0.3
+    for t in (sph[np.argmax(area)], sph[np.argmin(area)]):
+        A, B, C = v[el[t]]
+        nrm = np.cross(B - A, C - A)
+        nrm /= np.linalg.norm(nrm)
+        cen = (A + B + C) / 3
+        if np.dot(nrm, cen) < 0:
+            nrm = -nrm                                    # away from the sphere's centre
+        x = cen + 0.1 * nrm
+        h = np.zeros(len(el))
+        h[t] = 1.0
+        pr = to_oracle(sc, neumann_h=h)
+        m, se = _step_mean(pr, x, R, 20000)
+        jac = 2 * 0.5 * np.linalg.norm(np.cross(B - A, C - A))
+        want = dblquad(lambda w, u: _green(3, np.linalg.norm(A + u * (B - A) + w * (C - A) - x), R) * jac,
+                       0, 1, 0, lambda u: 1 - u)[0]
+        assert abs(m - want) <= Z * se, (t, m, se, want)
