@@ -15,7 +15,8 @@ so the data reaches du/dtheta only through the nested walks).
   draw's probability proportional to each candidate's length (a uniform mesh
   would pass any draw); in 3D the same with data on the icosphere's largest
   and smallest triangle (areas 1.6x apart; a uniform draw misses the smaller
-  by 4.7 SE).
+  by 4.7 SE); with screening (sigma = 4) the sample follows the screened ball's
+  Green's function in 2D and 3D, far from the Laplace one.
 * The data only adds to the estimate: the walks' paths do not depend on it,
   and each walk's u and udot are affine in it (superposition of two data sets).
 * Whole walks against closed forms: u = b x + c (y^2 - x^2) on a square and
@@ -264,3 +265,24 @@ def test_one_step_draws_triangles_in_proportion_to_their_area():
         want = dblquad(lambda w, u: _green(3, np.linalg.norm(A + u * (B - A) + w * (C - A) - x), R) * jac,
                        0, 1, 0, lambda u: 1 - u)[0]
         assert abs(m - want) <= Z * se, (t, m, se, want)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_one_step_uses_the_screened_green_function(dim):
+    # sigma = 4: the sample weighs by the screened ball's Green's function (the oracle's source
+    # weight over the ball's volume, pinned to its flux elsewhere), not the Laplace one
+    sigma, R, s = 4.0, 0.5, 0.2
+    sc = scenes.neumann_data_box_scene(dim, c=0.5)
+    sc.sigma = sigma
+    pr = to_oracle(sc)
+    x = [0.1, -1 + s, 0.05][:dim]
+    vol = np.pi * R * R if dim == 2 else 4.0 / 3.0 * np.pi * R ** 3
+    G = lambda t, sg: oracle.source_weight(dim, sg, R, t / R) / vol
+    L = np.sqrt(R * R - s * s)
+    if dim == 2:
+        want, lap = (quad(lambda q: G(np.hypot(s, q), sg), -L, L)[0] for sg in (sigma, 0.0))
+    else:
+        want, lap = (quad(lambda r: G(np.hypot(s, r), sg) * 2 * np.pi * r, 0, L)[0] for sg in (sigma, 0.0))
+    m, se = _step_mean(pr, x, R, 40000)
+    assert abs(lap - want) > 4 * Z * se
+    assert abs(m - want) <= Z * se, (m, se, want, lap)
